@@ -1,0 +1,76 @@
+"""Pins of the oracle's energy and topological charge: exact energies of
+uniform states (including the cube demag factor 1/3 by symmetry), the
+charge of a Neel skyrmion against the lattice solid-angle charge, and
+invariances."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.constants import MU0
+from oracle.demag import demag_spectrum
+from oracle.fields import Problem
+from oracle.observables import energy, topological_charge, topological_charge_bl
+
+
+def test_uniform_state_energies():
+    n = 5
+    grid = W.Grid(n, n, n, 2e-9, 2e-9, 2e-9)
+    Ms, Ku = 7e5, 3e5
+    u = np.array([0.0, 0.6, 0.8])
+    B = np.array([0.01, -0.02, 0.03])
+    p = Problem.from_workload(grid, W.Material(Ms=Ms, A=1.3e-11, alpha=0.1, Ku1=Ku, u=tuple(u), D=2e-3), B_ext=tuple(B))
+    mv = np.array([1.0, 0.0, 0.0])
+    m = np.broadcast_to(mv[:, None, None, None], (3, n, n, n)).copy()
+    E = energy(m, p, demag_spectrum(p.shape, p.d))
+    V = grid.dx * grid.dy * grid.dz
+    N = n ** 3
+    assert E["exchange"] == 0.0
+    assert abs(E["anisotropy"] - (-Ku * np.dot(mv, u) ** 2 * V * N)) < 1e-12 * Ku * V * N
+    assert abs(E["zeeman"] - (-Ms * np.dot(mv, B) * V * N)) < 1e-12 * Ms * V * N
+    # cube: body-averaged demag factor is exactly 1/3 along any axis
+    assert abs(E["demag"] - 0.5 * MU0 * Ms ** 2 * V * N / 3) < 1e-10 * MU0 * Ms ** 2 * V * N
+    assert abs(E["total"] - sum(v for k, v in E.items() if k != "total")) < 1e-20
+
+
+def _neel_skyrmion(grid, R, w, pol=-1):
+    x = (np.arange(grid.nx) - grid.nx / 2 + 0.5) * grid.dx
+    y = (np.arange(grid.ny) - grid.ny / 2 + 0.5) * grid.dy
+    X, Y = np.meshgrid(x, y)
+    r = np.hypot(X, Y)
+    # theta(r): pi at the centre, 0 far away (domain-wall profile at radius R)
+    th = 2 * np.arctan(np.exp(-(r - R) / w))
+    ph = np.arctan2(Y, X)
+    m = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+    if pol > 0:
+        m[2] *= -1
+        m[:2] *= 1
+    return m[:, None, :, :]
+
+
+def test_skyrmion_charge_is_minus_one():
+    for n in (64, 128):
+        grid = W.Grid(n, n, 1, 1e-9 * 64 / n, 1e-9 * 64 / n, 1e-9)
+        p = Problem.from_workload(grid, W.Material(Ms=5.8e5, A=1.5e-11, alpha=0.1))
+        m = _neel_skyrmion(grid, R=12e-9, w=3e-9)
+        Q = topological_charge(m, p)
+        Qbl = topological_charge_bl(m, p)
+        assert abs(Qbl - round(Qbl)) < 1e-3 and round(Qbl) == -1
+        assert abs(Q + 1) < (0.02 if n == 64 else 0.006)
+    # O(h^2) convergence of the finite-difference density
+
+
+def test_charge_zero_for_uniform_and_rotation_invariant():
+    grid = W.Grid(48, 48, 2, 1e-9, 1e-9, 1e-9)
+    p = Problem.from_workload(grid, W.Material(Ms=5.8e5, A=1.5e-11, alpha=0.1))
+    m = np.zeros((3,) + p.shape)
+    m[2] = 1
+    assert topological_charge(m, p) == 0.0
+    sk = _neel_skyrmion(W.Grid(48, 48, 1, 1e-9, 1e-9, 1e-9), R=8e-9, w=2e-9)
+    m = np.concatenate([sk, sk], axis=1)
+    Q = topological_charge(m, p)
+    a = 0.7
+    Rz = np.array([[math.cos(a), -math.sin(a), 0], [math.sin(a), math.cos(a), 0], [0, 0, 1]])
+    mr = np.einsum("ab,bkji->akji", Rz, m)
+    assert abs(topological_charge(mr, p) - Q) < 1e-12
