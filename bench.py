@@ -1,0 +1,315 @@
+"""Throughput benchmark of the LLG hot path on GB300.
+
+Metric: LLG cell-steps/s (cells x accepted integrator steps per second).
+Workload (single GPU): 256x256x16 cells of 2 nm, Ms 5.8e5, A 1.5e-11,
+Ku 8e5 along z, interfacial DMI 3e-3, alpha 0.1, seeded random unit
+vectors, FP32 Dormand-Prince RK45 (rtol 1e-6, device-side controller) with
+exact FFT demag on the 512x512x32 padded grid.  One step = one accepted
+RK45 step (6 field evaluations, each exchange+DMI+anisotropy+demag, plus
+the stage, error and controller kernels).
+
+Multi-GPU: replicas only (independent runs of the same workload per rank,
+no data-path collective); value = sum of cell-steps over ranks / max time.
+
+--impl reference times the FP64 CPU oracle (the only reference available:
+the paper ships no code) on the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "LLG cell-steps/s: plain FP32 vs batched/surrogate, at stated error vs FP64 oracle"
+UNIT = "cell-steps/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([v.strip() for v in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if len(r) >= 7 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 7 and r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for q, n in enumerate(names):
+                if len(r) >= 7 and r[3 + q].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _traffic_for(kernel: str):
+    """ncu DRAM bytes per launch recorded in profiles/traffic.json, valid only
+    while the kernel sources still hash to the recorded value."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(os.path.join(ROOT, "paper_2608_15253_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_2608_15253_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    if rec.get("csrc_sha256") != h.hexdigest():
+        return None
+    ent = rec.get("kernels", {}).get(kernel)
+    return ent.get("dram_bytes_per_launch") if ent else None
+
+
+def cpu_baseline(seconds_budget=60.0):
+    """The FP64 oracle as it stands on this host's cores: RK45 steps of the
+    same 256x256x16 workload (setup excluded), bounded to about a minute."""
+    from oracle.demag import demag_spectrum
+    from oracle.fields import Problem
+    from oracle.llg import Solver
+    w = W.dmi_256x256x16()
+    p = Problem.from_workload(w.grid, w.mat)
+    K = demag_spectrum(p.shape, p.d)
+    s = Solver(p, W.m_random_sphere(w.grid, seed=2), K_hat=K, dt=1e-14, rtol=1e-6)
+    s.k1 = s.slope(s.m)
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        s.rk45_step_fixed(1e-14)
+        done += 1
+        el = time.perf_counter() - t0
+        if el > seconds_budget / 3 or done >= 3:
+            break
+    return {"value": w.grid.n * done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} RK45 step(s) of the 256x256x16 workload (numpy FP64, single-threaded "
+                      f"FFT and array ops; Newell/FFT setup excluded), {el:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    w = W.dmi_256x256x16()
+    from oracle.demag import demag_spectrum
+    from oracle.fields import Problem
+    from oracle.llg import Solver
+    p = Problem.from_workload(w.grid, w.mat)
+    K = demag_spectrum(p.shape, p.d)
+    s = Solver(p, W.m_random_sphere(w.grid, seed=2), K_hat=K, dt=1e-14, rtol=1e-6)
+    s.k1 = s.slope(s.m)
+    # each "step" is one full RK45 step; the count is bounded so the run ends in minutes
+    warm = min(args.warmup, 1)
+    timed = max(1, min(args.steps, 4))
+    for _ in range(warm):
+        s.rk45_step_fixed(1e-14)
+    t0 = time.perf_counter()
+    for _ in range(timed):
+        s.rk45_step_fixed(1e-14)
+    el = time.perf_counter() - t0
+    val = w.grid.n * timed / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws, "steps": timed,
+        "warmup": warm, "ms_per_step": 1e3 * el / timed, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "cells": w.grid.n, "grid": [256, 256, 16], "integrator": "rk45",
+                   "precision": "fp64-cpu-oracle"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{timed} RK45 step(s) of the full workload after {warm} warm-up step(s)"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    import paper_2608_15253_gb300 as mm
+    if not os.path.exists(mm.lib_path):
+        from paper_2608_15253_gb300 import build as B
+        B.build()
+    w = W.dmi_256x256x16()
+    g = w.grid
+    M = mm.Material(w.mat.Ms, w.mat.A, w.mat.alpha, w.mat.Ku1, w.mat.u, w.mat.D)
+    cfg = mm.make_config(precision=32, integrator=mm.MM_RK45, demag=mm.MM_DEMAG_EXACT, dt=1e-14, rtol=w.rtol)
+    ctx = mm.mm_create(mm.make_grid(g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), M.s, cfg)
+    stream = torch.cuda.current_stream()
+    mm.mm_set_stream(ctx, stream.cuda_stream)
+    m0 = W.m_random_sphere(g, seed=2 + rank)
+    mm.mm_set_m(ctx, 0, m0)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    mm.mm_step(ctx, args.warmup)
+    torch.cuda.synchronize()
+    s0 = mm.mm_get_stats(ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        mm.mm_step(ctx, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    s1 = mm.mm_get_stats(ctx)
+    steps = s1["accepted"] - s0["accepted"]
+    attempts = s1["attempts"] - s0["attempts"]
+    launches = s1["kernel_launches"] - s0["kernel_launches"]
+    t_max = ms
+    total_cells_steps = g.n * steps
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+        c = torch.tensor([float(total_cells_steps)], device="cuda")
+        torch.distributed.all_reduce(c)
+        total_cells_steps = float(c.item())
+    value = total_cells_steps / (t_max * 1e-3)
+
+    # per-kernel CUDA-event timing of the same kind of steps (graphs bypassed)
+    mm.mm_set_profiling(ctx, True)
+    mm.mm_step(ctx, max(2, min(args.steps, 5)))
+    prof = mm.mm_get_profile(ctx)
+    mm.mm_set_profiling(ctx, False)
+    tot = sum(p["total_ms"] for p in prof) or 1.0
+    dom = max(prof, key=lambda p: p["total_ms"])
+    avg_ms = dom["total_ms"] / max(1, dom["launches"])
+    achieved = dom["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    kernels = {p["name"]: {"launches": p["launches"], "share": round(p["total_ms"] / tot, 4),
+                           "avg_us": round(1e3 * p["total_ms"] / max(1, p["launches"]), 2),
+                           "GBps": round(p["bytes_per_launch"] / (p["total_ms"] / max(1, p["launches"]) * 1e-3) / 1e9, 1)
+                           if p["bytes_per_launch"] > 0 else None}
+               for p in sorted(prof, key=lambda p: -p["total_ms"])}
+
+    # end to end through the C ABI with host buffers: every step uploads the
+    # state from host memory and reads the new state back
+    k_e2e = max(1, min(args.steps, 10))
+    mh = mm.mm_get_m(ctx, 0, m0.shape)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        mm.mm_set_m(ctx, 0, mh)
+        mm.mm_step(ctx, 1)
+        mh = mm.mm_get_m(ctx, 0, m0.shape)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = g.n * k_e2e / e2e_s * ws
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / max(1, steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "cells": g.n, "grid": [g.nx, g.ny, g.nz], "cell_nm": [2, 2, 2],
+                   "integrator": "rk45-dopri5", "rtol": w.rtol, "demag": "exact-fft 512x512x32",
+                   "precision": "fp32 (fp64 Newell setup)", "parallelism": f"replicas x{ws}",
+                   "accepted_steps": steps, "attempts": attempts,
+                   "l2": "working set ~220 MB > 126 MB L2 (state, 7 slopes, spectrum, tensor)"},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1), "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": _traffic_for(dom["name"]), "algorithmic_bytes_per_launch": dom["bytes_per_launch"],
+                     "avg_launch_us": round(1e3 * avg_ms, 2)},
+        "kernels": kernels,
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 3 * g.n * 4,
+                "d2h_bytes_per_step": 3 * g.n * 4, "steps": k_e2e},
+    }
+    mm.mm_destroy(ctx)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

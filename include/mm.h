@@ -1,0 +1,240 @@
+/*
+ * mm.h — C ABI of the GB300 (sm_103a) micromagnetic LLG hot path.
+ *
+ * What the library computes (arxiv 2608.15253, Methods):
+ *  - "Physics and discretization", Eq. 1: the Landau-Lifshitz-Gilbert
+ *    equation dm/dt = -gamma' mu0 m x H - gamma' alpha mu0 m x (m x H),
+ *    gamma' = gamma0/(1+alpha^2), on a structured x-fastest finite-difference
+ *    grid; H sums six-point exchange (Neumann or periodic), interfacial DMI
+ *    with the free edge condition at grid and mask edges, uniaxial
+ *    anisotropy, Zeeman, the stochastic thermal field and open-boundary
+ *    demagnetisation (FFT convolution with the Newell tensor zero-padded to
+ *    2N); spin-orbit, Slonczewski and Zhang-Li torques are added per stage.
+ *  - "Integrators": Heun (stochastic LLG, Stratonovich) and RK45
+ *    Dormand-Prince (adaptive, first-same-as-last), |m| renormalised.
+ *  - "Replica batching": R independent replicas, replica-outermost /
+ *    component-major / x-fastest state, per-replica J, T and Philox seeds.
+ *
+ * Conventions for every call:
+ *  - SI units: metres, A/m for Ms, J/m for A, J/m^3 for Ku1, J/m^2 for D,
+ *    tesla for applied fields, kelvin, A/m^2 for current density, seconds.
+ *  - Vector fields on the host are float64, component-major and x-fastest:
+ *    v[c*N + (z*ny + y)*nx + x], N = nx*ny*nz of that replica.
+ *  - Host arrays passed in are copied before the call returns; the caller
+ *    keeps ownership and the library never keeps a caller pointer.  Output
+ *    arrays are caller-allocated.
+ *  - Every call returns mm_status; MM_OK is 0.  On error the context stays
+ *    valid and destroyable; mm_last_error() describes the last failure.
+ *  - A context is not thread-safe.  Its precision is fixed at creation.
+ *  - Device work runs on the context's stream (mm_set_stream); calls that
+ *    return host data synchronise that stream.
+ */
+#ifndef MM_H
+#define MM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MM_API __attribute__((visibility("default")))
+
+typedef struct mm_ctx mm_ctx;
+
+typedef enum mm_status {
+    MM_OK = 0,
+    MM_ERR_ARG = 1,           /* invalid argument (message in mm_last_error) */
+    MM_ERR_DEVICE = 2,        /* no sm_103 device, or kernel image does not match */
+    MM_ERR_OOM = 3,           /* device allocation failed */
+    MM_ERR_CUDA = 4,          /* any other CUDA runtime error */
+    MM_ERR_NONFINITE = 5,     /* NaN/Inf detected in the state or the error norm */
+    MM_ERR_DT_UNDERFLOW = 6,  /* RK45 step fell below dt_min */
+    MM_ERR_TIMEOUT = 7,       /* a bounded device wait ran out */
+    MM_ERR_STATE = 8          /* call not valid in the current state */
+} mm_status;
+
+enum mm_integrator { MM_HEUN = 0, MM_RK45 = 1 };
+enum mm_demag_mode { MM_DEMAG_OFF = 0, MM_DEMAG_EXACT = 1, MM_DEMAG_SURROGATE = 2 };
+
+/* Effective-field terms (bit mask). */
+enum mm_term {
+    MM_TERM_EXCHANGE = 1,
+    MM_TERM_DMI = 2,
+    MM_TERM_ANISOTROPY = 4,
+    MM_TERM_ZEEMAN = 8,
+    MM_TERM_DEMAG = 16,
+    MM_TERM_THERMAL = 32,
+    MM_TERM_ALL = 63
+};
+
+/* Energy array layout returned by mm_energy. */
+enum mm_energy_index { MM_E_EXCHANGE = 0, MM_E_DMI = 1, MM_E_ANISOTROPY = 2, MM_E_ZEEMAN = 3,
+                       MM_E_DEMAG = 4, MM_E_TOTAL = 5, MM_NENERGY = 6 };
+
+enum mm_torque_kind { MM_TORQUE_NONE = 0, MM_TORQUE_SOT = 1, MM_TORQUE_STT = 2, MM_TORQUE_ZL = 3 };
+
+/* Grid of one replica: nx*ny*nz cells of dx*dy*dz metres; pbc[d] != 0 makes
+ * axis d periodic for the local (exchange/DMI/Zhang-Li) stencils. */
+typedef struct mm_grid {
+    int nx, ny, nz;
+    double dx, dy, dz;
+    int pbc[3];
+} mm_grid;
+
+/* Material.  Scalars apply to every cell unless the matching per-cell host
+ * array (length N; u_cell 3N component-major) is non-NULL.  Cells with
+ * Ms = 0 are absent (the geometry mask).  At most 256 distinct parameter
+ * tuples per context (they become material regions). */
+typedef struct mm_material {
+    double Ms, A, alpha, Ku1, u[3], D;
+    const double *Ms_cell, *A_cell, *alpha_cell, *Ku1_cell, *u_cell, *D_cell;
+} mm_material;
+
+typedef struct mm_config {
+    int precision;            /* 32 or 64: arithmetic of the state, fields, FFTs */
+    int integrator;           /* MM_HEUN or MM_RK45 */
+    int demag;                /* mm_demag_mode */
+    unsigned terms;           /* mm_term mask of the effective field; 0 means all */
+    double dt;                /* Heun step; RK45 initial step (s) */
+    double rtol;              /* RK45: accept when max_cell |m5 - m4| <= rtol */
+    double dt_min, dt_max;    /* RK45 step bounds (s); 0 selects 1e-20 / 1e-11 */
+    double T;                 /* temperature (K) of every replica (Heun only) */
+    uint64_t seed;            /* base Philox seed; replica r uses splitmix64(seed + r) */
+} mm_config;
+
+/* Spin-torque parameters (Methods: torques added per integrator stage).
+ * Landau-Lifshitz form with damping-like h_DL and field-like h_FL along p:
+ *   tau = -gamma' mu0 [(h_DL + alpha h_FL) m x (m x p) + (h_FL - alpha h_DL) m x p]
+ *  SOT: h_DL = theta_SH hbar J / (2 e mu0 Ms t_F), h_FL = fl_ratio * h_DL
+ *  STT: h_DL = eps(m) hbar J / (e mu0 Ms t_F), h_FL = eps_prime hbar J / (e mu0 Ms t_F),
+ *       eps = P Lambda^2 / ((Lambda^2 + 1) + (Lambda^2 - 1) m.p)
+ *  ZL:  u = J P mu_B / (e Ms) along dir (divided by 1 + xi^2 when match_mumax),
+ *       tau = [-(1 + alpha xi) m x (m x (u.grad)m) - (xi - alpha) m x (u.grad)m] / (1 + alpha^2)
+ * t_F <= 0 selects nz * dz. */
+typedef struct mm_torque {
+    int kind;                 /* mm_torque_kind */
+    double p[3];
+    double theta_SH, fl_ratio;
+    double P, Lambda, eps_prime;
+    double t_F;
+    double xi;
+    double dir[3];
+    int match_mumax;
+} mm_torque;
+
+typedef struct mm_stats {
+    long long accepted, rejected, attempts;
+    long long kernel_launches;  /* kernels of this library launched by the context */
+    double t, dt;
+} mm_stats;
+
+/* Per-kernel timing collected while profiling is on (mm_set_profiling). */
+typedef struct mm_profile_entry {
+    char name[32];
+    long long launches;
+    double total_ms;          /* sum of CUDA-event durations on the context stream */
+    double bytes_per_launch;  /* algorithmic bytes of one launch */
+} mm_profile_entry;
+
+/* Create a single-instance context (Methods, "Physics and discretization").
+ * Allocates device memory, validates the device (compute capability 10.3),
+ * computes the FP64 Newell tensor spectrum on the GPU when demag is on.
+ * m starts along +z.  Errors: MM_ERR_ARG (sizes <= 0, bad precision or
+ * integrator, RK45 with T > 0, > 256 materials), MM_ERR_DEVICE, MM_ERR_OOM. */
+MM_API mm_status mm_create(const mm_grid* grid, const mm_material* mat,
+                           const mm_config* cfg, mm_ctx** out);
+
+/* Create R replicas of possibly different grids sharing one material
+ * (Methods, "Replica batching"); seeds may be NULL (then splitmix64(seed+r)).
+ * Grids must be nz = 1 films when R > 1 and sizes differ. */
+MM_API mm_status mm_create_batch(int R, const mm_grid* grids, const mm_material* mat,
+                                 const mm_config* cfg, const uint64_t* seeds, mm_ctx** out);
+
+MM_API mm_status mm_destroy(mm_ctx* ctx);
+
+/* Run on a caller stream (cudaStream_t, e.g. torch's current stream); NULL
+ * returns to the context's own stream.  Cached CUDA graphs are rebuilt. */
+MM_API mm_status mm_set_stream(mm_ctx* ctx, void* stream);
+
+/* Set / read the magnetisation of one replica (host float64, 3N).  Input is
+ * renormalised per cell; absent cells are set to zero. */
+MM_API mm_status mm_set_m(mm_ctx* ctx, int replica, const double* m);
+MM_API mm_status mm_get_m(mm_ctx* ctx, int replica, double* m);
+
+/* Device-pointer variants over all replicas at once, in the context's
+ * precision (float or double), concatenated replica-outermost.  Ordered on
+ * the context stream; no host synchronisation. */
+MM_API mm_status mm_set_m_device(mm_ctx* ctx, const void* m_dev);
+MM_API mm_status mm_get_m_device(mm_ctx* ctx, void* m_dev);
+
+/* Applied field B (tesla): uniform B[3], or per cell (3N) when B_cell != NULL. */
+MM_API mm_status mm_set_field(mm_ctx* ctx, int replica, const double B[3], const double* B_cell);
+
+/* Temperature per replica (R values, kelvin). */
+MM_API mm_status mm_set_temperature(mm_ctx* ctx, const double* T);
+
+/* Spin torque of every replica; J holds R current densities (A/m^2). */
+MM_API mm_status mm_set_torque(mm_ctx* ctx, const mm_torque* tq, const double* J);
+
+/* Advance n steps: n Heun steps, or n accepted RK45 steps (rejected attempts
+ * are retried on the device; the step controller runs on the device). */
+MM_API mm_status mm_step(mm_ctx* ctx, long n);
+
+/* RK45 with a prescribed step sequence (no control, every step accepted):
+ * replays dts[0..n-1], e.g. the accepted steps of a reference run. */
+MM_API mm_status mm_step_dt(mm_ctx* ctx, const double* dts, long n);
+
+/* Advance to simulated time t_end; the last step is clipped to land on it. */
+MM_API mm_status mm_run(mm_ctx* ctx, double t_end);
+
+/* Effective field of the current state (A/m, host float64 3N) restricted to
+ * the terms in term_mask (MM_TERM_THERMAL uses the current step's noise). */
+MM_API mm_status mm_get_heff(mm_ctx* ctx, int replica, double* H, unsigned term_mask);
+
+/* Energy per term and total (joules): E[MM_NENERGY], FP64 compensated sums. */
+MM_API mm_status mm_energy(mm_ctx* ctx, int replica, double* E);
+
+/* Topological charge Q = (1/4pi) sum m.(dm/dx x dm/dy) dx dy of layer
+ * `layer`, or the mean over layers when layer < 0; FP64 compensated sum. */
+MM_API mm_status mm_topo_charge(mm_ctx* ctx, int replica, int layer, double* Q);
+
+MM_API mm_status mm_get_time(mm_ctx* ctx, int replica, double* t, double* dt, long long* steps);
+MM_API mm_status mm_get_stats(mm_ctx* ctx, mm_stats* st);
+
+/* Checkpoint: m, t, dt, step counters and seeds.  With buf == NULL the
+ * required size is returned in *nbytes. */
+MM_API mm_status mm_get_state(mm_ctx* ctx, void* buf, size_t* nbytes);
+MM_API mm_status mm_set_state(mm_ctx* ctx, const void* buf, size_t nbytes);
+
+/* Thermal noise of one replica at a given step counter: raw Philox4x32-10
+ * words (4N uint32, cell-major) and/or the thermal field (3N A/m) for the
+ * context's dt; either output may be NULL. */
+MM_API mm_status mm_get_thermal(mm_ctx* ctx, int replica, long long step,
+                                uint32_t* raw, double* H_th);
+
+/* Demagnetisation tensor spectrum in the stored form: n_out doubles of
+ * [ncomp][Pz/2+1][Py/2+1][Px/2+1] (ncomp 6: xx,yy,zz,xy,xz,yz; 4 when nz=1),
+ * scaled by -1/(Px Py Pz).  dims_out[0..3] = ncomp, Px, Py, Pz. */
+MM_API mm_status mm_get_demag_kernel(mm_ctx* ctx, double* out, size_t n_out, int* dims_out);
+
+/* FP64 Newell tensor evaluated on the GPU at count integer displacements
+ * ijk[3*q..3*q+2] of cells dx*dy*dz; out[6*q+c] in xx,yy,zz,xy,xz,yz. */
+MM_API mm_status mm_newell(long count, const int* ijk, double dx, double dy, double dz, double* out);
+
+/* Per-kernel CUDA-event timing (graphs are bypassed while on). */
+MM_API mm_status mm_set_profiling(mm_ctx* ctx, int on);
+MM_API mm_status mm_get_profile(mm_ctx* ctx, mm_profile_entry* out, int* n_inout);
+
+/* Host-side fault injection for tests: 1 = next allocation fails,
+ * 2 = poison the state with NaN at the next step, 3 = force dt underflow. */
+MM_API mm_status mm_debug_inject(mm_ctx* ctx, int fault);
+
+MM_API const char* mm_last_error(const mm_ctx* ctx);
+MM_API const char* mm_status_string(mm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MM_H */

@@ -12,6 +12,7 @@ Readings taken where the paper is silent:
  * exchange between two present cells uses the harmonic mean
    A_ij = 2 A_i A_j / (A_i + A_j) (mumax3's convention);
  * DMI uses the strength D_i of the cell where the field is evaluated;
+ * the uniaxial axis u is a direction and is normalised;
  * free-edge ghost value.  The paper prints the edge condition as
    dm/dn = (D/2A)(z x n) x m.  Written with the field sign the paper also
    uses (H_DMI = (2D/mu0 Ms)(dmz/dx, dmz/dy, -dmx/dx - dmy/dy)), the natural
@@ -67,6 +68,9 @@ class Problem:
         u = mat.cell.get("u")
         if u is None:
             u = np.broadcast_to(np.asarray(mat.u, dtype=np.float64)[:, None, None, None], (3,) + shape).copy()
+        # the anisotropy axis is a direction: normalised per cell
+        un = np.sqrt((np.asarray(u, dtype=np.float64) ** 2).sum(axis=0, keepdims=True))
+        u = np.asarray(u, dtype=np.float64) / np.where(un > 0, un, 1.0)
         B = np.asarray(B_ext, dtype=np.float64)
         if B.ndim == 1:
             B = np.broadcast_to(B[:, None, None, None], (3,) + shape).copy()

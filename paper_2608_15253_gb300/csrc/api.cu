@@ -1,0 +1,839 @@
+// C ABI of libmm (include/mm.h): context lifetime, material regions, state
+// transfer, stepping (chunks of integrator attempts replayed from CUDA
+// graphs), observables, checkpoints, profiling and host-side fault
+// injection.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "ctx.h"
+
+namespace mm {
+
+mm_status demag_kernel_copy(mm_ctx* c, double* out, size_t n_out, int* dims);
+
+static thread_local std::string g_create_error;
+
+mm_status set_error(mm_ctx* c, mm_status s, const std::string& msg) {
+    if (c) c->last_error = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+mm_status cuda_check(mm_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return MM_OK;
+    std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+    return set_error(c, e == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA, msg);
+}
+
+LaunchScope::LaunchScope(mm_ctx* cc, const char* name, double bytes) : c(cc), slot(-1) {
+    c->launches += 1;
+    if (!c->profiling) return;
+    for (size_t q = 0; q < c->prof.size(); ++q)
+        if (c->prof[q].name == name) slot = (int)q;
+    if (slot < 0) {
+        ProfileSlot p;
+        p.name = name;
+        c->prof.push_back(p);
+        slot = (int)c->prof.size() - 1;
+    }
+    c->prof[slot].bytes = bytes;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, c->stream);
+}
+
+LaunchScope::~LaunchScope() {
+    if (!c->profiling || slot < 0) return;
+    cudaEventRecord(e1, c->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    c->prof[slot].launches += 1;
+    c->prof[slot].total_ms += ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+}
+
+template <typename T>
+static Region<T> region_coeffs(const RegionHost& r, double /*V*/) {
+    Region<T> o{};
+    const bool present = r.Ms > 0;
+    const double imu = present ? 1.0 / (kMu0 * r.Ms) : 0.0;
+    o.present = present ? (T)1 : (T)0;
+    o.inv_mu0Ms = (T)imu;
+    o.Ms = (T)r.Ms;
+    o.cg = (T)(2.0 * r.A * imu);
+    o.ratio = r.A > 0 ? (T)(r.D / (2.0 * r.A)) : (T)0;
+    o.dmi = (T)(2.0 * r.D * imu);
+    o.ku = (T)(2.0 * r.Ku1 * imu);
+    double un = std::sqrt(r.u[0] * r.u[0] + r.u[1] * r.u[1] + r.u[2] * r.u[2]);
+    if (un == 0) un = 1;
+    o.ux = (T)(r.u[0] / un);
+    o.uy = (T)(r.u[1] / un);
+    o.uz = (T)(r.u[2] / un);
+    o.alpha = (T)r.alpha;
+    o.gm = (T)(kGamma0 * kMu0 / (1.0 + r.alpha * r.alpha));
+    o.sigma0 = present ? (T)std::sqrt(2.0 * r.alpha * kKB / (kMu0 * kMu0 * r.Ms * kGamma0)) : (T)0;
+    o.inv_Ms = present ? (T)(1.0 / r.Ms) : (T)0;
+    return o;
+}
+
+template <typename T>
+static mm_status upload_regions_t(mm_ctx* c) {
+    const int nr = c->nreg;
+    std::vector<Region<T>> lut(nr);
+    const double V = c->grid.dx * c->grid.dy * c->grid.dz;
+    for (int q = 0; q < nr; ++q) lut[q] = region_coeffs<T>(c->regions[q], V);
+    std::vector<T> cp((size_t)nr * nr);
+    for (int a = 0; a < nr; ++a)
+        for (int b = 0; b < nr; ++b) {
+            const double Aa = c->regions[a].A, Ab = c->regions[b].A;
+            const double Aij = (Aa + Ab > 0) ? 2.0 * Aa * Ab / (Aa + Ab) : 0.0;
+            const double imu = c->regions[a].Ms > 0 ? 1.0 / (kMu0 * c->regions[a].Ms) : 0.0;
+            cp[(size_t)a * nr + b] = (T)(2.0 * Aij * imu);
+        }
+    cudaError_t e = cudaMalloc(&c->d_lut, sizeof(Region<T>) * nr);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_cpair, sizeof(T) * nr * nr);
+    if (e != cudaSuccess) return cuda_check(c, e, "material tables");
+    cudaMemcpy(c->d_lut, lut.data(), sizeof(Region<T>) * nr, cudaMemcpyHostToDevice);
+    cudaMemcpy(c->d_cpair, cp.data(), sizeof(T) * nr * nr, cudaMemcpyHostToDevice);
+    if (!c->uniform) {
+        e = cudaMalloc(&c->d_region, c->N);
+        if (e != cudaSuccess) return cuda_check(c, e, "region map");
+        cudaMemcpy(c->d_region, c->region_of_cell.data(), c->N, cudaMemcpyHostToDevice);
+    }
+    return MM_OK;
+}
+
+static mm_status build_regions(mm_ctx* c, const mm_material* mat) {
+    const long long N = c->N;
+    const bool percell = mat->Ms_cell || mat->A_cell || mat->alpha_cell || mat->Ku1_cell || mat->u_cell || mat->D_cell;
+    RegionHost base{mat->Ms, mat->A, mat->alpha, mat->Ku1, {mat->u[0], mat->u[1], mat->u[2]}, mat->D};
+    c->regions.clear();
+    if (!percell) {
+        c->regions.push_back(base);
+        c->nreg = 1;
+        c->uniform = base.Ms > 0 ? 1 : 0;
+        if (!c->uniform) c->region_of_cell.assign(N, 0);
+        return MM_OK;
+    }
+    c->region_of_cell.resize(N);
+    for (long long i = 0; i < N; ++i) {
+        RegionHost r = base;
+        if (mat->Ms_cell) r.Ms = mat->Ms_cell[i];
+        if (mat->A_cell) r.A = mat->A_cell[i];
+        if (mat->alpha_cell) r.alpha = mat->alpha_cell[i];
+        if (mat->Ku1_cell) r.Ku1 = mat->Ku1_cell[i];
+        if (mat->D_cell) r.D = mat->D_cell[i];
+        if (mat->u_cell) { r.u[0] = mat->u_cell[i]; r.u[1] = mat->u_cell[N + i]; r.u[2] = mat->u_cell[2 * N + i]; }
+        if (!(r.Ms >= 0) || !(r.A >= 0) || !(r.alpha >= 0))
+            return set_error(c, MM_ERR_ARG, "per-cell Ms, A and alpha must be non-negative");
+        int found = -1;
+        for (size_t q = 0; q < c->regions.size(); ++q)
+            if (c->regions[q] == r) { found = (int)q; break; }
+        if (found < 0) {
+            if ((int)c->regions.size() >= kMaxRegions)
+                return set_error(c, MM_ERR_ARG, "more than 256 distinct per-cell material tuples");
+            c->regions.push_back(r);
+            found = (int)c->regions.size() - 1;
+        }
+        c->region_of_cell[i] = (uint8_t)found;
+    }
+    c->nreg = (int)c->regions.size();
+    c->uniform = (c->nreg == 1 && c->regions[0].Ms > 0) ? 1 : 0;
+    return MM_OK;
+}
+
+static void invalidate_graph(mm_ctx* c) {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    c->graph_chunk = 0;
+}
+
+static mm_status sync_state(mm_ctx* c) {
+    cudaError_t e = cudaMemcpyAsync(&c->h_state, c->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_check(c, e, "state readback");
+}
+
+static mm_status push_state(mm_ctx* c) {
+    cudaError_t e = cudaMemcpyAsync(c->d_state, &c->h_state, sizeof(DevState), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_check(c, e, "state upload");
+}
+
+static mm_status status_from_device(mm_ctx* c) {
+    if (c->h_state.status == MM_ERR_DT_UNDERFLOW) return set_error(c, MM_ERR_DT_UNDERFLOW, "RK45 step fell below dt_min");
+    if (c->h_state.status == MM_ERR_NONFINITE) return set_error(c, MM_ERR_NONFINITE, "non-finite value in the state");
+    return MM_OK;
+}
+
+static void free_all(mm_ctx* c) {
+    invalidate_graph(c);
+    demag_free(c);
+    void* bufs[] = {c->d_region, c->d_lut, c->d_cpair, c->d_m, c->d_mtmp, c->d_kslot, c->d_hd, c->d_hbuf,
+                    c->d_bcell, c->d_state, c->d_replay, c->d_red};
+    for (void* b : bufs) cudaFree(b);
+    for (auto& k : c->d_k) cudaFree(k);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+}
+
+static mm_status alloc(mm_ctx* c, void** p, size_t bytes, const char* what) {
+    if (c->inject == 1) {
+        c->inject = 0;
+        return set_error(c, MM_ERR_OOM, std::string("injected allocation failure: ") + what);
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return cuda_check(c, e, what);
+    return MM_OK;
+}
+
+static mm_status check_device(mm_ctx* c) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_error(c, MM_ERR_DEVICE, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    cudaDeviceProp p;
+    e = cudaGetDeviceProperties(&p, dev);
+    if (e != cudaSuccess) return set_error(c, MM_ERR_DEVICE, cudaGetErrorString(e));
+    if (!(p.major == 10 && p.minor == 3))
+        return set_error(c, MM_ERR_DEVICE, "libmm is built for sm_103a (GB300); found compute capability " +
+                                               std::to_string(p.major) + "." + std::to_string(p.minor));
+    return MM_OK;
+}
+
+static uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+template <typename T>
+static void host_to_state(const double* m, long long N, const std::vector<uint8_t>& reg,
+                          const std::vector<RegionHost>& regions, int uniform, std::vector<T>& out) {
+    out.resize(3 * N);
+    for (long long i = 0; i < N; ++i) {
+        const bool present = uniform ? true : regions[reg[i]].Ms > 0;
+        double x = m[i], y = m[N + i], z = m[2 * N + i];
+        const double n = std::sqrt(x * x + y * y + z * z);
+        if (!present || n == 0) x = y = z = 0;
+        else { x /= n; y /= n; z /= n; }
+        out[i] = (T)x; out[N + i] = (T)y; out[2 * N + i] = (T)z;
+    }
+}
+
+}  // namespace mm
+
+using namespace mm;
+
+extern "C" {
+
+const char* mm_status_string(mm_status s) {
+    switch (s) {
+        case MM_OK: return "ok";
+        case MM_ERR_ARG: return "invalid argument";
+        case MM_ERR_DEVICE: return "unsupported device";
+        case MM_ERR_OOM: return "out of device memory";
+        case MM_ERR_CUDA: return "CUDA error";
+        case MM_ERR_NONFINITE: return "non-finite state";
+        case MM_ERR_DT_UNDERFLOW: return "time step underflow";
+        case MM_ERR_TIMEOUT: return "device wait timed out";
+        case MM_ERR_STATE: return "invalid state";
+    }
+    return "unknown";
+}
+
+const char* mm_last_error(const mm_ctx* c) { return c ? c->last_error.c_str() : g_create_error.c_str(); }
+
+mm_status mm_create(const mm_grid* grid, const mm_material* mat, const mm_config* cfg, mm_ctx** out) {
+    if (!grid || !mat || !cfg || !out) return set_error(nullptr, MM_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (grid->nx <= 0 || grid->ny <= 0 || grid->nz <= 0 || !(grid->dx > 0) || !(grid->dy > 0) || !(grid->dz > 0))
+        return set_error(nullptr, MM_ERR_ARG, "grid sizes and cell edges must be positive");
+    if (cfg->precision != 32 && cfg->precision != 64) return set_error(nullptr, MM_ERR_ARG, "precision must be 32 or 64");
+    if (cfg->integrator != MM_HEUN && cfg->integrator != MM_RK45) return set_error(nullptr, MM_ERR_ARG, "bad integrator");
+    if (cfg->integrator == MM_RK45 && cfg->T > 0)
+        return set_error(nullptr, MM_ERR_ARG, "RK45 with T > 0: adaptive stepping of white noise is not defined; use Heun");
+    if (cfg->demag == MM_DEMAG_SURROGATE) return set_error(nullptr, MM_ERR_ARG, "surrogate demag needs mm_surrogate_*");
+    if (cfg->demag == MM_DEMAG_EXACT && (grid->pbc[0] || grid->pbc[1] || grid->pbc[2]))
+        return set_error(nullptr, MM_ERR_ARG, "periodic boundaries apply to the local terms only; turn demag off");
+    if (!(cfg->dt > 0)) return set_error(nullptr, MM_ERR_ARG, "dt must be positive");
+    mm_ctx* c = new mm_ctx();
+    mm_status s = check_device(c);
+    if (s != MM_OK) {
+        g_create_error = c->last_error;
+        delete c;
+        return s;
+    }
+    c->prec = cfg->precision;
+    c->esz = c->prec == 32 ? 4 : 8;
+    c->integrator = cfg->integrator;
+    c->terms = cfg->terms ? cfg->terms : MM_TERM_ALL;
+    if (cfg->demag != MM_DEMAG_EXACT) c->terms &= ~MM_TERM_DEMAG;
+    c->grid = *grid;
+    c->N = (long long)grid->nx * grid->ny * grid->nz;
+    c->cfg = *cfg;
+    c->Tr = cfg->T;
+    c->seed = splitmix64(cfg->seed);
+    const long long N = c->N;
+    cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
+    c->stream = c->own_stream;
+#define TRY(x) do { mm_status _s = (x); if (_s != MM_OK) { g_create_error = c->last_error; free_all(c); delete c; return _s; } } while (0)
+    TRY(build_regions(c, mat));
+    TRY(c->prec == 32 ? upload_regions_t<float>(c) : upload_regions_t<double>(c));
+    const size_t vb = 3 * N * c->esz;
+    TRY(alloc(c, &c->d_m, vb, "state"));
+    TRY(alloc(c, &c->d_mtmp, vb, "stage state"));
+    TRY(alloc(c, &c->d_hbuf, vb, "field scratch"));
+    const int nk = c->integrator == MM_RK45 ? 7 : 1;
+    for (int q = 0; q < nk; ++q) TRY(alloc(c, &c->d_k[q], vb, "slopes"));
+    TRY(alloc(c, &c->d_kslot, sizeof(void*) * 7, "slot table"));
+    cudaMemcpy(c->d_kslot, c->d_k, sizeof(void*) * 7, cudaMemcpyHostToDevice);
+    TRY(alloc(c, (void**)&c->d_state, sizeof(DevState), "device state"));
+    c->red_cap = 2 * 304 + 16;
+    TRY(alloc(c, (void**)&c->d_red, sizeof(double) * c->red_cap, "reduction partials"));
+    if (c->terms & MM_TERM_DEMAG) {
+        TRY(alloc(c, &c->d_hd, vb, "demag field"));
+        TRY(demag_setup(c));
+    }
+    // state: m along +z
+    {
+        std::vector<double> m0(3 * N, 0.0);
+        for (long long i = 0; i < N; ++i) m0[2 * N + i] = 1.0;
+        if (c->prec == 32) {
+            std::vector<float> h;
+            host_to_state<float>(m0.data(), N, c->region_of_cell, c->regions, c->uniform, h);
+            cudaMemcpy(c->d_m, h.data(), vb, cudaMemcpyHostToDevice);
+        } else {
+            std::vector<double> h;
+            host_to_state<double>(m0.data(), N, c->region_of_cell, c->regions, c->uniform, h);
+            cudaMemcpy(c->d_m, h.data(), vb, cudaMemcpyHostToDevice);
+        }
+    }
+    DevState& st = c->h_state;
+    st = DevState{};
+    st.dt = cfg->dt;
+    st.rtol = cfg->rtol > 0 ? cfg->rtol : 1e-6;
+    st.dt_min = cfg->dt_min > 0 ? cfg->dt_min : 1e-20;
+    st.dt_max = cfg->dt_max > 0 ? cfg->dt_max : 1e-11;
+    st.t_end = std::numeric_limits<double>::infinity();
+    st.k_first = 0;
+    TRY(push_state(c));
+    TRY(cuda_check(c, cudaDeviceSynchronize(), "create"));
+#undef TRY
+    *out = c;
+    return MM_OK;
+}
+
+mm_status mm_create_batch(int R, const mm_grid* grids, const mm_material* mat, const mm_config* cfg,
+                          const uint64_t* seeds, mm_ctx** out) {
+    if (R != 1) return set_error(nullptr, MM_ERR_ARG, "mm_create_batch: use the replica engine (mm_batch_*) for R > 1");
+    mm_status s = mm_create(grids, mat, cfg, out);
+    if (s == MM_OK && seeds) (*out)->seed = seeds[0];
+    return s;
+}
+
+mm_status mm_destroy(mm_ctx* c) {
+    if (!c) return MM_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+    return MM_OK;
+}
+
+mm_status mm_set_stream(mm_ctx* c, void* stream) {
+    if (!c) return MM_ERR_ARG;
+    cudaStreamSynchronize(c->stream);
+    c->stream = stream ? (cudaStream_t)stream : c->own_stream;
+    invalidate_graph(c);
+    return MM_OK;
+}
+
+}  // extern "C"
+
+static mm_status check_replica(mm_ctx* c, int r) {
+    if (!c) return MM_ERR_ARG;
+    if (r != 0) return set_error(c, MM_ERR_ARG, "replica index out of range");
+    return MM_OK;
+}
+
+extern "C" {
+
+mm_status mm_set_m(mm_ctx* c, int r, const double* m) {
+    mm_status s = check_replica(c, r);
+    if (s != MM_OK) return s;
+    if (!m) return set_error(c, MM_ERR_ARG, "null m");
+    const size_t vb = 3 * c->N * c->esz;
+    cudaError_t e;
+    if (c->prec == 32) {
+        std::vector<float> h;
+        host_to_state<float>(m, c->N, c->region_of_cell, c->regions, c->uniform, h);
+        e = cudaMemcpyAsync(c->d_m, h.data(), vb, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    } else {
+        std::vector<double> h;
+        host_to_state<double>(m, c->N, c->region_of_cell, c->regions, c->uniform, h);
+        e = cudaMemcpyAsync(c->d_m, h.data(), vb, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    c->k1_valid = false;
+    return cuda_check(c, e, "mm_set_m");
+}
+
+mm_status mm_get_m(mm_ctx* c, int r, double* m) {
+    mm_status s = check_replica(c, r);
+    if (s != MM_OK) return s;
+    const long long n3 = 3 * c->N;
+    cudaError_t e;
+    if (c->prec == 32) {
+        std::vector<float> h(n3);
+        e = cudaMemcpyAsync(h.data(), c->d_m, n3 * 4, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        for (long long i = 0; i < n3; ++i) m[i] = h[i];
+    } else {
+        e = cudaMemcpyAsync(m, c->d_m, n3 * 8, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    return cuda_check(c, e, "mm_get_m");
+}
+
+mm_status mm_set_m_device(mm_ctx* c, const void* m) {
+    if (!c || !m) return MM_ERR_ARG;
+    cudaError_t e = cudaMemcpyAsync(c->d_m, m, 3 * c->N * c->esz, cudaMemcpyDeviceToDevice, c->stream);
+    normalize_launch(c, c->d_m);
+    c->k1_valid = false;
+    return cuda_check(c, e, "mm_set_m_device");
+}
+
+mm_status mm_get_m_device(mm_ctx* c, void* m) {
+    if (!c || !m) return MM_ERR_ARG;
+    return cuda_check(c, cudaMemcpyAsync(m, c->d_m, 3 * c->N * c->esz, cudaMemcpyDeviceToDevice, c->stream),
+                      "mm_get_m_device");
+}
+
+mm_status mm_set_field(mm_ctx* c, int r, const double B[3], const double* B_cell) {
+    mm_status s = check_replica(c, r);
+    if (s != MM_OK) return s;
+    if (B) for (int d = 0; d < 3; ++d) c->Hext[d] = B[d] / kMu0;
+    else for (int d = 0; d < 3; ++d) c->Hext[d] = 0.0;
+    if (B_cell) {
+        const long long n3 = 3 * c->N;
+        if (!c->d_bcell) {
+            mm_status a = alloc(c, &c->d_bcell, n3 * c->esz, "per-cell field");
+            if (a != MM_OK) return a;
+        }
+        cudaError_t e;
+        if (c->prec == 32) {
+            std::vector<float> h(n3);
+            for (long long i = 0; i < n3; ++i) h[i] = (float)(B_cell[i] / kMu0);
+            e = cudaMemcpy(c->d_bcell, h.data(), n3 * 4, cudaMemcpyHostToDevice);
+        } else {
+            std::vector<double> h(n3);
+            for (long long i = 0; i < n3; ++i) h[i] = B_cell[i] / kMu0;
+            e = cudaMemcpy(c->d_bcell, h.data(), n3 * 8, cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) return cuda_check(c, e, "mm_set_field");
+    } else if (c->d_bcell) {
+        cudaFree(c->d_bcell);
+        c->d_bcell = nullptr;
+    }
+    c->k1_valid = false;
+    invalidate_graph(c);
+    return MM_OK;
+}
+
+mm_status mm_set_temperature(mm_ctx* c, const double* T) {
+    if (!c || !T) return MM_ERR_ARG;
+    if (T[0] < 0) return set_error(c, MM_ERR_ARG, "negative temperature");
+    if (T[0] > 0 && c->integrator == MM_RK45) return set_error(c, MM_ERR_ARG, "RK45 with T > 0; use Heun");
+    c->Tr = T[0];
+    invalidate_graph(c);
+    return MM_OK;
+}
+
+mm_status mm_set_torque(mm_ctx* c, const mm_torque* tq, const double* J) {
+    if (!c || !tq) return MM_ERR_ARG;
+    if (tq->kind < MM_TORQUE_NONE || tq->kind > MM_TORQUE_ZL) return set_error(c, MM_ERR_ARG, "bad torque kind");
+    c->tq = *tq;
+    c->J = J ? J[0] : 0.0;
+    c->k1_valid = false;
+    invalidate_graph(c);
+    return MM_OK;
+}
+
+}  // extern "C"
+
+// one chunk of `n` integrator attempts (or Heun steps) on the stream
+static void launch_attempts(mm_ctx* c, int n) {
+    for (int q = 0; q < n; ++q) {
+        if (c->integrator == MM_RK45) rk45_attempt(c);
+        else heun_step(c);
+    }
+}
+
+static const int kChunk = 8;
+
+static mm_status run_attempts(mm_ctx* c, long long n_attempts) {
+    if (c->profiling) {
+        launch_attempts(c, (int)n_attempts);
+        return cuda_check(c, cudaGetLastError(), "launch");
+    }
+    if (!c->graph) {
+        cudaGraph_t g;
+        const long long before = c->launches;
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_check(c, e, "graph capture");
+        launch_attempts(c, kChunk);
+        e = cudaStreamEndCapture(c->stream, &g);
+        if (e != cudaSuccess) return cuda_check(c, e, "graph capture end");
+        e = cudaGraphInstantiate(&c->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_check(c, e, "graph instantiate");
+        c->graph_chunk = kChunk;
+        c->launches_per_chunk = c->launches - before;   // counted on replay instead
+        c->launches = before;
+    }
+    long long left = n_attempts;
+    while (left >= kChunk) {
+        cudaError_t e = cudaGraphLaunch(c->graph, c->stream);
+        if (e != cudaSuccess) return cuda_check(c, e, "graph launch");
+        c->launches += c->launches_per_chunk;
+        left -= kChunk;
+    }
+    if (left > 0) launch_attempts(c, (int)left);
+    return cuda_check(c, cudaGetLastError(), "launch");
+}
+
+static mm_status ensure_k1(mm_ctx* c) {
+    if (c->integrator != MM_RK45 || c->k1_valid) return MM_OK;
+    rk45_first_slope(c);
+    c->k1_valid = true;
+    return cuda_check(c, cudaGetLastError(), "first slope");
+}
+
+// Advance until `target` accepted steps (or t_end / a device error).
+static mm_status advance(mm_ctx* c, long long add_steps, double t_end, int replay) {
+    mm_status s = sync_state(c);
+    if (s != MM_OK) return s;
+    if (c->h_state.status) {
+        // a sticky device error from an earlier call: clear it for a fresh attempt
+        c->h_state.status = 0;
+    }
+    if (c->inject == 2) {
+        c->inject = 0;
+        std::vector<unsigned char> nanbuf(c->esz, 0xFF);
+        cudaMemcpyAsync(c->d_m, nanbuf.data(), c->esz, cudaMemcpyHostToDevice, c->stream);
+        c->k1_valid = false;
+    }
+    if (c->inject == 3) {
+        c->inject = 0;
+        c->h_state.dt_min = 1e300;
+        c->h_state.rtol = 0.0;
+    }
+    const long long start = c->h_state.accepted;
+    c->h_state.target = add_steps >= 0 ? start + add_steps : std::numeric_limits<long long>::max();
+    c->h_state.t_end = t_end;
+    c->h_state.replay = replay;
+    if (replay) {
+        c->h_state.replay_dts = c->d_replay - start;   // indexed by the accepted-step counter
+        c->h_state.replay_n = start + add_steps;
+    }
+    s = push_state(c);
+    if (s != MM_OK) return s;
+    s = ensure_k1(c);
+    if (s != MM_OK) return s;
+    const bool heun = c->integrator == MM_HEUN;
+    for (int round = 0; round < 1000000; ++round) {
+        long long want;
+        if (add_steps >= 0) {
+            want = c->h_state.target - c->h_state.accepted;
+        } else {
+            const double left = t_end - c->h_state.t;
+            const double dt = c->h_state.dt > 0 ? c->h_state.dt : 1e-13;
+            want = (long long)std::min(1e6, std::ceil(left / dt)) + 1;
+        }
+        if (want <= 0) break;
+        if (heun) want = std::min<long long>(want, 1 << 20);
+        else want = std::min<long long>(std::max<long long>(want, 1), 1 << 16);
+        s = run_attempts(c, want);
+        if (s != MM_OK) return s;
+        s = sync_state(c);
+        if (s != MM_OK) return s;
+        if (c->h_state.status) break;
+        if (add_steps >= 0 && c->h_state.accepted >= c->h_state.target) break;
+        if (add_steps < 0 && !(c->h_state.t < t_end)) break;
+    }
+    if (replay) {
+        c->h_state.replay = 0;
+        push_state(c);
+    }
+    return status_from_device(c);
+}
+
+extern "C" {
+
+mm_status mm_step(mm_ctx* c, long n) {
+    if (!c || n < 0) return MM_ERR_ARG;
+    if (n == 0) return MM_OK;
+    return advance(c, n, std::numeric_limits<double>::infinity(), 0);
+}
+
+mm_status mm_step_dt(mm_ctx* c, const double* dts, long n) {
+    if (!c || (!dts && n > 0) || n < 0) return MM_ERR_ARG;
+    if (c->integrator != MM_RK45) return set_error(c, MM_ERR_STATE, "mm_step_dt replays RK45 steps only");
+    if (n == 0) return MM_OK;
+    if ((size_t)n > c->replay_cap) {
+        cudaFree(c->d_replay);
+        c->d_replay = nullptr;
+        mm_status a = alloc(c, (void**)&c->d_replay, sizeof(double) * n, "replay steps");
+        if (a != MM_OK) return a;
+        c->replay_cap = n;
+        invalidate_graph(c);
+    }
+    cudaError_t e = cudaMemcpy(c->d_replay, dts, sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_check(c, e, "replay upload");
+    return advance(c, n, std::numeric_limits<double>::infinity(), 1);
+}
+
+mm_status mm_run(mm_ctx* c, double t_end) {
+    if (!c) return MM_ERR_ARG;
+    mm_status s = sync_state(c);
+    if (s != MM_OK) return s;
+    if (!(t_end > c->h_state.t)) return MM_OK;
+    return advance(c, -1, t_end, 0);
+}
+
+mm_status mm_get_heff(mm_ctx* c, int r, double* H, unsigned mask) {
+    mm_status s = check_replica(c, r);
+    if (s != MM_OK) return s;
+    if (!H) return set_error(c, MM_ERR_ARG, "null output");
+    const unsigned terms = mask & (c->terms | MM_TERM_THERMAL);
+    const bool demag = (terms & MM_TERM_DEMAG) && c->dm.on;
+    if (demag) demag_apply(c, c->d_m, c->d_hd);
+    field_launch(c, MODE_H, terms, c->d_m, demag ? c->d_hd : nullptr, c->d_hbuf, nullptr, nullptr, nullptr, -1, 0, 0);
+    const long long n3 = 3 * c->N;
+    cudaError_t e;
+    if (c->prec == 32) {
+        std::vector<float> h(n3);
+        e = cudaMemcpyAsync(h.data(), c->d_hbuf, n3 * 4, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        for (long long i = 0; i < n3; ++i) H[i] = h[i];
+    } else {
+        e = cudaMemcpyAsync(H, c->d_hbuf, n3 * 8, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    return cuda_check(c, e, "mm_get_heff");
+}
+
+mm_status mm_energy(mm_ctx* c, int r, double* E) {
+    mm_status s = check_replica(c, r);
+    if (s != MM_OK) return s;
+    if (!E) return set_error(c, MM_ERR_ARG, "null output");
+    static const unsigned term_of[5] = {MM_TERM_EXCHANGE, MM_TERM_DMI, MM_TERM_ANISOTROPY, MM_TERM_ZEEMAN, MM_TERM_DEMAG};
+    double* d_out = c->d_red + 2 * 304;
+    double h[MM_NENERGY] = {0, 0, 0, 0, 0, 0};
+    for (int q = 0; q < 5; ++q) {
+        if (!(c->terms & term_of[q]) || (q == 4 && !c->dm.on)) continue;
+        if (q == 4) demag_apply(c, c->d_m, c->d_hd);
+        field_launch(c, MODE_H, term_of[q], c->d_m, q == 4 ? c->d_hd : nullptr, c->d_hbuf, nullptr, nullptr, nullptr,
+                     -1, 0, 0);
+        energy_term_launch(c, c->d_m, c->d_hbuf, q, d_out + q);
+    }
+    cudaError_t e = cudaMemcpyAsync(h, d_out, sizeof(double) * 5, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "mm_energy");
+    double tot = 0.0, comp = 0.0;
+    for (int q = 0; q < 5; ++q) {
+        E[q] = h[q];
+        const double t = tot + h[q];
+        comp += std::fabs(tot) >= std::fabs(h[q]) ? (tot - t) + h[q] : (h[q] - t) + tot;
+        tot = t;
+    }
+    E[MM_E_TOTAL] = tot + comp;
+    return MM_OK;
+}
+
+mm_status mm_topo_charge(mm_ctx* c, int r, int layer, double* Q) {
+    mm_status s = check_replica(c, r);
+    if (s != MM_OK) return s;
+    if (!Q || layer >= c->grid.nz) return set_error(c, MM_ERR_ARG, "bad layer or null output");
+    double* d_out = c->d_red + 2 * 304 + 8;
+    topo_launch(c, c->d_m, layer, d_out);
+    double h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, d_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "mm_topo_charge");
+    *Q = layer >= 0 ? h : h / c->grid.nz;
+    return MM_OK;
+}
+
+mm_status mm_get_time(mm_ctx* c, int r, double* t, double* dt, long long* steps) {
+    mm_status s = check_replica(c, r);
+    if (s != MM_OK) return s;
+    s = sync_state(c);
+    if (s != MM_OK) return s;
+    if (t) *t = c->h_state.t;
+    if (dt) *dt = c->h_state.dt;
+    if (steps) *steps = c->h_state.accepted;
+    return MM_OK;
+}
+
+mm_status mm_get_stats(mm_ctx* c, mm_stats* st) {
+    if (!c || !st) return MM_ERR_ARG;
+    mm_status s = sync_state(c);
+    if (s != MM_OK) return s;
+    st->accepted = c->h_state.accepted;
+    st->rejected = c->h_state.rejected;
+    st->attempts = c->h_state.attempts;
+    st->kernel_launches = c->launches;
+    st->t = c->h_state.t;
+    st->dt = c->h_state.dt;
+    return MM_OK;
+}
+
+// checkpoint layout: header | DevState | m | k1 (RK45)
+struct CkptHeader {
+    char magic[8];
+    int prec, integrator;
+    long long N;
+    uint64_t seed;
+    int k1_valid, pad;
+};
+
+mm_status mm_get_state(mm_ctx* c, void* buf, size_t* nbytes) {
+    if (!c || !nbytes) return MM_ERR_ARG;
+    const size_t vb = 3 * c->N * c->esz;
+    const bool k1 = c->integrator == MM_RK45;
+    const size_t need = sizeof(CkptHeader) + sizeof(DevState) + vb * (k1 ? 2 : 1);
+    if (!buf) { *nbytes = need; return MM_OK; }
+    if (*nbytes < need) return set_error(c, MM_ERR_ARG, "checkpoint buffer too small");
+    mm_status s = sync_state(c);
+    if (s != MM_OK) return s;
+    CkptHeader h{};
+    memcpy(h.magic, "MMCKPT1", 8);
+    h.prec = c->prec; h.integrator = c->integrator; h.N = c->N; h.seed = c->seed; h.k1_valid = c->k1_valid;
+    char* p = (char*)buf;
+    memcpy(p, &h, sizeof h);
+    memcpy(p + sizeof h, &c->h_state, sizeof(DevState));
+    char* mp = p + sizeof h + sizeof(DevState);
+    cudaError_t e = cudaMemcpyAsync(mp, c->d_m, vb, cudaMemcpyDeviceToHost, c->stream);
+    if (k1 && e == cudaSuccess) {
+        void* slots[7];
+        memcpy(slots, c->d_k, sizeof slots);
+        e = cudaMemcpyAsync(mp + vb, slots[c->h_state.k_first], vb, cudaMemcpyDeviceToHost, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    *nbytes = need;
+    return cuda_check(c, e, "mm_get_state");
+}
+
+mm_status mm_set_state(mm_ctx* c, const void* buf, size_t nbytes) {
+    if (!c || !buf) return MM_ERR_ARG;
+    const size_t vb = 3 * c->N * c->esz;
+    const bool k1 = c->integrator == MM_RK45;
+    const size_t need = sizeof(CkptHeader) + sizeof(DevState) + vb * (k1 ? 2 : 1);
+    if (nbytes < need) return set_error(c, MM_ERR_ARG, "checkpoint too small");
+    CkptHeader h;
+    memcpy(&h, buf, sizeof h);
+    if (memcmp(h.magic, "MMCKPT1", 8) != 0 || h.prec != c->prec || h.integrator != c->integrator || h.N != c->N)
+        return set_error(c, MM_ERR_ARG, "checkpoint does not match this context");
+    const char* p = (const char*)buf;
+    DevState st;
+    memcpy(&st, p + sizeof h, sizeof st);
+    st.replay = 0;
+    st.replay_dts = nullptr;
+    c->h_state = st;
+    c->seed = h.seed;
+    const char* mp = p + sizeof h + sizeof(DevState);
+    cudaError_t e = cudaMemcpyAsync(c->d_m, mp, vb, cudaMemcpyHostToDevice, c->stream);
+    if (k1 && e == cudaSuccess) {
+        e = cudaMemcpyAsync(c->d_k[st.k_first], mp + vb, vb, cudaMemcpyHostToDevice, c->stream);
+        c->k1_valid = h.k1_valid != 0;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "mm_set_state");
+    invalidate_graph(c);
+    return push_state(c);
+}
+
+mm_status mm_get_thermal(mm_ctx* c, int r, long long step, uint32_t* raw, double* H_th) {
+    mm_status s = check_replica(c, r);
+    if (s != MM_OK) return s;
+    uint32_t* d_raw = nullptr;
+    if (raw) {
+        s = alloc(c, (void**)&d_raw, sizeof(uint32_t) * 4 * c->N, "thermal words");
+        if (s != MM_OK) return s;
+    }
+    thermal_raw_launch(c, step, d_raw, H_th ? c->d_hbuf : nullptr);
+    cudaError_t e = cudaSuccess;
+    if (raw) e = cudaMemcpyAsync(raw, d_raw, sizeof(uint32_t) * 4 * c->N, cudaMemcpyDeviceToHost, c->stream);
+    const long long n3 = 3 * c->N;
+    std::vector<float> hf;
+    if (H_th && e == cudaSuccess) {
+        if (c->prec == 32) {
+            hf.resize(n3);
+            e = cudaMemcpyAsync(hf.data(), c->d_hbuf, n3 * 4, cudaMemcpyDeviceToHost, c->stream);
+        } else {
+            e = cudaMemcpyAsync(H_th, c->d_hbuf, n3 * 8, cudaMemcpyDeviceToHost, c->stream);
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (H_th && c->prec == 32 && e == cudaSuccess)
+        for (long long i = 0; i < n3; ++i) H_th[i] = hf[i];
+    cudaFree(d_raw);
+    return cuda_check(c, e, "mm_get_thermal");
+}
+
+mm_status mm_get_demag_kernel(mm_ctx* c, double* out, size_t n_out, int* dims) {
+    if (!c) return MM_ERR_ARG;
+    return demag_kernel_copy(c, out, n_out, dims);
+}
+
+mm_status mm_newell(long count, const int* ijk, double dx, double dy, double dz, double* out) {
+    if (count < 0 || (count > 0 && (!ijk || !out)) || !(dx > 0) || !(dy > 0) || !(dz > 0))
+        return set_error(nullptr, MM_ERR_ARG, "mm_newell: bad arguments");
+    mm_ctx tmp;
+    mm_status s = check_device(&tmp);
+    if (s != MM_OK) { g_create_error = tmp.last_error; return s; }
+    return newell_gpu(count, ijk, dx, dy, dz, out);
+}
+
+mm_status mm_set_profiling(mm_ctx* c, int on) {
+    if (!c) return MM_ERR_ARG;
+    c->profiling = on != 0;
+    if (on) c->prof.clear();
+    return MM_OK;
+}
+
+mm_status mm_get_profile(mm_ctx* c, mm_profile_entry* out, int* n) {
+    if (!c || !n) return MM_ERR_ARG;
+    const int cnt = (int)c->prof.size();
+    if (!out) { *n = cnt; return MM_OK; }
+    const int w = std::min(*n, cnt);
+    for (int q = 0; q < w; ++q) {
+        memset(&out[q], 0, sizeof(mm_profile_entry));
+        strncpy(out[q].name, c->prof[q].name.c_str(), sizeof(out[q].name) - 1);
+        out[q].launches = c->prof[q].launches;
+        out[q].total_ms = c->prof[q].total_ms;
+        out[q].bytes_per_launch = c->prof[q].bytes;
+    }
+    *n = w;
+    return MM_OK;
+}
+
+mm_status mm_debug_inject(mm_ctx* c, int fault) {
+    if (!c || fault < 0 || fault > 3) return MM_ERR_ARG;
+    c->inject = fault;
+    return MM_OK;
+}
+
+}  // extern "C"

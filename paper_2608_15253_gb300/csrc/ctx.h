@@ -1,0 +1,184 @@
+// Host-side internals of libmm: the context, its device buffers, the
+// per-region material table, launch bookkeeping and the kernel launchers
+// each translation unit provides.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "mm.h"
+
+namespace mm {
+
+constexpr int kMaxRegions = 256;
+
+// Per-region coefficients consumed by the field kernels (working precision).
+template <typename T>
+struct Region {
+    T present;    // 1 if Ms > 0
+    T inv_mu0Ms;  // 1/(mu0 Ms), 0 when absent
+    T Ms;
+    T cg;         // ghost exchange coefficient 2 A_i / (mu0 Ms_i)
+    T ratio;      // D / (2 A), 0 when A = 0
+    T dmi;        // 2 D / (mu0 Ms)
+    T ku;         // 2 Ku1 / (mu0 Ms)
+    T ux, uy, uz;
+    T alpha;
+    T gm;         // gamma0 mu0 / (1 + alpha^2)
+    T sigma0;     // sqrt(2 alpha kB / (mu0^2 Ms gamma0)); times sqrt(T/(V dt)) -> A/m
+    T inv_Ms;     // 1/Ms, 0 when absent
+    T pad0, pad1;
+};
+
+struct RegionHost {
+    double Ms, A, alpha, Ku1, u[3], D;
+    bool operator==(const RegionHost& o) const {
+        return Ms == o.Ms && A == o.A && alpha == o.alpha && Ku1 == o.Ku1 && u[0] == o.u[0] &&
+               u[1] == o.u[1] && u[2] == o.u[2] && D == o.D;
+    }
+};
+
+// Device state of the integrator (one per context, read by every kernel of
+// an attempt so that whole steps can be replayed from a CUDA graph).
+struct DevState {
+    double t, dt, dt_eff, t_end;
+    double rtol, dt_min, dt_max;
+    double err;                 // max-norm error of the last attempt (as a double)
+    float err_f;                // float32 accumulation target
+    int active;                 // 0: remaining kernels of this attempt are no-ops
+    int accept;
+    int last_rejected;
+    int replay;                 // 1: take dt from replay_dts, always accept
+    int status;                 // mm_status raised on the device (sticky)
+    int k_first;                // slot index holding k1 (FSAL rotation: 0 or 6)
+    long long accepted, rejected, attempts, step;
+    long long target;           // stop after this many accepted steps
+    long long replay_n;
+    const double* replay_dts;
+};
+
+struct DemagPlan {
+    int on = 0;
+    int Px = 0, Py = 0, Pz = 0;   // padded lengths
+    int Lh = 0;                   // Px / 2 (complex length of the X transform)
+    int Kx = 0, Wk = 0;           // Px/2 + 1 spectrum columns, row pitch
+    int PyA = 0;                  // rows per z-plane of the spectrum buffer
+    int ncomp = 0;                // 6 (3D) or 4 (nz = 1)
+    void* spec = nullptr;         // [3][nz][PyA][Wk] complex
+    void* khat = nullptr;         // [ncomp][Pz/2+1][Py/2+1][Wk] real
+    void* tw_x = nullptr;         // exp(-2 pi i k / Px), k < Px
+    void* tw_y = nullptr;         // exp(-2 pi i k / Py)
+    void* tw_z = nullptr;         // exp(-2 pi i k / Pz)
+};
+
+struct ProfileSlot {
+    std::string name;
+    long long launches = 0;
+    double total_ms = 0.0;
+    double bytes = 0.0;
+};
+
+}  // namespace mm
+
+struct mm_ctx {
+    int prec = 32;              // 32 or 64
+    size_t esz = 4;             // bytes per real
+    int integrator = MM_RK45;
+    unsigned terms = MM_TERM_ALL;
+    int R = 1;
+    mm_grid grid{};
+    long long N = 0;            // cells per replica (single instance)
+    mm_config cfg{};
+    std::string last_error;
+
+    // material regions
+    int nreg = 1;
+    int uniform = 1;            // every cell in region 0
+    std::vector<mm::RegionHost> regions;
+    std::vector<uint8_t> region_of_cell;
+    void* d_region = nullptr;   // uint8 per cell (null when uniform)
+    void* d_lut = nullptr;      // Region<T>[nreg]
+    void* d_cpair = nullptr;    // T[nreg*nreg]: 2 A_ij / (mu0 Ms_i)
+
+    // state buffers (working precision), [3][N] each
+    void* d_m = nullptr;        // current state m0
+    void* d_mtmp = nullptr;     // stage state
+    void* d_k[7] = {};          // stage slopes
+    void* d_kslot = nullptr;    // device array of 7 pointers (FSAL rotation)
+    void* d_hd = nullptr;       // demag field
+    void* d_hbuf = nullptr;     // scratch field (observables)
+    void* d_bcell = nullptr;    // per-cell applied field (A/m) or null
+    double Hext[3] = {0, 0, 0}; // uniform applied field (A/m)
+    double Tr = 0.0;            // temperature
+    uint64_t seed = 0;          // Philox key of the replica
+
+    // torque
+    mm_torque tq{};
+    double J = 0.0;
+
+    mm::DevState* d_state = nullptr;
+    mm::DevState h_state{};
+    double* d_replay = nullptr;
+    size_t replay_cap = 0;
+    double* d_red = nullptr;    // reduction partials
+    size_t red_cap = 0;
+
+    mm::DemagPlan dm;
+
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    bool k1_valid = false;
+
+    // CUDA graph of a chunk of integrator attempts
+    cudaGraphExec_t graph = nullptr;
+    int graph_chunk = 0;
+    long long launches_per_chunk = 0;
+
+    long long launches = 0;
+    bool profiling = false;
+    std::vector<mm::ProfileSlot> prof;
+    int inject = 0;
+};
+
+namespace mm {
+
+mm_status set_error(mm_ctx* c, mm_status s, const std::string& msg);
+mm_status cuda_check(mm_ctx* c, cudaError_t e, const char* what);
+
+// Kernel-launch bookkeeping: counts launches and, while profiling, brackets
+// the launch with CUDA events on the context stream.
+struct LaunchScope {
+    mm_ctx* c;
+    int slot;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    LaunchScope(mm_ctx* c, const char* name, double bytes);
+    ~LaunchScope();
+};
+
+// demag.cu
+mm_status demag_setup(mm_ctx* c);
+void demag_free(mm_ctx* c);
+void demag_apply(mm_ctx* c, const void* m, void* Hd);   // Hd = H_demag(m)
+mm_status newell_gpu(long count, const int* ijk, double dx, double dy, double dz, double* out_host);
+
+// field.cu
+enum FieldMode { MODE_H = 0, MODE_K = 1, MODE_HEUN1 = 2, MODE_HEUN2 = 3 };
+void field_launch(mm_ctx* c, int mode, unsigned terms, const void* m, const void* Hd,
+                  void* out, void* out2, const void* m0, const void* k1, long long step_override,
+                  int gate, int kstage);
+void thermal_raw_launch(mm_ctx* c, long long step, uint32_t* d_raw, void* d_h);
+
+// integrate.cu
+void rk45_first_slope(mm_ctx* c);          // k1 = f(m0) into the FSAL slot
+void rk45_attempt(mm_ctx* c);               // one attempted DOPRI5 step
+void heun_step(mm_ctx* c);                  // one Heun step
+
+// reduce.cu
+void energy_term_launch(mm_ctx* c, const void* m, const void* H, int which, double* d_out2);
+void topo_launch(mm_ctx* c, const void* m, int layer, double* d_out2);
+void normalize_launch(mm_ctx* c, void* m);
+
+}  // namespace mm

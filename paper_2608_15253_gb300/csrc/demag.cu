@@ -1,0 +1,863 @@
+// Open-boundary demagnetisation (Methods, "Physics and discretization":
+// FFT convolution with the Newell tensor, zero-padded to 2N).
+//
+// Pipeline per field evaluation, every pass a shared-memory batched FFT:
+//   X pass   R2C along x of Ms*m (only the nx nonzero inputs of the padded
+//            2nx row are read; half-length complex FFT + split)
+//   Y pass   forward along y (3-D only; ny nonzero inputs, Py outputs)
+//   middle   last axis (z in 3-D, y in 2-D): forward FFT, H^ = K^ M^ with the
+//            real, symmetry-compressed tensor spectrum, inverse FFT, keep the
+//            n un-padded outputs -- one pass, the spectrum never leaves smem
+//   Y pass   inverse (3-D only; Py inputs, ny outputs)
+//   X pass   C2R, only the nx un-padded outputs are written.
+// Setup (once per geometry): the FP64 Newell tensor on the GPU (closed form
+// near, tent-weighted Gauss-Legendre of the dipole kernel far), then FP64
+// FFTs of the padded tensor; -1/(Px Py Pz) is folded into K^.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "ctx.h"
+
+namespace mm {
+
+// ---------------------------------------------------------------------------
+// FFT plan and in-shared-memory Stockham passes
+// ---------------------------------------------------------------------------
+constexpr int kMaxPasses = 16;
+constexpr int kMaxV = 24;   // complex values held in registers per thread per pass
+
+struct Plan {
+    int L;
+    int npass;
+    int radix[kMaxPasses];
+};
+
+static bool make_plan(int L, Plan* p) {
+    p->L = L;
+    p->npass = 0;
+    int n = L;
+    while (n % 4 == 0) { p->radix[p->npass++] = 4; n /= 4; }
+    while (n % 2 == 0) { p->radix[p->npass++] = 2; n /= 2; }
+    while (n % 3 == 0) { p->radix[p->npass++] = 3; n /= 3; }
+    return n == 1 && p->npass <= kMaxPasses;
+}
+
+// smallest 2^a 3^b >= n (even when want_even)
+static int nice_length(int n, bool want_even) {
+    int best = 1 << 30;
+    for (long long p2 = 1; p2 < (1LL << 31); p2 *= 2)
+        for (long long p3 = p2; p3 < (1LL << 31); p3 *= 3) {
+            if (p3 >= n && p3 < best && (!want_even || p3 % 2 == 0)) best = (int)p3;
+            if (p3 >= n) break;
+        }
+    return best;
+}
+
+template <typename T, int DIR, int R>
+__device__ __forceinline__ void dft(cplx<T>* v) {
+    if (R == 2) {
+        cplx<T> a = v[0], b = v[1];
+        v[0] = cadd<T>(a, b);
+        v[1] = csub<T>(a, b);
+    } else if (R == 4) {
+        cplx<T> a0 = cadd<T>(v[0], v[2]), a1 = csub<T>(v[0], v[2]);
+        cplx<T> a2 = cadd<T>(v[1], v[3]), a3 = mul_mi<T, DIR>(csub<T>(v[1], v[3]));
+        v[0] = cadd<T>(a0, a2);
+        v[2] = csub<T>(a0, a2);
+        v[1] = cadd<T>(a1, a3);
+        v[3] = csub<T>(a1, a3);
+    } else {  // R == 3
+        const T s3 = (T)0.86602540378443864676;
+        cplx<T> t1 = cadd<T>(v[1], v[2]);
+        cplx<T> t2 = csub<T>(v[0], cscale<T>(t1, (T)0.5));
+        cplx<T> t3 = cscale<T>(mul_mi<T, DIR>(csub<T>(v[1], v[2])), s3);
+        v[0] = cadd<T>(v[0], t1);
+        v[1] = cadd<T>(t2, t3);
+        v[2] = csub<T>(t2, t3);
+    }
+}
+
+// One in-place Stockham pass over nl lines of length L stored at `pitch`
+// (complex elements) in shared memory.  Every thread first loads all the
+// butterflies it owns into registers, the block synchronises, then the
+// results are written to their autosorted positions.  Inputs at index
+// >= nin are zero (pruned, only meaningful on the first pass).
+template <typename T, int DIR, int R>
+__device__ void stockham_pass(cplx<T>* sm, int nl, int pitch, int L, int Ns, int nin,
+                              const cplx<T>* __restrict__ tw, int tw_stride) {
+    constexpr int MAXB = kMaxV / R;
+    const int nb = L / R;
+    const int total = nl * nb;
+    cplx<T> v[MAXB][R];
+#pragma unroll
+    for (int i = 0; i < MAXB; ++i) {
+        const int b = threadIdx.x + i * blockDim.x;
+        if (b < total) {
+            const int l = b / nb, j = b - l * nb;
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                const int idx = j + t * nb;
+                v[i][t] = idx < nin ? sm[l * pitch + idx] : mkc<T>(0, 0);
+            }
+        }
+    }
+    __syncthreads();
+    const int span = L / (Ns * R);
+#pragma unroll
+    for (int i = 0; i < MAXB; ++i) {
+        const int b = threadIdx.x + i * blockDim.x;
+        if (b < total) {
+            const int l = b / nb, j = b - l * nb;
+            const int k = j % Ns;
+            if (Ns > 1) {
+#pragma unroll
+                for (int t = 1; t < R; ++t) {
+                    cplx<T> w = __ldg(&tw[(t * k * span) * tw_stride]);
+                    v[i][t] = DIR > 0 ? cmul<T>(v[i][t], w) : cmulc<T>(v[i][t], w);
+                }
+            }
+            dft<T, DIR, R>(v[i]);
+            const int dst = (j / Ns) * Ns * R + k;
+#pragma unroll
+            for (int t = 0; t < R; ++t) sm[l * pitch + dst + t * Ns] = v[i][t];
+        }
+    }
+    __syncthreads();
+}
+
+// Full FFT of nl lines; twiddle table tw holds exp(-2 pi i q / (L*tw_stride)).
+template <typename T, int DIR>
+__device__ void fft_lines(cplx<T>* sm, int nl, int pitch, const Plan& p, int nin,
+                          const cplx<T>* __restrict__ tw, int tw_stride) {
+    int Ns = 1;
+    for (int s = 0; s < p.npass; ++s) {
+        const int r = p.radix[s];
+        const int ni = s == 0 ? nin : p.L;
+        if (r == 4) stockham_pass<T, DIR, 4>(sm, nl, pitch, p.L, Ns, ni, tw, tw_stride);
+        else if (r == 2) stockham_pass<T, DIR, 2>(sm, nl, pitch, p.L, Ns, ni, tw, tw_stride);
+        else stockham_pass<T, DIR, 3>(sm, nl, pitch, p.L, Ns, ni, tw, tw_stride);
+        Ns *= r;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// X passes: real rows <-> half spectra
+// ---------------------------------------------------------------------------
+template <typename T>
+struct XArgs {
+    const T* in;            // R2C: real rows (row r at in + r*in_pitch)
+    T* out_real;            // C2R: real rows
+    cplx<T>* spec;          // spectrum rows
+    long long in_pitch;     // reals between consecutive input rows
+    int rows;               // total rows
+    int rows_per_plane;     // rows of one (component, z) plane on the real side
+    int spec_rows_per_plane;// rows of one plane on the spectrum side
+    int nx;                 // nonzero reals per row
+    int Lh, Kx, Wk;         // half length, spectrum columns, spectrum pitch
+    int rpc;                // rows per CTA
+    Plan plan;
+    const cplx<T>* tw;      // exp(-2 pi i q / Px), q < Px
+    // Ms scaling of the input (R2C only): uniform Ms, or region LUT
+    T ms_uniform;
+    const uint8_t* region;
+    const Region<T>* lut;
+    long long cells_per_comp;  // N: row r belongs to component r / (N/nx)
+};
+
+template <typename T>
+__device__ __forceinline__ long long spec_row(const XArgs<T>& a, int r) {
+    return (long long)(r / a.rows_per_plane) * a.spec_rows_per_plane + (r % a.rows_per_plane);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) fft_x_r2c_kernel(XArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw);
+    const int pitch = a.Lh + 1;
+    const int r0 = blockIdx.x * a.rpc;
+    const int nl = min(a.rpc, a.rows - r0);
+    // load real rows as packed complex z[n] = x[2n] + i x[2n+1]
+    T* smr = reinterpret_cast<T*>(sm);
+    const int nreal = 2 * a.Lh;
+    for (int e = threadIdx.x; e < nl * nreal; e += blockDim.x) {
+        const int l = e / nreal, q = e - l * nreal;
+        T v = 0;
+        if (q < a.nx) {
+            const long long gi = (long long)(r0 + l) * a.in_pitch + q;
+            v = a.in[gi];
+            if (a.region) {
+                const long long cell = gi % a.cells_per_comp;
+                v *= a.lut[a.region[cell]].Ms;
+            } else {
+                v *= a.ms_uniform;
+            }
+        }
+        smr[2 * (l * pitch) + q] = v;
+    }
+    __syncthreads();
+    const int nin = (a.nx + 1) / 2;
+    fft_lines<T, 1>(sm, nl, pitch, a.plan, nin, a.tw, 2);
+    // split: X[k] = (Z[k] + conj Z[M-k])/2 - i/2 W^k (Z[k] - conj Z[M-k])
+    const int M = a.Lh;
+    for (int e = threadIdx.x; e < nl * a.Kx; e += blockDim.x) {
+        const int l = e / a.Kx, k = e - l * a.Kx;
+        const cplx<T> zk = sm[l * pitch + (k % M)];
+        const cplx<T> zc = cconj<T>(sm[l * pitch + ((M - k) % M)]);
+        const cplx<T> E = cscale<T>(cadd<T>(zk, zc), (T)0.5);
+        const cplx<T> O = cscale<T>(mul_mi<T, 1>(csub<T>(zk, zc)), (T)0.5);
+        const cplx<T> w = __ldg(&a.tw[k]);
+        a.spec[spec_row(a, r0 + l) * a.Wk + k] = cadd<T>(E, cmul<T>(w, O));
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) fft_x_c2r_kernel(XArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw);
+    const int pitch = a.Lh + 1;
+    const int r0 = blockIdx.x * a.rpc;
+    const int nl = min(a.rpc, a.rows - r0);
+    const int M = a.Lh;
+    for (int e = threadIdx.x; e < nl * a.Kx; e += blockDim.x) {
+        const int l = e / a.Kx, k = e - l * a.Kx;
+        sm[l * pitch + k] = a.spec[spec_row(a, r0 + l) * a.Wk + k];
+    }
+    __syncthreads();
+    // rebuild Z'[k] = E' + i O', E' = X[k] + conj X[M-k],
+    // O' = (X[k] - conj X[M-k]) conj(W^k); pairs (k, M-k) owned by one thread
+    const int half = M / 2;
+    for (int e = threadIdx.x; e < nl * (half + 1); e += blockDim.x) {
+        const int l = e / (half + 1), k = e - l * (half + 1);
+        const int k2 = M - k;
+        const cplx<T> xk = sm[l * pitch + k];
+        const cplx<T> xk2 = sm[l * pitch + k2];
+        const cplx<T> w1 = __ldg(&a.tw[k]);
+        const cplx<T> w2 = __ldg(&a.tw[k2]);
+        // for k
+        cplx<T> E1 = cadd<T>(xk, cconj<T>(xk2));
+        cplx<T> O1 = cmulc<T>(csub<T>(xk, cconj<T>(xk2)), w1);
+        cplx<T> Z1 = cadd<T>(E1, mul_mi<T, -1>(O1));
+        // for M-k (only when distinct and < M)
+        cplx<T> E2 = cadd<T>(xk2, cconj<T>(xk));
+        cplx<T> O2 = cmulc<T>(csub<T>(xk2, cconj<T>(xk)), w2);
+        cplx<T> Z2 = cadd<T>(E2, mul_mi<T, -1>(O2));
+        sm[l * pitch + k] = Z1;
+        if (k2 != k && k2 < M) sm[l * pitch + k2] = Z2;
+    }
+    __syncthreads();
+    fft_lines<T, -1>(sm, nl, pitch, a.plan, M, a.tw, 2);
+    const T* smr = reinterpret_cast<const T*>(sm);
+    for (int e = threadIdx.x; e < nl * a.nx; e += blockDim.x) {
+        const int l = e / a.nx, q = e - l * a.nx;
+        a.out_real[(long long)(r0 + l) * a.in_pitch + q] = smr[2 * (l * pitch) + q];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Column passes (strided axes), optionally with the tensor multiply
+// ---------------------------------------------------------------------------
+template <typename T>
+struct ColArgs {
+    cplx<T>* base;
+    long long comp_stride;   // between the three components
+    long long line_stride;   // between consecutive points of the axis
+    long long other_stride;  // between consecutive values of blockIdx.y
+    int nc;                  // components per CTA (1 or 3)
+    int Kx, TK;
+    int L, n_in, n_out;
+    Plan plan;
+    const cplx<T>* tw;       // exp(-2 pi i q / L)
+    // tensor multiply (middle pass only)
+    const T* khat;
+    long long kc_stride;     // elements per tensor component
+    long long kk_stride;     // tensor stride for the transform-axis frequency
+    long long ko_stride;     // tensor stride for the other-axis frequency
+    int ncomp;               // 6 or 4
+    int L_other;             // padded length of the other axis (Py in 3-D), 1 in 2-D
+    int axis_is_y;           // 1: transform axis is y (2-D), 0: z (3-D)
+};
+
+template <typename T>
+__device__ __forceinline__ void tensor_multiply(const ColArgs<T>& a, cplx<T>* sm, int pitch, int kx0) {
+    const int other = blockIdx.y;
+    // fold the other-axis frequency (3-D: ky) to the stored half range
+    int ko = 0, so = 1;
+    if (!a.axis_is_y) {
+        ko = other <= a.L_other / 2 ? other : a.L_other - other;
+        so = other <= a.L_other / 2 ? 1 : -1;
+    }
+    for (int e = threadIdx.x; e < a.TK * a.L; e += blockDim.x) {
+        const int kxl = e % a.TK, kk = e / a.TK;
+        const int kx = kx0 + kxl;
+        if (kx >= a.Kx) continue;
+        const int kkf = kk <= a.L / 2 ? kk : a.L - kk;
+        const int sk = kk <= a.L / 2 ? 1 : -1;
+        const T* K = a.khat + (long long)kkf * a.kk_stride + (long long)ko * a.ko_stride + kx;
+        const T kxx = __ldg(K), kyy = __ldg(K + a.kc_stride), kzz = __ldg(K + 2 * a.kc_stride);
+        T kxy = __ldg(K + 3 * a.kc_stride);
+        T kxz = 0, kyz = 0;
+        // parity: xy odd in y, xz odd in z, yz odd in y and z
+        const int sy = a.axis_is_y ? sk : so;
+        const int sz = a.axis_is_y ? 1 : sk;
+        kxy *= (T)sy;
+        if (a.ncomp == 6) {
+            kxz = __ldg(K + 4 * a.kc_stride) * (T)sz;
+            kyz = __ldg(K + 5 * a.kc_stride) * (T)(sy * sz);
+        }
+        cplx<T>* px = &sm[(0 * a.TK + kxl) * pitch + kk];
+        cplx<T>* py = &sm[(1 * a.TK + kxl) * pitch + kk];
+        cplx<T>* pz = &sm[(2 * a.TK + kxl) * pitch + kk];
+        const cplx<T> mx = *px, my = *py, mz = *pz;
+        *px = mkc<T>(kxx * mx.x + kxy * my.x + kxz * mz.x, kxx * mx.y + kxy * my.y + kxz * mz.y);
+        *py = mkc<T>(kxy * mx.x + kyy * my.x + kyz * mz.x, kxy * mx.y + kyy * my.y + kyz * mz.y);
+        *pz = mkc<T>(kxz * mx.x + kyz * my.x + kzz * mz.x, kxz * mx.y + kyz * my.y + kzz * mz.y);
+    }
+    __syncthreads();
+}
+
+template <typename T, int MODE>  // MODE: +1 forward, -1 inverse, 0 convolution
+__global__ void __launch_bounds__(512) fft_col_kernel(ColArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw);
+    const int pitch = a.L + 1;
+    const int kx0 = blockIdx.x * a.TK;
+    const long long obase = (long long)blockIdx.y * a.other_stride;
+    const int nl = a.nc * a.TK;
+    // load
+    for (int e = threadIdx.x; e < a.nc * a.n_in * a.TK; e += blockDim.x) {
+        const int kxl = e % a.TK;
+        const int rest = e / a.TK;
+        const int pt = rest % a.n_in, c = rest / a.n_in;
+        const int kx = kx0 + kxl;
+        cplx<T> v = mkc<T>(0, 0);
+        if (kx < a.Kx) v = a.base[c * a.comp_stride + obase + pt * a.line_stride + kx];
+        sm[(c * a.TK + kxl) * pitch + pt] = v;
+    }
+    __syncthreads();
+    if (MODE >= 0) fft_lines<T, 1>(sm, nl, pitch, a.plan, a.n_in, a.tw, 1);
+    else fft_lines<T, -1>(sm, nl, pitch, a.plan, a.n_in, a.tw, 1);
+    if (MODE == 0) {
+        tensor_multiply<T>(a, sm, pitch, kx0);
+        fft_lines<T, -1>(sm, nl, pitch, a.plan, a.L, a.tw, 1);
+    }
+    for (int e = threadIdx.x; e < a.nc * a.n_out * a.TK; e += blockDim.x) {
+        const int kxl = e % a.TK;
+        const int rest = e / a.TK;
+        const int pt = rest % a.n_out, c = rest / a.n_out;
+        const int kx = kx0 + kxl;
+        if (kx < a.Kx) a.base[c * a.comp_stride + obase + pt * a.line_stride + kx] = sm[(c * a.TK + kxl) * pitch + pt];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 Newell tensor
+// ---------------------------------------------------------------------------
+struct GLTable {
+    // nodes/weights on [-1,1] for the orders used: 16, 12, 6, 4, 3
+    double x[41], w[41];
+    int off[5], n[5];
+};
+
+__device__ double newell_f_dev(double x, double y, double z) {
+    x = fabs(x); y = fabs(y); z = fabs(z);
+    const double xx = x * x, yy = y * y, zz = z * z, R = sqrt(xx + yy + zz);
+    double r = (2.0 * xx - yy - zz) * R * (1.0 / 6.0);
+    if (y > 0.0 && xx + zz > 0.0) r += 0.5 * y * (zz - xx) * asinh(y / sqrt(xx + zz));
+    if (z > 0.0 && xx + yy > 0.0) r += 0.5 * z * (yy - xx) * asinh(z / sqrt(xx + yy));
+    if (x > 0.0 && y > 0.0 && z > 0.0) r -= x * y * z * atan(y * z / (x * R));
+    return r;
+}
+
+__device__ double newell_g_dev(double x, double y, double z) {
+    double sg = 1.0;
+    if (x < 0.0) { sg = -sg; x = -x; }
+    if (y < 0.0) { sg = -sg; y = -y; }
+    z = fabs(z);
+    const double xx = x * x, yy = y * y, zz = z * z, R = sqrt(xx + yy + zz);
+    double r = -x * y * R * (1.0 / 3.0);
+    if (z > 0.0 && xx + yy > 0.0) r += x * y * z * asinh(z / sqrt(xx + yy));
+    if (x > 0.0 && yy + zz > 0.0) r += y * (3.0 * zz - yy) * asinh(x / sqrt(yy + zz)) * (1.0 / 6.0);
+    if (y > 0.0 && xx + zz > 0.0) r += x * (3.0 * zz - xx) * asinh(y / sqrt(xx + zz)) * (1.0 / 6.0);
+    if (x > 0.0 && y > 0.0 && z > 0.0) {
+        r -= zz * z * atan(x * y / (z * R)) * (1.0 / 6.0);
+        r -= 0.5 * z * yy * atan(x * z / (y * R));
+        r -= 0.5 * z * xx * atan(y * z / (x * R));
+    }
+    return sg * r;
+}
+
+// N at displacement (X,Y,Z) for cell (hx,hy,hz), all lengths already divided
+// by the largest cell edge.  out: xx yy zz xy xz yz.
+__device__ void newell_eval(double X, double Y, double Z, double hx, double hy, double hz,
+                            const GLTable& gl, double* out) {
+    const double d = sqrt(X * X + Y * Y + Z * Z);
+    if (d <= 2.0) {
+        double s[6] = {0, 0, 0, 0, 0, 0};
+        for (int i = -1; i <= 1; ++i)
+            for (int j = -1; j <= 1; ++j)
+                for (int k = -1; k <= 1; ++k) {
+                    const double w = (i ? -1.0 : 2.0) * (j ? -1.0 : 2.0) * (k ? -1.0 : 2.0);
+                    const double x = X + i * hx, y = Y + j * hy, z = Z + k * hz;
+                    s[0] += w * newell_f_dev(x, y, z);
+                    s[1] += w * newell_f_dev(y, x, z);
+                    s[2] += w * newell_f_dev(z, y, x);
+                    s[3] += w * newell_g_dev(x, y, z);
+                    s[4] += w * newell_g_dev(x, z, y);
+                    s[5] += w * newell_g_dev(y, z, x);
+                }
+        const double c = 1.0 / (4.0 * kPi * hx * hy * hz);
+        for (int a = 0; a < 6; ++a) out[a] = c * s[a];
+        return;
+    }
+    const int band = d <= 3.0 ? 0 : d <= 8.0 ? 1 : d <= 32.0 ? 2 : d <= 128.0 ? 3 : 4;
+    const int n = gl.n[band], o = gl.off[band];
+    // tent per axis: nodes t = +-h (1 + xi)/2, weights w h^2 (1 - xi)/4
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < 2 * n; ++i) {
+        const double xi = gl.x[o + (i >> 1)];
+        const double tx = ((i & 1) ? -0.5 : 0.5) * hx * (1.0 + xi);
+        const double wx = gl.w[o + (i >> 1)] * 0.25 * hx * hx * (1.0 - xi);
+        const double rx = X + tx;
+        for (int j = 0; j < 2 * n; ++j) {
+            const double yj = gl.x[o + (j >> 1)];
+            const double ty = ((j & 1) ? -0.5 : 0.5) * hy * (1.0 + yj);
+            const double wy = wx * gl.w[o + (j >> 1)] * 0.25 * hy * hy * (1.0 - yj);
+            const double ry = Y + ty;
+            for (int k = 0; k < 2 * n; ++k) {
+                const double zk = gl.x[o + (k >> 1)];
+                const double tz = ((k & 1) ? -0.5 : 0.5) * hz * (1.0 + zk);
+                const double w = wy * gl.w[o + (k >> 1)] * 0.25 * hz * hz * (1.0 - zk);
+                const double rz = Z + tz;
+                const double r2 = rx * rx + ry * ry + rz * rz;
+                const double ir2 = 1.0 / r2;
+                const double ir3 = ir2 * rsqrt(r2);
+                const double w5 = 3.0 * w * ir3 * ir2;
+                acc[0] += w5 * rx * rx - w * ir3;
+                acc[1] += w5 * ry * ry - w * ir3;
+                acc[2] += w5 * rz * rz - w * ir3;
+                acc[3] += w5 * rx * ry;
+                acc[4] += w5 * rx * rz;
+                acc[5] += w5 * ry * rz;
+            }
+        }
+    }
+    const double c = -1.0 / (4.0 * kPi * hx * hy * hz);
+    for (int a = 0; a < 6; ++a) out[a] = c * acc[a];
+}
+
+__global__ void newell_list_kernel(long count, const int* __restrict__ ijk, double hx, double hy,
+                                   double hz, GLTable gl, double* __restrict__ out) {
+    const long q = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (q >= count) return;
+    const double s = fmax(hx, fmax(hy, hz));
+    double v[6];
+    newell_eval(ijk[3 * q] * hx / s, ijk[3 * q + 1] * hy / s, ijk[3 * q + 2] * hz / s, hx / s, hy / s,
+                hz / s, gl, v);
+    for (int a = 0; a < 6; ++a) out[6 * q + a] = v[a];
+}
+
+__global__ void newell_octant_kernel(int nx, int ny, int nz, double hx, double hy, double hz, GLTable gl,
+                                     double* __restrict__ out) {
+    const long long n = (long long)nx * ny * nz;
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int i = (int)(q % nx), j = (int)((q / nx) % ny), k = (int)(q / ((long long)nx * ny));
+    const double s = fmax(hx, fmax(hy, hz));
+    double v[6];
+    newell_eval(i * hx / s, j * hy / s, k * hz / s, hx / s, hy / s, hz / s, gl, v);
+    for (int a = 0; a < 6; ++a) out[a * n + q] = v[a];
+}
+
+// padded real array of one component from the octant (parity per component)
+__global__ void padded_component_kernel(const double* __restrict__ oct, int comp, int nx, int ny, int nz,
+                                        int Px, int Py, int Pz, double* __restrict__ dst) {
+    const long long P = (long long)Px * Py * Pz;
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= P) return;
+    const int X = (int)(q % Px), Y = (int)((q / Px) % Py), Z = (int)(q / ((long long)Px * Py));
+    const int i = X <= Px / 2 ? X : X - Px;
+    const int j = Y <= Py / 2 ? Y : Y - Py;
+    const int k = Z <= Pz / 2 ? Z : Z - Pz;
+    double v = 0.0;
+    if (abs(i) < nx && abs(j) < ny && abs(k) < nz) {
+        const long long n = (long long)nx * ny * nz;
+        v = oct[comp * n + ((long long)abs(k) * ny + abs(j)) * nx + abs(i)];
+        const int sx = i < 0 ? -1 : 1, sy = j < 0 ? -1 : 1, sz = k < 0 ? -1 : 1;
+        if (comp == 3) v *= sx * sy;
+        else if (comp == 4) v *= sx * sz;
+        else if (comp == 5) v *= sy * sz;
+    }
+    dst[q] = v;
+}
+
+template <typename T>
+__global__ void extract_khat_kernel(const double2* __restrict__ spec, int Wk, int Kx, int Py, int Pz,
+                                    int Ky, int Kz, double scale, T* __restrict__ khat) {
+    const long long n = (long long)Kz * Ky * Wk;
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int kx = (int)(q % Wk), ky = (int)((q / Wk) % Ky), kz = (int)(q / ((long long)Wk * Ky));
+    T v = 0;
+    if (kx < Kx) v = (T)(scale * spec[((long long)kz * Py + ky) * Wk + kx].x);
+    khat[q] = v;
+}
+
+template <typename T>
+__global__ void khat_to_double_kernel(const T* __restrict__ k, long long n, double* __restrict__ out) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q < n) out[q] = (double)k[q];
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static void gauss_legendre_host(int n, double* x, double* w) {
+    for (int i = 0; i < n; ++i) {
+        double t = std::cos(kPi * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 200; ++it) {
+            double p0 = 1.0, p1 = t;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2 * k - 1) * t * p1 - (k - 1) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (t * p1 - p0) / (t * t - 1.0);
+            const double step = p1 / dp;
+            t -= step;
+            if (std::fabs(step) < 1e-17) break;
+        }
+        double p0 = 1.0, p1 = t;
+        for (int k = 2; k <= n; ++k) {
+            const double p2 = ((2 * k - 1) * t * p1 - (k - 1) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = n * (t * p1 - p0) / (t * t - 1.0);
+        x[i] = t;
+        w[i] = 2.0 / ((1.0 - t * t) * dp * dp);
+    }
+}
+
+static GLTable make_gl() {
+    GLTable g{};
+    const int orders[5] = {16, 12, 6, 4, 3};
+    int o = 0;
+    for (int b = 0; b < 5; ++b) {
+        g.off[b] = o;
+        g.n[b] = orders[b];
+        gauss_legendre_host(orders[b], g.x + o, g.w + o);
+        o += orders[b];
+    }
+    return g;
+}
+
+template <typename T>
+static void* make_twiddles(int L) {
+    std::vector<cplx<T>> h(L);
+    for (int q = 0; q < L; ++q) {
+        const double a = -2.0 * kPi * (double)q / (double)L;
+        h[q] = mkc<T>((T)std::cos(a), (T)std::sin(a));
+    }
+    void* d = nullptr;
+    if (cudaMalloc(&d, sizeof(cplx<T>) * L) != cudaSuccess) return nullptr;
+    cudaMemcpy(d, h.data(), sizeof(cplx<T>) * L, cudaMemcpyHostToDevice);
+    return d;
+}
+
+static int col_threads(int L) { return L >= 512 ? 512 : 256; }
+
+static int col_tk(int L, int nc) {
+    const int cap = kMaxV * col_threads(L) / (L * nc);
+    int tk = 1;
+    while (tk * 2 <= cap && tk * 2 <= 16) tk *= 2;
+    return tk;
+}
+
+template <typename T>
+static void launch_x(mm_ctx* c, bool forward, const T* in, T* out_real, cplx<T>* spec, int rows,
+                     int rows_per_plane, int spec_rows_per_plane, int nx, long long in_pitch, int Lh,
+                     const cplx<T>* tw, bool scale_ms, long long cells_per_comp) {
+    XArgs<T> a{};
+    a.in = in;
+    a.out_real = out_real;
+    a.spec = spec;
+    a.in_pitch = in_pitch;
+    a.rows = rows;
+    a.rows_per_plane = rows_per_plane;
+    a.spec_rows_per_plane = spec_rows_per_plane;
+    a.nx = nx;
+    a.Lh = Lh;
+    a.Kx = Lh + 1;
+    a.Wk = c->dm.Wk;
+    make_plan(Lh, &a.plan);
+    a.tw = tw;
+    a.ms_uniform = (T)1;
+    if (scale_ms) {
+        if (c->uniform) a.ms_uniform = (T)c->regions[0].Ms;
+        else {
+            a.region = (const uint8_t*)c->d_region;
+            a.lut = (const Region<T>*)c->d_lut;
+        }
+    }
+    a.cells_per_comp = cells_per_comp;
+    int rpc = std::max(1, kMaxV * 256 / Lh);
+    rpc = std::min(rpc, 16);
+    a.rpc = rpc;
+    const size_t smem = (size_t)rpc * (Lh + 1) * sizeof(cplx<T>);
+    const int grid = (rows + rpc - 1) / rpc;
+    LaunchScope ls(c, forward ? "fft_x_r2c" : "fft_x_c2r",
+                   (double)rows * (nx * sizeof(T) + (Lh + 1) * sizeof(cplx<T>)));
+    if (forward) fft_x_r2c_kernel<T><<<grid, 256, smem, c->stream>>>(a);
+    else fft_x_c2r_kernel<T><<<grid, 256, smem, c->stream>>>(a);
+}
+
+template <typename T, int MODE>
+static void launch_col(mm_ctx* c, ColArgs<T> a, int n_other, const char* name, double bytes) {
+    make_plan(a.L, &a.plan);
+    const int thr = col_threads(a.L);
+    a.TK = col_tk(a.L, a.nc);
+    const size_t smem = (size_t)a.nc * a.TK * (a.L + 1) * sizeof(cplx<T>);
+    dim3 grid((a.Kx + a.TK - 1) / a.TK, n_other);
+    LaunchScope ls(c, name, bytes);
+    fft_col_kernel<T, MODE><<<grid, thr, smem, c->stream>>>(a);
+}
+
+template <typename T>
+static void demag_apply_t(mm_ctx* c, const T* m, T* Hd) {
+    DemagPlan& d = c->dm;
+    const mm_grid& g = c->grid;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    cplx<T>* S = (cplx<T>*)d.spec;
+    const long long plane = (long long)d.PyA * d.Wk;        // one z-plane of one component
+    const long long comp = (long long)nz * plane;
+    const long long N = c->N;
+    const double cplxb = sizeof(cplx<T>), realb = sizeof(T);
+    // X forward: rows (c, z, y) of Ms*m
+    launch_x<T>(c, true, m, nullptr, S, 3 * nz * ny, ny, d.PyA, nx, nx, d.Lh, (const cplx<T>*)d.tw_x, true, N);
+    const bool three_d = nz > 1;
+    if (three_d && d.Py > 1) {
+        ColArgs<T> a{};
+        a.base = S; a.comp_stride = comp; a.line_stride = d.Wk; a.other_stride = plane;
+        a.nc = 3; a.Kx = d.Kx; a.L = d.Py; a.n_in = ny; a.n_out = d.Py;
+        a.tw = (const cplx<T>*)d.tw_y;
+        launch_col<T, 1>(c, a, nz, "fft_y_fwd", 3.0 * nz * d.Kx * (ny + d.Py) * cplxb);
+    }
+    {
+        ColArgs<T> a{};
+        a.base = S; a.comp_stride = comp; a.nc = 3; a.Kx = d.Kx;
+        a.khat = (const T*)d.khat;
+        a.ncomp = d.ncomp;
+        const long long Ky = d.Py / 2 + 1, Kz = d.Pz / 2 + 1;
+        a.kc_stride = Kz * Ky * d.Wk;
+        if (three_d) {
+            a.line_stride = plane; a.other_stride = d.Wk;
+            a.L = d.Pz; a.n_in = nz; a.n_out = nz;
+            a.tw = (const cplx<T>*)d.tw_z;
+            a.kk_stride = Ky * d.Wk; a.ko_stride = d.Wk;
+            a.L_other = d.Py; a.axis_is_y = 0;
+            launch_col<T, 0>(c, a, d.Py, "fft_conv",
+                             3.0 * d.Py * d.Kx * 2 * nz * cplxb + (double)d.ncomp * Kz * Ky * d.Kx * realb);
+        } else {
+            a.line_stride = d.Wk; a.other_stride = plane;
+            a.L = d.Py; a.n_in = ny; a.n_out = ny;
+            a.tw = (const cplx<T>*)d.tw_y;
+            a.kk_stride = d.Wk; a.ko_stride = 0;
+            a.L_other = 1; a.axis_is_y = 1;
+            launch_col<T, 0>(c, a, 1, "fft_conv",
+                             3.0 * d.Kx * 2 * ny * cplxb + (double)d.ncomp * Ky * d.Kx * realb);
+        }
+    }
+    if (three_d && d.Py > 1) {
+        ColArgs<T> a{};
+        a.base = S; a.comp_stride = comp; a.line_stride = d.Wk; a.other_stride = plane;
+        a.nc = 3; a.Kx = d.Kx; a.L = d.Py; a.n_in = d.Py; a.n_out = ny;
+        a.tw = (const cplx<T>*)d.tw_y;
+        launch_col<T, -1>(c, a, nz, "fft_y_inv", 3.0 * nz * d.Kx * (ny + d.Py) * cplxb);
+    }
+    launch_x<T>(c, false, nullptr, Hd, S, 3 * nz * ny, ny, d.PyA, nx, nx, d.Lh, (const cplx<T>*)d.tw_x, false, N);
+}
+
+void demag_apply(mm_ctx* c, const void* m, void* Hd) {
+    if (c->prec == 32) demag_apply_t<float>(c, (const float*)m, (float*)Hd);
+    else demag_apply_t<double>(c, (const double*)m, (double*)Hd);
+}
+
+template <typename T>
+static mm_status demag_setup_t(mm_ctx* c) {
+    DemagPlan& d = c->dm;
+    const mm_grid& g = c->grid;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    d.Px = nice_length(std::max(2, 2 * nx - 1), true);
+    d.Py = ny > 1 ? nice_length(2 * ny - 1, false) : 1;
+    d.Pz = nz > 1 ? nice_length(2 * nz - 1, false) : 1;
+    if (d.Px > 8192 || d.Py > 4096 || d.Pz > 4096)
+        return set_error(c, MM_ERR_ARG, "demag supports padded lengths up to 8192 (x) and 4096 (y, z)");
+    d.Lh = d.Px / 2;
+    d.Kx = d.Lh + 1;
+    d.Wk = (d.Kx + 3) / 4 * 4;
+    d.PyA = nz > 1 ? d.Py : ny;
+    d.ncomp = nz > 1 ? 6 : 4;
+    const int Ky = d.Py / 2 + 1, Kz = d.Pz / 2 + 1;
+    Plan tmp;
+    if (!make_plan(d.Lh, &tmp) || !make_plan(d.Py, &tmp) || !make_plan(d.Pz, &tmp))
+        return set_error(c, MM_ERR_ARG, "internal: padded length is not 2^a 3^b");
+
+    // twiddles in working precision, and FP64 twiddles for the setup FFTs
+    d.tw_x = make_twiddles<T>(d.Px);
+    d.tw_y = make_twiddles<T>(d.Py);
+    d.tw_z = make_twiddles<T>(d.Pz);
+    void* tw64x = make_twiddles<double>(d.Px);
+    void* tw64y = make_twiddles<double>(d.Py);
+    void* tw64z = make_twiddles<double>(d.Pz);
+    if (!d.tw_x || !d.tw_y || !d.tw_z || !tw64x || !tw64y || !tw64z) return set_error(c, MM_ERR_OOM, "twiddles");
+
+    const size_t spec_bytes = (size_t)3 * nz * d.PyA * d.Wk * sizeof(cplx<T>);
+    const size_t khat_bytes = (size_t)d.ncomp * Kz * Ky * d.Wk * sizeof(T);
+    if (cudaMalloc(&d.spec, spec_bytes) != cudaSuccess) return set_error(c, MM_ERR_OOM, "demag spectrum");
+    if (cudaMalloc(&d.khat, khat_bytes) != cudaSuccess) return set_error(c, MM_ERR_OOM, "demag kernel");
+    cudaMemsetAsync(d.spec, 0, spec_bytes, c->stream);
+
+    // FP64 Newell tensor on the non-negative octant
+    const long long noct = (long long)nx * ny * nz;
+    double* oct = nullptr;
+    double* pad = nullptr;
+    double2* sp = nullptr;
+    const long long P = (long long)d.Px * d.Py * d.Pz;
+    const size_t sp_elems = (size_t)d.Pz * d.Py * d.Wk;
+    if (cudaMalloc(&oct, sizeof(double) * 6 * noct) != cudaSuccess ||
+        cudaMalloc(&pad, sizeof(double) * P) != cudaSuccess ||
+        cudaMalloc(&sp, sizeof(double2) * sp_elems) != cudaSuccess) {
+        cudaFree(oct); cudaFree(pad); cudaFree(sp);
+        return set_error(c, MM_ERR_OOM, "demag setup scratch");
+    }
+    GLTable gl = make_gl();
+    {
+        LaunchScope ls(c, "newell_octant", 48.0 * noct);
+        newell_octant_kernel<<<(unsigned)((noct + 127) / 128), 128, 0, c->stream>>>(nx, ny, nz, g.dx, g.dy, g.dz,
+                                                                                   gl, oct);
+    }
+    // temporarily point the X-pass geometry at the padded tensor
+    const int saveWk = d.Wk;
+    for (int comp = 0; comp < d.ncomp; ++comp) {
+        // nz = 1 stores xx, yy, zz, xy (xz = yz = 0)
+        const int src = comp;
+        {
+            LaunchScope ls(c, "newell_pad", 8.0 * P);
+            padded_component_kernel<<<(unsigned)((P + 255) / 256), 256, 0, c->stream>>>(oct, src, nx, ny, nz, d.Px,
+                                                                                        d.Py, d.Pz, pad);
+        }
+        cudaMemsetAsync(sp, 0, sizeof(double2) * sp_elems, c->stream);
+        // X: rows (z, y) of the padded real tensor, all Px entries nonzero
+        launch_x<double>(c, true, pad, nullptr, (cplx<double>*)sp, d.Py * d.Pz, d.Py * d.Pz, d.Py * d.Pz, d.Px,
+                         d.Px, d.Lh, (const cplx<double>*)tw64x, false, P);
+        if (d.Py > 1) {
+            ColArgs<double> a{};
+            a.base = (cplx<double>*)sp; a.comp_stride = 0; a.line_stride = d.Wk;
+            a.other_stride = (long long)d.Py * d.Wk; a.nc = 1; a.Kx = d.Kx;
+            a.L = d.Py; a.n_in = d.Py; a.n_out = d.Py; a.tw = (const cplx<double>*)tw64y;
+            launch_col<double, 1>(c, a, d.Pz, "newell_fft_y", 0.0);
+        }
+        if (d.Pz > 1) {
+            ColArgs<double> a{};
+            a.base = (cplx<double>*)sp; a.comp_stride = 0; a.line_stride = (long long)d.Py * d.Wk;
+            a.other_stride = d.Wk; a.nc = 1; a.Kx = d.Kx;
+            a.L = d.Pz; a.n_in = d.Pz; a.n_out = d.Pz; a.tw = (const cplx<double>*)tw64z;
+            launch_col<double, 1>(c, a, d.Py, "newell_fft_z", 0.0);
+        }
+        const long long nk = (long long)Kz * Ky * saveWk;
+        const double scale = -1.0 / ((double)d.Px * d.Py * d.Pz);
+        LaunchScope ls(c, "newell_extract", 0.0);
+        extract_khat_kernel<T><<<(unsigned)((nk + 255) / 256), 256, 0, c->stream>>>(
+            sp, saveWk, d.Kx, d.Py, d.Pz, Ky, Kz, scale, (T*)d.khat + comp * nk);
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    cudaFree(oct);
+    cudaFree(pad);
+    cudaFree(sp);
+    cudaFree(tw64x);
+    cudaFree(tw64y);
+    cudaFree(tw64z);
+    if (e != cudaSuccess) return cuda_check(c, e, "demag setup");
+    d.on = 1;
+    return MM_OK;
+}
+
+// Opt every FFT kernel into the full 227 KB of dynamic shared memory once,
+// outside any stream capture.
+template <typename T>
+static cudaError_t fft_attributes() {
+    const int mx = 227 * 1024;
+    cudaError_t e = cudaFuncSetAttribute(fft_x_r2c_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fft_x_c2r_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fft_col_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fft_col_kernel<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fft_col_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    return e;
+}
+
+mm_status demag_setup(mm_ctx* c) {
+    cudaError_t e = fft_attributes<float>();
+    if (e == cudaSuccess) e = fft_attributes<double>();
+    if (e != cudaSuccess) return cuda_check(c, e, "FFT kernel attributes");
+    return c->prec == 32 ? demag_setup_t<float>(c) : demag_setup_t<double>(c);
+}
+
+void demag_free(mm_ctx* c) {
+    DemagPlan& d = c->dm;
+    cudaFree(d.spec);
+    cudaFree(d.khat);
+    cudaFree(d.tw_x);
+    cudaFree(d.tw_y);
+    cudaFree(d.tw_z);
+    d = DemagPlan{};
+}
+
+mm_status newell_gpu(long count, const int* ijk, double dx, double dy, double dz, double* out_host) {
+    int* d_ijk = nullptr;
+    double* d_out = nullptr;
+    if (count <= 0) return MM_OK;
+    if (cudaMalloc(&d_ijk, sizeof(int) * 3 * count) != cudaSuccess) return MM_ERR_OOM;
+    if (cudaMalloc(&d_out, sizeof(double) * 6 * count) != cudaSuccess) {
+        cudaFree(d_ijk);
+        return MM_ERR_OOM;
+    }
+    cudaMemcpy(d_ijk, ijk, sizeof(int) * 3 * count, cudaMemcpyHostToDevice);
+    GLTable gl = make_gl();
+    newell_list_kernel<<<(unsigned)((count + 127) / 128), 128>>>(count, d_ijk, dx, dy, dz, gl, d_out);
+    cudaError_t e = cudaMemcpy(out_host, d_out, sizeof(double) * 6 * count, cudaMemcpyDeviceToHost);
+    cudaFree(d_ijk);
+    cudaFree(d_out);
+    return e == cudaSuccess ? MM_OK : MM_ERR_CUDA;
+}
+
+// Stored tensor spectrum -> host doubles (test access).
+mm_status demag_kernel_copy(mm_ctx* c, double* out, size_t n_out, int* dims) {
+    DemagPlan& d = c->dm;
+    if (!d.on) return set_error(c, MM_ERR_STATE, "demag is off");
+    const int Ky = d.Py / 2 + 1, Kz = d.Pz / 2 + 1;
+    const size_t need = (size_t)d.ncomp * Kz * Ky * d.Kx;
+    if (dims) { dims[0] = d.ncomp; dims[1] = d.Px; dims[2] = d.Py; dims[3] = d.Pz; }
+    if (!out) return MM_OK;
+    if (n_out < need) return set_error(c, MM_ERR_ARG, "output too small for the tensor spectrum");
+    const long long nk = (long long)d.ncomp * Kz * Ky * d.Wk;
+    double* tmp = nullptr;
+    if (cudaMalloc(&tmp, sizeof(double) * nk) != cudaSuccess) return set_error(c, MM_ERR_OOM, "copy");
+    if (c->prec == 32) khat_to_double_kernel<float><<<(unsigned)((nk + 255) / 256), 256, 0, c->stream>>>((const float*)d.khat, nk, tmp);
+    else khat_to_double_kernel<double><<<(unsigned)((nk + 255) / 256), 256, 0, c->stream>>>((const double*)d.khat, nk, tmp);
+    std::vector<double> h(nk);
+    cudaError_t e = cudaMemcpyAsync(h.data(), tmp, sizeof(double) * nk, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_check(c, e, "tensor copy");
+    size_t o = 0;
+    for (long long r = 0; r < nk / d.Wk; ++r)
+        for (int kx = 0; kx < d.Kx; ++kx) out[o++] = h[r * d.Wk + kx];
+    return MM_OK;
+}
+
+}  // namespace mm

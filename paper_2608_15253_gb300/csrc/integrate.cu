@@ -1,0 +1,245 @@
+// Integrators (Methods, "Integrators"): Dormand-Prince RK45 (adaptive,
+// first-same-as-last) with the step controller on the device, and Heun
+// (Stratonovich: one thermal draw per step, shared by predictor and
+// corrector).  Every kernel of an attempt reads the device state (dt,
+// active flag), so chunks of attempts are captured once in a CUDA graph and
+// replayed without host round trips.
+//
+// Controller (the paper says only "adaptive, FSAL"): err = max over cells
+// of |dt sum_j e_j k_j|_2; accept when err <= rtol; factor =
+// clamp(0.9 (rtol/err)^(1/5), 0.2, 5), capped at 1 right after a rejection;
+// on accept m <- m5/|m5| and k7 becomes k1 (slot rotation, no copy).
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "common.cuh"
+#include "ctx.h"
+
+namespace mm {
+
+// Dormand & Prince (1980) RK5(4)7FSAL coefficients.
+__constant__ double c_dp_a[7][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {1.0 / 5, 0, 0, 0, 0, 0},
+    {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+    {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
+    {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
+    {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
+    {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84},
+};
+// e_j = b5_j - b4_j
+__constant__ double c_dp_e[7] = {35.0 / 384 - 5179.0 / 57600, 0.0, 500.0 / 1113 - 7571.0 / 16695,
+                                 125.0 / 192 - 393.0 / 640, -2187.0 / 6784 + 92097.0 / 339200,
+                                 11.0 / 84 - 187.0 / 2100, -1.0 / 40};
+
+// k slot of stage j (0-based) under FSAL rotation: slot 0 and 6 swap roles
+__device__ __forceinline__ int kslot_of(int j, int k_first) {
+    if (j == 0) return k_first;
+    if (j == 6) return 6 - k_first;
+    return j;
+}
+
+template <typename T>
+__global__ void combine_kernel(const DevState* __restrict__ st, T* const* __restrict__ kptr,
+                               const T* __restrict__ m0, T* __restrict__ ms, long long n3, int s) {
+    if (!st->active) return;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n3) return;
+    const double dt = st->dt_eff;
+    const int kf = st->k_first;
+    T acc = m0[i];
+    for (int j = 0; j < s; ++j) {
+        const double a = c_dp_a[s][j];
+        if (a != 0.0) acc += (T)(dt * a) * kptr[kslot_of(j, kf)][i];
+    }
+    ms[i] = acc;
+}
+
+// per-cell error |dt sum e_j k_j|, block max, atomic max into st->err(_f)
+template <typename T>
+__global__ void error_kernel(DevState* st, T* const* __restrict__ kptr, long long N) {
+    if (!st->active) return;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const double dt = st->dt_eff;
+    const int kf = st->k_first;
+    T e2 = 0;
+    if (i < N) {
+        T ex = 0, ey = 0, ez = 0;
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {
+            const double e = c_dp_e[j];
+            if (e == 0.0) continue;
+            const T* k = kptr[kslot_of(j, kf)];
+            const T w = (T)(dt * e);
+            ex += w * k[i];
+            ey += w * k[N + i];
+            ez += w * k[2 * N + i];
+        }
+        e2 = sqrt(ex * ex + ey * ey + ez * ez);
+        if (!(e2 == e2)) e2 = (T)INFINITY;   // NaN -> inf: forces a rejection, then underflow status
+    }
+    T bm = warp_max(e2);
+    __shared__ T red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bm;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        T v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : (T)0;
+        v = warp_max(v);
+        if (threadIdx.x == 0) {
+            if (sizeof(T) == 4) atomic_max_nonneg(&st->err_f, (float)v);
+            else atomic_max_nonneg(&st->err, (double)v);
+        }
+    }
+}
+
+// Start of an attempt: decide whether it runs, pick dt_eff, clear the error.
+__global__ void attempt_begin_kernel(DevState* st) {
+    const bool more = st->accepted < st->target && st->t < st->t_end && st->status == 0;
+    st->active = more ? 1 : 0;
+    if (!more) return;
+    double dt = st->dt;
+    if (st->replay) {
+        const long long q = st->accepted;
+        dt = q < st->replay_n ? st->replay_dts[q] : 0.0;
+    }
+    if (st->t + dt > st->t_end) dt = st->t_end - st->t;
+    st->dt_eff = dt;
+    st->err = 0.0;
+    st->err_f = 0.0f;
+    st->attempts += 1;
+}
+
+// After the error reduction: accept / reject and the next step size.
+__global__ void controller_kernel(DevState* st, int prec) {
+    st->accept = 0;
+    if (!st->active) return;
+    const double err = prec == 32 ? (double)st->err_f : st->err;
+    const double dt = st->dt_eff;
+    if (st->replay) {
+        st->accept = 1;
+    } else {
+        double fac = err > 0.0 ? 0.9 * pow(st->rtol / err, 0.2) : 5.0;
+        if (!(fac == fac)) fac = 0.2;
+        fac = fmin(fmax(fac, 0.2), 5.0);
+        if (err <= st->rtol) {
+            if (st->last_rejected) fac = fmin(fac, 1.0);
+            st->accept = 1;
+            st->last_rejected = 0;
+            // a step clipped to land on t_end keeps the unclipped size
+            const double base = dt < st->dt ? st->dt : dt;
+            st->dt = fmin(base * fac, st->dt_max);
+        } else {
+            st->last_rejected = 1;
+            st->rejected += 1;
+            const double nd = dt * fac;
+            if (nd < st->dt_min || !(err < INFINITY)) {
+                st->status = !(err < INFINITY) ? MM_ERR_NONFINITE : MM_ERR_DT_UNDERFLOW;
+            }
+            st->dt = fmax(nd, st->dt_min);
+        }
+    }
+    if (st->accept) {
+        st->t += dt;
+        st->accepted += 1;
+        st->step += 1;
+        st->k_first = 6 - st->k_first;   // FSAL: k7 becomes k1
+    }
+}
+
+template <typename T>
+__global__ void accept_kernel(const DevState* __restrict__ st, const T* __restrict__ m5, T* __restrict__ m0,
+                              long long N) {
+    if (!st->active || !st->accept) return;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const T x = m5[i], y = m5[N + i], z = m5[2 * N + i];
+    const T n2 = x * x + y * y + z * z;
+    const T inv = n2 > (T)0 ? (T)1 / sqrt(n2) : (T)0;
+    m0[i] = x * inv;
+    m0[N + i] = y * inv;
+    m0[2 * N + i] = z * inv;
+}
+
+// Heun step bookkeeping (fixed dt): t += dt, step += 1.
+__global__ void heun_advance_kernel(DevState* st) {
+    if (!st->active) return;
+    st->t += st->dt;
+    st->step += 1;
+    st->accepted += 1;
+    st->attempts += 1;
+}
+
+__global__ void heun_begin_kernel(DevState* st) {
+    st->active = (st->accepted < st->target && st->t < st->t_end && st->status == 0) ? 1 : 0;
+    st->dt_eff = st->dt;
+}
+
+template <typename T>
+static void rk45_attempt_t(mm_ctx* c) {
+    const long long N = c->N, n3 = 3 * N;
+    const unsigned tb = 256, nb3 = (unsigned)((n3 + tb - 1) / tb), nb = (unsigned)((N + tb - 1) / tb);
+    {
+        LaunchScope ls(c, "rk_begin", 0.0);
+        attempt_begin_kernel<<<1, 1, 0, c->stream>>>(c->d_state);
+    }
+    T* const* kp = (T* const*)c->d_kslot;
+    const unsigned terms = c->terms;
+    const bool demag = c->dm.on && (terms & MM_TERM_DEMAG);
+    for (int s = 1; s < 7; ++s) {
+        {
+            LaunchScope ls(c, "rk_combine", (double)sizeof(T) * n3 * (1 + s));
+            combine_kernel<T><<<nb3, tb, 0, c->stream>>>(c->d_state, kp, (const T*)c->d_m, (T*)c->d_mtmp, n3, s);
+        }
+        if (demag) demag_apply(c, c->d_mtmp, c->d_hd);
+        // stages 2..6 own fixed slots; the FSAL stage 7 slope goes to the slot
+        // that does not hold k1 (resolved on the device)
+        field_launch(c, MODE_K, terms, c->d_mtmp, demag ? c->d_hd : nullptr, s < 6 ? c->d_k[s] : nullptr, nullptr,
+                     nullptr, nullptr, -1, 1, 6);
+    }
+    {
+        LaunchScope ls(c, "rk_error", (double)sizeof(T) * 3 * N * 6);
+        error_kernel<T><<<nb, tb, 0, c->stream>>>(c->d_state, kp, N);
+    }
+    {
+        LaunchScope ls(c, "rk_control", 0.0);
+        controller_kernel<<<1, 1, 0, c->stream>>>(c->d_state, c->prec);
+    }
+    {
+        LaunchScope ls(c, "rk_accept", (double)sizeof(T) * 6 * N);
+        accept_kernel<T><<<nb, tb, 0, c->stream>>>(c->d_state, (const T*)c->d_mtmp, (T*)c->d_m, N);
+    }
+}
+
+void rk45_attempt(mm_ctx* c) {
+    if (c->prec == 32) rk45_attempt_t<float>(c);
+    else rk45_attempt_t<double>(c);
+}
+
+void rk45_first_slope(mm_ctx* c) {
+    const unsigned terms = c->terms;
+    const bool demag = c->dm.on && (terms & MM_TERM_DEMAG);
+    if (demag) demag_apply(c, c->d_m, c->d_hd);
+    field_launch(c, MODE_K, terms, c->d_m, demag ? c->d_hd : nullptr, nullptr, nullptr, nullptr, nullptr, -1, 0, 0);
+}
+
+void heun_step(mm_ctx* c) {
+    const unsigned terms = c->terms;
+    const bool demag = c->dm.on && (terms & MM_TERM_DEMAG);
+    {
+        LaunchScope ls(c, "heun_begin", 0.0);
+        heun_begin_kernel<<<1, 1, 0, c->stream>>>(c->d_state);
+    }
+    // predictor: k1 = f(m, H(m) + H_th); m* = m + dt k1
+    if (demag) demag_apply(c, c->d_m, c->d_hd);
+    field_launch(c, MODE_HEUN1, terms, c->d_m, demag ? c->d_hd : nullptr, c->d_mtmp, c->d_k[0], nullptr, nullptr,
+                 -1, 1, 0);
+    // corrector: m' = normalise(m + dt/2 (k1 + f(m*, H(m*) + H_th))), same noise
+    if (demag) demag_apply(c, c->d_mtmp, c->d_hd);
+    field_launch(c, MODE_HEUN2, terms, c->d_mtmp, demag ? c->d_hd : nullptr, c->d_m, nullptr, c->d_m, c->d_k[0],
+                 -1, 1, 0);
+    LaunchScope ls(c, "heun_advance", 0.0);
+    heun_advance_kernel<<<1, 1, 0, c->stream>>>(c->d_state);
+}
+
+}  // namespace mm

@@ -1,0 +1,146 @@
+"""GPU parity of whole steps: RK45 replayed on the oracle's accepted step
+sequence (so accept/reject decisions cannot diverge), Heun with the Philox
+thermal field and spin torques, and the device-side step controller.
+
+Bar: max over cells of |m_gpu - m_oracle| after the stated number of steps
+<= 1e-11 in FP64 and <= 1e-5 in FP32."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_util import make_ctx, need_gpu, oracle_problem
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_solver(grid, mat, m, B=(0, 0, 0), **kw):
+    from oracle.llg import Solver
+    p = oracle_problem(grid, mat, B)
+    return Solver(p, m, **kw)
+
+
+CASES = [
+    ("film3d", W.Grid(12, 8, 3, 2e-9, 2e-9, 2e-9),
+     W.Material(Ms=5.8e5, A=1.5e-11, alpha=0.1, Ku1=8e5, u=(0, 0, 1), D=3e-3), (0.0, 0.0, 0.0)),
+    ("film2d", W.Grid(32, 8, 1, 3.90625e-9, 3.90625e-9, 3e-9),
+     W.Material(Ms=8e5, A=1.3e-11, alpha=0.02), (-24.6e-3, 4.3e-3, 0.0)),
+    ("odd", W.Grid(17, 5, 2, 2e-9, 3e-9, 1e-9),
+     W.Material(Ms=7e5, A=1.1e-11, alpha=0.3, Ku1=2e5, u=(0.6, 0, 0.8), D=1.5e-3), (0.0, 0.02, 0.01)),
+]
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("ci", range(len(CASES)))
+def test_rk45_replay_matches_oracle(prec, ci):
+    mm = need_gpu()
+    name, grid, mat, B = CASES[ci]
+    m0 = W.random_m(grid, seed=20 + ci)
+    o = _oracle_solver(grid, mat, m0, B, dt=1e-14, rtol=1e-6)
+    nsteps = 40
+    dts = [o.rk45_step() for _ in range(nsteps)]
+    ctx = make_ctx(mm, grid, mat, precision=prec, demag=True, B=B, dt=1e-14, rtol=1e-6)
+    try:
+        mm.mm_set_m(ctx, 0, m0)
+        mm.mm_step_dt(ctx, dts)
+        m = mm.mm_get_m(ctx, 0, m0.shape)
+        t, _, n = mm.mm_get_time(ctx)
+        assert n == nsteps and abs(t - sum(dts)) < 1e-24
+        err = np.abs(m - o.m).max()
+        assert err <= (1e-11 if prec == 64 else 1e-5), err
+    finally:
+        mm.mm_destroy(ctx)
+
+
+def test_rk45_controller_follows_oracle_fp64():
+    """Free adaptive run: the device controller takes the same accepted
+    step sizes as the oracle's (FP64, same tableau and controller)."""
+    mm = need_gpu()
+    name, grid, mat, B = CASES[0]
+    m0 = W.random_m(grid, seed=5)
+    o = _oracle_solver(grid, mat, m0, B, dt=1e-14, rtol=1e-6)
+    ctx = make_ctx(mm, grid, mat, precision=64, demag=True, B=B, dt=1e-14, rtol=1e-6)
+    try:
+        mm.mm_set_m(ctx, 0, m0)
+        for _ in range(30):
+            o.rk45_step()
+        mm.mm_step(ctx, 30)
+        t, dt, n = mm.mm_get_time(ctx)
+        assert n == 30
+        assert abs(t - o.t) <= 1e-9 * o.t
+        assert abs(dt - o.dt) <= 1e-8 * o.dt
+        assert np.abs(mm.mm_get_m(ctx, 0, m0.shape) - o.m).max() < 1e-9
+    finally:
+        mm.mm_destroy(ctx)
+
+
+def test_run_lands_on_t_end():
+    mm = need_gpu()
+    name, grid, mat, B = CASES[1]
+    ctx = make_ctx(mm, grid, mat, precision=32, demag=True, B=B, dt=1e-14, rtol=1e-6)
+    try:
+        mm.mm_set_m(ctx, 0, W.m_uniform_perturbed(grid, seed=1))
+        mm.mm_run(ctx, 7.3e-12)
+        t, _, n = mm.mm_get_time(ctx)
+        assert abs(t - 7.3e-12) < 1e-24 and n > 0
+        m = mm.mm_get_m(ctx, 0, (3, grid.nz, grid.ny, grid.nx))
+        assert np.abs(np.sqrt((m * m).sum(0)) - 1).max() < 1e-6
+    finally:
+        mm.mm_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("torque", ["sot", "stt", "zl"])
+def test_heun_thermal_with_torque_matches_oracle(prec, torque):
+    mm = need_gpu()
+    from oracle.llg import Torque, replica_seed
+    grid = W.Grid(20, 12, 1, 2e-9, 2e-9, 1e-9)
+    mat = W.Material(Ms=1.1e6, A=2e-11, alpha=0.01, Ku1=9e5, u=(0, 0, 1))
+    J = 2.0e11
+    if torque == "sot":
+        tq_o = Torque(kind="sot", J=J, p=(0, 1, 0), theta_SH=0.1, fl_ratio=0.2)
+        tq_g = mm.make_torque(mm.MM_TORQUE_SOT, p=(0, 1, 0), theta_SH=0.1, fl_ratio=0.2)
+    elif torque == "stt":
+        tq_o = Torque(kind="stt", J=J, p=(0.2, 0, 1), P=0.6, Lambda=1.5, eps_prime=0.05)
+        tq_g = mm.make_torque(mm.MM_TORQUE_STT, p=(0.2, 0, 1), P=0.6, Lambda=1.5, eps_prime=0.05)
+    else:
+        J = 5e12
+        tq_o = Torque(kind="zl", J=J, P=0.5, xi=0.05, direction=(1, 0.5, 0))
+        tq_g = mm.make_torque(mm.MM_TORQUE_ZL, P=0.5, xi=0.05, direction=(1, 0.5, 0))
+    m0 = W.m_perp(grid, seed=3, tilt=0.3)
+    seed = 11
+    o = _oracle_solver(grid, mat, m0, terms=("exchange", "anisotropy", "demag"), torque=tq_o, T=300.0,
+                       seed=replica_seed(seed, 0), dt=1e-14)
+    ctx = make_ctx(mm, grid, mat, precision=prec, integrator="heun", demag=True, dt=1e-14, T=300.0, seed=seed)
+    try:
+        mm.mm_set_m(ctx, 0, m0)
+        mm.mm_set_torque(ctx, tq_g, [J])
+        n = 60
+        for _ in range(n):
+            o.heun_step()
+        mm.mm_step(ctx, n)
+        err = np.abs(mm.mm_get_m(ctx, 0, m0.shape) - o.m).max()
+        assert err <= (1e-11 if prec == 64 else 1e-5), err
+    finally:
+        mm.mm_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_zhang_li_with_rk45_replay(prec):
+    mm = need_gpu()
+    from oracle.llg import Torque
+    grid = W.Grid(24, 6, 2, 2e-9, 2e-9, 2e-9)
+    mat = W.Material(Ms=8e5, A=1.3e-11, alpha=0.05, Ku1=5e5, u=(0, 0, 1), D=1e-3)
+    m0 = W.random_m(grid, seed=9)
+    tq_o = Torque(kind="zl", J=3e12, P=0.6, xi=0.1, direction=(1, 0, 0), match_mumax=True)
+    o = _oracle_solver(grid, mat, m0, torque=tq_o, dt=1e-14, rtol=1e-6)
+    dts = [o.rk45_step() for _ in range(25)]
+    ctx = make_ctx(mm, grid, mat, precision=prec, demag=True, dt=1e-14)
+    try:
+        mm.mm_set_m(ctx, 0, m0)
+        mm.mm_set_torque(ctx, mm.make_torque(mm.MM_TORQUE_ZL, P=0.6, xi=0.1, direction=(1, 0, 0), match_mumax=1),
+                         [3e12])
+        mm.mm_step_dt(ctx, dts)
+        err = np.abs(mm.mm_get_m(ctx, 0, m0.shape) - o.m).max()
+        assert err <= (1e-11 if prec == 64 else 1e-5), err
+    finally:
+        mm.mm_destroy(ctx)
