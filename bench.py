@@ -196,6 +196,10 @@ def run_gpu(args):
         from paper_2608_15253_gb300 import build as B
         B.build()
     w = W.dmi_256x256x16()
+    if args.grid:
+        nx, ny, nz = (int(v) for v in args.grid.split(","))
+        from dataclasses import replace
+        w = replace(w, name=f"dmi_{nx}x{ny}x{nz}_rk45", grid=W.Grid(nx, ny, nz, 2e-9, 2e-9, 2e-9))
     g = w.grid
     M = mm.Material(w.mat.Ms, w.mat.A, w.mat.alpha, w.mat.Ku1, w.mat.u, w.mat.D)
     cfg = mm.make_config(precision=32, integrator=mm.MM_RK45, demag=mm.MM_DEMAG_EXACT, dt=1e-14, rtol=w.rtol)
@@ -272,7 +276,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": t_max / max(1, steps), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "cells": g.n, "grid": [g.nx, g.ny, g.nz], "cell_nm": [2, 2, 2],
-                   "integrator": "rk45-dopri5", "rtol": w.rtol, "demag": "exact-fft 512x512x32",
+                   "integrator": "rk45-dopri5", "rtol": w.rtol, "demag": f"exact-fft {2*g.nx}x{2*g.ny}x{2*g.nz}",
                    "precision": "fp32 (fp64 Newell setup)", "parallelism": f"replicas x{ws}",
                    "accepted_steps": steps, "attempts": attempts,
                    "l2": "working set ~220 MB > 126 MB L2 (state, 7 slopes, spectrum, tensor)"},
@@ -303,6 +307,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", default="", help="nx,ny,nz: a smaller case of the same workload (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
