@@ -147,8 +147,14 @@ MM_API mm_status mm_create(const mm_grid* grid, const mm_material* mat,
                            const mm_config* cfg, mm_ctx** out);
 
 /* Create R replicas of possibly different grids sharing one material
- * (Methods, "Replica batching"); seeds may be NULL (then splitmix64(seed+r)).
- * Grids must be nz = 1 films when R > 1 and sizes differ. */
+ * (Methods, "Replica batching"): state replica-outermost, each replica with
+ * its own Philox key (seeds[r], or splitmix64(cfg->seed + r) when seeds is
+ * NULL), temperature (mm_set_temperature) and current (mm_set_torque).
+ * R = 1 is the single-instance context.  For R > 1: FP32, Heun, nz = 1
+ * open films sharing one cell size and one uniform material (Ms > 0);
+ * nx, ny may differ per replica (sizes of the same shape share one tensor
+ * spectrum).  Each Heun stage is one persistent launch (mm_batch_autotune
+ * picks its shape).  Errors: MM_ERR_ARG for any other combination. */
 MM_API mm_status mm_create_batch(int R, const mm_grid* grids, const mm_material* mat,
                                  const mm_config* cfg, const uint64_t* seeds, mm_ctx** out);
 
@@ -222,6 +228,15 @@ MM_API mm_status mm_get_demag_kernel(mm_ctx* ctx, double* out, size_t n_out, int
 /* FP64 Newell tensor evaluated on the GPU at count integer displacements
  * ijk[3*q..3*q+2] of cells dx*dy*dz; out[6*q+c] in xx,yy,zz,xy,xz,yz. */
 MM_API mm_status mm_newell(long count, const int* ijk, double dx, double dy, double dz, double* out);
+
+/* Launch-shape autotuner of a replica-batched context (Methods, "Replica
+ * batching": one persistent launch per stage).  Times a few Heun steps for
+ * every candidate (threads per CTA x resident CTAs per SM), keeps the
+ * fastest and restores the state (m, t, step counters) afterwards.  When
+ * cache_path is non-NULL the choice is read from / appended to that JSON
+ * file, keyed by the replica-size histogram.  nt_out / blocks_out may be
+ * NULL.  MM_ERR_STATE for single-instance contexts. */
+MM_API mm_status mm_batch_autotune(mm_ctx* ctx, const char* cache_path, int* nt_out, int* blocks_out);
 
 /* Per-kernel CUDA-event timing (graphs are bypassed while on). */
 MM_API mm_status mm_set_profiling(mm_ctx* ctx, int on);

@@ -180,6 +180,8 @@ static mm_status status_from_device(mm_ctx* c) {
 static void free_all(mm_ctx* c) {
     invalidate_graph(c);
     demag_free(c);
+    batch_free(c->batch);
+    c->batch = nullptr;
     void* bufs[] = {c->d_region, c->d_lut, c->d_cpair, c->d_m, c->d_mtmp, c->d_kslot, c->d_hd, c->d_hbuf,
                     c->d_bcell, c->d_state, c->d_replay, c->d_red};
     for (void* b : bufs) cudaFree(b);
@@ -336,10 +338,97 @@ mm_status mm_create(const mm_grid* grid, const mm_material* mat, const mm_config
 
 mm_status mm_create_batch(int R, const mm_grid* grids, const mm_material* mat, const mm_config* cfg,
                           const uint64_t* seeds, mm_ctx** out) {
-    if (R != 1) return set_error(nullptr, MM_ERR_ARG, "mm_create_batch: use the replica engine (mm_batch_*) for R > 1");
-    mm_status s = mm_create(grids, mat, cfg, out);
-    if (s == MM_OK && seeds) (*out)->seed = seeds[0];
-    return s;
+    if (!grids || !mat || !cfg || !out || R <= 0) return set_error(nullptr, MM_ERR_ARG, "null argument or R <= 0");
+    *out = nullptr;
+    if (R == 1) {
+        mm_status s = mm_create(grids, mat, cfg, out);
+        if (s == MM_OK && seeds) (*out)->seed = seeds[0];
+        return s;
+    }
+    // replica-batched thin films (Methods, "Replica batching")
+    if (cfg->precision != 32) return set_error(nullptr, MM_ERR_ARG, "replica batching runs in FP32");
+    if (cfg->integrator != MM_HEUN) return set_error(nullptr, MM_ERR_ARG, "replica batching integrates with Heun");
+    if (cfg->demag == MM_DEMAG_SURROGATE) return set_error(nullptr, MM_ERR_ARG, "surrogate demag is single-instance");
+    if (!(cfg->dt > 0)) return set_error(nullptr, MM_ERR_ARG, "dt must be positive");
+    if (mat->Ms_cell || mat->A_cell || mat->alpha_cell || mat->Ku1_cell || mat->u_cell || mat->D_cell || !(mat->Ms > 0))
+        return set_error(nullptr, MM_ERR_ARG, "replica batching takes one uniform material with Ms > 0");
+    for (int r = 0; r < R; ++r) {
+        const mm_grid& g = grids[r];
+        if (g.nx <= 0 || g.ny <= 0 || g.nz != 1) return set_error(nullptr, MM_ERR_ARG, "batched replicas are nz = 1 films");
+        if (g.dx != grids[0].dx || g.dy != grids[0].dy || g.dz != grids[0].dz || !(g.dx > 0) || !(g.dy > 0) || !(g.dz > 0))
+            return set_error(nullptr, MM_ERR_ARG, "batched replicas share one cell size");
+        if (g.pbc[0] || g.pbc[1] || g.pbc[2]) return set_error(nullptr, MM_ERR_ARG, "batched replicas are open films");
+        if (g.nx > 1024 || g.ny > 1024) return set_error(nullptr, MM_ERR_ARG, "batched replicas are at most 1024 x 1024");
+    }
+    mm_ctx* c = new mm_ctx();
+    mm_status s = check_device(c);
+    if (s != MM_OK) {
+        g_create_error = c->last_error;
+        delete c;
+        return s;
+    }
+    c->prec = 32;
+    c->esz = 4;
+    c->integrator = MM_HEUN;
+    c->terms = cfg->terms ? cfg->terms : MM_TERM_ALL;
+    if (cfg->demag != MM_DEMAG_EXACT) c->terms &= ~MM_TERM_DEMAG;
+    c->cfg = *cfg;
+    c->R = R;
+    c->grid = grids[0];
+    c->Tr = cfg->T;
+    long long off = 0, maxN = 0;
+    for (int r = 0; r < R; ++r) {
+        c->rgrid.push_back(grids[r]);
+        c->roff.push_back(off);
+        const long long n = (long long)grids[r].nx * grids[r].ny;
+        off += 3 * n;
+        maxN = std::max(maxN, n);
+        c->rkey.push_back(seeds ? seeds[r] : splitmix64(cfg->seed + (uint64_t)r));
+        c->rT.push_back(cfg->T);
+        c->rJ.push_back(0.0);
+    }
+    c->Ntot = off / 3;
+    c->N = maxN;
+    c->seed = c->rkey[0];
+    cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
+    c->stream = c->own_stream;
+#define TRY(x) do { mm_status _s = (x); if (_s != MM_OK) { g_create_error = c->last_error; free_all(c); delete c; return _s; } } while (0)
+    TRY(build_regions(c, mat));
+    TRY(upload_regions_t<float>(c));
+    const size_t vb = 3 * c->Ntot * 4;
+    TRY(alloc(c, &c->d_m, vb, "state"));
+    TRY(alloc(c, &c->d_mtmp, vb, "predictor state"));
+    TRY(alloc(c, &c->d_k[0], vb, "predictor slope"));
+    TRY(alloc(c, &c->d_hbuf, 3 * maxN * 4, "field scratch"));
+    TRY(alloc(c, &c->d_hd, 3 * maxN * 4, "demag field"));
+    TRY(alloc(c, &c->d_kslot, sizeof(void*) * 7, "slot table"));
+    cudaMemcpy(c->d_kslot, c->d_k, sizeof(void*) * 7, cudaMemcpyHostToDevice);
+    TRY(alloc(c, (void**)&c->d_state, sizeof(DevState), "device state"));
+    c->red_cap = 2 * 304 + 16;
+    TRY(alloc(c, (void**)&c->d_red, sizeof(double) * c->red_cap, "reduction partials"));
+    c->batch = batch_new();
+    TRY(batch_setup(c, c->batch, c->rgrid, c->rkey, (c->terms & MM_TERM_DEMAG) != 0));
+    TRY(batch_upload(c, c->batch, c->rT, c->rJ));
+    {
+        std::vector<float> h(3 * c->Ntot, 0.f);
+        for (int r = 0; r < R; ++r) {
+            const long long n = (long long)grids[r].nx * grids[r].ny;
+            for (long long i = 0; i < n; ++i) h[c->roff[r] + 2 * n + i] = 1.f;
+        }
+        cudaMemcpy(c->d_m, h.data(), vb, cudaMemcpyHostToDevice);
+    }
+    DevState& st = c->h_state;
+    st = DevState{};
+    st.dt = cfg->dt;
+    st.rtol = 1e-6;
+    st.dt_min = 1e-20;
+    st.dt_max = 1e-11;
+    st.t_end = std::numeric_limits<double>::infinity();
+    TRY(push_state(c));
+    TRY(cuda_check(c, cudaDeviceSynchronize(), "create batch"));
+#undef TRY
+    *out = c;
+    return MM_OK;
 }
 
 mm_status mm_destroy(mm_ctx* c) {
@@ -362,9 +451,38 @@ mm_status mm_set_stream(mm_ctx* c, void* stream) {
 
 static mm_status check_replica(mm_ctx* c, int r) {
     if (!c) return MM_ERR_ARG;
-    if (r != 0) return set_error(c, MM_ERR_ARG, "replica index out of range");
+    if (r < 0 || r >= c->R) return set_error(c, MM_ERR_ARG, "replica index out of range");
     return MM_OK;
 }
+
+// Points the single-instance view of the context (grid, N, state pointer,
+// seed, temperature, current, demag plan) at replica r of a batch, so the
+// per-instance observables run unchanged; restored on scope exit.
+struct ReplicaView {
+    mm_ctx* c;
+    bool on;
+    mm_grid g;
+    long long N;
+    void* m;
+    uint64_t seed;
+    double T, J;
+    DemagPlan dm;
+    ReplicaView(mm_ctx* cc, int r) : c(cc), on(cc->batch != nullptr) {
+        if (!on) return;
+        g = c->grid; N = c->N; m = c->d_m; seed = c->seed; T = c->Tr; J = c->J; dm = c->dm;
+        c->grid = c->rgrid[r];
+        c->N = (long long)c->grid.nx * c->grid.ny;
+        c->d_m = (char*)c->d_m + c->roff[r] * 4;
+        c->seed = c->rkey[r];
+        c->Tr = c->rT[r];
+        c->J = c->rJ[r];
+        if (c->terms & MM_TERM_DEMAG) c->dm = batch_plan(c->batch, batch_class_of(c->batch, r));
+    }
+    ~ReplicaView() {
+        if (!on) return;
+        c->grid = g; c->N = N; c->d_m = m; c->seed = seed; c->Tr = T; c->J = J; c->dm = dm;
+    }
+};
 
 extern "C" {
 
@@ -372,6 +490,7 @@ mm_status mm_set_m(mm_ctx* c, int r, const double* m) {
     mm_status s = check_replica(c, r);
     if (s != MM_OK) return s;
     if (!m) return set_error(c, MM_ERR_ARG, "null m");
+    ReplicaView view(c, r);
     const size_t vb = 3 * c->N * c->esz;
     cudaError_t e;
     if (c->prec == 32) {
@@ -392,6 +511,7 @@ mm_status mm_set_m(mm_ctx* c, int r, const double* m) {
 mm_status mm_get_m(mm_ctx* c, int r, double* m) {
     mm_status s = check_replica(c, r);
     if (s != MM_OK) return s;
+    ReplicaView view(c, r);
     const long long n3 = 3 * c->N;
     cudaError_t e;
     if (c->prec == 32) {
@@ -408,21 +528,31 @@ mm_status mm_get_m(mm_ctx* c, int r, double* m) {
 
 mm_status mm_set_m_device(mm_ctx* c, const void* m) {
     if (!c || !m) return MM_ERR_ARG;
-    cudaError_t e = cudaMemcpyAsync(c->d_m, m, 3 * c->N * c->esz, cudaMemcpyDeviceToDevice, c->stream);
-    normalize_launch(c, c->d_m);
+    const long long ncell = c->batch ? c->Ntot : c->N;
+    cudaError_t e = cudaMemcpyAsync(c->d_m, m, 3 * ncell * c->esz, cudaMemcpyDeviceToDevice, c->stream);
+    if (c->batch) {
+        for (int r = 0; r < c->R; ++r) {
+            ReplicaView view(c, r);
+            normalize_launch(c, c->d_m);
+        }
+    } else {
+        normalize_launch(c, c->d_m);
+    }
     c->k1_valid = false;
     return cuda_check(c, e, "mm_set_m_device");
 }
 
 mm_status mm_get_m_device(mm_ctx* c, void* m) {
     if (!c || !m) return MM_ERR_ARG;
-    return cuda_check(c, cudaMemcpyAsync(m, c->d_m, 3 * c->N * c->esz, cudaMemcpyDeviceToDevice, c->stream),
+    const long long ncell = c->batch ? c->Ntot : c->N;
+    return cuda_check(c, cudaMemcpyAsync(m, c->d_m, 3 * ncell * c->esz, cudaMemcpyDeviceToDevice, c->stream),
                       "mm_get_m_device");
 }
 
 mm_status mm_set_field(mm_ctx* c, int r, const double B[3], const double* B_cell) {
     mm_status s = check_replica(c, r);
     if (s != MM_OK) return s;
+    if (c->batch && B_cell) return set_error(c, MM_ERR_ARG, "batched replicas take one uniform applied field");
     if (B) for (int d = 0; d < 3; ++d) c->Hext[d] = B[d] / kMu0;
     else for (int d = 0; d < 3; ++d) c->Hext[d] = 0.0;
     if (B_cell) {
@@ -453,9 +583,15 @@ mm_status mm_set_field(mm_ctx* c, int r, const double B[3], const double* B_cell
 
 mm_status mm_set_temperature(mm_ctx* c, const double* T) {
     if (!c || !T) return MM_ERR_ARG;
-    if (T[0] < 0) return set_error(c, MM_ERR_ARG, "negative temperature");
+    for (int r = 0; r < c->R; ++r)
+        if (!(T[r] >= 0)) return set_error(c, MM_ERR_ARG, "negative temperature");
     if (T[0] > 0 && c->integrator == MM_RK45) return set_error(c, MM_ERR_ARG, "RK45 with T > 0; use Heun");
     c->Tr = T[0];
+    if (c->batch) {
+        for (int r = 0; r < c->R; ++r) c->rT[r] = T[r];
+        mm_status s = batch_upload(c, c->batch, c->rT, c->rJ);
+        if (s != MM_OK) return s;
+    }
     invalidate_graph(c);
     return MM_OK;
 }
@@ -463,8 +599,14 @@ mm_status mm_set_temperature(mm_ctx* c, const double* T) {
 mm_status mm_set_torque(mm_ctx* c, const mm_torque* tq, const double* J) {
     if (!c || !tq) return MM_ERR_ARG;
     if (tq->kind < MM_TORQUE_NONE || tq->kind > MM_TORQUE_ZL) return set_error(c, MM_ERR_ARG, "bad torque kind");
+    if (c->batch && tq->kind == MM_TORQUE_ZL) return set_error(c, MM_ERR_ARG, "batched replicas take SOT or STT");
     c->tq = *tq;
     c->J = J ? J[0] : 0.0;
+    if (c->batch) {
+        for (int r = 0; r < c->R; ++r) c->rJ[r] = J ? J[r] : 0.0;
+        mm_status s = batch_upload(c, c->batch, c->rT, c->rJ);
+        if (s != MM_OK) return s;
+    }
     c->k1_valid = false;
     invalidate_graph(c);
     return MM_OK;
@@ -475,7 +617,8 @@ mm_status mm_set_torque(mm_ctx* c, const mm_torque* tq, const double* J) {
 // one chunk of `n` integrator attempts (or Heun steps) on the stream
 static void launch_attempts(mm_ctx* c, int n) {
     for (int q = 0; q < n; ++q) {
-        if (c->integrator == MM_RK45) rk45_attempt(c);
+        if (c->batch) batch_heun_step(c, c->batch);
+        else if (c->integrator == MM_RK45) rk45_attempt(c);
         else heun_step(c);
     }
 }
@@ -615,6 +758,7 @@ mm_status mm_run(mm_ctx* c, double t_end) {
 mm_status mm_get_heff(mm_ctx* c, int r, double* H, unsigned mask) {
     mm_status s = check_replica(c, r);
     if (s != MM_OK) return s;
+    ReplicaView view(c, r);
     if (!H) return set_error(c, MM_ERR_ARG, "null output");
     const unsigned terms = mask & (c->terms | MM_TERM_THERMAL);
     const bool demag = (terms & MM_TERM_DEMAG) && c->dm.on;
@@ -637,6 +781,7 @@ mm_status mm_get_heff(mm_ctx* c, int r, double* H, unsigned mask) {
 mm_status mm_energy(mm_ctx* c, int r, double* E) {
     mm_status s = check_replica(c, r);
     if (s != MM_OK) return s;
+    ReplicaView view(c, r);
     if (!E) return set_error(c, MM_ERR_ARG, "null output");
     static const unsigned term_of[5] = {MM_TERM_EXCHANGE, MM_TERM_DMI, MM_TERM_ANISOTROPY, MM_TERM_ZEEMAN, MM_TERM_DEMAG};
     double* d_out = c->d_red + 2 * 304;
@@ -665,6 +810,7 @@ mm_status mm_energy(mm_ctx* c, int r, double* E) {
 mm_status mm_topo_charge(mm_ctx* c, int r, int layer, double* Q) {
     mm_status s = check_replica(c, r);
     if (s != MM_OK) return s;
+    ReplicaView view(c, r);
     if (!Q || layer >= c->grid.nz) return set_error(c, MM_ERR_ARG, "bad layer or null output");
     double* d_out = c->d_red + 2 * 304 + 8;
     topo_launch(c, c->d_m, layer, d_out);
@@ -711,7 +857,7 @@ struct CkptHeader {
 
 mm_status mm_get_state(mm_ctx* c, void* buf, size_t* nbytes) {
     if (!c || !nbytes) return MM_ERR_ARG;
-    const size_t vb = 3 * c->N * c->esz;
+    const size_t vb = 3 * (c->batch ? c->Ntot : c->N) * c->esz;
     const bool k1 = c->integrator == MM_RK45;
     const size_t need = sizeof(CkptHeader) + sizeof(DevState) + vb * (k1 ? 2 : 1);
     if (!buf) { *nbytes = need; return MM_OK; }
@@ -720,7 +866,8 @@ mm_status mm_get_state(mm_ctx* c, void* buf, size_t* nbytes) {
     if (s != MM_OK) return s;
     CkptHeader h{};
     memcpy(h.magic, "MMCKPT1", 8);
-    h.prec = c->prec; h.integrator = c->integrator; h.N = c->N; h.seed = c->seed; h.k1_valid = c->k1_valid;
+    h.prec = c->prec; h.integrator = c->integrator; h.N = c->batch ? c->Ntot : c->N; h.seed = c->seed;
+    h.k1_valid = c->k1_valid;
     char* p = (char*)buf;
     memcpy(p, &h, sizeof h);
     memcpy(p + sizeof h, &c->h_state, sizeof(DevState));
@@ -738,13 +885,14 @@ mm_status mm_get_state(mm_ctx* c, void* buf, size_t* nbytes) {
 
 mm_status mm_set_state(mm_ctx* c, const void* buf, size_t nbytes) {
     if (!c || !buf) return MM_ERR_ARG;
-    const size_t vb = 3 * c->N * c->esz;
+    const size_t vb = 3 * (c->batch ? c->Ntot : c->N) * c->esz;
     const bool k1 = c->integrator == MM_RK45;
     const size_t need = sizeof(CkptHeader) + sizeof(DevState) + vb * (k1 ? 2 : 1);
     if (nbytes < need) return set_error(c, MM_ERR_ARG, "checkpoint too small");
     CkptHeader h;
     memcpy(&h, buf, sizeof h);
-    if (memcmp(h.magic, "MMCKPT1", 8) != 0 || h.prec != c->prec || h.integrator != c->integrator || h.N != c->N)
+    if (memcmp(h.magic, "MMCKPT1", 8) != 0 || h.prec != c->prec || h.integrator != c->integrator ||
+        h.N != (c->batch ? c->Ntot : c->N))
         return set_error(c, MM_ERR_ARG, "checkpoint does not match this context");
     const char* p = (const char*)buf;
     DevState st;
@@ -768,6 +916,7 @@ mm_status mm_set_state(mm_ctx* c, const void* buf, size_t nbytes) {
 mm_status mm_get_thermal(mm_ctx* c, int r, long long step, uint32_t* raw, double* H_th) {
     mm_status s = check_replica(c, r);
     if (s != MM_OK) return s;
+    ReplicaView view(c, r);
     uint32_t* d_raw = nullptr;
     if (raw) {
         s = alloc(c, (void**)&d_raw, sizeof(uint32_t) * 4 * c->N, "thermal words");
@@ -805,6 +954,101 @@ mm_status mm_newell(long count, const int* ijk, double dx, double dy, double dz,
     mm_status s = check_device(&tmp);
     if (s != MM_OK) { g_create_error = tmp.last_error; return s; }
     return newell_gpu(count, ijk, dx, dy, dz, out);
+}
+
+static bool cache_lookup(const char* path, const std::string& key, int* nt, int* blocks) {
+    if (!path) return false;
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    while (fgets(line, sizeof line, f)) {
+        const std::string l(line);
+        const std::string tag = "\"" + key + "\"";
+        const size_t p = l.find(tag);
+        if (p == std::string::npos) continue;
+        int a = 0, b = 0;
+        if (sscanf(l.c_str() + p + tag.size(), ": {\"nt\": %d, \"blocks\": %d", &a, &b) == 2 && a > 0 && b > 0) {
+            *nt = a;
+            *blocks = b;
+            found = true;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+mm_status mm_batch_autotune(mm_ctx* c, const char* cache_path, int* nt_out, int* blocks_out) {
+    if (!c) return MM_ERR_ARG;
+    if (!c->batch) return set_error(c, MM_ERR_STATE, "autotuning applies to replica-batched contexts");
+    const std::string key = batch_signature(c->batch, c->terms);
+    int nt = 0, blocks = 0;
+    if (cache_lookup(cache_path, key, &nt, &blocks)) {
+        batch_set_shape(c->batch, nt, blocks);
+        invalidate_graph(c);
+    } else {
+        mm_status s = sync_state(c);
+        if (s != MM_OK) return s;
+        const DevState saved = c->h_state;
+        const size_t vb = 3 * c->Ntot * 4;
+        void* backup = nullptr;
+        s = alloc(c, &backup, vb, "autotune backup");
+        if (s != MM_OK) return s;
+        cudaMemcpyAsync(backup, c->d_m, vb, cudaMemcpyDeviceToDevice, c->stream);
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        float best = 1e30f;
+        int bnt = 256, bblocks = std::min(c->R, 2 * sms);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        const bool prof = c->profiling;
+        c->profiling = false;
+        for (int cand_nt : {256, 512}) {
+            const int occ = batch_occupancy(c->batch, cand_nt);
+            for (int k = 1; k <= std::max(1, occ); ++k) {
+                const int nb = std::min(c->R, k * sms);
+                batch_set_shape(c->batch, cand_nt, nb);
+                c->h_state.target = std::numeric_limits<long long>::max();
+                c->h_state.t_end = std::numeric_limits<double>::infinity();
+                push_state(c);
+                launch_attempts(c, 1);     // warm-up
+                cudaEventRecord(e0, c->stream);
+                launch_attempts(c, 3);
+                cudaEventRecord(e1, c->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) { best = ms; bnt = cand_nt; bblocks = nb; }
+                if (nb == c->R) break;
+            }
+        }
+        c->profiling = prof;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaMemcpyAsync(c->d_m, backup, vb, cudaMemcpyDeviceToDevice, c->stream);
+        cudaStreamSynchronize(c->stream);
+        cudaFree(backup);
+        c->h_state = saved;
+        s = push_state(c);
+        if (s != MM_OK) return s;
+        batch_set_shape(c->batch, bnt, bblocks);
+        invalidate_graph(c);
+        if (cache_path) {
+            FILE* f = fopen(cache_path, "a");
+            if (f) {
+                fprintf(f, "{\"%s\": {\"nt\": %d, \"blocks\": %d, \"ms_per_step\": %.6f}}\n", key.c_str(), bnt,
+                        bblocks, best / 3.0f);
+                fclose(f);
+            }
+        }
+        nt = bnt;
+        blocks = bblocks;
+    }
+    if (nt_out) *nt_out = nt;
+    if (blocks_out) *blocks_out = blocks;
+    return cuda_check(c, cudaGetLastError(), "autotune");
 }
 
 mm_status mm_set_profiling(mm_ctx* c, int on) {

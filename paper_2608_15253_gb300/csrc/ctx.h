@@ -58,6 +58,12 @@ struct DevState {
     long long target;           // stop after this many accepted steps
     long long replay_n;
     const double* replay_dts;
+    // dt-scaled tableau of the current attempt in working precision, set once
+    // per attempt so that the per-element kernels do no FP64 arithmetic
+    float cf32[7][7];           // dt * a_sj
+    float ce32[7];              // dt * (b5_j - b4_j)
+    double cf64[7][7];
+    double ce64[7];
 };
 
 struct DemagPlan {
@@ -73,6 +79,8 @@ struct DemagPlan {
     void* tw_y = nullptr;         // exp(-2 pi i k / Py)
     void* tw_z = nullptr;         // exp(-2 pi i k / Pz)
 };
+
+struct BatchHost;
 
 struct ProfileSlot {
     std::string name;
@@ -137,6 +145,14 @@ struct mm_ctx {
     int graph_chunk = 0;
     long long launches_per_chunk = 0;
 
+    // replica batching (R > 1): per-replica grids, offsets, keys, T and J
+    mm::BatchHost* batch = nullptr;
+    std::vector<mm_grid> rgrid;
+    std::vector<long long> roff;       // element offset of replica r's [3][ny][nx] block
+    std::vector<uint64_t> rkey;
+    std::vector<double> rT, rJ;
+    long long Ntot = 0;                // cells over all replicas
+
     long long launches = 0;
     bool profiling = false;
     std::vector<mm::ProfileSlot> prof;
@@ -171,7 +187,27 @@ void field_launch(mm_ctx* c, int mode, unsigned terms, const void* m, const void
                   int gate, int kstage);
 void thermal_raw_launch(mm_ctx* c, long long step, uint32_t* d_raw, void* d_h);
 
+// batch.cu
+BatchHost* batch_new();
+void batch_free(BatchHost* b);
+mm_status batch_setup(mm_ctx* c, BatchHost* b, const std::vector<mm_grid>& grids, const std::vector<uint64_t>& keys,
+                      bool demag);
+mm_status batch_upload(mm_ctx* c, BatchHost* b, const std::vector<double>& T, const std::vector<double>& J);
+void batch_heun_step(mm_ctx* c, BatchHost* b);
+void batch_set_shape(BatchHost* b, int nt, int blocks);
+int batch_max_blocks(BatchHost* b);
+size_t batch_smem_for(BatchHost* b, int nt);
+mm_status demag_setup_for(mm_ctx* c, const mm_grid& g, DemagPlan* out);
+void demag_free_plan(DemagPlan& d);
+const DemagPlan& batch_plan(BatchHost* b, int r_cls);
+int batch_occupancy(BatchHost* b, int nt);
+void batch_get_shape(BatchHost* b, int* nt, int* blocks);
+std::string batch_signature(BatchHost* b, unsigned terms);
+int batch_class_of(BatchHost* b, int r);
+
 // integrate.cu
+void heun_batch_begin(mm_ctx* c);
+void heun_batch_advance(mm_ctx* c);
 void rk45_first_slope(mm_ctx* c);          // k1 = f(m0) into the FSAL slot
 void rk45_attempt(mm_ctx* c);               // one attempted DOPRI5 step
 void heun_step(mm_ctx* c);                  // one Heun step

@@ -21,128 +21,10 @@
 
 #include "common.cuh"
 #include "ctx.h"
+#include "fft_ct.cuh"
+#include "fft_rt.cuh"
 
 namespace mm {
-
-// ---------------------------------------------------------------------------
-// FFT plan and in-shared-memory Stockham passes
-// ---------------------------------------------------------------------------
-constexpr int kMaxPasses = 16;
-constexpr int kMaxV = 24;   // complex values held in registers per thread per pass
-
-struct Plan {
-    int L;
-    int npass;
-    int radix[kMaxPasses];
-};
-
-static bool make_plan(int L, Plan* p) {
-    p->L = L;
-    p->npass = 0;
-    int n = L;
-    while (n % 4 == 0) { p->radix[p->npass++] = 4; n /= 4; }
-    while (n % 2 == 0) { p->radix[p->npass++] = 2; n /= 2; }
-    while (n % 3 == 0) { p->radix[p->npass++] = 3; n /= 3; }
-    return n == 1 && p->npass <= kMaxPasses;
-}
-
-// smallest 2^a 3^b >= n (even when want_even)
-static int nice_length(int n, bool want_even) {
-    int best = 1 << 30;
-    for (long long p2 = 1; p2 < (1LL << 31); p2 *= 2)
-        for (long long p3 = p2; p3 < (1LL << 31); p3 *= 3) {
-            if (p3 >= n && p3 < best && (!want_even || p3 % 2 == 0)) best = (int)p3;
-            if (p3 >= n) break;
-        }
-    return best;
-}
-
-template <typename T, int DIR, int R>
-__device__ __forceinline__ void dft(cplx<T>* v) {
-    if (R == 2) {
-        cplx<T> a = v[0], b = v[1];
-        v[0] = cadd<T>(a, b);
-        v[1] = csub<T>(a, b);
-    } else if (R == 4) {
-        cplx<T> a0 = cadd<T>(v[0], v[2]), a1 = csub<T>(v[0], v[2]);
-        cplx<T> a2 = cadd<T>(v[1], v[3]), a3 = mul_mi<T, DIR>(csub<T>(v[1], v[3]));
-        v[0] = cadd<T>(a0, a2);
-        v[2] = csub<T>(a0, a2);
-        v[1] = cadd<T>(a1, a3);
-        v[3] = csub<T>(a1, a3);
-    } else {  // R == 3
-        const T s3 = (T)0.86602540378443864676;
-        cplx<T> t1 = cadd<T>(v[1], v[2]);
-        cplx<T> t2 = csub<T>(v[0], cscale<T>(t1, (T)0.5));
-        cplx<T> t3 = cscale<T>(mul_mi<T, DIR>(csub<T>(v[1], v[2])), s3);
-        v[0] = cadd<T>(v[0], t1);
-        v[1] = cadd<T>(t2, t3);
-        v[2] = csub<T>(t2, t3);
-    }
-}
-
-// One in-place Stockham pass over nl lines of length L stored at `pitch`
-// (complex elements) in shared memory.  Every thread first loads all the
-// butterflies it owns into registers, the block synchronises, then the
-// results are written to their autosorted positions.  Inputs at index
-// >= nin are zero (pruned, only meaningful on the first pass).
-template <typename T, int DIR, int R>
-__device__ void stockham_pass(cplx<T>* sm, int nl, int pitch, int L, int Ns, int nin,
-                              const cplx<T>* __restrict__ tw, int tw_stride) {
-    constexpr int MAXB = kMaxV / R;
-    const int nb = L / R;
-    const int total = nl * nb;
-    cplx<T> v[MAXB][R];
-#pragma unroll
-    for (int i = 0; i < MAXB; ++i) {
-        const int b = threadIdx.x + i * blockDim.x;
-        if (b < total) {
-            const int l = b / nb, j = b - l * nb;
-#pragma unroll
-            for (int t = 0; t < R; ++t) {
-                const int idx = j + t * nb;
-                v[i][t] = idx < nin ? sm[l * pitch + idx] : mkc<T>(0, 0);
-            }
-        }
-    }
-    __syncthreads();
-    const int span = L / (Ns * R);
-#pragma unroll
-    for (int i = 0; i < MAXB; ++i) {
-        const int b = threadIdx.x + i * blockDim.x;
-        if (b < total) {
-            const int l = b / nb, j = b - l * nb;
-            const int k = j % Ns;
-            if (Ns > 1) {
-#pragma unroll
-                for (int t = 1; t < R; ++t) {
-                    cplx<T> w = __ldg(&tw[(t * k * span) * tw_stride]);
-                    v[i][t] = DIR > 0 ? cmul<T>(v[i][t], w) : cmulc<T>(v[i][t], w);
-                }
-            }
-            dft<T, DIR, R>(v[i]);
-            const int dst = (j / Ns) * Ns * R + k;
-#pragma unroll
-            for (int t = 0; t < R; ++t) sm[l * pitch + dst + t * Ns] = v[i][t];
-        }
-    }
-    __syncthreads();
-}
-
-// Full FFT of nl lines; twiddle table tw holds exp(-2 pi i q / (L*tw_stride)).
-template <typename T, int DIR>
-__device__ void fft_lines(cplx<T>* sm, int nl, int pitch, const Plan& p, int nin,
-                          const cplx<T>* __restrict__ tw, int tw_stride) {
-    int Ns = 1;
-    for (int s = 0; s < p.npass; ++s) {
-        const int r = p.radix[s];
-        const int ni = s == 0 ? nin : p.L;
-        if (r == 4) stockham_pass<T, DIR, 4>(sm, nl, pitch, p.L, Ns, ni, tw, tw_stride);
-        else if (r == 2) stockham_pass<T, DIR, 2>(sm, nl, pitch, p.L, Ns, ni, tw, tw_stride);
-        else stockham_pass<T, DIR, 3>(sm, nl, pitch, p.L, Ns, ni, tw, tw_stride);
-        Ns *= r;
-    }
-}
 
 // ---------------------------------------------------------------------------
 // X passes: real rows <-> half spectra
@@ -173,87 +55,89 @@ __device__ __forceinline__ long long spec_row(const XArgs<T>& a, int r) {
     return (long long)(r / a.rows_per_plane) * a.spec_rows_per_plane + (r % a.rows_per_plane);
 }
 
-template <typename T>
+// LT > 0: compile-time half length (specialised FFT), LT == 0: runtime plan
+template <typename T, int LT>
 __global__ void __launch_bounds__(256) fft_x_r2c_kernel(XArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw);
-    const int pitch = a.Lh + 1;
+    const int Lh = LT > 0 ? LT : a.Lh;
+    const int pitch = Lh + 1;
     const int r0 = blockIdx.x * a.rpc;
     const int nl = min(a.rpc, a.rows - r0);
     // load real rows as packed complex z[n] = x[2n] + i x[2n+1]
     T* smr = reinterpret_cast<T*>(sm);
-    const int nreal = 2 * a.Lh;
-    for (int e = threadIdx.x; e < nl * nreal; e += blockDim.x) {
-        const int l = e / nreal, q = e - l * nreal;
-        T v = 0;
-        if (q < a.nx) {
-            const long long gi = (long long)(r0 + l) * a.in_pitch + q;
-            v = a.in[gi];
-            if (a.region) {
-                const long long cell = gi % a.cells_per_comp;
-                v *= a.lut[a.region[cell]].Ms;
-            } else {
-                v *= a.ms_uniform;
+    const int nreal = 2 * Lh;
+    for (int l = 0; l < nl; ++l) {
+        const long long g0 = (long long)(r0 + l) * a.in_pitch;
+        T ms = a.ms_uniform;
+        for (int q = threadIdx.x; q < nreal; q += blockDim.x) {
+            T v = 0;
+            if (q < a.nx) {
+                v = a.in[g0 + q];
+                if (a.region) v *= a.lut[a.region[(g0 + q) % a.cells_per_comp]].Ms;
+                else v *= ms;
             }
+            smr[2 * (l * pitch) + q] = v;
         }
-        smr[2 * (l * pitch) + q] = v;
     }
     __syncthreads();
     const int nin = (a.nx + 1) / 2;
-    fft_lines<T, 1>(sm, nl, pitch, a.plan, nin, a.tw, 2);
+    if constexpr (LT > 0) ct_fft<T, 1, LT, LT + 1, 256, kMaxV>(sm, nl, nin, a.tw, 2);
+    else fft_lines<T, 1>(sm, nl, pitch, a.plan, nin, a.tw, 2);
     // split: X[k] = (Z[k] + conj Z[M-k])/2 - i/2 W^k (Z[k] - conj Z[M-k])
-    const int M = a.Lh;
-    for (int e = threadIdx.x; e < nl * a.Kx; e += blockDim.x) {
-        const int l = e / a.Kx, k = e - l * a.Kx;
-        const cplx<T> zk = sm[l * pitch + (k % M)];
-        const cplx<T> zc = cconj<T>(sm[l * pitch + ((M - k) % M)]);
-        const cplx<T> E = cscale<T>(cadd<T>(zk, zc), (T)0.5);
-        const cplx<T> O = cscale<T>(mul_mi<T, 1>(csub<T>(zk, zc)), (T)0.5);
-        const cplx<T> w = __ldg(&a.tw[k]);
-        a.spec[spec_row(a, r0 + l) * a.Wk + k] = cadd<T>(E, cmul<T>(w, O));
+    const int M = Lh, Kx = Lh + 1;
+    for (int l = 0; l < nl; ++l) {
+        cplx<T>* out = a.spec + spec_row(a, r0 + l) * a.Wk;
+        for (int k = threadIdx.x; k < Kx; k += blockDim.x) {
+            const cplx<T> zk = sm[l * pitch + (k == M ? 0 : k)];
+            const cplx<T> zc = cconj<T>(sm[l * pitch + (k == 0 ? 0 : M - k)]);
+            const cplx<T> E = cscale<T>(cadd<T>(zk, zc), (T)0.5);
+            const cplx<T> O = cscale<T>(mul_mi<T, 1>(csub<T>(zk, zc)), (T)0.5);
+            const cplx<T> w = __ldg(&a.tw[k]);
+            out[k] = cadd<T>(E, cmul<T>(w, O));
+        }
     }
 }
 
-template <typename T>
+template <typename T, int LT>
 __global__ void __launch_bounds__(256) fft_x_c2r_kernel(XArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw);
-    const int pitch = a.Lh + 1;
+    const int Lh = LT > 0 ? LT : a.Lh;
+    const int pitch = Lh + 1;
     const int r0 = blockIdx.x * a.rpc;
     const int nl = min(a.rpc, a.rows - r0);
-    const int M = a.Lh;
-    for (int e = threadIdx.x; e < nl * a.Kx; e += blockDim.x) {
-        const int l = e / a.Kx, k = e - l * a.Kx;
-        sm[l * pitch + k] = a.spec[spec_row(a, r0 + l) * a.Wk + k];
+    const int M = Lh, Kx = Lh + 1;
+    for (int l = 0; l < nl; ++l) {
+        const cplx<T>* in = a.spec + spec_row(a, r0 + l) * a.Wk;
+        for (int k = threadIdx.x; k < Kx; k += blockDim.x) sm[l * pitch + k] = in[k];
     }
     __syncthreads();
     // rebuild Z'[k] = E' + i O', E' = X[k] + conj X[M-k],
     // O' = (X[k] - conj X[M-k]) conj(W^k); pairs (k, M-k) owned by one thread
     const int half = M / 2;
-    for (int e = threadIdx.x; e < nl * (half + 1); e += blockDim.x) {
-        const int l = e / (half + 1), k = e - l * (half + 1);
-        const int k2 = M - k;
-        const cplx<T> xk = sm[l * pitch + k];
-        const cplx<T> xk2 = sm[l * pitch + k2];
-        const cplx<T> w1 = __ldg(&a.tw[k]);
-        const cplx<T> w2 = __ldg(&a.tw[k2]);
-        // for k
-        cplx<T> E1 = cadd<T>(xk, cconj<T>(xk2));
-        cplx<T> O1 = cmulc<T>(csub<T>(xk, cconj<T>(xk2)), w1);
-        cplx<T> Z1 = cadd<T>(E1, mul_mi<T, -1>(O1));
-        // for M-k (only when distinct and < M)
-        cplx<T> E2 = cadd<T>(xk2, cconj<T>(xk));
-        cplx<T> O2 = cmulc<T>(csub<T>(xk2, cconj<T>(xk)), w2);
-        cplx<T> Z2 = cadd<T>(E2, mul_mi<T, -1>(O2));
-        sm[l * pitch + k] = Z1;
-        if (k2 != k && k2 < M) sm[l * pitch + k2] = Z2;
+    for (int l = 0; l < nl; ++l) {
+        for (int k = threadIdx.x; k <= half; k += blockDim.x) {
+            const int k2 = M - k;
+            const cplx<T> xk = sm[l * pitch + k];
+            const cplx<T> xk2 = sm[l * pitch + k2];
+            const cplx<T> w1 = __ldg(&a.tw[k]);
+            const cplx<T> w2 = __ldg(&a.tw[k2]);
+            const cplx<T> E1 = cadd<T>(xk, cconj<T>(xk2));
+            const cplx<T> O1 = cmulc<T>(csub<T>(xk, cconj<T>(xk2)), w1);
+            const cplx<T> E2 = cadd<T>(xk2, cconj<T>(xk));
+            const cplx<T> O2 = cmulc<T>(csub<T>(xk2, cconj<T>(xk)), w2);
+            sm[l * pitch + k] = cadd<T>(E1, mul_mi<T, -1>(O1));
+            if (k2 != k && k2 < M) sm[l * pitch + k2] = cadd<T>(E2, mul_mi<T, -1>(O2));
+        }
     }
     __syncthreads();
-    fft_lines<T, -1>(sm, nl, pitch, a.plan, M, a.tw, 2);
+    if constexpr (LT > 0) ct_fft<T, -1, LT, LT + 1, 256, kMaxV>(sm, nl, M, a.tw, 2);
+    else fft_lines<T, -1>(sm, nl, pitch, a.plan, M, a.tw, 2);
     const T* smr = reinterpret_cast<const T*>(sm);
-    for (int e = threadIdx.x; e < nl * a.nx; e += blockDim.x) {
-        const int l = e / a.nx, q = e - l * a.nx;
-        a.out_real[(long long)(r0 + l) * a.in_pitch + q] = smr[2 * (l * pitch) + q];
+    for (int l = 0; l < nl; ++l) {
+        T* out = a.out_real + (long long)(r0 + l) * a.in_pitch;
+        for (int q = threadIdx.x; q < a.nx; q += blockDim.x) out[q] = smr[2 * (l * pitch) + q];
     }
 }
 
@@ -282,7 +166,7 @@ struct ColArgs {
 };
 
 template <typename T>
-__device__ __forceinline__ void tensor_multiply(const ColArgs<T>& a, cplx<T>* sm, int pitch, int kx0) {
+__device__ __forceinline__ void tensor_multiply(const ColArgs<T>& a, cplx<T>* sm, int pitch, int kx0, int L, int tks) {
     const int other = blockIdx.y;
     // fold the other-axis frequency (3-D: ky) to the stored half range
     int ko = 0, so = 1;
@@ -290,12 +174,12 @@ __device__ __forceinline__ void tensor_multiply(const ColArgs<T>& a, cplx<T>* sm
         ko = other <= a.L_other / 2 ? other : a.L_other - other;
         so = other <= a.L_other / 2 ? 1 : -1;
     }
-    for (int e = threadIdx.x; e < a.TK * a.L; e += blockDim.x) {
-        const int kxl = e % a.TK, kk = e / a.TK;
+    for (int e = threadIdx.x; e < (L << tks); e += blockDim.x) {
+        const int kxl = e & (a.TK - 1), kk = e >> tks;
         const int kx = kx0 + kxl;
         if (kx >= a.Kx) continue;
-        const int kkf = kk <= a.L / 2 ? kk : a.L - kk;
-        const int sk = kk <= a.L / 2 ? 1 : -1;
+        const int kkf = kk <= L / 2 ? kk : L - kk;
+        const int sk = kk <= L / 2 ? 1 : -1;
         const T* K = a.khat + (long long)kkf * a.kk_stride + (long long)ko * a.ko_stride + kx;
         const T kxx = __ldg(K), kyy = __ldg(K + a.kc_stride), kzz = __ldg(K + 2 * a.kc_stride);
         T kxy = __ldg(K + 3 * a.kc_stride);
@@ -319,37 +203,47 @@ __device__ __forceinline__ void tensor_multiply(const ColArgs<T>& a, cplx<T>* sm
     __syncthreads();
 }
 
-template <typename T, int MODE>  // MODE: +1 forward, -1 inverse, 0 convolution
+template <typename T, int MODE, int LT>  // MODE: +1 forward, -1 inverse, 0 convolution
 __global__ void __launch_bounds__(512) fft_col_kernel(ColArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw);
-    const int pitch = a.L + 1;
+    const int L = LT > 0 ? LT : a.L;
+    const int pitch = L + 1;
     const int kx0 = blockIdx.x * a.TK;
     const long long obase = (long long)blockIdx.y * a.other_stride;
     const int nl = a.nc * a.TK;
-    // load
-    for (int e = threadIdx.x; e < a.nc * a.n_in * a.TK; e += blockDim.x) {
-        const int kxl = e % a.TK;
-        const int rest = e / a.TK;
-        const int pt = rest % a.n_in, c = rest / a.n_in;
-        const int kx = kx0 + kxl;
-        cplx<T> v = mkc<T>(0, 0);
-        if (kx < a.Kx) v = a.base[c * a.comp_stride + obase + pt * a.line_stride + kx];
-        sm[(c * a.TK + kxl) * pitch + pt] = v;
+    const int tks = __ffs(a.TK) - 1;            // TK is a power of two
+    const int tkm = a.TK - 1;
+    // load: consecutive threads take consecutive kx (coalesced rows of TK)
+    for (int c = 0; c < a.nc; ++c) {
+        const cplx<T>* src = a.base + c * a.comp_stride + obase + kx0;
+        for (int e = threadIdx.x; e < (a.n_in << tks); e += blockDim.x) {
+            const int kxl = e & tkm, pt = e >> tks;
+            cplx<T> v = mkc<T>(0, 0);
+            if (kx0 + kxl < a.Kx) v = src[pt * a.line_stride + kxl];
+            sm[((c << tks) + kxl) * pitch + pt] = v;
+        }
     }
     __syncthreads();
-    if (MODE >= 0) fft_lines<T, 1>(sm, nl, pitch, a.plan, a.n_in, a.tw, 1);
-    else fft_lines<T, -1>(sm, nl, pitch, a.plan, a.n_in, a.tw, 1);
-    if (MODE == 0) {
-        tensor_multiply<T>(a, sm, pitch, kx0);
-        fft_lines<T, -1>(sm, nl, pitch, a.plan, a.L, a.tw, 1);
+    constexpr int NT = LT >= 512 ? 512 : 256;
+    if constexpr (LT > 0) {
+        if (MODE >= 0) ct_fft<T, 1, LT, LT + 1, NT, kMaxV>(sm, nl, a.n_in, a.tw, 1);
+        else ct_fft<T, -1, LT, LT + 1, NT, kMaxV>(sm, nl, a.n_in, a.tw, 1);
+    } else {
+        if (MODE >= 0) fft_lines<T, 1>(sm, nl, pitch, a.plan, a.n_in, a.tw, 1);
+        else fft_lines<T, -1>(sm, nl, pitch, a.plan, a.n_in, a.tw, 1);
     }
-    for (int e = threadIdx.x; e < a.nc * a.n_out * a.TK; e += blockDim.x) {
-        const int kxl = e % a.TK;
-        const int rest = e / a.TK;
-        const int pt = rest % a.n_out, c = rest / a.n_out;
-        const int kx = kx0 + kxl;
-        if (kx < a.Kx) a.base[c * a.comp_stride + obase + pt * a.line_stride + kx] = sm[(c * a.TK + kxl) * pitch + pt];
+    if (MODE == 0) {
+        tensor_multiply<T>(a, sm, pitch, kx0, L, tks);
+        if constexpr (LT > 0) ct_fft<T, -1, LT, LT + 1, NT, kMaxV>(sm, nl, LT, a.tw, 1);
+        else fft_lines<T, -1>(sm, nl, pitch, a.plan, L, a.tw, 1);
+    }
+    for (int c = 0; c < a.nc; ++c) {
+        cplx<T>* dst = a.base + c * a.comp_stride + obase + kx0;
+        for (int e = threadIdx.x; e < (a.n_out << tks); e += blockDim.x) {
+            const int kxl = e & tkm, pt = e >> tks;
+            if (kx0 + kxl < a.Kx) dst[pt * a.line_stride + kxl] = sm[((c << tks) + kxl) * pitch + pt];
+        }
     }
 }
 
@@ -578,6 +472,40 @@ static int col_tk(int L, int nc) {
     return tk;
 }
 
+// Lengths with a compile-time FFT (FP32): every half-length and column
+// length of the benchmark workloads; other lengths and FP64 take the
+// runtime-planned path.
+#define MM_CT_LENGTHS(X) X(16) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(512) X(1024)
+
+template <typename T> using XKern = void (*)(XArgs<T>);
+template <typename T> using CKern = void (*)(ColArgs<T>);
+
+template <typename T>
+static XKern<T> x_kernel(bool fwd, int Lh) {
+    if constexpr (sizeof(T) == 4) {
+        switch (Lh) {
+#define MM_CASE(n) case n: return fwd ? fft_x_r2c_kernel<T, n> : fft_x_c2r_kernel<T, n>;
+            MM_CT_LENGTHS(MM_CASE)
+#undef MM_CASE
+            default: break;
+        }
+    }
+    return fwd ? fft_x_r2c_kernel<T, 0> : fft_x_c2r_kernel<T, 0>;
+}
+
+template <typename T, int MODE>
+static CKern<T> col_kernel(int L) {
+    if constexpr (sizeof(T) == 4) {
+        switch (L) {
+#define MM_CASE(n) case n: return fft_col_kernel<T, MODE, n>;
+            MM_CT_LENGTHS(MM_CASE)
+#undef MM_CASE
+            default: break;
+        }
+    }
+    return fft_col_kernel<T, MODE, 0>;
+}
+
 template <typename T>
 static void launch_x(mm_ctx* c, bool forward, const T* in, T* out_real, cplx<T>* spec, int rows,
                      int rows_per_plane, int spec_rows_per_plane, int nx, long long in_pitch, int Lh,
@@ -612,8 +540,7 @@ static void launch_x(mm_ctx* c, bool forward, const T* in, T* out_real, cplx<T>*
     const int grid = (rows + rpc - 1) / rpc;
     LaunchScope ls(c, forward ? "fft_x_r2c" : "fft_x_c2r",
                    (double)rows * (nx * sizeof(T) + (Lh + 1) * sizeof(cplx<T>)));
-    if (forward) fft_x_r2c_kernel<T><<<grid, 256, smem, c->stream>>>(a);
-    else fft_x_c2r_kernel<T><<<grid, 256, smem, c->stream>>>(a);
+    x_kernel<T>(forward, Lh)<<<grid, 256, smem, c->stream>>>(a);
 }
 
 template <typename T, int MODE>
@@ -624,7 +551,7 @@ static void launch_col(mm_ctx* c, ColArgs<T> a, int n_other, const char* name, d
     const size_t smem = (size_t)a.nc * a.TK * (a.L + 1) * sizeof(cplx<T>);
     dim3 grid((a.Kx + a.TK - 1) / a.TK, n_other);
     LaunchScope ls(c, name, bytes);
-    fft_col_kernel<T, MODE><<<grid, thr, smem, c->stream>>>(a);
+    col_kernel<T, MODE>(a.L)<<<grid, thr, smem, c->stream>>>(a);
 }
 
 template <typename T>
@@ -789,14 +716,24 @@ static mm_status demag_setup_t(mm_ctx* c) {
 
 // Opt every FFT kernel into the full 227 KB of dynamic shared memory once,
 // outside any stream capture.
+template <typename K>
+static cudaError_t smem_attr(K k) {
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
 template <typename T>
 static cudaError_t fft_attributes() {
-    const int mx = 227 * 1024;
-    cudaError_t e = cudaFuncSetAttribute(fft_x_r2c_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(fft_x_c2r_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(fft_col_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(fft_col_kernel<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(fft_col_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    static const int lengths[] = {0, 16, 32, 48, 64, 96, 128, 192, 256, 512, 1024};
+    cudaError_t e = cudaSuccess;
+    for (int L : lengths) {
+        if (L != 0 && sizeof(T) != 4) continue;
+        const int n = L == 0 ? 7 : L;
+        if (e == cudaSuccess) e = smem_attr(x_kernel<T>(true, n));
+        if (e == cudaSuccess) e = smem_attr(x_kernel<T>(false, n));
+        if (e == cudaSuccess) e = smem_attr(col_kernel<T, 1>(n));
+        if (e == cudaSuccess) e = smem_attr(col_kernel<T, -1>(n));
+        if (e == cudaSuccess) e = smem_attr(col_kernel<T, 0>(n));
+    }
     return e;
 }
 
@@ -805,6 +742,32 @@ mm_status demag_setup(mm_ctx* c) {
     if (e == cudaSuccess) e = fft_attributes<double>();
     if (e != cudaSuccess) return cuda_check(c, e, "FFT kernel attributes");
     return c->prec == 32 ? demag_setup_t<float>(c) : demag_setup_t<double>(c);
+}
+
+// Tensor spectrum and twiddles of one grid (a replica size class), built
+// with the context's precision without touching the context's own plan.
+mm_status demag_setup_for(mm_ctx* c, const mm_grid& g, DemagPlan* out) {
+    const mm_grid sg = c->grid;
+    const long long sN = c->N;
+    const DemagPlan sd = c->dm;
+    c->grid = g;
+    c->N = (long long)g.nx * g.ny * g.nz;
+    c->dm = DemagPlan{};
+    mm_status s = demag_setup(c);
+    *out = c->dm;
+    c->grid = sg;
+    c->N = sN;
+    c->dm = sd;
+    return s;
+}
+
+void demag_free_plan(DemagPlan& d) {
+    cudaFree(d.spec);
+    cudaFree(d.khat);
+    cudaFree(d.tw_x);
+    cudaFree(d.tw_y);
+    cudaFree(d.tw_z);
+    d = DemagPlan{};
 }
 
 void demag_free(mm_ctx* c) {

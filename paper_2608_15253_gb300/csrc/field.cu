@@ -12,99 +12,9 @@
 
 #include "common.cuh"
 #include "ctx.h"
+#include "field_dev.cuh"
 
 namespace mm {
-
-// Philox4x32-10 (Salmon et al., SC'11): ten rounds, Weyl key schedule.
-struct U4 { uint32_t x, y, z, w; };
-
-__device__ __forceinline__ U4 philox(U4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    return c;
-}
-
-// u = ((x >> 8) + 1) 2^-24 in (0, 1]: exact in float and double
-template <typename T> __device__ __forceinline__ T unit_uniform(uint32_t x) {
-    return (T)((x >> 8) + 1u) * (T)5.9604644775390625e-08;
-}
-
-template <typename T> __device__ __forceinline__ void box_muller(U4 r, T* n) {
-    const T u0 = unit_uniform<T>(r.x), u1 = unit_uniform<T>(r.y);
-    const T u2 = unit_uniform<T>(r.z), u3 = unit_uniform<T>(r.w);
-    T s1, c1, s3, c3;
-    if (sizeof(T) == 4) {
-        const float a = sqrtf(-2.0f * logf((float)u0)), b = sqrtf(-2.0f * logf((float)u2));
-        float fs1, fc1, fs3, fc3;
-        sincospif(2.0f * (float)u1, &fs1, &fc1);
-        sincospif(2.0f * (float)u3, &fs3, &fc3);
-        n[0] = (T)(a * fc1); n[1] = (T)(a * fs1); n[2] = (T)(b * fc3);
-    } else {
-        const double a = sqrt(-2.0 * log((double)u0)), b = sqrt(-2.0 * log((double)u2));
-        double ds1, dc1, ds3, dc3;
-        sincospi(2.0 * (double)u1, &ds1, &dc1);
-        sincospi(2.0 * (double)u3, &ds3, &dc3);
-        n[0] = (T)(a * dc1); n[1] = (T)(a * ds1); n[2] = (T)(b * dc3);
-        (void)s1; (void)c1; (void)s3; (void)c3;
-    }
-}
-
-template <typename T>
-struct FieldArgs {
-    const T* m;           // state the field is evaluated at, [3][N]
-    const T* m0;          // HEUN2: base state
-    const T* k1;          // HEUN2: predictor slope
-    T* out;               // H | k | m* | m_new
-    T* out2;              // HEUN1: k1
-    const T* Hd;          // demag field or null
-    const T* Bc;          // per-cell applied field (A/m) or null
-    T hext[3];
-    const uint8_t* region;
-    const Region<T>* lut;
-    const T* cpair;
-    int nreg;
-    int nx, ny, nz;
-    long long N;
-    T hx, hy, hz;         // cell size
-    T ix2, iy2, iz2;      // 1/h^2
-    int px, py, pz;       // periodic flags
-    unsigned terms;
-    int mode;
-    // thermal
-    uint32_t key0, key1;
-    T th_scale;           // sqrt(T / (V dt)); sigma = lut.sigma0 * th_scale
-    const DevState* st;   // step counter, dt, active flag
-    int gate;             // 1: skip the launch when st->active == 0
-    long long step_override;  // >= 0: use this step for the noise
-    T* const* kptr;       // MODE_K with out == null: write to the FSAL slot of stage kstage
-    int kstage;           // 0 (k1) or 6 (k7)
-    // torques
-    int tq;               // mm_torque_kind
-    T tq_base;            // SOT/STT: hbar J / (e mu0 t_F) (times 1/Ms -> A/m)
-    T p[3];
-    T theta_half, fl_ratio, P, L2, eps_p;
-    T zl_u;               // J P mu_B / e [/(1+xi^2)] (times 1/Ms -> m/s)
-    T xi;
-    T dir[3];
-};
-
-template <typename T>
-__device__ __forceinline__ v3<T> ld3(const T* __restrict__ a, long long N, long long i) {
-    return mk3<T>(__ldg(a + i), __ldg(a + N + i), __ldg(a + 2 * N + i));
-}
-
-template <typename T>
-__device__ __forceinline__ void st3(T* a, long long N, long long i, v3<T> v) {
-    a[i] = v.x;
-    a[N + i] = v.y;
-    a[2 * N + i] = v.z;
-}
 
 template <typename T>
 __global__ void __launch_bounds__(256) field_kernel(FieldArgs<T> a) {
@@ -129,118 +39,12 @@ __global__ void __launch_bounds__(256) field_kernel(FieldArgs<T> a) {
         else st3(o, N, i, zero);
         return;
     }
-    v3<T> H = mk3<T>(0, 0, 0);
-    const bool need_nb = (a.terms & (MM_TERM_EXCHANGE | MM_TERM_DMI)) || a.tq == MM_TORQUE_ZL;
-    // neighbour values (ghosts where absent) and raw presence for Zhang-Li
-    v3<T> nbv[6];
-    bool nbp[6];
-    T cnb[6];
-    if (need_nb) {
-        const int dims[3] = {a.nx, a.ny, a.nz};
-        const int per[3] = {a.px, a.py, a.pz};
-        const int pos[3] = {x, y, z};
-        const long long strides[3] = {1, a.nx, (long long)a.nx * a.ny};
-        const T hh[3] = {a.hx, a.hy, a.hz};
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const int sg = s == 0 ? 1 : -1;
-                int q = pos[d] + sg;
-                bool inside = q >= 0 && q < dims[d];
-                if (!inside && per[d]) { q = (q + dims[d]) % dims[d]; inside = true; }
-                bool present = false;
-                long long j = 0;
-                int rj = 0;
-                if (inside) {
-                    j = i + (long long)(q - pos[d]) * strides[d];
-                    rj = a.region ? a.region[j] : 0;
-                    present = a.lut[rj].present != (T)0;
-                }
-                const int slot = 2 * d + s;
-                nbp[slot] = present;
-                if (present) {
-                    nbv[slot] = ld3(a.m, N, j);
-                    cnb[slot] = __ldg(&a.cpair[ri * a.nreg + rj]);
-                } else {
-                    // ghost: m - h (D/2A) (z x n) x m, n = sg e_d
-                    v3<T> zn = mk3<T>(0, 0, 0);
-                    if (d == 0) zn = mk3<T>(sg * m.z, (T)0, -sg * m.x);
-                    else if (d == 1) zn = mk3<T>((T)0, sg * m.z, -sg * m.y);
-                    nbv[slot] = m - (hh[d] * R.ratio) * zn;
-                    cnb[slot] = R.cg;
-                }
-            }
-        }
-        if (a.terms & MM_TERM_EXCHANGE) {
-            v3<T> e = mk3<T>(0, 0, 0);
-            e = e + (a.ix2 * cnb[0]) * (nbv[0] - m) + (a.ix2 * cnb[1]) * (nbv[1] - m);
-            e = e + (a.iy2 * cnb[2]) * (nbv[2] - m) + (a.iy2 * cnb[3]) * (nbv[3] - m);
-            e = e + (a.iz2 * cnb[4]) * (nbv[4] - m) + (a.iz2 * cnb[5]) * (nbv[5] - m);
-            H = H + e;
-        }
-        if (a.terms & MM_TERM_DMI) {
-            const T gx = (T)0.5 / a.hx, gy = (T)0.5 / a.hy;
-            const v3<T> dx = gx * (nbv[0] - nbv[1]);
-            const v3<T> dy = gy * (nbv[2] - nbv[3]);
-            H = H + R.dmi * mk3<T>(dx.z, dy.z, -dx.x - dy.y);
-        }
-    }
-    if (a.terms & MM_TERM_ANISOTROPY) {
-        const v3<T> u = mk3<T>(R.ux, R.uy, R.uz);
-        H = H + (R.ku * dot(m, u)) * u;
-    }
-    if (a.terms & MM_TERM_ZEEMAN) {
-        if (a.Bc) H = H + ld3(a.Bc, N, i);
-        else H = H + mk3<T>(a.hext[0], a.hext[1], a.hext[2]);
-    }
-    if ((a.terms & MM_TERM_DEMAG) && a.Hd) H = H + ld3(a.Hd, N, i);
-    if ((a.terms & MM_TERM_THERMAL) && a.th_scale != (T)0) {
-        const long long step = a.step_override >= 0 ? a.step_override : (a.st ? a.st->step : 0);
-        const U4 r = philox(U4{(uint32_t)i, (uint32_t)step, (uint32_t)((unsigned long long)step >> 32), 0u},
-                            a.key0, a.key1);
-        T n[3];
-        box_muller<T>(r, n);
-        const T sg = R.sigma0 * a.th_scale;
-        H = H + mk3<T>(sg * n[0], sg * n[1], sg * n[2]);
-    }
+    const long long step = a.step_override >= 0 ? a.step_override : (a.st ? a.st->step : 0);
+    v3<T> H, k;
+    cell_field<T>(a, x, y, z, i, ri, R, m, nullptr, step, H, k, a.mode != MODE_H);
     if (a.mode == MODE_H) {
         st3(a.out, N, i, H);
         return;
-    }
-    // LLG torque, Eq. 1: -gamma' mu0 [m x H + alpha m x (m x H)]
-    const v3<T> mxH = cross(m, H);
-    v3<T> k = (-R.gm) * (mxH + R.alpha * cross(m, mxH));
-    if (a.tq == MM_TORQUE_SOT || a.tq == MM_TORQUE_STT) {
-        const v3<T> p = mk3<T>(a.p[0], a.p[1], a.p[2]);
-        const T base = a.tq_base * R.inv_Ms;
-        T hdl, hfl;
-        if (a.tq == MM_TORQUE_SOT) {
-            hdl = a.theta_half * base;
-            hfl = a.fl_ratio * hdl;
-        } else {
-            const T eps = a.P * a.L2 / ((a.L2 + (T)1) + (a.L2 - (T)1) * dot(m, p));
-            hdl = eps * base;
-            hfl = a.eps_p * base;
-        }
-        const v3<T> mxp = cross(m, p);
-        k = k + (-R.gm) * ((hdl + R.alpha * hfl) * cross(m, mxp) + (hfl - R.alpha * hdl) * mxp);
-    } else if (a.tq == MM_TORQUE_ZL) {
-        // (u.grad) m, central differences, absent neighbour = the cell itself
-        const T u = a.zl_u * R.inv_Ms;
-        v3<T> g = mk3<T>(0, 0, 0);
-        const T hh[3] = {a.hx, a.hy, a.hz};
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if (a.dir[d] == (T)0) continue;
-            const v3<T> mp = nbp[2 * d] ? nbv[2 * d] : m;
-            const v3<T> mm = nbp[2 * d + 1] ? nbv[2 * d + 1] : m;
-            g = g + (a.dir[d] / ((T)2 * hh[d])) * (mp - mm);
-        }
-        const v3<T> ug = u * g;
-        const v3<T> mxug = cross(m, ug);
-        const T inv = (T)1 / ((T)1 + R.alpha * R.alpha);
-        k = k + inv * ((-((T)1 + R.alpha * a.xi)) * cross(m, mxug) + (-(a.xi - R.alpha)) * mxug);
     }
     if (a.mode == MODE_K) {
         T* o = a.out;

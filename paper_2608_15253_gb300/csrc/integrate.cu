@@ -40,18 +40,27 @@ __device__ __forceinline__ int kslot_of(int j, int k_first) {
     return j;
 }
 
-template <typename T>
-__global__ void combine_kernel(const DevState* __restrict__ st, T* const* __restrict__ kptr,
-                               const T* __restrict__ m0, T* __restrict__ ms, long long n3, int s) {
+template <typename T> __device__ __forceinline__ const T* stage_coef(const DevState* st, int s);
+template <> __device__ __forceinline__ const float* stage_coef<float>(const DevState* st, int s) { return st->cf32[s]; }
+template <> __device__ __forceinline__ const double* stage_coef<double>(const DevState* st, int s) { return st->cf64[s]; }
+template <typename T> __device__ __forceinline__ const T* err_coef(const DevState* st);
+template <> __device__ __forceinline__ const float* err_coef<float>(const DevState* st) { return st->ce32; }
+template <> __device__ __forceinline__ const double* err_coef<double>(const DevState* st) { return st->ce64; }
+
+// m_s = m0 + sum_j (dt a_sj) k_j, S = stage index (compile time)
+template <typename T, int S>
+__global__ void __launch_bounds__(256) combine_kernel(const DevState* __restrict__ st, T* const* __restrict__ kptr,
+                                                      const T* __restrict__ m0, T* __restrict__ ms, long long n3) {
     if (!st->active) return;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n3) return;
-    const double dt = st->dt_eff;
     const int kf = st->k_first;
+    const T* cf = stage_coef<T>(st, S);
     T acc = m0[i];
-    for (int j = 0; j < s; ++j) {
-        const double a = c_dp_a[s][j];
-        if (a != 0.0) acc += (T)(dt * a) * kptr[kslot_of(j, kf)][i];
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+        if (j == 1 && S == 6) continue;             // a_7,2 = 0
+        acc += cf[j] * __ldg(&kptr[kslot_of(j, kf)][i]);
     }
     ms[i] = acc;
 }
@@ -61,17 +70,16 @@ template <typename T>
 __global__ void error_kernel(DevState* st, T* const* __restrict__ kptr, long long N) {
     if (!st->active) return;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const double dt = st->dt_eff;
     const int kf = st->k_first;
+    const T* ce = err_coef<T>(st);
     T e2 = 0;
     if (i < N) {
         T ex = 0, ey = 0, ez = 0;
 #pragma unroll
         for (int j = 0; j < 7; ++j) {
-            const double e = c_dp_e[j];
-            if (e == 0.0) continue;
+            if (j == 1) continue;                   // e_2 = 0
             const T* k = kptr[kslot_of(j, kf)];
-            const T w = (T)(dt * e);
+            const T w = ce[j];
             ex += w * k[i];
             ey += w * k[N + i];
             ez += w * k[2 * N + i];
@@ -105,6 +113,14 @@ __global__ void attempt_begin_kernel(DevState* st) {
     }
     if (st->t + dt > st->t_end) dt = st->t_end - st->t;
     st->dt_eff = dt;
+    for (int s = 0; s < 7; ++s) {
+        for (int j = 0; j < 6; ++j) {
+            st->cf64[s][j] = dt * c_dp_a[s][j];
+            st->cf32[s][j] = (float)(dt * c_dp_a[s][j]);
+        }
+        st->ce64[s] = dt * c_dp_e[s];
+        st->ce32[s] = (float)(dt * c_dp_e[s]);
+    }
     st->err = 0.0;
     st->err_f = 0.0f;
     st->attempts += 1;
@@ -188,8 +204,11 @@ static void rk45_attempt_t(mm_ctx* c) {
     const bool demag = c->dm.on && (terms & MM_TERM_DEMAG);
     for (int s = 1; s < 7; ++s) {
         {
-            LaunchScope ls(c, "rk_combine", (double)sizeof(T) * n3 * (1 + s));
-            combine_kernel<T><<<nb3, tb, 0, c->stream>>>(c->d_state, kp, (const T*)c->d_m, (T*)c->d_mtmp, n3, s);
+            LaunchScope ls(c, "rk_combine", (double)sizeof(T) * n3 * (1 + s + (s == 6 ? 0 : 1)));
+            static void (*const kern[7])(const DevState*, T* const*, const T*, T*, long long) = {
+                nullptr, combine_kernel<T, 1>, combine_kernel<T, 2>, combine_kernel<T, 3>,
+                combine_kernel<T, 4>, combine_kernel<T, 5>, combine_kernel<T, 6>};
+            kern[s]<<<nb3, tb, 0, c->stream>>>(c->d_state, kp, (const T*)c->d_m, (T*)c->d_mtmp, n3);
         }
         if (demag) demag_apply(c, c->d_mtmp, c->d_hd);
         // stages 2..6 own fixed slots; the FSAL stage 7 slope goes to the slot
@@ -221,6 +240,16 @@ void rk45_first_slope(mm_ctx* c) {
     const bool demag = c->dm.on && (terms & MM_TERM_DEMAG);
     if (demag) demag_apply(c, c->d_m, c->d_hd);
     field_launch(c, MODE_K, terms, c->d_m, demag ? c->d_hd : nullptr, nullptr, nullptr, nullptr, nullptr, -1, 0, 0);
+}
+
+void heun_batch_begin(mm_ctx* c) {
+    LaunchScope ls(c, "heun_begin", 0.0);
+    heun_begin_kernel<<<1, 1, 0, c->stream>>>(c->d_state);
+}
+
+void heun_batch_advance(mm_ctx* c) {
+    LaunchScope ls(c, "heun_advance", 0.0);
+    heun_advance_kernel<<<1, 1, 0, c->stream>>>(c->d_state);
 }
 
 void heun_step(mm_ctx* c) {
