@@ -1,0 +1,474 @@
+// Learned demagnetising-field surrogate (not in the paper; the benchmark's
+// own addition): a 4-layer CNN, 3 -> 32 -> 32 -> 32 -> 3 channels, 5x5
+// kernels, zero "same" padding, ReLU after layers 1-3, BF16 operands with
+// FP32 accumulation.  It maps a magnetisation increment dm = m - m_ref to
+// the demag increment dH = H_demag(dm) (the field is linear in m), so
+// between exact FFT evaluations H ~ H_exact(m_ref) + CNN(m - m_ref).
+//
+// Forward convolution = implicit GEMM on the 5th-generation tensor cores:
+//   D[128 pixels x Cout] += A[128 pixels x 16 ch] * B[16 ch x Cout]
+// per (tap, 16-channel chunk), tcgen05.mma kind::f16 with BF16 operands in
+// shared memory (K-major, no swizzle) and the FP32 accumulator in tensor
+// memory, read back with tcgen05.ld for the bias/ReLU/BF16 epilogue.
+// Activations are NHWC BF16 with a 2-pixel zero halo, so every tap's A
+// tile is a plain shifted window of an input row strip laid out
+// [16-byte channel chunk][pixel][16 B]: any pixel shift is a valid
+// descriptor start.  The input gradient reuses the same kernel with
+// flipped, transposed weights; weight gradients, loss and Adam are SIMT.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "ctx.h"
+
+namespace mm {
+
+constexpr int kTile = 128;     // pixels per MMA tile (M)
+constexpr int kStrip = kTile + 4;
+constexpr int kTaps = 25;
+
+// ---------------------------------------------------------------------------
+// tcgen05 / mbarrier primitives (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor: K-major, no swizzle.  lbo = byte stride
+// between core matrices adjacent along K, sbo = between 8-row groups.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;          // descriptor version for tcgen05
+    return d;                        // base offset 0, swizzle none
+}
+
+// Instruction descriptor, kind::f16: D f32, A and B bf16, both K-major.
+__host__ __device__ constexpr uint32_t umma_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ uint32_t mbar_try_wait(uint32_t mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+template <int NC>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v);
+
+template <>
+__device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float* v) {
+    tmem_ld<16>(taddr, v);
+    tmem_ld<16>(taddr + 16, v + 16);
+}
+
+// ---------------------------------------------------------------------------
+// convolution on tensor cores
+// ---------------------------------------------------------------------------
+struct ConvArgs {
+    const __nv_bfloat16* in;   // [B][H+4][W+4][CIN] (halo 2)
+    const uint4* wpk;          // packed weights [25][CIN/8][COUTP][8 bf16]
+    const float* bias;         // [COUTP] or null
+    void* out;                 // mode 0/2: bf16 [B][H+4][W+4][COUTP]; mode 1: f32 [B][H][W][3]
+    const __nv_bfloat16* mask; // mode 2: [B][H+4][W+4][COUTP], multiply by (mask > 0)
+    float out_scale;           // mode 1
+    int H, W;
+    int* err;                  // set to 1 when a bounded wait runs out
+};
+
+enum { OUT_BF16 = 0, OUT_FIELD = 1, OUT_MASKED = 2 };
+
+template <int CIN, int COUTP, int RPB>
+struct ConvSmem {
+    static constexpr int kChunks = CIN / 8;
+    static constexpr int kStripBytes = kChunks * kStrip * 16;
+    static constexpr int kStrips = RPB + 4;
+    static constexpr int kA = kStrips * kStripBytes;
+    static constexpr int kB = kTaps * kChunks * COUTP * 16;
+    static constexpr int kSlack = 16384;           // keeps every descriptor reach inside the allocation
+    static constexpr int kTotal = kA + kB + kSlack + 64;
+    static constexpr int kTmemCols = RPB * COUTP < 32 ? 32 : RPB * COUTP;
+};
+
+template <int CIN, int COUTP, int RPB, int MODE, bool RELU>
+__global__ void __launch_bounds__(128) conv_tc_kernel(ConvArgs a) {
+    using L = ConvSmem<CIN, COUTP, RPB>;
+    static_assert(L::kTmemCols == 32 || L::kTmemCols == 64 || L::kTmemCols == 128 || L::kTmemCols == 256,
+                  "tensor-memory allocation must be a power of two");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sA = smem;
+    unsigned char* sB = smem + L::kA;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::kA + L::kB + L::kSlack);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::kA + L::kB + L::kSlack + 16);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int H = a.H, W = a.W, Wp = W + 4;
+    const int j0 = blockIdx.x * kTile, i0 = blockIdx.y * RPB, b = blockIdx.z;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"((uint32_t)L::kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        mbar_init(smem_u32(mbar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // operands: weights (pre-packed in the shared layout) and input row strips
+    const uint4* wsrc = a.wpk;
+    for (int q = tid; q < L::kB / 16; q += 128) reinterpret_cast<uint4*>(sB)[q] = wsrc[q];
+    const uint4 zero = make_uint4(0, 0, 0, 0);
+    for (int q = tid; q < L::kStrips * L::kChunks * kStrip; q += 128) {
+        const int px = q % kStrip;
+        const int rest = q / kStrip;
+        const int ch = rest % L::kChunks, s = rest / L::kChunks;
+        const int row = i0 + s, col = j0 + px;   // padded coordinates
+        uint4 v = zero;
+        if (row < H + 4 && col < Wp)
+            v = *reinterpret_cast<const uint4*>(a.in + (((long long)b * (H + 4) + row) * Wp + col) * CIN + ch * 8);
+        reinterpret_cast<uint4*>(sA)[(s * L::kChunks + ch) * kStrip + px] = v;
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+    if (tid == 0) {
+        const uint32_t idesc = umma_idesc(kTile, COUTP);
+        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+        for (int r = 0; r < RPB; ++r) {
+            for (int p = 0; p < 5; ++p)
+                for (int q = 0; q < 5; ++q)
+#pragma unroll
+                    for (int kk = 0; kk < CIN / 16; ++kk) {
+                        const int tap = p * 5 + q;
+                        const uint32_t aa = a0 + (((r + p) * L::kChunks + 2 * kk) * kStrip + q) * 16;
+                        const uint32_t bb = b0 + ((tap * L::kChunks + 2 * kk) * COUTP) * 16;
+                        umma_f16(tbase + r * COUTP, umma_desc(aa, kStrip * 16, 128), umma_desc(bb, COUTP * 16, 128),
+                                 idesc, (p | q | kk) != 0);
+                    }
+        }
+        umma_commit(smem_u32(mbar));
+    }
+    // wait for the accumulators (bounded)
+    uint32_t done = 0;
+    for (long it = 0; it < (1L << 24) && !done; ++it) done = mbar_try_wait(smem_u32(mbar), 0);
+    if (!done && a.err) atomicExch(a.err, 1);
+    tc_fence_after();
+    if (done) {
+        const int m = warp * 32 + (tid & 31);
+        const int j = j0 + m;
+        for (int r = 0; r < RPB; ++r) {
+            float v[COUTP];
+            tmem_ld<COUTP>(tbase + ((uint32_t)(warp * 32) << 16) + r * COUTP, v);
+            const int i = i0 + r;
+            if (i >= H || j >= W) continue;
+            if (a.bias)
+#pragma unroll
+                for (int c = 0; c < COUTP; ++c) v[c] += a.bias[c];
+            if (RELU)
+#pragma unroll
+                for (int c = 0; c < COUTP; ++c) v[c] = fmaxf(v[c], 0.f);
+            if (MODE == OUT_FIELD) {
+                float* o = reinterpret_cast<float*>(a.out) + (((long long)b * H + i) * W + j) * 3;
+                o[0] = v[0] * a.out_scale;
+                o[1] = v[1] * a.out_scale;
+                o[2] = v[2] * a.out_scale;
+            } else {
+                const long long pix = ((long long)b * (H + 4) + i + 2) * Wp + j + 2;
+                if (MODE == OUT_MASKED) {
+                    const __nv_bfloat16* mk = a.mask + pix * COUTP;
+#pragma unroll
+                    for (int c = 0; c < COUTP; ++c)
+                        if (!(__bfloat162float(mk[c]) > 0.f)) v[c] = 0.f;
+                }
+                __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(a.out) + pix * COUTP;
+#pragma unroll
+                for (int c = 0; c < COUTP; c += 8) {
+                    uint4 pk;
+                    __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(&pk);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) h2[e] = __floats2bfloat162_rn(v[c + 2 * e], v[c + 2 * e + 1]);
+                    *reinterpret_cast<uint4*>(o + c) = pk;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
+                     "r"((uint32_t)L::kTmemCols));
+}
+
+// SIMT reference of the same convolution (on-GPU cross-check of the tensor
+// path; FP32 accumulation of the same BF16 operands).
+template <int CIN, int COUTP>
+__global__ void conv_simt_kernel(ConvArgs a, const __nv_bfloat16* __restrict__ w /*[COUTP][CIN][5][5]*/, int mode,
+                                 int relu) {
+    const long long n = (long long)gridDim.z * a.H * a.W;
+    const long long pidx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int b = blockIdx.z;
+    if (pidx >= (long long)a.H * a.W) return;
+    (void)n;
+    const int i = (int)(pidx / a.W), j = (int)(pidx % a.W);
+    const int Wp = a.W + 4;
+    float v[COUTP];
+    for (int c = 0; c < COUTP; ++c) v[c] = a.bias ? a.bias[c] : 0.f;
+    for (int p = 0; p < 5; ++p)
+        for (int q = 0; q < 5; ++q) {
+            const __nv_bfloat16* x = a.in + (((long long)b * (a.H + 4) + i + p) * Wp + j + q) * CIN;
+            for (int ci = 0; ci < CIN; ++ci) {
+                const float xv = __bfloat162float(x[ci]);
+                for (int co = 0; co < COUTP; ++co) v[co] += __bfloat162float(w[((co * CIN + ci) * 5 + p) * 5 + q]) * xv;
+            }
+        }
+    if (relu)
+        for (int c = 0; c < COUTP; ++c) v[c] = fmaxf(v[c], 0.f);
+    if (mode == OUT_FIELD) {
+        float* o = reinterpret_cast<float*>(a.out) + (((long long)b * a.H + i) * a.W + j) * 3;
+        for (int c = 0; c < 3; ++c) o[c] = v[c] * a.out_scale;
+    } else {
+        const long long pix = ((long long)b * (a.H + 4) + i + 2) * Wp + j + 2;
+        __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(a.out) + pix * COUTP;
+        for (int c = 0; c < COUTP; ++c) {
+            float val = v[c];
+            if (mode == OUT_MASKED && !(__bfloat162float(a.mask[pix * COUTP + c]) > 0.f)) val = 0.f;
+            o[c] = __float2bfloat16_rn(val);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// weight packing, gradients, loss, Adam
+// ---------------------------------------------------------------------------
+// master FP32 weights w[co][ci][5][5] (co < cout, ci < cin) -> packed bf16
+// [tap][ci/8][co(COUTP)][ci%8]; flip = 1 packs the input-gradient weights
+// w'[ci][co][4-p][4-q] (input/output channel roles swapped).
+__global__ void pack_weights_kernel(const float* __restrict__ w, int cout, int cin, int CINP, int COUTP, int flip,
+                                    __nv_bfloat16* __restrict__ out) {
+    const int n = kTaps * CINP * COUTP;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int e = q % 8;
+    const int co = (q / 8) % COUTP;
+    const int ch = (q / (8 * COUTP)) % (CINP / 8);
+    const int tap = q / (8 * COUTP * (CINP / 8));
+    const int ci = ch * 8 + e;
+    const int p = tap / 5, r = tap % 5;
+    float v = 0.f;
+    if (!flip) {
+        if (co < cout && ci < cin) v = w[((co * cin + ci) * 5 + p) * 5 + r];
+    } else {
+        // output channel co of the gradient conv = input channel of the layer
+        if (co < cin && ci < cout) v = w[((ci * cin + co) * 5 + (4 - p)) * 5 + (4 - r)];
+    }
+    out[q] = __float2bfloat16_rn(v);
+}
+
+// plain [COUTP][CIN][5][5] bf16 copy for the SIMT cross-check
+__global__ void plain_weights_kernel(const float* __restrict__ w, int cout, int cin, int CINP, int COUTP,
+                                     __nv_bfloat16* __restrict__ out) {
+    const int n = COUTP * CINP * 25;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int t = q % 25, ci = (q / 25) % CINP, co = q / (25 * CINP);
+    out[q] = __float2bfloat16_rn(co < cout && ci < cin ? w[(co * cin + ci) * 25 + t] : 0.f);
+}
+
+// dW[co][ci][p][q] += sum over pixels dZ[pix][co] * X[pix + (p-2, q-2)][ci]
+// one block per (tap, pixel chunk); thread (co, ci); FP32 atomics.
+__global__ void dweight_kernel(const __nv_bfloat16* __restrict__ dz, int CZ, int cout,
+                               const __nv_bfloat16* __restrict__ x, int CX, int cin, int B, int H, int W,
+                               int chunk, float* __restrict__ dw, float* __restrict__ db) {
+    __shared__ float sz[64][33];
+    __shared__ float sx[64][33];
+    const int tap = blockIdx.y, p = tap / 5, q = tap % 5;
+    const int co = threadIdx.x / 32, ci = threadIdx.x % 32;   // 32 x 32 threads (1024)
+    const long long npix = (long long)B * H * W;
+    const long long p0 = (long long)blockIdx.x * chunk;
+    const long long p1 = min(npix, p0 + chunk);
+    const int Wp = W + 4;
+    float acc = 0.f, accb = 0.f;
+    for (long long pb = p0; pb < p1; pb += 64) {
+        for (int e = threadIdx.x; e < 64 * 32; e += blockDim.x) {
+            const int lp = e / 32, c = e % 32;
+            const long long pix = pb + lp;
+            float zv = 0.f, xv = 0.f;
+            if (pix < p1) {
+                const int bb = (int)(pix / ((long long)H * W));
+                const int rem = (int)(pix % ((long long)H * W));
+                const int i = rem / W, j = rem % W;
+                if (c < CZ) zv = __bfloat162float(dz[(((long long)bb * (H + 4) + i + 2) * Wp + j + 2) * CZ + c]);
+                if (c < CX) xv = __bfloat162float(x[(((long long)bb * (H + 4) + i + p) * Wp + j + q) * CX + c]);
+            }
+            sz[lp][c] = zv;
+            sx[lp][c] = xv;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int lp = 0; lp < 64; ++lp) {
+            acc += sz[lp][co] * sx[lp][ci];
+            if (tap == 0 && ci == 0) accb += sz[lp][co];
+        }
+        __syncthreads();
+    }
+    if (co < cout && ci < cin) atomicAdd(&dw[((co * cin + ci) * 5 + p) * 5 + q], acc);
+    if (tap == 0 && ci == 0 && co < cout) atomicAdd(&db[co], accb);
+}
+
+// loss = sum (y - t)^2 / n; dy = 2 (y - t) / n scaled by gscale, as bf16 NHWC (16 ch)
+__global__ void mse_grad_kernel(const float* __restrict__ y, const float* __restrict__ t, int B, int H, int W,
+                                float gscale, __nv_bfloat16* __restrict__ dy, double* __restrict__ loss) {
+    const long long n = (long long)B * H * W;
+    const long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (pix < n) {
+        const int b = (int)(pix / ((long long)H * W));
+        const int rem = (int)(pix % ((long long)H * W));
+        const int i = rem / W, j = rem % W;
+        __nv_bfloat16* o = dy + (((long long)b * (H + 4) + i + 2) * (W + 4) + j + 2) * 16;
+        const float inv = 1.f / (float)(3 * n);
+        for (int c = 0; c < 3; ++c) {
+            const float d = y[pix * 3 + c] - t[pix * 3 + c];
+            l += (double)d * d;
+            o[c] = __float2bfloat16_rn(2.f * d * inv * gscale);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, l / (double)(3 * n));
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int n, float lr, float b1, float b2, float eps, float c1, float c2,
+                            float ginv) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const float gg = g[q] * ginv;
+    m[q] = b1 * m[q] + (1.f - b1) * gg;
+    v[q] = b2 * v[q] + (1.f - b2) * gg * gg;
+    p[q] -= lr * (m[q] / c1) / (sqrtf(v[q] / c2) + eps);
+}
+
+// dm = (m - m_ref) * c_in as bf16 NHWC (16 ch, halo 2) from the SoA state
+template <typename T>
+__global__ void dm_to_nhwc_kernel(const T* __restrict__ m, const T* __restrict__ mref, int H, int W, float c_in,
+                                  __nv_bfloat16* __restrict__ x) {
+    const long long N = (long long)H * W;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int r = (int)(i / W), c = (int)(i % W);
+    __nv_bfloat16* o = x + (((long long)r + 2) * (W + 4) + c + 2) * 16;
+    for (int k = 0; k < 3; ++k) {
+        const float d = mref ? (float)(m[k * N + i] - mref[k * N + i]) : (float)m[k * N + i];
+        o[k] = __float2bfloat16_rn(d * c_in);
+    }
+}
+
+// H = H_ref + Ms * out (out: [H][W][3] f32, already scaled back)
+template <typename T>
+__global__ void field_from_cnn_kernel(const float* __restrict__ out, const T* __restrict__ href, long long N, float Ms,
+                                      T* __restrict__ H) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    for (int k = 0; k < 3; ++k) H[k * N + i] = (href ? href[k * N + i] : (T)0) + (T)(Ms * out[i * 3 + k]);
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+template <int CIN, int COUTP, int RPB, int MODE, bool RELU>
+static cudaError_t launch_conv_tc(const ConvArgs& a, int B, cudaStream_t s) {
+    using L = ConvSmem<CIN, COUTP, RPB>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<CIN, COUTP, RPB, MODE, RELU>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, L::kTotal);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid((a.W + kTile - 1) / kTile, (a.H + RPB - 1) / RPB, B);
+    conv_tc_kernel<CIN, COUTP, RPB, MODE, RELU><<<grid, 128, L::kTotal, s>>>(a);
+    return cudaGetLastError();
+}
+
+// layer shapes of the 3 -> 32 -> 32 -> 32 -> 3 network (input padded to 16 ch,
+// output to 16 ch)
+struct CnnLayer {
+    int cin, cout, cinp, coutp;
+};
+static const CnnLayer kLayers[4] = {{3, 32, 16, 32}, {32, 32, 32, 32}, {32, 32, 32, 32}, {32, 3, 32, 16}};
+
+cudaError_t cnn_conv(int layer, bool backward, const ConvArgs& a, int B, cudaStream_t s) {
+    constexpr int RPB = 4;
+    if (!backward) {
+        switch (layer) {
+            case 0: return launch_conv_tc<16, 32, RPB, OUT_BF16, true>(a, B, s);
+            case 1:
+            case 2: return launch_conv_tc<32, 32, RPB, OUT_BF16, true>(a, B, s);
+            default: return launch_conv_tc<32, 16, RPB, OUT_FIELD, false>(a, B, s);
+        }
+    }
+    // input gradient of `layer`: channels in = its cout(p), out = its cin(p), masked by the layer's input
+    switch (layer) {
+        case 3: return launch_conv_tc<16, 32, RPB, OUT_MASKED, false>(a, B, s);
+        default: return launch_conv_tc<32, 32, RPB, OUT_MASKED, false>(a, B, s);
+    }
+}
+
+cudaError_t cnn_conv_simt(int layer, const ConvArgs& a, const __nv_bfloat16* wplain, int B, cudaStream_t s) {
+    dim3 grid((unsigned)((a.H * (long long)a.W + 127) / 128), 1, B);
+    switch (layer) {
+        case 0: conv_simt_kernel<16, 32><<<grid, 128, 0, s>>>(a, wplain, OUT_BF16, 1); break;
+        case 1:
+        case 2: conv_simt_kernel<32, 32><<<grid, 128, 0, s>>>(a, wplain, OUT_BF16, 1); break;
+        default: conv_simt_kernel<32, 16><<<grid, 128, 0, s>>>(a, wplain, OUT_FIELD, 0); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace mm
