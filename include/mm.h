@@ -238,6 +238,27 @@ MM_API mm_status mm_newell(long count, const int* ijk, double dx, double dy, dou
  * NULL.  MM_ERR_STATE for single-instance contexts. */
 MM_API mm_status mm_batch_autotune(mm_ctx* ctx, const char* cache_path, int* nt_out, int* blocks_out);
 
+/* Topological charge without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that may not allocate
+ * device memory -- code running while a CUDA graph is captured (a plain
+ * cudaMalloc is not allowed there), loops that must never enter the
+ * allocator, and hosts whose device memory belongs to another framework's
+ * pool.  The caller passes the state m_dev (device, [3][nz][ny][nx] in
+ * `precision` 32 = float or 64 = double, every cell present) and the output
+ * Q_dev (one device double); the result is the same quantity as
+ * mm_topo_charge (layer < 0: mean over layers).  Work is ordered on
+ * `stream` (cudaStream_t, NULL = default stream); nothing is synchronised.
+ * The only scratch is a fixed 64 KiB file-scope device array (one partial
+ * sum per block of 4096 cells) that every GPU loading the library keeps
+ * until exit; the first call on a device looks up its address, so make
+ * that first call before any stream capture.  Calls share the array:
+ * calls that overlap on the GPU race.  No cudaMalloc, cudaFree or
+ * allocating library routine is used.  Errors: MM_ERR_ARG for bad
+ * arguments or more than 16,777,216 cells (4096 blocks) in the reduced
+ * range, MM_ERR_DEVICE / MM_ERR_CUDA for runtime failures. */
+MM_API mm_status mm_topo_charge_noalloc(const void* m_dev, int precision, int nx, int ny, int nz,
+                                        double dx, double dy, int layer, double* Q_dev, void* stream);
+
 /* Per-kernel CUDA-event timing (graphs are bypassed while on). */
 MM_API mm_status mm_set_profiling(mm_ctx* ctx, int on);
 MM_API mm_status mm_get_profile(mm_ctx* ctx, mm_profile_entry* out, int* n_inout);

@@ -97,6 +97,8 @@ _SIGS = {
     "mm_get_thermal": [C.c_void_p, C.c_int, C.c_longlong, C.POINTER(C.c_uint32), _D],
     "mm_get_demag_kernel": [C.c_void_p, _D, C.c_size_t, C.POINTER(C.c_int)],
     "mm_newell": [C.c_long, C.POINTER(C.c_int), C.c_double, C.c_double, C.c_double, _D],
+    "mm_topo_charge_noalloc": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
+                               C.c_void_p, C.c_void_p],
     "mm_batch_autotune": [C.c_void_p, C.c_char_p, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "mm_set_profiling": [C.c_void_p, C.c_int],
     "mm_get_profile": [C.c_void_p, C.POINTER(mm_profile_entry), C.POINTER(C.c_int)],
@@ -286,6 +288,13 @@ def mm_newell(ijk, d):
     out = np.zeros((a.shape[0], 6), dtype=np.float64)
     _check(load().mm_newell(a.shape[0], a.ctypes.data_as(C.POINTER(C.c_int)), d[0], d[1], d[2], _dptr(out)))
     return out
+
+
+def mm_topo_charge_noalloc(m_dev: int, precision: int, nx: int, ny: int, nz: int, dx: float, dy: float,
+                           layer: int, q_dev: int, stream: int | None = None):
+    """Device pointers in and out (ints, e.g. torch data_ptr()); allocates nothing."""
+    _check(load().mm_topo_charge_noalloc(C.c_void_p(m_dev), precision, nx, ny, nz, dx, dy, layer, C.c_void_p(q_dev),
+                                         C.c_void_p(stream) if stream else None))
 
 
 def mm_batch_autotune(ctx, cache_path: str | None = None):
