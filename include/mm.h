@@ -259,6 +259,62 @@ MM_API mm_status mm_batch_autotune(mm_ctx* ctx, const char* cache_path, int* nt_
 MM_API mm_status mm_topo_charge_noalloc(const void* m_dev, int precision, int nx, int ny, int nz,
                                         double dx, double dy, int layer, double* Q_dev, void* stream);
 
+/* ---- learned demag surrogate (the benchmark's own addition; not in the paper)
+ * A 4-layer CNN (3 -> 32 -> 32 -> 32 -> 3 channels, 5x5 kernels, ReLU after
+ * layers 1-3) with BF16 operands and FP32 accumulation on the tensor cores
+ * maps a magnetisation increment dm = m - m_ref (scaled by c_in) to the demag
+ * increment H_demag(dm) / Ms (scaled by c_in); the demag field is linear in
+ * m, so between exact FFT evaluations H ~ H_exact(m_ref) + CNN(m - m_ref).
+ * Single-instance FP32 nz = 1 contexts with exact demag only. */
+typedef struct mm_train_cfg {
+    int n_snapshots;   /* exact RK45 snapshots from the current state */
+    int snap_every;    /* accepted RK45 steps between snapshots */
+    int max_gap;       /* pairs (i, j), 1 <= j - i <= max_gap, give dm = m_j - m_i */
+    int crop;          /* training window edge (cells, <= nx, ny) */
+    int batch;         /* windows per optimisation step */
+    int steps;         /* optimisation steps */
+    double lr;         /* Adam learning rate */
+    uint64_t seed;     /* window positions and weight initialisation */
+} mm_train_cfg;
+
+typedef struct mm_surrogate_stats {
+    long long exact_evals;      /* exact FFT demag evaluations while stepping */
+    long long surrogate_evals;  /* network evaluations while stepping */
+    long long refreshes;        /* exact refreshes of (m_ref, H_ref) */
+    int fallback;               /* 1 once the monitored error passed the threshold */
+    double last_error;          /* max|H_pred - H_exact| / max|H_exact| at the last refresh */
+    double max_error;
+    double train_loss;          /* last training loss */
+    double c_in;
+} mm_surrogate_stats;
+
+/* Generate (dm, H_demag(dm)) pairs with the exact FFT path from a relaxation
+ * started at the current state (the state is restored afterwards) and train
+ * the network with the library's own BF16 forward/backward kernels and Adam.
+ * final_loss may be NULL. */
+MM_API mm_status mm_surrogate_train(mm_ctx* ctx, const mm_train_cfg* cfg, double* final_loss);
+
+/* k >= 1: every k-th attempted step refreshes (m_ref, H_ref) with the exact
+ * demag and first compares the network's prediction at that state with the
+ * exact field; above tol (relative, max norm) every later evaluation is exact
+ * (fallback).  k = 0 turns the surrogate off. */
+MM_API mm_status mm_surrogate_set(mm_ctx* ctx, int k, double tol);
+MM_API mm_status mm_surrogate_get_stats(mm_ctx* ctx, mm_surrogate_stats* st);
+
+/* Network parameters as n doubles in layer order (w0 [32][3][5][5], b0,
+ * w1 [32][32][5][5], b1, w2, b2, w3 [3][32][5][5], b3; 56099 values).  get
+ * or set may be NULL; c_in (in/out, may be NULL) is the input scale. */
+MM_API mm_status mm_surrogate_weights(mm_ctx* ctx, double* get, const double* set, size_t n, double* c_in);
+
+/* Network on host data: x [B][3][H][W] -> y [B][3][H][W] (raw network output),
+ * path 0 = tensor-core kernels, 1 = SIMT cross-check kernels. */
+MM_API mm_status mm_surrogate_forward(mm_ctx* ctx, int B, int H, int W, const double* x, double* y, int path);
+
+/* One forward + mean-squared-error loss against t + backward pass: loss and
+ * the gradient of every parameter (n = 56099, same order as the weights). */
+MM_API mm_status mm_surrogate_grad(mm_ctx* ctx, int B, int H, int W, const double* x, const double* t,
+                                   double* loss, double* grad);
+
 /* Per-kernel CUDA-event timing (graphs are bypassed while on). */
 MM_API mm_status mm_set_profiling(mm_ctx* ctx, int on);
 MM_API mm_status mm_get_profile(mm_ctx* ctx, mm_profile_entry* out, int* n_inout);

@@ -182,6 +182,7 @@ static void free_all(mm_ctx* c) {
     demag_free(c);
     batch_free(c->batch);
     c->batch = nullptr;
+    surrogate_free(c);
     void* bufs[] = {c->d_region, c->d_lut, c->d_cpair, c->d_m, c->d_mtmp, c->d_kslot, c->d_hd, c->d_hbuf,
                     c->d_bcell, c->d_state, c->d_replay, c->d_red};
     for (void* b : bufs) cudaFree(b);
@@ -695,6 +696,23 @@ static mm_status advance(mm_ctx* c, long long add_steps, double t_end, int repla
     s = ensure_k1(c);
     if (s != MM_OK) return s;
     const bool heun = c->integrator == MM_HEUN;
+    if (surrogate_stepping(c)) {
+        // host-driven blocks: exact refresh (with the error monitor) + k-1 network attempts
+        for (int round = 0; round < 100000000; ++round) {
+            s = surrogate_block(c);
+            if (s != MM_OK) return s;
+            s = sync_state(c);
+            if (s != MM_OK) return s;
+            if (c->h_state.status) break;
+            if (add_steps >= 0 && c->h_state.accepted >= c->h_state.target) break;
+            if (add_steps < 0 && !(c->h_state.t < t_end)) break;
+        }
+        if (replay) {
+            c->h_state.replay = 0;
+            push_state(c);
+        }
+        return status_from_device(c);
+    }
     for (int round = 0; round < 1000000; ++round) {
         long long want;
         if (add_steps >= 0) {

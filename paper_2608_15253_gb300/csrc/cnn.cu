@@ -22,6 +22,7 @@
 #include <cstring>
 #include <vector>
 
+#include "cnn.h"
 #include "common.cuh"
 #include "ctx.h"
 
@@ -110,17 +111,6 @@ __device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float* v) {
 // ---------------------------------------------------------------------------
 // convolution on tensor cores
 // ---------------------------------------------------------------------------
-struct ConvArgs {
-    const __nv_bfloat16* in;   // [B][H+4][W+4][CIN] (halo 2)
-    const uint4* wpk;          // packed weights [25][CIN/8][COUTP][8 bf16]
-    const float* bias;         // [COUTP] or null
-    void* out;                 // mode 0/2: bf16 [B][H+4][W+4][COUTP]; mode 1: f32 [B][H][W][3]
-    const __nv_bfloat16* mask; // mode 2: [B][H+4][W+4][COUTP], multiply by (mask > 0)
-    float out_scale;           // mode 1
-    int H, W;
-    int* err;                  // set to 1 when a bounded wait runs out
-};
-
 enum { OUT_BF16 = 0, OUT_FIELD = 1, OUT_MASKED = 2 };
 
 template <int CIN, int COUTP, int RPB>
@@ -197,7 +187,10 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(ConvArgs a) {
     // wait for the accumulators (bounded)
     uint32_t done = 0;
     for (long it = 0; it < (1L << 24) && !done; ++it) done = mbar_try_wait(smem_u32(mbar), 0);
-    if (!done && a.err) atomicExch(a.err, 1);
+    // block-uniform outcome: the warp-collective loads below run in every
+    // warp or in none
+    done = __syncthreads_and(done);
+    if (!done && tid == 0 && a.err) atomicExch(a.err, 1);
     tc_fence_after();
     if (done) {
         const int m = warp * 32 + (tid & 31);
@@ -469,6 +462,44 @@ cudaError_t cnn_conv_simt(int layer, const ConvArgs& a, const __nv_bfloat16* wpl
         default: conv_simt_kernel<32, 16><<<grid, 128, 0, s>>>(a, wplain, OUT_FIELD, 0); break;
     }
     return cudaGetLastError();
+}
+
+void cnn_pack(cudaStream_t s, const float* w, int cout, int cin, int CINP, int COUTP, int flip, __nv_bfloat16* out) {
+    const int n = kTaps * CINP * COUTP;
+    pack_weights_kernel<<<(n + 255) / 256, 256, 0, s>>>(w, cout, cin, CINP, COUTP, flip, out);
+}
+
+void cnn_plain(cudaStream_t s, const float* w, int cout, int cin, int CINP, int COUTP, __nv_bfloat16* out) {
+    const int n = kTaps * CINP * COUTP;
+    plain_weights_kernel<<<(n + 255) / 256, 256, 0, s>>>(w, cout, cin, CINP, COUTP, out);
+}
+
+void cnn_dweight(cudaStream_t s, const __nv_bfloat16* dz, int CZ, int cout, const __nv_bfloat16* x, int CX, int cin,
+                 int B, int H, int W, float* dw, float* db) {
+    const long long npix = (long long)B * H * W;
+    const int chunk = 4096;
+    const dim3 g((unsigned)((npix + chunk - 1) / chunk), kTaps);
+    dweight_kernel<<<g, 1024, 0, s>>>(dz, CZ, cout, x, CX, cin, B, H, W, chunk, dw, db);
+}
+
+void cnn_mse_grad(cudaStream_t s, const float* y, const float* t, int B, int H, int W, __nv_bfloat16* dy,
+                  double* loss) {
+    mse_grad_kernel<<<(unsigned)((B * (long long)H * W + 255) / 256), 256, 0, s>>>(y, t, B, H, W, 1.f, dy, loss);
+}
+
+void cnn_adam(cudaStream_t s, float* p, const float* g, float* m, float* v, int n, float lr, int t) {
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    adam_kernel<<<(n + 255) / 256, 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, 1e-8f, c1, c2, 1.f);
+}
+
+void cnn_dm_to_input(cudaStream_t s, const float* m, const float* mref, int H, int W, float c_in, __nv_bfloat16* x) {
+    const long long N = (long long)H * W;
+    dm_to_nhwc_kernel<float><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(m, mref, H, W, c_in, x);
+}
+
+void cnn_field_from_output(cudaStream_t s, const float* out, const float* href, long long N, float Ms, float* H) {
+    field_from_cnn_kernel<float><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(out, href, N, Ms, H);
 }
 
 }  // namespace mm

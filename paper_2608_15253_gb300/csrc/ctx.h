@@ -81,6 +81,7 @@ struct DemagPlan {
 };
 
 struct BatchHost;
+struct SurrogateHost;
 
 struct ProfileSlot {
     std::string name;
@@ -153,6 +154,8 @@ struct mm_ctx {
     std::vector<double> rT, rJ;
     long long Ntot = 0;                // cells over all replicas
 
+    mm::SurrogateHost* surr = nullptr;  // learned demag surrogate (single instance)
+
     long long launches = 0;
     bool profiling = false;
     std::vector<mm::ProfileSlot> prof;
@@ -205,7 +208,15 @@ void batch_get_shape(BatchHost* b, int* nt, int* blocks);
 std::string batch_signature(BatchHost* b, unsigned terms);
 int batch_class_of(BatchHost* b, int r);
 
+// surrogate.cu
+void surrogate_free(mm_ctx* c);
+bool surrogate_active(mm_ctx* c);           // this evaluation uses the network
+bool surrogate_stepping(mm_ctx* c);         // surrogate-accelerated stepping is on
+void surrogate_apply(mm_ctx* c, const void* m, void* Hd);
+mm_status surrogate_block(mm_ctx* c);       // one exact refresh + k-1 network attempts
+
 // integrate.cu
+void demag_eval(mm_ctx* c, const void* m, void* Hd);   // exact or surrogate
 void heun_batch_begin(mm_ctx* c);
 void heun_batch_advance(mm_ctx* c);
 void rk45_first_slope(mm_ctx* c);          // k1 = f(m0) into the FSAL slot

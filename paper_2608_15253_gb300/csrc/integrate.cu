@@ -191,6 +191,11 @@ __global__ void heun_begin_kernel(DevState* st) {
     st->dt_eff = st->dt;
 }
 
+void demag_eval(mm_ctx* c, const void* m, void* Hd) {
+    if (surrogate_active(c)) surrogate_apply(c, m, Hd);
+    else demag_apply(c, m, Hd);
+}
+
 template <typename T>
 static void rk45_attempt_t(mm_ctx* c) {
     const long long N = c->N, n3 = 3 * N;
@@ -210,7 +215,7 @@ static void rk45_attempt_t(mm_ctx* c) {
                 combine_kernel<T, 4>, combine_kernel<T, 5>, combine_kernel<T, 6>};
             kern[s]<<<nb3, tb, 0, c->stream>>>(c->d_state, kp, (const T*)c->d_m, (T*)c->d_mtmp, n3);
         }
-        if (demag) demag_apply(c, c->d_mtmp, c->d_hd);
+        if (demag) demag_eval(c, c->d_mtmp, c->d_hd);
         // stages 2..6 own fixed slots; the FSAL stage 7 slope goes to the slot
         // that does not hold k1 (resolved on the device)
         field_launch(c, MODE_K, terms, c->d_mtmp, demag ? c->d_hd : nullptr, s < 6 ? c->d_k[s] : nullptr, nullptr,
@@ -238,7 +243,7 @@ void rk45_attempt(mm_ctx* c) {
 void rk45_first_slope(mm_ctx* c) {
     const unsigned terms = c->terms;
     const bool demag = c->dm.on && (terms & MM_TERM_DEMAG);
-    if (demag) demag_apply(c, c->d_m, c->d_hd);
+    if (demag) demag_eval(c, c->d_m, c->d_hd);
     field_launch(c, MODE_K, terms, c->d_m, demag ? c->d_hd : nullptr, nullptr, nullptr, nullptr, nullptr, -1, 0, 0);
 }
 

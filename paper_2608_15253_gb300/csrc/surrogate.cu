@@ -1,0 +1,599 @@
+// Host orchestration of the learned demag surrogate: parameters and Adam
+// state, activation buffers, forward / backward / training, training data
+// from exact relaxation snapshots, and surrogate-accelerated RK45 stepping
+// with the exact-demag error monitor and fallback.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "cnn.h"
+#include "common.cuh"
+#include "ctx.h"
+
+namespace mm {
+
+static const int kCin[4] = {3, 32, 32, 32}, kCout[4] = {32, 32, 32, 3};
+static const int kCinP[4] = {16, 32, 32, 32}, kCoutP[4] = {32, 32, 32, 16};
+
+struct SurrogateHost {
+    int np = 0;
+    int off_w[4], off_b[4];
+    float *d_p = nullptr, *d_g = nullptr, *d_m = nullptr, *d_v = nullptr;
+    int adam_t = 0;
+    float c_in = 1.f;
+    bool have_weights = false;
+    __nv_bfloat16 *wpk[4] = {}, *wpkT[4] = {}, *wplain[4] = {};
+    float* biasp[4] = {};       // bias zero-padded to the layer's padded output channels
+    int cB = 0, cH = 0, cW = 0;
+    __nv_bfloat16 *x0 = nullptr, *h1 = nullptr, *h2 = nullptr, *h3 = nullptr, *dy = nullptr, *dza = nullptr,
+                  *dzb = nullptr;
+    float *y = nullptr, *t = nullptr;
+    double* d_loss = nullptr;
+    int* d_err = nullptr;
+    // stepping
+    int k = 0;
+    double tol = 1e-3;
+    bool fallback = false, ref_valid = false, use_now = false;
+    long long n_exact = 0, n_surr = 0, n_refresh = 0, attempts = 0;
+    double last_err = 0, max_err = 0, train_loss = 0;
+    float* d_mref = nullptr;
+    float* d_href = nullptr;
+    double* d_red = nullptr;
+};
+
+static void sfree(SurrogateHost* s) {
+    if (!s) return;
+    void* ptrs[] = {s->d_p, s->d_g, s->d_m, s->d_v, s->x0, s->h1, s->h2, s->h3, s->dy, s->dza, s->dzb,
+                    s->y, s->t, s->d_loss, s->d_err, s->d_mref, s->d_href, s->d_red};
+    for (void* p : ptrs) cudaFree(p);
+    for (int l = 0; l < 4; ++l) {
+        cudaFree(s->wpk[l]);
+        cudaFree(s->wpkT[l]);
+        cudaFree(s->wplain[l]);
+        cudaFree(s->biasp[l]);
+    }
+    delete s;
+}
+
+void surrogate_free(mm_ctx* c) {
+    sfree(c->surr);
+    c->surr = nullptr;
+}
+
+static mm_status scheck(mm_ctx* c, cudaError_t e, const char* what) { return cuda_check(c, e, what); }
+
+static mm_status ensure_surrogate(mm_ctx* c) {
+    if (c->surr) return MM_OK;
+    if (c->batch || c->prec != 32 || c->grid.nz != 1 || !c->dm.on)
+        return set_error(c, MM_ERR_STATE, "the surrogate needs a single-instance FP32 nz = 1 context with exact demag");
+    SurrogateHost* s = new SurrogateHost();
+    int o = 0;
+    for (int l = 0; l < 4; ++l) {
+        s->off_w[l] = o;
+        o += kCout[l] * kCin[l] * 25;
+        s->off_b[l] = o;
+        o += kCout[l];
+    }
+    s->np = o;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](void** p, size_t b) { if (e == cudaSuccess) e = cudaMalloc(p, b); if (e == cudaSuccess) e = cudaMemset(*p, 0, b); };
+    A((void**)&s->d_p, sizeof(float) * s->np);
+    A((void**)&s->d_g, sizeof(float) * s->np);
+    A((void**)&s->d_m, sizeof(float) * s->np);
+    A((void**)&s->d_v, sizeof(float) * s->np);
+    for (int l = 0; l < 4; ++l) {
+        A((void**)&s->wpk[l], sizeof(__nv_bfloat16) * 25 * kCinP[l] * kCoutP[l]);
+        A((void**)&s->wpkT[l], sizeof(__nv_bfloat16) * 25 * kCoutP[l] * kCinP[l] * 2);
+        A((void**)&s->wplain[l], sizeof(__nv_bfloat16) * 25 * kCinP[l] * kCoutP[l]);
+        A((void**)&s->biasp[l], sizeof(float) * kCoutP[l]);
+    }
+    A((void**)&s->d_loss, sizeof(double));
+    A((void**)&s->d_err, sizeof(int));
+    A((void**)&s->d_red, sizeof(double) * 4);
+    if (e != cudaSuccess) {
+        sfree(s);
+        return cuda_check(c, e, "surrogate parameters");
+    }
+    c->surr = s;
+    return MM_OK;
+}
+
+static mm_status ensure_buffers(mm_ctx* c, int B, int H, int W) {
+    SurrogateHost* s = c->surr;
+    if (B <= s->cB && H == s->cH && W == s->cW) return MM_OK;
+    void* ptrs[] = {s->x0, s->h1, s->h2, s->h3, s->dy, s->dza, s->dzb, s->y, s->t};
+    for (void* p : ptrs) cudaFree(p);
+    const size_t pp = (size_t)B * (H + 4) * (W + 4);
+    cudaError_t e = cudaSuccess;
+    auto A = [&](void** p, size_t b) { if (e == cudaSuccess) e = cudaMalloc(p, b); if (e == cudaSuccess) e = cudaMemset(*p, 0, b); };
+    A((void**)&s->x0, pp * 16 * 2);
+    A((void**)&s->h1, pp * 32 * 2);
+    A((void**)&s->h2, pp * 32 * 2);
+    A((void**)&s->h3, pp * 32 * 2);
+    A((void**)&s->dy, pp * 16 * 2);
+    A((void**)&s->dza, pp * 32 * 2);
+    A((void**)&s->dzb, pp * 32 * 2);
+    A((void**)&s->y, (size_t)B * H * W * 3 * 4);
+    A((void**)&s->t, (size_t)B * H * W * 3 * 4);
+    s->cB = B;
+    s->cH = H;
+    s->cW = W;
+    return cuda_check(c, e, "surrogate activations");
+}
+
+static void pack_all(mm_ctx* c) {
+    SurrogateHost* s = c->surr;
+    for (int l = 0; l < 4; ++l) {
+        const int n = 25 * kCinP[l] * kCoutP[l];
+        (void)n;
+        LaunchScope ls(c, "cnn_pack", 0.0);
+        cnn_pack(c->stream, s->d_p + s->off_w[l], kCout[l], kCin[l], kCinP[l], kCoutP[l], 0, s->wpk[l]);
+        cnn_plain(c->stream, s->d_p + s->off_w[l], kCout[l], kCin[l], kCinP[l], kCoutP[l], s->wplain[l]);
+        // input-gradient weights: in channels = this layer's padded cout, out = padded cin
+        cnn_pack(c->stream, s->d_p + s->off_w[l], kCout[l], kCin[l], kCoutP[l], kCinP[l], 1, s->wpkT[l]);
+        cudaMemcpyAsync(s->biasp[l], s->d_p + s->off_b[l], sizeof(float) * kCout[l], cudaMemcpyDeviceToDevice,
+                        c->stream);
+    }
+}
+
+static void set_he_init(mm_ctx* c, uint64_t seed) {
+    SurrogateHost* s = c->surr;
+    std::vector<float> h(s->np, 0.f);
+    std::mt19937_64 gen(seed);
+    std::normal_distribution<double> nd(0.0, 1.0);
+    for (int l = 0; l < 4; ++l) {
+        const double sd = std::sqrt(2.0 / (kCin[l] * 25.0));
+        for (int q = 0; q < kCout[l] * kCin[l] * 25; ++q) h[s->off_w[l] + q] = (float)(sd * nd(gen));
+    }
+    cudaMemcpy(s->d_p, h.data(), sizeof(float) * s->np, cudaMemcpyHostToDevice);
+    cudaMemset(s->d_m, 0, sizeof(float) * s->np);
+    cudaMemset(s->d_v, 0, sizeof(float) * s->np);
+    s->adam_t = 0;
+    s->have_weights = true;
+}
+
+// x0 (bf16, filled) -> y (f32 [B][H][W][3] times out_scale)
+static mm_status run_forward(mm_ctx* c, int B, int H, int W, float out_scale, int path) {
+    SurrogateHost* s = c->surr;
+    __nv_bfloat16* in[4] = {s->x0, s->h1, s->h2, s->h3};
+    void* out[4] = {s->h1, s->h2, s->h3, s->y};
+    for (int l = 0; l < 4; ++l) {
+        ConvArgs a{};
+        a.in = in[l];
+        a.wpk = reinterpret_cast<const uint4*>(s->wpk[l]);
+        a.bias = s->biasp[l];
+        a.out = out[l];
+        a.out_scale = out_scale;
+        a.H = H;
+        a.W = W;
+        a.err = s->d_err;
+        LaunchScope ls(c, l == 0 ? "cnn_conv0" : l == 3 ? "cnn_conv3" : "cnn_conv12",
+                       (double)B * H * W * 2.0 * (kCinP[l] + kCoutP[l]));
+        cudaError_t e = path == 0 ? cnn_conv(l, false, a, B, c->stream) : cnn_conv_simt(l, a, s->wplain[l], B, c->stream);
+        if (e != cudaSuccess) return cuda_check(c, e, "surrogate forward");
+    }
+    return MM_OK;
+}
+
+static mm_status run_backward(mm_ctx* c, int B, int H, int W) {
+    SurrogateHost* s = c->surr;
+    cudaMemsetAsync(s->d_g, 0, sizeof(float) * s->np, c->stream);
+    __nv_bfloat16* xin[4] = {s->x0, s->h1, s->h2, s->h3};
+    const int cx[4] = {16, 32, 32, 32};
+    // layer 3: dZ = dy (16 ch)
+    const __nv_bfloat16* dz = s->dy;
+    int cz = 16;
+    __nv_bfloat16* bufs[2] = {s->dza, s->dzb};
+    for (int l = 3; l >= 0; --l) {
+        {
+            LaunchScope ls(c, "cnn_dweight", 0.0);
+            cnn_dweight(c->stream, dz, cz, kCout[l], xin[l], cx[l], kCin[l], B, H, W, s->d_g + s->off_w[l],
+                        s->d_g + s->off_b[l]);
+        }
+        if (l == 0) break;
+        ConvArgs a{};
+        a.in = dz;
+        a.wpk = reinterpret_cast<const uint4*>(s->wpkT[l]);
+        a.bias = nullptr;
+        __nv_bfloat16* o = bufs[l % 2];
+        a.out = o;
+        a.mask = xin[l];   // dZ_{l-1} = dH ⊙ (h_l > 0), h_l = input of layer l
+        a.H = H;
+        a.W = W;
+        a.err = s->d_err;
+        LaunchScope ls(c, "cnn_dgrad", 0.0);
+        cudaError_t e = cnn_conv(l, true, a, B, c->stream);
+        if (e != cudaSuccess) return cuda_check(c, e, "surrogate backward");
+        dz = o;
+        cz = 32;
+    }
+    return cuda_check(c, cudaGetLastError(), "surrogate backward");
+}
+
+// host [B][3][H][W] -> x0 interior (bf16, 3 of 16 channels)
+__global__ void host_x_to_nhwc_kernel(const float* __restrict__ x, int B, int H, int W, __nv_bfloat16* __restrict__ o) {
+    const long long n = (long long)B * H * W;
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int b = (int)(q / ((long long)H * W));
+    const int rem = (int)(q % ((long long)H * W));
+    const int i = rem / W, j = rem % W;
+    __nv_bfloat16* d = o + (((long long)b * (H + 4) + i + 2) * (W + 4) + j + 2) * 16;
+    for (int cc = 0; cc < 3; ++cc) d[cc] = __float2bfloat16_rn(x[((long long)b * 3 + cc) * H * W + (long long)i * W + j]);
+}
+
+static mm_status upload_x(mm_ctx* c, int B, int H, int W, const double* x) {
+    SurrogateHost* s = c->surr;
+    const size_t n = (size_t)B * 3 * H * W;
+    std::vector<float> h(n);
+    for (size_t q = 0; q < n; ++q) h[q] = (float)x[q];
+    float* tmp = nullptr;
+    cudaError_t e = cudaMalloc(&tmp, n * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(tmp, h.data(), n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        host_x_to_nhwc_kernel<<<(unsigned)((B * (long long)H * W + 255) / 256), 256, 0, c->stream>>>(tmp, B, H, W, s->x0);
+        e = cudaStreamSynchronize(c->stream);
+    }
+    cudaFree(tmp);
+    return cuda_check(c, e, "surrogate input");
+}
+
+// ---- training data -----------------------------------------------------
+__global__ void diff_kernel(const float* __restrict__ a, const float* __restrict__ b, long long n, float* __restrict__ o) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q < n) o[q] = a[q] - b[q];
+}
+
+__global__ void sumsq_kernel(const float* __restrict__ a, long long n, double* __restrict__ out) {
+    double acc = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        acc += (double)a[q] * a[q];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
+// crop windows: item b takes field p = idx[3b] at offsets (idx[3b+1], idx[3b+2])
+__global__ void crop_kernel(const float* __restrict__ dm, const float* __restrict__ dh, long long field_elems,
+                            int nx, int ny, const int* __restrict__ idx, int B, int S, float c_in, float inv_ms,
+                            __nv_bfloat16* __restrict__ x0, float* __restrict__ t) {
+    const long long n = (long long)B * S * S;
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int b = (int)(q / ((long long)S * S));
+    const int rem = (int)(q % ((long long)S * S));
+    const int i = rem / S, j = rem % S;
+    const int p = idx[3 * b], oy = idx[3 * b + 1], ox = idx[3 * b + 2];
+    const long long N = (long long)nx * ny;
+    const long long cell = (long long)(oy + i) * nx + ox + j;
+    const float* f = dm + p * field_elems;
+    const float* g = dh + p * field_elems;
+    __nv_bfloat16* d = x0 + (((long long)b * (S + 4) + i + 2) * (S + 4) + j + 2) * 16;
+    float* tt = t + (((long long)b * S + i) * S + j) * 3;
+    for (int cc = 0; cc < 3; ++cc) {
+        d[cc] = __float2bfloat16_rn(c_in * f[cc * N + cell]);
+        tt[cc] = c_in * inv_ms * g[cc * N + cell];
+    }
+}
+
+__global__ void copy_kernel(const float* __restrict__ a, long long n, float* __restrict__ o) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q < n) o[q] = a[q];
+}
+
+// max |a - b| and max |b| over 3N values -> red[0], red[1] (as ordered bits)
+__global__ void err_max_kernel(const float* __restrict__ a, const float* __restrict__ b, long long n,
+                               double* __restrict__ red) {
+    double e = 0.0, m = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        e = fmax(e, fabs((double)a[q] - (double)b[q]));
+        m = fmax(m, fabs((double)b[q]));
+    }
+    e = warp_max(e);
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(&red[0], e);
+        atomic_max_nonneg(&red[1], m);
+    }
+}
+
+// H_pred(m) = H_ref + Ms * CNN(c_in (m - m_ref)) / c_in into Hd
+void surrogate_apply(mm_ctx* c, const void* m, void* Hd) {
+    SurrogateHost* s = c->surr;
+    const int H = c->grid.ny, W = c->grid.nx;
+    const long long N = c->N;
+    {
+        LaunchScope ls(c, "cnn_input", 24.0 * N);
+        cnn_dm_to_input(c->stream, (const float*)m, s->d_mref, H, W, s->c_in, s->x0);
+    }
+    run_forward(c, 1, H, W, 1.f / s->c_in, 0);
+    LaunchScope ls(c, "cnn_output", 36.0 * N);
+    cnn_field_from_output(c->stream, s->y, s->d_href, N, (float)c->regions[0].Ms, (float*)Hd);
+    s->n_surr++;
+}
+
+bool surrogate_active(mm_ctx* c) { return c->surr && c->surr->use_now; }
+
+// one block of k attempts: an exact refresh attempt (with the error monitor)
+// followed by k-1 surrogate attempts
+void rk45_attempt(mm_ctx* c);
+mm_status sync_state_pub(mm_ctx* c);
+
+mm_status surrogate_block(mm_ctx* c) {
+    SurrogateHost* s = c->surr;
+    const long long N = c->N;
+    const unsigned nb = (unsigned)((3 * N + 255) / 256);
+    if (s->fallback) {
+        s->use_now = false;
+        rk45_attempt(c);
+        s->n_exact += 6;
+        return cuda_check(c, cudaGetLastError(), "attempt");
+    }
+    if (s->ref_valid) {
+        // monitor: the network's prediction at the current state vs the exact field
+        surrogate_apply(c, c->d_m, c->d_hbuf);
+        demag_apply(c, c->d_m, c->d_hd);
+        cudaMemsetAsync(s->d_red, 0, sizeof(double) * 2, c->stream);
+        err_max_kernel<<<304, 256, 0, c->stream>>>((const float*)c->d_hbuf, (const float*)c->d_hd, 3 * N, s->d_red);
+        double h[2] = {0, 0};
+        cudaMemcpyAsync(h, s->d_red, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_check(c, e, "surrogate monitor");
+        s->last_err = h[1] > 0 ? h[0] / h[1] : 0.0;
+        s->max_err = std::max(s->max_err, s->last_err);
+        if (!(s->last_err <= s->tol)) s->fallback = true;
+    } else {
+        demag_apply(c, c->d_m, c->d_hd);
+    }
+    // refresh (m_ref, H_ref) at the current state
+    copy_kernel<<<nb, 256, 0, c->stream>>>((const float*)c->d_m, 3 * N, s->d_mref);
+    copy_kernel<<<nb, 256, 0, c->stream>>>((const float*)c->d_hd, 3 * N, s->d_href);
+    s->ref_valid = true;
+    s->n_refresh++;
+    s->n_exact++;
+    s->use_now = false;
+    rk45_attempt(c);
+    s->n_exact += 6;
+    for (int q = 1; q < s->k && !s->fallback; ++q) {
+        s->use_now = true;
+        rk45_attempt(c);
+        s->use_now = false;
+    }
+    return cuda_check(c, cudaGetLastError(), "surrogate block");
+}
+
+bool surrogate_stepping(mm_ctx* c) { return c->surr && c->surr->k > 0; }
+
+}  // namespace mm
+
+using namespace mm;
+
+extern "C" {
+
+mm_status mm_surrogate_weights(mm_ctx* c, double* get, const double* set, size_t n, double* c_in) {
+    if (!c) return MM_ERR_ARG;
+    mm_status st = ensure_surrogate(c);
+    if (st != MM_OK) return st;
+    SurrogateHost* s = c->surr;
+    if ((get || set) && n != (size_t)s->np) return set_error(c, MM_ERR_ARG, "surrogate weights: n must be 56099");
+    if (set) {
+        std::vector<float> h(s->np);
+        for (int q = 0; q < s->np; ++q) h[q] = (float)set[q];
+        cudaMemcpy(s->d_p, h.data(), sizeof(float) * s->np, cudaMemcpyHostToDevice);
+        cudaMemset(s->d_m, 0, sizeof(float) * s->np);
+        cudaMemset(s->d_v, 0, sizeof(float) * s->np);
+        s->adam_t = 0;
+        s->have_weights = true;
+        if (c_in) s->c_in = (float)*c_in;
+        pack_all(c);
+    } else if (!s->have_weights) {
+        set_he_init(c, 1);
+        pack_all(c);
+    }
+    if (get) {
+        std::vector<float> h(s->np);
+        cudaMemcpy(h.data(), s->d_p, sizeof(float) * s->np, cudaMemcpyDeviceToHost);
+        for (int q = 0; q < s->np; ++q) get[q] = h[q];
+    }
+    if (c_in && !set) *c_in = s->c_in;
+    return cuda_check(c, cudaDeviceSynchronize(), "surrogate weights");
+}
+
+mm_status mm_surrogate_forward(mm_ctx* c, int B, int H, int W, const double* x, double* y, int path) {
+    if (!c || !x || !y || B <= 0 || H <= 0 || W <= 0 || (path != 0 && path != 1)) return MM_ERR_ARG;
+    mm_status st = ensure_surrogate(c);
+    if (st == MM_OK && !c->surr->have_weights) st = mm_surrogate_weights(c, nullptr, nullptr, 0, nullptr);
+    if (st == MM_OK) st = ensure_buffers(c, B, H, W);
+    if (st == MM_OK) st = upload_x(c, B, H, W, x);
+    if (st == MM_OK) st = run_forward(c, B, H, W, 1.f, path);
+    if (st != MM_OK) return st;
+    std::vector<float> h((size_t)B * H * W * 3);
+    cudaError_t e = cudaMemcpyAsync(h.data(), c->surr->y, h.size() * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "surrogate forward");
+    int err = 0;
+    cudaMemcpy(&err, c->surr->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (err) return set_error(c, MM_ERR_TIMEOUT, "tensor-core accumulator wait ran out");
+    for (int b = 0; b < B; ++b)
+        for (int cc = 0; cc < 3; ++cc)
+            for (long long p = 0; p < (long long)H * W; ++p)
+                y[((long long)b * 3 + cc) * H * W + p] = h[((long long)b * H * W + p) * 3 + cc];
+    return MM_OK;
+}
+
+mm_status mm_surrogate_grad(mm_ctx* c, int B, int H, int W, const double* x, const double* t, double* loss,
+                            double* grad) {
+    if (!c || !x || !t || B <= 0 || H <= 0 || W <= 0) return MM_ERR_ARG;
+    mm_status st = ensure_surrogate(c);
+    if (st == MM_OK && !c->surr->have_weights) st = mm_surrogate_weights(c, nullptr, nullptr, 0, nullptr);
+    if (st == MM_OK) st = ensure_buffers(c, B, H, W);
+    if (st == MM_OK) st = upload_x(c, B, H, W, x);
+    if (st == MM_OK) st = run_forward(c, B, H, W, 1.f, 0);
+    if (st != MM_OK) return st;
+    SurrogateHost* s = c->surr;
+    const size_t n = (size_t)B * H * W * 3;
+    std::vector<float> ht(n);
+    for (int b = 0; b < B; ++b)
+        for (int cc = 0; cc < 3; ++cc)
+            for (long long p = 0; p < (long long)H * W; ++p)
+                ht[((long long)b * H * W + p) * 3 + cc] = (float)t[((long long)b * 3 + cc) * H * W + p];
+    cudaMemcpy(s->t, ht.data(), n * 4, cudaMemcpyHostToDevice);
+    cudaMemsetAsync(s->d_loss, 0, sizeof(double), c->stream);
+    cnn_mse_grad(c->stream, s->y, s->t, B, H, W, s->dy, s->d_loss);
+    st = run_backward(c, B, H, W);
+    if (st != MM_OK) return st;
+    std::vector<float> hg(s->np);
+    double l = 0;
+    cudaError_t e = cudaMemcpyAsync(hg.data(), s->d_g, sizeof(float) * s->np, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&l, s->d_loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "surrogate gradient");
+    if (loss) *loss = l;
+    if (grad)
+        for (int q = 0; q < s->np; ++q) grad[q] = hg[q];
+    return MM_OK;
+}
+
+mm_status mm_surrogate_train(mm_ctx* c, const mm_train_cfg* cfg, double* final_loss) {
+    if (!c || !cfg) return MM_ERR_ARG;
+    mm_status st = ensure_surrogate(c);
+    if (st != MM_OK) return st;
+    SurrogateHost* s = c->surr;
+    const int nx = c->grid.nx, ny = c->grid.ny;
+    const int S = cfg->crop;
+    if (cfg->n_snapshots < 2 || cfg->snap_every < 1 || cfg->max_gap < 1 || S < 8 || S > nx || S > ny || cfg->batch < 1 ||
+        cfg->steps < 0 || !(cfg->lr > 0))
+        return set_error(c, MM_ERR_ARG, "bad surrogate training configuration");
+    const long long N = c->N, fe = 3 * N;
+    // keep the caller's state: checkpoint and restore
+    size_t nb = 0;
+    mm_get_state(c, nullptr, &nb);
+    std::vector<unsigned char> ck(nb);
+    st = mm_get_state(c, ck.data(), &nb);
+    if (st != MM_OK) return st;
+    const int k_saved = s->k;
+    s->k = 0;
+    // snapshots of an exact relaxation
+    const int ns = cfg->n_snapshots;
+    float* snaps = nullptr;
+    cudaError_t e = cudaMalloc(&snaps, sizeof(float) * fe * ns);
+    if (e != cudaSuccess) return cuda_check(c, e, "snapshots");
+    for (int q = 0; q < ns; ++q) {
+        if (q > 0) {
+            st = mm_step(c, cfg->snap_every);
+            if (st != MM_OK) { cudaFree(snaps); return st; }
+        }
+        cudaMemcpyAsync(snaps + q * fe, c->d_m, sizeof(float) * fe, cudaMemcpyDeviceToDevice, c->stream);
+    }
+    std::vector<std::pair<int, int>> pairs;
+    for (int i = 0; i < ns; ++i)
+        for (int j = i + 1; j < ns && j - i <= cfg->max_gap; ++j) pairs.push_back({i, j});
+    const int np = (int)pairs.size();
+    float *dm = nullptr, *dh = nullptr;
+    e = cudaMalloc(&dm, sizeof(float) * fe * np);
+    if (e == cudaSuccess) e = cudaMalloc(&dh, sizeof(float) * fe * np);
+    if (e != cudaSuccess) {
+        cudaFree(snaps); cudaFree(dm); cudaFree(dh);
+        return cuda_check(c, e, "training pairs");
+    }
+    const unsigned gb = (unsigned)((fe + 255) / 256);
+    for (int q = 0; q < np; ++q) {
+        diff_kernel<<<gb, 256, 0, c->stream>>>(snaps + pairs[q].second * fe, snaps + pairs[q].first * fe, fe, dm + q * fe);
+        demag_apply(c, dm + q * fe, dh + q * fe);   // exact FFT demag of the increment (linear in m)
+    }
+    cudaMemsetAsync(s->d_red, 0, sizeof(double), c->stream);
+    sumsq_kernel<<<304, 256, 0, c->stream>>>(dm, fe * np, s->d_red);
+    double ss = 0;
+    cudaMemcpyAsync(&ss, s->d_red, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    e = cudaStreamSynchronize(c->stream);
+    cudaFree(snaps);
+    if (e != cudaSuccess) { cudaFree(dm); cudaFree(dh); return cuda_check(c, e, "training data"); }
+    const double rms = std::sqrt(ss / (double)(fe * np));
+    s->c_in = rms > 0 ? (float)(1.0 / rms) : 1.f;
+    if (!s->have_weights) set_he_init(c, cfg->seed);
+    pack_all(c);
+    const int B = cfg->batch;
+    st = ensure_buffers(c, B, S, S);
+    if (st != MM_OK) { cudaFree(dm); cudaFree(dh); return st; }
+    int* d_idx = nullptr;
+    cudaMalloc(&d_idx, sizeof(int) * 3 * B);
+    std::mt19937_64 gen(cfg->seed ^ 0x5DEECE66Dull);
+    std::vector<int> idx(3 * B);
+    const float inv_ms = (float)(1.0 / c->regions[0].Ms);
+    double loss = 0;
+    for (int it = 0; it < cfg->steps; ++it) {
+        for (int b = 0; b < B; ++b) {
+            idx[3 * b] = (int)(gen() % (uint64_t)np);
+            idx[3 * b + 1] = (int)(gen() % (uint64_t)(ny - S + 1));
+            idx[3 * b + 2] = (int)(gen() % (uint64_t)(nx - S + 1));
+        }
+        cudaMemcpyAsync(d_idx, idx.data(), sizeof(int) * 3 * B, cudaMemcpyHostToDevice, c->stream);
+        crop_kernel<<<(unsigned)((B * (long long)S * S + 255) / 256), 256, 0, c->stream>>>(
+            dm, dh, fe, nx, ny, d_idx, B, S, s->c_in, inv_ms, s->x0, s->t);
+        run_forward(c, B, S, S, 1.f, 0);
+        cudaMemsetAsync(s->d_loss, 0, sizeof(double), c->stream);
+        cnn_mse_grad(c->stream, s->y, s->t, B, S, S, s->dy, s->d_loss);
+        run_backward(c, B, S, S);
+        s->adam_t += 1;
+        cnn_adam(c->stream, s->d_p, s->d_g, s->d_m, s->d_v, s->np, (float)cfg->lr, s->adam_t);
+        pack_all(c);
+        if (it == cfg->steps - 1 || (it % 100) == 0) {
+            cudaMemcpyAsync(&loss, s->d_loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+            cudaStreamSynchronize(c->stream);
+        }
+    }
+    e = cudaStreamSynchronize(c->stream);
+    cudaFree(d_idx);
+    cudaFree(dm);
+    cudaFree(dh);
+    if (e != cudaSuccess) return cuda_check(c, e, "surrogate training");
+    s->train_loss = loss;
+    if (final_loss) *final_loss = loss;
+    s->k = k_saved;
+    s->ref_valid = false;
+    return mm_set_state(c, ck.data(), nb);
+}
+
+mm_status mm_surrogate_set(mm_ctx* c, int k, double tol) {
+    if (!c || k < 0 || !(tol > 0)) return MM_ERR_ARG;
+    mm_status st = ensure_surrogate(c);
+    if (st != MM_OK) return st;
+    SurrogateHost* s = c->surr;
+    if (k > 0 && !s->have_weights) return set_error(c, MM_ERR_STATE, "train or set the surrogate weights first");
+    if (k > 0 && !s->d_mref) {
+        cudaError_t e = cudaMalloc(&s->d_mref, sizeof(float) * 3 * c->N);
+        if (e == cudaSuccess) e = cudaMalloc(&s->d_href, sizeof(float) * 3 * c->N);
+        if (e != cudaSuccess) return cuda_check(c, e, "surrogate reference");
+        st = ensure_buffers(c, 1, c->grid.ny, c->grid.nx);
+        if (st != MM_OK) return st;
+    }
+    s->k = k;
+    s->tol = tol;
+    s->fallback = false;
+    s->ref_valid = false;
+    s->last_err = s->max_err = 0;
+    s->n_exact = s->n_surr = s->n_refresh = 0;
+    return MM_OK;
+}
+
+mm_status mm_surrogate_get_stats(mm_ctx* c, mm_surrogate_stats* out) {
+    if (!c || !out) return MM_ERR_ARG;
+    memset(out, 0, sizeof(*out));
+    if (!c->surr) return MM_OK;
+    SurrogateHost* s = c->surr;
+    out->exact_evals = s->n_exact;
+    out->surrogate_evals = s->n_surr;
+    out->refreshes = s->n_refresh;
+    out->fallback = s->fallback;
+    out->last_error = s->last_err;
+    out->max_error = s->max_err;
+    out->train_loss = s->train_loss;
+    out->c_in = s->c_in;
+    return MM_OK;
+}
+
+}  // extern "C"

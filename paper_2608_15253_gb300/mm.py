@@ -65,6 +65,17 @@ class mm_profile_entry(C.Structure):
                 ("bytes_per_launch", C.c_double)]
 
 
+class mm_train_cfg(C.Structure):
+    _fields_ = [("n_snapshots", C.c_int), ("snap_every", C.c_int), ("max_gap", C.c_int), ("crop", C.c_int),
+                ("batch", C.c_int), ("steps", C.c_int), ("lr", C.c_double), ("seed", C.c_uint64)]
+
+
+class mm_surrogate_stats(C.Structure):
+    _fields_ = [("exact_evals", C.c_longlong), ("surrogate_evals", C.c_longlong), ("refreshes", C.c_longlong),
+                ("fallback", C.c_int), ("last_error", C.c_double), ("max_error", C.c_double),
+                ("train_loss", C.c_double), ("c_in", C.c_double)]
+
+
 class MMError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"libmm status {status}: {msg}")
@@ -100,6 +111,12 @@ _SIGS = {
     "mm_topo_charge_noalloc": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
                                C.c_void_p, C.c_void_p],
     "mm_batch_autotune": [C.c_void_p, C.c_char_p, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+    "mm_surrogate_train": [C.c_void_p, C.POINTER(mm_train_cfg), _D],
+    "mm_surrogate_set": [C.c_void_p, C.c_int, C.c_double],
+    "mm_surrogate_get_stats": [C.c_void_p, C.POINTER(mm_surrogate_stats)],
+    "mm_surrogate_weights": [C.c_void_p, _D, _D, C.c_size_t, _D],
+    "mm_surrogate_forward": [C.c_void_p, C.c_int, C.c_int, C.c_int, _D, _D, C.c_int],
+    "mm_surrogate_grad": [C.c_void_p, C.c_int, C.c_int, C.c_int, _D, _D, _D, _D],
     "mm_set_profiling": [C.c_void_p, C.c_int],
     "mm_get_profile": [C.c_void_p, C.POINTER(mm_profile_entry), C.POINTER(C.c_int)],
     "mm_debug_inject": [C.c_void_p, C.c_int],
@@ -302,6 +319,57 @@ def mm_batch_autotune(ctx, cache_path: str | None = None):
     _check(load().mm_batch_autotune(ctx, cache_path.encode() if cache_path else None, C.byref(nt), C.byref(blocks)),
            ctx)
     return nt.value, blocks.value
+
+
+SURROGATE_NPARAMS = 56099
+
+
+def mm_surrogate_train(ctx, cfg: mm_train_cfg) -> float:
+    loss = C.c_double(0.0)
+    _check(load().mm_surrogate_train(ctx, C.byref(cfg), C.byref(loss)), ctx)
+    return loss.value
+
+
+def mm_surrogate_set(ctx, k: int, tol: float = 1e-3):
+    _check(load().mm_surrogate_set(ctx, int(k), float(tol)), ctx)
+
+
+def mm_surrogate_get_stats(ctx):
+    s = mm_surrogate_stats()
+    _check(load().mm_surrogate_get_stats(ctx, C.byref(s)), ctx)
+    return {k: getattr(s, k) for k, _ in mm_surrogate_stats._fields_}
+
+
+def mm_surrogate_weights(ctx, set_params=None, c_in=None):
+    """Returns (params, c_in); set_params (56099 values) replaces them first."""
+    get = np.zeros(SURROGATE_NPARAMS)
+    st = _f64(set_params, SURROGATE_NPARAMS) if set_params is not None else None
+    ci = C.c_double(c_in if c_in is not None else 1.0)
+    _check(load().mm_surrogate_weights(ctx, _dptr(get), _dptr(st) if st is not None else None, SURROGATE_NPARAMS,
+                                       C.byref(ci) if (c_in is not None or st is None) else None), ctx)
+    return get, ci.value
+
+
+def mm_surrogate_forward(ctx, x, path: int = 0):
+    x = _f64(x)
+    B, _, H, W = x.shape
+    y = np.zeros((B, 3, H, W))
+    _check(load().mm_surrogate_forward(ctx, B, H, W, _dptr(x), _dptr(y), path), ctx)
+    return y
+
+
+def mm_surrogate_grad(ctx, x, t):
+    x = _f64(x)
+    t = _f64(t)
+    B, _, H, W = x.shape
+    loss = C.c_double(0.0)
+    g = np.zeros(SURROGATE_NPARAMS)
+    _check(load().mm_surrogate_grad(ctx, B, H, W, _dptr(x), _dptr(t), C.byref(loss), _dptr(g)), ctx)
+    return loss.value, g
+
+
+def make_train_cfg(n_snapshots=24, snap_every=4, max_gap=6, crop=128, batch=16, steps=1000, lr=1e-3, seed=4):
+    return mm_train_cfg(n_snapshots, snap_every, max_gap, crop, batch, steps, lr, seed)
 
 
 def mm_set_profiling(ctx, on: bool):

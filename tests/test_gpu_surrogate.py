@@ -1,0 +1,130 @@
+"""GPU checks of the learned demag surrogate (the benchmark's own addition;
+the paper has no learned part): the tensor-core (tcgen05) forward pass
+against the SIMT kernels and against the FP64 oracle network evaluated with
+the same BF16 rounding points; the backward pass against the oracle's
+gradients (themselves pinned by finite differences); training on pairs the
+exact FFT demag generates; surrogate-accelerated stepping with the exact
+demag as monitor and fallback.
+
+Tolerances: relative L2 error 1e-2 (BF16 operands, 8-bit mantissa)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_util import make_ctx, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _params_from_flat(flat):
+    from oracle import cnn
+    shapes = [(32, 3), (32, 32), (32, 32), (3, 32)]
+    out, o = [], 0
+    for co, ci in shapes:
+        n = co * ci * 25
+        w = flat[o:o + n].reshape(co, ci, 5, 5)
+        o += n
+        b = flat[o:o + co]
+        o += co
+        out.append({"w": cnn.bf16(w), "b": b.astype(np.float32).astype(np.float64)})
+    return out
+
+
+def _oracle_forward_bf16(params, x):
+    """Oracle network with activations rounded to bf16 where the kernels store them."""
+    from oracle import cnn
+    h = cnn.bf16(x)
+    for li, P in enumerate(params):
+        z = cnn.conv2d(h, P["w"], P["b"])
+        h = cnn.bf16(np.maximum(z, 0.0)) if li < 3 else z
+    return h
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _ctx(mm, n=64):
+    grid = W.Grid(n, n, 1, 2e-9, 2e-9, 1e-9)
+    mat = W.Material(Ms=5.8e5, A=1.5e-11, alpha=0.3, Ku1=8e5, u=(0, 0, 1), D=3.5e-3)
+    return make_ctx(mm, grid, mat, precision=32, demag=True, B=(0, 0, 0.2), rtol=1e-5), grid
+
+
+def test_tensor_core_forward_matches_simt_and_oracle():
+    mm = need_gpu()
+    from oracle import cnn
+    ctx, _ = _ctx(mm)
+    try:
+        rng = np.random.default_rng(0)
+        flat = np.concatenate([np.concatenate([P["w"].ravel(), P["b"] + rng.normal(0, 0.05, P["b"].shape)])
+                               for P in cnn.init_params(seed=3)])
+        mm.mm_surrogate_weights(ctx, flat, c_in=1.0)
+        for (B, H, Wd) in [(2, 20, 150), (1, 7, 33), (3, 64, 128)]:
+            x = rng.normal(size=(B, 3, H, Wd))
+            y_tc = mm.mm_surrogate_forward(ctx, x, path=0)
+            y_simt = mm.mm_surrogate_forward(ctx, x, path=1)
+            y_or = _oracle_forward_bf16(_params_from_flat(flat), x)
+            assert _rel(y_tc, y_simt) < 1e-2, _rel(y_tc, y_simt)
+            assert _rel(y_tc, y_or) < 1e-2, _rel(y_tc, y_or)
+    finally:
+        mm.mm_destroy(ctx)
+
+
+def test_gradients_match_oracle():
+    mm = need_gpu()
+    from oracle import cnn
+    ctx, _ = _ctx(mm)
+    try:
+        rng = np.random.default_rng(1)
+        flat = np.concatenate([np.concatenate([P["w"].ravel(), rng.normal(0, 0.05, P["b"].shape)])
+                               for P in cnn.init_params(seed=5)])
+        mm.mm_surrogate_weights(ctx, flat, c_in=1.0)
+        x = rng.normal(size=(2, 3, 24, 40))
+        t = rng.normal(size=(2, 3, 24, 40))
+        loss, g = mm.mm_surrogate_grad(ctx, x, t)
+        params = _params_from_flat(flat)
+        xb = cnn.bf16(x)
+        y, cache = cnn.forward(params, xb)
+        L, dy = cnn.mse(y, t)
+        grads, _ = cnn.backward(params, cache, dy)
+        assert abs(loss - L) <= 2e-2 * L
+        gflat = np.concatenate([np.concatenate([G["w"].ravel(), G["b"]]) for G in grads])
+        o = 0
+        for li, (co, ci) in enumerate([(32, 3), (32, 32), (32, 32), (3, 32)]):
+            n = co * ci * 25 + co
+            assert _rel(g[o:o + n], gflat[o:o + n]) < 5e-2, (li, _rel(g[o:o + n], gflat[o:o + n]))
+            o += n
+    finally:
+        mm.mm_destroy(ctx)
+
+
+def test_training_and_surrogate_stepping():
+    mm = need_gpu()
+    ctx, grid = _ctx(mm, n=128)
+    try:
+        m0 = W.m_skyrmion_lattice(grid, seed=4, spacing=40e-9, radius=8e-9)
+        mm.mm_set_m(ctx, 0, m0)
+        mm.mm_step(ctx, 30)                     # leave the initial transient
+        m_start = mm.mm_get_m(ctx, 0, m0.shape)
+        cfg = mm.make_train_cfg(n_snapshots=16, snap_every=2, max_gap=4, crop=64, batch=8, steps=400, lr=2e-3, seed=7)
+        loss = mm.mm_surrogate_train(ctx, cfg)
+        assert np.isfinite(loss)
+        assert np.array_equal(mm.mm_get_m(ctx, 0, m0.shape), m_start)      # training restores the state
+        # exact-only reference run
+        blob = mm.mm_get_state(ctx)
+        mm.mm_step(ctx, 40)
+        m_exact = mm.mm_get_m(ctx, 0, m0.shape)
+        mm.mm_set_state(ctx, blob)
+        mm.mm_surrogate_set(ctx, 5, 1e-2)
+        mm.mm_step(ctx, 40)
+        st = mm.mm_surrogate_get_stats(ctx)
+        m_surr = mm.mm_get_m(ctx, 0, m0.shape)
+        assert st["refreshes"] >= 1
+        if not st["fallback"]:
+            assert st["surrogate_evals"] > st["refreshes"]
+            assert st["last_error"] <= 1e-2
+            assert np.abs(m_surr - m_exact).max() < 5e-2
+        mm.mm_surrogate_set(ctx, 0, 1e-3)       # off again: exact stepping continues
+        mm.mm_step(ctx, 2)
+    finally:
+        mm.mm_destroy(ctx)
