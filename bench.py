@@ -180,6 +180,155 @@ def run_reference(args):
     return 0
 
 
+def _timed(stream, fn):
+    """Device time (ms) of fn() on `stream`, synchronised on both sides."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def fp32_error_vs_fp64(mm, w, m0, n_steps=20, dt=2e-14):
+    """max|m_fp32 - m_fp64| after n fixed RK45 steps from the same state: the
+    FP64 GPU path is the stand-in for the FP64 oracle here (the parity tests
+    hold it to the oracle within 1e-11)."""
+    g = w.grid
+    M = mm.Material(w.mat.Ms, w.mat.A, w.mat.alpha, w.mat.Ku1, w.mat.u, w.mat.D)
+    out = {}
+    for prec in (32, 64):
+        cfg = mm.make_config(precision=prec, integrator=mm.MM_RK45, demag=mm.MM_DEMAG_EXACT, dt=dt, rtol=w.rtol)
+        c = mm.mm_create(mm.make_grid(g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), M.s, cfg)
+        mm.mm_set_m(c, 0, m0)
+        mm.mm_step_dt(c, np.full(n_steps, dt))
+        out[prec] = mm.mm_get_m(c, 0, m0.shape)
+        mm.mm_destroy(c)
+    return float(np.abs(out[32] - out[64]).max())
+
+
+def variant_batched(mm, stream, steps):
+    """1024 finite-temperature replicas of uneven sizes, FP32 Heun, one
+    persistent launch per stage, graph-captured, autotuned launch shape."""
+    import torch
+    R = 1024
+    sizes = W.replica_sizes(R, seed=3)
+    J = W.replica_currents(R)
+    mat = W.Material(Ms=1.1e6, A=2e-11, alpha=0.01, Ku1=9e5, u=(0.0, 0.0, 1.0))
+    M = mm.Material(mat.Ms, mat.A, mat.alpha, mat.Ku1, mat.u, mat.D)
+    grids = [mm.make_grid(n, n, 1, 2e-9, 2e-9, 1e-9) for n in sizes]
+    base_seed = 3
+    cfg = mm.make_config(precision=32, integrator=mm.MM_HEUN, demag=mm.MM_DEMAG_EXACT, dt=1e-14, T=300.0,
+                         seed=base_seed)
+    ctx = mm.mm_create_batch(grids, M.s, cfg, None)
+    mm.mm_set_stream(ctx, stream.cuda_stream)
+    tq = mm.make_torque(mm.MM_TORQUE_SOT, p=(0, 1, 0), theta_SH=0.1)
+    mm.mm_set_torque(ctx, tq, J)
+    m0 = []
+    for r, n in enumerate(sizes):
+        m = W.m_perp(W.Grid(n, n, 1, 2e-9, 2e-9, 1e-9), seed=1000 + r, tilt=0.05)
+        mm.mm_set_m(ctx, r, m)
+        m0.append(m)
+    t_tune = time.perf_counter()
+    nt, blocks = mm.mm_batch_autotune(ctx, None)
+    t_tune = time.perf_counter() - t_tune
+    mm.mm_step(ctx, 3)
+    s0 = mm.mm_get_stats(ctx)
+    ms = _timed(stream, lambda: mm.mm_step(ctx, steps))
+    s1 = mm.mm_get_stats(ctx)
+    n_acc = s1["accepted"] - s0["accepted"]
+    cells = int(sum(n * n for n in sizes))
+    # FP32 batch vs FP64 single-instance runs of three replicas (same Philox key,
+    # same current) over the 3 + steps steps the batch has taken
+    n_total = 3 + steps
+    checks = sorted({0, int(np.argmin(sizes)), int(np.argmax(sizes))})
+    errs = []
+    for r in checks:
+        n = sizes[r]
+        c64 = mm.make_config(precision=64, integrator=mm.MM_HEUN, demag=mm.MM_DEMAG_EXACT, dt=1e-14, T=300.0,
+                             seed=base_seed + r)
+        s = mm.mm_create(mm.make_grid(n, n, 1, 2e-9, 2e-9, 1e-9), M.s, c64)
+        mm.mm_set_m(s, 0, m0[r])
+        mm.mm_set_torque(s, tq, J[r:r + 1])
+        mm.mm_step(s, n_total)
+        shape = m0[r].shape
+        errs.append(float(np.abs(mm.mm_get_m(ctx, r, shape) - mm.mm_get_m(s, 0, shape)).max()))
+        mm.mm_destroy(s)
+    mm.mm_destroy(ctx)
+    torch.cuda.synchronize()
+    return {"workload": "1024 perpendicular free layers, sizes {32,48,64,96,128}^2 x 1 of 2x2x1 nm, T=300 K, "
+                        "damping-like SOT J in [1e11,3e11] A/m^2, exact demag, FP32 Heun dt=1e-14 s",
+            "value": cells * n_acc / (ms * 1e-3), "unit": UNIT, "cells": cells, "replicas": R,
+            "steps": n_acc, "ms_per_step": ms / max(1, n_acc), "launch_shape": {"threads": nt, "ctas": blocks},
+            "autotune_s": round(t_tune, 2),
+            "error_vs_fp64": {"max_abs_dm": max(errs), "after_steps": n_total, "replicas_checked": checks,
+                              "against": "FP64 single-instance GPU runs with the same Philox key"}}
+
+
+def variant_surrogate(mm, stream, steps, train_steps=600):
+    """512x512x1 skyrmion-lattice film, FP32 RK45: exact FFT demag against the
+    BF16 CNN surrogate refreshed exactly every k attempted steps."""
+    import torch
+    w = W.skyrmion_512()
+    g = w.grid
+    M = mm.Material(w.mat.Ms, w.mat.A, w.mat.alpha, w.mat.Ku1, w.mat.u, w.mat.D)
+    cfg = mm.make_config(precision=32, integrator=mm.MM_RK45, demag=mm.MM_DEMAG_EXACT, dt=1e-13, rtol=w.rtol)
+    ctx = mm.mm_create(mm.make_grid(g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), M.s, cfg)
+    mm.mm_set_stream(ctx, stream.cuda_stream)
+    mm.mm_set_field(ctx, 0, w.B_ext)
+    m0 = W.m_skyrmion_lattice(g, seed=w.seed, spacing=40e-9, radius=8e-9)
+    mm.mm_set_m(ctx, 0, m0)
+    mm.mm_step(ctx, 30)                          # leave the initial transient
+    tcfg = mm.make_train_cfg(n_snapshots=24, snap_every=4, max_gap=6, crop=128, batch=16, steps=train_steps,
+                             lr=1e-3, seed=4)
+    t_train = time.perf_counter()
+    loss = mm.mm_surrogate_train(ctx, tcfg)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t_train
+    blob = mm.mm_get_state(ctx)
+    t0 = mm.mm_get_time(ctx)[0]
+
+    def run(k, tol):
+        mm.mm_set_state(ctx, blob)
+        mm.mm_surrogate_set(ctx, k, tol)
+        s0 = mm.mm_get_stats(ctx)
+        ms = _timed(stream, lambda: mm.mm_step(ctx, steps))
+        s1 = mm.mm_get_stats(ctx)
+        n_acc = s1["accepted"] - s0["accepted"]
+        t1 = mm.mm_get_time(ctx)[0]
+        st = mm.mm_surrogate_get_stats(ctx) if k else None
+        m1 = mm.mm_get_m(ctx, 0, m0.shape)
+        mm.mm_surrogate_set(ctx, 0, tol)
+        return {"value": g.n * n_acc / (ms * 1e-3), "steps": n_acc, "ms_per_step": ms / max(1, n_acc),
+                "t_sim": t1 - t0, "stats": st, "m": m1}
+
+    exact = run(0, 1e-3)
+    # exact reference at each surrogate run's end time (RK45 step sizes differ)
+    out = {"workload": "512x512x1 skyrmion-lattice film of 2x2x1 nm, Ms 5.8e5, A 1.5e-11, Ku 8e5, D 3.5e-3, "
+                       "alpha 0.3, Bz 0.2 T, FP32 RK45 rtol 1e-6",
+           "exact": {k: v for k, v in exact.items() if k not in ("m", "stats")},
+           "train": {"pairs_from_snapshots": 24, "optimiser_steps": train_steps, "final_loss": loss,
+                     "seconds": round(t_train, 2)}, "tol": 1e-3, "k": {}}
+    for k in (5, 10, 20):
+        r = run(k, 1e-3)
+        mm.mm_set_state(ctx, blob)
+        mm.mm_run(ctx, t0 + r["t_sim"])
+        m_ref = mm.mm_get_m(ctx, 0, m0.shape)
+        st = r["stats"]
+        out["k"][str(k)] = {"value": r["value"], "speedup_vs_exact": r["value"] / exact["value"],
+                            "steps": r["steps"], "ms_per_step": r["ms_per_step"],
+                            "max_abs_dm_vs_exact_run": float(np.abs(r["m"] - m_ref).max()),
+                            "fallback": bool(st["fallback"]), "field_error_last": st["last_error"],
+                            "field_error_max": st["max_error"], "exact_evals": st["exact_evals"],
+                            "surrogate_evals": st["surrogate_evals"]}
+    out["unit"] = UNIT
+    mm.mm_destroy(ctx)
+    torch.cuda.synchronize()
+    return out
+
+
 def run_gpu(args):
     import torch
 
@@ -291,6 +440,18 @@ def run_gpu(args):
                 "d2h_bytes_per_step": 3 * g.n * 4, "steps": k_e2e},
     }
     mm.mm_destroy(ctx)
+    if not args.no_variants:
+        m0_err = W.m_random_sphere(g, seed=2)
+        line["error_vs_fp64"] = {"max_abs_dm": fp32_error_vs_fp64(mm, w, m0_err), "after_steps": 20,
+                                 "dt_s": 2e-14, "against": "FP64 GPU path on the same steps (held to the "
+                                 "FP64 oracle within 1e-11 by the parity tests)"}
+        line["variants"] = {}
+        for name, fn in (("batched", lambda: variant_batched(mm, stream, args.batch_steps)),
+                         ("surrogate", lambda: variant_surrogate(mm, stream, args.surrogate_steps))):
+            try:
+                line["variants"][name] = fn()
+            except Exception as e:  # a failed variant is reported, the headline line still prints
+                line["variants"][name] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0:
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
@@ -308,6 +469,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", default="", help="nx,ny,nz: a smaller case of the same workload (profiling)")
+    ap.add_argument("--no-variants", action="store_true", help="skip the batched and surrogate lines")
+    ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--surrogate-steps", type=int, default=100)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

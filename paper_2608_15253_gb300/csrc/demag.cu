@@ -22,6 +22,7 @@
 #include "common.cuh"
 #include "ctx.h"
 #include "fft_ct.cuh"
+#include "fft_direct.cuh"
 #include "fft_rt.cuh"
 
 namespace mm {
@@ -141,6 +142,169 @@ __global__ void __launch_bounds__(256) fft_x_c2r_kernel(XArgs<T> a) {
     }
 }
 
+// FP32 X passes with the first (R2C) or first and last (C2R) Stockham pass
+// working straight between global memory and registers.  Rows per CTA are a
+// compile-time constant (the same rule the host uses for the generic path).
+__host__ __device__ constexpr int x_rows_per_cta(int Lh) {
+    return (kMaxV * 256 / Lh) < 1 ? 1 : (kMaxV * 256 / Lh) > 16 ? 16 : (kMaxV * 256 / Lh);
+}
+
+template <int LT>
+__global__ void __launch_bounds__(256) fft_x_r2c_direct_kernel(XArgs<float> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* sm = reinterpret_cast<float2*>(smem_raw);
+    constexpr int NT = 256, LP = LT + 1, RPC = x_rows_per_cta(LT);
+    constexpr int R0 = ct_radix(LT, 0), NB0 = LT / R0;
+    constexpr int MAXB = (RPC * NB0 + NT - 1) / NT;
+    const int r0 = blockIdx.x * RPC;
+    const int nl = min(RPC, a.rows - r0);
+    const int nin = (a.nx + 1) / 2;
+    const int total = nl * NB0;
+    const bool vec2 = (a.nx % 2 == 0) && (a.in_pitch % 2 == 0);
+    // packed complex z[n] = Ms (x[2n] + i x[2n+1]), loaded into registers
+    float2 v[MAXB][R0];
+#pragma unroll
+    for (int i = 0; i < MAXB; ++i) {
+        const int b = threadIdx.x + i * NT;
+        if (b < total) {
+            const int l = b / NB0, j = b % NB0;
+            const long long g0 = (long long)(r0 + l) * a.in_pitch;
+#pragma unroll
+            for (int t = 0; t < R0; ++t) {
+                const int n = j + t * NB0;
+                float2 z = make_float2(0.f, 0.f);
+                if (n < nin) {
+                    const long long q = g0 + 2 * n;
+                    const bool has_y = 2 * n + 1 < a.nx;
+                    if (vec2) z = *reinterpret_cast<const float2*>(a.in + q);
+                    else {
+                        z.x = a.in[q];
+                        z.y = has_y ? a.in[q + 1] : 0.f;
+                    }
+                    if (a.region) {
+                        z.x *= a.lut[a.region[q % a.cells_per_comp]].Ms;
+                        z.y = has_y ? z.y * a.lut[a.region[(q + 1) % a.cells_per_comp]].Ms : 0.f;
+                    } else {
+                        z.x *= a.ms_uniform;
+                        z.y *= a.ms_uniform;
+                    }
+                }
+                v[i][t] = z;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < MAXB; ++i) {
+        const int b = threadIdx.x + i * NT;
+        if (b < total) {
+            const int l = b / NB0, j = b % NB0;
+            dft_ct<float, 1, R0>(v[i]);
+#pragma unroll
+            for (int t = 0; t < R0; ++t) sm[l * LP + j * R0 + t] = v[i][t];
+        }
+    }
+    __syncthreads();
+    ct_fft<float, 1, LT, LP, NT, kMaxV, 1>(sm, nl, LT, a.tw, 2);
+    // split: X[k] = (Z[k] + conj Z[M-k])/2 - i/2 W^k (Z[k] - conj Z[M-k])
+    constexpr int M = LT, Kx = LT + 1;
+    for (int l = 0; l < nl; ++l) {
+        float2* out = a.spec + spec_row(a, r0 + l) * a.Wk;
+        for (int k = threadIdx.x; k < Kx; k += NT) {
+            const float2 zk = sm[l * LP + (k == M ? 0 : k)];
+            const float2 zc = cconj<float>(sm[l * LP + (k == 0 ? 0 : M - k)]);
+            const float2 E = cscale<float>(cadd<float>(zk, zc), 0.5f);
+            const float2 O = cscale<float>(mul_mi<float, 1>(csub<float>(zk, zc)), 0.5f);
+            const float2 w = __ldg(&a.tw[k]);
+            out[k] = cadd<float>(E, cmul<float>(w, O));
+        }
+    }
+}
+
+template <int LT>
+__global__ void __launch_bounds__(256) fft_x_c2r_direct_kernel(XArgs<float> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* sm = reinterpret_cast<float2*>(smem_raw);
+    constexpr int NT = 256, LP = LT + 1, RPC = x_rows_per_cta(LT), M = LT, Kx = LT + 1;
+    constexpr int NP = ct_npass(LT);
+    static_assert(NP >= 2, "first and last pass must differ");
+    const int r0 = blockIdx.x * RPC;
+    const int nl = min(RPC, a.rows - r0);
+    for (int l = 0; l < nl; ++l) {
+        const float2* in = a.spec + spec_row(a, r0 + l) * a.Wk;
+        for (int k = threadIdx.x; k < Kx; k += NT) sm[l * LP + k] = in[k];
+    }
+    __syncthreads();
+    // first pass, fed by the rebuild Z'[k] = (X[k] + conj X[M-k]) + i (X[k] - conj X[M-k]) conj(W^k)
+    {
+        constexpr int R0 = ct_radix(LT, 0), NB0 = LT / R0;
+        constexpr int MAXB = (RPC * NB0 + NT - 1) / NT;
+        const int total = nl * NB0;
+        float2 v[MAXB][R0];
+#pragma unroll
+        for (int i = 0; i < MAXB; ++i) {
+            const int b = threadIdx.x + i * NT;
+            if (b < total) {
+                const int l = b / NB0, j = b % NB0;
+#pragma unroll
+                for (int t = 0; t < R0; ++t) {
+                    const int k = j + t * NB0;
+                    const float2 xk = sm[l * LP + k];
+                    const float2 xc = cconj<float>(sm[l * LP + M - k]);
+                    const float2 w = __ldg(&a.tw[k]);
+                    const float2 E = cadd<float>(xk, xc);
+                    const float2 O = cmulc<float>(csub<float>(xk, xc), w);
+                    v[i][t] = cadd<float>(E, mul_mi<float, -1>(O));
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < MAXB; ++i) {
+            const int b = threadIdx.x + i * NT;
+            if (b < total) {
+                const int l = b / NB0, j = b % NB0;
+                dft_ct<float, -1, R0>(v[i]);
+#pragma unroll
+                for (int t = 0; t < R0; ++t) sm[l * LP + j * R0 + t] = v[i][t];
+            }
+        }
+        __syncthreads();
+    }
+    ct_fft<float, -1, LT, LP, NT, kMaxV, 1, NP - 1>(sm, nl, LT, a.tw, 2);
+    // last pass straight to the real rows: z[n] -> (x[2n], x[2n+1])
+    {
+        constexpr int P = NP - 1, R = ct_radix(LT, P), NS = ct_ns(LT, P), NB = LT / R;
+        static_assert(NB == NS, "last pass writes natural order");
+        constexpr int MAXB = (RPC * NB + NT - 1) / NT;
+        const int total = nl * NB;
+        const bool vec2 = (a.nx % 2 == 0) && (a.in_pitch % 2 == 0);
+#pragma unroll
+        for (int i = 0; i < MAXB; ++i) {
+            const int b = threadIdx.x + i * NT;
+            if (b < total) {
+                const int l = b / NB, j = b % NB;
+                float2 v[R];
+#pragma unroll
+                for (int t = 0; t < R; ++t) v[t] = sm[l * LP + j + t * NB];
+#pragma unroll
+                for (int t = 1; t < R; ++t) v[t] = cmulc<float>(v[t], __ldg(&a.tw[(t * j) * 2]));
+                dft_ct<float, -1, R>(v);
+                float* out = a.out_real + (long long)(r0 + l) * a.in_pitch;
+#pragma unroll
+                for (int t = 0; t < R; ++t) {
+                    const int n = j + t * NS;
+                    if (2 * n + 1 < a.nx) {
+                        if (vec2) *reinterpret_cast<float2*>(out + 2 * n) = v[t];
+                        else { out[2 * n] = v[t].x; out[2 * n + 1] = v[t].y; }
+                    } else if (2 * n < a.nx) {
+                        out[2 * n] = v[t].x;
+                    }
+                }
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Column passes (strided axes), optionally with the tensor multiply
 // ---------------------------------------------------------------------------
@@ -244,6 +408,115 @@ __global__ void __launch_bounds__(512) fft_col_kernel(ColArgs<T> a) {
             const int kxl = e & tkm, pt = e >> tks;
             if (kx0 + kxl < a.Kx) dst[pt * a.line_stride + kxl] = sm[((c << tks) + kxl) * pitch + pt];
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 3-D fast paths
+// ---------------------------------------------------------------------------
+// Y passes: TK = 16 columns per CTA taken from the flattened (component, z,
+// kx) column list, so no CTA is left with a ragged handful of columns; the
+// first Stockham pass reads global memory straight into registers and the
+// last one writes its outputs straight back (128-byte row segments).
+template <typename T>
+struct YArgs {
+    cplx<T>* base;        // spectrum [3][nz][Py][Wk]
+    long long plane;      // Py * Wk: between consecutive (component, z) planes
+    int Kx, Wk;
+    int ncols;            // 3 * nz * Kx
+    int n_in, n_out;
+    const cplx<T>* tw;    // exp(-2 pi i q / Py)
+};
+
+constexpr int kYTK = 16;
+__host__ __device__ constexpr int y_direct_threads(int L) { return L >= 512 ? 512 : 256; }
+
+template <typename T, int DIR, int L>
+__global__ void __launch_bounds__(y_direct_threads(L)) fft_y_direct_kernel(YArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw);
+    const int col = blockIdx.x * kYTK + (int)(threadIdx.x % kYTK);
+    long long gcol = -1;
+    if (col < a.ncols) {
+        const int q = col / a.Kx, kx = col - q * a.Kx;
+        gcol = (long long)q * a.plane + kx;
+    }
+    cd_fft<T, DIR, L, y_direct_threads(L), kYTK>(sm, a.base, a.base, gcol, a.Wk, a.n_in, a.n_out, a.tw);
+}
+
+// Middle (z) pass for Pz a power of two <= 32: one thread per (component,
+// column) keeps its whole z line in registers.  Forward by decimation in
+// frequency (bit-reversed spectrum), the three components exchanged once
+// through shared memory for H^ = K^ M^ (row c of the symmetric tensor), then
+// the inverse by decimation in time straight back to natural order; only the
+// nz un-padded outputs are stored.  Columns are the flattened (ky, kx)
+// positions of a z-plane, kZT per CTA, so loads are contiguous 256-byte runs.
+template <typename T>
+struct ZArgs {
+    cplx<T>* base;          // spectrum [3][nz][Py][Wk]
+    long long comp_stride;  // nz * Py * Wk
+    long long plane;        // Py * Wk: between consecutive z
+    int nz, Py, Kx, Wk;
+    const cplx<T>* tw;      // exp(-2 pi i q / Pz)
+    const T* khat;          // [6][Pz/2+1][Py/2+1][Wk]
+    long long kc_stride;    // per tensor component
+    long long kk_stride;    // per kz: (Py/2+1) * Wk
+};
+
+constexpr int kZT = 64;
+
+template <typename T, int L>
+__global__ void __launch_bounds__(3 * kZT, 2) fft_zconv_reg_kernel(ZArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<T>* tws = reinterpret_cast<cplx<T>*>(smem_raw);   // [L]
+    cplx<T>* sm = tws + L;                                  // [3][L][kZT]
+    constexpr int LOG = ilog2_c(L);
+    const int tx = threadIdx.x % kZT, c = threadIdx.x / kZT;
+    if (threadIdx.x < L) tws[threadIdx.x] = a.tw[threadIdx.x];
+    const long long p = (long long)blockIdx.x * kZT + tx;
+    const int ky = (int)(p / a.Wk), kx = (int)(p - (long long)ky * a.Wk);
+    const bool valid = ky < a.Py && kx < a.Kx;
+    cplx<T>* col = a.base + c * a.comp_stride + (valid ? p : 0);
+    cplx<T> v[L];
+#pragma unroll
+    for (int z = 0; z < L; ++z) v[z] = (valid && z < a.nz) ? col[z * a.plane] : mkc<T>(0, 0);
+    __syncthreads();
+    reg_dif<T, L>(v, tws);
+#pragma unroll
+    for (int i = 0; i < L; ++i) sm[(c * L + i) * kZT + tx] = v[i];
+    __syncthreads();
+    // row c of the tensor: xx yy zz xy xz yz = 0..5; xy is odd in ky, xz odd
+    // in kz, yz odd in both (the stored half spectra hold ky, kz <= P/2)
+    const int i0 = c == 0 ? 0 : c == 1 ? 3 : 4;
+    const int i1 = c == 0 ? 3 : c == 1 ? 1 : 5;
+    const int i2 = c == 0 ? 4 : c == 1 ? 5 : 2;
+    const bool yfold = ky > a.Py / 2;
+    const int kyf = yfold ? a.Py - ky : ky;
+    const T sy = yfold ? (T)-1 : (T)1;
+    const T y0 = c == 1 ? sy : (T)1, y1 = c == 1 ? (T)1 : sy, y2 = c == 1 ? sy : (T)1;
+    const bool zc2 = c == 2;
+    const T* K = a.khat + (valid ? (long long)kyf * a.Wk + kx : 0);
+    const T* K0 = K + i0 * a.kc_stride;
+    const T* K1 = K + i1 * a.kc_stride;
+    const T* K2 = K + i2 * a.kc_stride;
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        const int kz = bitrev_c(i, LOG);
+        const int kzf = kz <= L / 2 ? kz : L - kz;
+        const T sz = kz <= L / 2 ? (T)1 : (T)-1;
+        const T k0 = __ldg(K0 + kzf * a.kk_stride) * y0 * (zc2 ? sz : (T)1);
+        const T k1 = __ldg(K1 + kzf * a.kk_stride) * y1 * (zc2 ? sz : (T)1);
+        const T k2 = __ldg(K2 + kzf * a.kk_stride) * y2 * (zc2 ? (T)1 : sz);
+        const cplx<T> m0 = sm[(0 * L + i) * kZT + tx];
+        const cplx<T> m1 = sm[(1 * L + i) * kZT + tx];
+        const cplx<T> m2 = sm[(2 * L + i) * kZT + tx];
+        v[i] = mkc<T>(k0 * m0.x + k1 * m1.x + k2 * m2.x, k0 * m0.y + k1 * m1.y + k2 * m2.y);
+    }
+    reg_dit_inv<T, L>(v, tws);
+    if (valid) {
+#pragma unroll
+        for (int z = 0; z < L; ++z)
+            if (z < a.nz) col[z * a.plane] = v[z];
     }
 }
 
@@ -484,7 +757,7 @@ template <typename T>
 static XKern<T> x_kernel(bool fwd, int Lh) {
     if constexpr (sizeof(T) == 4) {
         switch (Lh) {
-#define MM_CASE(n) case n: return fwd ? fft_x_r2c_kernel<T, n> : fft_x_c2r_kernel<T, n>;
+#define MM_CASE(n) case n: return fwd ? fft_x_r2c_direct_kernel<n> : fft_x_c2r_direct_kernel<n>;
             MM_CT_LENGTHS(MM_CASE)
 #undef MM_CASE
             default: break;
@@ -505,6 +778,31 @@ static CKern<T> col_kernel(int L) {
     }
     return fft_col_kernel<T, MODE, 0>;
 }
+
+using YKern = void (*)(YArgs<float>);
+using ZKern = void (*)(ZArgs<float>);
+
+static YKern y_direct_kernel(bool fwd, int L) {
+    switch (L) {
+#define MM_CASE(n) case n: return fwd ? fft_y_direct_kernel<float, 1, n> : fft_y_direct_kernel<float, -1, n>;
+        MM_CT_LENGTHS(MM_CASE)
+#undef MM_CASE
+        default: return nullptr;
+    }
+}
+
+static ZKern zconv_reg_kernel(int L) {
+    switch (L) {
+        case 4: return fft_zconv_reg_kernel<float, 4>;
+        case 8: return fft_zconv_reg_kernel<float, 8>;
+        case 16: return fft_zconv_reg_kernel<float, 16>;
+        case 32: return fft_zconv_reg_kernel<float, 32>;
+        default: return nullptr;
+    }
+}
+
+static size_t y_direct_smem(int L) { return (size_t)L * kYTK * sizeof(cplx<float>); }
+static size_t zconv_reg_smem(int L) { return (size_t)(L + 3 * L * kZT) * sizeof(cplx<float>); }
 
 template <typename T>
 static void launch_x(mm_ctx* c, bool forward, const T* in, T* out_real, cplx<T>* spec, int rows,
@@ -554,6 +852,19 @@ static void launch_col(mm_ctx* c, ColArgs<T> a, int n_other, const char* name, d
     col_kernel<T, MODE>(a.L)<<<grid, thr, smem, c->stream>>>(a);
 }
 
+static void launch_y_direct(mm_ctx* c, bool fwd, cplx<float>* S, long long plane, int n_in, int n_out,
+                            const char* name, double bytes) {
+    const DemagPlan& d = c->dm;
+    YArgs<float> a{};
+    a.base = S; a.plane = plane; a.Kx = d.Kx; a.Wk = d.Wk;
+    a.ncols = 3 * c->grid.nz * d.Kx;
+    a.n_in = n_in; a.n_out = n_out;
+    a.tw = (const cplx<float>*)d.tw_y;
+    LaunchScope ls(c, name, bytes);
+    y_direct_kernel(fwd, d.Py)<<<(unsigned)((a.ncols + kYTK - 1) / kYTK), y_direct_threads(d.Py), y_direct_smem(d.Py),
+                                 c->stream>>>(a);
+}
+
 template <typename T>
 static void demag_apply_t(mm_ctx* c, const T* m, T* Hd) {
     DemagPlan& d = c->dm;
@@ -567,7 +878,12 @@ static void demag_apply_t(mm_ctx* c, const T* m, T* Hd) {
     // X forward: rows (c, z, y) of Ms*m
     launch_x<T>(c, true, m, nullptr, S, 3 * nz * ny, ny, d.PyA, nx, nx, d.Lh, (const cplx<T>*)d.tw_x, true, N);
     const bool three_d = nz > 1;
-    if (three_d && d.Py > 1) {
+    const bool fast_y = sizeof(T) == 4 && three_d && y_direct_kernel(true, d.Py) != nullptr;
+    const bool fast_z = sizeof(T) == 4 && three_d && zconv_reg_kernel(d.Pz) != nullptr;
+    if (three_d && d.Py > 1 && fast_y) {
+        launch_y_direct(c, true, (cplx<float>*)S, plane, ny, d.Py, "fft_y_fwd",
+                        3.0 * nz * d.Kx * (ny + d.Py) * cplxb);
+    } else if (three_d && d.Py > 1) {
         ColArgs<T> a{};
         a.base = S; a.comp_stride = comp; a.line_stride = d.Wk; a.other_stride = plane;
         a.nc = 3; a.Kx = d.Kx; a.L = d.Py; a.n_in = ny; a.n_out = d.Py;
@@ -581,7 +897,18 @@ static void demag_apply_t(mm_ctx* c, const T* m, T* Hd) {
         a.ncomp = d.ncomp;
         const long long Ky = d.Py / 2 + 1, Kz = d.Pz / 2 + 1;
         a.kc_stride = Kz * Ky * d.Wk;
-        if (three_d) {
+        if (three_d && fast_z) {
+            ZArgs<float> z{};
+            z.base = (cplx<float>*)S; z.comp_stride = comp; z.plane = plane;
+            z.nz = nz; z.Py = d.Py; z.Kx = d.Kx; z.Wk = d.Wk;
+            z.tw = (const cplx<float>*)d.tw_z;
+            z.khat = (const float*)d.khat;
+            z.kc_stride = a.kc_stride; z.kk_stride = Ky * d.Wk;
+            const long long cols = (long long)d.Py * d.Wk;
+            LaunchScope ls(c, "fft_conv",
+                           3.0 * d.Py * d.Kx * 2 * nz * cplxb + (double)d.ncomp * Kz * Ky * d.Kx * realb);
+            zconv_reg_kernel(d.Pz)<<<(unsigned)((cols + kZT - 1) / kZT), 3 * kZT, zconv_reg_smem(d.Pz), c->stream>>>(z);
+        } else if (three_d) {
             a.line_stride = plane; a.other_stride = d.Wk;
             a.L = d.Pz; a.n_in = nz; a.n_out = nz;
             a.tw = (const cplx<T>*)d.tw_z;
@@ -599,7 +926,10 @@ static void demag_apply_t(mm_ctx* c, const T* m, T* Hd) {
                              3.0 * d.Kx * 2 * ny * cplxb + (double)d.ncomp * Ky * d.Kx * realb);
         }
     }
-    if (three_d && d.Py > 1) {
+    if (three_d && d.Py > 1 && fast_y) {
+        launch_y_direct(c, false, (cplx<float>*)S, plane, d.Py, ny, "fft_y_inv",
+                        3.0 * nz * d.Kx * (ny + d.Py) * cplxb);
+    } else if (three_d && d.Py > 1) {
         ColArgs<T> a{};
         a.base = S; a.comp_stride = comp; a.line_stride = d.Wk; a.other_stride = plane;
         a.nc = 3; a.Kx = d.Kx; a.L = d.Py; a.n_in = d.Py; a.n_out = ny;
@@ -737,8 +1067,20 @@ static cudaError_t fft_attributes() {
     return e;
 }
 
+static cudaError_t fast_attributes() {
+    cudaError_t e = cudaSuccess;
+    for (int L : {16, 32, 48, 64, 96, 128, 192, 256, 512, 1024}) {
+        if (e == cudaSuccess) e = smem_attr(y_direct_kernel(true, L));
+        if (e == cudaSuccess) e = smem_attr(y_direct_kernel(false, L));
+    }
+    for (int L : {4, 8, 16, 32})
+        if (e == cudaSuccess) e = smem_attr(zconv_reg_kernel(L));
+    return e;
+}
+
 mm_status demag_setup(mm_ctx* c) {
     cudaError_t e = fft_attributes<float>();
+    if (e == cudaSuccess) e = fast_attributes();
     if (e == cudaSuccess) e = fft_attributes<double>();
     if (e != cudaSuccess) return cuda_check(c, e, "FFT kernel attributes");
     return c->prec == 32 ? demag_setup_t<float>(c) : demag_setup_t<double>(c);

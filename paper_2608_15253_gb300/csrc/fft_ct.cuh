@@ -8,7 +8,7 @@
 
 namespace mm {
 
-constexpr int ct_radix(int L, int p) {
+__host__ __device__ constexpr int ct_radix(int L, int p) {
     int n = L;
     for (int q = 0;; ++q) {
         int r = n % 8 == 0 ? 8 : n % 4 == 0 ? 4 : n % 2 == 0 ? 2 : n % 3 == 0 ? 3 : 1;
@@ -16,12 +16,12 @@ constexpr int ct_radix(int L, int p) {
         n /= r;
     }
 }
-constexpr int ct_npass(int L) {
+__host__ __device__ constexpr int ct_npass(int L) {
     int n = L, p = 0;
     while (n > 1) { n /= ct_radix(L, p); ++p; }
     return p;
 }
-constexpr int ct_ns(int L, int p) {
+__host__ __device__ constexpr int ct_ns(int L, int p) {
     int ns = 1;
     for (int q = 0; q < p; ++q) ns *= ct_radix(L, q);
     return ns;
@@ -113,13 +113,14 @@ __device__ __forceinline__ void ct_pass(cplx<T>* sm, int nl, int nin, const cplx
     __syncthreads();
 }
 
-template <typename T, int DIR, int L, int LP, int NT, int MAXV, int P = 0>
+// Passes P .. PEND-1 (PEND = -1: through the last pass).
+template <typename T, int DIR, int L, int LP, int NT, int MAXV, int P = 0, int PEND = -1>
 __device__ __forceinline__ void ct_fft(cplx<T>* sm, int nl, int nin, const cplx<T>* __restrict__ tw, int tws) {
-    if constexpr (P < ct_npass(L)) {
+    if constexpr (P < (PEND < 0 ? ct_npass(L) : PEND)) {
         constexpr int R = ct_radix(L, P);
         constexpr int NS = ct_ns(L, P);
         ct_pass<T, DIR, L, LP, R, NS, NT, (MAXV / R) * R>(sm, nl, P == 0 ? nin : L, tw, tws);
-        ct_fft<T, DIR, L, LP, NT, MAXV, P + 1>(sm, nl, nin, tw, tws);
+        ct_fft<T, DIR, L, LP, NT, MAXV, P + 1, PEND>(sm, nl, nin, tw, tws);
     }
 }
 

@@ -1,0 +1,149 @@
+// FFT building blocks that keep data in registers between global memory and
+// the transform, used by the FP32 demag passes of 3-D grids:
+//  * reg_dif / reg_dit: a whole power-of-two line in one thread's registers.
+//    The forward transform (decimation in frequency) leaves the spectrum in
+//    bit-reversed order and the inverse (decimation in time) takes it back
+//    in that order, so a pointwise product between them needs no reordering.
+//  * cd_pass: one Stockham pass over TK interleaved columns held in shared
+//    memory as [index][column]; its first pass may read straight from global
+//    memory and its last pass may write straight to global memory.
+#pragma once
+
+#include "common.cuh"
+#include "fft_ct.cuh"
+
+namespace mm {
+
+__host__ __device__ constexpr int ilog2_c(int n) {
+    int b = 0;
+    while ((1 << b) < n) ++b;
+    return b;
+}
+__host__ __device__ constexpr int bitrev_c(int i, int bits) {
+    int r = 0;
+    for (int b = 0; b < bits; ++b)
+        if ((i >> b) & 1) r |= 1 << (bits - 1 - b);
+    return r;
+}
+
+// In-register forward DFT of length L (a power of two), natural order in,
+// bit-reversed order out.  tw[q] = exp(-2 pi i q / L).  One template level
+// per stage so that every register index is a compile-time constant.
+template <typename T, int L, int S = 0>
+__device__ __forceinline__ void reg_dif(cplx<T> (&v)[L], const cplx<T>* tw) {
+    if constexpr ((L >> S) >= 2) {
+        constexpr int len = L >> S, h = len >> 1;
+#pragma unroll
+        for (int q = 0; q < L / 2; ++q) {
+            const int b = (q / h) * len, j = q % h;
+            const cplx<T> u = v[b + j], t = v[b + j + h];
+            v[b + j] = cadd<T>(u, t);
+            const cplx<T> d = csub<T>(u, t);
+            v[b + j + h] = j == 0 ? d : cmul<T>(d, tw[j * (L / len)]);
+        }
+        reg_dif<T, L, S + 1>(v, tw);
+    }
+}
+
+// In-register inverse DFT (unnormalised, exp(+2 pi i k n / L)), bit-reversed
+// order in, natural order out.
+template <typename T, int L, int S = 0>
+__device__ __forceinline__ void reg_dit_inv(cplx<T> (&v)[L], const cplx<T>* tw) {
+    if constexpr ((2 << S) <= L) {
+        constexpr int len = 2 << S, h = len >> 1;
+#pragma unroll
+        for (int q = 0; q < L / 2; ++q) {
+            const int b = (q / h) * len, j = q % h;
+            const cplx<T> u = v[b + j];
+            const cplx<T> t = j == 0 ? v[b + j + h] : cmulc<T>(v[b + j + h], tw[j * (L / len)]);
+            v[b + j] = cadd<T>(u, t);
+            v[b + j + h] = csub<T>(u, t);
+        }
+        reg_dit_inv<T, L, S + 1>(v, tw);
+    }
+}
+
+// Where a column pass reads its input from / writes its output to.
+enum { CD_SMEM = 0, CD_GLOBAL = 1 };
+
+// One Stockham pass (radix R, current sub-length NS) over TK columns of
+// length L.  Butterfly b of NT threads: column l = b % TK, butterfly j =
+// b / TK, so a warp touches consecutive columns (one contiguous row segment
+// in global memory, consecutive words in shared memory).  Shared layout:
+// element idx of column l at sm[idx * TK + l].  Global: element idx of
+// column l at g[l] + idx * gstride (g[l] < 0: the column is absent).
+// Reads at idx >= nin are zero; global writes at idx >= nout are dropped.
+// gin and gout may be the same buffer: every element a CTA writes was read
+// by the same CTA in its first pass.
+template <typename T, int DIR, int L, int R, int NS, int NT, int TK, int SRC, int DST>
+__device__ __forceinline__ void cd_pass(cplx<T>* sm, const cplx<T>* gin, cplx<T>* gout, long long gcol,
+                                        long long gstride, int nin, int nout, const cplx<T>* __restrict__ tw) {
+    constexpr int NB = L / R;
+    constexpr int SPAN = L / (NS * R);
+    constexpr int TOT = TK * NB;                 // butterflies in the pass
+    constexpr int NBT = (TOT + NT - 1) / NT;     // per thread
+    static_assert(NT % TK == 0, "a thread keeps one column");
+    const int l = threadIdx.x % TK;
+    cplx<T> v[NBT][R];
+#pragma unroll
+    for (int i = 0; i < NBT; ++i) {
+        const int b = threadIdx.x + i * NT;
+        if (TOT % NT == 0 || b < TOT) {
+            const int j = b / TK;
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                const int idx = j + t * NB;
+                if constexpr (SRC == CD_GLOBAL) {
+                    v[i][t] = (gcol >= 0 && idx < nin) ? gin[gcol + idx * gstride] : mkc<T>(0, 0);
+                } else {
+                    v[i][t] = sm[idx * TK + l];
+                }
+            }
+        }
+    }
+    if constexpr (SRC == CD_SMEM && DST == CD_SMEM) __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NBT; ++i) {
+        const int b = threadIdx.x + i * NT;
+        if (TOT % NT != 0 && b >= TOT) continue;
+        const int j = b / TK;
+        const int k = j % NS;
+        if constexpr (NS > 1) {
+#pragma unroll
+            for (int t = 1; t < R; ++t) {
+                const cplx<T> w = __ldg(&tw[t * k * SPAN]);
+                v[i][t] = DIR > 0 ? cmul<T>(v[i][t], w) : cmulc<T>(v[i][t], w);
+            }
+        }
+        dft_ct<T, DIR, R>(v[i]);
+        const int dst = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int idx = dst + t * NS;
+            if constexpr (DST == CD_GLOBAL) {
+                if (gcol >= 0 && idx < nout) gout[gcol + idx * gstride] = v[i][t];
+            } else {
+                sm[idx * TK + l] = v[i][t];
+            }
+        }
+    }
+    if constexpr (DST == CD_SMEM) __syncthreads();
+}
+
+// Whole column transform: global -> registers -> (shared passes) -> global.
+template <typename T, int DIR, int L, int NT, int TK, int P = 0>
+__device__ __forceinline__ void cd_fft(cplx<T>* sm, const cplx<T>* gin, cplx<T>* gout,
+                                       long long gcol, long long gstride, int nin, int nout,
+                                       const cplx<T>* __restrict__ tw) {
+    constexpr int NP = ct_npass(L);
+    if constexpr (P < NP) {
+        constexpr int R = ct_radix(L, P);
+        constexpr int NS = ct_ns(L, P);
+        constexpr int SRC = P == 0 ? CD_GLOBAL : CD_SMEM;
+        constexpr int DST = P == NP - 1 ? CD_GLOBAL : CD_SMEM;
+        cd_pass<T, DIR, L, R, NS, NT, TK, SRC, DST>(sm, gin, gout, gcol, gstride, nin, nout, tw);
+        cd_fft<T, DIR, L, NT, TK, P + 1>(sm, gin, gout, gcol, gstride, nin, nout, tw);
+    }
+}
+
+}  // namespace mm

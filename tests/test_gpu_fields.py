@@ -108,6 +108,12 @@ DEMAG_GRIDS = [
     W.Grid(1, 1, 1, 2e-9, 2e-9, 2e-9),
     W.Grid(48, 48, 1, 2e-9, 2e-9, 1e-9),
     W.Grid(32, 16, 8, 3e-9, 3e-9, 3e-9),
+    # FP32 3-D fast paths: padded y lengths 48 / 128 / 32 (direct column
+    # passes, ragged final CTA), padded z lengths 32 / 16 / 8 (z line in
+    # registers, ragged final column block)
+    W.Grid(40, 24, 16, 2e-9, 2e-9, 2e-9),
+    W.Grid(24, 64, 8, 2e-9, 2e-9, 1e-9),
+    W.Grid(13, 16, 4, 3e-9, 2e-9, 2e-9),
 ]
 
 
@@ -128,6 +134,26 @@ def test_demag_field_matches_oracle(prec, gi):
         H = mm.mm_get_heff(ctx, 0, m.shape, TERMS["demag"])
         tol = 1e-11 if prec == 64 else 5e-6
         assert rel_err(H, ref) < tol, rel_err(H, ref)
+    finally:
+        mm.mm_destroy(ctx)
+
+
+def test_demag_field_full_size_256x256x16():
+    """The benchmark's grid (256x256x16 cells of 2 nm, padded 512x512x32) in
+    FP32 against the FP64 oracle, every cell compared."""
+    mm = need_gpu()
+    from oracle.demag import demag_spectrum, h_demag
+    w = W.dmi_256x256x16()
+    grid = w.grid
+    ctx = make_ctx(mm, grid, w.mat, precision=32, demag=True)
+    try:
+        m = W.m_random_sphere(grid, seed=2)
+        mm.mm_set_m(ctx, 0, m)
+        m_dev = mm.mm_get_m(ctx, 0, m.shape)
+        p = oracle_problem(grid, w.mat)
+        ref = h_demag(m_dev, p, demag_spectrum(p.shape, p.d))
+        H = mm.mm_get_heff(ctx, 0, m.shape, TERMS["demag"])
+        assert rel_err(H, ref) < 5e-6, rel_err(H, ref)
     finally:
         mm.mm_destroy(ctx)
 

@@ -1,0 +1,118 @@
+"""Parity at the full sizes of the benchmark workloads.
+
+* 128x32x1 thin film, FP64 RK45 (rtol 1e-6) for the whole 0.5 ns: the GPU
+  replays the oracle's accepted step sequence; every cell compared.
+* 256x256x16 DMI film: FP32 and FP64 replays of the oracle's first accepted
+  RK45 steps from a random state; energy and topological charge of the
+  final state against the oracle's compensated sums.
+* 512x512x64 vortex (16.7 M cells, padded 1024x1024x128): too large for
+  the oracle to step, so the FP32 run is held to the FP64 GPU run (itself
+  held to the oracle at the smaller sizes) on the same steps, plus |m| = 1
+  and energy decay (alpha > 0, no applied field).
+
+Bars: FP64 max|dm| <= 1e-11, FP32 max|dm| <= 1e-5 (Methods, "Physics and
+discretization": LLG of Eq. 1 integrated by the Dormand-Prince pair)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_util import make_ctx, need_gpu, oracle_problem
+
+pytestmark = pytest.mark.gpu
+
+
+def _solver(w, m0, **kw):
+    from oracle.demag import demag_spectrum
+    from oracle.llg import Solver
+    p = oracle_problem(w.grid, w.mat, w.B_ext)
+    return Solver(p, m0, K_hat=demag_spectrum(p.shape, p.d), **kw), p
+
+
+def test_thin_film_full_run_fp64():
+    mm = need_gpu()
+    w = W.film_128x32()
+    m0 = W.m_uniform_perturbed(w.grid, seed=w.seed)
+    o, p = _solver(w, m0, dt=1e-14, rtol=w.rtol)
+    dts = []
+    while o.t < w.t_end:
+        dts.append(o.rk45_step())
+    ctx = make_ctx(mm, w.grid, w.mat, precision=64, demag=True, B=w.B_ext, dt=1e-14, rtol=w.rtol)
+    try:
+        mm.mm_set_m(ctx, 0, m0)
+        mm.mm_step_dt(ctx, dts)
+        t, _, n = mm.mm_get_time(ctx)
+        assert n == len(dts) and t >= w.t_end
+        err = np.abs(mm.mm_get_m(ctx, 0, m0.shape) - o.m).max()
+        assert err <= 1e-11, (len(dts), err)
+    finally:
+        mm.mm_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_dmi_film_256x256x16_replay(prec):
+    mm = need_gpu()
+    from oracle.observables import energy, topological_charge
+    w = W.dmi_256x256x16()
+    m0 = W.m_random_sphere(w.grid, seed=w.seed)
+    o, p = _solver(w, m0, dt=1e-14, rtol=w.rtol)
+    dts = [o.rk45_step() for _ in range(3)]
+    ctx = make_ctx(mm, w.grid, w.mat, precision=prec, demag=True, B=w.B_ext, dt=1e-14, rtol=w.rtol)
+    try:
+        mm.mm_set_m(ctx, 0, m0)
+        mm.mm_step_dt(ctx, dts)
+        m = mm.mm_get_m(ctx, 0, m0.shape)
+        err = np.abs(m - o.m).max()
+        assert err <= (1e-11 if prec == 64 else 1e-5), err
+        if prec == 64:
+            E = mm.mm_energy(ctx, 0)
+            ref = energy(m, p, o.K_hat)
+            assert abs(E[5] - ref["total"]) <= 1e-12 * max(abs(v) for v in ref.values())
+            Q = mm.mm_topo_charge(ctx, 0)
+            assert abs(Q - topological_charge(m, p)) <= 1e-9
+    finally:
+        mm.mm_destroy(ctx)
+
+
+def test_vortex_512x512x64_fp32_against_fp64():
+    mm = need_gpu()
+    w = W.vortex_512x512x64()
+    m0 = W.m_vortex(w.grid, seed=w.seed)
+    c64 = make_ctx(mm, w.grid, w.mat, precision=64, demag=True, dt=1e-14, rtol=w.rtol)
+    try:
+        mm.mm_set_m(c64, 0, m0)
+        E0 = mm.mm_energy(c64, 0)[5]
+        ts = [0.0]
+        for _ in range(3):
+            mm.mm_step(c64, 1)
+            ts.append(mm.mm_get_time(c64, 0)[0])
+        dts = np.diff(ts)
+        m64 = mm.mm_get_m(c64, 0, m0.shape)
+        E1 = mm.mm_energy(c64, 0)[5]
+    finally:
+        mm.mm_destroy(c64)
+    assert E1 <= E0
+    assert np.abs(np.sqrt((m64 ** 2).sum(axis=0)) - 1.0).max() < 1e-12
+    c32 = make_ctx(mm, w.grid, w.mat, precision=32, demag=True, dt=1e-14, rtol=w.rtol)
+    try:
+        mm.mm_set_m(c32, 0, m0)
+        mm.mm_step_dt(c32, dts)
+        m32 = mm.mm_get_m(c32, 0, m0.shape)
+    finally:
+        mm.mm_destroy(c32)
+    assert np.abs(np.sqrt((m32 ** 2).sum(axis=0)) - 1.0).max() < 1e-6
+    err = np.abs(m32 - m64).max()
+    assert err <= 1e-5, err
+
+
+def test_newell_entries_at_the_largest_displacements():
+    """FP64 Newell entries of the 512x512x64 grid of 3 nm cubes at the far
+    corners of the padded tensor, against the oracle's evaluation."""
+    mm = need_gpu()
+    from oracle.demag import newell_at
+    ijk = np.array([[511, 511, 63], [511, 0, 0], [0, 511, 0], [0, 0, 63], [300, 200, 40], [1, 511, 63],
+                    [2, 0, 0], [3, 2, 1]], dtype=np.int32)
+    d = (3e-9, 3e-9, 3e-9)
+    g = mm.mm_newell(ijk, d)
+    o = newell_at(ijk, d)
+    scale = np.abs(o).max(axis=1, keepdims=True)
+    assert np.all(np.abs(g - o) <= 1e-11 * scale + 1e-18)
