@@ -164,8 +164,13 @@ MM_API mm_status mm_destroy(mm_ctx* ctx);
  * returns to the context's own stream.  Cached CUDA graphs are rebuilt. */
 MM_API mm_status mm_set_stream(mm_ctx* ctx, void* stream);
 
-/* Set / read the magnetisation of one replica (host float64, 3N).  Input is
- * renormalised per cell; absent cells are set to zero. */
+/* Set / read the magnetisation of one replica (host float64, 3N, layout
+ * [component][z][y][x]).  The doubles are copied to a device staging buffer
+ * (3N doubles, allocated on first use and kept) and converted there:
+ * input is renormalised per cell; absent cells and zero vectors are set to
+ * zero.  Page-locked host memory gives the fastest copies.  Both calls
+ * return after the copy has completed (they synchronise the context
+ * stream).  Errors: MM_ERR_ARG (bad replica, NULL m), MM_ERR_OOM, MM_ERR_CUDA. */
 MM_API mm_status mm_set_m(mm_ctx* ctx, int replica, const double* m);
 MM_API mm_status mm_get_m(mm_ctx* ctx, int replica, double* m);
 

@@ -106,6 +106,8 @@ static mm_status upload_regions_t(mm_ctx* c) {
     if (e != cudaSuccess) return cuda_check(c, e, "material tables");
     cudaMemcpy(c->d_lut, lut.data(), sizeof(Region<T>) * nr, cudaMemcpyHostToDevice);
     cudaMemcpy(c->d_cpair, cp.data(), sizeof(T) * nr * nr, cudaMemcpyHostToDevice);
+    if constexpr (sizeof(T) == 4) { c->r0f = lut[0]; c->c00f = cp[0]; }
+    else { c->r0d = lut[0]; c->c00d = cp[0]; }
     if (!c->uniform) {
         e = cudaMalloc(&c->d_region, c->N);
         if (e != cudaSuccess) return cuda_check(c, e, "region map");
@@ -184,7 +186,7 @@ static void free_all(mm_ctx* c) {
     c->batch = nullptr;
     surrogate_free(c);
     void* bufs[] = {c->d_region, c->d_lut, c->d_cpair, c->d_m, c->d_mtmp, c->d_kslot, c->d_hd, c->d_hbuf,
-                    c->d_bcell, c->d_state, c->d_replay, c->d_red};
+                    c->d_bcell, c->d_state, c->d_replay, c->d_red, c->d_stage};
     for (void* b : bufs) cudaFree(b);
     for (auto& k : c->d_k) cudaFree(k);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -232,6 +234,39 @@ static void host_to_state(const double* m, long long N, const std::vector<uint8_
         else { x /= n; y /= n; z /= n; }
         out[i] = (T)x; out[N + i] = (T)y; out[2 * N + i] = (T)z;
     }
+}
+
+// Host doubles (already copied to the device) -> normalised state in the
+// working precision; absent cells (Ms = 0) and zero vectors become 0.
+template <typename T>
+__global__ void state_in_kernel(const double* __restrict__ src, long long N, const uint8_t* __restrict__ region,
+                                const Region<T>* __restrict__ lut, T* __restrict__ dst) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const bool present = region ? lut[region[i]].present != (T)0 : true;
+    double x = src[i], y = src[N + i], z = src[2 * N + i];
+    const double n = sqrt(x * x + y * y + z * z);
+    if (!present || n == 0.0) x = y = z = 0.0;
+    else { x /= n; y /= n; z /= n; }
+    dst[i] = (T)x; dst[N + i] = (T)y; dst[2 * N + i] = (T)z;
+}
+
+template <typename T>
+__global__ void state_out_kernel(const T* __restrict__ src, long long n, double* __restrict__ dst) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (double)src[i];
+}
+
+// Device staging buffer for host <-> state transfers (3 N doubles of the
+// largest replica), allocated on first use.
+static mm_status ensure_stage(mm_ctx* c, long long n3) {
+    if (c->d_stage && c->stage_n >= n3) return MM_OK;
+    cudaFree(c->d_stage);
+    c->d_stage = nullptr;
+    c->stage_n = 0;
+    mm_status s = alloc(c, &c->d_stage, sizeof(double) * n3, "host transfer staging");
+    if (s == MM_OK) c->stage_n = n3;
+    return s;
 }
 
 }  // namespace mm
@@ -492,19 +527,22 @@ mm_status mm_set_m(mm_ctx* c, int r, const double* m) {
     if (s != MM_OK) return s;
     if (!m) return set_error(c, MM_ERR_ARG, "null m");
     ReplicaView view(c, r);
-    const size_t vb = 3 * c->N * c->esz;
-    cudaError_t e;
-    if (c->prec == 32) {
-        std::vector<float> h;
-        host_to_state<float>(m, c->N, c->region_of_cell, c->regions, c->uniform, h);
-        e = cudaMemcpyAsync(c->d_m, h.data(), vb, cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    } else {
-        std::vector<double> h;
-        host_to_state<double>(m, c->N, c->region_of_cell, c->regions, c->uniform, h);
-        e = cudaMemcpyAsync(c->d_m, h.data(), vb, cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    const long long n3 = 3 * c->N;
+    s = ensure_stage(c, n3);
+    if (s != MM_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(c->d_stage, m, sizeof(double) * n3, cudaMemcpyHostToDevice, c->stream);
+    const unsigned nb = (unsigned)((c->N + 255) / 256);
+    const uint8_t* reg = c->uniform ? nullptr : (const uint8_t*)c->d_region;
+    if (e == cudaSuccess) {
+        if (c->prec == 32)
+            state_in_kernel<float><<<nb, 256, 0, c->stream>>>((const double*)c->d_stage, c->N, reg,
+                                                             (const Region<float>*)c->d_lut, (float*)c->d_m);
+        else
+            state_in_kernel<double><<<nb, 256, 0, c->stream>>>((const double*)c->d_stage, c->N, reg,
+                                                              (const Region<double>*)c->d_lut, (double*)c->d_m);
+        e = cudaGetLastError();
     }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     c->k1_valid = false;
     return cuda_check(c, e, "mm_set_m");
 }
@@ -512,18 +550,22 @@ mm_status mm_set_m(mm_ctx* c, int r, const double* m) {
 mm_status mm_get_m(mm_ctx* c, int r, double* m) {
     mm_status s = check_replica(c, r);
     if (s != MM_OK) return s;
+    if (!m) return set_error(c, MM_ERR_ARG, "null m");
     ReplicaView view(c, r);
     const long long n3 = 3 * c->N;
     cudaError_t e;
     if (c->prec == 32) {
-        std::vector<float> h(n3);
-        e = cudaMemcpyAsync(h.data(), c->d_m, n3 * 4, cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        for (long long i = 0; i < n3; ++i) m[i] = h[i];
+        s = ensure_stage(c, n3);
+        if (s != MM_OK) return s;
+        state_out_kernel<float><<<(unsigned)((n3 + 255) / 256), 256, 0, c->stream>>>((const float*)c->d_m, n3,
+                                                                                    (double*)c->d_stage);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(m, c->d_stage, sizeof(double) * n3, cudaMemcpyDeviceToHost, c->stream);
     } else {
-        e = cudaMemcpyAsync(m, c->d_m, n3 * 8, cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        e = cudaMemcpyAsync(m, c->d_m, sizeof(double) * n3, cudaMemcpyDeviceToHost, c->stream);
     }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     return cuda_check(c, e, "mm_get_m");
 }
 

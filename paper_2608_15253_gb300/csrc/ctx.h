@@ -111,6 +111,10 @@ struct mm_ctx {
     void* d_region = nullptr;   // uint8 per cell (null when uniform)
     void* d_lut = nullptr;      // Region<T>[nreg]
     void* d_cpair = nullptr;    // T[nreg*nreg]: 2 A_ij / (mu0 Ms_i)
+    mm::Region<float> r0f{};    // host copies of region 0 (the one material when uniform)
+    mm::Region<double> r0d{};
+    float c00f = 0.f;           // cpair[0]
+    double c00d = 0.0;
 
     // state buffers (working precision), [3][N] each
     void* d_m = nullptr;        // current state m0
@@ -119,6 +123,8 @@ struct mm_ctx {
     void* d_kslot = nullptr;    // device array of 7 pointers (FSAL rotation)
     void* d_hd = nullptr;       // demag field
     void* d_hbuf = nullptr;     // scratch field (observables)
+    void* d_stage = nullptr;    // host-transfer staging, stage_n doubles
+    long long stage_n = 0;
     void* d_bcell = nullptr;    // per-cell applied field (A/m) or null
     double Hext[3] = {0, 0, 0}; // uniform applied field (A/m)
     double Tr = 0.0;            // temperature

@@ -305,6 +305,94 @@ __global__ void __launch_bounds__(256) fft_x_c2r_direct_kernel(XArgs<float> a) {
     }
 }
 
+// FP32 X passes for long rows (Lh >= 192): one row per warp, eight warps per
+// CTA, no CTA-wide barrier.  R2C: packed pairs straight from global memory
+// into the first pass, later passes in warp-private shared memory, then the
+// split to the Lh+1 spectrum.  C2R: the rebuild of Z' from X[k] and
+// X[M-k] (both read from global memory) feeds the first pass; the last pass
+// writes the real row.
+constexpr int kXW = 8;   // warps (rows) per CTA
+
+template <int LT>
+__global__ void __launch_bounds__(32 * kXW) fft_x_r2c_warp_kernel(XArgs<float> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * kXW + warp;
+    if (row >= a.rows) return;                  // whole warp: no CTA barrier below
+    float2* sm = reinterpret_cast<float2*>(smem_raw) + warp * wline(LT);
+    constexpr int NP = ct_npass(LT);
+    const int nin = (a.nx + 1) / 2;
+    const long long g0 = (long long)row * a.in_pitch;
+    const bool vec2 = (a.nx % 2 == 0) && (a.in_pitch % 2 == 0);
+    auto load_in = [&](int n) {
+        float2 z = make_float2(0.f, 0.f);
+        if (n < nin) {
+            const long long q = g0 + 2 * n;
+            const bool has_y = 2 * n + 1 < a.nx;
+            if (vec2) z = *reinterpret_cast<const float2*>(a.in + q);
+            else {
+                z.x = a.in[q];
+                z.y = has_y ? a.in[q + 1] : 0.f;
+            }
+            if (a.region) {
+                z.x *= a.lut[a.region[q % a.cells_per_comp]].Ms;
+                z.y = has_y ? z.y * a.lut[a.region[(q + 1) % a.cells_per_comp]].Ms : 0.f;
+            } else {
+                z.x *= a.ms_uniform;
+                z.y *= a.ms_uniform;
+            }
+        }
+        return z;
+    };
+    warp_pass<float, 1, LT, ct_radix(LT, 0), 1>(a.tw, 2, load_in, [&](int i, float2 v) { sm[wpad(i)] = v; });
+    warp_fft_smem<float, 1, LT, 1, NP>(sm, a.tw, 2);
+    constexpr int M = LT, Kx = LT + 1;
+    float2* out = a.spec + spec_row(a, row) * a.Wk;
+    for (int k = lane; k < Kx; k += 32) {
+        const float2 zk = sm[wpad(k == M ? 0 : k)];
+        const float2 zc = cconj<float>(sm[wpad(k == 0 ? 0 : M - k)]);
+        const float2 E = cscale<float>(cadd<float>(zk, zc), 0.5f);
+        const float2 O = cscale<float>(mul_mi<float, 1>(csub<float>(zk, zc)), 0.5f);
+        out[k] = cadd<float>(E, cmul<float>(__ldg(&a.tw[k]), O));
+    }
+}
+
+template <int LT>
+__global__ void __launch_bounds__(32 * kXW) fft_x_c2r_warp_kernel(XArgs<float> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    const int row = blockIdx.x * kXW + warp;
+    if (row >= a.rows) return;
+    float2* sm = reinterpret_cast<float2*>(smem_raw) + warp * wline(LT);
+    constexpr int NP = ct_npass(LT), M = LT;
+    static_assert(NP >= 2, "first and last pass must differ");
+    const float2* X = a.spec + spec_row(a, row) * a.Wk;
+    // Z'[k] = (X[k] + conj X[M-k]) + i (X[k] - conj X[M-k]) conj(W^k)
+    auto load_rebuild = [&](int k) {
+        const float2 xk = X[k];
+        const float2 xc = cconj<float>(X[M - k]);
+        const float2 E = cadd<float>(xk, xc);
+        const float2 O = cmulc<float>(csub<float>(xk, xc), __ldg(&a.tw[k]));
+        return cadd<float>(E, mul_mi<float, -1>(O));
+    };
+    auto to_smem = [&](int i, float2 v) { sm[wpad(i)] = v; };
+    warp_pass<float, -1, LT, ct_radix(LT, 0), 1>(a.tw, 2, load_rebuild, to_smem);
+    warp_fft_smem<float, -1, LT, 1, NP - 1>(sm, a.tw, 2);
+    float* out = a.out_real + (long long)row * a.in_pitch;
+    const bool vec2 = (a.nx % 2 == 0) && (a.in_pitch % 2 == 0);
+    const int nx = a.nx;
+    warp_pass<float, -1, LT, ct_radix(LT, NP - 1), ct_ns(LT, NP - 1)>(
+        a.tw, 2, [&](int i) { return sm[wpad(i)]; },
+        [&](int n, float2 v) {
+            if (2 * n + 1 < nx) {
+                if (vec2) *reinterpret_cast<float2*>(out + 2 * n) = v;
+                else { out[2 * n] = v.x; out[2 * n + 1] = v.y; }
+            } else if (2 * n < nx) {
+                out[2 * n] = v.x;
+            }
+        });
+}
+
 // ---------------------------------------------------------------------------
 // Column passes (strided axes), optionally with the tensor multiply
 // ---------------------------------------------------------------------------
@@ -465,7 +553,7 @@ struct ZArgs {
 
 constexpr int kZT = 64;
 
-template <typename T, int L>
+template <typename T, int L, bool HALF>
 __global__ void __launch_bounds__(3 * kZT, 2) fft_zconv_reg_kernel(ZArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* tws = reinterpret_cast<cplx<T>*>(smem_raw);   // [L]
@@ -479,9 +567,9 @@ __global__ void __launch_bounds__(3 * kZT, 2) fft_zconv_reg_kernel(ZArgs<T> a) {
     cplx<T>* col = a.base + c * a.comp_stride + (valid ? p : 0);
     cplx<T> v[L];
 #pragma unroll
-    for (int z = 0; z < L; ++z) v[z] = (valid && z < a.nz) ? col[z * a.plane] : mkc<T>(0, 0);
+    for (int z = 0; z < L; ++z) v[z] = (valid && z < a.nz && (!HALF || z < L / 2)) ? col[z * a.plane] : mkc<T>(0, 0);
     __syncthreads();
-    reg_dif<T, L>(v, tws);
+    reg_dif<T, L, HALF>(v, tws);
 #pragma unroll
     for (int i = 0; i < L; ++i) sm[(c * L + i) * kZT + tx] = v[i];
     __syncthreads();
@@ -512,10 +600,10 @@ __global__ void __launch_bounds__(3 * kZT, 2) fft_zconv_reg_kernel(ZArgs<T> a) {
         const cplx<T> m2 = sm[(2 * L + i) * kZT + tx];
         v[i] = mkc<T>(k0 * m0.x + k1 * m1.x + k2 * m2.x, k0 * m0.y + k1 * m1.y + k2 * m2.y);
     }
-    reg_dit_inv<T, L>(v, tws);
+    reg_dit_inv<T, L, HALF>(v, tws);
     if (valid) {
 #pragma unroll
-        for (int z = 0; z < L; ++z)
+        for (int z = 0; z < (HALF ? L / 2 : L); ++z)
             if (z < a.nz) col[z * a.plane] = v[z];
     }
 }
@@ -779,6 +867,15 @@ static CKern<T> col_kernel(int L) {
     return fft_col_kernel<T, MODE, 0>;
 }
 
+static XKern<float> x_warp_kernel(bool fwd, int Lh) {
+    switch (Lh) {
+#define MM_CASE(n) case n: return fwd ? fft_x_r2c_warp_kernel<n> : fft_x_c2r_warp_kernel<n>;
+        MM_CASE(192) MM_CASE(256) MM_CASE(512)
+#undef MM_CASE
+        default: return nullptr;
+    }
+}
+
 using YKern = void (*)(YArgs<float>);
 using ZKern = void (*)(ZArgs<float>);
 
@@ -791,12 +888,12 @@ static YKern y_direct_kernel(bool fwd, int L) {
     }
 }
 
-static ZKern zconv_reg_kernel(int L) {
+// half: nz <= Pz/2 (the zero-padded upper half of every z line is known)
+static ZKern zconv_reg_kernel(int L, bool half) {
     switch (L) {
-        case 4: return fft_zconv_reg_kernel<float, 4>;
-        case 8: return fft_zconv_reg_kernel<float, 8>;
-        case 16: return fft_zconv_reg_kernel<float, 16>;
-        case 32: return fft_zconv_reg_kernel<float, 32>;
+#define MM_CASE(n) case n: return half ? fft_zconv_reg_kernel<float, n, true> : fft_zconv_reg_kernel<float, n, false>;
+        MM_CASE(4) MM_CASE(8) MM_CASE(16) MM_CASE(32)
+#undef MM_CASE
         default: return nullptr;
     }
 }
@@ -831,6 +928,15 @@ static void launch_x(mm_ctx* c, bool forward, const T* in, T* out_real, cplx<T>*
         }
     }
     a.cells_per_comp = cells_per_comp;
+    if constexpr (sizeof(T) == 4) {
+        if (XKern<float> wk = x_warp_kernel(forward, Lh)) {
+            const size_t smem = (size_t)kXW * wline(Lh) * sizeof(float2);
+            LaunchScope ls(c, forward ? "fft_x_r2c" : "fft_x_c2r",
+                           (double)rows * (nx * sizeof(T) + (Lh + 1) * sizeof(cplx<T>)));
+            wk<<<(rows + kXW - 1) / kXW, 32 * kXW, smem, c->stream>>>(a);
+            return;
+        }
+    }
     int rpc = std::max(1, kMaxV * 256 / Lh);
     rpc = std::min(rpc, 16);
     a.rpc = rpc;
@@ -879,7 +985,7 @@ static void demag_apply_t(mm_ctx* c, const T* m, T* Hd) {
     launch_x<T>(c, true, m, nullptr, S, 3 * nz * ny, ny, d.PyA, nx, nx, d.Lh, (const cplx<T>*)d.tw_x, true, N);
     const bool three_d = nz > 1;
     const bool fast_y = sizeof(T) == 4 && three_d && y_direct_kernel(true, d.Py) != nullptr;
-    const bool fast_z = sizeof(T) == 4 && three_d && zconv_reg_kernel(d.Pz) != nullptr;
+    const bool fast_z = sizeof(T) == 4 && three_d && zconv_reg_kernel(d.Pz, false) != nullptr;
     if (three_d && d.Py > 1 && fast_y) {
         launch_y_direct(c, true, (cplx<float>*)S, plane, ny, d.Py, "fft_y_fwd",
                         3.0 * nz * d.Kx * (ny + d.Py) * cplxb);
@@ -907,7 +1013,7 @@ static void demag_apply_t(mm_ctx* c, const T* m, T* Hd) {
             const long long cols = (long long)d.Py * d.Wk;
             LaunchScope ls(c, "fft_conv",
                            3.0 * d.Py * d.Kx * 2 * nz * cplxb + (double)d.ncomp * Kz * Ky * d.Kx * realb);
-            zconv_reg_kernel(d.Pz)<<<(unsigned)((cols + kZT - 1) / kZT), 3 * kZT, zconv_reg_smem(d.Pz), c->stream>>>(z);
+            zconv_reg_kernel(d.Pz, 2 * nz <= d.Pz)<<<(unsigned)((cols + kZT - 1) / kZT), 3 * kZT, zconv_reg_smem(d.Pz), c->stream>>>(z);
         } else if (three_d) {
             a.line_stride = plane; a.other_stride = d.Wk;
             a.L = d.Pz; a.n_in = nz; a.n_out = nz;
@@ -1073,8 +1179,14 @@ static cudaError_t fast_attributes() {
         if (e == cudaSuccess) e = smem_attr(y_direct_kernel(true, L));
         if (e == cudaSuccess) e = smem_attr(y_direct_kernel(false, L));
     }
-    for (int L : {4, 8, 16, 32})
-        if (e == cudaSuccess) e = smem_attr(zconv_reg_kernel(L));
+    for (int L : {4, 8, 16, 32}) {
+        if (e == cudaSuccess) e = smem_attr(zconv_reg_kernel(L, false));
+        if (e == cudaSuccess) e = smem_attr(zconv_reg_kernel(L, true));
+    }
+    for (int L : {192, 256, 512}) {
+        if (e == cudaSuccess) e = smem_attr(x_warp_kernel(true, L));
+        if (e == cudaSuccess) e = smem_attr(x_warp_kernel(false, L));
+    }
     return e;
 }
 

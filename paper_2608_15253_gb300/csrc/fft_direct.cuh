@@ -26,40 +26,58 @@ __host__ __device__ constexpr int bitrev_c(int i, int bits) {
     return r;
 }
 
+// Multiply by the twiddle tw[q] = exp(-2 pi i q / L) (DIR > 0) or its
+// conjugate; q is a compile-time constant after unrolling, so the exact
+// cases q = 0 and q = L/4 (a swap and a sign) cost no multiplication.
+template <typename T, int DIR, int L>
+__device__ __forceinline__ cplx<T> twiddle_mul(cplx<T> v, int q, const cplx<T>* tw) {
+    if (q == 0) return v;
+    if (4 * q == L) return mul_mi<T, DIR>(v);
+    return DIR > 0 ? cmul<T>(v, tw[q]) : cmulc<T>(v, tw[q]);
+}
+
 // In-register forward DFT of length L (a power of two), natural order in,
 // bit-reversed order out.  tw[q] = exp(-2 pi i q / L).  One template level
 // per stage so that every register index is a compile-time constant.
-template <typename T, int L, int S = 0>
+// HALF: the upper half of the input is known to be zero (a zero-padded
+// line), which removes the first stage's additions.
+template <typename T, int L, bool HALF = false, int S = 0>
 __device__ __forceinline__ void reg_dif(cplx<T> (&v)[L], const cplx<T>* tw) {
     if constexpr ((L >> S) >= 2) {
         constexpr int len = L >> S, h = len >> 1;
 #pragma unroll
         for (int q = 0; q < L / 2; ++q) {
             const int b = (q / h) * len, j = q % h;
-            const cplx<T> u = v[b + j], t = v[b + j + h];
-            v[b + j] = cadd<T>(u, t);
-            const cplx<T> d = csub<T>(u, t);
-            v[b + j + h] = j == 0 ? d : cmul<T>(d, tw[j * (L / len)]);
+            const cplx<T> u = v[b + j];
+            if (HALF && S == 0) {
+                v[b + j + h] = twiddle_mul<T, 1, L>(u, j * (L / len), tw);
+            } else {
+                const cplx<T> t = v[b + j + h];
+                v[b + j] = cadd<T>(u, t);
+                v[b + j + h] = twiddle_mul<T, 1, L>(csub<T>(u, t), j * (L / len), tw);
+            }
         }
-        reg_dif<T, L, S + 1>(v, tw);
+        reg_dif<T, L, HALF, S + 1>(v, tw);
     }
 }
 
 // In-register inverse DFT (unnormalised, exp(+2 pi i k n / L)), bit-reversed
-// order in, natural order out.
-template <typename T, int L, int S = 0>
+// order in, natural order out.  HALF: only the lower half of the output is
+// used (the last stage skips the upper half).
+template <typename T, int L, bool HALF = false, int S = 0>
 __device__ __forceinline__ void reg_dit_inv(cplx<T> (&v)[L], const cplx<T>* tw) {
     if constexpr ((2 << S) <= L) {
         constexpr int len = 2 << S, h = len >> 1;
+        constexpr bool last = (2 << S) == L;
 #pragma unroll
         for (int q = 0; q < L / 2; ++q) {
             const int b = (q / h) * len, j = q % h;
             const cplx<T> u = v[b + j];
-            const cplx<T> t = j == 0 ? v[b + j + h] : cmulc<T>(v[b + j + h], tw[j * (L / len)]);
+            const cplx<T> t = twiddle_mul<T, -1, L>(v[b + j + h], j * (L / len), tw);
             v[b + j] = cadd<T>(u, t);
-            v[b + j + h] = csub<T>(u, t);
+            if (!(HALF && last)) v[b + j + h] = csub<T>(u, t);
         }
-        reg_dit_inv<T, L, S + 1>(v, tw);
+        reg_dit_inv<T, L, HALF, S + 1>(v, tw);
     }
 }
 
@@ -143,6 +161,63 @@ __device__ __forceinline__ void cd_fft(cplx<T>* sm, const cplx<T>* gin, cplx<T>*
         constexpr int DST = P == NP - 1 ? CD_GLOBAL : CD_SMEM;
         cd_pass<T, DIR, L, R, NS, NT, TK, SRC, DST>(sm, gin, gout, gcol, gstride, nin, nout, tw);
         cd_fft<T, DIR, L, NT, TK, P + 1>(sm, gin, gout, gcol, gstride, nin, nout, tw);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One line per warp.  The line lives in warp-private shared memory with one
+// pad slot every 8 entries (index i at wpad(i)), which keeps the stride-R
+// writes of the early Stockham passes free of bank conflicts; passes are
+// separated by __syncwarp only, so warps never wait on each other.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int wpad(int i) { return i + (i >> 3); }
+__host__ __device__ constexpr int wline(int L) { return wpad(L) + 1; }
+
+template <typename T, int DIR, int L, int R, int NS, typename Load, typename Store>
+__device__ __forceinline__ void warp_pass(const cplx<T>* __restrict__ tw, int tws, Load load, Store store) {
+    constexpr int NB = L / R;
+    constexpr int SPAN = L / (NS * R);
+    constexpr int NBL = (NB + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    cplx<T> v[NBL][R];
+#pragma unroll
+    for (int i = 0; i < NBL; ++i) {
+        const int j = lane + 32 * i;
+        if (NB % 32 == 0 || j < NB) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) v[i][t] = load(j + t * NB);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < NBL; ++i) {
+        const int j = lane + 32 * i;
+        if (NB % 32 != 0 && j >= NB) continue;
+        const int k = j % NS;
+        if constexpr (NS > 1) {
+#pragma unroll
+            for (int t = 1; t < R; ++t) {
+                const cplx<T> w = __ldg(&tw[(t * k * SPAN) * tws]);
+                v[i][t] = DIR > 0 ? cmul<T>(v[i][t], w) : cmulc<T>(v[i][t], w);
+            }
+        }
+        dft_ct<T, DIR, R>(v[i]);
+        const int dst = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int t = 0; t < R; ++t) store(dst + t * NS, v[i][t]);
+    }
+    __syncwarp();
+}
+
+// Passes P .. PEND-1 of a warp's line, all shared memory -> shared memory.
+template <typename T, int DIR, int L, int P, int PEND>
+__device__ __forceinline__ void warp_fft_smem(cplx<T>* sm, const cplx<T>* __restrict__ tw, int tws) {
+    if constexpr (P < PEND) {
+        constexpr int R = ct_radix(L, P);
+        constexpr int NS = ct_ns(L, P);
+        warp_pass<T, DIR, L, R, NS>(tw, tws, [&](int i) { return sm[wpad(i)]; },
+                                    [&](int i, cplx<T> v) { sm[wpad(i)] = v; });
+        warp_fft_smem<T, DIR, L, P + 1, PEND>(sm, tw, tws);
     }
 }
 

@@ -16,7 +16,9 @@
 
 namespace mm {
 
-template <typename T>
+// UNIF: one material (coefficients passed by value in the launch
+// parameters, no region map or coefficient-table loads).
+template <typename T, bool UNIF>
 __global__ void __launch_bounds__(256) field_kernel(FieldArgs<T> a) {
     if (a.gate && !a.st->active) return;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -25,8 +27,8 @@ __global__ void __launch_bounds__(256) field_kernel(FieldArgs<T> a) {
     if (x >= a.nx || y >= a.ny) return;
     const long long N = a.N;
     const long long i = ((long long)z * a.ny + y) * a.nx + x;
-    const int ri = a.region ? a.region[i] : 0;
-    const Region<T>& R = a.lut[ri];
+    const int ri = UNIF ? 0 : (a.region ? a.region[i] : 0);
+    const Region<T>& R = UNIF ? a.R0 : a.lut[ri];
     const v3<T> m = ld3(a.m, N, i);
     if (R.present == (T)0) {
         const v3<T> zero = mk3<T>(0, 0, 0);
@@ -41,7 +43,7 @@ __global__ void __launch_bounds__(256) field_kernel(FieldArgs<T> a) {
     }
     const long long step = a.step_override >= 0 ? a.step_override : (a.st ? a.st->step : 0);
     v3<T> H, k;
-    cell_field<T>(a, x, y, z, i, ri, R, m, nullptr, step, H, k, a.mode != MODE_H);
+    cell_field<T, UNIF>(a, x, y, z, i, ri, R, m, nullptr, step, H, k, a.mode != MODE_H);
     if (a.mode == MODE_H) {
         st3(a.out, N, i, H);
         return;
@@ -127,7 +129,13 @@ static void field_launch_t(mm_ctx* c, int mode, unsigned terms, const T* m, cons
     if (mode == MODE_HEUN2) bytes += 6 * es * c->N;
     static const char* names[4] = {"field_H", "field_k", "field_heun1", "field_heun2"};
     LaunchScope ls(c, names[mode], bytes);
-    field_kernel<T><<<grd, blk, 0, c->stream>>>(a);
+    if (c->uniform && !a.region) {
+        if constexpr (sizeof(T) == 4) { a.R0 = c->r0f; a.c_uniform = c->c00f; }
+        else { a.R0 = c->r0d; a.c_uniform = c->c00d; }
+        field_kernel<T, true><<<grd, blk, 0, c->stream>>>(a);
+    } else {
+        field_kernel<T, false><<<grd, blk, 0, c->stream>>>(a);
+    }
 }
 
 void field_launch(mm_ctx* c, int mode, unsigned terms, const void* m, const void* Hd, void* out, void* out2,

@@ -64,6 +64,8 @@ struct FieldArgs {
     const Region<T>* lut;
     const T* cpair;
     int nreg;
+    T c_uniform;          // cpair[0] when there is one material
+    Region<T> R0;         // that material's coefficients
     int nx, ny, nz;
     long long N;
     T hx, hy, hz;         // cell size
@@ -104,7 +106,10 @@ __device__ __forceinline__ void st3(T* a, long long N, long long i, v3<T> v) {
 // Effective field of one present cell (x, y, z; linear index i) and, when
 // want_k, its LLG slope with the configured spin torque.  hd is added as the
 // demag field when the caller supplies it (batched path); a.Hd otherwise.
-template <typename T>
+// UNIF: one material everywhere (no region map): every in-grid neighbour is
+// present (the caller has checked the cell itself) and every exchange pair
+// uses the one coefficient a.cpair[0].
+template <typename T, bool UNIF = false>
 __device__ __forceinline__ void cell_field(const FieldArgs<T>& a, int x, int y, int z, long long i, int ri,
                                            const Region<T>& R, const v3<T>& m, const v3<T>* hd, long long step,
                                            v3<T>& H, v3<T>& k, bool want_k) {
@@ -135,14 +140,18 @@ __device__ __forceinline__ void cell_field(const FieldArgs<T>& a, int x, int y, 
                 int rj = 0;
                 if (inside) {
                     j = i + (long long)(q - pos[d]) * strides[d];
-                    rj = a.region ? a.region[j] : 0;
-                    present = a.lut[rj].present != (T)0;
+                    if constexpr (UNIF) {
+                        present = true;
+                    } else {
+                        rj = a.region ? a.region[j] : 0;
+                        present = a.lut[rj].present != (T)0;
+                    }
                 }
                 const int slot = 2 * d + s;
                 nbp[slot] = present;
                 if (present) {
                     nbv[slot] = ld3(a.m, N, j);
-                    cnb[slot] = __ldg(&a.cpair[ri * a.nreg + rj]);
+                    cnb[slot] = UNIF ? a.c_uniform : __ldg(&a.cpair[ri * a.nreg + rj]);
                 } else {
                     // ghost: m - h (D/2A) (z x n) x m, n = sg e_d
                     v3<T> zn = mk3<T>(0, 0, 0);

@@ -195,8 +195,13 @@ def mm_set_m(ctx, replica: int, m):
     _check(load().mm_set_m(ctx, replica, _dptr(a)), ctx)
 
 
-def mm_get_m(ctx, replica: int, shape):
-    out = np.zeros(shape, dtype=np.float64)
+def mm_get_m(ctx, replica: int, shape, out=None):
+    """out: optional C-contiguous float64 array of `shape` to fill (e.g. a
+    view of page-locked memory)."""
+    if out is None:
+        out = np.zeros(shape, dtype=np.float64)
+    elif out.dtype != np.float64 or not out.flags.c_contiguous or out.shape != tuple(shape):
+        raise ValueError("out must be a C-contiguous float64 array of the given shape")
     _check(load().mm_get_m(ctx, replica, _dptr(out)), ctx)
     return out
 

@@ -114,6 +114,9 @@ DEMAG_GRIDS = [
     W.Grid(40, 24, 16, 2e-9, 2e-9, 2e-9),
     W.Grid(24, 64, 8, 2e-9, 2e-9, 1e-9),
     W.Grid(13, 16, 4, 3e-9, 2e-9, 2e-9),
+    # one-row-per-warp X passes: half lengths 192 (odd nx: scalar loads) and 512
+    W.Grid(171, 10, 1, 2e-9, 2e-9, 1e-9),
+    W.Grid(500, 4, 2, 2e-9, 2e-9, 2e-9),
 ]
 
 
