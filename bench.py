@@ -102,22 +102,22 @@ def _dist():
 
 
 def _traffic_for(kernel: str):
-    """ncu DRAM bytes per launch recorded in profiles/traffic.json, valid only
-    while the kernel sources still hash to the recorded value."""
+    """ncu DRAM bytes per launch recorded in profiles/traffic.json, used only
+    while the source files that define the kernel still hash to the values
+    recorded with the capture (any change to them makes it null)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
-            rec = json.load(f)
+            ent = json.load(f)["kernels"][kernel]
+        h = hashlib.sha256()
+        for rel in ent["sources"]:
+            with open(os.path.join(ROOT, rel), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != ent["sources_sha256"]:
+            return None
+        return ent["dram_bytes_per_launch"]
     except Exception:
         return None
-    h = hashlib.sha256()
-    for name in sorted(os.listdir(os.path.join(ROOT, "paper_2608_15253_gb300", "csrc"))):
-        with open(os.path.join(ROOT, "paper_2608_15253_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
-    if rec.get("csrc_sha256") != h.hexdigest():
-        return None
-    ent = rec.get("kernels", {}).get(kernel)
-    return ent.get("dram_bytes_per_launch") if ent else None
 
 
 def cpu_baseline(seconds_budget=60.0):
@@ -192,21 +192,26 @@ def _timed(stream, fn):
     return e0.elapsed_time(e1)
 
 
-def fp32_error_vs_fp64(mm, w, m0, n_steps=20, dt=2e-14):
-    """max|m_fp32 - m_fp64| after n fixed RK45 steps from the same state: the
-    FP64 GPU path is the stand-in for the FP64 oracle here (the parity tests
-    hold it to the oracle within 1e-11)."""
+def fp32_vs_fp64(mm, stream, w, m0, n_steps=20, dt=2e-14):
+    """The same n fixed RK45 steps from the same state in FP32 and in FP64:
+    max|m_fp32 - m_fp64| (the FP64 GPU path stands in for the FP64 oracle
+    here; the parity tests hold it to the oracle within 1e-11) and each
+    precision's device throughput on those steps."""
     g = w.grid
     M = mm.Material(w.mat.Ms, w.mat.A, w.mat.alpha, w.mat.Ku1, w.mat.u, w.mat.D)
-    out = {}
+    out, rate = {}, {}
     for prec in (32, 64):
         cfg = mm.make_config(precision=prec, integrator=mm.MM_RK45, demag=mm.MM_DEMAG_EXACT, dt=dt, rtol=w.rtol)
         c = mm.mm_create(mm.make_grid(g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), M.s, cfg)
+        mm.mm_set_stream(c, stream.cuda_stream)
         mm.mm_set_m(c, 0, m0)
-        mm.mm_step_dt(c, np.full(n_steps, dt))
+        mm.mm_step_dt(c, np.full(3, dt))          # warm-up (graph capture, first slope)
+        mm.mm_set_m(c, 0, m0)
+        ms = _timed(stream, lambda: mm.mm_step_dt(c, np.full(n_steps, dt)))
+        rate[prec] = g.n * n_steps / (ms * 1e-3)
         out[prec] = mm.mm_get_m(c, 0, m0.shape)
         mm.mm_destroy(c)
-    return float(np.abs(out[32] - out[64]).max())
+    return float(np.abs(out[32] - out[64]).max()), rate
 
 
 def variant_batched(mm, stream, steps):
@@ -446,9 +451,12 @@ def run_gpu(args):
     mm.mm_destroy(ctx)
     if not args.no_variants:
         m0_err = W.m_random_sphere(g, seed=2)
-        line["error_vs_fp64"] = {"max_abs_dm": fp32_error_vs_fp64(mm, w, m0_err), "after_steps": 20,
-                                 "dt_s": 2e-14, "against": "FP64 GPU path on the same steps (held to the "
-                                 "FP64 oracle within 1e-11 by the parity tests)"}
+        err, rate = fp32_vs_fp64(mm, stream, w, m0_err)
+        line["error_vs_fp64"] = {"max_abs_dm": err, "after_steps": 20, "dt_s": 2e-14,
+                                 "against": "FP64 GPU path on the same steps (held to the FP64 oracle "
+                                            "within 1e-11 by the parity tests)"}
+        line["fp64"] = {"value": rate[64], "unit": UNIT, "fp32_same_steps": rate[32],
+                        "note": "20 replayed RK45 steps of dt 2e-14 s from the same random state"}
         line["variants"] = {}
         for name, fn in (("batched", lambda: variant_batched(mm, stream, args.batch_steps)),
                          ("surrogate", lambda: variant_surrogate(mm, stream, args.surrogate_steps))):
@@ -468,8 +476,8 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", default="", help="nx,ny,nz: a smaller case of the same workload (profiling)")

@@ -551,10 +551,10 @@ struct ZArgs {
     long long kk_stride;    // per kz: (Py/2+1) * Wk
 };
 
-constexpr int kZT = 64;
+constexpr int kZT = 32;
 
 template <typename T, int L, bool HALF>
-__global__ void __launch_bounds__(3 * kZT, 2) fft_zconv_reg_kernel(ZArgs<T> a) {
+__global__ void __launch_bounds__(3 * kZT, HALF ? 5 : 4) fft_zconv_reg_kernel(ZArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* tws = reinterpret_cast<cplx<T>*>(smem_raw);   // [L]
     cplx<T>* sm = tws + L;                                  // [3][L][kZT]
@@ -1013,7 +1013,8 @@ static void demag_apply_t(mm_ctx* c, const T* m, T* Hd) {
             const long long cols = (long long)d.Py * d.Wk;
             LaunchScope ls(c, "fft_conv",
                            3.0 * d.Py * d.Kx * 2 * nz * cplxb + (double)d.ncomp * Kz * Ky * d.Kx * realb);
-            zconv_reg_kernel(d.Pz, 2 * nz <= d.Pz)<<<(unsigned)((cols + kZT - 1) / kZT), 3 * kZT, zconv_reg_smem(d.Pz), c->stream>>>(z);
+            zconv_reg_kernel(d.Pz, 2 * nz <= d.Pz)<<<(unsigned)((cols + kZT - 1) / kZT), 3 * kZT, zconv_reg_smem(d.Pz),
+                                                      c->stream>>>(z);
         } else if (three_d) {
             a.line_stride = plane; a.other_stride = d.Wk;
             a.L = d.Pz; a.n_in = nz; a.n_out = nz;

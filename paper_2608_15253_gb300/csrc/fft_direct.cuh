@@ -29,11 +29,11 @@ __host__ __device__ constexpr int bitrev_c(int i, int bits) {
 // Multiply by the twiddle tw[q] = exp(-2 pi i q / L) (DIR > 0) or its
 // conjugate; q is a compile-time constant after unrolling, so the exact
 // cases q = 0 and q = L/4 (a swap and a sign) cost no multiplication.
-template <typename T, int DIR, int L>
+template <typename T, int DIR, int L, int TS = 1>
 __device__ __forceinline__ cplx<T> twiddle_mul(cplx<T> v, int q, const cplx<T>* tw) {
     if (q == 0) return v;
     if (4 * q == L) return mul_mi<T, DIR>(v);
-    return DIR > 0 ? cmul<T>(v, tw[q]) : cmulc<T>(v, tw[q]);
+    return DIR > 0 ? cmul<T>(v, tw[q * TS]) : cmulc<T>(v, tw[q * TS]);
 }
 
 // In-register forward DFT of length L (a power of two), natural order in,
@@ -41,7 +41,8 @@ __device__ __forceinline__ cplx<T> twiddle_mul(cplx<T> v, int q, const cplx<T>* 
 // per stage so that every register index is a compile-time constant.
 // HALF: the upper half of the input is known to be zero (a zero-padded
 // line), which removes the first stage's additions.
-template <typename T, int L, bool HALF = false, int S = 0>
+// TS: stride of tw (the table may belong to a length TS * L).
+template <typename T, int L, bool HALF = false, int TS = 1, int S = 0>
 __device__ __forceinline__ void reg_dif(cplx<T> (&v)[L], const cplx<T>* tw) {
     if constexpr ((L >> S) >= 2) {
         constexpr int len = L >> S, h = len >> 1;
@@ -50,21 +51,21 @@ __device__ __forceinline__ void reg_dif(cplx<T> (&v)[L], const cplx<T>* tw) {
             const int b = (q / h) * len, j = q % h;
             const cplx<T> u = v[b + j];
             if (HALF && S == 0) {
-                v[b + j + h] = twiddle_mul<T, 1, L>(u, j * (L / len), tw);
+                v[b + j + h] = twiddle_mul<T, 1, L, TS>(u, j * (L / len), tw);
             } else {
                 const cplx<T> t = v[b + j + h];
                 v[b + j] = cadd<T>(u, t);
-                v[b + j + h] = twiddle_mul<T, 1, L>(csub<T>(u, t), j * (L / len), tw);
+                v[b + j + h] = twiddle_mul<T, 1, L, TS>(csub<T>(u, t), j * (L / len), tw);
             }
         }
-        reg_dif<T, L, HALF, S + 1>(v, tw);
+        reg_dif<T, L, HALF, TS, S + 1>(v, tw);
     }
 }
 
 // In-register inverse DFT (unnormalised, exp(+2 pi i k n / L)), bit-reversed
 // order in, natural order out.  HALF: only the lower half of the output is
 // used (the last stage skips the upper half).
-template <typename T, int L, bool HALF = false, int S = 0>
+template <typename T, int L, bool HALF = false, int TS = 1, int S = 0>
 __device__ __forceinline__ void reg_dit_inv(cplx<T> (&v)[L], const cplx<T>* tw) {
     if constexpr ((2 << S) <= L) {
         constexpr int len = 2 << S, h = len >> 1;
@@ -73,11 +74,11 @@ __device__ __forceinline__ void reg_dit_inv(cplx<T> (&v)[L], const cplx<T>* tw) 
         for (int q = 0; q < L / 2; ++q) {
             const int b = (q / h) * len, j = q % h;
             const cplx<T> u = v[b + j];
-            const cplx<T> t = twiddle_mul<T, -1, L>(v[b + j + h], j * (L / len), tw);
+            const cplx<T> t = twiddle_mul<T, -1, L, TS>(v[b + j + h], j * (L / len), tw);
             v[b + j] = cadd<T>(u, t);
             if (!(HALF && last)) v[b + j + h] = csub<T>(u, t);
         }
-        reg_dit_inv<T, L, HALF, S + 1>(v, tw);
+        reg_dit_inv<T, L, HALF, TS, S + 1>(v, tw);
     }
 }
 

@@ -106,75 +106,32 @@ __device__ __forceinline__ void st3(T* a, long long N, long long i, v3<T> v) {
 // Effective field of one present cell (x, y, z; linear index i) and, when
 // want_k, its LLG slope with the configured spin torque.  hd is added as the
 // demag field when the caller supplies it (batched path); a.Hd otherwise.
-// UNIF: one material everywhere (no region map): every in-grid neighbour is
-// present (the caller has checked the cell itself) and every exchange pair
-// uses the one coefficient a.cpair[0].
-template <typename T, bool UNIF = false>
-__device__ __forceinline__ void cell_field(const FieldArgs<T>& a, int x, int y, int z, long long i, int ri,
-                                           const Region<T>& R, const v3<T>& m, const v3<T>* hd, long long step,
-                                           v3<T>& H, v3<T>& k, bool want_k) {
+// Field and slope of one present cell from its six neighbour values
+// (nbv, ghosts already substituted where absent), their raw presence nbp
+// (Zhang-Li uses the cell itself for an absent neighbour) and exchange
+// coefficients cnb.  use_hd: hdv is the demag field; otherwise a.Hd[i] is
+// read (when set).  Neighbour arrays are only read when the
+// exchange or DMI term or the Zhang-Li torque is on.
+template <typename T>
+__device__ __forceinline__ void cell_field_nb(const FieldArgs<T>& a, long long i, const Region<T>& R,
+                                              const v3<T>& m, const v3<T>* nbv, const bool* nbp, const T* cnb,
+                                              bool use_hd, const v3<T>& hdv, long long step, v3<T>& H, v3<T>& k,
+                                              bool want_k) {
     const long long N = a.N;
     H = mk3<T>(0, 0, 0);
     k = mk3<T>(0, 0, 0);
-    const bool need_nb = (a.terms & (MM_TERM_EXCHANGE | MM_TERM_DMI)) || a.tq == MM_TORQUE_ZL;
-    // neighbour values (ghosts where absent) and raw presence for Zhang-Li
-    v3<T> nbv[6];
-    bool nbp[6];
-    T cnb[6];
-    if (need_nb) {
-        const int dims[3] = {a.nx, a.ny, a.nz};
-        const int per[3] = {a.px, a.py, a.pz};
-        const int pos[3] = {x, y, z};
-        const long long strides[3] = {1, a.nx, (long long)a.nx * a.ny};
-        const T hh[3] = {a.hx, a.hy, a.hz};
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const int sg = s == 0 ? 1 : -1;
-                int q = pos[d] + sg;
-                bool inside = q >= 0 && q < dims[d];
-                if (!inside && per[d]) { q = (q + dims[d]) % dims[d]; inside = true; }
-                bool present = false;
-                long long j = 0;
-                int rj = 0;
-                if (inside) {
-                    j = i + (long long)(q - pos[d]) * strides[d];
-                    if constexpr (UNIF) {
-                        present = true;
-                    } else {
-                        rj = a.region ? a.region[j] : 0;
-                        present = a.lut[rj].present != (T)0;
-                    }
-                }
-                const int slot = 2 * d + s;
-                nbp[slot] = present;
-                if (present) {
-                    nbv[slot] = ld3(a.m, N, j);
-                    cnb[slot] = UNIF ? a.c_uniform : __ldg(&a.cpair[ri * a.nreg + rj]);
-                } else {
-                    // ghost: m - h (D/2A) (z x n) x m, n = sg e_d
-                    v3<T> zn = mk3<T>(0, 0, 0);
-                    if (d == 0) zn = mk3<T>(sg * m.z, (T)0, -sg * m.x);
-                    else if (d == 1) zn = mk3<T>((T)0, sg * m.z, -sg * m.y);
-                    nbv[slot] = m - (hh[d] * R.ratio) * zn;
-                    cnb[slot] = R.cg;
-                }
-            }
-        }
-        if (a.terms & MM_TERM_EXCHANGE) {
-            v3<T> e = mk3<T>(0, 0, 0);
-            e = e + (a.ix2 * cnb[0]) * (nbv[0] - m) + (a.ix2 * cnb[1]) * (nbv[1] - m);
-            e = e + (a.iy2 * cnb[2]) * (nbv[2] - m) + (a.iy2 * cnb[3]) * (nbv[3] - m);
-            e = e + (a.iz2 * cnb[4]) * (nbv[4] - m) + (a.iz2 * cnb[5]) * (nbv[5] - m);
-            H = H + e;
-        }
-        if (a.terms & MM_TERM_DMI) {
-            const T gx = (T)0.5 / a.hx, gy = (T)0.5 / a.hy;
-            const v3<T> dx = gx * (nbv[0] - nbv[1]);
-            const v3<T> dy = gy * (nbv[2] - nbv[3]);
-            H = H + R.dmi * mk3<T>(dx.z, dy.z, -dx.x - dy.y);
-        }
+    if (a.terms & MM_TERM_EXCHANGE) {
+        v3<T> e = mk3<T>(0, 0, 0);
+        e = e + (a.ix2 * cnb[0]) * (nbv[0] - m) + (a.ix2 * cnb[1]) * (nbv[1] - m);
+        e = e + (a.iy2 * cnb[2]) * (nbv[2] - m) + (a.iy2 * cnb[3]) * (nbv[3] - m);
+        e = e + (a.iz2 * cnb[4]) * (nbv[4] - m) + (a.iz2 * cnb[5]) * (nbv[5] - m);
+        H = H + e;
+    }
+    if (a.terms & MM_TERM_DMI) {
+        const T gx = (T)0.5 / a.hx, gy = (T)0.5 / a.hy;
+        const v3<T> dx = gx * (nbv[0] - nbv[1]);
+        const v3<T> dy = gy * (nbv[2] - nbv[3]);
+        H = H + R.dmi * mk3<T>(dx.z, dy.z, -dx.x - dy.y);
     }
     if (a.terms & MM_TERM_ANISOTROPY) {
         const v3<T> u = mk3<T>(R.ux, R.uy, R.uz);
@@ -185,7 +142,7 @@ __device__ __forceinline__ void cell_field(const FieldArgs<T>& a, int x, int y, 
         else H = H + mk3<T>(a.hext[0], a.hext[1], a.hext[2]);
     }
     if (a.terms & MM_TERM_DEMAG) {
-        if (hd) H = H + *hd;
+        if (use_hd) H = H + hdv;
         else if (a.Hd) H = H + ld3(a.Hd, N, i);
     }
     if ((a.terms & MM_TERM_THERMAL) && a.th_scale != (T)0) {
@@ -231,6 +188,71 @@ __device__ __forceinline__ void cell_field(const FieldArgs<T>& a, int x, int y, 
         const T inv = (T)1 / ((T)1 + R.alpha * R.alpha);
         k = k + inv * ((-((T)1 + R.alpha * a.xi)) * cross(m, mxug) + (-(a.xi - R.alpha)) * mxug);
     }
+}
+
+// Ghost value of an absent neighbour in direction d (0 x, 1 y, 2 z) and
+// side sg (+1 / -1): m - h (D/2A) (z x n) x m with n = sg e_d.
+template <typename T>
+__device__ __forceinline__ v3<T> ghost_value(const v3<T>& m, int d, int sg, T h, T ratio) {
+    v3<T> zn = mk3<T>(0, 0, 0);
+    if (d == 0) zn = mk3<T>(sg * m.z, (T)0, -sg * m.x);
+    else if (d == 1) zn = mk3<T>((T)0, sg * m.z, -sg * m.y);
+    return m - (h * ratio) * zn;
+}
+
+// Effective field of one present cell (x, y, z; linear index i) and, when
+// want_k, its LLG slope with the configured spin torque.  UNIF: one material
+// everywhere (no region map): every in-grid neighbour is present and every
+// exchange pair uses the one coefficient a.c_uniform.
+template <typename T, bool UNIF = false>
+__device__ __forceinline__ void cell_field(const FieldArgs<T>& a, int x, int y, int z, long long i, int ri,
+                                           const Region<T>& R, const v3<T>& m, const v3<T>* hd, long long step,
+                                           v3<T>& H, v3<T>& k, bool want_k) {
+    const long long N = a.N;
+    const bool need_nb = (a.terms & (MM_TERM_EXCHANGE | MM_TERM_DMI)) || a.tq == MM_TORQUE_ZL;
+    // neighbour values (ghosts where absent) and raw presence for Zhang-Li
+    v3<T> nbv[6];
+    bool nbp[6];
+    T cnb[6];
+    if (need_nb) {
+        const int dims[3] = {a.nx, a.ny, a.nz};
+        const int per[3] = {a.px, a.py, a.pz};
+        const int pos[3] = {x, y, z};
+        const long long strides[3] = {1, a.nx, (long long)a.nx * a.ny};
+        const T hh[3] = {a.hx, a.hy, a.hz};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const int sg = s == 0 ? 1 : -1;
+                int q = pos[d] + sg;
+                bool inside = q >= 0 && q < dims[d];
+                if (!inside && per[d]) { q = (q + dims[d]) % dims[d]; inside = true; }
+                bool present = false;
+                long long j = 0;
+                int rj = 0;
+                if (inside) {
+                    j = i + (long long)(q - pos[d]) * strides[d];
+                    if constexpr (UNIF) {
+                        present = true;
+                    } else {
+                        rj = a.region ? a.region[j] : 0;
+                        present = a.lut[rj].present != (T)0;
+                    }
+                }
+                const int slot = 2 * d + s;
+                nbp[slot] = present;
+                if (present) {
+                    nbv[slot] = ld3(a.m, N, j);
+                    cnb[slot] = UNIF ? a.c_uniform : __ldg(&a.cpair[ri * a.nreg + rj]);
+                } else {
+                    nbv[slot] = ghost_value<T>(m, d, sg, hh[d], R.ratio);
+                    cnb[slot] = R.cg;
+                }
+            }
+        }
+    }
+    cell_field_nb<T>(a, i, R, m, nbv, nbp, cnb, hd != nullptr, hd ? *hd : mk3<T>(0, 0, 0), step, H, k, want_k);
 }
 
 }  // namespace mm

@@ -65,6 +65,28 @@ __global__ void __launch_bounds__(256) combine_kernel(const DevState* __restrict
     ms[i] = acc;
 }
 
+// FP32, 3N a multiple of 4: four elements per thread as 16-byte vectors.
+template <int S>
+__global__ void __launch_bounds__(256) combine_vec4_kernel(const DevState* __restrict__ st,
+                                                           float* const* __restrict__ kptr,
+                                                           const float* __restrict__ m0, float* __restrict__ ms,
+                                                           long long n4) {
+    if (!st->active) return;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n4) return;
+    const int kf = st->k_first;
+    const float* cf = st->cf32[S];
+    float4 acc = __ldg(reinterpret_cast<const float4*>(m0) + i);
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+        if (j == 1 && S == 6) continue;             // a_7,2 = 0
+        const float c = cf[j];
+        const float4 k = __ldg(reinterpret_cast<const float4*>(kptr[kslot_of(j, kf)]) + i);
+        acc.x += c * k.x; acc.y += c * k.y; acc.z += c * k.z; acc.w += c * k.w;
+    }
+    reinterpret_cast<float4*>(ms)[i] = acc;
+}
+
 // per-cell error |dt sum e_j k_j|, block max, atomic max into st->err(_f)
 template <typename T>
 __global__ void error_kernel(DevState* st, T* const* __restrict__ kptr, long long N) {
@@ -213,7 +235,20 @@ static void rk45_attempt_t(mm_ctx* c) {
             static void (*const kern[7])(const DevState*, T* const*, const T*, T*, long long) = {
                 nullptr, combine_kernel<T, 1>, combine_kernel<T, 2>, combine_kernel<T, 3>,
                 combine_kernel<T, 4>, combine_kernel<T, 5>, combine_kernel<T, 6>};
-            kern[s]<<<nb3, tb, 0, c->stream>>>(c->d_state, kp, (const T*)c->d_m, (T*)c->d_mtmp, n3);
+            if constexpr (sizeof(T) == 4) {
+                if (n3 % 4 == 0) {
+                    static void (*const k4[7])(const DevState*, float* const*, const float*, float*, long long) = {
+                        nullptr, combine_vec4_kernel<1>, combine_vec4_kernel<2>, combine_vec4_kernel<3>,
+                        combine_vec4_kernel<4>, combine_vec4_kernel<5>, combine_vec4_kernel<6>};
+                    const long long n4 = n3 / 4;
+                    k4[s]<<<(unsigned)((n4 + tb - 1) / tb), tb, 0, c->stream>>>(
+                        c->d_state, (float* const*)kp, (const float*)c->d_m, (float*)c->d_mtmp, n4);
+                } else {
+                    kern[s]<<<nb3, tb, 0, c->stream>>>(c->d_state, kp, (const T*)c->d_m, (T*)c->d_mtmp, n3);
+                }
+            } else {
+                kern[s]<<<nb3, tb, 0, c->stream>>>(c->d_state, kp, (const T*)c->d_m, (T*)c->d_mtmp, n3);
+            }
         }
         if (demag) demag_eval(c, c->d_mtmp, c->d_hd);
         // stages 2..6 own fixed slots; the FSAL stage 7 slope goes to the slot

@@ -17,6 +17,51 @@
 
 namespace mm {
 
+// The demag operator restricted to in-plane displacements |dx|, |dy| <= 2
+// of a one-cell-thick film: N(d) as xx, yy, zz, xy (xz = yz = 0).  The
+// network learns only what this exact near-field part leaves over.
+struct NearKernel {
+    float n[25][4];
+};
+
+// out += scale * sum_d N(d) (m - mref)(r - d) over source cells inside the
+// grid; mref may be null (m is already an increment).
+__global__ void near_demag_kernel(const float* __restrict__ m, const float* __restrict__ mref, int nx, int ny,
+                                  NearKernel K, float scale, float* __restrict__ out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    const long long N = (long long)nx * ny;
+    float hx = 0.f, hy = 0.f, hz = 0.f;
+#pragma unroll
+    for (int dy = -2; dy <= 2; ++dy) {
+        const int ys = y - dy;
+        if (ys < 0 || ys >= ny) continue;
+#pragma unroll
+        for (int dx = -2; dx <= 2; ++dx) {
+            const int xs = x - dx;
+            if (xs < 0 || xs >= nx) continue;
+            const long long j = (long long)ys * nx + xs;
+            float ax = m[j], ay = m[N + j], az = m[2 * N + j];
+            if (mref) { ax -= mref[j]; ay -= mref[N + j]; az -= mref[2 * N + j]; }
+            const float* k = K.n[(dy + 2) * 5 + dx + 2];
+            hx += k[0] * ax + k[3] * ay;
+            hy += k[3] * ax + k[1] * ay;
+            hz += k[2] * az;
+        }
+    }
+    const long long i = (long long)y * nx + x;
+    out[i] += scale * hx;
+    out[N + i] += scale * hy;
+    out[2 * N + i] += scale * hz;
+}
+
+static void near_launch(mm_ctx* c, const float* m, const float* mref, const NearKernel& K, float scale, float* out) {
+    const int nx = c->grid.nx, ny = c->grid.ny;
+    dim3 blk(32, 8), grd((nx + 31) / 32, (ny + 7) / 8);
+    LaunchScope ls(c, "near_demag", 36.0 * nx * ny);
+    near_demag_kernel<<<grd, blk, 0, c->stream>>>(m, mref, nx, ny, K, scale, out);
+}
+
 static const int kCin[4] = {3, 32, 32, 32}, kCout[4] = {32, 32, 32, 3};
 static const int kCinP[4] = {16, 32, 32, 32}, kCoutP[4] = {32, 32, 32, 16};
 
@@ -44,6 +89,7 @@ struct SurrogateHost {
     float* d_mref = nullptr;
     float* d_href = nullptr;
     double* d_red = nullptr;
+    NearKernel near{};      // exact Newell tensor on the 5x5 in-plane neighbourhood
 };
 
 static void sfree(SurrogateHost* s) {
@@ -98,6 +144,25 @@ static mm_status ensure_surrogate(mm_ctx* c) {
     if (e != cudaSuccess) {
         sfree(s);
         return cuda_check(c, e, "surrogate parameters");
+    }
+    // near-field Newell entries (FP64 on the GPU, same evaluation as the setup)
+    std::vector<int> ijk(75);
+    std::vector<double> nv(150);
+    for (int dy = -2; dy <= 2; ++dy)
+        for (int dx = -2; dx <= 2; ++dx) {
+            const int q = (dy + 2) * 5 + dx + 2;
+            ijk[3 * q] = dx; ijk[3 * q + 1] = dy; ijk[3 * q + 2] = 0;
+        }
+    mm_status ns = newell_gpu(25, ijk.data(), c->grid.dx, c->grid.dy, c->grid.dz, nv.data());
+    if (ns != MM_OK) {
+        sfree(s);
+        return set_error(c, ns, "near-field Newell entries");
+    }
+    for (int q = 0; q < 25; ++q) {
+        s->near.n[q][0] = (float)nv[6 * q + 0];
+        s->near.n[q][1] = (float)nv[6 * q + 1];
+        s->near.n[q][2] = (float)nv[6 * q + 2];
+        s->near.n[q][3] = (float)nv[6 * q + 3];
     }
     c->surr = s;
     return MM_OK;
@@ -301,7 +366,7 @@ __global__ void err_max_kernel(const float* __restrict__ a, const float* __restr
     }
 }
 
-// H_pred(m) = H_ref + Ms * CNN(c_in (m - m_ref)) / c_in into Hd
+// H_pred(m) = H_ref - Ms N_near * (m - m_ref) + Ms * CNN(c_in (m - m_ref)) / c_in into Hd
 void surrogate_apply(mm_ctx* c, const void* m, void* Hd) {
     SurrogateHost* s = c->surr;
     const int H = c->grid.ny, W = c->grid.nx;
@@ -313,6 +378,7 @@ void surrogate_apply(mm_ctx* c, const void* m, void* Hd) {
     run_forward(c, 1, H, W, 1.f / s->c_in, 0);
     LaunchScope ls(c, "cnn_output", 36.0 * N);
     cnn_field_from_output(c->stream, s->y, s->d_href, N, (float)c->regions[0].Ms, (float*)Hd);
+    near_launch(c, (const float*)m, s->d_mref, s->near, -(float)c->regions[0].Ms, (float*)Hd);
     s->n_surr++;
 }
 
@@ -326,6 +392,10 @@ mm_status sync_state_pub(mm_ctx* c);
 mm_status surrogate_block(mm_ctx* c) {
     SurrogateHost* s = c->surr;
     const long long N = c->N;
+    // activations sized for the whole grid (training or a direct forward call
+    // may have resized them); allocates only when the geometry changed
+    mm_status bs = ensure_buffers(c, 1, c->grid.ny, c->grid.nx);
+    if (bs != MM_OK) return bs;
     const unsigned nb = (unsigned)((3 * N + 255) / 256);
     if (s->fallback) {
         s->use_now = false;
@@ -504,6 +574,8 @@ mm_status mm_surrogate_train(mm_ctx* c, const mm_train_cfg* cfg, double* final_l
     for (int q = 0; q < np; ++q) {
         diff_kernel<<<gb, 256, 0, c->stream>>>(snaps + pairs[q].second * fe, snaps + pairs[q].first * fe, fe, dm + q * fe);
         demag_apply(c, dm + q * fe, dh + q * fe);   // exact FFT demag of the increment (linear in m)
+        // the network's target: what the exact near-field part leaves over
+        near_launch(c, dm + q * fe, nullptr, s->near, (float)c->regions[0].Ms, dh + q * fe);
     }
     cudaMemsetAsync(s->d_red, 0, sizeof(double), c->stream);
     sumsq_kernel<<<304, 256, 0, c->stream>>>(dm, fe * np, s->d_red);
