@@ -272,7 +272,7 @@ def variant_batched(mm, stream, steps):
                               "against": "FP64 single-instance GPU runs with the same Philox key"}}
 
 
-def variant_surrogate(mm, stream, steps, train_steps=600):
+def variant_surrogate(mm, stream, steps, train_steps=1500):
     """512x512x1 skyrmion-lattice film, FP32 RK45: exact FFT demag against the
     BF16 CNN surrogate refreshed exactly every k attempted steps."""
     import torch

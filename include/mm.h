@@ -299,7 +299,7 @@ typedef struct mm_surrogate_stats {
  * Prediction model between exact refreshes:
  *   H(m) = H_ref - Ms N_near * dm + Ms CNN(c_in dm) / c_in,  dm = m - m_ref,
  * where N_near is the exact Newell tensor on in-plane displacements
- * |dx|, |dy| <= 2 (a fixed convolution) and the network is trained on what
+ * |dx|, |dy| <= 5 (a fixed convolution) and the network is trained on what
  * it leaves over, c_in (H_demag(dm) + Ms N_near * dm) / Ms, with
  * c_in = 1 / rms(dm) of the training pairs.  final_loss may be NULL. */
 MM_API mm_status mm_surrogate_train(mm_ctx* ctx, const mm_train_cfg* cfg, double* final_loss);

@@ -157,7 +157,9 @@ static mm_status build_regions(mm_ctx* c, const mm_material* mat) {
 
 static void invalidate_graph(mm_ctx* c) {
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->graph1) cudaGraphExecDestroy(c->graph1);
     c->graph = nullptr;
+    c->graph1 = nullptr;
     c->graph_chunk = 0;
 }
 
@@ -668,34 +670,50 @@ static void launch_attempts(mm_ctx* c, int n) {
 
 static const int kChunk = 8;
 
+// Capture `n` attempts on the context stream into an executable graph;
+// *launches receives the kernel launches one replay makes.
+static mm_status capture_attempts(mm_ctx* c, int n, cudaGraphExec_t* out, long long* launches) {
+    cudaGraph_t g;
+    const long long before = c->launches;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_check(c, e, "graph capture");
+    launch_attempts(c, n);
+    e = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess) return cuda_check(c, e, "graph capture end");
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_check(c, e, "graph instantiate");
+    *launches = c->launches - before;   // counted on replay instead
+    c->launches = before;
+    return MM_OK;
+}
+
 static mm_status run_attempts(mm_ctx* c, long long n_attempts) {
     if (c->profiling) {
         launch_attempts(c, (int)n_attempts);
         return cuda_check(c, cudaGetLastError(), "launch");
     }
-    if (!c->graph) {
-        cudaGraph_t g;
-        const long long before = c->launches;
-        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return cuda_check(c, e, "graph capture");
-        launch_attempts(c, kChunk);
-        e = cudaStreamEndCapture(c->stream, &g);
-        if (e != cudaSuccess) return cuda_check(c, e, "graph capture end");
-        e = cudaGraphInstantiate(&c->graph, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return cuda_check(c, e, "graph instantiate");
-        c->graph_chunk = kChunk;
-        c->launches_per_chunk = c->launches - before;   // counted on replay instead
-        c->launches = before;
-    }
     long long left = n_attempts;
+    if (left >= kChunk && !c->graph) {
+        mm_status s = capture_attempts(c, kChunk, &c->graph, &c->launches_per_chunk);
+        if (s != MM_OK) return s;
+        c->graph_chunk = kChunk;
+    }
     while (left >= kChunk) {
         cudaError_t e = cudaGraphLaunch(c->graph, c->stream);
         if (e != cudaSuccess) return cuda_check(c, e, "graph launch");
         c->launches += c->launches_per_chunk;
         left -= kChunk;
     }
-    if (left > 0) launch_attempts(c, (int)left);
+    if (left > 0 && !c->graph1) {
+        mm_status s = capture_attempts(c, 1, &c->graph1, &c->launches_per_attempt);
+        if (s != MM_OK) return s;
+    }
+    for (; left > 0; --left) {
+        cudaError_t e = cudaGraphLaunch(c->graph1, c->stream);
+        if (e != cudaSuccess) return cuda_check(c, e, "graph launch");
+        c->launches += c->launches_per_attempt;
+    }
     return cuda_check(c, cudaGetLastError(), "launch");
 }
 

@@ -150,6 +150,8 @@ struct mm_ctx {
     // CUDA graph of a chunk of integrator attempts
     cudaGraphExec_t graph = nullptr;
     int graph_chunk = 0;
+    cudaGraphExec_t graph1 = nullptr;   // one attempt (the remainder of a request)
+    long long launches_per_attempt = 0;
     long long launches_per_chunk = 0;
 
     // replica batching (R > 1): per-replica grids, offsets, keys, T and J

@@ -553,14 +553,45 @@ struct ZArgs {
 
 constexpr int kZT = 32;
 
+// v[i] (bit-reversed kz = bitrev(i)) = sum_j K_cj(kx, ky, kz) M_j, the three
+// spectra M_j read from shared memory.  Tensor components xx yy zz xy xz yz
+// = 0..5 stored for ky, kz <= P/2; xy is odd in ky, xz odd in kz, yz odd in
+// both, so row C needs the signs (1, sy, sz), (sy, 1, sy sz), (sz, sy sz, 1).
+template <typename T, int L, int C, bool YF>
+__device__ __forceinline__ void zconv_multiply(cplx<T> (&v)[L], const cplx<T>* sm, int tx, const T* K,
+                                               long long kcs, long long kks) {
+    constexpr int LOG = ilog2_c(L);
+    constexpr int j0 = C == 0 ? 0 : C == 1 ? 3 : 4;
+    constexpr int j1 = C == 0 ? 3 : C == 1 ? 1 : 5;
+    constexpr int j2 = C == 0 ? 4 : C == 1 ? 5 : 2;
+    constexpr T sy = YF ? (T)-1 : (T)1;
+    const T* K0 = K + j0 * kcs;
+    const T* K1 = K + j1 * kcs;
+    const T* K2 = K + j2 * kcs;
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        const int kz = bitrev_c(i, LOG);
+        const int kzf = kz <= L / 2 ? kz : L - kz;
+        const T sz = kz <= L / 2 ? (T)1 : (T)-1;
+        const T s0 = C == 0 ? (T)1 : C == 1 ? sy : sz;
+        const T s1 = C == 0 ? sy : C == 1 ? (T)1 : sy * sz;
+        const T s2 = C == 0 ? sz : C == 1 ? sy * sz : (T)1;
+        const T k0 = s0 * __ldg(K0 + kzf * kks);
+        const T k1 = s1 * __ldg(K1 + kzf * kks);
+        const T k2 = s2 * __ldg(K2 + kzf * kks);
+        const cplx<T> m0 = sm[(0 * L + i) * kZT + tx];
+        const cplx<T> m1 = sm[(1 * L + i) * kZT + tx];
+        const cplx<T> m2 = sm[(2 * L + i) * kZT + tx];
+        v[i] = mkc<T>(k0 * m0.x + k1 * m1.x + k2 * m2.x, k0 * m0.y + k1 * m1.y + k2 * m2.y);
+    }
+}
+
 template <typename T, int L, bool HALF>
 __global__ void __launch_bounds__(3 * kZT, HALF ? 5 : 4) fft_zconv_reg_kernel(ZArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cplx<T>* tws = reinterpret_cast<cplx<T>*>(smem_raw);   // [L]
-    cplx<T>* sm = tws + L;                                  // [3][L][kZT]
-    constexpr int LOG = ilog2_c(L);
+    cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw) + L;  // [3][L][kZT]
+    const cplx<T>* tws = nullptr;                            // twiddles from c_tw32
     const int tx = threadIdx.x % kZT, c = threadIdx.x / kZT;
-    if (threadIdx.x < L) tws[threadIdx.x] = a.tw[threadIdx.x];
     const long long p = (long long)blockIdx.x * kZT + tx;
     const int ky = (int)(p / a.Wk), kx = (int)(p - (long long)ky * a.Wk);
     const bool valid = ky < a.Py && kx < a.Kx;
@@ -568,37 +599,25 @@ __global__ void __launch_bounds__(3 * kZT, HALF ? 5 : 4) fft_zconv_reg_kernel(ZA
     cplx<T> v[L];
 #pragma unroll
     for (int z = 0; z < L; ++z) v[z] = (valid && z < a.nz && (!HALF || z < L / 2)) ? col[z * a.plane] : mkc<T>(0, 0);
-    __syncthreads();
     reg_dif<T, L, HALF>(v, tws);
 #pragma unroll
     for (int i = 0; i < L; ++i) sm[(c * L + i) * kZT + tx] = v[i];
     __syncthreads();
-    // row c of the tensor: xx yy zz xy xz yz = 0..5; xy is odd in ky, xz odd
-    // in kz, yz odd in both (the stored half spectra hold ky, kz <= P/2)
-    const int i0 = c == 0 ? 0 : c == 1 ? 3 : 4;
-    const int i1 = c == 0 ? 3 : c == 1 ? 1 : 5;
-    const int i2 = c == 0 ? 4 : c == 1 ? 5 : 2;
+    // row c of the tensor times the three spectra; c is uniform over a warp
+    // (kZT is a multiple of 32) and the ky fold nearly so, which makes every
+    // parity sign a compile-time constant
     const bool yfold = ky > a.Py / 2;
     const int kyf = yfold ? a.Py - ky : ky;
-    const T sy = yfold ? (T)-1 : (T)1;
-    const T y0 = c == 1 ? sy : (T)1, y1 = c == 1 ? (T)1 : sy, y2 = c == 1 ? sy : (T)1;
-    const bool zc2 = c == 2;
     const T* K = a.khat + (valid ? (long long)kyf * a.Wk + kx : 0);
-    const T* K0 = K + i0 * a.kc_stride;
-    const T* K1 = K + i1 * a.kc_stride;
-    const T* K2 = K + i2 * a.kc_stride;
-#pragma unroll
-    for (int i = 0; i < L; ++i) {
-        const int kz = bitrev_c(i, LOG);
-        const int kzf = kz <= L / 2 ? kz : L - kz;
-        const T sz = kz <= L / 2 ? (T)1 : (T)-1;
-        const T k0 = __ldg(K0 + kzf * a.kk_stride) * y0 * (zc2 ? sz : (T)1);
-        const T k1 = __ldg(K1 + kzf * a.kk_stride) * y1 * (zc2 ? sz : (T)1);
-        const T k2 = __ldg(K2 + kzf * a.kk_stride) * y2 * (zc2 ? (T)1 : sz);
-        const cplx<T> m0 = sm[(0 * L + i) * kZT + tx];
-        const cplx<T> m1 = sm[(1 * L + i) * kZT + tx];
-        const cplx<T> m2 = sm[(2 * L + i) * kZT + tx];
-        v[i] = mkc<T>(k0 * m0.x + k1 * m1.x + k2 * m2.x, k0 * m0.y + k1 * m1.y + k2 * m2.y);
+    if (c == 0) {
+        if (yfold) zconv_multiply<T, L, 0, true>(v, sm, tx, K, a.kc_stride, a.kk_stride);
+        else zconv_multiply<T, L, 0, false>(v, sm, tx, K, a.kc_stride, a.kk_stride);
+    } else if (c == 1) {
+        if (yfold) zconv_multiply<T, L, 1, true>(v, sm, tx, K, a.kc_stride, a.kk_stride);
+        else zconv_multiply<T, L, 1, false>(v, sm, tx, K, a.kc_stride, a.kk_stride);
+    } else {
+        if (yfold) zconv_multiply<T, L, 2, true>(v, sm, tx, K, a.kc_stride, a.kk_stride);
+        else zconv_multiply<T, L, 2, false>(v, sm, tx, K, a.kc_stride, a.kk_stride);
     }
     reg_dit_inv<T, L, HALF>(v, tws);
     if (valid) {
@@ -1192,7 +1211,15 @@ static cudaError_t fast_attributes() {
 }
 
 mm_status demag_setup(mm_ctx* c) {
-    cudaError_t e = fft_attributes<float>();
+    // length-32 twiddles of the register z pass (per device; cheap to repeat)
+    float2 tw32[32];
+    for (int q = 0; q < 32; ++q) {
+        const double ang = -2.0 * kPi * (double)q / 32.0;
+        tw32[q] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+    cudaError_t e = cudaMemcpyToSymbol(c_tw32, tw32, sizeof tw32);
+    if (e != cudaSuccess) return cuda_check(c, e, "twiddle table");
+    e = fft_attributes<float>();
     if (e == cudaSuccess) e = fast_attributes();
     if (e == cudaSuccess) e = fft_attributes<double>();
     if (e != cudaSuccess) return cuda_check(c, e, "FFT kernel attributes");

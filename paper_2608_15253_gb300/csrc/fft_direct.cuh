@@ -26,14 +26,31 @@ __host__ __device__ constexpr int bitrev_c(int i, int bits) {
     return r;
 }
 
+// exp(-2 pi i q / 32), q < 32, in constant memory (filled by the demag
+// setup of the including translation unit): with a compile-time index it is
+// read as an instruction operand.
+static __constant__ float2 c_tw32[32];
+
 // Multiply by the twiddle tw[q] = exp(-2 pi i q / L) (DIR > 0) or its
 // conjugate; q is a compile-time constant after unrolling, so the exact
 // cases q = 0 and q = L/4 (a swap and a sign) cost no multiplication.
+// tw == nullptr (FP32, L dividing 32): the constant table c_tw32.
 template <typename T, int DIR, int L, int TS = 1>
 __device__ __forceinline__ cplx<T> twiddle_mul(cplx<T> v, int q, const cplx<T>* tw) {
     if (q == 0) return v;
     if (4 * q == L) return mul_mi<T, DIR>(v);
-    return DIR > 0 ? cmul<T>(v, tw[q * TS]) : cmulc<T>(v, tw[q * TS]);
+    cplx<T> w;
+    if constexpr (sizeof(T) == 4 && 32 % (L * TS) == 0) {
+        if (tw == nullptr) {
+            const float2 c = c_tw32[q * TS * (32 / (L * TS))];
+            w = mkc<T>(c.x, c.y);
+        } else {
+            w = tw[q * TS];
+        }
+    } else {
+        w = tw[q * TS];
+    }
+    return DIR > 0 ? cmul<T>(v, w) : cmulc<T>(v, w);
 }
 
 // In-register forward DFT of length L (a power of two), natural order in,

@@ -17,33 +17,34 @@
 
 namespace mm {
 
-// The demag operator restricted to in-plane displacements |dx|, |dy| <= 2
+// The demag operator restricted to in-plane displacements |dx|, |dy| <= kNearR
 // of a one-cell-thick film: N(d) as xx, yy, zz, xy (xz = yz = 0).  The
 // network learns only what this exact near-field part leaves over.
+constexpr int kNearR = 5, kNearW = 2 * kNearR + 1, kNearTaps = kNearW * kNearW;
 struct NearKernel {
-    float n[25][4];
+    float n[kNearTaps][4];
 };
 
 // out += scale * sum_d N(d) (m - mref)(r - d) over source cells inside the
-// grid; mref may be null (m is already an increment).
+// grid; mref may be null (m is already an increment).  The tensor table
+// is a launch parameter (kNearTaps x 4 floats).
 __global__ void near_demag_kernel(const float* __restrict__ m, const float* __restrict__ mref, int nx, int ny,
                                   NearKernel K, float scale, float* __restrict__ out) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= nx || y >= ny) return;
     const long long N = (long long)nx * ny;
     float hx = 0.f, hy = 0.f, hz = 0.f;
-#pragma unroll
-    for (int dy = -2; dy <= 2; ++dy) {
+    for (int dy = -kNearR; dy <= kNearR; ++dy) {
         const int ys = y - dy;
         if (ys < 0 || ys >= ny) continue;
 #pragma unroll
-        for (int dx = -2; dx <= 2; ++dx) {
+        for (int dx = -kNearR; dx <= kNearR; ++dx) {
             const int xs = x - dx;
             if (xs < 0 || xs >= nx) continue;
             const long long j = (long long)ys * nx + xs;
             float ax = m[j], ay = m[N + j], az = m[2 * N + j];
             if (mref) { ax -= mref[j]; ay -= mref[N + j]; az -= mref[2 * N + j]; }
-            const float* k = K.n[(dy + 2) * 5 + dx + 2];
+            const float* k = K.n[(dy + kNearR) * kNearW + dx + kNearR];
             hx += k[0] * ax + k[3] * ay;
             hy += k[3] * ax + k[1] * ay;
             hz += k[2] * az;
@@ -58,7 +59,7 @@ __global__ void near_demag_kernel(const float* __restrict__ m, const float* __re
 static void near_launch(mm_ctx* c, const float* m, const float* mref, const NearKernel& K, float scale, float* out) {
     const int nx = c->grid.nx, ny = c->grid.ny;
     dim3 blk(32, 8), grd((nx + 31) / 32, (ny + 7) / 8);
-    LaunchScope ls(c, "near_demag", 36.0 * nx * ny);
+    LaunchScope ls(c, "near_demag", (mref ? 36.0 : 24.0) * nx * ny);
     near_demag_kernel<<<grd, blk, 0, c->stream>>>(m, mref, nx, ny, K, scale, out);
 }
 
@@ -146,19 +147,19 @@ static mm_status ensure_surrogate(mm_ctx* c) {
         return cuda_check(c, e, "surrogate parameters");
     }
     // near-field Newell entries (FP64 on the GPU, same evaluation as the setup)
-    std::vector<int> ijk(75);
-    std::vector<double> nv(150);
-    for (int dy = -2; dy <= 2; ++dy)
-        for (int dx = -2; dx <= 2; ++dx) {
-            const int q = (dy + 2) * 5 + dx + 2;
+    std::vector<int> ijk(3 * kNearTaps);
+    std::vector<double> nv(6 * kNearTaps);
+    for (int dy = -kNearR; dy <= kNearR; ++dy)
+        for (int dx = -kNearR; dx <= kNearR; ++dx) {
+            const int q = (dy + kNearR) * kNearW + dx + kNearR;
             ijk[3 * q] = dx; ijk[3 * q + 1] = dy; ijk[3 * q + 2] = 0;
         }
-    mm_status ns = newell_gpu(25, ijk.data(), c->grid.dx, c->grid.dy, c->grid.dz, nv.data());
+    mm_status ns = newell_gpu(kNearTaps, ijk.data(), c->grid.dx, c->grid.dy, c->grid.dz, nv.data());
     if (ns != MM_OK) {
         sfree(s);
         return set_error(c, ns, "near-field Newell entries");
     }
-    for (int q = 0; q < 25; ++q) {
+    for (int q = 0; q < kNearTaps; ++q) {
         s->near.n[q][0] = (float)nv[6 * q + 0];
         s->near.n[q][1] = (float)nv[6 * q + 1];
         s->near.n[q][2] = (float)nv[6 * q + 2];

@@ -131,9 +131,10 @@ def test_training_and_surrogate_stepping():
 
 
 def _near_field(mm, grid, dm):
-    """sum over |dx|, |dy| <= 2 of N(d) dm(r - d) with the library's Newell
+    """sum over |dx|, |dy| <= 5 of N(d) dm(r - d) with the library's Newell
     entries (the fixed near-field part of the surrogate's prediction)."""
-    ijk = np.array([[dx, dy, 0] for dy in range(-2, 3) for dx in range(-2, 3)], dtype=np.int32)
+    R = 5
+    ijk = np.array([[dx, dy, 0] for dy in range(-R, R + 1) for dx in range(-R, R + 1)], dtype=np.int32)
     Nd = mm.mm_newell(ijk, (grid.dx, grid.dy, grid.dz))
     d = dm[:, 0]
     out = np.zeros_like(d)
