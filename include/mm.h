@@ -290,18 +290,20 @@ typedef struct mm_surrogate_stats {
     double last_error;          /* max|H_pred - H_exact| / max|H_exact| at the last refresh */
     double max_error;
     double train_loss;          /* last training loss */
-    double c_in;
+    double c_in;                /* network input scale (input = c_in dm) */
+    double c_out;               /* network output scale (output = c_out dH_far / Ms) */
 } mm_surrogate_stats;
 
 /* Generate (dm, H_demag(dm)) pairs with the exact FFT path from a relaxation
  * started at the current state (the state is restored afterwards) and train
  * the network with the library's own BF16 forward/backward kernels and Adam.
  * Prediction model between exact refreshes:
- *   H(m) = H_ref - Ms N_near * dm + Ms CNN(c_in dm) / c_in,  dm = m - m_ref,
+ *   H(m) = H_ref - Ms N_near * dm + Ms CNN(c_in dm) / c_out,  dm = m - m_ref,
  * where N_near is the exact Newell tensor on in-plane displacements
  * |dx|, |dy| <= 5 (a fixed convolution) and the network is trained on what
- * it leaves over, c_in (H_demag(dm) + Ms N_near * dm) / Ms, with
- * c_in = 1 / rms(dm) of the training pairs.  final_loss may be NULL. */
+ * it leaves over, c_out (H_demag(dm) + Ms N_near * dm) / Ms, with
+ * c_in = 1 / rms(dm) and c_out = 1 / rms of that remainder over the
+ * training pairs.  final_loss may be NULL. */
 MM_API mm_status mm_surrogate_train(mm_ctx* ctx, const mm_train_cfg* cfg, double* final_loss);
 
 /* k >= 1: every k-th attempted step refreshes (m_ref, H_ref) with the exact
@@ -313,7 +315,8 @@ MM_API mm_status mm_surrogate_get_stats(mm_ctx* ctx, mm_surrogate_stats* st);
 
 /* Network parameters as n doubles in layer order (w0 [32][3][5][5], b0,
  * w1 [32][32][5][5], b1, w2, b2, w3 [3][32][5][5], b3; 56099 values).  get
- * or set may be NULL; c_in (in/out, may be NULL) is the input scale. */
+ * or set may be NULL; c_in (in/out, may be NULL) is the input scale; setting
+ * weights also sets the output scale c_out to c_in. */
 MM_API mm_status mm_surrogate_weights(mm_ctx* ctx, double* get, const double* set, size_t n, double* c_in);
 
 /* Network on host data: x [B][3][H][W] -> y [B][3][H][W] (raw network output),

@@ -161,6 +161,7 @@ static void invalidate_graph(mm_ctx* c) {
     c->graph = nullptr;
     c->graph1 = nullptr;
     c->graph_chunk = 0;
+    surrogate_invalidate_graph(c);
 }
 
 static mm_status sync_state(mm_ctx* c) {
@@ -688,6 +689,23 @@ static mm_status capture_attempts(mm_ctx* c, int n, cudaGraphExec_t* out, long l
     return MM_OK;
 }
 
+// One attempt from the graph *g (captured on first use with the context's
+// current settings); eager launches while profiling.
+mm_status mm::attempt_graph_launch(mm_ctx* c, cudaGraphExec_t* g, long long* launches) {
+    if (c->profiling) {
+        launch_attempts(c, 1);
+        return cuda_check(c, cudaGetLastError(), "launch");
+    }
+    if (!*g) {
+        mm_status s = capture_attempts(c, 1, g, launches);
+        if (s != MM_OK) return s;
+    }
+    cudaError_t e = cudaGraphLaunch(*g, c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "graph launch");
+    c->launches += *launches;
+    return MM_OK;
+}
+
 static mm_status run_attempts(mm_ctx* c, long long n_attempts) {
     if (c->profiling) {
         launch_attempts(c, (int)n_attempts);
@@ -756,23 +774,29 @@ static mm_status advance(mm_ctx* c, long long add_steps, double t_end, int repla
     s = ensure_k1(c);
     if (s != MM_OK) return s;
     const bool heun = c->integrator == MM_HEUN;
-    if (surrogate_stepping(c)) {
-        // host-driven blocks: exact refresh (with the error monitor) + k-1 network attempts
+    if (surrogate_stepping(c) && !surrogate_fallen_back(c)) {
+        // host-driven blocks: exact refresh (with the error monitor) + k-1
+        // network attempts; after a fallback the exact loop below takes over
+        bool done = false;
         for (int round = 0; round < 100000000; ++round) {
             s = surrogate_block(c);
             if (s != MM_OK) return s;
             s = sync_state(c);
             if (s != MM_OK) return s;
-            if (c->h_state.status) break;
-            if (add_steps >= 0 && c->h_state.accepted >= c->h_state.target) break;
-            if (add_steps < 0 && !(c->h_state.t < t_end)) break;
+            if (c->h_state.status) { done = true; break; }
+            if (add_steps >= 0 && c->h_state.accepted >= c->h_state.target) { done = true; break; }
+            if (add_steps < 0 && !(c->h_state.t < t_end)) { done = true; break; }
+            if (surrogate_fallen_back(c)) break;
         }
-        if (replay) {
-            c->h_state.replay = 0;
-            push_state(c);
+        if (done) {
+            if (replay) {
+                c->h_state.replay = 0;
+                push_state(c);
+            }
+            return status_from_device(c);
         }
-        return status_from_device(c);
     }
+    const long long attempts0 = c->h_state.attempts;
     for (int round = 0; round < 1000000; ++round) {
         long long want;
         if (add_steps >= 0) {
@@ -793,6 +817,7 @@ static mm_status advance(mm_ctx* c, long long add_steps, double t_end, int repla
         if (add_steps >= 0 && c->h_state.accepted >= c->h_state.target) break;
         if (add_steps < 0 && !(c->h_state.t < t_end)) break;
     }
+    if (surrogate_stepping(c)) surrogate_count_exact(c, c->h_state.attempts - attempts0);
     if (replay) {
         c->h_state.replay = 0;
         push_state(c);

@@ -189,6 +189,10 @@ struct LaunchScope {
 mm_status demag_setup(mm_ctx* c);
 void demag_free(mm_ctx* c);
 void demag_apply(mm_ctx* c, const void* m, void* Hd);   // Hd = H_demag(m)
+// FP32 RK45 stage s fused into the X pass: forms m_s = m0 + sum (dt a_sj) k_j
+// into d_mtmp while transforming it, then Hd = H_demag(m_s)
+bool demag_stage_fusable(const mm_ctx* c);
+void demag_apply_stage(mm_ctx* c, int stage, void* Hd);
 mm_status newell_gpu(long count, const int* ijk, double dx, double dy, double dz, double* out_host);
 
 // field.cu
@@ -219,6 +223,10 @@ int batch_class_of(BatchHost* b, int r);
 // surrogate.cu
 void surrogate_free(mm_ctx* c);
 bool surrogate_active(mm_ctx* c);           // this evaluation uses the network
+bool surrogate_fallen_back(mm_ctx* c);      // the monitor switched to exact evaluations
+void surrogate_count_exact(mm_ctx* c, long long attempts);   // exact attempts after a fallback
+void surrogate_invalidate_graph(mm_ctx* c); // drop the captured network attempt
+mm_status attempt_graph_launch(mm_ctx* c, cudaGraphExec_t* g, long long* launches);
 bool surrogate_stepping(mm_ctx* c);         // surrogate-accelerated stepping is on
 void surrogate_apply(mm_ctx* c, const void* m, void* Hd);
 mm_status surrogate_block(mm_ctx* c);       // one exact refresh + k-1 network attempts

@@ -49,6 +49,12 @@ struct XArgs {
     const uint8_t* region;
     const Region<T>* lut;
     long long cells_per_comp;  // N: row r belongs to component r / (N/nx)
+    // fused RK stage (FP32 warp R2C, stage >= 1): the input rows are
+    // m_s = m0 + sum_j (dt a_sj) k_j, formed here and also written to ms
+    const DevState* st;
+    T* const* kptr;
+    const T* m0;
+    T* ms;
 };
 
 template <typename T>
@@ -313,9 +319,33 @@ __global__ void __launch_bounds__(256) fft_x_c2r_direct_kernel(XArgs<float> a) {
 // writes the real row.
 constexpr int kXW = 8;   // warps (rows) per CTA
 
-template <int LT>
+// Slot of stage j's slope under the first-same-as-last rotation (slots 0
+// and 6 swap roles between steps).
+__device__ __forceinline__ int stage_slot(int j, int k_first) {
+    return j == 0 ? k_first : j == 6 ? 6 - k_first : j;
+}
+
+// m_s = m0 + sum_{j<S} (dt a_sj) k_j at the float2 pair starting at q
+template <int S>
+__device__ __forceinline__ float2 stage_pair(const XArgs<float>& a, const float* cf, int kf, long long q) {
+    float2 acc = __ldg(reinterpret_cast<const float2*>(a.m0 + q));
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+        if (j == 1 && S == 6) continue;             // a_7,2 = 0
+        const float2 k = __ldg(reinterpret_cast<const float2*>(a.kptr[stage_slot(j, kf)] + q));
+        acc.x += cf[j] * k.x;
+        acc.y += cf[j] * k.y;
+    }
+    return acc;
+}
+
+// S = 0: rows of a.in.  S >= 1 (RK45 stage S, nx even): rows of the stage
+// state formed from m0 and the slopes, which is also stored to a.ms; the
+// whole launch is a no-op when the attempt is inactive.
+template <int LT, int S>
 __global__ void __launch_bounds__(32 * kXW) fft_x_r2c_warp_kernel(XArgs<float> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (S > 0 && !a.st->active) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = blockIdx.x * kXW + warp;
     if (row >= a.rows) return;                  // whole warp: no CTA barrier below
@@ -324,13 +354,19 @@ __global__ void __launch_bounds__(32 * kXW) fft_x_r2c_warp_kernel(XArgs<float> a
     const int nin = (a.nx + 1) / 2;
     const long long g0 = (long long)row * a.in_pitch;
     const bool vec2 = (a.nx % 2 == 0) && (a.in_pitch % 2 == 0);
+    const float* cf = S > 0 ? a.st->cf32[S] : nullptr;
+    const int kf = S > 0 ? a.st->k_first : 0;
     auto load_in = [&](int n) {
         float2 z = make_float2(0.f, 0.f);
         if (n < nin) {
             const long long q = g0 + 2 * n;
             const bool has_y = 2 * n + 1 < a.nx;
-            if (vec2) z = *reinterpret_cast<const float2*>(a.in + q);
-            else {
+            if constexpr (S > 0) {
+                z = stage_pair<S>(a, cf, kf, q);
+                *reinterpret_cast<float2*>(a.ms + q) = z;
+            } else if (vec2) {
+                z = *reinterpret_cast<const float2*>(a.in + q);
+            } else {
                 z.x = a.in[q];
                 z.y = has_y ? a.in[q + 1] : 0.f;
             }
@@ -888,11 +924,27 @@ static CKern<T> col_kernel(int L) {
 
 static XKern<float> x_warp_kernel(bool fwd, int Lh) {
     switch (Lh) {
-#define MM_CASE(n) case n: return fwd ? fft_x_r2c_warp_kernel<n> : fft_x_c2r_warp_kernel<n>;
+#define MM_CASE(n) case n: return fwd ? fft_x_r2c_warp_kernel<n, 0> : fft_x_c2r_warp_kernel<n>;
         MM_CASE(192) MM_CASE(256) MM_CASE(512)
 #undef MM_CASE
         default: return nullptr;
     }
+}
+
+// R2C fused with RK45 stage s (1..6); null where the warp path does not apply
+static XKern<float> x_stage_kernel(int s, int Lh) {
+#define MM_ST(n) \
+    case n: { \
+        static XKern<float> const t[7] = {nullptr, fft_x_r2c_warp_kernel<n, 1>, fft_x_r2c_warp_kernel<n, 2>, \
+                                          fft_x_r2c_warp_kernel<n, 3>, fft_x_r2c_warp_kernel<n, 4>, \
+                                          fft_x_r2c_warp_kernel<n, 5>, fft_x_r2c_warp_kernel<n, 6>}; \
+        return (s >= 1 && s <= 6) ? t[s] : nullptr; \
+    }
+    switch (Lh) {
+        MM_ST(192) MM_ST(256) MM_ST(512)
+        default: return nullptr;
+    }
+#undef MM_ST
 }
 
 using YKern = void (*)(YArgs<float>);
@@ -923,8 +975,14 @@ static size_t zconv_reg_smem(int L) { return (size_t)(L + 3 * L * kZT) * sizeof(
 template <typename T>
 static void launch_x(mm_ctx* c, bool forward, const T* in, T* out_real, cplx<T>* spec, int rows,
                      int rows_per_plane, int spec_rows_per_plane, int nx, long long in_pitch, int Lh,
-                     const cplx<T>* tw, bool scale_ms, long long cells_per_comp) {
+                     const cplx<T>* tw, bool scale_ms, long long cells_per_comp, int stage = 0) {
     XArgs<T> a{};
+    if (stage > 0) {
+        a.st = c->d_state;
+        a.kptr = (T* const*)c->d_kslot;
+        a.m0 = (const T*)c->d_m;
+        a.ms = (T*)c->d_mtmp;
+    }
     a.in = in;
     a.out_real = out_real;
     a.spec = spec;
@@ -948,6 +1006,15 @@ static void launch_x(mm_ctx* c, bool forward, const T* in, T* out_real, cplx<T>*
     }
     a.cells_per_comp = cells_per_comp;
     if constexpr (sizeof(T) == 4) {
+        if (stage > 0) {
+            // stage s reads m0 and the s slopes (s - 1 at stage 7), writes m_s and the spectrum
+            const double reads = (double)(1 + stage - (stage == 6 ? 1 : 0));
+            const size_t smem = (size_t)kXW * wline(Lh) * sizeof(float2);
+            LaunchScope ls(c, "fft_x_r2c_stage",
+                           (double)rows * ((reads + 1.0) * nx * sizeof(T) + (Lh + 1) * sizeof(cplx<T>)));
+            x_stage_kernel(stage, Lh)<<<(rows + kXW - 1) / kXW, 32 * kXW, smem, c->stream>>>(a);
+            return;
+        }
         if (XKern<float> wk = x_warp_kernel(forward, Lh)) {
             const size_t smem = (size_t)kXW * wline(Lh) * sizeof(float2);
             LaunchScope ls(c, forward ? "fft_x_r2c" : "fft_x_c2r",
@@ -991,7 +1058,7 @@ static void launch_y_direct(mm_ctx* c, bool fwd, cplx<float>* S, long long plane
 }
 
 template <typename T>
-static void demag_apply_t(mm_ctx* c, const T* m, T* Hd) {
+static void demag_apply_t(mm_ctx* c, const T* m, T* Hd, int stage = 0) {
     DemagPlan& d = c->dm;
     const mm_grid& g = c->grid;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -1001,7 +1068,8 @@ static void demag_apply_t(mm_ctx* c, const T* m, T* Hd) {
     const long long N = c->N;
     const double cplxb = sizeof(cplx<T>), realb = sizeof(T);
     // X forward: rows (c, z, y) of Ms*m
-    launch_x<T>(c, true, m, nullptr, S, 3 * nz * ny, ny, d.PyA, nx, nx, d.Lh, (const cplx<T>*)d.tw_x, true, N);
+    launch_x<T>(c, true, m, nullptr, S, 3 * nz * ny, ny, d.PyA, nx, nx, d.Lh, (const cplx<T>*)d.tw_x, true, N,
+                stage);
     const bool three_d = nz > 1;
     const bool fast_y = sizeof(T) == 4 && three_d && y_direct_kernel(true, d.Py) != nullptr;
     const bool fast_z = sizeof(T) == 4 && three_d && zconv_reg_kernel(d.Pz, false) != nullptr;
@@ -1068,6 +1136,14 @@ static void demag_apply_t(mm_ctx* c, const T* m, T* Hd) {
 void demag_apply(mm_ctx* c, const void* m, void* Hd) {
     if (c->prec == 32) demag_apply_t<float>(c, (const float*)m, (float*)Hd);
     else demag_apply_t<double>(c, (const double*)m, (double*)Hd);
+}
+
+bool demag_stage_fusable(const mm_ctx* c) {
+    return c->prec == 32 && c->dm.on && c->grid.nx % 2 == 0 && x_stage_kernel(1, c->dm.Lh) != nullptr;
+}
+
+void demag_apply_stage(mm_ctx* c, int stage, void* Hd) {
+    demag_apply_t<float>(c, (const float*)c->d_mtmp, (float*)Hd, stage);
 }
 
 template <typename T>
@@ -1206,6 +1282,8 @@ static cudaError_t fast_attributes() {
     for (int L : {192, 256, 512}) {
         if (e == cudaSuccess) e = smem_attr(x_warp_kernel(true, L));
         if (e == cudaSuccess) e = smem_attr(x_warp_kernel(false, L));
+        for (int st = 1; st <= 6; ++st)
+            if (e == cudaSuccess) e = smem_attr(x_stage_kernel(st, L));
     }
     return e;
 }

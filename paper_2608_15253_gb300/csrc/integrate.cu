@@ -229,8 +229,11 @@ static void rk45_attempt_t(mm_ctx* c) {
     T* const* kp = (T* const*)c->d_kslot;
     const unsigned terms = c->terms;
     const bool demag = c->dm.on && (terms & MM_TERM_DEMAG);
+    const bool fused = demag && sizeof(T) == 4 && !surrogate_active(c) && demag_stage_fusable(c);
     for (int s = 1; s < 7; ++s) {
-        {
+        if (fused) {
+            demag_apply_stage(c, s, c->d_hd);
+        } else {
             LaunchScope ls(c, "rk_combine", (double)sizeof(T) * n3 * (1 + s + (s == 6 ? 0 : 1)));
             static void (*const kern[7])(const DevState*, T* const*, const T*, T*, long long) = {
                 nullptr, combine_kernel<T, 1>, combine_kernel<T, 2>, combine_kernel<T, 3>,
@@ -250,7 +253,7 @@ static void rk45_attempt_t(mm_ctx* c) {
                 kern[s]<<<nb3, tb, 0, c->stream>>>(c->d_state, kp, (const T*)c->d_m, (T*)c->d_mtmp, n3);
             }
         }
-        if (demag) demag_eval(c, c->d_mtmp, c->d_hd);
+        if (demag && !fused) demag_eval(c, c->d_mtmp, c->d_hd);
         // stages 2..6 own fixed slots; the FSAL stage 7 slope goes to the slot
         // that does not hold k1 (resolved on the device)
         field_launch(c, MODE_K, terms, c->d_mtmp, demag ? c->d_hd : nullptr, s < 6 ? c->d_k[s] : nullptr, nullptr,

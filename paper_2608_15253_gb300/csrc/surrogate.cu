@@ -27,24 +27,44 @@ struct NearKernel {
 
 // out += scale * sum_d N(d) (m - mref)(r - d) over source cells inside the
 // grid; mref may be null (m is already an increment).  The tensor table
-// is a launch parameter (kNearTaps x 4 floats).
-__global__ void near_demag_kernel(const float* __restrict__ m, const float* __restrict__ mref, int nx, int ny,
-                                  NearKernel K, float scale, float* __restrict__ out) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= nx || y >= ny) return;
+// is a launch parameter (kNearTaps x 4 floats).  A CTA stages its output
+// tile plus a kNearR halo of the increment in shared memory (zero outside
+// the grid), so each source value is read from global memory once per tile.
+constexpr int kNearTX = 32, kNearTY = 8;
+constexpr int kNearSX = kNearTX + 2 * kNearR, kNearSY = kNearTY + 2 * kNearR;
+
+__global__ void __launch_bounds__(kNearTX * kNearTY) near_demag_kernel(const float* __restrict__ m,
+                                                                       const float* __restrict__ mref, int nx,
+                                                                       int ny, NearKernel K, float scale,
+                                                                       float* __restrict__ out) {
+    __shared__ float sd[3][kNearSY][kNearSX];
     const long long N = (long long)nx * ny;
+    const int x0 = blockIdx.x * kNearTX - kNearR, y0 = blockIdx.y * kNearTY - kNearR;
+    const int tid = threadIdx.y * kNearTX + threadIdx.x;
+    for (int q = tid; q < kNearSX * kNearSY; q += kNearTX * kNearTY) {
+        const int sx = q % kNearSX, sy = q / kNearSX;
+        const int xs = x0 + sx, ys = y0 + sy;
+        float ax = 0.f, ay = 0.f, az = 0.f;
+        if (xs >= 0 && xs < nx && ys >= 0 && ys < ny) {
+            const long long j = (long long)ys * nx + xs;
+            ax = m[j]; ay = m[N + j]; az = m[2 * N + j];
+            if (mref) { ax -= mref[j]; ay -= mref[N + j]; az -= mref[2 * N + j]; }
+        }
+        sd[0][sy][sx] = ax; sd[1][sy][sx] = ay; sd[2][sy][sx] = az;
+    }
+    __syncthreads();
+    const int x = blockIdx.x * kNearTX + threadIdx.x, y = blockIdx.y * kNearTY + threadIdx.y;
+    if (x >= nx || y >= ny) return;
     float hx = 0.f, hy = 0.f, hz = 0.f;
+    // source (x - dx, y - dy) sits at shared (tx + kNearR - dx, ty + kNearR - dy)
+#pragma unroll 1
     for (int dy = -kNearR; dy <= kNearR; ++dy) {
-        const int ys = y - dy;
-        if (ys < 0 || ys >= ny) continue;
+        const int sy = threadIdx.y + kNearR - dy;
 #pragma unroll
         for (int dx = -kNearR; dx <= kNearR; ++dx) {
-            const int xs = x - dx;
-            if (xs < 0 || xs >= nx) continue;
-            const long long j = (long long)ys * nx + xs;
-            float ax = m[j], ay = m[N + j], az = m[2 * N + j];
-            if (mref) { ax -= mref[j]; ay -= mref[N + j]; az -= mref[2 * N + j]; }
+            const int sx = threadIdx.x + kNearR - dx;
             const float* k = K.n[(dy + kNearR) * kNearW + dx + kNearR];
+            const float ax = sd[0][sy][sx], ay = sd[1][sy][sx], az = sd[2][sy][sx];
             hx += k[0] * ax + k[3] * ay;
             hy += k[3] * ax + k[1] * ay;
             hz += k[2] * az;
@@ -58,7 +78,7 @@ __global__ void near_demag_kernel(const float* __restrict__ m, const float* __re
 
 static void near_launch(mm_ctx* c, const float* m, const float* mref, const NearKernel& K, float scale, float* out) {
     const int nx = c->grid.nx, ny = c->grid.ny;
-    dim3 blk(32, 8), grd((nx + 31) / 32, (ny + 7) / 8);
+    dim3 blk(kNearTX, kNearTY), grd((nx + kNearTX - 1) / kNearTX, (ny + kNearTY - 1) / kNearTY);
     LaunchScope ls(c, "near_demag", (mref ? 36.0 : 24.0) * nx * ny);
     near_demag_kernel<<<grd, blk, 0, c->stream>>>(m, mref, nx, ny, K, scale, out);
 }
@@ -71,7 +91,8 @@ struct SurrogateHost {
     int off_w[4], off_b[4];
     float *d_p = nullptr, *d_g = nullptr, *d_m = nullptr, *d_v = nullptr;
     int adam_t = 0;
-    float c_in = 1.f;
+    float c_in = 1.f;       // network input  = c_in dm
+    float c_out = 1.f;      // network output = c_out (far-field increment) / Ms
     bool have_weights = false;
     __nv_bfloat16 *wpk[4] = {}, *wpkT[4] = {}, *wplain[4] = {};
     float* biasp[4] = {};       // bias zero-padded to the layer's padded output channels
@@ -90,11 +111,14 @@ struct SurrogateHost {
     float* d_mref = nullptr;
     float* d_href = nullptr;
     double* d_red = nullptr;
-    NearKernel near{};      // exact Newell tensor on the 5x5 in-plane neighbourhood
+    NearKernel near{};      // exact Newell tensor on the in-plane near neighbourhood
+    cudaGraphExec_t g_attempt = nullptr;   // one network-evaluated attempt
+    long long g_launches = 0;
 };
 
 static void sfree(SurrogateHost* s) {
     if (!s) return;
+    if (s->g_attempt) cudaGraphExecDestroy(s->g_attempt);
     void* ptrs[] = {s->d_p, s->d_g, s->d_m, s->d_v, s->x0, s->h1, s->h2, s->h3, s->dy, s->dza, s->dzb,
                     s->y, s->t, s->d_loss, s->d_err, s->d_mref, s->d_href, s->d_red};
     for (void* p : ptrs) cudaFree(p);
@@ -169,9 +193,23 @@ static mm_status ensure_surrogate(mm_ctx* c) {
     return MM_OK;
 }
 
+void surrogate_invalidate_graph(mm_ctx* c) {
+    if (c->surr && c->surr->g_attempt) {
+        cudaGraphExecDestroy(c->surr->g_attempt);
+        c->surr->g_attempt = nullptr;
+    }
+}
+
+bool surrogate_fallen_back(mm_ctx* c) { return c->surr && c->surr->fallback; }
+
+void surrogate_count_exact(mm_ctx* c, long long attempts) {
+    if (c->surr && attempts > 0) c->surr->n_exact += 6 * attempts;
+}
+
 static mm_status ensure_buffers(mm_ctx* c, int B, int H, int W) {
     SurrogateHost* s = c->surr;
     if (B <= s->cB && H == s->cH && W == s->cW) return MM_OK;
+    surrogate_invalidate_graph(c);   // the captured attempt holds the old buffers
     void* ptrs[] = {s->x0, s->h1, s->h2, s->h3, s->dy, s->dza, s->dzb, s->y, s->t};
     for (void* p : ptrs) cudaFree(p);
     const size_t pp = (size_t)B * (H + 4) * (W + 4);
@@ -325,7 +363,7 @@ __global__ void sumsq_kernel(const float* __restrict__ a, long long n, double* _
 
 // crop windows: item b takes field p = idx[3b] at offsets (idx[3b+1], idx[3b+2])
 __global__ void crop_kernel(const float* __restrict__ dm, const float* __restrict__ dh, long long field_elems,
-                            int nx, int ny, const int* __restrict__ idx, int B, int S, float c_in, float inv_ms,
+                            int nx, int ny, const int* __restrict__ idx, int B, int S, float c_in, float t_scale,
                             __nv_bfloat16* __restrict__ x0, float* __restrict__ t) {
     const long long n = (long long)B * S * S;
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -342,7 +380,7 @@ __global__ void crop_kernel(const float* __restrict__ dm, const float* __restric
     float* tt = t + (((long long)b * S + i) * S + j) * 3;
     for (int cc = 0; cc < 3; ++cc) {
         d[cc] = __float2bfloat16_rn(c_in * f[cc * N + cell]);
-        tt[cc] = c_in * inv_ms * g[cc * N + cell];
+        tt[cc] = t_scale * g[cc * N + cell];
     }
 }
 
@@ -367,7 +405,7 @@ __global__ void err_max_kernel(const float* __restrict__ a, const float* __restr
     }
 }
 
-// H_pred(m) = H_ref - Ms N_near * (m - m_ref) + Ms * CNN(c_in (m - m_ref)) / c_in into Hd
+// H_pred(m) = H_ref - Ms N_near * (m - m_ref) + Ms * CNN(c_in (m - m_ref)) / c_out into Hd
 void surrogate_apply(mm_ctx* c, const void* m, void* Hd) {
     SurrogateHost* s = c->surr;
     const int H = c->grid.ny, W = c->grid.nx;
@@ -376,11 +414,12 @@ void surrogate_apply(mm_ctx* c, const void* m, void* Hd) {
         LaunchScope ls(c, "cnn_input", 24.0 * N);
         cnn_dm_to_input(c->stream, (const float*)m, s->d_mref, H, W, s->c_in, s->x0);
     }
-    run_forward(c, 1, H, W, 1.f / s->c_in, 0);
-    LaunchScope ls(c, "cnn_output", 36.0 * N);
-    cnn_field_from_output(c->stream, s->y, s->d_href, N, (float)c->regions[0].Ms, (float*)Hd);
+    run_forward(c, 1, H, W, 1.f / s->c_out, 0);
+    {
+        LaunchScope ls(c, "cnn_output", 36.0 * N);
+        cnn_field_from_output(c->stream, s->y, s->d_href, N, (float)c->regions[0].Ms, (float*)Hd);
+    }
     near_launch(c, (const float*)m, s->d_mref, s->near, -(float)c->regions[0].Ms, (float*)Hd);
-    s->n_surr++;
 }
 
 bool surrogate_active(mm_ctx* c) { return c->surr && c->surr->use_now; }
@@ -407,6 +446,7 @@ mm_status surrogate_block(mm_ctx* c) {
     if (s->ref_valid) {
         // monitor: the network's prediction at the current state vs the exact field
         surrogate_apply(c, c->d_m, c->d_hbuf);
+        s->n_surr++;
         demag_apply(c, c->d_m, c->d_hd);
         cudaMemsetAsync(s->d_red, 0, sizeof(double) * 2, c->stream);
         err_max_kernel<<<304, 256, 0, c->stream>>>((const float*)c->d_hbuf, (const float*)c->d_hd, 3 * N, s->d_red);
@@ -427,12 +467,17 @@ mm_status surrogate_block(mm_ctx* c) {
     s->n_refresh++;
     s->n_exact++;
     s->use_now = false;
-    rk45_attempt(c);
+    mm_status st = attempt_graph_launch(c, &c->graph1, &c->launches_per_attempt);
+    if (st != MM_OK) return st;
     s->n_exact += 6;
     for (int q = 1; q < s->k && !s->fallback; ++q) {
+        // the network attempt is captured once (its scales are launch
+        // parameters: retraining or new weights drop the graph)
         s->use_now = true;
-        rk45_attempt(c);
+        st = attempt_graph_launch(c, &s->g_attempt, &s->g_launches);
         s->use_now = false;
+        if (st != MM_OK) return st;
+        s->n_surr += 6;
     }
     return cuda_check(c, cudaGetLastError(), "surrogate block");
 }
@@ -459,7 +504,8 @@ mm_status mm_surrogate_weights(mm_ctx* c, double* get, const double* set, size_t
         cudaMemset(s->d_v, 0, sizeof(float) * s->np);
         s->adam_t = 0;
         s->have_weights = true;
-        if (c_in) s->c_in = (float)*c_in;
+        if (c_in) s->c_in = s->c_out = (float)*c_in;
+        surrogate_invalidate_graph(c);
         pack_all(c);
     } else if (!s->have_weights) {
         set_he_init(c, 1);
@@ -587,6 +633,15 @@ mm_status mm_surrogate_train(mm_ctx* c, const mm_train_cfg* cfg, double* final_l
     if (e != cudaSuccess) { cudaFree(dm); cudaFree(dh); return cuda_check(c, e, "training data"); }
     const double rms = std::sqrt(ss / (double)(fe * np));
     s->c_in = rms > 0 ? (float)(1.0 / rms) : 1.f;
+    // output scale: unit rms targets (the far-field residual is much smaller than dm)
+    cudaMemsetAsync(s->d_red, 0, sizeof(double), c->stream);
+    sumsq_kernel<<<304, 256, 0, c->stream>>>(dh, fe * np, s->d_red);
+    double sr = 0;
+    cudaMemcpyAsync(&sr, s->d_red, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) { cudaFree(dm); cudaFree(dh); return cuda_check(c, e, "training targets"); }
+    const double rr = std::sqrt(sr / (double)(fe * np)) / c->regions[0].Ms;
+    s->c_out = rr > 0 ? (float)(1.0 / rr) : 1.f;
     if (!s->have_weights) set_he_init(c, cfg->seed);
     pack_all(c);
     const int B = cfg->batch;
@@ -606,7 +661,7 @@ mm_status mm_surrogate_train(mm_ctx* c, const mm_train_cfg* cfg, double* final_l
         }
         cudaMemcpyAsync(d_idx, idx.data(), sizeof(int) * 3 * B, cudaMemcpyHostToDevice, c->stream);
         crop_kernel<<<(unsigned)((B * (long long)S * S + 255) / 256), 256, 0, c->stream>>>(
-            dm, dh, fe, nx, ny, d_idx, B, S, s->c_in, inv_ms, s->x0, s->t);
+            dm, dh, fe, nx, ny, d_idx, B, S, s->c_in, s->c_out * inv_ms, s->x0, s->t);
         run_forward(c, B, S, S, 1.f, 0);
         cudaMemsetAsync(s->d_loss, 0, sizeof(double), c->stream);
         cnn_mse_grad(c->stream, s->y, s->t, B, S, S, s->dy, s->d_loss);
@@ -625,6 +680,7 @@ mm_status mm_surrogate_train(mm_ctx* c, const mm_train_cfg* cfg, double* final_l
     cudaFree(dh);
     if (e != cudaSuccess) return cuda_check(c, e, "surrogate training");
     s->train_loss = loss;
+    surrogate_invalidate_graph(c);
     if (final_loss) *final_loss = loss;
     s->k = k_saved;
     s->ref_valid = false;
@@ -666,6 +722,7 @@ mm_status mm_surrogate_get_stats(mm_ctx* c, mm_surrogate_stats* out) {
     out->max_error = s->max_err;
     out->train_loss = s->train_loss;
     out->c_in = s->c_in;
+    out->c_out = s->c_out;
     return MM_OK;
 }
 

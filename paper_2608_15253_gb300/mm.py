@@ -73,7 +73,7 @@ class mm_train_cfg(C.Structure):
 class mm_surrogate_stats(C.Structure):
     _fields_ = [("exact_evals", C.c_longlong), ("surrogate_evals", C.c_longlong), ("refreshes", C.c_longlong),
                 ("fallback", C.c_int), ("last_error", C.c_double), ("max_error", C.c_double),
-                ("train_loss", C.c_double), ("c_in", C.c_double)]
+                ("train_loss", C.c_double), ("c_in", C.c_double), ("c_out", C.c_double)]
 
 
 class MMError(RuntimeError):

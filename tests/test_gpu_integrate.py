@@ -26,6 +26,11 @@ CASES = [
      W.Material(Ms=8e5, A=1.3e-11, alpha=0.02), (-24.6e-3, 4.3e-3, 0.0)),
     ("odd", W.Grid(17, 5, 2, 2e-9, 3e-9, 1e-9),
      W.Material(Ms=7e5, A=1.1e-11, alpha=0.3, Ku1=2e5, u=(0.6, 0, 0.8), D=1.5e-3), (0.0, 0.02, 0.01)),
+    # half length 192: the FP32 stage combine runs inside the X pass; granular
+    # regions with holes exercise the per-cell Ms there
+    ("fused", W.Grid(170, 12, 2, 2e-9, 2e-9, 2e-9),
+     W.with_cells(W.Material(Ms=5.8e5, A=1.5e-11, alpha=0.1, Ku1=8e5, u=(0, 0, 1), D=3e-3),
+                  W.random_material_cells(W.Grid(170, 12, 2, 2e-9, 2e-9, 2e-9), 9)), (0.0, 0.0, 0.05)),
 ]
 
 
