@@ -180,6 +180,21 @@ def run_reference(args):
     return 0
 
 
+def aggregate_ranks(ms: float, cell_steps: float, ws: int, device: str):
+    """Whole-job numbers of a replicas-only run: the slowest rank's time and
+    the cell-steps of all ranks (one all-reduce each; no data-path
+    collective exists)."""
+    if ws <= 1:
+        return ms, float(cell_steps)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(cell_steps)], dtype=torch.float64, device=device)
+    dist.all_reduce(c)
+    return float(t.item()), float(c.item())
+
+
 def _timed(stream, fn):
     """Device time (ms) of fn() on `stream`, synchronised on both sides."""
     import torch
@@ -384,15 +399,7 @@ def run_gpu(args):
     steps = s1["accepted"] - s0["accepted"]
     attempts = s1["attempts"] - s0["attempts"]
     launches = s1["kernel_launches"] - s0["kernel_launches"]
-    t_max = ms
-    total_cells_steps = g.n * steps
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-        c = torch.tensor([float(total_cells_steps)], device="cuda")
-        torch.distributed.all_reduce(c)
-        total_cells_steps = float(c.item())
+    t_max, total_cells_steps = aggregate_ranks(ms, g.n * steps, ws, "cuda")
     value = total_cells_steps / (t_max * 1e-3)
 
     # per-kernel CUDA-event timing of the same kind of steps (graphs bypassed)
@@ -449,7 +456,7 @@ def run_gpu(args):
                 "host_buffers": "page-locked float64 [3][z][y][x]"},
     }
     mm.mm_destroy(ctx)
-    if not args.no_variants:
+    if not args.no_variants and rank == 0:
         m0_err = W.m_random_sphere(g, seed=2)
         err, rate = fp32_vs_fp64(mm, stream, w, m0_err)
         line["error_vs_fp64"] = {"max_abs_dm": err, "after_steps": 20, "dt_s": 2e-14,

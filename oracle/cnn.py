@@ -13,7 +13,8 @@ exact FFT convolution.  Convolutions are cross-correlations:
 Parity status: this network has no closed form; its forward pass is pinned
 against scipy's correlate2d and its gradients against finite differences
 of its own loss ("parity unpinned" in physics terms: the surrogate is a
-learned approximation judged against the exact demag field).
+learned approximation whose error is measured against the exact demag
+field).
 """
 from __future__ import annotations
 
