@@ -465,8 +465,11 @@ def run_gpu(args):
         line["fp64"] = {"value": rate[64], "unit": UNIT, "fp32_same_steps": rate[32],
                         "note": "20 replayed RK45 steps of dt 2e-14 s from the same random state"}
         line["variants"] = {}
+        wanted = [v for v in args.variants.split(",") if v]
         for name, fn in (("batched", lambda: variant_batched(mm, stream, args.batch_steps)),
                          ("surrogate", lambda: variant_surrogate(mm, stream, args.surrogate_steps))):
+            if name not in wanted:
+                continue
             try:
                 line["variants"][name] = fn()
             except Exception as e:  # a failed variant is reported, the headline line still prints
@@ -488,7 +491,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", default="", help="nx,ny,nz: a smaller case of the same workload (profiling)")
-    ap.add_argument("--no-variants", action="store_true", help="skip the batched and surrogate lines")
+    ap.add_argument("--no-variants", action="store_true", help="skip the FP64, batched and surrogate lines")
+    ap.add_argument("--variants", default="batched,surrogate", help="comma list of variant lines to run")
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--surrogate-steps", type=int, default=100)
     args = ap.parse_args()

@@ -23,6 +23,7 @@ struct BatchHost {
     RepDev* d_rep = nullptr;
     ClsDev* d_cls = nullptr;
     int* d_order = nullptr;
+    int* d_next = nullptr;     // per-stage work counters
     float2* d_scratch = nullptr;
     long long scratch_stride = 0;
     int nt = 256;
@@ -49,6 +50,7 @@ void batch_free(BatchHost* b) {
     cudaFree(b->d_rep);
     cudaFree(b->d_cls);
     cudaFree(b->d_order);
+    cudaFree(b->d_next);
     cudaFree(b->d_scratch);
     for (auto& p : b->plans) demag_free_plan(p);
     delete b;
@@ -106,14 +108,26 @@ mm_status batch_setup(mm_ctx* c, BatchHost* b, const std::vector<mm_grid>& grids
         b->plans.push_back(p);
         b->cls.push_back(cd);
     }
-    b->order.resize(R);
-    for (int r = 0; r < R; ++r) b->order[r] = r;
-    std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
+    // work order: replicas sorted by size, the largest paired with the
+    // smallest of the head so the CTA-private spectra in flight at any time
+    // stay within L2; the smallest quarter closes the order so the dynamic
+    // schedule ends on short jobs
+    std::vector<int> desc(R);
+    for (int r = 0; r < R; ++r) desc[r] = r;
+    std::stable_sort(desc.begin(), desc.end(), [&](int x, int y) {
         return (long long)b->rep[x].nx * b->rep[x].ny > (long long)b->rep[y].nx * b->rep[y].ny;
     });
+    const int tail = R / 4, head = R - tail;
+    b->order.clear();
+    for (int lo = 0, hi = head - 1; lo <= hi; ++lo, --hi) {
+        b->order.push_back(desc[lo]);
+        if (hi != lo) b->order.push_back(desc[hi]);
+    }
+    for (int q = head; q < R; ++q) b->order.push_back(desc[q]);
     cudaError_t e = cudaMalloc(&b->d_rep, sizeof(RepDev) * R);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_cls, sizeof(ClsDev) * b->cls.size());
     if (e == cudaSuccess) e = cudaMalloc(&b->d_order, sizeof(int) * R);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_next, sizeof(int) * 2);
     if (e != cudaSuccess) return cuda_check(c, e, "batch tables");
     cudaMemcpy(b->d_cls, b->cls.data(), sizeof(ClsDev) * b->cls.size(), cudaMemcpyHostToDevice);
     cudaMemcpy(b->d_order, b->order.data(), sizeof(int) * R, cudaMemcpyHostToDevice);
@@ -154,6 +168,7 @@ static void launch_stage(mm_ctx* c, BatchHost* b, int stage) {
     a.rep = b->d_rep;
     a.cls = b->d_cls;
     a.order = b->d_order;
+    a.next = b->d_next + (stage - 1);
     a.R = (int)b->rep.size();
     a.m0 = (float*)c->d_m;
     a.ms = (float*)c->d_mtmp;
@@ -186,6 +201,7 @@ static void launch_stage(mm_ctx* c, BatchHost* b, int stage) {
     f.eps_p = (float)q.eps_prime;
     double cells = 0;
     for (const RepDev& r : b->rep) cells += (double)r.nx * r.ny;
+    cudaMemsetAsync(a.next, 0, sizeof(int), c->stream);
     LaunchScope ls(c, stage == 1 ? "batch_stage1" : "batch_stage2", cells * (stage == 1 ? 36.0 : 48.0));
     if (b->nt == 512) batch_kernel_launch_512(a, b->blocks, b->smem, c->stream);
     else batch_kernel_launch_256(a, b->blocks, b->smem, c->stream);

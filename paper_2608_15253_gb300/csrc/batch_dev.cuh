@@ -1,8 +1,9 @@
 // Replica batching (Methods, "Replica batching"): R independent thin-film
 // replicas (nz = 1) of possibly different sizes advance together, each with
 // its own Philox key, temperature and current density.  One persistent
-// launch per Heun stage: every CTA takes whole replicas from a
-// largest-first work order and runs, for each, the three demag phases
+// launch per Heun stage: every CTA takes whole replicas, one after another,
+// from a shared work counter over a size-mixed order and runs, for each, the
+// three demag phases
 // (row R2C, column convolution with the size class's tensor spectrum,
 // row C2R) and the fused field + torque + stage update.  The replica's
 // half spectrum lives in a CTA-private scratch slab (small enough to stay
@@ -30,6 +31,9 @@
 
 namespace mm {
 
+// complex values a thread holds per Stockham pass; a multiple of every
+// radix (8, 4, 3, 2) so each pass covers all the butterflies of b_rows_x /
+// b_tk lines
 constexpr int kMaxVB = 24;
 
 struct RepDev {
@@ -52,6 +56,7 @@ struct BatchArgs {
     const RepDev* rep;
     const ClsDev* cls;
     const int* order;
+    int* next;              // work counter of this stage (zeroed before the launch)
     int R;
     float* m0;              // state
     float* ms;              // predictor state
@@ -234,7 +239,14 @@ __global__ void __launch_bounds__(NT) batch_stage_kernel(BatchArgs a) {
     const long long step = a.st->step;
     const float dt = (float)a.st->dt;
     float2* S = a.scratch + blockIdx.x * a.scratch_stride;
-    for (int w = blockIdx.x; w < a.R; w += gridDim.x) {
+    __shared__ int s_w;
+    for (;;) {
+        // dynamic schedule: each CTA takes the next replica of the work order
+        if (threadIdx.x == 0) s_w = atomicAdd(a.next, 1);
+        __syncthreads();
+        const int w = s_w;
+        __syncthreads();
+        if (w >= a.R) break;
         const RepDev rp = a.rep[a.order[w]];
         const ClsDev& cd = a.cls[rp.cls];
         const int key = cd.Lh * 10000 + cd.Py;

@@ -6,7 +6,7 @@ namespace mm {
 template __global__ void batch_stage_kernel<256>(BatchArgs a);
 
 cudaError_t batch_kernel_attributes_256() {
-    return cudaFuncSetAttribute(batch_stage_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    return cudaFuncSetAttribute(batch_stage_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);  // room for the static work slot
 }
 
 void batch_kernel_launch_256(const BatchArgs& a, int blocks, size_t smem, cudaStream_t s) {

@@ -69,21 +69,35 @@ __global__ void __launch_bounds__(256) field_kernel(FieldArgs<T> a) {
     }
 }
 
-// One material, FP32, nx a multiple of 4: each thread owns four consecutive
-// cells of a row.  The state, its y/z neighbours, the demag field and the
-// outputs move as 16-byte vectors; the x neighbours of the inner cells come
-// from the thread's own registers, only the two row-end neighbours are
-// scalar loads.
-__device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
-__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
-__device__ __forceinline__ float f4(const float4& v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
-__device__ __forceinline__ void f4set(float4& v, int q, float x) {
+// One material, FP32, nx a multiple of V (2 or 4): each thread owns V
+// consecutive cells of a row.  The state, its y/z neighbours, the demag
+// field and the outputs move as 8- or 16-byte vectors; the x neighbours of
+// the inner cells come from the thread's own registers, only the two
+// row-end neighbours are scalar loads.
+template <int V> struct fvec;
+template <> struct fvec<2> { using t = float2; };
+template <> struct fvec<4> { using t = float4; };
+
+template <int V>
+__device__ __forceinline__ typename fvec<V>::t ldv(const float* p) {
+    return __ldg(reinterpret_cast<const typename fvec<V>::t*>(p));
+}
+template <int V>
+__device__ __forceinline__ void stv(float* p, const typename fvec<V>::t& v) {
+    *reinterpret_cast<typename fvec<V>::t*>(p) = v;
+}
+__device__ __forceinline__ float fget(const float2& v, int q) { return q == 0 ? v.x : v.y; }
+__device__ __forceinline__ float fget(const float4& v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
+__device__ __forceinline__ void fset(float2& v, int q, float x) { if (q == 0) v.x = x; else v.y = x; }
+__device__ __forceinline__ void fset(float4& v, int q, float x) {
     if (q == 0) v.x = x; else if (q == 1) v.y = x; else if (q == 2) v.z = x; else v.w = x;
 }
 
-__global__ void __launch_bounds__(256) field_vec4_kernel(FieldArgs<float> a) {
+template <int V>
+__global__ void __launch_bounds__(256) field_vec_kernel(FieldArgs<float> a) {
+    using VT = typename fvec<V>::t;
     if (a.gate && !a.st->active) return;
-    const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int x0 = V * (blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x0 >= a.nx || y >= a.ny) return;
@@ -91,12 +105,12 @@ __global__ void __launch_bounds__(256) field_vec4_kernel(FieldArgs<float> a) {
     const long long i0 = ((long long)z * a.ny + y) * a.nx + x0;
     const Region<float>& R = a.R0;
     const long long step = a.step_override >= 0 ? a.step_override : (a.st ? a.st->step : 0);
-    float4 mc[3];
+    VT mc[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) mc[c] = ld4(a.m + c * N + i0);
+    for (int c = 0; c < 3; ++c) mc[c] = ldv<V>(a.m + c * N + i0);
     const bool need_nb = (a.terms & (MM_TERM_EXCHANGE | MM_TERM_DMI)) || a.tq == MM_TORQUE_ZL;
-    // neighbour rows (y-, y+, z-, z+) as vectors, row-end x neighbours as scalars
-    float4 nr[4][3];
+    // neighbour rows (y+, y-, z+, z-) as vectors, row-end x neighbours as scalars
+    VT nr[4][3];
     bool rin[4] = {false, false, false, false};
     float xl[3] = {0, 0, 0}, xr[3] = {0, 0, 0};
     bool lin = false, rinx = false;
@@ -117,10 +131,10 @@ __global__ void __launch_bounds__(256) field_vec4_kernel(FieldArgs<float> a) {
             if (inside) {
                 const long long j = i0 + (long long)(q - ps[s]) * st[s];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) nr[s][c] = ld4(a.m + c * N + j);
+                for (int c = 0; c < 3; ++c) nr[s][c] = ldv<V>(a.m + c * N + j);
             }
         }
-        int ql = x0 - 1, qr = x0 + 4;
+        int ql = x0 - 1, qr = x0 + V;
         lin = ql >= 0;
         rinx = qr < a.nx;
         if (!lin && a.px) { ql += a.nx; lin = true; }
@@ -132,27 +146,27 @@ __global__ void __launch_bounds__(256) field_vec4_kernel(FieldArgs<float> a) {
             if (rinx) xr[c] = __ldg(a.m + c * N + row + qr);
         }
     }
-    float4 hd[3];
+    VT hd[3];
     const bool dem = (a.terms & MM_TERM_DEMAG) && a.Hd;
     if (dem) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) hd[c] = ld4(a.Hd + c * N + i0);
+        for (int c = 0; c < 3; ++c) hd[c] = ldv<V>(a.Hd + c * N + i0);
     }
-    float4 o1[3], o2[3];
+    VT o1[3], o2[3];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const v3<float> m = mk3<float>(f4(mc[0], q), f4(mc[1], q), f4(mc[2], q));
+    for (int q = 0; q < V; ++q) {
+        const v3<float> m = mk3<float>(fget(mc[0], q), fget(mc[1], q), fget(mc[2], q));
         v3<float> nbv[6];
         bool nbp[6];
         float cnb[6];
         if (need_nb) {
             // x+ / x-
-            const bool pp = q < 3 || rinx, pm = q > 0 || lin;
+            const bool pp = q < V - 1 || rinx, pm = q > 0 || lin;
             nbp[0] = pp;
             nbp[1] = pm;
-            nbv[0] = q < 3 ? mk3<float>(f4(mc[0], q + 1), f4(mc[1], q + 1), f4(mc[2], q + 1))
-                           : (rinx ? mk3<float>(xr[0], xr[1], xr[2]) : ghost_value<float>(m, 0, 1, a.hx, R.ratio));
-            nbv[1] = q > 0 ? mk3<float>(f4(mc[0], q - 1), f4(mc[1], q - 1), f4(mc[2], q - 1))
+            nbv[0] = q < V - 1 ? mk3<float>(fget(mc[0], q + 1), fget(mc[1], q + 1), fget(mc[2], q + 1))
+                               : (rinx ? mk3<float>(xr[0], xr[1], xr[2]) : ghost_value<float>(m, 0, 1, a.hx, R.ratio));
+            nbv[1] = q > 0 ? mk3<float>(fget(mc[0], q - 1), fget(mc[1], q - 1), fget(mc[2], q - 1))
                            : (lin ? mk3<float>(xl[0], xl[1], xl[2]) : ghost_value<float>(m, 0, -1, a.hx, R.ratio));
             cnb[0] = pp ? a.c_uniform : R.cg;
             cnb[1] = pm ? a.c_uniform : R.cg;
@@ -160,12 +174,12 @@ __global__ void __launch_bounds__(256) field_vec4_kernel(FieldArgs<float> a) {
             for (int s = 0; s < 4; ++s) {
                 const int slot = 2 + s, d = 1 + s / 2, sg = (s & 1) ? -1 : 1;
                 nbp[slot] = rin[s];
-                nbv[slot] = rin[s] ? mk3<float>(f4(nr[s][0], q), f4(nr[s][1], q), f4(nr[s][2], q))
+                nbv[slot] = rin[s] ? mk3<float>(fget(nr[s][0], q), fget(nr[s][1], q), fget(nr[s][2], q))
                                    : ghost_value<float>(m, d, sg, d == 1 ? a.hy : a.hz, R.ratio);
                 cnb[slot] = rin[s] ? a.c_uniform : R.cg;
             }
         }
-        const v3<float> hq = dem ? mk3<float>(f4(hd[0], q), f4(hd[1], q), f4(hd[2], q)) : mk3<float>(0, 0, 0);
+        const v3<float> hq = dem ? mk3<float>(fget(hd[0], q), fget(hd[1], q), fget(hd[2], q)) : mk3<float>(0, 0, 0);
         v3<float> H, k;
         cell_field_nb<float>(a, i0 + q, R, m, nbv, nbp, cnb, dem, hq, step, H, k, a.mode != MODE_H);
         v3<float> r1 = H, r2 = k;
@@ -182,8 +196,8 @@ __global__ void __launch_bounds__(256) field_vec4_kernel(FieldArgs<float> a) {
             v3<float> mn = m0 + (0.5f * dt) * (k1 + k);
             r1 = (1.0f / sqrtf(dot(mn, mn))) * mn;
         }
-        f4set(o1[0], q, r1.x); f4set(o1[1], q, r1.y); f4set(o1[2], q, r1.z);
-        f4set(o2[0], q, r2.x); f4set(o2[1], q, r2.y); f4set(o2[2], q, r2.z);
+        fset(o1[0], q, r1.x); fset(o1[1], q, r1.y); fset(o1[2], q, r1.z);
+        fset(o2[0], q, r2.x); fset(o2[1], q, r2.y); fset(o2[2], q, r2.z);
     }
     float* o = a.out;
     if (!o) {
@@ -191,12 +205,14 @@ __global__ void __launch_bounds__(256) field_vec4_kernel(FieldArgs<float> a) {
         o = a.kptr[a.kstage == 0 ? kf : 6 - kf];
     }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) st4(o + c * N + i0, o1[c]);
+    for (int c = 0; c < 3; ++c) stv<V>(o + c * N + i0, o1[c]);
     if (a.mode == MODE_HEUN1) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) st4(a.out2 + c * N + i0, o2[c]);
+        for (int c = 0; c < 3; ++c) stv<V>(a.out2 + c * N + i0, o2[c]);
     }
 }
+
+constexpr int kFieldV = 2;   // cells per thread of the one-material FP32 kernel
 
 template <typename T>
 static void field_launch_t(mm_ctx* c, int mode, unsigned terms, const T* m, const T* Hd, T* out, T* out2,
@@ -262,9 +278,9 @@ static void field_launch_t(mm_ctx* c, int mode, unsigned terms, const T* m, cons
         if constexpr (sizeof(T) == 4) { a.R0 = c->r0f; a.c_uniform = c->c00f; }
         else { a.R0 = c->r0d; a.c_uniform = c->c00d; }
         if constexpr (sizeof(T) == 4) {
-            if (g.nx % 4 == 0 && a.R0.present != 0.f) {
-                dim3 grd4((g.nx / 4 + 31) / 32, (g.ny + 7) / 8, g.nz);
-                field_vec4_kernel<<<grd4, blk, 0, c->stream>>>(a);
+            if (g.nx % kFieldV == 0 && a.R0.present != 0.f) {
+                dim3 grdv((g.nx / kFieldV + 31) / 32, (g.ny + 7) / 8, g.nz);
+                field_vec_kernel<kFieldV><<<grdv, blk, 0, c->stream>>>(a);
                 return;
             }
         }
