@@ -89,14 +89,94 @@ __device__ __forceinline__ void col_fft(float2* sm, int nl, int nin, const ClsDe
     else fft_lines<float, DIR>(sm, nl, cd.Py + 1, cd.py, nin, cd.twy, 1);
 }
 
-// One replica, one stage.  LX / LY: compile-time half length / column
-// length (0 = runtime plan).
-template <int LX, int LY, int NT>
-__device__ void replica_stage(const BatchArgs& a, const RepDev& rp, const ClsDev& cd, float2* S, float2* sm,
-                              long long step, float dt) {
-    const int nx = rp.nx, ny = rp.ny;
-    const long long N = (long long)nx * ny;
-    float* mE = (a.stage == 1 ? a.m0 : a.ms) + rp.off;
+// One replica, one stage, in three phases.  Each phase is its own
+// (non-inlined) function so the register allocation of one phase does not
+// burden the others.  LX / LY: compile-time half length / column length
+// (0 = runtime plan).
+
+// phase X: rows (c, y) of Ms*m -> half spectra in S[(c ny + y) Wk + kx]
+template <int LX, int NT>
+__device__ __noinline__ void stage_phase_x(const float* mE, long long N, int nx, int ny, float ms, const ClsDev& cd,
+                                           float2* S, float2* sm) {
+    const int Lh = LX > 0 ? LX : cd.Lh;
+    const int pitch = Lh + 1;
+    float* smr = reinterpret_cast<float*>(sm);
+    // ---- phase X: rows (c, y) -> half spectra in S[(c ny + y) Wk + kx]
+    const int RB = b_rows_x(Lh, NT);
+    for (int r0 = 0; r0 < 3 * ny; r0 += RB) {
+        const int nl = min(RB, 3 * ny - r0);
+        for (int l = 0; l < nl; ++l) {
+            const int row = r0 + l, c = row / ny, y = row - c * ny;
+            const float* src = mE + c * N + (long long)y * nx;
+            for (int q = threadIdx.x; q < 2 * Lh; q += NT) smr[2 * l * pitch + q] = q < nx ? src[q] * ms : 0.f;
+        }
+        __syncthreads();
+        row_fft<LX, NT, 1>(sm, nl, (nx + 1) / 2, cd);
+        for (int l = 0; l < nl; ++l) {
+            float2* out = S + (long long)(r0 + l) * cd.Wk;
+            for (int k = threadIdx.x; k <= Lh; k += NT) {
+                const float2 zk = sm[l * pitch + (k == Lh ? 0 : k)];
+                const float2 zc = cconj<float>(sm[l * pitch + (k == 0 ? 0 : Lh - k)]);
+                const float2 E = cscale<float>(cadd<float>(zk, zc), 0.5f);
+                const float2 O = cscale<float>(mul_mi<float, 1>(csub<float>(zk, zc)), 0.5f);
+                out[k] = cadd<float>(E, cmul<float>(__ldg(&cd.twx[k]), O));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// phase Y: columns, FFT along y, tensor multiply, inverse, keep ny
+template <int LY, int NT>
+__device__ __noinline__ void stage_phase_y(int ny, const ClsDev& cd, float2* S, float2* sm) {
+    const int Py = LY > 0 ? LY : cd.Py;
+    // ---- phase Y: columns, FFT along y, tensor multiply, inverse, keep ny
+    const int TK = b_tk(Py, NT);
+    const int tks = __ffs(TK) - 1;
+    const int cp = Py + 1;
+    for (int kx0 = 0; kx0 < cd.Kx; kx0 += TK) {
+        for (int c = 0; c < 3; ++c)
+            for (int e = threadIdx.x; e < (ny << tks); e += NT) {
+                const int kxl = e & (TK - 1), pt = e >> tks;
+                float2 v = mkc<float>(0.f, 0.f);
+                if (kx0 + kxl < cd.Kx) v = S[(long long)(c * ny + pt) * cd.Wk + kx0 + kxl];
+                sm[(c * TK + kxl) * cp + pt] = v;
+            }
+        __syncthreads();
+        col_fft<LY, NT, 1>(sm, 3 * TK, ny, cd);
+        const long long kcs = (long long)cd.Ky * cd.Wk;
+        for (int e = threadIdx.x; e < (Py << tks); e += NT) {
+            const int kxl = e & (TK - 1), kk = e >> tks;
+            const int kx = kx0 + kxl;
+            if (kx >= cd.Kx) continue;
+            const int kf = kk <= Py / 2 ? kk : Py - kk;
+            const float sy = kk <= Py / 2 ? 1.f : -1.f;
+            const float* K = cd.khat + (long long)kf * cd.Wk + kx;
+            const float kxx = __ldg(K), kyy = __ldg(K + kcs), kzz = __ldg(K + 2 * kcs), kxy = sy * __ldg(K + 3 * kcs);
+            float2* px = &sm[(0 * TK + kxl) * cp + kk];
+            float2* py = &sm[(1 * TK + kxl) * cp + kk];
+            float2* pz = &sm[(2 * TK + kxl) * cp + kk];
+            const float2 mx = *px, my = *py, mz = *pz;
+            *px = mkc<float>(kxx * mx.x + kxy * my.x, kxx * mx.y + kxy * my.y);
+            *py = mkc<float>(kxy * mx.x + kyy * my.x, kxy * mx.y + kyy * my.y);
+            *pz = mkc<float>(kzz * mz.x, kzz * mz.y);
+        }
+        __syncthreads();
+        col_fft<LY, NT, -1>(sm, 3 * TK, Py, cd);
+        for (int c = 0; c < 3; ++c)
+            for (int e = threadIdx.x; e < (ny << tks); e += NT) {
+                const int kxl = e & (TK - 1), pt = e >> tks;
+                if (kx0 + kxl < cd.Kx) S[(long long)(c * ny + pt) * cd.Wk + kx0 + kxl] = sm[(c * TK + kxl) * cp + pt];
+            }
+        __syncthreads();
+    }
+}
+
+// phase C: C2R rows of a block of y (three components) + field + update
+template <int LX, int NT>
+__device__ __noinline__ void stage_phase_c(const BatchArgs& a, const RepDev& rp, const ClsDev& cd, float* mE,
+                                           long long N, int nx, int ny, float2* S, float2* sm, long long step,
+                                           float dt) {
     FieldArgs<float> fa = a.fa;
     fa.m = mE;
     fa.N = N;
@@ -109,76 +189,8 @@ __device__ void replica_stage(const BatchArgs& a, const RepDev& rp, const ClsDev
     fa.tq_base = rp.tq_base;
     const Region<float>& R = fa.lut[0];
     const int Lh = LX > 0 ? LX : cd.Lh;
-    const int Py = LY > 0 ? LY : cd.Py;
     const int pitch = Lh + 1;
     float* smr = reinterpret_cast<float*>(sm);
-    const float ms = R.Ms;
-
-    if (a.demag) {
-        // ---- phase X: rows (c, y) -> half spectra in S[(c ny + y) Wk + kx]
-        const int RB = b_rows_x(Lh, NT);
-        for (int r0 = 0; r0 < 3 * ny; r0 += RB) {
-            const int nl = min(RB, 3 * ny - r0);
-            for (int l = 0; l < nl; ++l) {
-                const int row = r0 + l, c = row / ny, y = row - c * ny;
-                const float* src = mE + c * N + (long long)y * nx;
-                for (int q = threadIdx.x; q < 2 * Lh; q += NT) smr[2 * l * pitch + q] = q < nx ? src[q] * ms : 0.f;
-            }
-            __syncthreads();
-            row_fft<LX, NT, 1>(sm, nl, (nx + 1) / 2, cd);
-            for (int l = 0; l < nl; ++l) {
-                float2* out = S + (long long)(r0 + l) * cd.Wk;
-                for (int k = threadIdx.x; k <= Lh; k += NT) {
-                    const float2 zk = sm[l * pitch + (k == Lh ? 0 : k)];
-                    const float2 zc = cconj<float>(sm[l * pitch + (k == 0 ? 0 : Lh - k)]);
-                    const float2 E = cscale<float>(cadd<float>(zk, zc), 0.5f);
-                    const float2 O = cscale<float>(mul_mi<float, 1>(csub<float>(zk, zc)), 0.5f);
-                    out[k] = cadd<float>(E, cmul<float>(__ldg(&cd.twx[k]), O));
-                }
-            }
-            __syncthreads();
-        }
-        // ---- phase Y: columns, FFT along y, tensor multiply, inverse, keep ny
-        const int TK = b_tk(Py, NT);
-        const int tks = __ffs(TK) - 1;
-        const int cp = Py + 1;
-        for (int kx0 = 0; kx0 < cd.Kx; kx0 += TK) {
-            for (int c = 0; c < 3; ++c)
-                for (int e = threadIdx.x; e < (ny << tks); e += NT) {
-                    const int kxl = e & (TK - 1), pt = e >> tks;
-                    float2 v = mkc<float>(0.f, 0.f);
-                    if (kx0 + kxl < cd.Kx) v = S[(long long)(c * ny + pt) * cd.Wk + kx0 + kxl];
-                    sm[(c * TK + kxl) * cp + pt] = v;
-                }
-            __syncthreads();
-            col_fft<LY, NT, 1>(sm, 3 * TK, ny, cd);
-            const long long kcs = (long long)cd.Ky * cd.Wk;
-            for (int e = threadIdx.x; e < (Py << tks); e += NT) {
-                const int kxl = e & (TK - 1), kk = e >> tks;
-                const int kx = kx0 + kxl;
-                if (kx >= cd.Kx) continue;
-                const int kf = kk <= Py / 2 ? kk : Py - kk;
-                const float sy = kk <= Py / 2 ? 1.f : -1.f;
-                const float* K = cd.khat + (long long)kf * cd.Wk + kx;
-                const float kxx = __ldg(K), kyy = __ldg(K + kcs), kzz = __ldg(K + 2 * kcs), kxy = sy * __ldg(K + 3 * kcs);
-                float2* px = &sm[(0 * TK + kxl) * cp + kk];
-                float2* py = &sm[(1 * TK + kxl) * cp + kk];
-                float2* pz = &sm[(2 * TK + kxl) * cp + kk];
-                const float2 mx = *px, my = *py, mz = *pz;
-                *px = mkc<float>(kxx * mx.x + kxy * my.x, kxx * mx.y + kxy * my.y);
-                *py = mkc<float>(kxy * mx.x + kyy * my.x, kxy * mx.y + kyy * my.y);
-                *pz = mkc<float>(kzz * mz.x, kzz * mz.y);
-            }
-            __syncthreads();
-            col_fft<LY, NT, -1>(sm, 3 * TK, Py, cd);
-            for (int c = 0; c < 3; ++c)
-                for (int e = threadIdx.x; e < (ny << tks); e += NT) {
-                    const int kxl = e & (TK - 1), pt = e >> tks;
-                    if (kx0 + kxl < cd.Kx) S[(long long)(c * ny + pt) * cd.Wk + kx0 + kxl] = sm[(c * TK + kxl) * cp + pt];
-                }
-            __syncthreads();
-        }
-    }
     // ---- phase C: C2R rows of a block of y (three components) + field + update
     const int RBc = a.demag ? max(1, b_rows_c(Lh, NT)) : ny;
     for (int y0 = 0; y0 < ny; y0 += RBc) {
@@ -229,6 +241,19 @@ __device__ void replica_stage(const BatchArgs& a, const RepDev& rp, const ClsDev
         }
         __syncthreads();
     }
+}
+
+template <int LX, int LY, int NT>
+__device__ __forceinline__ void replica_stage(const BatchArgs& a, const RepDev& rp, const ClsDev& cd, float2* S,
+                                              float2* sm, long long step, float dt) {
+    const int nx = rp.nx, ny = rp.ny;
+    const long long N = (long long)nx * ny;
+    float* mE = (a.stage == 1 ? a.m0 : a.ms) + rp.off;
+    if (a.demag) {
+        stage_phase_x<LX, NT>(mE, N, nx, ny, a.fa.lut[0].Ms, cd, S, sm);
+        stage_phase_y<LY, NT>(ny, cd, S, sm);
+    }
+    stage_phase_c<LX, NT>(a, rp, cd, mE, N, nx, ny, S, sm, step, dt);
 }
 
 template <int NT>

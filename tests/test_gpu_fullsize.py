@@ -116,3 +116,60 @@ def test_newell_entries_at_the_largest_displacements():
     o = newell_at(ijk, d)
     scale = np.abs(o).max(axis=1, keepdims=True)
     assert np.all(np.abs(g - o) <= 1e-11 * scale + 1e-18)
+
+
+def test_skyrmion_film_512x512_replay_fp32():
+    """The 512x512x1 DMI film (the surrogate workload's exact path: one-row-per-
+    warp X passes, stage combine fused into them) against the oracle."""
+    mm = need_gpu()
+    w = W.skyrmion_512()
+    m0 = W.m_skyrmion_lattice(w.grid, seed=w.seed, spacing=40e-9, radius=8e-9)
+    o, p = _solver(w, m0, dt=1e-14, rtol=w.rtol)
+    dts = [o.rk45_step() for _ in range(3)]
+    ctx = make_ctx(mm, w.grid, w.mat, precision=32, demag=True, B=w.B_ext, dt=1e-14, rtol=w.rtol)
+    try:
+        mm.mm_set_m(ctx, 0, m0)
+        mm.mm_step_dt(ctx, dts)
+        err = np.abs(mm.mm_get_m(ctx, 0, m0.shape) - o.m).max()
+        assert err <= 1e-5, err
+    finally:
+        mm.mm_destroy(ctx)
+
+
+def test_replicas_1024_sampled_against_oracle():
+    """All 1024 perpendicular free layers of uneven sizes in one batch
+    (T = 300 K, per-replica Philox keys splitmix64(3 + r), SOT current per
+    replica), 10 Heun steps; the smallest, the largest and the first replica
+    against the oracle run replica by replica."""
+    mm = need_gpu()
+    from oracle.llg import Solver, Torque, replica_seed
+    R = 1024
+    sizes = W.replica_sizes(R, seed=3)
+    J = W.replica_currents(R)
+    mat = W.Material(Ms=1.1e6, A=2e-11, alpha=0.01, Ku1=9e5, u=(0.0, 0.0, 1.0))
+    M = mm.Material(mat.Ms, mat.A, mat.alpha, mat.Ku1, mat.u, mat.D)
+    grids = [mm.make_grid(n, n, 1, 2e-9, 2e-9, 1e-9) for n in sizes]
+    cfg = mm.make_config(precision=32, integrator=mm.MM_HEUN, demag=mm.MM_DEMAG_EXACT, dt=1e-14, T=300.0, seed=3)
+    ctx = mm.mm_create_batch(grids, M.s, cfg, None)
+    ctx._mat = M
+    try:
+        mm.mm_set_torque(ctx, mm.make_torque(mm.MM_TORQUE_SOT, p=(0, 1, 0), theta_SH=0.1), J)
+        m0 = []
+        for r, n in enumerate(sizes):
+            m = W.m_perp(W.Grid(n, n, 1, 2e-9, 2e-9, 1e-9), seed=1000 + r, tilt=0.05)
+            mm.mm_set_m(ctx, r, m)
+            m0.append(m)
+        n_steps = 10
+        mm.mm_step(ctx, n_steps)
+        for r in sorted({0, int(np.argmin(sizes)), int(np.argmax(sizes))}):
+            g = W.Grid(sizes[r], sizes[r], 1, 2e-9, 2e-9, 1e-9)
+            p = oracle_problem(g, mat)
+            o = Solver(p, m0[r], terms=("exchange", "anisotropy", "zeeman", "demag"), T=300.0,
+                       seed=replica_seed(3, r), dt=1e-14,
+                       torque=Torque(kind="sot", J=J[r], p=(0, 1, 0), theta_SH=0.1))
+            for _ in range(n_steps):
+                o.heun_step()
+            err = np.abs(mm.mm_get_m(ctx, r, m0[r].shape) - o.m).max()
+            assert err <= 1e-5, (r, sizes[r], err)
+    finally:
+        mm.mm_destroy(ctx)
