@@ -35,9 +35,10 @@ struct BatchHost {
 static size_t batch_smem(const BatchHost& b, int NT) {
     size_t mx = 0;
     for (const ClsDev& cd : b.cls) {
-        const size_t x = (size_t)std::min(b_rows_x(cd.Lh, NT), 3 * cd.ny) * (cd.Lh + 1) * 8;
-        const size_t y = (size_t)3 * b_tk(cd.Py, NT) * (cd.Py + 1) * 8;
-        const size_t cc = (size_t)3 * std::min(std::max(1, b_rows_c(cd.Lh, NT)), cd.ny) * (cd.Lh + 1) * 8;
+        const bool ct = b_compiled(cd.Lh, cd.Py);
+        const size_t x = (size_t)std::min(b_rows_x(cd.Lh, NT, ct), 3 * cd.ny) * (cd.Lh + 1) * 8;
+        const size_t y = (size_t)3 * b_tk(cd.Py, NT, ct) * (cd.Py + 1) * 8;
+        const size_t cc = (size_t)3 * std::min(std::max(1, b_rows_c(cd.Lh, NT, ct)), cd.ny) * (cd.Lh + 1) * 8;
         mx = std::max(mx, std::max(x, std::max(y, cc)));
     }
     return std::max<size_t>(mx, 16);

@@ -31,9 +31,11 @@
 
 namespace mm {
 
-// complex values a thread holds per Stockham pass; a multiple of every
-// radix (8, 4, 3, 2) so each pass covers all the butterflies of b_rows_x /
-// b_tk lines
+// complex values a thread holds per Stockham pass of a compile-time plan
+// (the runtime-planned path holds kMaxV); a pass of radix R can use
+// (kMaxVB / R) R of them, so the lines per pass are sized by ct_cap.  24
+// (every radix divides it) measured faster than 8: fewer spills did not
+// pay for three times the passes and barriers.
 constexpr int kMaxVB = 24;
 
 struct RepDev {
@@ -69,13 +71,29 @@ struct BatchArgs {
     const DevState* st;
 };
 
-__host__ __device__ constexpr int b_rows_x(int Lh, int NT) { return (kMaxVB * NT) / Lh; }
-__host__ __device__ inline int b_tk(int Py, int NT) {
-    int cap = (kMaxVB * NT) / (3 * Py), tk = 1;
+// values per thread every pass of the compile-time plan of length L can hold
+__host__ __device__ constexpr int ct_cap(int L, int maxv) {
+    int cap = maxv;
+    for (int p = 0; p < ct_npass(L); ++p) {
+        const int r = ct_radix(L, p), c = (maxv / r) * r;
+        if (c < cap) cap = c;
+    }
+    return cap;
+}
+// size classes with compile-time plans (half length, column length): the
+// cases of batch_stage_kernel's dispatch
+__host__ __device__ inline bool b_compiled(int Lh, int Py) {
+    return (Lh == 16 && Py == 32) || (Lh == 32 && Py == 64) || (Lh == 48 && Py == 96) || (Lh == 64 && Py == 128) ||
+           (Lh == 96 && Py == 192) || (Lh == 128 && Py == 256) || (Lh == 256 && Py == 512);
+}
+__host__ __device__ inline int b_cap(int L, bool ct) { return ct ? ct_cap(L, kMaxVB) : kMaxV; }
+__host__ __device__ inline int b_rows_x(int Lh, int NT, bool ct) { return b_cap(Lh, ct) * NT / Lh; }
+__host__ __device__ inline int b_tk(int Py, int NT, bool ct) {
+    int cap = b_cap(Py, ct) * NT / (3 * Py), tk = 1;
     while (tk * 2 <= cap && tk * 2 <= 16) tk *= 2;
     return tk;
 }
-__host__ __device__ constexpr int b_rows_c(int Lh, int NT) { return (kMaxVB * NT) / (3 * Lh); }
+__host__ __device__ inline int b_rows_c(int Lh, int NT, bool ct) { return b_cap(Lh, ct) * NT / (3 * Lh); }
 
 template <int LX, int NT, int DIR>
 __device__ __forceinline__ void row_fft(float2* sm, int nl, int nin, const ClsDev& cd) {
@@ -102,7 +120,7 @@ __device__ __noinline__ void stage_phase_x(const float* mE, long long N, int nx,
     const int pitch = Lh + 1;
     float* smr = reinterpret_cast<float*>(sm);
     // ---- phase X: rows (c, y) -> half spectra in S[(c ny + y) Wk + kx]
-    const int RB = b_rows_x(Lh, NT);
+    const int RB = b_rows_x(Lh, NT, LX > 0);
     for (int r0 = 0; r0 < 3 * ny; r0 += RB) {
         const int nl = min(RB, 3 * ny - r0);
         for (int l = 0; l < nl; ++l) {
@@ -131,7 +149,7 @@ template <int LY, int NT>
 __device__ __noinline__ void stage_phase_y(int ny, const ClsDev& cd, float2* S, float2* sm) {
     const int Py = LY > 0 ? LY : cd.Py;
     // ---- phase Y: columns, FFT along y, tensor multiply, inverse, keep ny
-    const int TK = b_tk(Py, NT);
+    const int TK = b_tk(Py, NT, LY > 0);
     const int tks = __ffs(TK) - 1;
     const int cp = Py + 1;
     for (int kx0 = 0; kx0 < cd.Kx; kx0 += TK) {
@@ -192,7 +210,7 @@ __device__ __noinline__ void stage_phase_c(const BatchArgs& a, const RepDev& rp,
     const int pitch = Lh + 1;
     float* smr = reinterpret_cast<float*>(sm);
     // ---- phase C: C2R rows of a block of y (three components) + field + update
-    const int RBc = a.demag ? max(1, b_rows_c(Lh, NT)) : ny;
+    const int RBc = a.demag ? max(1, b_rows_c(Lh, NT, LX > 0)) : ny;
     for (int y0 = 0; y0 < ny; y0 += RBc) {
         const int nyb = min(RBc, ny - y0);
         if (a.demag) {
