@@ -287,6 +287,45 @@ def variant_batched(mm, stream, steps):
                               "against": "FP64 single-instance GPU runs with the same Philox key"}}
 
 
+# The paper's throughput scenarios (ms per field evaluation, FP32) and its
+# published numbers on its own hardware (an RTX 5060 Ti): this code's cuFFT
+# build and the best solver of its comparison.  Grid shapes are not printed
+# there beyond the cell counts; the ones used here are stated per scenario.
+PAPER_SCENARIOS = [
+    ("SP#4-like 2-D film, T = 0", (200, 50, 1), (2.5e-9, 2.5e-9, 3e-9), 0.042, 0.042),
+    ("power-of-two 3-D", (64, 64, 16), (3e-9, 3e-9, 3e-9), 0.155, 0.155),
+    ("medium 3-D", (150, 150, 24), (3e-9, 3e-9, 3e-9), 2.610, 1.663),
+    ("large 3-D", (250, 250, 40), (3e-9, 3e-9, 3e-9), 12.72, 11.13),
+]
+
+
+def variant_scenarios(mm, stream, steps=60):
+    """ms per field evaluation on the paper's four throughput scenarios:
+    permalloy (Ms 8e5, A 1.3e-11, alpha 0.02), exchange + exact demag,
+    FP32 RK45 (six evaluations per step) from a seeded perturbed state."""
+    out = []
+    M = mm.Material(8.0e5, 1.3e-11, 0.02)
+    for name, (nx, ny, nz), (dx, dy, dz), paper_cs, paper_best in PAPER_SCENARIOS:
+        g = W.Grid(nx, ny, nz, dx, dy, dz)
+        cfg = mm.make_config(precision=32, integrator=mm.MM_RK45, demag=mm.MM_DEMAG_EXACT, dt=1e-14, rtol=1e-6)
+        ctx = mm.mm_create(mm.make_grid(nx, ny, nz, dx, dy, dz), M.s, cfg)
+        mm.mm_set_stream(ctx, stream.cuda_stream)
+        mm.mm_set_m(ctx, 0, W.m_uniform_perturbed(g, seed=1))
+        mm.mm_step(ctx, 10)
+        s0 = mm.mm_get_stats(ctx)
+        ms = _timed(stream, lambda: mm.mm_step(ctx, steps))
+        s1 = mm.mm_get_stats(ctx)
+        attempts = max(1, s1["attempts"] - s0["attempts"])
+        per_eval = ms / (6 * attempts)
+        out.append({"scenario": name, "grid": [nx, ny, nz], "cell_nm": [dx * 1e9, dy * 1e9, dz * 1e9],
+                    "cells": g.n, "ms_per_field_eval": round(per_eval, 5),
+                    "paper_ms_per_field_eval": {"this_code_cufft": paper_cs, "best_in_paper": paper_best,
+                                                "hardware": "RTX 5060 Ti"},
+                    "attempts": attempts})
+        mm.mm_destroy(ctx)
+    return {"metric": "ms per field evaluation (RK45: 6 per attempted step)", "scenarios": out}
+
+
 def variant_surrogate(mm, stream, steps, train_steps=1500):
     """512x512x1 skyrmion-lattice film, FP32 RK45: exact FFT demag against the
     BF16 CNN surrogate refreshed exactly every k attempted steps."""
@@ -467,7 +506,8 @@ def run_gpu(args):
         line["variants"] = {}
         wanted = [v for v in args.variants.split(",") if v]
         for name, fn in (("batched", lambda: variant_batched(mm, stream, args.batch_steps)),
-                         ("surrogate", lambda: variant_surrogate(mm, stream, args.surrogate_steps))):
+                         ("surrogate", lambda: variant_surrogate(mm, stream, args.surrogate_steps)),
+                         ("paper_scenarios", lambda: variant_scenarios(mm, stream))):
             if name not in wanted:
                 continue
             try:
@@ -492,7 +532,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", default="", help="nx,ny,nz: a smaller case of the same workload (profiling)")
     ap.add_argument("--no-variants", action="store_true", help="skip the FP64, batched and surrogate lines")
-    ap.add_argument("--variants", default="batched,surrogate", help="comma list of variant lines to run")
+    ap.add_argument("--variants", default="batched,surrogate,paper_scenarios",
+                    help="comma list of variant lines to run")
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--surrogate-steps", type=int, default=100)
     args = ap.parse_args()

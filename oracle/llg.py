@@ -210,6 +210,21 @@ class Solver:
         self.step += 1
         self.accepted += 1
 
+    # -- classical Runge-Kutta (fixed step) -----------------------------------
+    def rk4_step(self, dt=None):
+        """Methods, "Integrators" (RK4, fixed step): four slopes, the weighted
+        sum (k1 + 2 k2 + 2 k3 + k4) / 6, stages not renormalised, |m| = 1
+        restored after the step."""
+        dt = self.dt if dt is None else dt
+        k1 = self.slope(self.m)
+        k2 = self.slope(self.m + 0.5 * dt * k1)
+        k3 = self.slope(self.m + 0.5 * dt * k2)
+        k4 = self.slope(self.m + dt * k3)
+        self.m = _unit(self.m + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4), self.p.present)
+        self.t += dt
+        self.step += 1
+        self.accepted += 1
+
     # -- Dormand-Prince -----------------------------------------------------
     def dopri_attempt(self, dt):
         """Returns (m5, err, k7) for one attempted step from self.m."""
