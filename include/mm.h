@@ -55,7 +55,10 @@ typedef enum mm_status {
     MM_ERR_STATE = 8          /* call not valid in the current state */
 } mm_status;
 
-enum mm_integrator { MM_HEUN = 0, MM_RK45 = 1 };
+/* Integrators (Methods, "Integrators"): Heun (fixed dt, thermal field
+ * allowed), Dormand-Prince RK45 (adaptive, FSAL), classical RK4 (fixed dt,
+ * four evaluations, |m| restored after each step). */
+enum mm_integrator { MM_HEUN = 0, MM_RK45 = 1, MM_RK4 = 2 };
 enum mm_demag_mode { MM_DEMAG_OFF = 0, MM_DEMAG_EXACT = 1, MM_DEMAG_SURROGATE = 2 };
 
 /* Effective-field terms (bit mask). */
@@ -94,13 +97,13 @@ typedef struct mm_material {
 
 typedef struct mm_config {
     int precision;            /* 32 or 64: arithmetic of the state, fields, FFTs */
-    int integrator;           /* MM_HEUN or MM_RK45 */
+    int integrator;           /* MM_HEUN, MM_RK45 or MM_RK4 */
     int demag;                /* mm_demag_mode */
     unsigned terms;           /* mm_term mask of the effective field; 0 means all */
-    double dt;                /* Heun step; RK45 initial step (s) */
+    double dt;                /* Heun / RK4 step; RK45 initial step (s) */
     double rtol;              /* RK45: accept when max_cell |m5 - m4| <= rtol */
     double dt_min, dt_max;    /* RK45 step bounds (s); 0 selects 1e-20 / 1e-11 */
-    double T;                 /* temperature (K) of every replica (Heun only) */
+    double T;                 /* temperature (K) of every replica (Heun only; > 0 is rejected otherwise) */
     uint64_t seed;            /* base Philox seed; replica r uses splitmix64(seed + r) */
 } mm_config;
 

@@ -301,9 +301,12 @@ mm_status mm_create(const mm_grid* grid, const mm_material* mat, const mm_config
     if (grid->nx <= 0 || grid->ny <= 0 || grid->nz <= 0 || !(grid->dx > 0) || !(grid->dy > 0) || !(grid->dz > 0))
         return set_error(nullptr, MM_ERR_ARG, "grid sizes and cell edges must be positive");
     if (cfg->precision != 32 && cfg->precision != 64) return set_error(nullptr, MM_ERR_ARG, "precision must be 32 or 64");
-    if (cfg->integrator != MM_HEUN && cfg->integrator != MM_RK45) return set_error(nullptr, MM_ERR_ARG, "bad integrator");
+    if (cfg->integrator != MM_HEUN && cfg->integrator != MM_RK45 && cfg->integrator != MM_RK4)
+        return set_error(nullptr, MM_ERR_ARG, "bad integrator");
     if (cfg->integrator == MM_RK45 && cfg->T > 0)
         return set_error(nullptr, MM_ERR_ARG, "RK45 with T > 0: adaptive stepping of white noise is not defined; use Heun");
+    if (cfg->integrator == MM_RK4 && cfg->T > 0)
+        return set_error(nullptr, MM_ERR_ARG, "RK4 with T > 0: the thermal field needs the Heun scheme");
     if (cfg->demag == MM_DEMAG_SURROGATE) return set_error(nullptr, MM_ERR_ARG, "surrogate demag needs mm_surrogate_*");
     if (cfg->demag == MM_DEMAG_EXACT && (grid->pbc[0] || grid->pbc[1] || grid->pbc[2]))
         return set_error(nullptr, MM_ERR_ARG, "periodic boundaries apply to the local terms only; turn demag off");
@@ -335,7 +338,7 @@ mm_status mm_create(const mm_grid* grid, const mm_material* mat, const mm_config
     TRY(alloc(c, &c->d_m, vb, "state"));
     TRY(alloc(c, &c->d_mtmp, vb, "stage state"));
     TRY(alloc(c, &c->d_hbuf, vb, "field scratch"));
-    const int nk = c->integrator == MM_RK45 ? 7 : 1;
+    const int nk = c->integrator == MM_RK45 ? 7 : c->integrator == MM_RK4 ? 4 : 1;
     for (int q = 0; q < nk; ++q) TRY(alloc(c, &c->d_k[q], vb, "slopes"));
     TRY(alloc(c, &c->d_kslot, sizeof(void*) * 7, "slot table"));
     cudaMemcpy(c->d_kslot, c->d_k, sizeof(void*) * 7, cudaMemcpyHostToDevice);
@@ -631,7 +634,7 @@ mm_status mm_set_temperature(mm_ctx* c, const double* T) {
     if (!c || !T) return MM_ERR_ARG;
     for (int r = 0; r < c->R; ++r)
         if (!(T[r] >= 0)) return set_error(c, MM_ERR_ARG, "negative temperature");
-    if (T[0] > 0 && c->integrator == MM_RK45) return set_error(c, MM_ERR_ARG, "RK45 with T > 0; use Heun");
+    if (T[0] > 0 && c->integrator != MM_HEUN) return set_error(c, MM_ERR_ARG, "T > 0 needs the Heun integrator");
     c->Tr = T[0];
     if (c->batch) {
         for (int r = 0; r < c->R; ++r) c->rT[r] = T[r];
@@ -665,6 +668,7 @@ static void launch_attempts(mm_ctx* c, int n) {
     for (int q = 0; q < n; ++q) {
         if (c->batch) batch_heun_step(c, c->batch);
         else if (c->integrator == MM_RK45) rk45_attempt(c);
+        else if (c->integrator == MM_RK4) rk4_step(c);
         else heun_step(c);
     }
 }
@@ -773,7 +777,7 @@ static mm_status advance(mm_ctx* c, long long add_steps, double t_end, int repla
     if (s != MM_OK) return s;
     s = ensure_k1(c);
     if (s != MM_OK) return s;
-    const bool heun = c->integrator == MM_HEUN;
+    const bool heun = c->integrator != MM_RK45;   // fixed-step schemes: every attempt is accepted
     if (surrogate_stepping(c) && !surrogate_fallen_back(c)) {
         // host-driven blocks: exact refresh (with the error monitor) + k-1
         // network attempts; after a fallback the exact loop below takes over

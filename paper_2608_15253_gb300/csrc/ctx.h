@@ -238,6 +238,7 @@ void heun_batch_advance(mm_ctx* c);
 void rk45_first_slope(mm_ctx* c);          // k1 = f(m0) into the FSAL slot
 void rk45_attempt(mm_ctx* c);               // one attempted DOPRI5 step
 void heun_step(mm_ctx* c);                  // one Heun step
+void rk4_step(mm_ctx* c);                   // one classical RK4 step
 
 // reduce.cu
 void energy_term_launch(mm_ctx* c, const void* m, const void* H, int which, double* d_out2);

@@ -295,6 +295,77 @@ void heun_batch_advance(mm_ctx* c) {
     heun_advance_kernel<<<1, 1, 0, c->stream>>>(c->d_state);
 }
 
+// Classical RK4 (Methods, "Integrators": fixed step): stage states
+// m0 + c dt k with c = 1/2, 1/2, 1, then m0 <- normalise(m0 + dt/6 (k1 +
+// 2 k2 + 2 k3 + k4)); dt from the device state (fixed per context).
+template <typename T>
+__global__ void __launch_bounds__(256) rk4_stage_kernel(const DevState* __restrict__ st, const T* __restrict__ m0,
+                                                        const T* __restrict__ k, double c, T* __restrict__ out,
+                                                        long long n3) {
+    if (!st->active) return;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n3) return;
+    const T h = (T)(c * st->dt);
+    out[i] = m0[i] + h * __ldg(k + i);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) rk4_final_kernel(const DevState* __restrict__ st, T* __restrict__ m0,
+                                                        const T* __restrict__ k1, const T* __restrict__ k2,
+                                                        const T* __restrict__ k3, const T* __restrict__ k4,
+                                                        long long N) {
+    if (!st->active) return;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const T h6 = (T)(st->dt / 6.0);
+    T v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const long long j = c * N + i;
+        v[c] = m0[j] + h6 * (k1[j] + (T)2 * k2[j] + (T)2 * k3[j] + k4[j]);
+    }
+    const T n2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    const T inv = n2 > (T)0 ? (T)1 / sqrt(n2) : (T)0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) m0[c * N + i] = v[c] * inv;
+}
+
+template <typename T>
+static void rk4_step_t(mm_ctx* c) {
+    const unsigned terms = c->terms;
+    const bool demag = c->dm.on && (terms & MM_TERM_DEMAG);
+    const long long N = c->N, n3 = 3 * N;
+    const unsigned tb = 256, nb3 = (unsigned)((n3 + tb - 1) / tb), nb = (unsigned)((N + tb - 1) / tb);
+    {
+        LaunchScope ls(c, "rk4_begin", 0.0);
+        heun_begin_kernel<<<1, 1, 0, c->stream>>>(c->d_state);
+    }
+    static const double cs[4] = {0.0, 0.5, 0.5, 1.0};
+    for (int s = 0; s < 4; ++s) {
+        const void* ms = c->d_m;
+        if (s > 0) {
+            LaunchScope ls(c, "rk4_stage", (double)sizeof(T) * n3 * 3);
+            rk4_stage_kernel<T><<<nb3, tb, 0, c->stream>>>(c->d_state, (const T*)c->d_m, (const T*)c->d_k[s - 1],
+                                                            cs[s], (T*)c->d_mtmp, n3);
+            ms = c->d_mtmp;
+        }
+        if (demag) demag_apply(c, ms, c->d_hd);
+        field_launch(c, MODE_K, terms, ms, demag ? c->d_hd : nullptr, c->d_k[s], nullptr, nullptr, nullptr, -1, 1, 0);
+    }
+    {
+        LaunchScope ls(c, "rk4_final", (double)sizeof(T) * N * 18);
+        rk4_final_kernel<T><<<nb, tb, 0, c->stream>>>(c->d_state, (T*)c->d_m, (const T*)c->d_k[0], (const T*)c->d_k[1],
+                                                       (const T*)c->d_k[2], (const T*)c->d_k[3], N);
+    }
+    LaunchScope ls(c, "rk4_advance", 0.0);
+    heun_advance_kernel<<<1, 1, 0, c->stream>>>(c->d_state);
+}
+
+void rk4_step(mm_ctx* c) {
+    if (c->prec == 32) rk4_step_t<float>(c);
+    else rk4_step_t<double>(c);
+}
+
 void heun_step(mm_ctx* c) {
     const unsigned terms = c->terms;
     const bool demag = c->dm.on && (terms & MM_TERM_DEMAG);

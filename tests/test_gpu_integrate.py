@@ -149,3 +149,33 @@ def test_zhang_li_with_rk45_replay(prec):
         assert err <= (1e-11 if prec == 64 else 1e-5), err
     finally:
         mm.mm_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("ci", range(len(CASES)))
+def test_rk4_matches_oracle(prec, ci):
+    """Classical RK4 (fixed step) against the oracle's RK4, same steps."""
+    mm = need_gpu()
+    name, grid, mat, B = CASES[ci]
+    m0 = W.random_m(grid, seed=40 + ci)
+    dt, nsteps = 5e-15, 30
+    o = _oracle_solver(grid, mat, m0, B, dt=dt)
+    for _ in range(nsteps):
+        o.rk4_step(dt)
+    ctx = make_ctx(mm, grid, mat, precision=prec, integrator="rk4", demag=True, B=B, dt=dt)
+    try:
+        mm.mm_set_m(ctx, 0, m0)
+        mm.mm_step(ctx, nsteps)
+        t, _, n = mm.mm_get_time(ctx)
+        assert n == nsteps and abs(t - nsteps * dt) < 1e-25
+        err = np.abs(mm.mm_get_m(ctx, 0, m0.shape) - o.m).max()
+        assert err <= (1e-11 if prec == 64 else 1e-5), err
+    finally:
+        mm.mm_destroy(ctx)
+
+
+def test_rk4_rejects_finite_temperature():
+    mm = need_gpu()
+    name, grid, mat, B = CASES[0]
+    with pytest.raises(mm.MMError):
+        make_ctx(mm, grid, mat, precision=32, integrator="rk4", demag=False, T=300.0)
