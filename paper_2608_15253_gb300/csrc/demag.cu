@@ -938,7 +938,8 @@ static int col_tk(int L, int nc) {
 // Lengths with a compile-time FFT (FP32): every half-length and column
 // length of the benchmark workloads; other lengths and FP64 take the
 // runtime-planned path.
-#define MM_CT_LENGTHS(X) X(16) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(512) X(1024)
+#define MM_CT_LENGTHS(X) \
+    X(16) X(32) X(48) X(64) X(81) X(96) X(108) X(128) X(162) X(192) X(216) X(256) X(324) X(432) X(512) X(1024)
 
 template <typename T> using XKern = void (*)(XArgs<T>);
 template <typename T> using CKern = void (*)(ColArgs<T>);
@@ -972,7 +973,7 @@ static CKern<T> col_kernel(int L) {
 static XKern<float> x_warp_kernel(bool fwd, int Lh) {
     switch (Lh) {
 #define MM_CASE(n) case n: return fwd ? fft_x_r2c_warp_kernel<n, 0> : fft_x_c2r_warp_kernel<n>;
-        MM_CASE(192) MM_CASE(256) MM_CASE(512)
+        MM_CASE(192) MM_CASE(216) MM_CASE(256) MM_CASE(324) MM_CASE(432) MM_CASE(512)
 #undef MM_CASE
         default: return nullptr;
     }
@@ -988,7 +989,7 @@ static XKern<float> x_stage_kernel(int s, int Lh) {
         return (s >= 1 && s <= 6) ? t[s] : nullptr; \
     }
     switch (Lh) {
-        MM_ST(192) MM_ST(256) MM_ST(512)
+        MM_ST(192) MM_ST(216) MM_ST(256) MM_ST(324) MM_ST(432) MM_ST(512)
         default: return nullptr;
     }
 #undef MM_ST
@@ -1313,7 +1314,7 @@ static cudaError_t smem_attr(K k) {
 
 template <typename T>
 static cudaError_t fft_attributes() {
-    static const int lengths[] = {0, 16, 32, 48, 64, 96, 128, 192, 256, 512, 1024};
+    static const int lengths[] = {0, 16, 32, 48, 64, 81, 96, 108, 128, 162, 192, 216, 256, 324, 432, 512, 1024};
     cudaError_t e = cudaSuccess;
     for (int L : lengths) {
         if (L != 0 && sizeof(T) != 4) continue;
@@ -1329,7 +1330,7 @@ static cudaError_t fft_attributes() {
 
 static cudaError_t fast_attributes() {
     cudaError_t e = cudaSuccess;
-    for (int L : {16, 32, 48, 64, 96, 128, 192, 256, 512, 1024}) {
+    for (int L : {16, 32, 48, 64, 81, 96, 108, 128, 162, 192, 216, 256, 324, 432, 512, 1024}) {
         if (e == cudaSuccess) e = smem_attr(y_direct_kernel(true, L));
         if (e == cudaSuccess) e = smem_attr(y_direct_kernel(false, L));
     }
@@ -1337,7 +1338,7 @@ static cudaError_t fast_attributes() {
         if (e == cudaSuccess) e = smem_attr(zconv_reg_kernel(L, false));
         if (e == cudaSuccess) e = smem_attr(zconv_reg_kernel(L, true));
     }
-    for (int L : {192, 256, 512}) {
+    for (int L : {192, 216, 256, 324, 432, 512}) {
         if (e == cudaSuccess) e = smem_attr(x_warp_kernel(true, L));
         if (e == cudaSuccess) e = smem_attr(x_warp_kernel(false, L));
         for (int st = 1; st <= 6; ++st)

@@ -117,6 +117,13 @@ DEMAG_GRIDS = [
     # one-row-per-warp X passes: half lengths 192 (odd nx: scalar loads) and 512
     W.Grid(171, 10, 1, 2e-9, 2e-9, 1e-9),
     W.Grid(500, 4, 2, 2e-9, 2e-9, 2e-9),
+    # 3-smooth compile-time lengths: half lengths 108 / 81 / 216 / 162 / 324,
+    # column lengths 108 / 81 (odd) / 48 / 324
+    W.Grid(100, 50, 1, 2.5e-9, 2.5e-9, 3e-9),
+    W.Grid(75, 41, 3, 2e-9, 2e-9, 2e-9),
+    W.Grid(200, 20, 2, 2e-9, 2e-9, 2e-9),
+    W.Grid(150, 24, 24, 3e-9, 3e-9, 3e-9),
+    W.Grid(300, 150, 1, 2e-9, 2e-9, 1e-9),
 ]
 
 
