@@ -5,8 +5,9 @@ Methods, "Physics and discretization", Eq. 1:
     gamma' = gamma0 / (1 + alpha^2),
 with spin torques "added per integrator stage" (Slonczewski STT, spin-orbit
 torque, Zhang-Li), and Methods, "Integrators": Heun (stochastic LLG,
-Stratonovich: the same thermal field in predictor and corrector) and RK45
-Dormand-Prince (adaptive, first-same-as-last).
+Stratonovich: the same thermal field in predictor and corrector), RK45
+Dormand-Prince (adaptive, first-same-as-last), classical RK4 and the
+norm-exact Depondt-Mertens rotation scheme (Rodrigues update).
 
 Spin-torque forms (the paper names the torques, not their formulas).  A
 damping-like coefficient h_DL and a field-like coefficient h_FL (A/m) along
@@ -91,8 +92,9 @@ def llg_rhs(m, H, p: Problem):
     return np.where(p.present, out, 0.0)
 
 
-def spin_torque(m, p: Problem, tq: Torque, nz: int):
-    """SOT or Slonczewski STT term in Landau-Lifshitz form."""
+def _st_coefficients(m, p: Problem, tq: Torque, nz: int):
+    """Damping-like and field-like coefficients h_DL, h_FL (A/m) and the unit
+    polarisation p of the SOT / Slonczewski STT term, or None."""
     pol = np.asarray(tq.p, dtype=np.float64)
     pol = pol / np.linalg.norm(pol)
     pv = np.broadcast_to(pol[:, None, None, None], m.shape)
@@ -108,14 +110,25 @@ def spin_torque(m, p: Problem, tq: Torque, nz: int):
         hDL = eps * base
         hFL = tq.eps_prime * base
     else:
+        return None
+    return hDL, hFL, pv
+
+
+def spin_torque(m, p: Problem, tq: Torque, nz: int):
+    """SOT or Slonczewski STT term in Landau-Lifshitz form."""
+    c = _st_coefficients(m, p, tq, nz)
+    if c is None:
         return np.zeros_like(m)
+    hDL, hFL, pv = c
     gp = GAMMA0 / (1.0 + p.alpha ** 2)
     mxp = cross(m, pv)
     out = -gp * MU0 * ((hDL + p.alpha * hFL) * cross(m, mxp) + (hFL - p.alpha * hDL) * mxp)
     return np.where(p.present, out, 0.0)
 
 
-def zhang_li_torque(m, p: Problem, tq: Torque):
+def _zl_drive(m, p: Problem, tq: Torque):
+    """(u.grad) m of the Zhang-Li torque (A/m per m/s: the drift u times the
+    central-difference gradient, the absent neighbour taken as the cell)."""
     d = np.asarray(tq.direction, dtype=np.float64)
     d = d / np.linalg.norm(d)
     with np.errstate(divide="ignore", invalid="ignore"):
@@ -132,10 +145,27 @@ def zhang_li_torque(m, p: Problem, tq: Torque):
         mp = np.where(Ms_p > 0, _shift(m, direction, +1, per), m)
         mm = np.where(Ms_m > 0, _shift(m, direction, -1, per), m)
         grad += d[direction] * (mp - mm) / (2.0 * p.d[direction])
-    ug = u * grad
+    return u * grad
+
+
+def zhang_li_torque(m, p: Problem, tq: Torque):
+    ug = _zl_drive(m, p, tq)
     mxug = cross(m, ug)
     out = (-(1.0 + p.alpha * tq.xi) * cross(m, mxug) - (tq.xi - p.alpha) * mxug) / (1.0 + p.alpha ** 2)
     return np.where(p.present, out, 0.0)
+
+
+def rotate(m, w, dt):
+    """Rotation of every cell's m about its own axis w / |w| by the angle
+    |w| dt (right-handed), Rodrigues' formula
+        R m = m cos a + (n x m) sin a + n (n . m)(1 - cos a),  a = |w| dt,
+    so that for constant w the result solves dm/dt = w x m exactly.  Cells
+    with w = 0 are unchanged."""
+    wn = np.sqrt(dot(w, w))
+    a = wn * dt
+    n = w / np.where(wn > 0, wn, 1.0)
+    c, s = np.cos(a), np.sin(a)
+    return m * c + cross(n, m) * s + n * (dot(n, m) * (1.0 - c))
 
 
 def _unit(m, present):
@@ -148,8 +178,8 @@ class Solver:
     """One instance advanced by Heun or RK45 in FP64.
 
     ``terms`` selects the effective-field contributions; ``T`` > 0 adds the
-    Philox thermal field (Heun only, as adaptive stepping with white noise
-    is not defined).
+    Philox thermal field (Heun and Depondt-Mertens only, as adaptive
+    stepping with white noise is not defined).
     """
     p: Problem
     m: np.ndarray
@@ -221,6 +251,46 @@ class Solver:
         k3 = self.slope(self.m + 0.5 * dt * k2)
         k4 = self.slope(self.m + dt * k3)
         self.m = _unit(self.m + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4), self.p.present)
+        self.t += dt
+        self.step += 1
+        self.accepted += 1
+
+    # -- Depondt-Mertens rotation scheme ---------------------------------------
+    def omega(self, m, h_th=None):
+        """Methods, "Integrators" (norm-exact Depondt-Mertens scheme): Eq. 1
+        written as a rotation, dm/dt = Omega x m.  Since -m x H = H x m and
+        -m x (m x H) = (m x H) x m,
+            Omega = gamma' mu0 (H + alpha m x H)
+        and the spin torques above contribute, by the same two identities,
+            gamma' mu0 [ (h_DL + alpha h_FL) m x p + (h_FL - alpha h_DL) p ]
+            (1 + alpha xi) m x u' + (xi - alpha) u'   over (1 + alpha^2)
+        (SOT/STT; Zhang-Li with u' = (u.grad) m).  Omega x m is the slope."""
+        p = self.p
+        H = self.field(m, h_th)
+        gp = GAMMA0 / (1.0 + p.alpha ** 2)
+        w = gp * MU0 * (H + p.alpha * cross(m, H))
+        if self.torque.kind in ("sot", "stt"):
+            hDL, hFL, pv = _st_coefficients(m, p, self.torque, p.shape[0])
+            w = w + gp * MU0 * ((hDL + p.alpha * hFL) * cross(m, pv) + (hFL - p.alpha * hDL) * pv)
+        elif self.torque.kind == "zl":
+            tq = self.torque
+            ug = _zl_drive(m, p, tq)
+            w = w + ((1.0 + p.alpha * tq.xi) * cross(m, ug) + (tq.xi - p.alpha) * ug) / (1.0 + p.alpha ** 2)
+        return np.where(p.present, w, 0.0)
+
+    def dm_step(self, dt=None):
+        """Methods, "Integrators" and "Replica batching" (Depondt and Mertens,
+        2009): a predictor-corrector on rotations.  Omega_1 = Omega(m_n);
+        the predictor m* rotates m_n about Omega_1 for dt; Omega_2 =
+        Omega(m*); m_{n+1} rotates m_n about (Omega_1 + Omega_2) / 2 for dt.
+        One thermal draw serves both Omega evaluations (Stratonovich).  A
+        rotation keeps |m|, so nothing is renormalised."""
+        dt = self.dt if dt is None else dt
+        h_th = self.thermal(dt)
+        w1 = self.omega(self.m, h_th)
+        m_star = rotate(self.m, w1, dt)
+        w2 = self.omega(m_star, h_th)
+        self.m = np.where(self.p.present, rotate(self.m, 0.5 * (w1 + w2), dt), 0.0)
         self.t += dt
         self.step += 1
         self.accepted += 1
