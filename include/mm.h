@@ -57,8 +57,15 @@ typedef enum mm_status {
 
 /* Integrators (Methods, "Integrators"): Heun (fixed dt, thermal field
  * allowed), Dormand-Prince RK45 (adaptive, FSAL), classical RK4 (fixed dt,
- * four evaluations, |m| restored after each step). */
-enum mm_integrator { MM_HEUN = 0, MM_RK45 = 1, MM_RK4 = 2 };
+ * four evaluations, |m| restored after each step), and the Depondt-Mertens
+ * rotation scheme MM_DM (fixed dt, thermal field allowed; the integrator of
+ * the replica-batched engine): with dm/dt = Omega x m,
+ *   Omega = gamma' mu0 (H + alpha m x H) + spin-torque terms,
+ * the predictor rotates m about Omega(m) by |Omega| dt (Rodrigues), the
+ * corrector rotates the step's initial m about the mean of Omega(m) and
+ * Omega(predictor); one thermal draw serves both.  Rotations keep |m| = 1;
+ * the corrector also rescales by 1/|m| (a round-off-level change). */
+enum mm_integrator { MM_HEUN = 0, MM_RK45 = 1, MM_RK4 = 2, MM_DM = 3 };
 enum mm_demag_mode { MM_DEMAG_OFF = 0, MM_DEMAG_EXACT = 1, MM_DEMAG_SURROGATE = 2 };
 
 /* Effective-field terms (bit mask). */
@@ -97,7 +104,7 @@ typedef struct mm_material {
 
 typedef struct mm_config {
     int precision;            /* 32 or 64: arithmetic of the state, fields, FFTs */
-    int integrator;           /* MM_HEUN, MM_RK45 or MM_RK4 */
+    int integrator;           /* MM_HEUN, MM_RK45, MM_RK4 or MM_DM */
     int demag;                /* mm_demag_mode */
     unsigned terms;           /* mm_term mask of the effective field; 0 means all */
     double dt;                /* Heun / RK4 step; RK45 initial step (s) */
@@ -145,7 +152,8 @@ typedef struct mm_profile_entry {
  * Allocates device memory, validates the device (compute capability 10.3),
  * computes the FP64 Newell tensor spectrum on the GPU when demag is on.
  * m starts along +z.  Errors: MM_ERR_ARG (sizes <= 0, bad precision or
- * integrator, RK45 with T > 0, > 256 materials), MM_ERR_DEVICE, MM_ERR_OOM. */
+ * integrator, RK45 or RK4 with T > 0, > 256 materials), MM_ERR_DEVICE,
+ * MM_ERR_OOM. */
 MM_API mm_status mm_create(const mm_grid* grid, const mm_material* mat,
                            const mm_config* cfg, mm_ctx** out);
 
@@ -153,10 +161,11 @@ MM_API mm_status mm_create(const mm_grid* grid, const mm_material* mat,
  * (Methods, "Replica batching"): state replica-outermost, each replica with
  * its own Philox key (seeds[r], or splitmix64(cfg->seed + r) when seeds is
  * NULL), temperature (mm_set_temperature) and current (mm_set_torque).
- * R = 1 is the single-instance context.  For R > 1: FP32, Heun, nz = 1
- * open films sharing one cell size and one uniform material (Ms > 0);
+ * R = 1 is the single-instance context.  For R > 1: FP32, Heun or
+ * Depondt-Mertens, nz = 1 open films sharing one cell size and one uniform
+ * material (Ms > 0);
  * nx, ny may differ per replica (sizes of the same shape share one tensor
- * spectrum).  Each Heun stage is one persistent launch (mm_batch_autotune
+ * spectrum).  Each stage is one persistent launch (mm_batch_autotune
  * picks its shape).  Errors: MM_ERR_ARG for any other combination. */
 MM_API mm_status mm_create_batch(int R, const mm_grid* grids, const mm_material* mat,
                                  const mm_config* cfg, const uint64_t* seeds, mm_ctx** out);
@@ -237,8 +246,44 @@ MM_API mm_status mm_get_demag_kernel(mm_ctx* ctx, double* out, size_t n_out, int
  * ijk[3*q..3*q+2] of cells dx*dy*dz; out[6*q+c] in xx,yy,zz,xy,xz,yz. */
 MM_API mm_status mm_newell(long count, const int* ijk, double dx, double dy, double dz, double* out);
 
+/* Retire/refill of batched trials (Results, "Replica batching"): the slots
+ * of a replica-batched context (R >= 2 replicas of one grid) run n_trials
+ * independent trials.  Trial q has current density J[q] (A/m^2, with the
+ * context's torque, mm_set_torque) and temperature T[q] (K), Philox key
+ * splitmix64(base_seed + q) and its own step counter (from 0) as the noise
+ * counter, and starts from m_init (host float64, [3][ny][nx], renormalised
+ * per cell).  After every step a slot whose trial has
+ *     mean over cells of m . axis/|axis| <= threshold     (stopped = 1)
+ * or has taken max_steps steps (stopped = 0) records the trial's step count
+ * and, with refill, starts the next trial not yet begun (a fresh noise
+ * stream); otherwise, or when none is left, the slot idles.  A trial's
+ * outcome depends on q alone, not on its slot or start step.  Slots start
+ * with trials 0 .. min(R, n_trials) - 1 at the current step; mm_step
+ * advances every busy slot.  Per-replica temperatures and currents set
+ * before are replaced.  Errors: MM_ERR_STATE (single-instance context),
+ * MM_ERR_ARG (replicas of different sizes, n_trials < 1, max_steps < 1,
+ * NULL tables, negative T, zero axis). */
+typedef struct mm_trials {
+    long long n_trials;
+    const double* J;          /* [n_trials] */
+    const double* T;          /* [n_trials] */
+    const double* m_init;     /* [3][ny][nx] */
+    double axis[3];
+    double threshold;
+    long long max_steps;
+    uint64_t base_seed;
+    int refill;               /* 1: a finished slot starts the next trial */
+} mm_trials;
+MM_API mm_status mm_trials_start(mm_ctx* ctx, const mm_trials* spec);
+
+/* Outcomes so far (synchronises the context stream): steps[q] = steps the
+ * trial took (-1 while unfinished or not started), stopped[q] = 1 if the
+ * stop condition ended it; *done = finished trials.  Any output may be NULL.
+ * Errors: MM_ERR_STATE before mm_trials_start. */
+MM_API mm_status mm_trials_result(mm_ctx* ctx, long long* steps, int* stopped, long long* done);
+
 /* Launch-shape autotuner of a replica-batched context (Methods, "Replica
- * batching": one persistent launch per stage).  Times a few Heun steps for
+ * batching": one persistent launch per stage).  Times a few steps for
  * every candidate (threads per CTA x resident CTAs per SM), keeps the
  * fastest and restores the state (m, t, step counters) afterwards.  When
  * cache_path is non-NULL the choice is read from / appended to that JSON

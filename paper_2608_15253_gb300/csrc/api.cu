@@ -301,12 +301,13 @@ mm_status mm_create(const mm_grid* grid, const mm_material* mat, const mm_config
     if (grid->nx <= 0 || grid->ny <= 0 || grid->nz <= 0 || !(grid->dx > 0) || !(grid->dy > 0) || !(grid->dz > 0))
         return set_error(nullptr, MM_ERR_ARG, "grid sizes and cell edges must be positive");
     if (cfg->precision != 32 && cfg->precision != 64) return set_error(nullptr, MM_ERR_ARG, "precision must be 32 or 64");
-    if (cfg->integrator != MM_HEUN && cfg->integrator != MM_RK45 && cfg->integrator != MM_RK4)
+    if (cfg->integrator != MM_HEUN && cfg->integrator != MM_RK45 && cfg->integrator != MM_RK4 &&
+        cfg->integrator != MM_DM)
         return set_error(nullptr, MM_ERR_ARG, "bad integrator");
     if (cfg->integrator == MM_RK45 && cfg->T > 0)
         return set_error(nullptr, MM_ERR_ARG, "RK45 with T > 0: adaptive stepping of white noise is not defined; use Heun");
     if (cfg->integrator == MM_RK4 && cfg->T > 0)
-        return set_error(nullptr, MM_ERR_ARG, "RK4 with T > 0: the thermal field needs the Heun scheme");
+        return set_error(nullptr, MM_ERR_ARG, "RK4 with T > 0: the thermal field needs Heun or Depondt-Mertens");
     if (cfg->demag == MM_DEMAG_SURROGATE) return set_error(nullptr, MM_ERR_ARG, "surrogate demag needs mm_surrogate_*");
     if (cfg->demag == MM_DEMAG_EXACT && (grid->pbc[0] || grid->pbc[1] || grid->pbc[2]))
         return set_error(nullptr, MM_ERR_ARG, "periodic boundaries apply to the local terms only; turn demag off");
@@ -389,7 +390,8 @@ mm_status mm_create_batch(int R, const mm_grid* grids, const mm_material* mat, c
     }
     // replica-batched thin films (Methods, "Replica batching")
     if (cfg->precision != 32) return set_error(nullptr, MM_ERR_ARG, "replica batching runs in FP32");
-    if (cfg->integrator != MM_HEUN) return set_error(nullptr, MM_ERR_ARG, "replica batching integrates with Heun");
+    if (cfg->integrator != MM_HEUN && cfg->integrator != MM_DM)
+        return set_error(nullptr, MM_ERR_ARG, "replica batching integrates with Heun or Depondt-Mertens");
     if (cfg->demag == MM_DEMAG_SURROGATE) return set_error(nullptr, MM_ERR_ARG, "surrogate demag is single-instance");
     if (!(cfg->dt > 0)) return set_error(nullptr, MM_ERR_ARG, "dt must be positive");
     if (mat->Ms_cell || mat->A_cell || mat->alpha_cell || mat->Ku1_cell || mat->u_cell || mat->D_cell || !(mat->Ms > 0))
@@ -401,6 +403,8 @@ mm_status mm_create_batch(int R, const mm_grid* grids, const mm_material* mat, c
             return set_error(nullptr, MM_ERR_ARG, "batched replicas share one cell size");
         if (g.pbc[0] || g.pbc[1] || g.pbc[2]) return set_error(nullptr, MM_ERR_ARG, "batched replicas are open films");
         if (g.nx > 1024 || g.ny > 1024) return set_error(nullptr, MM_ERR_ARG, "batched replicas are at most 1024 x 1024");
+        if (cfg->demag == MM_DEMAG_EXACT && (g.nx < 2 || g.ny < 2))
+            return set_error(nullptr, MM_ERR_ARG, "batched demag needs replicas of at least 2 x 2 cells; turn demag off");
     }
     mm_ctx* c = new mm_ctx();
     mm_status s = check_device(c);
@@ -411,7 +415,7 @@ mm_status mm_create_batch(int R, const mm_grid* grids, const mm_material* mat, c
     }
     c->prec = 32;
     c->esz = 4;
-    c->integrator = MM_HEUN;
+    c->integrator = cfg->integrator;
     c->terms = cfg->terms ? cfg->terms : MM_TERM_ALL;
     if (cfg->demag != MM_DEMAG_EXACT) c->terms &= ~MM_TERM_DEMAG;
     c->cfg = *cfg;
@@ -632,9 +636,14 @@ mm_status mm_set_field(mm_ctx* c, int r, const double B[3], const double* B_cell
 
 mm_status mm_set_temperature(mm_ctx* c, const double* T) {
     if (!c || !T) return MM_ERR_ARG;
+    if (c->batch && batch_trials_on(c->batch))
+        return set_error(c, MM_ERR_STATE, "retire/refill sets each trial's temperature");
     for (int r = 0; r < c->R; ++r)
         if (!(T[r] >= 0)) return set_error(c, MM_ERR_ARG, "negative temperature");
-    if (T[0] > 0 && c->integrator != MM_HEUN) return set_error(c, MM_ERR_ARG, "T > 0 needs the Heun integrator");
+    bool hot = false;
+    for (int r = 0; r < c->R; ++r) hot = hot || T[r] > 0;
+    if (hot && c->integrator != MM_HEUN && c->integrator != MM_DM)
+        return set_error(c, MM_ERR_ARG, "T > 0 needs the Heun or Depondt-Mertens integrator");
     c->Tr = T[0];
     if (c->batch) {
         for (int r = 0; r < c->R; ++r) c->rT[r] = T[r];
@@ -649,6 +658,8 @@ mm_status mm_set_torque(mm_ctx* c, const mm_torque* tq, const double* J) {
     if (!c || !tq) return MM_ERR_ARG;
     if (tq->kind < MM_TORQUE_NONE || tq->kind > MM_TORQUE_ZL) return set_error(c, MM_ERR_ARG, "bad torque kind");
     if (c->batch && tq->kind == MM_TORQUE_ZL) return set_error(c, MM_ERR_ARG, "batched replicas take SOT or STT");
+    if (c->batch && batch_trials_on(c->batch))
+        return set_error(c, MM_ERR_STATE, "retire/refill sets each trial's current; set the torque before");
     c->tq = *tq;
     c->J = J ? J[0] : 0.0;
     if (c->batch) {
@@ -666,14 +677,16 @@ mm_status mm_set_torque(mm_ctx* c, const mm_torque* tq, const double* J) {
 // one chunk of `n` integrator attempts (or Heun steps) on the stream
 static void launch_attempts(mm_ctx* c, int n) {
     for (int q = 0; q < n; ++q) {
-        if (c->batch) batch_heun_step(c, c->batch);
+        if (c->batch) batch_step(c, c->batch);
         else if (c->integrator == MM_RK45) rk45_attempt(c);
         else if (c->integrator == MM_RK4) rk4_step(c);
+        else if (c->integrator == MM_DM) dm_step(c);
         else heun_step(c);
     }
 }
 
 static const int kChunk = 8;
+static const int kMacroBlock = 1024;   // steps per launch of the one-cell replica kernel
 
 // Capture `n` attempts on the context stream into an executable graph;
 // *launches receives the kernel launches one replay makes.
@@ -778,6 +791,21 @@ static mm_status advance(mm_ctx* c, long long add_steps, double t_end, int repla
     s = ensure_k1(c);
     if (s != MM_OK) return s;
     const bool heun = c->integrator != MM_RK45;   // fixed-step schemes: every attempt is accepted
+    if (c->batch && batch_is_macro(c->batch)) {
+        // one-cell replicas: blocks of fused steps, no graph needed
+        long long want = add_steps >= 0 ? add_steps
+                                        : (long long)std::ceil((t_end - c->h_state.t) / c->h_state.dt);
+        while (want > 0) {
+            const int k = (int)std::min<long long>(want, kMacroBlock);
+            batch_macro_steps(c, c->batch, k);
+            want -= k;
+        }
+        s = cuda_check(c, cudaGetLastError(), "launch");
+        if (s != MM_OK) return s;
+        s = sync_state(c);
+        if (s != MM_OK) return s;
+        return status_from_device(c);
+    }
     if (surrogate_stepping(c) && !surrogate_fallen_back(c)) {
         // host-driven blocks: exact refresh (with the error monitor) + k-1
         // network attempts; after a fallback the exact loop below takes over
@@ -852,6 +880,32 @@ mm_status mm_step_dt(mm_ctx* c, const double* dts, long n) {
     cudaError_t e = cudaMemcpy(c->d_replay, dts, sizeof(double) * n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_check(c, e, "replay upload");
     return advance(c, n, std::numeric_limits<double>::infinity(), 1);
+}
+
+mm_status mm_trials_start(mm_ctx* c, const mm_trials* sp) {
+    if (!c || !sp) return MM_ERR_ARG;
+    if (!c->batch) return set_error(c, MM_ERR_STATE, "retire/refill needs a replica-batched context (R >= 2)");
+    if (sp->n_trials < 1 || sp->max_steps < 1 || !sp->J || !sp->T || !sp->m_init)
+        return set_error(c, MM_ERR_ARG, "n_trials, max_steps >= 1 and the J, T, m_init tables are required");
+    for (int r = 1; r < c->R; ++r)
+        if (c->rgrid[r].nx != c->rgrid[0].nx || c->rgrid[r].ny != c->rgrid[0].ny)
+            return set_error(c, MM_ERR_ARG, "retire/refill needs replicas of one grid");
+    if (!(sp->axis[0] * sp->axis[0] + sp->axis[1] * sp->axis[1] + sp->axis[2] * sp->axis[2] > 0))
+        return set_error(c, MM_ERR_ARG, "zero stop axis");
+    for (long long q = 0; q < sp->n_trials; ++q)
+        if (!(sp->T[q] >= 0) || !std::isfinite(sp->J[q])) return set_error(c, MM_ERR_ARG, "bad trial T or J");
+    mm_status s = sync_state(c);
+    if (s != MM_OK) return s;
+    s = batch_trials_start(c, c->batch, sp, c->h_state.step);
+    if (s != MM_OK) return s;
+    invalidate_graph(c);
+    return MM_OK;
+}
+
+mm_status mm_trials_result(mm_ctx* c, long long* steps, int* stopped, long long* done) {
+    if (!c) return MM_ERR_ARG;
+    if (!c->batch) return set_error(c, MM_ERR_STATE, "no trials on a single-instance context");
+    return batch_trials_result(c, c->batch, steps, stopped, done);
 }
 
 mm_status mm_run(mm_ctx* c, double t_end) {

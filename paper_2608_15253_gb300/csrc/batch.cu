@@ -30,6 +30,16 @@ struct BatchHost {
     int blocks = 0;
     size_t smem = 0;
     double sigma_V = 1.0;   // cell volume used in the thermal scale
+    bool macro = false;     // every replica one cell, no demag: macro_kernel
+    // retire/refill
+    bool trials_on = false;
+    TrialDev tr{};
+    float* d_trJ = nullptr;
+    float* d_trT = nullptr;
+    float* d_minit = nullptr;
+    unsigned long long* d_trc = nullptr;   // next, done
+    long long* d_trsteps = nullptr;
+    int* d_trstop = nullptr;
 };
 
 static size_t batch_smem(const BatchHost& b, int NT) {
@@ -53,6 +63,12 @@ void batch_free(BatchHost* b) {
     cudaFree(b->d_order);
     cudaFree(b->d_next);
     cudaFree(b->d_scratch);
+    cudaFree(b->d_trJ);
+    cudaFree(b->d_trT);
+    cudaFree(b->d_minit);
+    cudaFree(b->d_trc);
+    cudaFree(b->d_trsteps);
+    cudaFree(b->d_trstop);
     for (auto& p : b->plans) demag_free_plan(p);
     delete b;
 }
@@ -79,11 +95,16 @@ mm_status batch_setup(mm_ctx* c, BatchHost* b, const std::vector<mm_grid>& grids
         d.ny = g.ny;
         d.cls = cls;
         d.off = off;
+        d.active = 1;
+        d.trial = -1;
+        d.step0 = 0;
         d.key0 = (uint32_t)(keys[r] & 0xFFFFFFFFull);
         d.key1 = (uint32_t)(keys[r] >> 32);
         b->rep[r] = d;
         off += 3LL * g.nx * g.ny;
     }
+    b->macro = !demag;
+    for (const RepDev& d : b->rep) b->macro = b->macro && d.nx == 1 && d.ny == 1;
     long long max_spec = 1;
     for (size_t q = 0; q < b->cgrid.size(); ++q) {
         const mm_grid& g = b->cgrid[q];
@@ -164,6 +185,29 @@ mm_status batch_upload(mm_ctx* c, BatchHost* b, const std::vector<double>& T, co
                       "batch descriptors");
 }
 
+// field parameters shared by every replica (per-replica ones are set in
+// the kernels)
+static void batch_field_args(mm_ctx* c, FieldArgs<float>& f) {
+    const mm_grid& g = c->grid;
+    f.lut = (const Region<float>*)c->d_lut;
+    f.cpair = (const float*)c->d_cpair;
+    f.nreg = c->nreg;
+    f.hx = (float)g.dx; f.hy = (float)g.dy; f.hz = (float)g.dz;
+    f.ix2 = (float)(1.0 / (g.dx * g.dx)); f.iy2 = (float)(1.0 / (g.dy * g.dy)); f.iz2 = (float)(1.0 / (g.dz * g.dz));
+    for (int d = 0; d < 3; ++d) f.hext[d] = (float)c->Hext[d];
+    f.st = c->d_state;
+    const mm_torque& q = c->tq;
+    f.tq = q.kind;
+    double pn = std::sqrt(q.p[0] * q.p[0] + q.p[1] * q.p[1] + q.p[2] * q.p[2]);
+    if (pn == 0) pn = 1;
+    for (int d = 0; d < 3; ++d) f.p[d] = (float)(q.p[d] / pn);
+    f.theta_half = (float)(0.5 * q.theta_SH);
+    f.fl_ratio = (float)q.fl_ratio;
+    f.P = (float)q.P;
+    f.L2 = (float)(q.Lambda * q.Lambda);
+    f.eps_p = (float)q.eps_prime;
+}
+
 static void launch_stage(mm_ctx* c, BatchHost* b, int stage) {
     BatchArgs a{};
     a.rep = b->d_rep;
@@ -178,28 +222,14 @@ static void launch_stage(mm_ctx* c, BatchHost* b, int stage) {
     a.scratch_stride = b->scratch_stride;
     a.demag = (c->terms & MM_TERM_DEMAG) ? 1 : 0;
     a.stage = stage;
+    a.dm = c->integrator == MM_DM ? 1 : 0;
+    a.trials = b->trials_on ? 1 : 0;
+    a.tr = b->tr;
     a.st = c->d_state;
     FieldArgs<float>& f = a.fa;
-    const mm_grid& g = c->grid;
-    f.lut = (const Region<float>*)c->d_lut;
-    f.cpair = (const float*)c->d_cpair;
-    f.nreg = c->nreg;
-    f.hx = (float)g.dx; f.hy = (float)g.dy; f.hz = (float)g.dz;
-    f.ix2 = (float)(1.0 / (g.dx * g.dx)); f.iy2 = (float)(1.0 / (g.dy * g.dy)); f.iz2 = (float)(1.0 / (g.dz * g.dz));
-    for (int d = 0; d < 3; ++d) f.hext[d] = (float)c->Hext[d];
+    batch_field_args(c, f);
     f.terms = c->terms & ~MM_TERM_DEMAG;
     f.terms |= a.demag ? MM_TERM_DEMAG : 0;
-    f.st = c->d_state;
-    const mm_torque& q = c->tq;
-    f.tq = q.kind;
-    double pn = std::sqrt(q.p[0] * q.p[0] + q.p[1] * q.p[1] + q.p[2] * q.p[2]);
-    if (pn == 0) pn = 1;
-    for (int d = 0; d < 3; ++d) f.p[d] = (float)(q.p[d] / pn);
-    f.theta_half = (float)(0.5 * q.theta_SH);
-    f.fl_ratio = (float)q.fl_ratio;
-    f.P = (float)q.P;
-    f.L2 = (float)(q.Lambda * q.Lambda);
-    f.eps_p = (float)q.eps_prime;
     double cells = 0;
     for (const RepDev& r : b->rep) cells += (double)r.nx * r.ny;
     cudaMemsetAsync(a.next, 0, sizeof(int), c->stream);
@@ -208,7 +238,126 @@ static void launch_stage(mm_ctx* c, BatchHost* b, int stage) {
     else batch_kernel_launch_256(a, b->blocks, b->smem, c->stream);
 }
 
-void batch_heun_step(mm_ctx* c, BatchHost* b) {
+bool batch_is_macro(BatchHost* b) { return b->macro; }
+
+// one launch of `nsteps` steps of every one-cell replica, then the step
+// bookkeeping
+void batch_macro_steps(mm_ctx* c, BatchHost* b, int nsteps) {
+    MacroArgs a{};
+    a.rep = b->d_rep;
+    a.R = (int)b->rep.size();
+    a.m = (float*)c->d_m;
+    a.dm = c->integrator == MM_DM ? 1 : 0;
+    a.trials = b->trials_on ? 1 : 0;
+    a.tr = b->tr;
+    a.st = c->d_state;
+    a.nsteps = nsteps;
+    batch_field_args(c, a.fa);
+    a.fa.terms = c->terms & ~MM_TERM_DEMAG;
+    {
+        LaunchScope ls(c, "macro_steps", (double)a.R * 24.0);
+        macro_kernel_launch(a, c->stream);
+    }
+    LaunchScope ls(c, "macro_advance", 0.0);
+    macro_advance_launch(c->d_state, nsteps, c->stream);
+}
+
+// Retire/refill (Results, "Replica batching"): trial tables, results, and
+// the first min(R, n_trials) trials loaded into the slots at the current
+// global step.
+mm_status batch_trials_start(mm_ctx* c, BatchHost* b, const mm_trials* sp, long long step_now) {
+    const long long n = sp->n_trials;
+    const int R = (int)b->rep.size();
+    const long long N = (long long)b->rep[0].nx * b->rep[0].ny;
+    cudaFree(b->d_trJ); cudaFree(b->d_trT); cudaFree(b->d_minit); cudaFree(b->d_trc);
+    cudaFree(b->d_trsteps); cudaFree(b->d_trstop);
+    b->d_trJ = b->d_trT = b->d_minit = nullptr;
+    b->d_trc = nullptr; b->d_trsteps = nullptr; b->d_trstop = nullptr;
+    cudaError_t e = cudaMalloc(&b->d_trJ, sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_trT, sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_minit, sizeof(float) * 3 * N);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_trc, sizeof(unsigned long long) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_trsteps, sizeof(long long) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_trstop, sizeof(int) * n);
+    if (e != cudaSuccess) return cuda_check(c, e, "trial tables");
+    std::vector<float> J(n), T(n);
+    for (long long q = 0; q < n; ++q) { J[q] = (float)sp->J[q]; T[q] = (float)sp->T[q]; }
+    std::vector<float> m0(3 * N, 0.f);
+    for (long long i = 0; i < N; ++i) {
+        const double x = sp->m_init[i], y = sp->m_init[N + i], z = sp->m_init[2 * N + i];
+        const double nn = std::sqrt(x * x + y * y + z * z);
+        if (nn > 0) { m0[i] = (float)(x / nn); m0[N + i] = (float)(y / nn); m0[2 * N + i] = (float)(z / nn); }
+    }
+    const unsigned long long cnt[2] = {(unsigned long long)std::min<long long>(R, n), 0ull};
+    std::vector<long long> steps(n, -1);
+    cudaMemcpy(b->d_trJ, J.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+    cudaMemcpy(b->d_trT, T.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+    cudaMemcpy(b->d_minit, m0.data(), sizeof(float) * 3 * N, cudaMemcpyHostToDevice);
+    cudaMemcpy(b->d_trc, cnt, sizeof(cnt), cudaMemcpyHostToDevice);
+    cudaMemcpy(b->d_trsteps, steps.data(), sizeof(long long) * n, cudaMemcpyHostToDevice);
+    cudaMemset(b->d_trstop, 0, sizeof(int) * n);
+    const mm_grid& g = b->cgrid[0];
+    const mm_torque& q = c->tq;
+    const double tF = q.t_F > 0 ? q.t_F : g.nz * g.dz;
+    TrialDev& t = b->tr;
+    t = TrialDev{};
+    t.n_trials = n;
+    t.max_steps = sp->max_steps;
+    t.J = b->d_trJ;
+    t.T = b->d_trT;
+    t.m_init = b->d_minit;
+    const double an = std::sqrt(sp->axis[0] * sp->axis[0] + sp->axis[1] * sp->axis[1] + sp->axis[2] * sp->axis[2]);
+    for (int d = 0; d < 3; ++d) t.axis[d] = (float)(sp->axis[d] / an);
+    t.threshold = (float)sp->threshold;
+    t.base_seed = sp->base_seed;
+    t.tq_per_J = (float)(kHbar / (kQe * kMu0 * tF));
+    t.th_per_sqrtT = (float)(1.0 / std::sqrt(g.dx * g.dy * g.dz * c->cfg.dt));
+    t.refill = sp->refill ? 1 : 0;
+    t.next = b->d_trc;
+    t.done = b->d_trc + 1;
+    t.steps = b->d_trsteps;
+    t.stopped = b->d_trstop;
+    std::vector<float> all(3 * c->Ntot);
+    e = cudaMemcpy(all.data(), c->d_m, sizeof(float) * 3 * c->Ntot, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_check(c, e, "trial state");
+    for (int r = 0; r < R; ++r) {
+        RepDev& d = b->rep[r];
+        if (r < n) {
+            const unsigned long long key = splitmix64_dev(sp->base_seed + (unsigned long long)r);
+            d.active = 1;
+            d.trial = r;
+            d.step0 = step_now;
+            d.key0 = (uint32_t)(key & 0xFFFFFFFFull);
+            d.key1 = (uint32_t)(key >> 32);
+            d.th_scale = T[r] > 0 ? (float)std::sqrt((double)T[r]) * t.th_per_sqrtT : 0.f;
+            d.tq_base = J[r] * t.tq_per_J;
+            std::copy(m0.begin(), m0.end(), all.begin() + d.off);
+        } else {
+            d.active = 0;
+            d.trial = -1;
+        }
+    }
+    cudaMemcpy(c->d_m, all.data(), sizeof(float) * 3 * c->Ntot, cudaMemcpyHostToDevice);
+    b->trials_on = true;
+    return cuda_check(c, cudaMemcpy(b->d_rep, b->rep.data(), sizeof(RepDev) * R, cudaMemcpyHostToDevice),
+                      "trial slots");
+}
+
+mm_status batch_trials_result(mm_ctx* c, BatchHost* b, long long* steps, int* stopped, long long* done) {
+    if (!b->trials_on) return set_error(c, MM_ERR_STATE, "no trials started");
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    const long long n = b->tr.n_trials;
+    if (e == cudaSuccess && steps) e = cudaMemcpy(steps, b->d_trsteps, sizeof(long long) * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && stopped) e = cudaMemcpy(stopped, b->d_trstop, sizeof(int) * n, cudaMemcpyDeviceToHost);
+    unsigned long long cnt[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(cnt, b->d_trc, sizeof(cnt), cudaMemcpyDeviceToHost);
+    if (done) *done = (long long)cnt[1];
+    return cuda_check(c, e, "trial results");
+}
+
+bool batch_trials_on(BatchHost* b) { return b->trials_on; }
+
+void batch_step(mm_ctx* c, BatchHost* b) {
     heun_batch_begin(c);
     launch_stage(c, b, 1);
     launch_stage(c, b, 2);

@@ -1,7 +1,7 @@
 // Replica batching (Methods, "Replica batching"): R independent thin-film
 // replicas (nz = 1) of possibly different sizes advance together, each with
 // its own Philox key, temperature and current density.  One persistent
-// launch per Heun stage: every CTA takes whole replicas, one after another,
+// launch per stage of the Heun or Depondt-Mertens step: every CTA takes whole replicas, one after another,
 // from a shared work counter over a size-mixed order and runs, for each, the
 // three demag phases
 // (row R2C, column convolution with the size class's tensor spectrum,
@@ -39,12 +39,84 @@ namespace mm {
 constexpr int kMaxVB = 24;
 
 struct RepDev {
-    int nx, ny, cls, pad;
+    int nx, ny, cls;
+    int active;             // 0: an idle slot (retire/refill ran out of trials)
     long long off;          // element offset of the replica's [3][ny][nx] block
     uint32_t key0, key1;    // Philox key
     float th_scale;         // sqrt(T / (V dt))
     float tq_base;          // hbar J / (e mu0 t_F)
+    long long trial;        // trial running in this slot (retire/refill), else -1
+    long long step0;        // global step at which that trial started: the noise
+                            // counter is the trial's own step, step - step0
 };
+
+// Retire/refill of batched trials (Results, "Replica batching"): trial q has
+// its own current J[q], temperature T[q] and Philox key splitmix64(base + q)
+// and starts from m_init; after every step a slot whose trial has
+// mean(m . axis) <= threshold, or has taken max_steps steps, records the
+// outcome and, with refill, starts the next trial not yet started.
+struct TrialDev {
+    long long n_trials, max_steps;
+    const float* J;                 // [n_trials]
+    const float* T;                 // [n_trials]
+    const float* m_init;            // [3][N] of the common replica grid
+    float axis[3];
+    float threshold;
+    unsigned long long base_seed;
+    float tq_per_J;                 // hbar / (e mu0 t_F)
+    float th_per_sqrtT;             // 1 / sqrt(V dt)
+    int refill;
+    unsigned long long* next;       // next trial to start
+    unsigned long long* done;       // trials finished
+    long long* steps;               // per trial: steps taken (-1 until finished)
+    int* stopped;                   // per trial: 1 if the stop condition ended it
+};
+
+// splitmix64 (Steele, Lea and Flood, 2014): the trial key schedule
+__host__ __device__ __forceinline__ unsigned long long splitmix64_dev(unsigned long long x) {
+    unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// End-of-step check of one slot (one thread): records a finished trial and
+// loads the next one into rp (and into the slot's descriptor in global
+// memory).  Returns 1 when a new trial starts (the caller resets m to
+// m_init), 0 otherwise.  steps_taken counts the trial's steps including the
+// one just finished; step_next is the global step the next trial starts at.
+__device__ __forceinline__ int trial_check(const TrialDev& tr, RepDev& rp, RepDev* rp_glob, float mean_proj,
+                                           long long steps_taken, long long step_next) {
+    const bool stop = mean_proj <= tr.threshold;
+    if (!stop && steps_taken < tr.max_steps) return 0;
+    const long long q = rp.trial;
+    tr.steps[q] = steps_taken;
+    tr.stopped[q] = stop ? 1 : 0;
+    atomicAdd(tr.done, 1ull);
+    const unsigned long long qn = tr.refill ? atomicAdd(tr.next, 1ull) : (unsigned long long)tr.n_trials;
+    if (qn >= (unsigned long long)tr.n_trials) {
+        rp.active = 0;
+        rp.trial = -1;
+        rp_glob->active = 0;
+        rp_glob->trial = -1;
+        return 0;
+    }
+    const unsigned long long key = splitmix64_dev(tr.base_seed + qn);
+    rp.trial = (long long)qn;
+    rp.step0 = step_next;
+    rp.key0 = (uint32_t)(key & 0xFFFFFFFFull);
+    rp.key1 = (uint32_t)(key >> 32);
+    const float T = tr.T[qn];
+    rp.th_scale = T > 0.f ? sqrtf(T) * tr.th_per_sqrtT : 0.f;
+    rp.tq_base = tr.J[qn] * tr.tq_per_J;
+    rp_glob->trial = rp.trial;
+    rp_glob->step0 = rp.step0;
+    rp_glob->key0 = rp.key0;
+    rp_glob->key1 = rp.key1;
+    rp_glob->th_scale = rp.th_scale;
+    rp_glob->tq_base = rp.tq_base;
+    return 1;
+}
 
 struct ClsDev {
     int nx, ny, Lh, Py, Kx, Wk, Ky;
@@ -55,7 +127,7 @@ struct ClsDev {
 };
 
 struct BatchArgs {
-    const RepDev* rep;
+    RepDev* rep;
     const ClsDev* cls;
     const int* order;
     int* next;              // work counter of this stage (zeroed before the launch)
@@ -68,6 +140,9 @@ struct BatchArgs {
     FieldArgs<float> fa;    // shared field parameters (per-replica fields set in-kernel)
     int demag;
     int stage;              // 1: predictor, 2: corrector
+    int dm;                 // 1: Depondt-Mertens rotation, 0: Heun
+    int trials;             // 1: retire/refill is on (tr is valid)
+    TrialDev tr;
     const DevState* st;
 };
 
@@ -191,10 +266,12 @@ __device__ __noinline__ void stage_phase_y(int ny, const ClsDev& cd, float2* S, 
 }
 
 // phase C: C2R rows of a block of y (three components) + field + update
+// Returns this thread's share of sum over cells of m_new . axis (stage 2
+// with retire/refill on; 0 otherwise).
 template <int LX, int NT>
-__device__ __noinline__ void stage_phase_c(const BatchArgs& a, const RepDev& rp, const ClsDev& cd, float* mE,
-                                           long long N, int nx, int ny, float2* S, float2* sm, long long step,
-                                           float dt) {
+__device__ __noinline__ float stage_phase_c(const BatchArgs& a, const RepDev& rp, const ClsDev& cd, float* mE,
+                                            long long N, int nx, int ny, float2* S, float2* sm, long long step,
+                                            float dt) {
     FieldArgs<float> fa = a.fa;
     fa.m = mE;
     fa.N = N;
@@ -206,6 +283,9 @@ __device__ __noinline__ void stage_phase_c(const BatchArgs& a, const RepDev& rp,
     fa.th_scale = rp.th_scale;
     fa.tq_base = rp.tq_base;
     const Region<float>& R = fa.lut[0];
+    const bool proj_on = a.trials && a.stage == 2;
+    const v3<float> ax = mk3<float>(a.tr.axis[0], a.tr.axis[1], a.tr.axis[2]);
+    float proj = 0.f;
     const int Lh = LX > 0 ? LX : cd.Lh;
     const int pitch = Lh + 1;
     float* smr = reinterpret_cast<float*>(sm);
@@ -246,24 +326,54 @@ __device__ __noinline__ void stage_phase_c(const BatchArgs& a, const RepDev& rp,
                 hd = mk3<float>(smr[2 * (0 * nyb + yl) * pitch + x], smr[2 * (1 * nyb + yl) * pitch + x],
                                 smr[2 * (2 * nyb + yl) * pitch + x]);
             v3<float> H, k;
-            cell_field<float>(fa, x, y, 0, i, 0, R, m, a.demag ? &hd : nullptr, step, H, k, true);
+            cell_field<float>(fa, x, y, 0, i, 0, R, m, a.demag ? &hd : nullptr, step - rp.step0, H, k, true,
+                              a.dm != 0);
+            // k: the slope (Heun) or the rotation vector Omega (Depondt-Mertens)
             if (a.stage == 1) {
                 st3(a.k1 + rp.off, N, i, k);
-                st3(a.ms + rp.off, N, i, m + dt * k);
+                st3(a.ms + rp.off, N, i, a.dm ? rodrigues<float>(m, k, dt) : m + dt * k);
             } else {
                 const v3<float> m0 = ld3(a.m0 + rp.off, N, i);
                 const v3<float> kp = ld3(a.k1 + rp.off, N, i);
-                const v3<float> mn = m0 + (0.5f * dt) * (kp + k);
-                st3(a.m0 + rp.off, N, i, rsqrtf(dot(mn, mn)) * mn);
+                const v3<float> mn = a.dm ? rodrigues<float>(m0, 0.5f * (kp + k), dt) : m0 + (0.5f * dt) * (kp + k);
+                const v3<float> mu = rsqrtf(dot(mn, mn)) * mn;
+                st3(a.m0 + rp.off, N, i, mu);
+                if (proj_on) proj += dot(mu, ax);
             }
         }
         __syncthreads();
     }
+    return proj;
+}
+
+// Retire/refill after the corrector: the mean of m . axis over the replica
+// (block reduction), the stop test by one thread, and, when a new trial
+// takes the slot, its initial state written by the whole CTA.
+template <int NT>
+__device__ __forceinline__ void slot_retire_refill(const BatchArgs& a, RepDev rp, int idx, float part, long long N,
+                                                   long long step) {
+    __shared__ float s_red[NT / 32];
+    __shared__ int s_new;
+    float v = part;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float tot = 0.f;
+        for (int w = 0; w < NT / 32; ++w) tot += s_red[w];
+        s_new = trial_check(a.tr, rp, a.rep + idx, tot / (float)N, step + 1 - rp.step0, step + 1);
+    }
+    __syncthreads();
+    if (s_new) {
+        float* m = a.m0 + rp.off;
+        for (long long e = threadIdx.x; e < 3 * N; e += NT) m[e] = __ldg(a.tr.m_init + e);
+    }
+    __syncthreads();
 }
 
 template <int LX, int LY, int NT>
-__device__ __forceinline__ void replica_stage(const BatchArgs& a, const RepDev& rp, const ClsDev& cd, float2* S,
-                                              float2* sm, long long step, float dt) {
+__device__ __forceinline__ void replica_stage(const BatchArgs& a, const RepDev& rp, int idx, const ClsDev& cd,
+                                              float2* S, float2* sm, long long step, float dt) {
     const int nx = rp.nx, ny = rp.ny;
     const long long N = (long long)nx * ny;
     float* mE = (a.stage == 1 ? a.m0 : a.ms) + rp.off;
@@ -271,7 +381,8 @@ __device__ __forceinline__ void replica_stage(const BatchArgs& a, const RepDev& 
         stage_phase_x<LX, NT>(mE, N, nx, ny, a.fa.lut[0].Ms, cd, S, sm);
         stage_phase_y<LY, NT>(ny, cd, S, sm);
     }
-    stage_phase_c<LX, NT>(a, rp, cd, mE, N, nx, ny, S, sm, step, dt);
+    const float part = stage_phase_c<LX, NT>(a, rp, cd, mE, N, nx, ny, S, sm, step, dt);
+    if (a.trials && a.stage == 2) slot_retire_refill<NT>(a, rp, idx, part, N, step);
 }
 
 template <int NT>
@@ -290,17 +401,36 @@ __global__ void __launch_bounds__(NT) batch_stage_kernel(BatchArgs a) {
         const int w = s_w;
         __syncthreads();
         if (w >= a.R) break;
-        const RepDev rp = a.rep[a.order[w]];
+        const int idx = a.order[w];
+        const RepDev rp = a.rep[idx];
+        if (!rp.active) continue;   // uniform across the CTA
         const ClsDev& cd = a.cls[rp.cls];
         const int key = cd.Lh * 10000 + cd.Py;
         switch (key) {
-#define MM_B(lh, py) case lh * 10000 + py: replica_stage<lh, py, NT>(a, rp, cd, S, sm, step, dt); break;
+#define MM_B(lh, py) case lh * 10000 + py: replica_stage<lh, py, NT>(a, rp, idx, cd, S, sm, step, dt); break;
             MM_B(16, 32) MM_B(32, 64) MM_B(48, 96) MM_B(64, 128) MM_B(96, 192) MM_B(128, 256) MM_B(256, 512)
 #undef MM_B
-            default: replica_stage<0, 0, NT>(a, rp, cd, S, sm, step, dt); break;
+            default: replica_stage<0, 0, NT>(a, rp, idx, cd, S, sm, step, dt); break;
         }
     }
 }
+
+// Replicas of one cell each (Results, "Replica batching", the macrospin
+// ensemble): one thread per slot keeps its moment in registers for a block
+// of nsteps steps (macro.cu).
+struct MacroArgs {
+    RepDev* rep;
+    int R;
+    float* m;               // [R][3]
+    FieldArgs<float> fa;
+    int dm;
+    int trials;
+    TrialDev tr;
+    const DevState* st;
+    int nsteps;
+};
+void macro_kernel_launch(const MacroArgs& a, cudaStream_t s);
+void macro_advance_launch(DevState* st, int nsteps, cudaStream_t s);
 
 // host wrappers, one set per instantiated thread count
 cudaError_t batch_kernel_attributes_256();

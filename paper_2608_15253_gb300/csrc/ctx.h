@@ -196,7 +196,9 @@ void demag_apply_stage(mm_ctx* c, int stage, void* Hd);
 mm_status newell_gpu(long count, const int* ijk, double dx, double dy, double dz, double* out_host);
 
 // field.cu
-enum FieldMode { MODE_H = 0, MODE_K = 1, MODE_HEUN1 = 2, MODE_HEUN2 = 3 };
+// MODE_DM1 / MODE_DM2: Depondt-Mertens predictor (out <- rotated m, out2 <-
+// Omega) and corrector (out <- m0 rotated by the mean Omega, k1 = Omega_1)
+enum FieldMode { MODE_H = 0, MODE_K = 1, MODE_HEUN1 = 2, MODE_HEUN2 = 3, MODE_DM1 = 4, MODE_DM2 = 5 };
 void field_launch(mm_ctx* c, int mode, unsigned terms, const void* m, const void* Hd,
                   void* out, void* out2, const void* m0, const void* k1, long long step_override,
                   int gate, int kstage);
@@ -208,7 +210,12 @@ void batch_free(BatchHost* b);
 mm_status batch_setup(mm_ctx* c, BatchHost* b, const std::vector<mm_grid>& grids, const std::vector<uint64_t>& keys,
                       bool demag);
 mm_status batch_upload(mm_ctx* c, BatchHost* b, const std::vector<double>& T, const std::vector<double>& J);
-void batch_heun_step(mm_ctx* c, BatchHost* b);
+void batch_step(mm_ctx* c, BatchHost* b);
+bool batch_is_macro(BatchHost* b);
+void batch_macro_steps(mm_ctx* c, BatchHost* b, int nsteps);
+mm_status batch_trials_start(mm_ctx* c, BatchHost* b, const mm_trials* sp, long long step_now);
+mm_status batch_trials_result(mm_ctx* c, BatchHost* b, long long* steps, int* stopped, long long* done);
+bool batch_trials_on(BatchHost* b);
 void batch_set_shape(BatchHost* b, int nt, int blocks);
 int batch_max_blocks(BatchHost* b);
 size_t batch_smem_for(BatchHost* b, int nt);
@@ -237,7 +244,8 @@ void heun_batch_begin(mm_ctx* c);
 void heun_batch_advance(mm_ctx* c);
 void rk45_first_slope(mm_ctx* c);          // k1 = f(m0) into the FSAL slot
 void rk45_attempt(mm_ctx* c);               // one attempted DOPRI5 step
-void heun_step(mm_ctx* c);                  // one Heun step
+void heun_step(mm_ctx* c);
+void dm_step(mm_ctx* c);                  // one Heun step
 void rk4_step(mm_ctx* c);                   // one classical RK4 step
 
 // reduce.cu

@@ -37,13 +37,13 @@ __global__ void __launch_bounds__(256) field_kernel(FieldArgs<T> a) {
             const int kf = a.st->k_first;
             o = a.kptr[a.kstage == 0 ? kf : 6 - kf];
         }
-        if (a.mode == MODE_HEUN1) { st3(o, N, i, zero); st3(a.out2, N, i, zero); }
+        if (a.mode == MODE_HEUN1 || a.mode == MODE_DM1) { st3(o, N, i, zero); st3(a.out2, N, i, zero); }
         else st3(o, N, i, zero);
         return;
     }
     const long long step = a.step_override >= 0 ? a.step_override : (a.st ? a.st->step : 0);
     v3<T> H, k;
-    cell_field<T, UNIF>(a, x, y, z, i, ri, R, m, nullptr, step, H, k, a.mode != MODE_H);
+    cell_field<T, UNIF>(a, x, y, z, i, ri, R, m, nullptr, step, H, k, a.mode != MODE_H, a.mode >= MODE_DM1);
     if (a.mode == MODE_H) {
         st3(a.out, N, i, H);
         return;
@@ -59,11 +59,22 @@ __global__ void __launch_bounds__(256) field_kernel(FieldArgs<T> a) {
         const T dt = (T)a.st->dt;
         st3(a.out2, N, i, k);
         st3(a.out, N, i, m + dt * k);
-    } else {  // MODE_HEUN2: m_new = normalise(m0 + dt/2 (k1 + k2))
+    } else if (a.mode == MODE_HEUN2) {  // m_new = normalise(m0 + dt/2 (k1 + k2))
         const T dt = (T)a.st->dt;
         const v3<T> m0 = ld3(a.m0, N, i);
         const v3<T> k1 = ld3(a.k1, N, i);
         v3<T> mn = m0 + ((T)0.5 * dt) * (k1 + k);
+        const T inv = (T)1 / sqrt(dot(mn, mn));
+        st3(a.out, N, i, inv * mn);
+    } else if (a.mode == MODE_DM1) {   // Omega_1 and m* = R(Omega_1 dt) m
+        const T dt = (T)a.st->dt;
+        st3(a.out2, N, i, k);
+        st3(a.out, N, i, rodrigues<T>(m, k, dt));
+    } else {  // MODE_DM2: m_new = R((Omega_1 + Omega_2) dt / 2) m0
+        const T dt = (T)a.st->dt;
+        const v3<T> m0 = ld3(a.m0, N, i);
+        const v3<T> w1 = ld3(a.k1, N, i);
+        const v3<T> mn = rodrigues<T>(m0, (T)0.5 * (w1 + k), dt);
         const T inv = (T)1 / sqrt(dot(mn, mn));
         st3(a.out, N, i, inv * mn);
     }
@@ -181,7 +192,8 @@ __global__ void __launch_bounds__(256) field_vec_kernel(FieldArgs<float> a) {
         }
         const v3<float> hq = dem ? mk3<float>(fget(hd[0], q), fget(hd[1], q), fget(hd[2], q)) : mk3<float>(0, 0, 0);
         v3<float> H, k;
-        cell_field_nb<float>(a, i0 + q, R, m, nbv, nbp, cnb, dem, hq, step, H, k, a.mode != MODE_H);
+        cell_field_nb<float>(a, i0 + q, R, m, nbv, nbp, cnb, dem, hq, step, H, k, a.mode != MODE_H,
+                             a.mode >= MODE_DM1);
         v3<float> r1 = H, r2 = k;
         if (a.mode == MODE_K) r1 = k;
         else if (a.mode == MODE_HEUN1) {
@@ -195,6 +207,15 @@ __global__ void __launch_bounds__(256) field_vec_kernel(FieldArgs<float> a) {
             const v3<float> k1 = ld3(a.k1, N, i);
             v3<float> mn = m0 + (0.5f * dt) * (k1 + k);
             r1 = (1.0f / sqrtf(dot(mn, mn))) * mn;
+        } else if (a.mode == MODE_DM1) {
+            r1 = rodrigues<float>(m, k, (float)a.st->dt);
+            r2 = k;
+        } else if (a.mode == MODE_DM2) {
+            const long long i = i0 + q;
+            const v3<float> m0 = ld3(a.m0, N, i);
+            const v3<float> w1 = ld3(a.k1, N, i);
+            const v3<float> mn = rodrigues<float>(m0, 0.5f * (w1 + k), (float)a.st->dt);
+            r1 = (1.0f / sqrtf(dot(mn, mn))) * mn;
         }
         fset(o1[0], q, r1.x); fset(o1[1], q, r1.y); fset(o1[2], q, r1.z);
         fset(o2[0], q, r2.x); fset(o2[1], q, r2.y); fset(o2[2], q, r2.z);
@@ -206,7 +227,7 @@ __global__ void __launch_bounds__(256) field_vec_kernel(FieldArgs<float> a) {
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) stv<V>(o + c * N + i0, o1[c]);
-    if (a.mode == MODE_HEUN1) {
+    if (a.mode == MODE_HEUN1 || a.mode == MODE_DM1) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) stv<V>(a.out2 + c * N + i0, o2[c]);
     }
@@ -270,9 +291,9 @@ static void field_launch_t(mm_ctx* c, int mode, unsigned terms, const T* m, cons
     const double es = sizeof(T);
     double bytes = 3 * es * 2 * c->N;          // read m, write out
     if (Hd && (terms & MM_TERM_DEMAG)) bytes += 3 * es * c->N;
-    if (mode == MODE_HEUN1) bytes += 3 * es * c->N;
-    if (mode == MODE_HEUN2) bytes += 6 * es * c->N;
-    static const char* names[4] = {"field_H", "field_k", "field_heun1", "field_heun2"};
+    if (mode == MODE_HEUN1 || mode == MODE_DM1) bytes += 3 * es * c->N;
+    if (mode == MODE_HEUN2 || mode == MODE_DM2) bytes += 6 * es * c->N;
+    static const char* names[6] = {"field_H", "field_k", "field_heun1", "field_heun2", "field_dm1", "field_dm2"};
     LaunchScope ls(c, names[mode], bytes);
     if (c->uniform && !a.region) {
         if constexpr (sizeof(T) == 4) { a.R0 = c->r0f; a.c_uniform = c->c00f; }

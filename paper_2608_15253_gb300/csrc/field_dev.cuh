@@ -112,11 +112,18 @@ __device__ __forceinline__ void st3(T* a, long long N, long long i, v3<T> v) {
 // coefficients cnb.  use_hd: hdv is the demag field; otherwise a.Hd[i] is
 // read (when set).  Neighbour arrays are only read when the
 // exchange or DMI term or the Zhang-Li torque is on.
+// as_omega: k receives instead the rotation vector Omega of the
+// Depondt-Mertens scheme, dm/dt = Omega x m (Methods, "Integrators"): with
+// -m x H = H x m and -m x (m x H) = (m x H) x m,
+//   Omega = gamma' mu0 [H + alpha m x H]
+//         + gamma' mu0 [(h_DL + alpha h_FL) m x p + (h_FL - alpha h_DL) p]
+//         + [(1 + alpha xi) m x u' + (xi - alpha) u'] / (1 + alpha^2),
+// u' = (u.grad) m, so that Omega x m is the slope.
 template <typename T>
 __device__ __forceinline__ void cell_field_nb(const FieldArgs<T>& a, long long i, const Region<T>& R,
                                               const v3<T>& m, const v3<T>* nbv, const bool* nbp, const T* cnb,
                                               bool use_hd, const v3<T>& hdv, long long step, v3<T>& H, v3<T>& k,
-                                              bool want_k) {
+                                              bool want_k, bool as_omega = false) {
     const long long N = a.N;
     H = mk3<T>(0, 0, 0);
     k = mk3<T>(0, 0, 0);
@@ -156,7 +163,8 @@ __device__ __forceinline__ void cell_field_nb(const FieldArgs<T>& a, long long i
     if (!want_k) return;
     // LLG torque, Eq. 1: -gamma' mu0 [m x H + alpha m x (m x H)]
     const v3<T> mxH = cross(m, H);
-    k = (-R.gm) * (mxH + R.alpha * cross(m, mxH));
+    if (as_omega) k = R.gm * (H + R.alpha * mxH);
+    else k = (-R.gm) * (mxH + R.alpha * cross(m, mxH));
     if (a.tq == MM_TORQUE_SOT || a.tq == MM_TORQUE_STT) {
         const v3<T> p = mk3<T>(a.p[0], a.p[1], a.p[2]);
         const T base = a.tq_base * R.inv_Ms;
@@ -170,7 +178,9 @@ __device__ __forceinline__ void cell_field_nb(const FieldArgs<T>& a, long long i
             hfl = a.eps_p * base;
         }
         const v3<T> mxp = cross(m, p);
-        k = k + (-R.gm) * ((hdl + R.alpha * hfl) * cross(m, mxp) + (hfl - R.alpha * hdl) * mxp);
+        const T cdl = hdl + R.alpha * hfl, cfl = hfl - R.alpha * hdl;
+        if (as_omega) k = k + R.gm * (cdl * mxp + cfl * p);
+        else k = k + (-R.gm) * (cdl * cross(m, mxp) + cfl * mxp);
     } else if (a.tq == MM_TORQUE_ZL) {
         // (u.grad) m, central differences, absent neighbour = the cell itself
         const T u = a.zl_u * R.inv_Ms;
@@ -186,8 +196,38 @@ __device__ __forceinline__ void cell_field_nb(const FieldArgs<T>& a, long long i
         const v3<T> ug = u * g;
         const v3<T> mxug = cross(m, ug);
         const T inv = (T)1 / ((T)1 + R.alpha * R.alpha);
-        k = k + inv * ((-((T)1 + R.alpha * a.xi)) * cross(m, mxug) + (-(a.xi - R.alpha)) * mxug);
+        if (as_omega) k = k + inv * (((T)1 + R.alpha * a.xi) * mxug + (a.xi - R.alpha) * ug);
+        else k = k + inv * ((-((T)1 + R.alpha * a.xi)) * cross(m, mxug) + (-(a.xi - R.alpha)) * mxug);
     }
+}
+
+__device__ __forceinline__ void sincos_t(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_t(double x, double* s, double* c) { sincos(x, s, c); }
+
+// Rotation of m about w by the angle a = |w| dt, right-handed (Rodrigues):
+//   m + s (w x m) + q (w (w.m) - |w|^2 m),  s = sin(a) / |w|,
+//   q = (1 - cos a) / |w|^2,
+// with sin a = 2 sin(a/2) cos(a/2) and 1 - cos a = 2 sin^2(a/2) from one
+// half-angle sincos; for a^2 < 1e-6 (w = 0 included) the Taylor series
+// sin(a)/a = 1 - a^2/6 + a^4/120 and (1 - cos a)/a^2 = 1/2 - a^2/24 + a^4/720
+// (next terms below 1e-21).  For constant w this is the exact solution of
+// dm/dt = w x m over dt.
+template <typename T>
+__device__ __forceinline__ v3<T> rodrigues(const v3<T>& m, const v3<T>& w, T dt) {
+    const T w2 = dot(w, w);
+    const T a2 = w2 * dt * dt;
+    T s, q;
+    if (a2 < (T)1e-6) {
+        s = dt * ((T)1 - a2 * ((T)(1.0 / 6.0) - a2 * (T)(1.0 / 120.0)));
+        q = dt * dt * ((T)0.5 - a2 * ((T)(1.0 / 24.0) - a2 * (T)(1.0 / 720.0)));
+    } else {
+        const T a = sqrt(a2);
+        T sh, ch;
+        sincos_t((T)0.5 * a, &sh, &ch);
+        s = dt * ((T)2 * sh * ch) / a;
+        q = dt * dt * ((T)2 * sh * sh) / a2;
+    }
+    return m + s * cross(w, m) + q * (dot(w, m) * w - w2 * m);
 }
 
 // Ghost value of an absent neighbour in direction d (0 x, 1 y, 2 z) and
@@ -201,13 +241,14 @@ __device__ __forceinline__ v3<T> ghost_value(const v3<T>& m, int d, int sg, T h,
 }
 
 // Effective field of one present cell (x, y, z; linear index i) and, when
-// want_k, its LLG slope with the configured spin torque.  UNIF: one material
+// want_k, its LLG slope with the configured spin torque (as_omega: the
+// rotation vector, see cell_field_nb).  UNIF: one material
 // everywhere (no region map): every in-grid neighbour is present and every
 // exchange pair uses the one coefficient a.c_uniform.
 template <typename T, bool UNIF = false>
 __device__ __forceinline__ void cell_field(const FieldArgs<T>& a, int x, int y, int z, long long i, int ri,
                                            const Region<T>& R, const v3<T>& m, const v3<T>* hd, long long step,
-                                           v3<T>& H, v3<T>& k, bool want_k) {
+                                           v3<T>& H, v3<T>& k, bool want_k, bool as_omega = false) {
     const long long N = a.N;
     const bool need_nb = (a.terms & (MM_TERM_EXCHANGE | MM_TERM_DMI)) || a.tq == MM_TORQUE_ZL;
     // neighbour values (ghosts where absent) and raw presence for Zhang-Li
@@ -252,7 +293,8 @@ __device__ __forceinline__ void cell_field(const FieldArgs<T>& a, int x, int y, 
             }
         }
     }
-    cell_field_nb<T>(a, i, R, m, nbv, nbp, cnb, hd != nullptr, hd ? *hd : mk3<T>(0, 0, 0), step, H, k, want_k);
+    cell_field_nb<T>(a, i, R, m, nbv, nbp, cnb, hd != nullptr, hd ? *hd : mk3<T>(0, 0, 0), step, H, k, want_k,
+                     as_omega);
 }
 
 }  // namespace mm

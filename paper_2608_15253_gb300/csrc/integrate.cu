@@ -385,4 +385,27 @@ void heun_step(mm_ctx* c) {
     heun_advance_kernel<<<1, 1, 0, c->stream>>>(c->d_state);
 }
 
+// Depondt-Mertens (Methods, "Integrators"): Omega_1 = Omega(m) and the
+// predictor m* = R(Omega_1 dt) m in one launch, then Omega_2 = Omega(m*) and
+// m <- R((Omega_1 + Omega_2) dt / 2) m in the next; one thermal draw per step
+// (the step counter advances after the corrector).  The rotation keeps |m|;
+// the corrector also rescales by 1/|m|, a round-off-level change that keeps
+// long FP32 runs from drifting.
+void dm_step(mm_ctx* c) {
+    const unsigned terms = c->terms;
+    const bool demag = c->dm.on && (terms & MM_TERM_DEMAG);
+    {
+        LaunchScope ls(c, "dm_begin", 0.0);
+        heun_begin_kernel<<<1, 1, 0, c->stream>>>(c->d_state);
+    }
+    if (demag) demag_apply(c, c->d_m, c->d_hd);
+    field_launch(c, MODE_DM1, terms, c->d_m, demag ? c->d_hd : nullptr, c->d_mtmp, c->d_k[0], nullptr, nullptr,
+                 -1, 1, 0);
+    if (demag) demag_apply(c, c->d_mtmp, c->d_hd);
+    field_launch(c, MODE_DM2, terms, c->d_mtmp, demag ? c->d_hd : nullptr, c->d_m, nullptr, c->d_m, c->d_k[0],
+                 -1, 1, 0);
+    LaunchScope ls(c, "dm_advance", 0.0);
+    heun_advance_kernel<<<1, 1, 0, c->stream>>>(c->d_state);
+}
+
 }  // namespace mm

@@ -21,7 +21,7 @@ _lock = threading.Lock()
 
 MM_OK, MM_ERR_ARG, MM_ERR_DEVICE, MM_ERR_OOM, MM_ERR_CUDA = 0, 1, 2, 3, 4
 MM_ERR_NONFINITE, MM_ERR_DT_UNDERFLOW, MM_ERR_TIMEOUT, MM_ERR_STATE = 5, 6, 7, 8
-MM_HEUN, MM_RK45, MM_RK4 = 0, 1, 2
+MM_HEUN, MM_RK45, MM_RK4, MM_DM = 0, 1, 2, 3
 MM_DEMAG_OFF, MM_DEMAG_EXACT, MM_DEMAG_SURROGATE = 0, 1, 2
 MM_TERM_EXCHANGE, MM_TERM_DMI, MM_TERM_ANISOTROPY = 1, 2, 4
 MM_TERM_ZEEMAN, MM_TERM_DEMAG, MM_TERM_THERMAL, MM_TERM_ALL = 8, 16, 32, 63
@@ -76,6 +76,12 @@ class mm_surrogate_stats(C.Structure):
                 ("train_loss", C.c_double), ("c_in", C.c_double), ("c_out", C.c_double)]
 
 
+class mm_trials(C.Structure):
+    _fields_ = [("n_trials", C.c_longlong), ("J", _D), ("T", _D), ("m_init", _D), ("axis", C.c_double * 3),
+                ("threshold", C.c_double), ("max_steps", C.c_longlong), ("base_seed", C.c_uint64),
+                ("refill", C.c_int)]
+
+
 class MMError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"libmm status {status}: {msg}")
@@ -111,6 +117,8 @@ _SIGS = {
     "mm_topo_charge_noalloc": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
                                C.c_void_p, C.c_void_p],
     "mm_batch_autotune": [C.c_void_p, C.c_char_p, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+    "mm_trials_start": [C.c_void_p, C.POINTER(mm_trials)],
+    "mm_trials_result": [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_longlong)],
     "mm_surrogate_train": [C.c_void_p, C.POINTER(mm_train_cfg), _D],
     "mm_surrogate_set": [C.c_void_p, C.c_int, C.c_double],
     "mm_surrogate_get_stats": [C.c_void_p, C.POINTER(mm_surrogate_stats)],
@@ -324,6 +332,31 @@ def mm_batch_autotune(ctx, cache_path: str | None = None):
     _check(load().mm_batch_autotune(ctx, cache_path.encode() if cache_path else None, C.byref(nt), C.byref(blocks)),
            ctx)
     return nt.value, blocks.value
+
+
+def mm_trials_start(ctx, J, T, m_init, axis=(0.0, 0.0, 1.0), threshold=0.0, max_steps=1000, base_seed=0,
+                    refill=True):
+    """Retire/refill over len(J) trials; J, T per trial, m_init (3, 1, ny, nx)."""
+    J = np.ascontiguousarray(J, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    m0 = np.ascontiguousarray(m_init, dtype=np.float64)
+    if J.shape != T.shape:
+        raise ValueError("J and T need one entry per trial")
+    sp = mm_trials(J.size, _dptr(J), _dptr(T), _dptr(m0), (C.c_double * 3)(*axis), threshold, max_steps,
+                   int(base_seed), 1 if refill else 0)
+    _check(load().mm_trials_start(ctx, C.byref(sp)), ctx)
+    ctx._trials_n = J.size
+
+
+def mm_trials_result(ctx):
+    """(steps[n], stopped[n], done): steps -1 while a trial is unfinished."""
+    n = ctx._trials_n
+    steps = np.zeros(n, dtype=np.int64)
+    stopped = np.zeros(n, dtype=np.int32)
+    done = C.c_longlong(0)
+    _check(load().mm_trials_result(ctx, steps.ctypes.data_as(C.POINTER(C.c_longlong)),
+                                   stopped.ctypes.data_as(C.POINTER(C.c_int)), C.byref(done)), ctx)
+    return steps, stopped.astype(bool), done.value
 
 
 SURROGATE_NPARAMS = 56099
