@@ -287,6 +287,101 @@ def variant_batched(mm, stream, steps):
                               "against": "FP64 single-instance GPU runs with the same Philox key"}}
 
 
+# The paper's replica-batching table (Results, "Replica batching"): physics,
+# replica grid, replica count R, and its published throughput (on its own
+# hardware, an RTX 5060 Ti).  Materials are not printed there; the
+# perpendicular Co-like film used here is stated in the output.
+BATCH_TABLE = [
+    ("macrospin: anisotropy + STT + thermal", (1, 1), 1024, 4 | 8 | 32, False, "replica-steps/s", 3.7e7),
+    ("8x8x1: exchange + uniaxial + Zeeman", (8, 8), 256, 1 | 4 | 8, False, "cell-steps/s", 1.4e8),
+    ("16x16x1: exchange + uniaxial + Zeeman + demag", (16, 16), 256, 1 | 4 | 8 | 16, True, "cell-steps/s", 8.9e7),
+]
+
+
+def variant_batching_table(mm, stream, steps=2048):
+    """The three rows of the paper's batching table with the
+    Depondt-Mertens engine: FP32, 4 nm cells, Ms 1e6, A 1.5e-11, alpha 0.05,
+    Ku 1.1e6 along z, Bz 50 mT, STT (p = z, P 0.6) at 1e12 A/m^2 and 300 K
+    on the macrospin row."""
+    out = []
+    M = mm.Material(1.0e6, 1.5e-11, 0.05, 1.1e6, (0.0, 0.0, 1.0), 0.0)
+    for name, (nx, ny), R, terms, demag, unit, paper in BATCH_TABLE:
+        cfg = mm.make_config(precision=32, integrator=mm.MM_DM,
+                             demag=mm.MM_DEMAG_EXACT if demag else mm.MM_DEMAG_OFF, dt=1e-13, terms=terms)
+        grids = [mm.make_grid(nx, ny, 1, 4e-9, 4e-9, 4e-9)] * R
+        ctx = mm.mm_create_batch(grids, M.s, cfg, None)
+        mm.mm_set_stream(ctx, stream.cuda_stream)
+        mm.mm_set_field(ctx, 0, (0.0, 0.0, 0.05))
+        if terms & 32:
+            mm.mm_set_temperature(ctx, np.full(R, 300.0))
+            mm.mm_set_torque(ctx, mm.make_torque(mm.MM_TORQUE_STT, p=(0, 0, 1), P=0.6, Lambda=1.0),
+                             np.full(R, 1e12))
+        for r in range(R):
+            mm.mm_set_m(ctx, r, W.m_perp(W.Grid(nx, ny, 1, 4e-9, 4e-9, 4e-9), seed=r, tilt=0.1))
+        mm.mm_step(ctx, 64)
+        ms = _timed(stream, lambda: mm.mm_step(ctx, steps))
+        per = R * (nx * ny if unit == "cell-steps/s" else 1)
+        value = per * steps / (ms * 1e-3)
+        st = mm.mm_get_stats(ctx)
+        out.append({"row": name, "grid": [nx, ny, 1], "R": R, "value": value, "unit": unit,
+                    "paper_value": paper, "ratio_vs_paper": value / paper, "steps": steps,
+                    "ms_per_step": ms / steps, "kernel_launches_total": st["kernel_launches"]})
+        mm.mm_destroy(ctx)
+    return {"integrator": "Depondt-Mertens (MM_DM), FP32", "rows": out,
+            "paper_hardware": "RTX 5060 Ti (the paper's); this run: one GB300"}
+
+
+# The paper's thermally assisted STT switching sweep (Results, "Replica
+# batching"): a Pt/Co-like macrospin with a 10 nm cell, thermal stability
+# Delta = K V / kB T = 121 at 300 K and T = 0 threshold Jc0 = 2.60e12 A/m^2;
+# 25 currents x 400 trials = 10,000 replicas, 20,000 steps.  Ms and alpha are
+# not printed: Ms = 1e6 A/m and alpha = 0.0513 give that Delta and, with
+# P = 0.6, Lambda = 1 (epsilon = 0.3) and t_F = 10 nm, that Jc0
+# (Jc0 = alpha H_K e mu0 Ms t_F / (hbar epsilon), H_K = 2 K / (mu0 Ms)).
+def variant_stt_sweep(mm, stream, steps=20000, n_points=25, trials=400, dt=1e-12):
+    import torch
+    kB, T = 1.380649e-23, 300.0
+    d = 10e-9
+    V = d ** 3
+    Ms, alpha = 1.0e6, 0.0513
+    K = 121.0 * kB * T / V
+    mu0, e, hbar = 4e-7 * np.pi, 1.602176634e-19, 1.054571817e-34
+    HK = 2 * K / (mu0 * Ms)
+    eps = 0.3
+    Jc0 = alpha * HK * e * mu0 * Ms * d / (hbar * eps)
+    ratios = np.linspace(0.6, 1.2, n_points)
+    J = np.repeat(ratios * Jc0, trials)
+    R = J.size
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    M = mm.Material(Ms, 1e-11, alpha, K, (0.0, 0.0, 1.0), 0.0)
+    cfg = mm.make_config(precision=32, integrator=mm.MM_DM, demag=mm.MM_DEMAG_OFF, dt=dt, terms=4 | 8 | 32)
+    ctx = mm.mm_create_batch([mm.make_grid(1, 1, 1, d, d, d)] * R, M.s, cfg, None)
+    mm.mm_set_stream(ctx, stream.cuda_stream)
+    mm.mm_set_torque(ctx, mm.make_torque(mm.MM_TORQUE_STT, p=(0, 0, 1), P=0.6, Lambda=1.0, t_F=d), np.zeros(R))
+    m0 = np.array([0.0, 0.0, -1.0]).reshape(3, 1, 1, 1)
+    mm.mm_trials_start(ctx, J, np.full(R, T), m0, axis=(0, 0, -1), threshold=0.0, max_steps=steps, base_seed=17,
+                       refill=False)
+    t_setup = time.perf_counter() - t0
+    ms = _timed(stream, lambda: mm.mm_step(ctx, steps))
+    st, sw, done = mm.mm_trials_result(ctx)
+    mm.mm_destroy(ctx)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    p_sw = sw.reshape(n_points, trials).mean(axis=1)
+    k = int(np.argmax(p_sw >= 0.5)) if (p_sw >= 0.5).any() else -1
+    return {"workload": f"{R} Pt/Co-like macrospin trials ({n_points} currents x {trials}), {steps} steps of "
+                        f"{dt * 1e12:.1f} ps, 300 K, FP32 Depondt-Mertens, retire at m_z >= 0",
+            "wall_s_end_to_end": wall, "setup_s": t_setup, "stepping_ms": ms,
+            "replica_steps_per_s_upper": R * steps / (ms * 1e-3),
+            "replica_steps_taken": int(st[st > 0].sum()),
+            "paper_wall_s": 0.6, "paper_naive_loop_wall_s": 2.5 * 3600,
+            "trials_done": done, "Jc0": Jc0, "J_over_Jc0": [round(float(x), 4) for x in ratios],
+            "P_sw": [round(float(x), 4) for x in p_sw],
+            "J_over_Jc0_at_P_half": float(ratios[k]) if k >= 0 else None,
+            "paper_J_over_Jc0_at_P_half": 0.97}
+
+
 # The paper's throughput scenarios (ms per field evaluation, FP32) and its
 # published numbers on its own hardware (an RTX 5060 Ti): this code's cuFFT
 # build and the best solver of its comparison.  Grid shapes are not printed
@@ -507,7 +602,9 @@ def run_gpu(args):
         wanted = [v for v in args.variants.split(",") if v]
         for name, fn in (("batched", lambda: variant_batched(mm, stream, args.batch_steps)),
                          ("surrogate", lambda: variant_surrogate(mm, stream, args.surrogate_steps)),
-                         ("paper_scenarios", lambda: variant_scenarios(mm, stream))):
+                         ("paper_scenarios", lambda: variant_scenarios(mm, stream)),
+                         ("batching_table", lambda: variant_batching_table(mm, stream)),
+                         ("stt_sweep", lambda: variant_stt_sweep(mm, stream))):
             if name not in wanted:
                 continue
             try:
@@ -532,7 +629,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", default="", help="nx,ny,nz: a smaller case of the same workload (profiling)")
     ap.add_argument("--no-variants", action="store_true", help="skip the FP64, batched and surrogate lines")
-    ap.add_argument("--variants", default="batched,surrogate,paper_scenarios",
+    ap.add_argument("--variants", default="batched,surrogate,paper_scenarios,batching_table,stt_sweep",
                     help="comma list of variant lines to run")
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--surrogate-steps", type=int, default=100)

@@ -91,6 +91,19 @@ struct FieldArgs {
     T dir[3];
 };
 
+// Thermal field of cell i at noise counter `step`: Philox4x32-10 keyed by
+// (key0, key1) on the counter (i, step), Box-Muller, times
+// sigma = sigma0 sqrt(T / (V dt)).
+template <typename T>
+__device__ __forceinline__ v3<T> thermal_h(const FieldArgs<T>& a, long long i, const Region<T>& R, long long step) {
+    const U4 r = philox(U4{(uint32_t)i, (uint32_t)step, (uint32_t)((unsigned long long)step >> 32), 0u},
+                        a.key0, a.key1);
+    T n[3];
+    box_muller<T>(r, n);
+    const T sg = R.sigma0 * a.th_scale;
+    return mk3<T>(sg * n[0], sg * n[1], sg * n[2]);
+}
+
 template <typename T>
 __device__ __forceinline__ v3<T> ld3(const T* __restrict__ a, long long N, long long i) {
     return mk3<T>(__ldg(a + i), __ldg(a + N + i), __ldg(a + 2 * N + i));
@@ -152,14 +165,7 @@ __device__ __forceinline__ void cell_field_nb(const FieldArgs<T>& a, long long i
         if (use_hd) H = H + hdv;
         else if (a.Hd) H = H + ld3(a.Hd, N, i);
     }
-    if ((a.terms & MM_TERM_THERMAL) && a.th_scale != (T)0) {
-        const U4 r = philox(U4{(uint32_t)i, (uint32_t)step, (uint32_t)((unsigned long long)step >> 32), 0u},
-                            a.key0, a.key1);
-        T n[3];
-        box_muller<T>(r, n);
-        const T sg = R.sigma0 * a.th_scale;
-        H = H + mk3<T>(sg * n[0], sg * n[1], sg * n[2]);
-    }
+    if ((a.terms & MM_TERM_THERMAL) && a.th_scale != (T)0) H = H + thermal_h<T>(a, i, R, step);
     if (!want_k) return;
     // LLG torque, Eq. 1: -gamma' mu0 [m x H + alpha m x (m x H)]
     const v3<T> mxH = cross(m, H);

@@ -25,6 +25,10 @@ __global__ void __launch_bounds__(32) macro_kernel(MacroArgs a) {
     fa.th_scale = rp.th_scale;
     fa.tq_base = rp.tq_base;
     const Region<float>& R = fa.lut[0];
+    // the step's thermal draw is the same in both evaluations: drawn once
+    // per step and added through the precomputed-field slot
+    const bool hot = (fa.terms & MM_TERM_THERMAL) != 0;
+    fa.terms = (fa.terms & ~MM_TERM_THERMAL) | MM_TERM_DEMAG;
     const float dt = (float)a.st->dt;
     const long long step0 = a.st->step;
     const bool dm = a.dm != 0;
@@ -35,9 +39,10 @@ __global__ void __launch_bounds__(32) macro_kernel(MacroArgs a) {
         const long long step = step0 + s;
         const long long ctr = step - rp.step0;    // the trial's own step: its noise counter
         v3<float> H, w1, w2;
-        cell_field<float>(fa, 0, 0, 0, 0, 0, R, m, nullptr, ctr, H, w1, true, dm);
+        const v3<float> hth = hot && fa.th_scale != 0.f ? thermal_h<float>(fa, 0, R, ctr) : mk3<float>(0.f, 0.f, 0.f);
+        cell_field<float>(fa, 0, 0, 0, 0, 0, R, m, &hth, ctr, H, w1, true, dm);
         const v3<float> ms = dm ? rodrigues<float>(m, w1, dt) : m + dt * w1;
-        cell_field<float>(fa, 0, 0, 0, 0, 0, R, ms, nullptr, ctr, H, w2, true, dm);
+        cell_field<float>(fa, 0, 0, 0, 0, 0, R, ms, &hth, ctr, H, w2, true, dm);
         const v3<float> mn = dm ? rodrigues<float>(m, 0.5f * (w1 + w2), dt) : m + (0.5f * dt) * (w1 + w2);
         m = rsqrtf(dot(mn, mn)) * mn;
         if (a.trials) {
