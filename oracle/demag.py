@@ -15,6 +15,17 @@ tent quadrature far).
 Readings: the source-cell Ms multiplies m (per-cell Ms); the padded length
 is 2n on every axis (2 on a singleton axis, where only the zero
 displacement exists).
+
+Periodic boundaries (Methods: "periodic-boundary demagnetization by an
+image-sum kernel"; the number of images is not printed).  With R_x images
+on a periodic x axis (likewise y, z) the field is that of the sample and
+its 2R_x + 1 copies shifted by multiples of the box length, evaluated in
+the central copy:
+
+    H_a(r) = - sum_{|p| <= R} sum_{r'} sum_b N_ab(r - r' - p L) Ms m_b(r'),
+
+so the tensor becomes the image sum  sum_p N(d - p L)  over displacements
+|d| < n, and the same zero-padded convolution applies unchanged.
 """
 from __future__ import annotations
 
@@ -107,6 +118,22 @@ def newell_octant(shape, d) -> np.ndarray:
     return out
 
 
+def newell_octant_images(shape, d, images) -> np.ndarray:
+    """Image-summed tensor on the octant displacements: sum over
+    a in [-R_x, R_x], b in [-R_y, R_y], c in [-R_z, R_z] of
+    N(i + a nx, j + b ny, k + c nz) -> (6, nz, ny, nx)."""
+    nz, ny, nx = shape
+    Rx, Ry, Rz = (int(v) for v in images)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    base = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1)
+    out = np.zeros((nz * ny * nx, 6))
+    for a in range(-Rx, Rx + 1):
+        for b in range(-Ry, Ry + 1):
+            for c in range(-Rz, Rz + 1):
+                out += newell_at(base + np.array([a * nx, b * ny, c * nz]), d)
+    return out.T.reshape(6, nz, ny, nx)
+
+
 # parity of each component under (x -> -x, y -> -y, z -> -z)
 _PARITY = {0: (1, 1, 1), 1: (1, 1, 1), 2: (1, 1, 1),
            3: (-1, -1, 1), 4: (-1, 1, -1), 5: (1, -1, -1)}
@@ -138,8 +165,11 @@ def padded_kernel(shape, d, octant=None) -> np.ndarray:
     return K
 
 
-def demag_spectrum(shape, d, octant=None) -> np.ndarray:
-    """Full complex FFT of each padded tensor component -> (6, 2nz, 2ny, 2nx)."""
+def demag_spectrum(shape, d, octant=None, images=(0, 0, 0)) -> np.ndarray:
+    """Full complex FFT of each padded tensor component -> (6, 2nz, 2ny, 2nx);
+    images: periodic image counts per axis (x, y, z), 0 = open."""
+    if octant is None and any(images):
+        octant = newell_octant_images(shape, d, images)
     K = padded_kernel(shape, d, octant)
     return np.fft.fftn(K, axes=(1, 2, 3))
 

@@ -22,6 +22,12 @@ Readings taken where the paper is silent:
    energy-consistent sign:  m_ghost = m_i - Delta (D_i/2A_i)(z x n) x m_i,
    used in both the exchange and the DMI sums, not renormalised.  The pin
    is tests/test_oracle_fields.py::test_edge_field_is_energy_gradient.
+ * bulk DMI (named, not written out, in the paper): energy density
+   Db m.(curl m), field H = -(2 Db/mu0 Ms) curl m, central differences in
+   x, y and z.  Its natural boundary condition, dm/dn = (Db/2A) n x m, adds
+   + Delta (Db_i/2A_i) n x m_i to the ghost value on every free face (the
+   top and bottom of a film included).  Pinned the same way
+   (test_bulk_edge_field_is_energy_gradient) and by the closed-form helix.
 """
 from __future__ import annotations
 
@@ -36,8 +42,10 @@ from .constants import MU0
 class Problem:
     """Per-cell description of one instance.
 
-    Ms, A, alpha, Ku1, D: (nz, ny, nx); u: (3, nz, ny, nx); B_ext: (3, nz,
-    ny, nx) tesla; d = (dx, dy, dz); pbc = (px, py, pz).
+    Ms, A, alpha, Ku1, D (interfacial DMI), Db (bulk DMI): (nz, ny, nx);
+    u: (3, nz, ny, nx); B_ext: (3, nz, ny, nx) tesla; d = (dx, dy, dz);
+    pbc = (px, py, pz): nonzero makes the axis periodic, and the demag field
+    then sums that many images of the sample on each side.
     """
     Ms: np.ndarray
     A: np.ndarray
@@ -48,6 +56,11 @@ class Problem:
     B_ext: np.ndarray
     d: tuple
     pbc: tuple = (0, 0, 0)
+    Db: np.ndarray = None
+
+    def __post_init__(self):
+        if self.Db is None:
+            self.Db = np.zeros_like(self.Ms)
 
     @property
     def shape(self):
@@ -76,7 +89,8 @@ class Problem:
             B = np.broadcast_to(B[:, None, None, None], (3,) + shape).copy()
         return Problem(Ms=scal("Ms", mat.Ms), A=scal("A", mat.A), alpha=scal("alpha", mat.alpha),
                        Ku1=scal("Ku1", mat.Ku1), u=np.asarray(u, dtype=np.float64), D=scal("D", mat.D),
-                       B_ext=B, d=(grid.dx, grid.dy, grid.dz), pbc=tuple(grid.pbc))
+                       B_ext=B, d=(grid.dx, grid.dy, grid.dz), pbc=tuple(grid.pbc),
+                       Db=scal("Db", getattr(mat, "Db", 0.0)))
 
 
 # array axis of each spatial direction in (nz, ny, nx) arrays
@@ -114,6 +128,16 @@ def _z_cross_n_cross_m(m: np.ndarray, direction: int, sign: int) -> np.ndarray:
     return out                  # z x (+-z) = 0
 
 
+def _n_cross_m(m: np.ndarray, direction: int, sign: int) -> np.ndarray:
+    """n x m for the outward normal n = sign * e_direction."""
+    out = np.zeros_like(m)
+    a, b = {0: (1, 2), 1: (2, 0), 2: (0, 1)}[direction]
+    # for the cyclic triple (d, a, b): e_d x m = -m_b e_a + m_a e_b
+    out[a] = -sign * m[b]
+    out[b] = sign * m[a]
+    return out
+
+
 def neighbour_values(m: np.ndarray, p: Problem, direction: int, sign: int):
     """Neighbour magnetisation in direction sign*e_direction, the ghost value
     where the neighbour is absent, and the exchange coupling A_ij.
@@ -127,8 +151,10 @@ def neighbour_values(m: np.ndarray, p: Problem, direction: int, sign: int):
     present_nb = Ms_nb > 0
     with np.errstate(divide="ignore", invalid="ignore"):
         ratio = np.where(p.A > 0, p.D / (2.0 * p.A), 0.0)
+        ratio_b = np.where(p.A > 0, p.Db / (2.0 * p.A), 0.0)
         A_ij = np.where(present_nb & (p.A + A_nb > 0), 2.0 * p.A * A_nb / (p.A + A_nb), 0.0)
     ghost = m - p.d[direction] * ratio * _z_cross_n_cross_m(m, direction, sign)
+    ghost = ghost + p.d[direction] * ratio_b * _n_cross_m(m, direction, sign)
     m_nb = np.where(present_nb, m_nb, ghost)
     A_ij = np.where(present_nb, A_ij, p.A)
     return m_nb, A_ij, present_nb
@@ -159,7 +185,27 @@ def h_dmi(m: np.ndarray, p: Problem) -> np.ndarray:
         grads.append((mp - mm) / (2.0 * p.d[direction]))
     gx, gy = grads
     H = np.stack([gx[2], gy[2], -gx[0] - gy[1]])
-    return 2.0 * p.D * _inv_mu0_Ms(p) * H
+    H = 2.0 * p.D * _inv_mu0_Ms(p) * H
+    if np.any(p.Db != 0):
+        H = H + h_dmi_bulk(m, p)
+    return H
+
+
+def h_dmi_bulk(m: np.ndarray, p: Problem) -> np.ndarray:
+    """Bulk DMI (Methods, "Physics and discretization"; energy density
+    Db m.(curl m)): H = -2Db/(mu0 Ms) curl m, central differences over
+    neighbour-or-ghost values along x, y and z."""
+    curl = np.zeros_like(m)
+    g = []
+    for direction in range(3):
+        mp, _, _ = neighbour_values(m, p, direction, +1)
+        mm, _, _ = neighbour_values(m, p, direction, -1)
+        g.append((mp - mm) / (2.0 * p.d[direction]))
+    gx, gy, gz = g
+    curl[0] = gy[2] - gz[1]
+    curl[1] = gz[0] - gx[2]
+    curl[2] = gx[1] - gy[0]
+    return -2.0 * p.Db * _inv_mu0_Ms(p) * curl
 
 
 def h_anisotropy(m: np.ndarray, p: Problem) -> np.ndarray:

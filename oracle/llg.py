@@ -202,7 +202,7 @@ class Solver:
     def __post_init__(self):
         self.m = _unit(np.array(self.m, dtype=np.float64), self.p.present)
         if "demag" in self.terms and self.K_hat is None:
-            self.K_hat = demag_spectrum(self.p.shape, self.p.d)
+            self.K_hat = demag_spectrum(self.p.shape, self.p.d, images=tuple(int(v) for v in self.p.pbc))
 
     # -- field and slope ----------------------------------------------------
     def field(self, m, h_th=None):

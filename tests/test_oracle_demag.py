@@ -92,3 +92,53 @@ def test_octant_symmetric_extension_matches_direct_evaluation():
     oct_ = newell_octant(p.shape, p.d)
     H = h_demag(m, p, demag_spectrum(p.shape, p.d, oct_))
     assert np.allclose(H, h_demag_direct(m, p), rtol=0, atol=1e-12 * np.abs(H).max())
+
+
+# -- periodic boundaries (image sums) -------------------------------------------
+@pytest.mark.parametrize("images", [(2, 1, 0), (0, 0, 1), (1, 2, 1)])
+def test_periodic_field_is_the_replicated_sample(images):
+    """With R images per periodic axis the field equals the open-boundary
+    field of the sample repeated 2R + 1 times along that axis, in the central
+    copy (computed independently through the pinned open-boundary path)."""
+    nx, ny, nz = 5, 4, 2
+    grid = W.Grid(nx, ny, nz, 2e-9, 3e-9, 1.5e-9, images)
+    p = _problem(grid, seed=3)
+    m = W.random_m(grid, seed=8)
+    H = h_demag(m, p, demag_spectrum(p.shape, p.d, images=images))
+    Rx, Ry, Rz = images
+    big = W.Grid(nx * (2 * Rx + 1), ny * (2 * Ry + 1), nz * (2 * Rz + 1), 2e-9, 3e-9, 1.5e-9)
+    reps = (1, 2 * Rz + 1, 2 * Ry + 1, 2 * Rx + 1)
+    pb = Problem.from_workload(big, W.with_cells(W.Material(Ms=8e5, A=1.3e-11, alpha=0.02),
+                                                 {"Ms": np.tile(p.Ms, reps[1:])}))
+    Hb = h_demag(np.tile(m, reps), pb, demag_spectrum(pb.shape, pb.d))
+    c = Hb[:, Rz * nz:(Rz + 1) * nz, Ry * ny:(Ry + 1) * ny, Rx * nx:(Rx + 1) * nx]
+    assert np.abs(H - c).max() < 1e-10 * np.abs(c).max()
+
+
+def test_periodic_film_limit():
+    """A film periodic in x and y approaches the infinite slab as the images
+    grow: H = -Ms m_z z for uniform m, and no in-plane field."""
+    n = 8
+    errs_z, errs_x = [], []
+    for R in (2, 8, 32):
+        grid = W.Grid(n, n, 1, 4e-9, 4e-9, 1e-9, (R, R, 0))
+        p = Problem.from_workload(grid, W.Material(Ms=8e5, A=1.3e-11, alpha=0.02))
+        K = demag_spectrum(p.shape, p.d, images=(R, R, 0))
+        mz = np.zeros((3,) + p.shape); mz[2] = 1
+        mx = np.zeros((3,) + p.shape); mx[0] = 1
+        errs_z.append(np.abs(h_demag(mz, p, K)[2] / 8e5 + 1).max())
+        errs_x.append(np.abs(h_demag(mx, p, K)[0] / 8e5).max())
+    assert errs_z[0] > errs_z[1] > errs_z[2] and errs_z[2] < 2e-3, errs_z
+    assert errs_x[0] > errs_x[1] > errs_x[2] and errs_x[2] < 2e-3, errs_x
+
+
+def test_periodic_rod_limit():
+    """A square rod periodic along x: magnetised along the rod there is no
+    field; across it the field tends to -Ms/2 (N_yy = N_zz = 1/2)."""
+    grid = W.Grid(6, 1, 1, 2e-9, 2e-9, 2e-9, (200, 0, 0))
+    p = Problem.from_workload(grid, W.Material(Ms=8e5, A=1.3e-11, alpha=0.02))
+    K = demag_spectrum(p.shape, p.d, images=(200, 0, 0))
+    mx = np.zeros((3,) + p.shape); mx[0] = 1
+    my = np.zeros((3,) + p.shape); my[1] = 1
+    assert np.abs(h_demag(mx, p, K)[0] / 8e5).max() < 2e-3
+    assert np.abs(h_demag(my, p, K)[1] / 8e5 + 0.5).max() < 2e-3

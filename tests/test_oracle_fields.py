@@ -180,3 +180,125 @@ def test_anisotropy_and_zeeman_closed_forms():
     p2 = Problem.from_workload(grid, W.Material(Ms=5e5, A=1e-11, alpha=0.1), B_ext=(0.01, 0.0, -0.2))
     Hz = h_zeeman(p2)
     assert np.allclose(Hz[:, 0, 0, 0], np.array([0.01, 0, -0.2]) / MU0)
+
+
+# -- bulk DMI -------------------------------------------------------------------
+def _bond_energy_general(m, p, Di, Db, A, Ms):
+    """Independent discrete energy with interfacial (Di) and bulk (Db) DMI
+    (uniform A, Ms; free faces and Ms = 0 holes):
+      exchange  A V/h^2 |m_i - m_j|^2 per bond,
+      DMI       (V/h) d_ij.(m_i x m_j) per bond, d_ij = Di z x r_ij - Db r_ij
+                (bulk: Db m.(curl m) = -Db sum_d e_d.(m x d_d m)),
+      face      -A V |c x m_i|^2 per missing neighbour, c = (Di z x n - Db n)/2A
+                (the first-order part of the ghost value, squared).
+    """
+    nz, ny, nx = p.shape
+    V = p.d[0] * p.d[1] * p.d[2]
+    pres = p.Ms > 0
+    E = 0.0
+    unit = np.eye(3)
+    zhat = unit[2]
+    for d in range(3):
+        h = p.d[d]
+        for k in range(nz):
+            for j in range(ny):
+                for i in range(nx):
+                    if not pres[k, j, i]:
+                        continue
+                    mi = m[:, k, j, i]
+                    for sgn in (+1, -1):
+                        nb = [i, j, k]
+                        nb[d] += sgn
+                        inside = 0 <= nb[0] < nx and 0 <= nb[1] < ny and 0 <= nb[2] < nz
+                        n = sgn * unit[d]
+                        if inside and pres[nb[2], nb[1], nb[0]]:
+                            if sgn > 0:
+                                mj = m[:, nb[2], nb[1], nb[0]]
+                                E += A * V / h ** 2 * np.dot(mi - mj, mi - mj)
+                                dvec = Di * np.cross(zhat, n) - Db * n
+                                E += V / h * np.dot(dvec, np.cross(mi, mj))
+                        else:
+                            c = (Di * np.cross(zhat, n) - Db * n) / (2 * A)
+                            w = np.cross(c, mi)
+                            E += -A * V * np.dot(w, w)
+    return E
+
+
+@pytest.mark.parametrize("Di,Db", [(0.0, 2.2e-3), (1.5e-3, -2.0e-3)])
+def test_bulk_edge_field_is_energy_gradient(Di, Db):
+    """H_ex + H_DMI = -(1/(mu0 Ms V)) dE/dm of the independent bond energy on
+    a two-layer block with free faces (top and bottom included) and holes,
+    for bulk DMI alone and together with interfacial DMI."""
+    from oracle.fields import h_dmi_bulk  # noqa: F401  (part of h_dmi when Db != 0)
+    grid = W.Grid(4, 3, 2, 2e-9, 3e-9, 1.5e-9)
+    A, Ms = 1.2e-11, 7e5
+    holes = np.zeros(grid.shape, bool)
+    holes[0, 1, 2] = holes[1, 2, 0] = True
+    mat = W.with_cells(W.Material(Ms=Ms, A=A, alpha=0.1, D=Di, Db=Db), {"Ms": np.where(holes, 0.0, Ms)})
+    p = Problem.from_workload(grid, mat)
+    m = W.random_m(grid, seed=13)
+    m[:, holes] = 0.0
+    H = h_exchange(m, p) + h_dmi(m, p)
+    V = grid.dx * grid.dy * grid.dz
+    eps = 1e-6
+    num = np.zeros_like(m)
+    for c in range(3):
+        for k in range(grid.nz):
+            for j in range(grid.ny):
+                for i in range(grid.nx):
+                    if holes[k, j, i]:
+                        continue
+                    mp = m.copy(); mp[c, k, j, i] += eps
+                    mm = m.copy(); mm[c, k, j, i] -= eps
+                    dE = (_bond_energy_general(mp, p, Di, Db, A, Ms) - _bond_energy_general(mm, p, Di, Db, A, Ms))
+                    num[c, k, j, i] = -dE / (2 * eps) / (MU0 * Ms * V)
+    assert np.max(np.abs(num - H)) < 1e-6 * np.abs(H).max()
+
+
+@pytest.mark.parametrize("q,hand", [(1, 1), (4, 1), (3, -1)])
+def test_bulk_dmi_helix_closed_form(q, hand):
+    """Periodic chain, Bloch helix m = (0, cos kx, hand sin kx): curl m =
+    -hand (sin(k dx)/dx) m by central differences, so H_bulk =
+    hand (2 Db/mu0 Ms)(sin(k dx)/dx) m; the exchange and DMI torques vanish
+    (the helix of either hand is a stationary state of the local terms)."""
+    n, dx, Db, Ms = 36, 2e-9, 2.5e-3, 8e5
+    grid = W.Grid(n, 1, 1, dx, 2e-9, 2e-9, (1, 1, 1))
+    p = Problem.from_workload(grid, W.Material(Ms=Ms, A=1.3e-11, alpha=0.1, Db=Db))
+    k = 2 * math.pi * q / (n * dx)
+    x = np.arange(n) * dx
+    m = np.zeros((3,) + p.shape)
+    m[1, 0, 0] = np.cos(k * x)
+    m[2, 0, 0] = hand * np.sin(k * x)
+    H = h_dmi(m, p)
+    exp = hand * (2 * Db / (MU0 * Ms)) * (math.sin(k * dx) / dx) * m
+    assert np.allclose(H, exp, rtol=1e-12, atol=1e-6)
+    # the right-handed helix lowers the DMI energy for Db > 0
+    assert hand * np.sum(m * H) > 0
+
+
+def test_bulk_ghost_sign_alternative_fails_the_gradient_identity():
+    """The bulk face condition with the opposite sign breaks the identity at
+    a face cell: the pin discriminates the two signs."""
+    from oracle import fields as F
+    grid = W.Grid(3, 3, 2, 2e-9, 2e-9, 1e-9)
+    A, Ms, Db = 1.5e-11, 6e5, 3e-3
+    p = Problem.from_workload(grid, W.Material(Ms=Ms, A=A, alpha=0.1, Db=Db))
+    m = W.random_m(grid, seed=6)
+    orig = F._n_cross_m
+    try:
+        F._n_cross_m = lambda mm, d, s: -orig(mm, d, s)
+        H_alt = h_exchange(m, p) + h_dmi(m, p)
+    finally:
+        F._n_cross_m = orig
+    H = h_exchange(m, p) + h_dmi(m, p)
+    V = grid.dx * grid.dy * grid.dz
+    eps = 1e-6
+    i, j, k = 0, 1, 0
+    num = np.zeros(3)
+    for c in range(3):
+        mp = m.copy(); mp[c, k, j, i] += eps
+        mm = m.copy(); mm[c, k, j, i] -= eps
+        num[c] = -(_bond_energy_general(mp, p, 0.0, Db, A, Ms) - _bond_energy_general(mm, p, 0.0, Db, A, Ms)) \
+            / (2 * eps) / (MU0 * Ms * V)
+    assert np.max(np.abs(num - H[:, k, j, i])) < 1e-6 * np.abs(H).max()
+    assert np.max(np.abs(num - H_alt[:, k, j, i])) > 1e-2 * np.abs(H).max()

@@ -49,6 +49,7 @@ class Material:
     u: tuple = (0.0, 0.0, 1.0)
     D: float = 0.0
     cell: dict = field(default_factory=dict)
+    Db: float = 0.0         # bulk DMI constant (J/m^2)
 
 
 @dataclass(frozen=True)
