@@ -85,8 +85,13 @@ enum mm_energy_index { MM_E_EXCHANGE = 0, MM_E_DMI = 1, MM_E_ANISOTROPY = 2, MM_
 
 enum mm_torque_kind { MM_TORQUE_NONE = 0, MM_TORQUE_SOT = 1, MM_TORQUE_STT = 2, MM_TORQUE_ZL = 3 };
 
-/* Grid of one replica: nx*ny*nz cells of dx*dy*dz metres; pbc[d] != 0 makes
- * axis d periodic for the local (exchange/DMI/Zhang-Li) stencils. */
+/* Grid of one replica: nx*ny*nz cells of dx*dy*dz metres.  pbc[d] > 0 makes
+ * axis d periodic: the local stencils (exchange, DMI, Zhang-Li) wrap, and
+ * the demag field (Methods: periodic-boundary demagnetisation by an
+ * image-sum kernel) is that of the sample and its copies shifted by
+ * a * n_d cells for |a| <= pbc[d], seen from the central copy (the Newell
+ * tensor summed over those images, then the usual zero-padded FFT
+ * convolution).  pbc[d] in [0, 4096]. */
 typedef struct mm_grid {
     int nx, ny, nz;
     double dx, dy, dz;
@@ -96,10 +101,17 @@ typedef struct mm_grid {
 /* Material.  Scalars apply to every cell unless the matching per-cell host
  * array (length N; u_cell 3N component-major) is non-NULL.  Cells with
  * Ms = 0 are absent (the geometry mask).  At most 256 distinct parameter
- * tuples per context (they become material regions). */
+ * tuples per context (they become material regions).  D: interfacial DMI
+ * (J/m^2).  D_bulk: bulk DMI (Methods, "Physics and discretization"),
+ * energy density D_bulk m.(curl m), field -(2 D_bulk / mu0 Ms) curl m by
+ * central differences in x, y and z; at a free face with outward normal n
+ * its boundary condition dm/dn = (D_bulk/2A) n x m enters the ghost value
+ * (film tops and bottoms included).  Both belong to MM_TERM_DMI. */
 typedef struct mm_material {
     double Ms, A, alpha, Ku1, u[3], D;
     const double *Ms_cell, *A_cell, *alpha_cell, *Ku1_cell, *u_cell, *D_cell;
+    double D_bulk;
+    const double* D_bulk_cell;
 } mm_material;
 
 typedef struct mm_config {

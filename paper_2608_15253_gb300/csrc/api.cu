@@ -84,6 +84,8 @@ static Region<T> region_coeffs(const RegionHost& r, double /*V*/) {
     o.gm = (T)(kGamma0 * kMu0 / (1.0 + r.alpha * r.alpha));
     o.sigma0 = present ? (T)std::sqrt(2.0 * r.alpha * kKB / (kMu0 * kMu0 * r.Ms * kGamma0)) : (T)0;
     o.inv_Ms = present ? (T)(1.0 / r.Ms) : (T)0;
+    o.ratio_b = r.A > 0 ? (T)(r.Db / (2.0 * r.A)) : (T)0;
+    o.dmib = (T)(2.0 * r.Db * imu);
     return o;
 }
 
@@ -118,8 +120,9 @@ static mm_status upload_regions_t(mm_ctx* c) {
 
 static mm_status build_regions(mm_ctx* c, const mm_material* mat) {
     const long long N = c->N;
-    const bool percell = mat->Ms_cell || mat->A_cell || mat->alpha_cell || mat->Ku1_cell || mat->u_cell || mat->D_cell;
-    RegionHost base{mat->Ms, mat->A, mat->alpha, mat->Ku1, {mat->u[0], mat->u[1], mat->u[2]}, mat->D};
+    const bool percell = mat->Ms_cell || mat->A_cell || mat->alpha_cell || mat->Ku1_cell || mat->u_cell ||
+                         mat->D_cell || mat->D_bulk_cell;
+    RegionHost base{mat->Ms, mat->A, mat->alpha, mat->Ku1, {mat->u[0], mat->u[1], mat->u[2]}, mat->D, mat->D_bulk};
     c->regions.clear();
     if (!percell) {
         c->regions.push_back(base);
@@ -136,6 +139,7 @@ static mm_status build_regions(mm_ctx* c, const mm_material* mat) {
         if (mat->alpha_cell) r.alpha = mat->alpha_cell[i];
         if (mat->Ku1_cell) r.Ku1 = mat->Ku1_cell[i];
         if (mat->D_cell) r.D = mat->D_cell[i];
+        if (mat->D_bulk_cell) r.Db = mat->D_bulk_cell[i];
         if (mat->u_cell) { r.u[0] = mat->u_cell[i]; r.u[1] = mat->u_cell[N + i]; r.u[2] = mat->u_cell[2 * N + i]; }
         if (!(r.Ms >= 0) || !(r.A >= 0) || !(r.alpha >= 0))
             return set_error(c, MM_ERR_ARG, "per-cell Ms, A and alpha must be non-negative");
@@ -309,8 +313,9 @@ mm_status mm_create(const mm_grid* grid, const mm_material* mat, const mm_config
     if (cfg->integrator == MM_RK4 && cfg->T > 0)
         return set_error(nullptr, MM_ERR_ARG, "RK4 with T > 0: the thermal field needs Heun or Depondt-Mertens");
     if (cfg->demag == MM_DEMAG_SURROGATE) return set_error(nullptr, MM_ERR_ARG, "surrogate demag needs mm_surrogate_*");
-    if (cfg->demag == MM_DEMAG_EXACT && (grid->pbc[0] || grid->pbc[1] || grid->pbc[2]))
-        return set_error(nullptr, MM_ERR_ARG, "periodic boundaries apply to the local terms only; turn demag off");
+    if (grid->pbc[0] < 0 || grid->pbc[1] < 0 || grid->pbc[2] < 0 || grid->pbc[0] > 4096 || grid->pbc[1] > 4096 ||
+        grid->pbc[2] > 4096)
+        return set_error(nullptr, MM_ERR_ARG, "pbc[d] is an image count in [0, 4096]");
     if (!(cfg->dt > 0)) return set_error(nullptr, MM_ERR_ARG, "dt must be positive");
     mm_ctx* c = new mm_ctx();
     mm_status s = check_device(c);
@@ -394,7 +399,8 @@ mm_status mm_create_batch(int R, const mm_grid* grids, const mm_material* mat, c
         return set_error(nullptr, MM_ERR_ARG, "replica batching integrates with Heun or Depondt-Mertens");
     if (cfg->demag == MM_DEMAG_SURROGATE) return set_error(nullptr, MM_ERR_ARG, "surrogate demag is single-instance");
     if (!(cfg->dt > 0)) return set_error(nullptr, MM_ERR_ARG, "dt must be positive");
-    if (mat->Ms_cell || mat->A_cell || mat->alpha_cell || mat->Ku1_cell || mat->u_cell || mat->D_cell || !(mat->Ms > 0))
+    if (mat->Ms_cell || mat->A_cell || mat->alpha_cell || mat->Ku1_cell || mat->u_cell || mat->D_cell ||
+        mat->D_bulk_cell || !(mat->Ms > 0))
         return set_error(nullptr, MM_ERR_ARG, "replica batching takes one uniform material with Ms > 0");
     for (int r = 0; r < R; ++r) {
         const mm_grid& g = grids[r];

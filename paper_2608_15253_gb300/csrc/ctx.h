@@ -30,14 +30,15 @@ struct Region {
     T gm;         // gamma0 mu0 / (1 + alpha^2)
     T sigma0;     // sqrt(2 alpha kB / (mu0^2 Ms gamma0)); times sqrt(T/(V dt)) -> A/m
     T inv_Ms;     // 1/Ms, 0 when absent
-    T pad0, pad1;
+    T ratio_b;    // bulk DMI: Db / (2 A), 0 when A = 0
+    T dmib;       // bulk DMI: 2 Db / (mu0 Ms)
 };
 
 struct RegionHost {
-    double Ms, A, alpha, Ku1, u[3], D;
+    double Ms, A, alpha, Ku1, u[3], D, Db;
     bool operator==(const RegionHost& o) const {
         return Ms == o.Ms && A == o.A && alpha == o.alpha && Ku1 == o.Ku1 && u[0] == o.u[0] &&
-               u[1] == o.u[1] && u[2] == o.u[2] && D == o.D;
+               u[1] == o.u[1] && u[2] == o.u[2] && D == o.D && Db == o.Db;
     }
 };
 

@@ -803,16 +803,28 @@ __global__ void newell_list_kernel(long count, const int* __restrict__ ijk, doub
     for (int a = 0; a < 6; ++a) out[6 * q + a] = v[a];
 }
 
+// Tensor on the octant displacements 0 <= i < nx, ... ; with periodic
+// images (Methods: periodic-boundary demagnetisation by an image-sum
+// kernel) the sum over a in [-Rx, Rx], b in [-Ry, Ry], c in [-Rz, Rz] of
+// N(i + a nx, j + b ny, k + c nz): the field of the sample and its shifted
+// copies, seen from the central copy.
 __global__ void newell_octant_kernel(int nx, int ny, int nz, double hx, double hy, double hz, GLTable gl,
-                                     double* __restrict__ out) {
+                                     int Rx, int Ry, int Rz, double* __restrict__ out) {
     const long long n = (long long)nx * ny * nz;
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= n) return;
     const int i = (int)(q % nx), j = (int)((q / nx) % ny), k = (int)(q / ((long long)nx * ny));
     const double s = fmax(hx, fmax(hy, hz));
-    double v[6];
-    newell_eval(i * hx / s, j * hy / s, k * hz / s, hx / s, hy / s, hz / s, gl, v);
-    for (int a = 0; a < 6; ++a) out[a * n + q] = v[a];
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int a = -Rx; a <= Rx; ++a)
+        for (int b = -Ry; b <= Ry; ++b)
+            for (int c = -Rz; c <= Rz; ++c) {
+                double w[6];
+                newell_eval((double)(i + (long long)a * nx) * hx / s, (double)(j + (long long)b * ny) * hy / s,
+                            (double)(k + (long long)c * nz) * hz / s, hx / s, hy / s, hz / s, gl, w);
+                for (int e = 0; e < 6; ++e) v[e] += w[e];
+            }
+    for (int e = 0; e < 6; ++e) out[e * n + q] = v[e];
 }
 
 // padded real array of one component from the octant (parity per component)
@@ -1256,8 +1268,9 @@ static mm_status demag_setup_t(mm_ctx* c) {
     GLTable gl = make_gl();
     {
         LaunchScope ls(c, "newell_octant", 48.0 * noct);
-        newell_octant_kernel<<<(unsigned)((noct + 127) / 128), 128, 0, c->stream>>>(nx, ny, nz, g.dx, g.dy, g.dz,
-                                                                                   gl, oct);
+        newell_octant_kernel<<<(unsigned)((noct + 127) / 128), 128, 0, c->stream>>>(
+            nx, ny, nz, g.dx, g.dy, g.dz, gl, std::max(0, g.pbc[0]), std::max(0, g.pbc[1]), std::max(0, g.pbc[2]),
+            oct);
     }
     // temporarily point the X-pass geometry at the padded tensor
     const int saveWk = d.Wk;

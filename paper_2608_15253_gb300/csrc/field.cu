@@ -176,9 +176,9 @@ __global__ void __launch_bounds__(256) field_vec_kernel(FieldArgs<float> a) {
             nbp[0] = pp;
             nbp[1] = pm;
             nbv[0] = q < V - 1 ? mk3<float>(fget(mc[0], q + 1), fget(mc[1], q + 1), fget(mc[2], q + 1))
-                               : (rinx ? mk3<float>(xr[0], xr[1], xr[2]) : ghost_value<float>(m, 0, 1, a.hx, R.ratio));
+                               : (rinx ? mk3<float>(xr[0], xr[1], xr[2]) : ghost_value<float>(m, 0, 1, a.hx, R.ratio, R.ratio_b));
             nbv[1] = q > 0 ? mk3<float>(fget(mc[0], q - 1), fget(mc[1], q - 1), fget(mc[2], q - 1))
-                           : (lin ? mk3<float>(xl[0], xl[1], xl[2]) : ghost_value<float>(m, 0, -1, a.hx, R.ratio));
+                           : (lin ? mk3<float>(xl[0], xl[1], xl[2]) : ghost_value<float>(m, 0, -1, a.hx, R.ratio, R.ratio_b));
             cnb[0] = pp ? a.c_uniform : R.cg;
             cnb[1] = pm ? a.c_uniform : R.cg;
 #pragma unroll
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(256) field_vec_kernel(FieldArgs<float> a) {
                 const int slot = 2 + s, d = 1 + s / 2, sg = (s & 1) ? -1 : 1;
                 nbp[slot] = rin[s];
                 nbv[slot] = rin[s] ? mk3<float>(fget(nr[s][0], q), fget(nr[s][1], q), fget(nr[s][2], q))
-                                   : ghost_value<float>(m, d, sg, d == 1 ? a.hy : a.hz, R.ratio);
+                                   : ghost_value<float>(m, d, sg, d == 1 ? a.hy : a.hz, R.ratio, R.ratio_b);
                 cnb[slot] = rin[s] ? a.c_uniform : R.cg;
             }
         }

@@ -152,6 +152,11 @@ __device__ __forceinline__ void cell_field_nb(const FieldArgs<T>& a, long long i
         const v3<T> dx = gx * (nbv[0] - nbv[1]);
         const v3<T> dy = gy * (nbv[2] - nbv[3]);
         H = H + R.dmi * mk3<T>(dx.z, dy.z, -dx.x - dy.y);
+        if (R.dmib != (T)0) {
+            // bulk: H = -(2 Db / mu0 Ms) curl m
+            const v3<T> dz = ((T)0.5 / a.hz) * (nbv[4] - nbv[5]);
+            H = H + (-R.dmib) * mk3<T>(dy.z - dz.y, dz.x - dx.z, dx.y - dy.x);
+        }
     }
     if (a.terms & MM_TERM_ANISOTROPY) {
         const v3<T> u = mk3<T>(R.ux, R.uy, R.uz);
@@ -239,11 +244,20 @@ __device__ __forceinline__ v3<T> rodrigues(const v3<T>& m, const v3<T>& w, T dt)
 // Ghost value of an absent neighbour in direction d (0 x, 1 y, 2 z) and
 // side sg (+1 / -1): m - h (D/2A) (z x n) x m with n = sg e_d.
 template <typename T>
-__device__ __forceinline__ v3<T> ghost_value(const v3<T>& m, int d, int sg, T h, T ratio) {
+__device__ __forceinline__ v3<T> ghost_value(const v3<T>& m, int d, int sg, T h, T ratio, T ratio_b) {
     v3<T> zn = mk3<T>(0, 0, 0);
     if (d == 0) zn = mk3<T>(sg * m.z, (T)0, -sg * m.x);
     else if (d == 1) zn = mk3<T>((T)0, sg * m.z, -sg * m.y);
-    return m - (h * ratio) * zn;
+    v3<T> g = m - (h * ratio) * zn;
+    if (ratio_b != (T)0) {
+        // bulk DMI: + h (Db/2A) n x m, n = sg e_d
+        v3<T> nm;
+        if (d == 0) nm = mk3<T>((T)0, -sg * m.z, sg * m.y);
+        else if (d == 1) nm = mk3<T>(sg * m.z, (T)0, -sg * m.x);
+        else nm = mk3<T>(-sg * m.y, sg * m.x, (T)0);
+        g = g + (h * ratio_b) * nm;
+    }
+    return g;
 }
 
 // Effective field of one present cell (x, y, z; linear index i) and, when
@@ -293,7 +307,7 @@ __device__ __forceinline__ void cell_field(const FieldArgs<T>& a, int x, int y, 
                     nbv[slot] = ld3(a.m, N, j);
                     cnb[slot] = UNIF ? a.c_uniform : __ldg(&a.cpair[ri * a.nreg + rj]);
                 } else {
-                    nbv[slot] = ghost_value<T>(m, d, sg, hh[d], R.ratio);
+                    nbv[slot] = ghost_value<T>(m, d, sg, hh[d], R.ratio, R.ratio_b);
                     cnb[slot] = R.cg;
                 }
             }

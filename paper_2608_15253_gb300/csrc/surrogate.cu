@@ -142,6 +142,8 @@ static mm_status ensure_surrogate(mm_ctx* c) {
     if (c->surr) return MM_OK;
     if (c->batch || c->prec != 32 || c->grid.nz != 1 || !c->dm.on)
         return set_error(c, MM_ERR_STATE, "the surrogate needs a single-instance FP32 nz = 1 context with exact demag");
+    if (c->grid.pbc[0] || c->grid.pbc[1] || c->grid.pbc[2])
+        return set_error(c, MM_ERR_STATE, "the surrogate's exact near field is open-boundary: no periodic axes");
     SurrogateHost* s = new SurrogateHost();
     int o = 0;
     for (int l = 0; l < 4; ++l) {

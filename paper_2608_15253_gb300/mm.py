@@ -40,7 +40,7 @@ class mm_material(C.Structure):
     _fields_ = [("Ms", C.c_double), ("A", C.c_double), ("alpha", C.c_double), ("Ku1", C.c_double),
                 ("u", C.c_double * 3), ("D", C.c_double),
                 ("Ms_cell", _D), ("A_cell", _D), ("alpha_cell", _D), ("Ku1_cell", _D),
-                ("u_cell", _D), ("D_cell", _D)]
+                ("u_cell", _D), ("D_cell", _D), ("D_bulk", C.c_double), ("D_bulk_cell", _D)]
 
 
 class mm_config(C.Structure):
@@ -449,15 +449,16 @@ def make_grid(nx, ny, nz, dx, dy, dz, pbc=(0, 0, 0)) -> mm_grid:
 class Material:
     """mm_material plus ownership of its per-cell arrays (kept alive here)."""
 
-    def __init__(self, Ms, A, alpha, Ku1=0.0, u=(0.0, 0.0, 1.0), D=0.0, cells=None):
+    def __init__(self, Ms, A, alpha, Ku1=0.0, u=(0.0, 0.0, 1.0), D=0.0, cells=None, Db=0.0):
         self.s = mm_material(Ms, A, alpha, Ku1)
         self.s.u[:] = list(u)
         self.s.D = D
+        self.s.D_bulk = Db
         self._keep = []
         for name, arr in (cells or {}).items():
             a = _f64(arr)
             self._keep.append(a)
-            setattr(self.s, f"{name}_cell", _dptr(a))
+            setattr(self.s, f"{'D_bulk' if name == 'Db' else name}_cell", _dptr(a))
 
 
 def make_config(precision=32, integrator=MM_RK45, demag=MM_DEMAG_EXACT, terms=0, dt=1e-14, rtol=1e-6,

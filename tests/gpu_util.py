@@ -21,7 +21,7 @@ def make_ctx(mm, grid: W.Grid, mat: W.Material, precision=64, integrator=None, d
              dt=1e-14, rtol=1e-6, T=0.0, seed=0, B=(0.0, 0.0, 0.0), B_cell=None):
     integ = {None: mm.MM_RK45, "rk45": mm.MM_RK45, "rk4": mm.MM_RK4, "heun": mm.MM_HEUN, "dm": mm.MM_DM}[integrator]
     g = mm.make_grid(grid.nx, grid.ny, grid.nz, grid.dx, grid.dy, grid.dz, grid.pbc)
-    m = mm.Material(mat.Ms, mat.A, mat.alpha, mat.Ku1, mat.u, mat.D, cells=mat.cell)
+    m = mm.Material(mat.Ms, mat.A, mat.alpha, mat.Ku1, mat.u, mat.D, cells=mat.cell, Db=mat.Db)
     cfg = mm.make_config(precision=precision, integrator=integ,
                          demag=mm.MM_DEMAG_EXACT if demag else mm.MM_DEMAG_OFF,
                          terms=terms, dt=dt, rtol=rtol, T=T, seed=seed)
