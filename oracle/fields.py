@@ -57,10 +57,30 @@ class Problem:
     d: tuple
     pbc: tuple = (0, 0, 0)
     Db: np.ndarray = None
+    # further local terms (Methods: cubic and surface anisotropy, RKKY
+    # interlayer exchange, magnetoelastic anisotropy)
+    Kc1: np.ndarray = None
+    Kc2: np.ndarray = None
+    c1: np.ndarray = None       # (3, nz, ny, nx)
+    c2: np.ndarray = None
+    Ks: np.ndarray = None
+    B1: np.ndarray = None
+    B2: np.ndarray = None
+    strain: np.ndarray = None   # (6, nz, ny, nx): xx, yy, zz, xy, xz, yz
+    rkky: tuple = None          # (layer k1, layer k2, J in J/m^2)
 
     def __post_init__(self):
-        if self.Db is None:
-            self.Db = np.zeros_like(self.Ms)
+        for name in ("Db", "Kc1", "Kc2", "Ks", "B1", "B2"):
+            if getattr(self, name) is None:
+                setattr(self, name, np.zeros_like(self.Ms))
+        if self.c1 is None:
+            self.c1 = np.zeros((3,) + self.Ms.shape)
+            self.c1[0] = 1.0
+        if self.c2 is None:
+            self.c2 = np.zeros((3,) + self.Ms.shape)
+            self.c2[1] = 1.0
+        if self.strain is None:
+            self.strain = np.zeros((6,) + self.Ms.shape)
 
     @property
     def shape(self):
@@ -87,10 +107,18 @@ class Problem:
         B = np.asarray(B_ext, dtype=np.float64)
         if B.ndim == 1:
             B = np.broadcast_to(B[:, None, None, None], (3,) + shape).copy()
+        def vec(name, default):
+            v = mat.cell.get(name)
+            if v is None:
+                v = np.broadcast_to(np.asarray(default, dtype=np.float64)[:, None, None, None], (3,) + shape)
+            return np.asarray(v, dtype=np.float64).copy()
+
         return Problem(Ms=scal("Ms", mat.Ms), A=scal("A", mat.A), alpha=scal("alpha", mat.alpha),
                        Ku1=scal("Ku1", mat.Ku1), u=np.asarray(u, dtype=np.float64), D=scal("D", mat.D),
                        B_ext=B, d=(grid.dx, grid.dy, grid.dz), pbc=tuple(grid.pbc),
-                       Db=scal("Db", getattr(mat, "Db", 0.0)))
+                       Db=scal("Db", mat.Db), Kc1=scal("Kc1", mat.Kc1), Kc2=scal("Kc2", mat.Kc2),
+                       c1=vec("c1", mat.c1), c2=vec("c2", mat.c2), Ks=scal("Ks", mat.Ks),
+                       B1=scal("B1", mat.B1), B2=scal("B2", mat.B2))
 
 
 # array axis of each spatial direction in (nz, ny, nx) arrays
@@ -219,6 +247,74 @@ def h_zeeman(p: Problem) -> np.ndarray:
     return np.where(p.present, p.B_ext / MU0, 0.0)
 
 
+def cubic_axes(p: Problem):
+    """Unit cubic axes per cell: c1, c2 with its c1 component removed, and
+    c3 = c1 x c2."""
+    c1 = p.c1 / np.sqrt((p.c1 ** 2).sum(axis=0, keepdims=True))
+    c2 = p.c2 - (p.c2 * c1).sum(axis=0, keepdims=True) * c1
+    c2 = c2 / np.sqrt((c2 ** 2).sum(axis=0, keepdims=True))
+    c3 = np.stack([c1[1] * c2[2] - c1[2] * c2[1], c1[2] * c2[0] - c1[0] * c2[2], c1[0] * c2[1] - c1[1] * c2[0]])
+    return c1, c2, c3
+
+
+def h_cubic(m: np.ndarray, p: Problem) -> np.ndarray:
+    """Cubic anisotropy (Methods, "Physics and discretization"; the paper
+    names the term): energy density Kc1 (a^2 b^2 + b^2 c^2 + c^2 a^2) +
+    Kc2 a^2 b^2 c^2 with a, b, c the components of m on the cubic axes;
+    H = -(1/mu0 Ms) dE/dm."""
+    c1, c2, c3 = cubic_axes(p)
+    a, b, c = (m * c1).sum(axis=0), (m * c2).sum(axis=0), (m * c3).sum(axis=0)
+    g1 = p.Kc1 * 2 * a * (b * b + c * c) + p.Kc2 * 2 * a * b * b * c * c
+    g2 = p.Kc1 * 2 * b * (a * a + c * c) + p.Kc2 * 2 * a * a * b * c * c
+    g3 = p.Kc1 * 2 * c * (a * a + b * b) + p.Kc2 * 2 * a * a * b * b * c
+    return -_inv_mu0_Ms(p) * (g1 * c1 + g2 * c2 + g3 * c3)
+
+
+def _free_z_faces(p: Problem) -> np.ndarray:
+    """Number (0, 1, 2) of absent z neighbours of every cell."""
+    per = bool(p.pbc[2])
+    up = _shift(p.Ms, 2, +1, per, fill=0.0) > 0
+    dn = _shift(p.Ms, 2, -1, per, fill=0.0) > 0
+    return (~up).astype(float) + (~dn).astype(float)
+
+
+def h_surface(m: np.ndarray, p: Problem) -> np.ndarray:
+    """Surface anisotropy (the paper names it): every free z face of a cell
+    (an absent neighbour above or below) adds an anisotropy energy
+    -Ks (m.z)^2 per face area, i.e. the uniaxial field
+    (2 Ks / (mu0 Ms dz)) m_z z per face."""
+    H = np.zeros_like(m)
+    H[2] = 2.0 * p.Ks * _inv_mu0_Ms(p) / p.d[2] * _free_z_faces(p) * m[2]
+    return H
+
+
+def h_rkky(m: np.ndarray, p: Problem) -> np.ndarray:
+    """RKKY interlayer exchange between layers k1 and k2 (the paper names
+    it): energy -J m(k1).m(k2) per column area, so each coupled cell sees
+    (J / (mu0 Ms dz)) times the moment of its partner across the spacer
+    (where both cells are present)."""
+    H = np.zeros_like(m)
+    if p.rkky is None:
+        return H
+    k1, k2, J = p.rkky
+    both = (p.Ms[k1] > 0) & (p.Ms[k2] > 0)
+    inv = _inv_mu0_Ms(p)
+    H[:, k1] += np.where(both, J * inv[k1] / p.d[2] * m[:, k2], 0.0)
+    H[:, k2] += np.where(both, J * inv[k2] / p.d[2] * m[:, k1], 0.0)
+    return H
+
+
+def h_magnetoelastic(m: np.ndarray, p: Problem) -> np.ndarray:
+    """Magnetoelastic anisotropy (the paper names it) for a given strain:
+    energy density B1 (e_xx m_x^2 + e_yy m_y^2 + e_zz m_z^2) +
+    2 B2 (e_xy m_x m_y + e_xz m_x m_z + e_yz m_y m_z); H = -(1/mu0 Ms) dE/dm."""
+    e = p.strain
+    g = np.stack([2 * p.B1 * e[0] * m[0] + 2 * p.B2 * (e[3] * m[1] + e[4] * m[2]),
+                  2 * p.B1 * e[1] * m[1] + 2 * p.B2 * (e[3] * m[0] + e[5] * m[2]),
+                  2 * p.B1 * e[2] * m[2] + 2 * p.B2 * (e[4] * m[0] + e[5] * m[1])])
+    return -_inv_mu0_Ms(p) * g
+
+
 def h_local(m, p: Problem, terms=("exchange", "dmi", "anisotropy", "zeeman")) -> dict:
     out = {}
     if "exchange" in terms:
@@ -229,6 +325,14 @@ def h_local(m, p: Problem, terms=("exchange", "dmi", "anisotropy", "zeeman")) ->
         out["anisotropy"] = h_anisotropy(m, p)
     if "zeeman" in terms:
         out["zeeman"] = h_zeeman(p)
+    if "cubic" in terms:
+        out["cubic"] = h_cubic(m, p)
+    if "surface" in terms:
+        out["surface"] = h_surface(m, p)
+    if "rkky" in terms:
+        out["rkky"] = h_rkky(m, p)
+    if "magnetoelastic" in terms:
+        out["magnetoelastic"] = h_magnetoelastic(m, p)
     return out
 
 

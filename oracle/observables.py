@@ -5,6 +5,10 @@ flower/vortex crossover and the skyrmion phase diagram): per cell
     e_ex  = -1/2 mu0 Ms m.H_ex,  e_dmi = -1/2 mu0 Ms m.H_dmi,
     e_dem = -1/2 mu0 Ms m.H_demag, e_anis = -Ku1 (m.u)^2,
     e_Z   = -mu0 Ms m.H_ext,
+and, written from their definitions (``oracle.fields``): cubic
+Kc1 (a^2 b^2 + b^2 c^2 + c^2 a^2) + Kc2 a^2 b^2 c^2, surface -(Ks/dz) m_z^2
+per free z face, RKKY -(J/dz) m(k1).m(k2) per coupled cell pair,
+magnetoelastic B1 sum e_ii m_i^2 + 2 B2 sum_{i<j} e_ij m_i m_j;
 E_term = V sum_cells e, summed exactly-rounded (math.fsum).
 
 Topological charge (the skyrmion-classification observable): per layer
@@ -22,7 +26,7 @@ import numpy as np
 
 from .constants import MU0
 from .demag import h_demag
-from .fields import Problem, _shift, h_anisotropy, h_dmi, h_exchange, h_zeeman
+from .fields import Problem, _free_z_faces, _shift, cubic_axes, h_anisotropy, h_dmi, h_exchange, h_zeeman
 from .llg import cross, dot
 
 TERMS = ("exchange", "dmi", "anisotropy", "zeeman", "demag")
@@ -41,6 +45,23 @@ def energy(m, p: Problem, K_hat=None, terms=TERMS) -> dict:
         out["zeeman"] = math.fsum((-MU0 * p.Ms * dot(m, h_zeeman(p)) * V).ravel())
     if "demag" in terms and K_hat is not None:
         out["demag"] = math.fsum((-0.5 * MU0 * p.Ms * dot(m, h_demag(m, p, K_hat)) * V).ravel())
+    pres = p.present
+    if "cubic" in terms:
+        c1, c2, c3 = cubic_axes(p)
+        a, b, c = dot(m, c1), dot(m, c2), dot(m, c3)
+        e = p.Kc1 * (a * a * b * b + b * b * c * c + c * c * a * a) + p.Kc2 * a * a * b * b * c * c
+        out["cubic"] = math.fsum((e * pres * V).ravel())
+    if "surface" in terms:
+        out["surface"] = math.fsum((-p.Ks / p.d[2] * _free_z_faces(p) * m[2] ** 2 * pres * V).ravel())
+    if "rkky" in terms and p.rkky is not None:
+        k1, k2, J = p.rkky
+        both = (p.Ms[k1] > 0) & (p.Ms[k2] > 0)
+        out["rkky"] = math.fsum((-J / p.d[2] * np.where(both, dot(m[:, k1], m[:, k2]), 0.0) * V).ravel())
+    if "magnetoelastic" in terms:
+        s = p.strain
+        e = p.B1 * (s[0] * m[0] ** 2 + s[1] * m[1] ** 2 + s[2] * m[2] ** 2) + \
+            2 * p.B2 * (s[3] * m[0] * m[1] + s[4] * m[0] * m[2] + s[5] * m[1] * m[2])
+        out["magnetoelastic"] = math.fsum((e * pres * V).ravel())
     out["total"] = math.fsum(out.values())
     return out
 

@@ -50,6 +50,13 @@ class Material:
     D: float = 0.0
     cell: dict = field(default_factory=dict)
     Db: float = 0.0         # bulk DMI constant (J/m^2)
+    Kc1: float = 0.0        # cubic anisotropy (J/m^3)
+    Kc2: float = 0.0
+    c1: tuple = (1.0, 0.0, 0.0)   # cubic axes (c3 = c1 x c2)
+    c2: tuple = (0.0, 1.0, 0.0)
+    Ks: float = 0.0         # surface anisotropy at free z faces (J/m^2)
+    B1: float = 0.0         # magnetoelastic coupling constants (J/m^3)
+    B2: float = 0.0
 
 
 @dataclass(frozen=True)
