@@ -76,12 +76,17 @@ enum mm_term {
     MM_TERM_ZEEMAN = 8,
     MM_TERM_DEMAG = 16,
     MM_TERM_THERMAL = 32,
-    MM_TERM_ALL = 63
+    MM_TERM_CUBIC = 64,       /* cubic anisotropy (mm_material Kc1, Kc2, c1, c2) */
+    MM_TERM_SURFACE = 128,    /* surface anisotropy at free z faces (Ks) */
+    MM_TERM_RKKY = 256,       /* RKKY interlayer exchange (mm_set_rkky) */
+    MM_TERM_MEL = 512,        /* magnetoelastic anisotropy (B1, B2, mm_set_strain) */
+    MM_TERM_ALL = 1023        /* terms whose parameters are all zero are skipped */
 };
 
 /* Energy array layout returned by mm_energy. */
 enum mm_energy_index { MM_E_EXCHANGE = 0, MM_E_DMI = 1, MM_E_ANISOTROPY = 2, MM_E_ZEEMAN = 3,
-                       MM_E_DEMAG = 4, MM_E_TOTAL = 5, MM_NENERGY = 6 };
+                       MM_E_DEMAG = 4, MM_E_TOTAL = 5, MM_E_CUBIC = 6, MM_E_SURFACE = 7,
+                       MM_E_RKKY = 8, MM_E_MEL = 9, MM_NENERGY = 10 };
 
 enum mm_torque_kind { MM_TORQUE_NONE = 0, MM_TORQUE_SOT = 1, MM_TORQUE_STT = 2, MM_TORQUE_ZL = 3 };
 
@@ -112,6 +117,19 @@ typedef struct mm_material {
     const double *Ms_cell, *A_cell, *alpha_cell, *Ku1_cell, *u_cell, *D_cell;
     double D_bulk;
     const double* D_bulk_cell;
+    /* Further anisotropies (Methods, "Physics and discretization"), uniform
+     * over the material's present cells:
+     *  cubic: energy density Kc1 (a^2 b^2 + b^2 c^2 + c^2 a^2) + Kc2 a^2 b^2 c^2,
+     *    a, b, c the components of m on the axes c1, c2 (its c1 component
+     *    removed) and c3 = c1 x c2 (J/m^3);
+     *  surface: -Ks (m.z)^2 per area of every free z face of a cell, an
+     *    absent neighbour above or below (J/m^2);
+     *  magnetoelastic: B1 (e_xx m_x^2 + e_yy m_y^2 + e_zz m_z^2) +
+     *    2 B2 (e_xy m_x m_y + e_xz m_x m_z + e_yz m_y m_z) with the strain of
+     *    mm_set_strain (J/m^3). */
+    double Kc1, Kc2, c1[3], c2[3];
+    double Ks;
+    double B1, B2;
 } mm_material;
 
 typedef struct mm_config {
@@ -207,6 +225,21 @@ MM_API mm_status mm_get_m_device(mm_ctx* ctx, void* m_dev);
 /* Applied field B (tesla): uniform B[3], or per cell (3N) when B_cell != NULL. */
 MM_API mm_status mm_set_field(mm_ctx* ctx, int replica, const double B[3], const double* B_cell);
 
+/* Strain tensor of the magnetoelastic term: eps[6] = xx, yy, zz, xy, xz, yz
+ * for every cell, or per cell (eps_cell, 6N doubles component-major) when
+ * eps_cell != NULL.  Replica-batched contexts take the uniform form only.
+ * Errors: MM_ERR_ARG (both NULL), MM_ERR_OOM. */
+MM_API mm_status mm_set_strain(mm_ctx* ctx, const double eps[6], const double* eps_cell);
+
+/* RKKY interlayer exchange (Methods, "Physics and discretization") between
+ * layers k1 and k2 (z indices, usually on either side of an Ms = 0 spacer):
+ * energy -J m(k1).m(k2) per column area (J in J/m^2, J > 0 favours
+ * parallel moments), so a coupled cell sees (J / (mu0 Ms dz)) times its
+ * partner's moment where both cells are present.  J = 0 turns the
+ * coupling off.  Errors: MM_ERR_ARG (layers out of range or equal),
+ * MM_ERR_STATE (replica-batched context). */
+MM_API mm_status mm_set_rkky(mm_ctx* ctx, int k1, int k2, double J);
+
 /* Temperature per replica (R values, kelvin). */
 MM_API mm_status mm_set_temperature(mm_ctx* ctx, const double* T);
 
@@ -228,7 +261,8 @@ MM_API mm_status mm_run(mm_ctx* ctx, double t_end);
  * the terms in term_mask (MM_TERM_THERMAL uses the current step's noise). */
 MM_API mm_status mm_get_heff(mm_ctx* ctx, int replica, double* H, unsigned term_mask);
 
-/* Energy per term and total (joules): E[MM_NENERGY], FP64 compensated sums. */
+/* Energy per term and total (joules): E[MM_NENERGY], FP64 compensated sums;
+ * E[MM_E_TOTAL] sums every term, those indexed after it included. */
 MM_API mm_status mm_energy(mm_ctx* ctx, int replica, double* E);
 
 /* Topological charge Q = (1/4pi) sum m.(dm/dx x dm/dy) dx dy of layer

@@ -86,6 +86,30 @@ static Region<T> region_coeffs(const RegionHost& r, double /*V*/) {
     o.inv_Ms = present ? (T)(1.0 / r.Ms) : (T)0;
     o.ratio_b = r.A > 0 ? (T)(r.Db / (2.0 * r.A)) : (T)0;
     o.dmib = (T)(2.0 * r.Db * imu);
+    o.kc1 = (T)(2.0 * r.Kc1 * imu);
+    o.kc2 = (T)(2.0 * r.Kc2 * imu);
+    // cubic axes: c1 normalised, c2 with its c1 part removed, c3 = c1 x c2
+    double a1[3] = {r.c1[0], r.c1[1], r.c1[2]}, a2[3] = {r.c2[0], r.c2[1], r.c2[2]};
+    double n1 = std::sqrt(a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2]);
+    if (n1 == 0) { a1[0] = 1; a1[1] = a1[2] = 0; n1 = 1; }
+    for (double& v : a1) v /= n1;
+    const double p12 = a2[0] * a1[0] + a2[1] * a1[1] + a2[2] * a1[2];
+    for (int k = 0; k < 3; ++k) a2[k] -= p12 * a1[k];
+    double n2 = std::sqrt(a2[0] * a2[0] + a2[1] * a2[1] + a2[2] * a2[2]);
+    if (n2 == 0) {   // any direction normal to c1
+        const double t[3] = {std::fabs(a1[0]) < 0.9 ? 1.0 : 0.0, std::fabs(a1[0]) < 0.9 ? 0.0 : 1.0, 0.0};
+        const double q = t[0] * a1[0] + t[1] * a1[1];
+        for (int k = 0; k < 3; ++k) a2[k] = t[k] - q * a1[k];
+        n2 = std::sqrt(a2[0] * a2[0] + a2[1] * a2[1] + a2[2] * a2[2]);
+    }
+    for (double& v : a2) v /= n2;
+    const double a3[3] = {a1[1] * a2[2] - a1[2] * a2[1], a1[2] * a2[0] - a1[0] * a2[2], a1[0] * a2[1] - a1[1] * a2[0]};
+    o.c1x = (T)a1[0]; o.c1y = (T)a1[1]; o.c1z = (T)a1[2];
+    o.c2x = (T)a2[0]; o.c2y = (T)a2[1]; o.c2z = (T)a2[2];
+    o.c3x = (T)a3[0]; o.c3y = (T)a3[1]; o.c3z = (T)a3[2];
+    o.ks = (T)(2.0 * r.Ks * imu);
+    o.b1 = (T)(2.0 * r.B1 * imu);
+    o.b2 = (T)(2.0 * r.B2 * imu);
     return o;
 }
 
@@ -122,7 +146,9 @@ static mm_status build_regions(mm_ctx* c, const mm_material* mat) {
     const long long N = c->N;
     const bool percell = mat->Ms_cell || mat->A_cell || mat->alpha_cell || mat->Ku1_cell || mat->u_cell ||
                          mat->D_cell || mat->D_bulk_cell;
-    RegionHost base{mat->Ms, mat->A, mat->alpha, mat->Ku1, {mat->u[0], mat->u[1], mat->u[2]}, mat->D, mat->D_bulk};
+    RegionHost base{mat->Ms, mat->A, mat->alpha, mat->Ku1, {mat->u[0], mat->u[1], mat->u[2]}, mat->D, mat->D_bulk,
+                    mat->Kc1, mat->Kc2, {mat->c1[0], mat->c1[1], mat->c1[2]}, {mat->c2[0], mat->c2[1], mat->c2[2]},
+                    mat->Ks, mat->B1, mat->B2};
     c->regions.clear();
     if (!percell) {
         c->regions.push_back(base);
@@ -186,6 +212,26 @@ static mm_status status_from_device(mm_ctx* c) {
     return MM_OK;
 }
 
+// Effective terms: the requested ones without those whose parameters are
+// all zero (cubic, surface, magnetoelastic, RKKY), so they cost nothing
+// unless used.
+static void update_terms(mm_ctx* c) {
+    unsigned t = c->terms_req;
+    bool cubic = false, surf = false, mel = false;
+    for (const RegionHost& r : c->regions) {
+        cubic = cubic || r.Kc1 != 0 || r.Kc2 != 0;
+        surf = surf || r.Ks != 0;
+        mel = mel || r.B1 != 0 || r.B2 != 0;
+    }
+    bool strain = c->d_strain != nullptr;
+    for (double e : c->strain) strain = strain || e != 0;
+    if (!cubic) t &= ~MM_TERM_CUBIC;
+    if (!surf) t &= ~MM_TERM_SURFACE;
+    if (!mel || !strain) t &= ~MM_TERM_MEL;
+    if (c->rkky_J == 0) t &= ~MM_TERM_RKKY;
+    c->terms = t;
+}
+
 static void free_all(mm_ctx* c) {
     invalidate_graph(c);
     demag_free(c);
@@ -193,7 +239,7 @@ static void free_all(mm_ctx* c) {
     c->batch = nullptr;
     surrogate_free(c);
     void* bufs[] = {c->d_region, c->d_lut, c->d_cpair, c->d_m, c->d_mtmp, c->d_kslot, c->d_hd, c->d_hbuf,
-                    c->d_bcell, c->d_state, c->d_replay, c->d_red, c->d_stage};
+                    c->d_bcell, c->d_state, c->d_replay, c->d_red, c->d_stage, c->d_strain};
     for (void* b : bufs) cudaFree(b);
     for (auto& k : c->d_k) cudaFree(k);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -329,6 +375,7 @@ mm_status mm_create(const mm_grid* grid, const mm_material* mat, const mm_config
     c->integrator = cfg->integrator;
     c->terms = cfg->terms ? cfg->terms : MM_TERM_ALL;
     if (cfg->demag != MM_DEMAG_EXACT) c->terms &= ~MM_TERM_DEMAG;
+    c->terms_req = c->terms;
     c->grid = *grid;
     c->N = (long long)grid->nx * grid->ny * grid->nz;
     c->cfg = *cfg;
@@ -339,6 +386,7 @@ mm_status mm_create(const mm_grid* grid, const mm_material* mat, const mm_config
     c->stream = c->own_stream;
 #define TRY(x) do { mm_status _s = (x); if (_s != MM_OK) { g_create_error = c->last_error; free_all(c); delete c; return _s; } } while (0)
     TRY(build_regions(c, mat));
+    update_terms(c);
     TRY(c->prec == 32 ? upload_regions_t<float>(c) : upload_regions_t<double>(c));
     const size_t vb = 3 * N * c->esz;
     TRY(alloc(c, &c->d_m, vb, "state"));
@@ -349,7 +397,7 @@ mm_status mm_create(const mm_grid* grid, const mm_material* mat, const mm_config
     TRY(alloc(c, &c->d_kslot, sizeof(void*) * 7, "slot table"));
     cudaMemcpy(c->d_kslot, c->d_k, sizeof(void*) * 7, cudaMemcpyHostToDevice);
     TRY(alloc(c, (void**)&c->d_state, sizeof(DevState), "device state"));
-    c->red_cap = 2 * 304 + 16;
+    c->red_cap = 2 * 304 + 32;
     TRY(alloc(c, (void**)&c->d_red, sizeof(double) * c->red_cap, "reduction partials"));
     if (c->terms & MM_TERM_DEMAG) {
         TRY(alloc(c, &c->d_hd, vb, "demag field"));
@@ -424,6 +472,7 @@ mm_status mm_create_batch(int R, const mm_grid* grids, const mm_material* mat, c
     c->integrator = cfg->integrator;
     c->terms = cfg->terms ? cfg->terms : MM_TERM_ALL;
     if (cfg->demag != MM_DEMAG_EXACT) c->terms &= ~MM_TERM_DEMAG;
+    c->terms_req = c->terms;
     c->cfg = *cfg;
     c->R = R;
     c->grid = grids[0];
@@ -446,6 +495,7 @@ mm_status mm_create_batch(int R, const mm_grid* grids, const mm_material* mat, c
     c->stream = c->own_stream;
 #define TRY(x) do { mm_status _s = (x); if (_s != MM_OK) { g_create_error = c->last_error; free_all(c); delete c; return _s; } } while (0)
     TRY(build_regions(c, mat));
+    update_terms(c);
     TRY(upload_regions_t<float>(c));
     const size_t vb = 3 * c->Ntot * 4;
     TRY(alloc(c, &c->d_m, vb, "state"));
@@ -456,7 +506,7 @@ mm_status mm_create_batch(int R, const mm_grid* grids, const mm_material* mat, c
     TRY(alloc(c, &c->d_kslot, sizeof(void*) * 7, "slot table"));
     cudaMemcpy(c->d_kslot, c->d_k, sizeof(void*) * 7, cudaMemcpyHostToDevice);
     TRY(alloc(c, (void**)&c->d_state, sizeof(DevState), "device state"));
-    c->red_cap = 2 * 304 + 16;
+    c->red_cap = 2 * 304 + 32;
     TRY(alloc(c, (void**)&c->d_red, sizeof(double) * c->red_cap, "reduction partials"));
     c->batch = batch_new();
     TRY(batch_setup(c, c->batch, c->rgrid, c->rkey, (c->terms & MM_TERM_DEMAG) != 0));
@@ -635,6 +685,51 @@ mm_status mm_set_field(mm_ctx* c, int r, const double B[3], const double* B_cell
         cudaFree(c->d_bcell);
         c->d_bcell = nullptr;
     }
+    c->k1_valid = false;
+    invalidate_graph(c);
+    return MM_OK;
+}
+
+mm_status mm_set_strain(mm_ctx* c, const double eps[6], const double* eps_cell) {
+    if (!c || (!eps && !eps_cell)) return set_error(c, MM_ERR_ARG, "strain: eps or eps_cell is required");
+    if (eps_cell && c->batch) return set_error(c, MM_ERR_ARG, "replica-batched contexts take a uniform strain");
+    cudaStreamSynchronize(c->stream);
+    if (eps_cell) {
+        const long long n6 = 6 * c->N;
+        if (!c->d_strain) {
+            mm_status a = alloc(c, &c->d_strain, n6 * c->esz, "per-cell strain");
+            if (a != MM_OK) return a;
+        }
+        cudaError_t e;
+        if (c->prec == 32) {
+            std::vector<float> h(eps_cell, eps_cell + n6);
+            e = cudaMemcpy(c->d_strain, h.data(), n6 * 4, cudaMemcpyHostToDevice);
+        } else {
+            e = cudaMemcpy(c->d_strain, eps_cell, n6 * 8, cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) return cuda_check(c, e, "strain upload");
+        for (double& v : c->strain) v = 0.0;
+    } else {
+        cudaFree(c->d_strain);
+        c->d_strain = nullptr;
+        for (int k = 0; k < 6; ++k) c->strain[k] = eps[k];
+    }
+    update_terms(c);
+    c->k1_valid = false;
+    invalidate_graph(c);
+    return MM_OK;
+}
+
+mm_status mm_set_rkky(mm_ctx* c, int k1, int k2, double J) {
+    if (!c) return MM_ERR_ARG;
+    if (c->batch) return set_error(c, MM_ERR_STATE, "RKKY couples layers of a single-instance context");
+    if (k1 < 0 || k2 < 0 || k1 >= c->grid.nz || k2 >= c->grid.nz || k1 == k2 || !std::isfinite(J))
+        return set_error(c, MM_ERR_ARG, "RKKY layers must be two different z indices of the grid");
+    cudaStreamSynchronize(c->stream);
+    c->rkky_k1 = k1;
+    c->rkky_k2 = k2;
+    c->rkky_J = J;
+    update_terms(c);
     c->k1_valid = false;
     invalidate_graph(c);
     return MM_OK;
@@ -950,21 +1045,31 @@ mm_status mm_energy(mm_ctx* c, int r, double* E) {
     if (s != MM_OK) return s;
     ReplicaView view(c, r);
     if (!E) return set_error(c, MM_ERR_ARG, "null output");
-    static const unsigned term_of[5] = {MM_TERM_EXCHANGE, MM_TERM_DMI, MM_TERM_ANISOTROPY, MM_TERM_ZEEMAN, MM_TERM_DEMAG};
+    // e = -1/2 mu0 Ms m.H_term for the terms quadratic in m (-mu0 Ms m.H for
+    // Zeeman); the cubic term is quartic (Kc1) and sextic (Kc2) in m, so its
+    // two parts enter with weights 1/2 and 1/3 (Euler: m.dE/dm = 4E, 6E)
+    static const unsigned term_of[9] = {MM_TERM_EXCHANGE, MM_TERM_DMI, MM_TERM_ANISOTROPY, MM_TERM_ZEEMAN,
+                                        MM_TERM_DEMAG, MM_TERM_CUBIC, MM_TERM_SURFACE, MM_TERM_RKKY, MM_TERM_MEL};
+    static const int slot_of[9] = {MM_E_EXCHANGE, MM_E_DMI, MM_E_ANISOTROPY, MM_E_ZEEMAN, MM_E_DEMAG,
+                                   MM_E_CUBIC, MM_E_SURFACE, MM_E_RKKY, MM_E_MEL};
     double* d_out = c->d_red + 2 * 304;
-    double h[MM_NENERGY] = {0, 0, 0, 0, 0, 0};
-    for (int q = 0; q < 5; ++q) {
+    double h[MM_NENERGY] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    cudaMemsetAsync(d_out, 0, sizeof(double) * MM_NENERGY, c->stream);
+    for (int q = 0; q < 9; ++q) {
         if (!(c->terms & term_of[q]) || (q == 4 && !c->dm.on)) continue;
         if (q == 4) demag_apply(c, c->d_m, c->d_hd);
+        c->cubic_energy = q == 5;
         field_launch(c, MODE_H, term_of[q], c->d_m, q == 4 ? c->d_hd : nullptr, c->d_hbuf, nullptr, nullptr, nullptr,
                      -1, 0, 0);
-        energy_term_launch(c, c->d_m, c->d_hbuf, q, d_out + q);
+        c->cubic_energy = false;
+        energy_term_launch(c, c->d_m, c->d_hbuf, slot_of[q], d_out + slot_of[q]);
     }
-    cudaError_t e = cudaMemcpyAsync(h, d_out, sizeof(double) * 5, cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e = cudaMemcpyAsync(h, d_out, sizeof(double) * MM_NENERGY, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_check(c, e, "mm_energy");
     double tot = 0.0, comp = 0.0;
-    for (int q = 0; q < 5; ++q) {
+    for (int q = 0; q < MM_NENERGY; ++q) {
+        if (q == MM_E_TOTAL) continue;
         E[q] = h[q];
         const double t = tot + h[q];
         comp += std::fabs(tot) >= std::fabs(h[q]) ? (tot - t) + h[q] : (h[q] - t) + tot;
@@ -979,7 +1084,7 @@ mm_status mm_topo_charge(mm_ctx* c, int r, int layer, double* Q) {
     if (s != MM_OK) return s;
     ReplicaView view(c, r);
     if (!Q || layer >= c->grid.nz) return set_error(c, MM_ERR_ARG, "bad layer or null output");
-    double* d_out = c->d_red + 2 * 304 + 8;
+    double* d_out = c->d_red + 2 * 304 + 16;
     topo_launch(c, c->d_m, layer, d_out);
     double h = 0;
     cudaError_t e = cudaMemcpyAsync(&h, d_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream);

@@ -206,6 +206,9 @@ static void batch_field_args(mm_ctx* c, FieldArgs<float>& f) {
     f.P = (float)q.P;
     f.L2 = (float)(q.Lambda * q.Lambda);
     f.eps_p = (float)q.eps_prime;
+    f.cubic_w1 = f.cubic_w2 = 1.f;
+    for (int k = 0; k < 6; ++k) f.strain[k] = (float)c->strain[k];
+    f.strain_cell = nullptr;
 }
 
 static void launch_stage(mm_ctx* c, BatchHost* b, int stage) {

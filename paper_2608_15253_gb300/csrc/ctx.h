@@ -32,10 +32,15 @@ struct Region {
     T inv_Ms;     // 1/Ms, 0 when absent
     T ratio_b;    // bulk DMI: Db / (2 A), 0 when A = 0
     T dmib;       // bulk DMI: 2 Db / (mu0 Ms)
+    T kc1, kc2;   // cubic: 2 Kc1 / (mu0 Ms), 2 Kc2 / (mu0 Ms)
+    T c1x, c1y, c1z, c2x, c2y, c2z, c3x, c3y, c3z;   // orthonormal cubic axes
+    T ks;         // surface: 2 Ks / (mu0 Ms) (divided by dz in the kernel)
+    T b1, b2;     // magnetoelastic: 2 B1 / (mu0 Ms), 2 B2 / (mu0 Ms)
 };
 
 struct RegionHost {
     double Ms, A, alpha, Ku1, u[3], D, Db;
+    double Kc1, Kc2, c1[3], c2[3], Ks, B1, B2;   // uniform over the material
     bool operator==(const RegionHost& o) const {
         return Ms == o.Ms && A == o.A && alpha == o.alpha && Ku1 == o.Ku1 && u[0] == o.u[0] &&
                u[1] == o.u[1] && u[2] == o.u[2] && D == o.D && Db == o.Db;
@@ -128,6 +133,13 @@ struct mm_ctx {
     long long stage_n = 0;
     void* d_bcell = nullptr;    // per-cell applied field (A/m) or null
     double Hext[3] = {0, 0, 0}; // uniform applied field (A/m)
+    unsigned terms_req = MM_TERM_ALL;   // requested terms; `terms` drops those without parameters
+    bool cubic_energy = false;          // field evaluation weighted for the cubic energy
+    double strain[6] = {0, 0, 0, 0, 0, 0};   // uniform strain (magnetoelastic)
+    void* d_strain = nullptr;   // per-cell strain [6][N] or null
+    bool strain_set = false;
+    int rkky_k1 = 0, rkky_k2 = 0;
+    double rkky_J = 0.0;        // J/m^2; 0: off
     double Tr = 0.0;            // temperature
     uint64_t seed = 0;          // Philox key of the replica
 

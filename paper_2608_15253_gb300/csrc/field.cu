@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) field_vec_kernel(FieldArgs<float> a) {
     VT mc[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) mc[c] = ldv<V>(a.m + c * N + i0);
-    const bool need_nb = (a.terms & (MM_TERM_EXCHANGE | MM_TERM_DMI)) || a.tq == MM_TORQUE_ZL;
+    const bool need_nb = (a.terms & (MM_TERM_EXCHANGE | MM_TERM_DMI | MM_TERM_SURFACE)) || a.tq == MM_TORQUE_ZL;
     // neighbour rows (y+, y-, z+, z-) as vectors, row-end x neighbours as scalars
     VT nr[4][3];
     bool rin[4] = {false, false, false, false};
@@ -264,6 +264,13 @@ static void field_launch_t(mm_ctx* c, int mode, unsigned terms, const T* m, cons
     a.th_scale = c->Tr > 0 ? (T)std::sqrt(c->Tr / (V * c->cfg.dt)) : (T)0;
     a.st = c->d_state;
     a.step_override = step_override;
+    a.cubic_w1 = c->cubic_energy ? (T)0.5 : (T)1;
+    a.cubic_w2 = c->cubic_energy ? (T)(1.0 / 3.0) : (T)1;
+    for (int k = 0; k < 6; ++k) a.strain[k] = (T)c->strain[k];
+    a.strain_cell = (const T*)c->d_strain;
+    a.rk1 = c->rkky_k1;
+    a.rk2 = c->rkky_k2;
+    a.rkky_c = (T)(c->rkky_J / g.dz);
     const mm_torque& q = c->tq;
     a.tq = q.kind;
     if (q.kind == MM_TORQUE_SOT || q.kind == MM_TORQUE_STT) {

@@ -89,6 +89,12 @@ struct FieldArgs {
     T zl_u;               // J P mu_B / e [/(1+xi^2)] (times 1/Ms -> m/s)
     T xi;
     T dir[3];
+    // further local terms
+    T cubic_w1, cubic_w2; // weights of the Kc1 / Kc2 parts (1; 1/2 and 1/3 for energies)
+    T strain[6];          // uniform strain xx yy zz xy xz yz
+    const T* strain_cell; // per-cell strain [6][N] or null
+    int rk1, rk2;         // RKKY layers
+    T rkky_c;             // J / dz (times 1/(mu0 Ms) -> A/m per unit m)
 };
 
 // Thermal field of cell i at noise counter `step`: Philox4x32-10 keyed by
@@ -165,6 +171,45 @@ __device__ __forceinline__ void cell_field_nb(const FieldArgs<T>& a, long long i
     if (a.terms & MM_TERM_ZEEMAN) {
         if (a.Bc) H = H + ld3(a.Bc, N, i);
         else H = H + mk3<T>(a.hext[0], a.hext[1], a.hext[2]);
+    }
+    if (a.terms & MM_TERM_CUBIC) {
+        // -(1/mu0 Ms) dE/dm of Kc1 (a^2 b^2 + b^2 c^2 + c^2 a^2) + Kc2 a^2 b^2 c^2
+        const v3<T> c1 = mk3<T>(R.c1x, R.c1y, R.c1z), c2 = mk3<T>(R.c2x, R.c2y, R.c2z);
+        const v3<T> c3 = mk3<T>(R.c3x, R.c3y, R.c3z);
+        const T p = dot(m, c1), q = dot(m, c2), r = dot(m, c3);
+        const T p2 = p * p, q2 = q * q, r2 = r * r;
+        const T k1 = R.kc1 * a.cubic_w1, k2 = R.kc2 * a.cubic_w2;
+        const T g1 = k1 * p * (q2 + r2) + k2 * p * q2 * r2;
+        const T g2 = k1 * q * (p2 + r2) + k2 * p2 * q * r2;
+        const T g3 = k1 * r * (p2 + q2) + k2 * p2 * q2 * r;
+        H = H - (g1 * c1 + g2 * c2 + g3 * c3);
+    }
+    if (a.terms & MM_TERM_SURFACE) {
+        // (2 Ks / mu0 Ms dz) m_z z per free z face
+        const T faces = (nbp[4] ? (T)0 : (T)1) + (nbp[5] ? (T)0 : (T)1);
+        H.z += R.ks / a.hz * faces * m.z;
+    }
+    if (a.terms & MM_TERM_RKKY) {
+        const long long plane = (long long)a.nx * a.ny;
+        const int z = (int)(i / plane);
+        if (z == a.rk1 || z == a.rk2) {
+            const long long j = i + (long long)((z == a.rk1 ? a.rk2 : a.rk1) - z) * plane;
+            const bool there = a.region ? a.lut[a.region[j]].present != (T)0 : true;
+            if (there) H = H + (a.rkky_c * R.inv_mu0Ms) * ld3(a.m, N, j);
+        }
+    }
+    if (a.terms & MM_TERM_MEL) {
+        T e[6];
+        if (a.strain_cell) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) e[k] = __ldg(a.strain_cell + k * N + i);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) e[k] = a.strain[k];
+        }
+        H = H - mk3<T>(R.b1 * e[0] * m.x + R.b2 * (e[3] * m.y + e[4] * m.z),
+                       R.b1 * e[1] * m.y + R.b2 * (e[3] * m.x + e[5] * m.z),
+                       R.b1 * e[2] * m.z + R.b2 * (e[4] * m.x + e[5] * m.y));
     }
     if (a.terms & MM_TERM_DEMAG) {
         if (use_hd) H = H + hdv;
@@ -270,8 +315,9 @@ __device__ __forceinline__ void cell_field(const FieldArgs<T>& a, int x, int y, 
                                            const Region<T>& R, const v3<T>& m, const v3<T>* hd, long long step,
                                            v3<T>& H, v3<T>& k, bool want_k, bool as_omega = false) {
     const long long N = a.N;
-    const bool need_nb = (a.terms & (MM_TERM_EXCHANGE | MM_TERM_DMI)) || a.tq == MM_TORQUE_ZL;
-    // neighbour values (ghosts where absent) and raw presence for Zhang-Li
+    const bool need_nb = (a.terms & (MM_TERM_EXCHANGE | MM_TERM_DMI | MM_TERM_SURFACE)) || a.tq == MM_TORQUE_ZL;
+    // neighbour values (ghosts where absent) and raw presence (Zhang-Li,
+    // the free faces of the surface term)
     v3<T> nbv[6];
     bool nbp[6];
     T cnb[6];

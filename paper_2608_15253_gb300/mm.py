@@ -24,8 +24,10 @@ MM_ERR_NONFINITE, MM_ERR_DT_UNDERFLOW, MM_ERR_TIMEOUT, MM_ERR_STATE = 5, 6, 7, 8
 MM_HEUN, MM_RK45, MM_RK4, MM_DM = 0, 1, 2, 3
 MM_DEMAG_OFF, MM_DEMAG_EXACT, MM_DEMAG_SURROGATE = 0, 1, 2
 MM_TERM_EXCHANGE, MM_TERM_DMI, MM_TERM_ANISOTROPY = 1, 2, 4
-MM_TERM_ZEEMAN, MM_TERM_DEMAG, MM_TERM_THERMAL, MM_TERM_ALL = 8, 16, 32, 63
-MM_E_EXCHANGE, MM_E_DMI, MM_E_ANISOTROPY, MM_E_ZEEMAN, MM_E_DEMAG, MM_E_TOTAL, MM_NENERGY = range(7)
+MM_TERM_ZEEMAN, MM_TERM_DEMAG, MM_TERM_THERMAL = 8, 16, 32
+MM_TERM_CUBIC, MM_TERM_SURFACE, MM_TERM_RKKY, MM_TERM_MEL, MM_TERM_ALL = 64, 128, 256, 512, 1023
+MM_E_EXCHANGE, MM_E_DMI, MM_E_ANISOTROPY, MM_E_ZEEMAN, MM_E_DEMAG, MM_E_TOTAL = range(6)
+MM_E_CUBIC, MM_E_SURFACE, MM_E_RKKY, MM_E_MEL, MM_NENERGY = 6, 7, 8, 9, 10
 MM_TORQUE_NONE, MM_TORQUE_SOT, MM_TORQUE_STT, MM_TORQUE_ZL = 0, 1, 2, 3
 
 _D = C.POINTER(C.c_double)
@@ -40,7 +42,9 @@ class mm_material(C.Structure):
     _fields_ = [("Ms", C.c_double), ("A", C.c_double), ("alpha", C.c_double), ("Ku1", C.c_double),
                 ("u", C.c_double * 3), ("D", C.c_double),
                 ("Ms_cell", _D), ("A_cell", _D), ("alpha_cell", _D), ("Ku1_cell", _D),
-                ("u_cell", _D), ("D_cell", _D), ("D_bulk", C.c_double), ("D_bulk_cell", _D)]
+                ("u_cell", _D), ("D_cell", _D), ("D_bulk", C.c_double), ("D_bulk_cell", _D),
+                ("Kc1", C.c_double), ("Kc2", C.c_double), ("c1", C.c_double * 3), ("c2", C.c_double * 3),
+                ("Ks", C.c_double), ("B1", C.c_double), ("B2", C.c_double)]
 
 
 class mm_config(C.Structure):
@@ -100,6 +104,8 @@ _SIGS = {
     "mm_get_m_device": [C.c_void_p, C.c_void_p],
     "mm_set_field": [C.c_void_p, C.c_int, _D, _D],
     "mm_set_temperature": [C.c_void_p, _D],
+    "mm_set_strain": [C.c_void_p, _D, _D],
+    "mm_set_rkky": [C.c_void_p, C.c_int, C.c_int, C.c_double],
     "mm_set_torque": [C.c_void_p, C.POINTER(mm_torque), _D],
     "mm_step": [C.c_void_p, C.c_long],
     "mm_step_dt": [C.c_void_p, _D, C.c_long],
@@ -255,6 +261,18 @@ def mm_get_heff(ctx, replica: int, shape, term_mask: int = MM_TERM_ALL):
     out = np.zeros(shape, dtype=np.float64)
     _check(load().mm_get_heff(ctx, replica, _dptr(out), term_mask), ctx)
     return out
+
+
+def mm_set_strain(ctx, eps=None, eps_cell=None):
+    """Uniform strain eps[6] (xx, yy, zz, xy, xz, yz) or per cell (6, nz, ny, nx)."""
+    e = None if eps is None else np.ascontiguousarray(eps, dtype=np.float64)
+    ec = None if eps_cell is None else _f64(eps_cell)
+    _check(load().mm_set_strain(ctx, _dptr(e) if e is not None else None, _dptr(ec) if ec is not None else None),
+           ctx)
+
+
+def mm_set_rkky(ctx, k1: int, k2: int, J: float):
+    _check(load().mm_set_rkky(ctx, int(k1), int(k2), float(J)), ctx)
 
 
 def mm_energy(ctx, replica: int = 0):
@@ -449,11 +467,15 @@ def make_grid(nx, ny, nz, dx, dy, dz, pbc=(0, 0, 0)) -> mm_grid:
 class Material:
     """mm_material plus ownership of its per-cell arrays (kept alive here)."""
 
-    def __init__(self, Ms, A, alpha, Ku1=0.0, u=(0.0, 0.0, 1.0), D=0.0, cells=None, Db=0.0):
+    def __init__(self, Ms, A, alpha, Ku1=0.0, u=(0.0, 0.0, 1.0), D=0.0, cells=None, Db=0.0, Kc1=0.0, Kc2=0.0,
+                 c1=(1.0, 0.0, 0.0), c2=(0.0, 1.0, 0.0), Ks=0.0, B1=0.0, B2=0.0):
         self.s = mm_material(Ms, A, alpha, Ku1)
         self.s.u[:] = list(u)
         self.s.D = D
         self.s.D_bulk = Db
+        self.s.Kc1, self.s.Kc2, self.s.Ks, self.s.B1, self.s.B2 = Kc1, Kc2, Ks, B1, B2
+        self.s.c1[:] = list(c1)
+        self.s.c2[:] = list(c2)
         self._keep = []
         for name, arr in (cells or {}).items():
             a = _f64(arr)

@@ -5,7 +5,8 @@ import pytest
 
 import workloads as W
 
-TERMS = {"exchange": 1, "dmi": 2, "anisotropy": 4, "zeeman": 8, "demag": 16, "thermal": 32}
+TERMS = {"exchange": 1, "dmi": 2, "anisotropy": 4, "zeeman": 8, "demag": 16, "thermal": 32, "cubic": 64,
+         "surface": 128, "rkky": 256, "magnetoelastic": 512}
 
 
 def need_gpu():
@@ -21,7 +22,8 @@ def make_ctx(mm, grid: W.Grid, mat: W.Material, precision=64, integrator=None, d
              dt=1e-14, rtol=1e-6, T=0.0, seed=0, B=(0.0, 0.0, 0.0), B_cell=None):
     integ = {None: mm.MM_RK45, "rk45": mm.MM_RK45, "rk4": mm.MM_RK4, "heun": mm.MM_HEUN, "dm": mm.MM_DM}[integrator]
     g = mm.make_grid(grid.nx, grid.ny, grid.nz, grid.dx, grid.dy, grid.dz, grid.pbc)
-    m = mm.Material(mat.Ms, mat.A, mat.alpha, mat.Ku1, mat.u, mat.D, cells=mat.cell, Db=mat.Db)
+    m = mm.Material(mat.Ms, mat.A, mat.alpha, mat.Ku1, mat.u, mat.D, cells=mat.cell, Db=mat.Db, Kc1=mat.Kc1,
+                    Kc2=mat.Kc2, c1=mat.c1, c2=mat.c2, Ks=mat.Ks, B1=mat.B1, B2=mat.B2)
     cfg = mm.make_config(precision=precision, integrator=integ,
                          demag=mm.MM_DEMAG_EXACT if demag else mm.MM_DEMAG_OFF,
                          terms=terms, dt=dt, rtol=rtol, T=T, seed=seed)
