@@ -230,6 +230,10 @@ static void update_terms(mm_ctx* c) {
     if (!mel || !strain) t &= ~MM_TERM_MEL;
     if (c->rkky_J == 0) t &= ~MM_TERM_RKKY;
     c->terms = t;
+    bool bulk = false;
+    for (const RegionHost& r : c->regions) bulk = bulk || r.Db != 0;
+    c->ext_terms = (bulk && (t & MM_TERM_DMI)) ||
+                   (t & (MM_TERM_CUBIC | MM_TERM_SURFACE | MM_TERM_RKKY | MM_TERM_MEL)) != 0;
 }
 
 static void free_all(mm_ctx* c) {
@@ -892,7 +896,7 @@ static mm_status advance(mm_ctx* c, long long add_steps, double t_end, int repla
     s = ensure_k1(c);
     if (s != MM_OK) return s;
     const bool heun = c->integrator != MM_RK45;   // fixed-step schemes: every attempt is accepted
-    if (c->batch && batch_is_macro(c->batch)) {
+    if (c->batch && batch_is_fused(c->batch)) {
         // one-cell replicas: blocks of fused steps, no graph needed
         long long want = add_steps >= 0 ? add_steps
                                         : (long long)std::ceil((t_end - c->h_state.t) / c->h_state.dt);

@@ -31,6 +31,8 @@ struct BatchHost {
     size_t smem = 0;
     double sigma_V = 1.0;   // cell volume used in the thermal scale
     bool macro = false;     // every replica one cell, no demag: macro_kernel
+    bool tile = false;      // no demag, every replica at most kTileMaxCells cells: tile_kernel
+    int nmax = 0;           // largest replica (cells)
     // retire/refill
     bool trials_on = false;
     TrialDev tr{};
@@ -104,7 +106,16 @@ mm_status batch_setup(mm_ctx* c, BatchHost* b, const std::vector<mm_grid>& grids
         off += 3LL * g.nx * g.ny;
     }
     b->macro = !demag;
-    for (const RepDev& d : b->rep) b->macro = b->macro && d.nx == 1 && d.ny == 1;
+    b->nmax = 0;
+    for (const RepDev& d : b->rep) {
+        b->macro = b->macro && d.nx == 1 && d.ny == 1;
+        b->nmax = std::max(b->nmax, d.nx * d.ny);
+    }
+    b->tile = !demag && !b->macro && b->nmax <= kTileMaxCells;
+    if (b->tile) {
+        cudaError_t ea = tile_kernel_attributes();
+        if (ea != cudaSuccess) return cuda_check(c, ea, "tile kernel attributes");
+    }
     long long max_spec = 1;
     for (size_t q = 0; q < b->cgrid.size(); ++q) {
         const mm_grid& g = b->cgrid[q];
@@ -241,10 +252,10 @@ static void launch_stage(mm_ctx* c, BatchHost* b, int stage) {
     else batch_kernel_launch_256(a, b->blocks, b->smem, c->stream);
 }
 
-bool batch_is_macro(BatchHost* b) { return b->macro; }
+bool batch_is_fused(BatchHost* b) { return b->macro || b->tile; }
 
-// one launch of `nsteps` steps of every one-cell replica, then the step
-// bookkeeping
+// one launch of `nsteps` fused steps of every replica (one-cell or small
+// films without demag), then the step bookkeeping
 void batch_macro_steps(mm_ctx* c, BatchHost* b, int nsteps) {
     MacroArgs a{};
     a.rep = b->d_rep;
@@ -255,11 +266,18 @@ void batch_macro_steps(mm_ctx* c, BatchHost* b, int nsteps) {
     a.tr = b->tr;
     a.st = c->d_state;
     a.nsteps = nsteps;
+    a.nmax = b->nmax;
+    a.ext = c->ext_terms ? 1 : 0;
     batch_field_args(c, a.fa);
     a.fa.terms = c->terms & ~MM_TERM_DEMAG;
-    {
+    if (b->macro) {
         LaunchScope ls(c, "macro_steps", (double)a.R * 24.0);
         macro_kernel_launch(a, c->stream);
+    } else {
+        double cells = 0;
+        for (const RepDev& r : b->rep) cells += (double)r.nx * r.ny;
+        LaunchScope ls(c, "tile_steps", cells * 24.0);
+        tile_kernel_launch(a, c->stream);
     }
     LaunchScope ls(c, "macro_advance", 0.0);
     macro_advance_launch(c->d_state, nsteps, c->stream);

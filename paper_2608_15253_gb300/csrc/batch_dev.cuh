@@ -415,21 +415,28 @@ __global__ void __launch_bounds__(NT) batch_stage_kernel(BatchArgs a) {
     }
 }
 
-// Replicas of one cell each (Results, "Replica batching", the macrospin
-// ensemble): one thread per slot keeps its moment in registers for a block
-// of nsteps steps (macro.cu).
+// Fused blocks of steps for replicas without demag (macro.cu): one-cell
+// replicas (the macrospin ensemble of the paper's batching table and
+// switching sweep) take one thread per slot with the moment in registers;
+// films of up to 1024 cells take one CTA per replica with the state in
+// shared memory and one cell per thread.
 struct MacroArgs {
     RepDev* rep;
     int R;
-    float* m;               // [R][3]
+    float* m;               // state, replica-outermost
     FieldArgs<float> fa;
     int dm;
     int trials;
     TrialDev tr;
     const DevState* st;
     int nsteps;
+    int nmax;               // tile kernel: largest replica (cells)
+    int ext;                // bulk DMI or a further local term is on
 };
+constexpr int kTileMaxCells = 1024;
 void macro_kernel_launch(const MacroArgs& a, cudaStream_t s);
+void tile_kernel_launch(const MacroArgs& a, cudaStream_t s);
+cudaError_t tile_kernel_attributes();
 void macro_advance_launch(DevState* st, int nsteps, cudaStream_t s);
 
 // host wrappers, one set per instantiated thread count

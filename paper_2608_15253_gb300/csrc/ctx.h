@@ -135,6 +135,7 @@ struct mm_ctx {
     double Hext[3] = {0, 0, 0}; // uniform applied field (A/m)
     unsigned terms_req = MM_TERM_ALL;   // requested terms; `terms` drops those without parameters
     bool cubic_energy = false;          // field evaluation weighted for the cubic energy
+    bool ext_terms = true;              // bulk DMI or a further local term is on: the full field kernels
     double strain[6] = {0, 0, 0, 0, 0, 0};   // uniform strain (magnetoelastic)
     void* d_strain = nullptr;   // per-cell strain [6][N] or null
     bool strain_set = false;
@@ -224,7 +225,7 @@ mm_status batch_setup(mm_ctx* c, BatchHost* b, const std::vector<mm_grid>& grids
                       bool demag);
 mm_status batch_upload(mm_ctx* c, BatchHost* b, const std::vector<double>& T, const std::vector<double>& J);
 void batch_step(mm_ctx* c, BatchHost* b);
-bool batch_is_macro(BatchHost* b);
+bool batch_is_fused(BatchHost* b);
 void batch_macro_steps(mm_ctx* c, BatchHost* b, int nsteps);
 mm_status batch_trials_start(mm_ctx* c, BatchHost* b, const mm_trials* sp, long long step_now);
 mm_status batch_trials_result(mm_ctx* c, BatchHost* b, long long* steps, int* stopped, long long* done);

@@ -18,7 +18,7 @@ namespace mm {
 
 // UNIF: one material (coefficients passed by value in the launch
 // parameters, no region map or coefficient-table loads).
-template <typename T, bool UNIF>
+template <typename T, bool UNIF, bool EXT>
 __global__ void __launch_bounds__(256) field_kernel(FieldArgs<T> a) {
     if (a.gate && !a.st->active) return;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(256) field_kernel(FieldArgs<T> a) {
     }
     const long long step = a.step_override >= 0 ? a.step_override : (a.st ? a.st->step : 0);
     v3<T> H, k;
-    cell_field<T, UNIF>(a, x, y, z, i, ri, R, m, nullptr, step, H, k, a.mode != MODE_H, a.mode >= MODE_DM1);
+    cell_field<T, UNIF, EXT>(a, x, y, z, i, ri, R, m, nullptr, step, H, k, a.mode != MODE_H, a.mode >= MODE_DM1);
     if (a.mode == MODE_H) {
         st3(a.out, N, i, H);
         return;
@@ -104,7 +104,7 @@ __device__ __forceinline__ void fset(float4& v, int q, float x) {
     if (q == 0) v.x = x; else if (q == 1) v.y = x; else if (q == 2) v.z = x; else v.w = x;
 }
 
-template <int V>
+template <int V, bool EXT>
 __global__ void __launch_bounds__(256) field_vec_kernel(FieldArgs<float> a) {
     using VT = typename fvec<V>::t;
     if (a.gate && !a.st->active) return;
@@ -119,7 +119,8 @@ __global__ void __launch_bounds__(256) field_vec_kernel(FieldArgs<float> a) {
     VT mc[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) mc[c] = ldv<V>(a.m + c * N + i0);
-    const bool need_nb = (a.terms & (MM_TERM_EXCHANGE | MM_TERM_DMI | MM_TERM_SURFACE)) || a.tq == MM_TORQUE_ZL;
+    const unsigned nbt = MM_TERM_EXCHANGE | MM_TERM_DMI | (EXT ? MM_TERM_SURFACE : 0u);
+    const bool need_nb = (a.terms & nbt) || a.tq == MM_TORQUE_ZL;
     // neighbour rows (y+, y-, z+, z-) as vectors, row-end x neighbours as scalars
     VT nr[4][3];
     bool rin[4] = {false, false, false, false};
@@ -176,9 +177,9 @@ __global__ void __launch_bounds__(256) field_vec_kernel(FieldArgs<float> a) {
             nbp[0] = pp;
             nbp[1] = pm;
             nbv[0] = q < V - 1 ? mk3<float>(fget(mc[0], q + 1), fget(mc[1], q + 1), fget(mc[2], q + 1))
-                               : (rinx ? mk3<float>(xr[0], xr[1], xr[2]) : ghost_value<float>(m, 0, 1, a.hx, R.ratio, R.ratio_b));
+                               : (rinx ? mk3<float>(xr[0], xr[1], xr[2]) : ghost_value<float, EXT>(m, 0, 1, a.hx, R.ratio, R.ratio_b));
             nbv[1] = q > 0 ? mk3<float>(fget(mc[0], q - 1), fget(mc[1], q - 1), fget(mc[2], q - 1))
-                           : (lin ? mk3<float>(xl[0], xl[1], xl[2]) : ghost_value<float>(m, 0, -1, a.hx, R.ratio, R.ratio_b));
+                           : (lin ? mk3<float>(xl[0], xl[1], xl[2]) : ghost_value<float, EXT>(m, 0, -1, a.hx, R.ratio, R.ratio_b));
             cnb[0] = pp ? a.c_uniform : R.cg;
             cnb[1] = pm ? a.c_uniform : R.cg;
 #pragma unroll
@@ -186,14 +187,14 @@ __global__ void __launch_bounds__(256) field_vec_kernel(FieldArgs<float> a) {
                 const int slot = 2 + s, d = 1 + s / 2, sg = (s & 1) ? -1 : 1;
                 nbp[slot] = rin[s];
                 nbv[slot] = rin[s] ? mk3<float>(fget(nr[s][0], q), fget(nr[s][1], q), fget(nr[s][2], q))
-                                   : ghost_value<float>(m, d, sg, d == 1 ? a.hy : a.hz, R.ratio, R.ratio_b);
+                                   : ghost_value<float, EXT>(m, d, sg, d == 1 ? a.hy : a.hz, R.ratio, R.ratio_b);
                 cnb[slot] = rin[s] ? a.c_uniform : R.cg;
             }
         }
         const v3<float> hq = dem ? mk3<float>(fget(hd[0], q), fget(hd[1], q), fget(hd[2], q)) : mk3<float>(0, 0, 0);
         v3<float> H, k;
-        cell_field_nb<float>(a, i0 + q, R, m, nbv, nbp, cnb, dem, hq, step, H, k, a.mode != MODE_H,
-                             a.mode >= MODE_DM1);
+        cell_field_nb<float, EXT>(a, i0 + q, R, m, nbv, nbp, cnb, dem, hq, step, H, k, a.mode != MODE_H,
+                                  a.mode >= MODE_DM1);
         v3<float> r1 = H, r2 = k;
         if (a.mode == MODE_K) r1 = k;
         else if (a.mode == MODE_HEUN1) {
@@ -308,13 +309,16 @@ static void field_launch_t(mm_ctx* c, int mode, unsigned terms, const T* m, cons
         if constexpr (sizeof(T) == 4) {
             if (g.nx % kFieldV == 0 && a.R0.present != 0.f) {
                 dim3 grdv((g.nx / kFieldV + 31) / 32, (g.ny + 7) / 8, g.nz);
-                field_vec_kernel<kFieldV><<<grdv, blk, 0, c->stream>>>(a);
+                if (c->ext_terms) field_vec_kernel<kFieldV, true><<<grdv, blk, 0, c->stream>>>(a);
+                else field_vec_kernel<kFieldV, false><<<grdv, blk, 0, c->stream>>>(a);
                 return;
             }
         }
-        field_kernel<T, true><<<grd, blk, 0, c->stream>>>(a);
+        if (c->ext_terms) field_kernel<T, true, true><<<grd, blk, 0, c->stream>>>(a);
+        else field_kernel<T, true, false><<<grd, blk, 0, c->stream>>>(a);
     } else {
-        field_kernel<T, false><<<grd, blk, 0, c->stream>>>(a);
+        if (c->ext_terms) field_kernel<T, false, true><<<grd, blk, 0, c->stream>>>(a);
+        else field_kernel<T, false, false><<<grd, blk, 0, c->stream>>>(a);
     }
 }
 

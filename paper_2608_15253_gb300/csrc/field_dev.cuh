@@ -138,7 +138,9 @@ __device__ __forceinline__ void st3(T* a, long long N, long long i, v3<T> v) {
 //         + gamma' mu0 [(h_DL + alpha h_FL) m x p + (h_FL - alpha h_DL) p]
 //         + [(1 + alpha xi) m x u' + (xi - alpha) u'] / (1 + alpha^2),
 // u' = (u.grad) m, so that Omega x m is the slope.
-template <typename T>
+// EXT = false compiles out bulk DMI and the further local terms (cubic,
+// surface, RKKY, magnetoelastic): the lean kernel for contexts without them.
+template <typename T, bool EXT = true>
 __device__ __forceinline__ void cell_field_nb(const FieldArgs<T>& a, long long i, const Region<T>& R,
                                               const v3<T>& m, const v3<T>* nbv, const bool* nbp, const T* cnb,
                                               bool use_hd, const v3<T>& hdv, long long step, v3<T>& H, v3<T>& k,
@@ -158,7 +160,7 @@ __device__ __forceinline__ void cell_field_nb(const FieldArgs<T>& a, long long i
         const v3<T> dx = gx * (nbv[0] - nbv[1]);
         const v3<T> dy = gy * (nbv[2] - nbv[3]);
         H = H + R.dmi * mk3<T>(dx.z, dy.z, -dx.x - dy.y);
-        if (R.dmib != (T)0) {
+        if (EXT && R.dmib != (T)0) {
             // bulk: H = -(2 Db / mu0 Ms) curl m
             const v3<T> dz = ((T)0.5 / a.hz) * (nbv[4] - nbv[5]);
             H = H + (-R.dmib) * mk3<T>(dy.z - dz.y, dz.x - dx.z, dx.y - dy.x);
@@ -172,7 +174,7 @@ __device__ __forceinline__ void cell_field_nb(const FieldArgs<T>& a, long long i
         if (a.Bc) H = H + ld3(a.Bc, N, i);
         else H = H + mk3<T>(a.hext[0], a.hext[1], a.hext[2]);
     }
-    if (a.terms & MM_TERM_CUBIC) {
+    if (EXT && (a.terms & MM_TERM_CUBIC)) {
         // -(1/mu0 Ms) dE/dm of Kc1 (a^2 b^2 + b^2 c^2 + c^2 a^2) + Kc2 a^2 b^2 c^2
         const v3<T> c1 = mk3<T>(R.c1x, R.c1y, R.c1z), c2 = mk3<T>(R.c2x, R.c2y, R.c2z);
         const v3<T> c3 = mk3<T>(R.c3x, R.c3y, R.c3z);
@@ -184,12 +186,12 @@ __device__ __forceinline__ void cell_field_nb(const FieldArgs<T>& a, long long i
         const T g3 = k1 * r * (p2 + q2) + k2 * p2 * q2 * r;
         H = H - (g1 * c1 + g2 * c2 + g3 * c3);
     }
-    if (a.terms & MM_TERM_SURFACE) {
+    if (EXT && (a.terms & MM_TERM_SURFACE)) {
         // (2 Ks / mu0 Ms dz) m_z z per free z face
         const T faces = (nbp[4] ? (T)0 : (T)1) + (nbp[5] ? (T)0 : (T)1);
         H.z += R.ks / a.hz * faces * m.z;
     }
-    if (a.terms & MM_TERM_RKKY) {
+    if (EXT && (a.terms & MM_TERM_RKKY)) {
         const long long plane = (long long)a.nx * a.ny;
         const int z = (int)(i / plane);
         if (z == a.rk1 || z == a.rk2) {
@@ -198,7 +200,7 @@ __device__ __forceinline__ void cell_field_nb(const FieldArgs<T>& a, long long i
             if (there) H = H + (a.rkky_c * R.inv_mu0Ms) * ld3(a.m, N, j);
         }
     }
-    if (a.terms & MM_TERM_MEL) {
+    if (EXT && (a.terms & MM_TERM_MEL)) {
         T e[6];
         if (a.strain_cell) {
 #pragma unroll
@@ -287,14 +289,15 @@ __device__ __forceinline__ v3<T> rodrigues(const v3<T>& m, const v3<T>& w, T dt)
 }
 
 // Ghost value of an absent neighbour in direction d (0 x, 1 y, 2 z) and
-// side sg (+1 / -1): m - h (D/2A) (z x n) x m with n = sg e_d.
-template <typename T>
+// side sg (+1 / -1): m - h (D/2A) (z x n) x m with n = sg e_d, plus (EXT)
+// the bulk-DMI part + h (Db/2A) n x m.
+template <typename T, bool EXT = true>
 __device__ __forceinline__ v3<T> ghost_value(const v3<T>& m, int d, int sg, T h, T ratio, T ratio_b) {
     v3<T> zn = mk3<T>(0, 0, 0);
     if (d == 0) zn = mk3<T>(sg * m.z, (T)0, -sg * m.x);
     else if (d == 1) zn = mk3<T>((T)0, sg * m.z, -sg * m.y);
     v3<T> g = m - (h * ratio) * zn;
-    if (ratio_b != (T)0) {
+    if (EXT && ratio_b != (T)0) {
         // bulk DMI: + h (Db/2A) n x m, n = sg e_d
         v3<T> nm;
         if (d == 0) nm = mk3<T>((T)0, -sg * m.z, sg * m.y);
@@ -310,12 +313,13 @@ __device__ __forceinline__ v3<T> ghost_value(const v3<T>& m, int d, int sg, T h,
 // rotation vector, see cell_field_nb).  UNIF: one material
 // everywhere (no region map): every in-grid neighbour is present and every
 // exchange pair uses the one coefficient a.c_uniform.
-template <typename T, bool UNIF = false>
+template <typename T, bool UNIF = false, bool EXT = true>
 __device__ __forceinline__ void cell_field(const FieldArgs<T>& a, int x, int y, int z, long long i, int ri,
                                            const Region<T>& R, const v3<T>& m, const v3<T>* hd, long long step,
                                            v3<T>& H, v3<T>& k, bool want_k, bool as_omega = false) {
     const long long N = a.N;
-    const bool need_nb = (a.terms & (MM_TERM_EXCHANGE | MM_TERM_DMI | MM_TERM_SURFACE)) || a.tq == MM_TORQUE_ZL;
+    const unsigned nbt = MM_TERM_EXCHANGE | MM_TERM_DMI | (EXT ? MM_TERM_SURFACE : 0u);
+    const bool need_nb = (a.terms & nbt) || a.tq == MM_TORQUE_ZL;
     // neighbour values (ghosts where absent) and raw presence (Zhang-Li,
     // the free faces of the surface term)
     v3<T> nbv[6];
@@ -353,13 +357,13 @@ __device__ __forceinline__ void cell_field(const FieldArgs<T>& a, int x, int y, 
                     nbv[slot] = ld3(a.m, N, j);
                     cnb[slot] = UNIF ? a.c_uniform : __ldg(&a.cpair[ri * a.nreg + rj]);
                 } else {
-                    nbv[slot] = ghost_value<T>(m, d, sg, hh[d], R.ratio, R.ratio_b);
+                    nbv[slot] = ghost_value<T, EXT>(m, d, sg, hh[d], R.ratio, R.ratio_b);
                     cnb[slot] = R.cg;
                 }
             }
         }
     }
-    cell_field_nb<T>(a, i, R, m, nbv, nbp, cnb, hd != nullptr, hd ? *hd : mk3<T>(0, 0, 0), step, H, k, want_k,
+    cell_field_nb<T, EXT>(a, i, R, m, nbv, nbp, cnb, hd != nullptr, hd ? *hd : mk3<T>(0, 0, 0), step, H, k, want_k,
                      as_omega);
 }
 

@@ -1,7 +1,9 @@
 """GPU parity of the batched trial engine (Results, "Replica batching"):
 one-cell replicas (the macrospin ensemble, one thread per slot with the
-moment in registers for blocks of steps), and retire/refill on one-cell and
-8 x 8 film replicas, against the oracle's trials run one by one.
+moment in registers for blocks of steps), small films without demag (one
+CTA per replica, state in shared memory), and retire/refill on one-cell and
+8 x 8 film replicas (with and without demag), against the oracle's trials
+run one by one.
 
 Bars: per-replica max |m_gpu - m_oracle| <= 1e-5 (FP32).  Trial outcomes:
 the step count and stop flag of every trial equal the oracle's, except
@@ -215,3 +217,70 @@ def test_trial_api_errors():
     with pytest.raises(mm.MMError):
         demag_cfg = mm.make_config(precision=32, integrator=mm.MM_DM, demag=mm.MM_DEMAG_EXACT, dt=1e-13)
         mm.mm_create_batch([G1, G1], M.s, demag_cfg, None)
+
+
+@pytest.mark.parametrize("integ", ["dm", "heun"])
+def test_small_films_without_demag_match_oracle(integ):
+    """Films of at most 1024 cells without demag run one CTA per replica with
+    the state in shared memory for blocks of steps: uneven sizes, interfacial
+    and bulk DMI, anisotropy, Zeeman, STT and the thermal field."""
+    mm = need_gpu()
+    from oracle.llg import Solver, Torque
+    sizes = [(8, 8), (16, 16), (32, 32), (17, 9), (5, 31), (1, 12)]
+    R = len(sizes)
+    cell = (2e-9, 2e-9, 1e-9)
+    mat = W.Material(Ms=1.1e6, A=2e-11, alpha=0.05, Ku1=9e5, u=(0, 0, 1), D=1.5e-3, Db=-1e-3)
+    M = mm.Material(mat.Ms, mat.A, mat.alpha, mat.Ku1, mat.u, mat.D, Db=mat.Db)
+    cfg = mm.make_config(precision=32, integrator=mm.MM_DM if integ == "dm" else mm.MM_HEUN,
+                         demag=mm.MM_DEMAG_OFF, dt=1e-14, terms=1 | 2 | 4 | 8 | 32)
+    seeds = (np.arange(R, dtype=np.uint64) + np.uint64(3)) * np.uint64(7919)
+    ctx = mm.mm_create_batch([mm.make_grid(nx, ny, 1, *cell) for nx, ny in sizes], M.s, cfg, seeds)
+    ctx._mat = M
+    T = np.linspace(50.0, 400.0, R)
+    J = np.linspace(-2e11, 3e11, R)
+    try:
+        mm.mm_set_field(ctx, 0, (0.01, 0.0, 0.02))
+        mm.mm_set_temperature(ctx, T)
+        mm.mm_set_torque(ctx, mm.make_torque(mm.MM_TORQUE_STT, p=(0, 0.3, 1), P=0.5, Lambda=1.4), J)
+        m0 = []
+        for r, (nx, ny) in enumerate(sizes):
+            m0.append(W.m_perp(W.Grid(nx, ny, 1, *cell), seed=300 + r, tilt=0.3))
+            mm.mm_set_m(ctx, r, m0[-1])
+        n = 40
+        mm.mm_step(ctx, n)
+        t, _, steps = mm.mm_get_time(ctx)
+        assert steps == n
+        for r, (nx, ny) in enumerate(sizes):
+            from gpu_util import oracle_problem
+            p = oracle_problem(W.Grid(nx, ny, 1, *cell), mat, (0.01, 0.0, 0.02))
+            o = Solver(p, m0[r], terms=("exchange", "dmi", "anisotropy", "zeeman"), T=T[r], seed=int(seeds[r]),
+                       dt=1e-14, torque=Torque(kind="stt", J=J[r], p=(0, 0.3, 1), P=0.5, Lambda=1.4))
+            for _ in range(n):
+                if integ == "dm":
+                    o.dm_step()
+                else:
+                    o.heun_step()
+            err = np.abs(mm.mm_get_m(ctx, r, m0[r].shape) - o.m).max()
+            assert err <= 1e-5, (r, sizes[r], err)
+    finally:
+        mm.mm_destroy(ctx)
+
+
+def test_retire_refill_small_films_without_demag():
+    """Retire/refill in the shared-memory film kernel: 12 trials over 4 slots
+    of 8 x 8 films with exchange, anisotropy, STT and 300 K."""
+    mm = need_gpu()
+    grid = W.Grid(8, 8, 1, D1, D1, D1)
+    mat = W.Material(Ms=1e6, A=1.5e-11, alpha=0.05, Ku1=1.1e6, u=(0, 0, 1))
+    n = 12
+    spec = _spec(grid, mat, ("exchange", "anisotropy", "zeeman"), np.linspace(5e11, 8e12, n),
+                 np.full(n, 300.0), 1e-13, 0.98, 300)
+    ctx = _context(mm, spec, 4, mm.MM_DM, 1 | 4 | 8 | 32, False)
+    try:
+        mm.mm_trials_start(ctx, spec.J, spec.T, spec.m_init, axis=spec.axis, threshold=spec.threshold,
+                           max_steps=spec.max_steps, base_seed=spec.base_seed, refill=True)
+        steps, stopped = _run_to_completion(mm, ctx, n, chunk=50)
+        assert stopped.any() and not stopped.all()
+        _compare_outcomes(spec, steps, stopped)
+    finally:
+        mm.mm_destroy(ctx)
