@@ -10,45 +10,24 @@
 // without writing H.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "ctx.h"
 #include "field_dev.cuh"
 
 namespace mm {
 
-// UNIF: one material (coefficients passed by value in the launch
-// parameters, no region map or coefficient-table loads).
-template <typename T, bool UNIF, bool EXT>
-__global__ void __launch_bounds__(256) field_kernel(FieldArgs<T> a) {
-    if (a.gate && !a.st->active) return;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= a.nx || y >= a.ny) return;
+// Output of one present cell for the launch's mode: H, the slope k (to
+// `out` or to the FSAL slot of stage kstage), the Heun / Depondt-Mertens
+// predictor (m*, with k or Omega to out2) or corrector (renormalised).
+template <typename T>
+__device__ __forceinline__ void cell_store(const FieldArgs<T>& a, long long i, const v3<T>& m, const v3<T>& H,
+                                           const v3<T>& k) {
     const long long N = a.N;
-    const long long i = ((long long)z * a.ny + y) * a.nx + x;
-    const int ri = UNIF ? 0 : (a.region ? a.region[i] : 0);
-    const Region<T>& R = UNIF ? a.R0 : a.lut[ri];
-    const v3<T> m = ld3(a.m, N, i);
-    if (R.present == (T)0) {
-        const v3<T> zero = mk3<T>(0, 0, 0);
-        T* o = a.out;
-        if (!o) {
-            const int kf = a.st->k_first;
-            o = a.kptr[a.kstage == 0 ? kf : 6 - kf];
-        }
-        if (a.mode == MODE_HEUN1 || a.mode == MODE_DM1) { st3(o, N, i, zero); st3(a.out2, N, i, zero); }
-        else st3(o, N, i, zero);
-        return;
-    }
-    const long long step = a.step_override >= 0 ? a.step_override : (a.st ? a.st->step : 0);
-    v3<T> H, k;
-    cell_field<T, UNIF, EXT>(a, x, y, z, i, ri, R, m, nullptr, step, H, k, a.mode != MODE_H, a.mode >= MODE_DM1);
     if (a.mode == MODE_H) {
         st3(a.out, N, i, H);
-        return;
-    }
-    if (a.mode == MODE_K) {
+    } else if (a.mode == MODE_K) {
         T* o = a.out;
         if (!o) {
             const int kf = a.st->k_first;
@@ -78,6 +57,37 @@ __global__ void __launch_bounds__(256) field_kernel(FieldArgs<T> a) {
         const T inv = (T)1 / sqrt(dot(mn, mn));
         st3(a.out, N, i, inv * mn);
     }
+}
+
+// UNIF: one material (coefficients passed by value in the launch
+// parameters, no region map or coefficient-table loads).
+template <typename T, bool UNIF, bool EXT>
+__global__ void __launch_bounds__(256) field_kernel(FieldArgs<T> a) {
+    if (a.gate && !a.st->active) return;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= a.nx || y >= a.ny) return;
+    const long long N = a.N;
+    const long long i = ((long long)z * a.ny + y) * a.nx + x;
+    const int ri = UNIF ? 0 : (a.region ? a.region[i] : 0);
+    const Region<T>& R = UNIF ? a.R0 : a.lut[ri];
+    const v3<T> m = ld3(a.m, N, i);
+    if (R.present == (T)0) {
+        const v3<T> zero = mk3<T>(0, 0, 0);
+        T* o = a.out;
+        if (!o) {
+            const int kf = a.st->k_first;
+            o = a.kptr[a.kstage == 0 ? kf : 6 - kf];
+        }
+        if (a.mode == MODE_HEUN1 || a.mode == MODE_DM1) { st3(o, N, i, zero); st3(a.out2, N, i, zero); }
+        else st3(o, N, i, zero);
+        return;
+    }
+    const long long step = a.step_override >= 0 ? a.step_override : (a.st ? a.st->step : 0);
+    v3<T> H, k;
+    cell_field<T, UNIF, EXT>(a, x, y, z, i, ri, R, m, nullptr, step, H, k, a.mode != MODE_H, a.mode >= MODE_DM1);
+    cell_store<T>(a, i, m, H, k);
 }
 
 // One material, FP32, nx a multiple of V (2 or 4): each thread owns V
