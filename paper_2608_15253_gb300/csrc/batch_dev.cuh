@@ -393,6 +393,12 @@ __global__ void __launch_bounds__(NT) batch_stage_kernel(BatchArgs a) {
     const long long step = a.st->step;
     const float dt = (float)a.st->dt;
     float2* S = a.scratch + blockIdx.x * a.scratch_stride;
+    // the launch parameters and the current replica's descriptor live in
+    // shared memory, so the non-inlined phases take them by reference
+    // without a private copy in every thread's local memory
+    __shared__ BatchArgs sa;
+    __shared__ RepDev srp;
+    if (threadIdx.x == 0) sa = a;
     __shared__ int s_w;
     for (;;) {
         // dynamic schedule: each CTA takes the next replica of the work order
@@ -402,16 +408,19 @@ __global__ void __launch_bounds__(NT) batch_stage_kernel(BatchArgs a) {
         __syncthreads();
         if (w >= a.R) break;
         const int idx = a.order[w];
-        const RepDev rp = a.rep[idx];
-        if (!rp.active) continue;   // uniform across the CTA
+        if (threadIdx.x == 0) srp = a.rep[idx];
+        __syncthreads();
+        const RepDev& rp = srp;
+        if (!rp.active) { __syncthreads(); continue; }   // uniform across the CTA
         const ClsDev& cd = a.cls[rp.cls];
         const int key = cd.Lh * 10000 + cd.Py;
         switch (key) {
-#define MM_B(lh, py) case lh * 10000 + py: replica_stage<lh, py, NT>(a, rp, idx, cd, S, sm, step, dt); break;
+#define MM_B(lh, py) case lh * 10000 + py: replica_stage<lh, py, NT>(sa, rp, idx, cd, S, sm, step, dt); break;
             MM_B(16, 32) MM_B(32, 64) MM_B(48, 96) MM_B(64, 128) MM_B(96, 192) MM_B(128, 256) MM_B(256, 512)
 #undef MM_B
-            default: replica_stage<0, 0, NT>(a, rp, idx, cd, S, sm, step, dt); break;
+            default: replica_stage<0, 0, NT>(sa, rp, idx, cd, S, sm, step, dt); break;
         }
+        __syncthreads();   // srp is rewritten for the next replica
     }
 }
 
