@@ -637,21 +637,29 @@ __device__ __forceinline__ void zconv_multiply(cplx<T> (&v)[L], const cplx<T>* s
     const T* K0 = K + j0 * kcs;
     const T* K1 = K + j1 * kcs;
     const T* K2 = K + j2 * kcs;
+    // kz and L - kz share the stored entries kzf (signs flip with sz): each
+    // tensor value is loaded once and used for both
 #pragma unroll
-    for (int i = 0; i < L; ++i) {
-        const int kz = bitrev_c(i, LOG);
-        const int kzf = kz <= L / 2 ? kz : L - kz;
-        const T sz = kz <= L / 2 ? (T)1 : (T)-1;
-        const T s0 = C == 0 ? (T)1 : C == 1 ? sy : sz;
-        const T s1 = C == 0 ? sy : C == 1 ? (T)1 : sy * sz;
-        const T s2 = C == 0 ? sz : C == 1 ? sy * sz : (T)1;
-        const T k0 = s0 * __ldg(K0 + kzf * kks);
-        const T k1 = s1 * __ldg(K1 + kzf * kks);
-        const T k2 = s2 * __ldg(K2 + kzf * kks);
-        const cplx<T> m0 = sm[(0 * L + i) * kZT + tx];
-        const cplx<T> m1 = sm[(1 * L + i) * kZT + tx];
-        const cplx<T> m2 = sm[(2 * L + i) * kZT + tx];
-        v[i] = mkc<T>(k0 * m0.x + k1 * m1.x + k2 * m2.x, k0 * m0.y + k1 * m1.y + k2 * m2.y);
+    for (int kzf = 0; kzf <= L / 2; ++kzf) {
+        const T a0 = __ldg(K0 + kzf * kks);
+        const T a1 = __ldg(K1 + kzf * kks);
+        const T a2 = __ldg(K2 + kzf * kks);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && (kzf == 0 || kzf == L / 2)) continue;
+            const int kz = h == 0 ? kzf : L - kzf;
+            const int i = bitrev_c(kz, LOG);             // register slot of kz (bit-reversed order)
+            const T sz = h == 0 ? (T)1 : (T)-1;
+            const T s0 = C == 0 ? (T)1 : C == 1 ? sy : sz;
+            const T s1 = C == 0 ? sy : C == 1 ? (T)1 : sy * sz;
+            const T s2 = C == 0 ? sz : C == 1 ? sy * sz : (T)1;
+            const T k0 = s0 * a0, k1 = s1 * a1, k2 = s2 * a2;
+            // the thread's own component is still in v[i]
+            const cplx<T> m0 = C == 0 ? v[i] : sm[(0 * L + i) * kZT + tx];
+            const cplx<T> m1 = C == 1 ? v[i] : sm[(1 * L + i) * kZT + tx];
+            const cplx<T> m2 = C == 2 ? v[i] : sm[(2 * L + i) * kZT + tx];
+            v[i] = mkc<T>(k0 * m0.x + k1 * m1.x + k2 * m2.x, k0 * m0.y + k1 * m1.y + k2 * m2.y);
+        }
     }
 }
 
