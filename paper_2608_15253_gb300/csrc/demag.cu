@@ -654,10 +654,9 @@ __device__ __forceinline__ void zconv_multiply(cplx<T> (&v)[L], const cplx<T>* s
             const T s1 = C == 0 ? sy : C == 1 ? (T)1 : sy * sz;
             const T s2 = C == 0 ? sz : C == 1 ? sy * sz : (T)1;
             const T k0 = s0 * a0, k1 = s1 * a1, k2 = s2 * a2;
-            // the thread's own component is still in v[i]
-            const cplx<T> m0 = C == 0 ? v[i] : sm[(0 * L + i) * kZT + tx];
-            const cplx<T> m1 = C == 1 ? v[i] : sm[(1 * L + i) * kZT + tx];
-            const cplx<T> m2 = C == 2 ? v[i] : sm[(2 * L + i) * kZT + tx];
+            const cplx<T> m0 = sm[(0 * L + i) * kZT + tx];
+            const cplx<T> m1 = sm[(1 * L + i) * kZT + tx];
+            const cplx<T> m2 = sm[(2 * L + i) * kZT + tx];
             v[i] = mkc<T>(k0 * m0.x + k1 * m1.x + k2 * m2.x, k0 * m0.y + k1 * m1.y + k2 * m2.y);
         }
     }
