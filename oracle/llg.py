@@ -295,6 +295,43 @@ class Solver:
         self.step += 1
         self.accepted += 1
 
+    def dm_adaptive_step(self):
+        """Methods, "Integrators": the Depondt-Mertens scheme, "optionally
+        adaptive".  Reading (the paper gives no controller): the predictor
+        m* (a first-order rotation) and the corrector m_{n+1} (second order)
+        form an embedded pair; err = max over cells |m_{n+1} - m*|; accept
+        when err <= rtol; dt_new = dt * clamp(0.9 (rtol/err)^(1/2), 0.2, 5),
+        capped at 1 right after a rejection; dt within [dt_min, dt_max].
+        T must be 0.  Returns the accepted dt."""
+        if self.T > 0:
+            raise ValueError("adaptive stepping with white noise is not defined")
+        while True:
+            dt = self.dt
+            w1 = self.omega(self.m)
+            m_star = rotate(self.m, w1, dt)
+            w2 = self.omega(m_star)
+            m_new = np.where(self.p.present, rotate(self.m, 0.5 * (w1 + w2), dt), 0.0)
+            d = m_new - np.where(self.p.present, m_star, 0.0)
+            err = float(np.sqrt(dot(d, d)).max()) if d.size else 0.0
+            fac = 0.9 * (self.rtol / err) ** 0.5 if err > 0 else 5.0
+            fac = min(max(fac, 0.2), 5.0)
+            if err <= self.rtol:
+                if self.last_rejected:
+                    fac = min(fac, 1.0)
+                self.m = m_new
+                self.t += dt
+                self.step += 1
+                self.accepted += 1
+                self.last_rejected = False
+                self.dt = min(dt * fac, self.dt_max)
+                return dt
+            self.rejected += 1
+            self.last_rejected = True
+            new_dt = dt * fac
+            if new_dt < self.dt_min:
+                raise FloatingPointError("Depondt-Mertens time step underflow")
+            self.dt = new_dt
+
     # -- Dormand-Prince -----------------------------------------------------
     def dopri_attempt(self, dt):
         """Returns (m5, err, k7) for one attempted step from self.m."""

@@ -269,3 +269,51 @@ def test_switching_needs_current_at_zero_temperature():
     out = [run_trial(spec, q)[:2] for q in range(3)]
     assert out[0] == (4000, False)
     assert out[1][1] and out[2][1] and out[2][0] < out[1][0]
+
+
+# -- adaptive variant -------------------------------------------------------------
+def test_adaptive_tracks_the_closed_form_and_its_tolerance():
+    """Damped precession in a constant field: every accepted step's embedded
+    error is below rtol, the trajectory error against the closed form falls
+    with rtol, and the step grows where the motion is slow (the end of the
+    relaxation) and shrinks after a rejection."""
+    from oracle.llg import rotate  # noqa: F401  (the step rotates)
+    alpha, H0 = 0.1, 5e5
+    p = _cell(alpha, B=(0, 0, MU0 * H0))
+    m0 = _m([math.sin(1.0) * math.cos(0.3), math.sin(1.0) * math.sin(0.3), math.cos(1.0)])
+    T = 60e-12
+    errs = []
+    for rtol in (1e-3, 1e-4, 1e-5):
+        s = Solver(p, m0, terms=("zeeman",), dt=1e-13, rtol=rtol, dt_max=1e-11)
+        dts = []
+        while s.t < T:
+            dts.append(s.dm_adaptive_step())
+        errs.append(np.abs(s.m[:, 0, 0, 0] - _damped_closed_form(s.t, alpha, H0, 1.0, 0.3)).max())
+        assert s.accepted == len(dts)
+    # the global error follows the tolerance: about rtol, a decade per decade
+    for e, rtol in zip(errs, (1e-3, 1e-4, 1e-5)):
+        assert e < 3 * rtol, errs
+    assert all(5 < errs[i] / errs[i + 1] < 20 for i in range(2)), errs
+
+
+def test_adaptive_rejects_an_oversized_step():
+    """A first step far above what rtol allows is rejected and retried
+    smaller; the accepted step then meets the tolerance."""
+    grid, p, m = _film(seed=4)
+    s = Solver(p, m, dt=5e-12, rtol=1e-5)
+    dt = s.dm_adaptive_step()
+    assert s.rejected >= 1 and dt < 5e-12
+    s2 = Solver(p, m)
+    w1 = s2.omega(s2.m)
+    from oracle.llg import rotate
+    ms = rotate(s2.m, w1, dt)
+    w2 = s2.omega(ms)
+    mn = rotate(s2.m, 0.5 * (w1 + w2), dt)
+    assert np.abs(mn - s.m).max() < 1e-15
+    assert np.sqrt(((mn - ms) ** 2).sum(axis=0)).max() <= 1e-5
+
+
+def test_adaptive_refuses_finite_temperature():
+    grid, p, m = _film()
+    with pytest.raises(ValueError):
+        Solver(p, m, T=300.0).dm_adaptive_step()
