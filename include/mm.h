@@ -65,7 +65,13 @@ typedef enum mm_status {
  * corrector rotates the step's initial m about the mean of Omega(m) and
  * Omega(predictor); one thermal draw serves both.  Rotations keep |m| = 1;
  * the corrector also rescales by 1/|m| (a round-off-level change). */
-enum mm_integrator { MM_HEUN = 0, MM_RK45 = 1, MM_RK4 = 2, MM_DM = 3 };
+enum mm_integrator { MM_HEUN = 0, MM_RK45 = 1, MM_RK4 = 2, MM_DM = 3, MM_DM_ADAPTIVE = 4 };
+/* MM_DM_ADAPTIVE (Methods: the Depondt-Mertens scheme, "optionally
+ * adaptive"; T = 0 only): the predictor m* (first order) and the corrector
+ * (second order) form an embedded pair, err = max over cells |m_new - m*|;
+ * accept when err <= rtol; dt *= clamp(0.9 (rtol/err)^(1/2), 0.2, 5), capped
+ * at 1 after a rejection, within [dt_min, dt_max]; the controller runs on
+ * the device like RK45's, and mm_step_dt replays a given step sequence. */
 enum mm_demag_mode { MM_DEMAG_OFF = 0, MM_DEMAG_EXACT = 1, MM_DEMAG_SURROGATE = 2 };
 
 /* Effective-field terms (bit mask). */
@@ -134,7 +140,7 @@ typedef struct mm_material {
 
 typedef struct mm_config {
     int precision;            /* 32 or 64: arithmetic of the state, fields, FFTs */
-    int integrator;           /* MM_HEUN, MM_RK45, MM_RK4 or MM_DM */
+    int integrator;           /* MM_HEUN, MM_RK45, MM_RK4, MM_DM or MM_DM_ADAPTIVE */
     int demag;                /* mm_demag_mode */
     unsigned terms;           /* mm_term mask of the effective field; 0 means all */
     double dt;                /* Heun / RK4 step; RK45 initial step (s) */
@@ -250,8 +256,9 @@ MM_API mm_status mm_set_torque(mm_ctx* ctx, const mm_torque* tq, const double* J
  * are retried on the device; the step controller runs on the device). */
 MM_API mm_status mm_step(mm_ctx* ctx, long n);
 
-/* RK45 with a prescribed step sequence (no control, every step accepted):
- * replays dts[0..n-1], e.g. the accepted steps of a reference run. */
+/* RK45 or adaptive Depondt-Mertens with a prescribed step sequence (no
+ * control, every step accepted): replays dts[0..n-1], e.g. the accepted
+ * steps of a reference run. */
 MM_API mm_status mm_step_dt(mm_ctx* ctx, const double* dts, long n);
 
 /* Advance to simulated time t_end; the last step is clipped to land on it. */

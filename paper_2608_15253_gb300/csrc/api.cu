@@ -356,8 +356,10 @@ mm_status mm_create(const mm_grid* grid, const mm_material* mat, const mm_config
         return set_error(nullptr, MM_ERR_ARG, "grid sizes and cell edges must be positive");
     if (cfg->precision != 32 && cfg->precision != 64) return set_error(nullptr, MM_ERR_ARG, "precision must be 32 or 64");
     if (cfg->integrator != MM_HEUN && cfg->integrator != MM_RK45 && cfg->integrator != MM_RK4 &&
-        cfg->integrator != MM_DM)
+        cfg->integrator != MM_DM && cfg->integrator != MM_DM_ADAPTIVE)
         return set_error(nullptr, MM_ERR_ARG, "bad integrator");
+    if (cfg->integrator == MM_DM_ADAPTIVE && cfg->T > 0)
+        return set_error(nullptr, MM_ERR_ARG, "adaptive Depondt-Mertens with T > 0: use the fixed-step scheme");
     if (cfg->integrator == MM_RK45 && cfg->T > 0)
         return set_error(nullptr, MM_ERR_ARG, "RK45 with T > 0: adaptive stepping of white noise is not defined; use Heun");
     if (cfg->integrator == MM_RK4 && cfg->T > 0)
@@ -396,7 +398,7 @@ mm_status mm_create(const mm_grid* grid, const mm_material* mat, const mm_config
     TRY(alloc(c, &c->d_m, vb, "state"));
     TRY(alloc(c, &c->d_mtmp, vb, "stage state"));
     TRY(alloc(c, &c->d_hbuf, vb, "field scratch"));
-    const int nk = c->integrator == MM_RK45 ? 7 : c->integrator == MM_RK4 ? 4 : 1;
+    const int nk = c->integrator == MM_RK45 ? 7 : c->integrator == MM_RK4 ? 4 : c->integrator == MM_DM_ADAPTIVE ? 2 : 1;
     for (int q = 0; q < nk; ++q) TRY(alloc(c, &c->d_k[q], vb, "slopes"));
     TRY(alloc(c, &c->d_kslot, sizeof(void*) * 7, "slot table"));
     cudaMemcpy(c->d_kslot, c->d_k, sizeof(void*) * 7, cudaMemcpyHostToDevice);
@@ -429,6 +431,8 @@ mm_status mm_create(const mm_grid* grid, const mm_material* mat, const mm_config
     st.dt_max = cfg->dt_max > 0 ? cfg->dt_max : 1e-11;
     st.t_end = std::numeric_limits<double>::infinity();
     st.k_first = 0;
+    st.fsal = c->integrator == MM_RK45 ? 1 : 0;
+    st.ctrl_exp = c->integrator == MM_DM_ADAPTIVE ? 0.5 : 0.2;
     TRY(push_state(c));
     TRY(cuda_check(c, cudaDeviceSynchronize(), "create"));
 #undef TRY
@@ -530,6 +534,8 @@ mm_status mm_create_batch(int R, const mm_grid* grids, const mm_material* mat, c
     st.dt_min = 1e-20;
     st.dt_max = 1e-11;
     st.t_end = std::numeric_limits<double>::infinity();
+    st.fsal = 0;
+    st.ctrl_exp = 0.2;
     TRY(push_state(c));
     TRY(cuda_check(c, cudaDeviceSynchronize(), "create batch"));
 #undef TRY
@@ -786,6 +792,7 @@ static void launch_attempts(mm_ctx* c, int n) {
         else if (c->integrator == MM_RK45) rk45_attempt(c);
         else if (c->integrator == MM_RK4) rk4_step(c);
         else if (c->integrator == MM_DM) dm_step(c);
+        else if (c->integrator == MM_DM_ADAPTIVE) dm_adaptive_attempt(c);
         else heun_step(c);
     }
 }
@@ -895,7 +902,8 @@ static mm_status advance(mm_ctx* c, long long add_steps, double t_end, int repla
     if (s != MM_OK) return s;
     s = ensure_k1(c);
     if (s != MM_OK) return s;
-    const bool heun = c->integrator != MM_RK45;   // fixed-step schemes: every attempt is accepted
+    // fixed-step schemes: every attempt is accepted
+    const bool heun = c->integrator != MM_RK45 && c->integrator != MM_DM_ADAPTIVE;
     if (c->batch && batch_is_fused(c->batch)) {
         // one-cell replicas: blocks of fused steps, no graph needed
         long long want = add_steps >= 0 ? add_steps
@@ -972,7 +980,8 @@ mm_status mm_step(mm_ctx* c, long n) {
 
 mm_status mm_step_dt(mm_ctx* c, const double* dts, long n) {
     if (!c || (!dts && n > 0) || n < 0) return MM_ERR_ARG;
-    if (c->integrator != MM_RK45) return set_error(c, MM_ERR_STATE, "mm_step_dt replays RK45 steps only");
+    if (c->integrator != MM_RK45 && c->integrator != MM_DM_ADAPTIVE)
+        return set_error(c, MM_ERR_STATE, "mm_step_dt replays RK45 or adaptive Depondt-Mertens steps");
     if (n == 0) return MM_OK;
     if ((size_t)n > c->replay_cap) {
         cudaFree(c->d_replay);

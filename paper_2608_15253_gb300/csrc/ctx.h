@@ -60,6 +60,8 @@ struct DevState {
     int replay;                 // 1: take dt from replay_dts, always accept
     int status;                 // mm_status raised on the device (sticky)
     int k_first;                // slot index holding k1 (FSAL rotation: 0 or 6)
+    int fsal;                   // 1: RK45 (k7 becomes k1 on accept)
+    double ctrl_exp;            // step-size exponent: 1/5 (RK45), 1/2 (adaptive Depondt-Mertens)
     long long accepted, rejected, attempts, step;
     long long target;           // stop after this many accepted steps
     long long replay_n;
@@ -259,7 +261,8 @@ void heun_batch_advance(mm_ctx* c);
 void rk45_first_slope(mm_ctx* c);          // k1 = f(m0) into the FSAL slot
 void rk45_attempt(mm_ctx* c);               // one attempted DOPRI5 step
 void heun_step(mm_ctx* c);
-void dm_step(mm_ctx* c);                  // one Heun step
+void dm_step(mm_ctx* c);
+void dm_adaptive_attempt(mm_ctx* c);                  // one Heun step
 void rk4_step(mm_ctx* c);                   // one classical RK4 step
 
 // reduce.cu

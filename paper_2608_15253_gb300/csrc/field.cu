@@ -20,7 +20,8 @@ namespace mm {
 
 // Output of one present cell for the launch's mode: H, the slope k (to
 // `out` or to the FSAL slot of stage kstage), the Heun / Depondt-Mertens
-// predictor (m*, with k or Omega to out2) or corrector (renormalised).
+// predictor (m*, with k or Omega to out2) or corrector (renormalised); the
+// step is the attempt's dt_eff (the fixed dt for the fixed-step schemes).
 template <typename T>
 __device__ __forceinline__ void cell_store(const FieldArgs<T>& a, long long i, const v3<T>& m, const v3<T>& H,
                                            const v3<T>& k) {
@@ -35,22 +36,22 @@ __device__ __forceinline__ void cell_store(const FieldArgs<T>& a, long long i, c
         }
         st3(o, N, i, k);
     } else if (a.mode == MODE_HEUN1) {
-        const T dt = (T)a.st->dt;
+        const T dt = (T)a.st->dt_eff;
         st3(a.out2, N, i, k);
         st3(a.out, N, i, m + dt * k);
     } else if (a.mode == MODE_HEUN2) {  // m_new = normalise(m0 + dt/2 (k1 + k2))
-        const T dt = (T)a.st->dt;
+        const T dt = (T)a.st->dt_eff;
         const v3<T> m0 = ld3(a.m0, N, i);
         const v3<T> k1 = ld3(a.k1, N, i);
         v3<T> mn = m0 + ((T)0.5 * dt) * (k1 + k);
         const T inv = (T)1 / sqrt(dot(mn, mn));
         st3(a.out, N, i, inv * mn);
     } else if (a.mode == MODE_DM1) {   // Omega_1 and m* = R(Omega_1 dt) m
-        const T dt = (T)a.st->dt;
+        const T dt = (T)a.st->dt_eff;
         st3(a.out2, N, i, k);
         st3(a.out, N, i, rodrigues<T>(m, k, dt));
     } else {  // MODE_DM2: m_new = R((Omega_1 + Omega_2) dt / 2) m0
-        const T dt = (T)a.st->dt;
+        const T dt = (T)a.st->dt_eff;
         const v3<T> m0 = ld3(a.m0, N, i);
         const v3<T> w1 = ld3(a.k1, N, i);
         const v3<T> mn = rodrigues<T>(m0, (T)0.5 * (w1 + k), dt);
@@ -208,24 +209,24 @@ __global__ void __launch_bounds__(256) field_vec_kernel(FieldArgs<float> a) {
         v3<float> r1 = H, r2 = k;
         if (a.mode == MODE_K) r1 = k;
         else if (a.mode == MODE_HEUN1) {
-            const float dt = (float)a.st->dt;
+            const float dt = (float)a.st->dt_eff;
             r1 = m + dt * k;
             r2 = k;
         } else if (a.mode == MODE_HEUN2) {
-            const float dt = (float)a.st->dt;
+            const float dt = (float)a.st->dt_eff;
             const long long i = i0 + q;
             const v3<float> m0 = ld3(a.m0, N, i);
             const v3<float> k1 = ld3(a.k1, N, i);
             v3<float> mn = m0 + (0.5f * dt) * (k1 + k);
             r1 = (1.0f / sqrtf(dot(mn, mn))) * mn;
         } else if (a.mode == MODE_DM1) {
-            r1 = rodrigues<float>(m, k, (float)a.st->dt);
+            r1 = rodrigues<float>(m, k, (float)a.st->dt_eff);
             r2 = k;
         } else if (a.mode == MODE_DM2) {
             const long long i = i0 + q;
             const v3<float> m0 = ld3(a.m0, N, i);
             const v3<float> w1 = ld3(a.k1, N, i);
-            const v3<float> mn = rodrigues<float>(m0, 0.5f * (w1 + k), (float)a.st->dt);
+            const v3<float> mn = rodrigues<float>(m0, 0.5f * (w1 + k), (float)a.st->dt_eff);
             r1 = (1.0f / sqrtf(dot(mn, mn))) * mn;
         }
         fset(o1[0], q, r1.x); fset(o1[1], q, r1.y); fset(o1[2], q, r1.z);

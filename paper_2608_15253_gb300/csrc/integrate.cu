@@ -157,7 +157,7 @@ __global__ void controller_kernel(DevState* st, int prec) {
     if (st->replay) {
         st->accept = 1;
     } else {
-        double fac = err > 0.0 ? 0.9 * pow(st->rtol / err, 0.2) : 5.0;
+        double fac = err > 0.0 ? 0.9 * pow(st->rtol / err, st->ctrl_exp) : 5.0;
         if (!(fac == fac)) fac = 0.2;
         fac = fmin(fmax(fac, 0.2), 5.0);
         if (err <= st->rtol) {
@@ -181,7 +181,7 @@ __global__ void controller_kernel(DevState* st, int prec) {
         st->t += dt;
         st->accepted += 1;
         st->step += 1;
-        st->k_first = 6 - st->k_first;   // FSAL: k7 becomes k1
+        if (st->fsal) st->k_first = 6 - st->k_first;   // FSAL: k7 becomes k1
     }
 }
 
@@ -406,6 +406,68 @@ void dm_step(mm_ctx* c) {
                  -1, 1, 0);
     LaunchScope ls(c, "dm_advance", 0.0);
     heun_advance_kernel<<<1, 1, 0, c->stream>>>(c->d_state);
+}
+
+// Adaptive Depondt-Mertens: err = max over cells |cand - m*| (the corrector
+// against the first-order predictor), block max, atomic max into st->err(_f).
+template <typename T>
+__global__ void dm_error_kernel(DevState* st, const T* __restrict__ cand, const T* __restrict__ mstar, long long N) {
+    if (!st->active) return;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    T e2 = 0;
+    if (i < N) {
+        const T dx = cand[i] - mstar[i], dy = cand[N + i] - mstar[N + i], dz = cand[2 * N + i] - mstar[2 * N + i];
+        e2 = sqrt(dx * dx + dy * dy + dz * dz);
+        if (!(e2 == e2)) e2 = (T)INFINITY;
+    }
+    T bm = warp_max(e2);
+    __shared__ T red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bm;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        T v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : (T)0;
+        v = warp_max(v);
+        if (threadIdx.x == 0) {
+            if (sizeof(T) == 4) atomic_max_nonneg(&st->err_f, (float)v);
+            else atomic_max_nonneg(&st->err, (double)v);
+        }
+    }
+}
+
+// One attempted adaptive step: begin (dt_eff, active, error cleared),
+// predictor (Omega_1 -> k[0], m* -> mtmp), corrector into the candidate
+// buffer k[1], the embedded error, the device controller, and the accept copy.
+template <typename T>
+static void dm_adaptive_attempt_t(mm_ctx* c) {
+    const unsigned terms = c->terms;
+    const bool demag = c->dm.on && (terms & MM_TERM_DEMAG);
+    const long long N = c->N;
+    const unsigned tb = 256, nb = (unsigned)((N + tb - 1) / tb);
+    {
+        LaunchScope ls(c, "dm_begin", 0.0);
+        attempt_begin_kernel<<<1, 1, 0, c->stream>>>(c->d_state);
+    }
+    if (demag) demag_apply(c, c->d_m, c->d_hd);
+    field_launch(c, MODE_DM1, terms, c->d_m, demag ? c->d_hd : nullptr, c->d_mtmp, c->d_k[0], nullptr, nullptr,
+                 -1, 1, 0);
+    if (demag) demag_apply(c, c->d_mtmp, c->d_hd);
+    field_launch(c, MODE_DM2, terms, c->d_mtmp, demag ? c->d_hd : nullptr, c->d_k[1], nullptr, c->d_m, c->d_k[0],
+                 -1, 1, 0);
+    {
+        LaunchScope ls(c, "dm_error", (double)sizeof(T) * 6 * N);
+        dm_error_kernel<T><<<nb, tb, 0, c->stream>>>(c->d_state, (const T*)c->d_k[1], (const T*)c->d_mtmp, N);
+    }
+    {
+        LaunchScope ls(c, "dm_control", 0.0);
+        controller_kernel<<<1, 1, 0, c->stream>>>(c->d_state, c->prec);
+    }
+    LaunchScope ls(c, "dm_accept", (double)sizeof(T) * 6 * N);
+    accept_kernel<T><<<nb, tb, 0, c->stream>>>(c->d_state, (const T*)c->d_k[1], (T*)c->d_m, N);
+}
+
+void dm_adaptive_attempt(mm_ctx* c) {
+    if (c->prec == 32) dm_adaptive_attempt_t<float>(c);
+    else dm_adaptive_attempt_t<double>(c);
 }
 
 }  // namespace mm

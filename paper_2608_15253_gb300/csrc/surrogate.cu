@@ -144,6 +144,8 @@ static mm_status ensure_surrogate(mm_ctx* c) {
         return set_error(c, MM_ERR_STATE, "the surrogate needs a single-instance FP32 nz = 1 context with exact demag");
     if (c->grid.pbc[0] || c->grid.pbc[1] || c->grid.pbc[2])
         return set_error(c, MM_ERR_STATE, "the surrogate's exact near field is open-boundary: no periodic axes");
+    if (c->integrator != MM_RK45)
+        return set_error(c, MM_ERR_STATE, "the surrogate steps with the RK45 integrator");
     SurrogateHost* s = new SurrogateHost();
     int o = 0;
     for (int l = 0; l < 4; ++l) {

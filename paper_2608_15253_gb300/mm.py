@@ -21,7 +21,7 @@ _lock = threading.Lock()
 
 MM_OK, MM_ERR_ARG, MM_ERR_DEVICE, MM_ERR_OOM, MM_ERR_CUDA = 0, 1, 2, 3, 4
 MM_ERR_NONFINITE, MM_ERR_DT_UNDERFLOW, MM_ERR_TIMEOUT, MM_ERR_STATE = 5, 6, 7, 8
-MM_HEUN, MM_RK45, MM_RK4, MM_DM = 0, 1, 2, 3
+MM_HEUN, MM_RK45, MM_RK4, MM_DM, MM_DM_ADAPTIVE = 0, 1, 2, 3, 4
 MM_DEMAG_OFF, MM_DEMAG_EXACT, MM_DEMAG_SURROGATE = 0, 1, 2
 MM_TERM_EXCHANGE, MM_TERM_DMI, MM_TERM_ANISOTROPY = 1, 2, 4
 MM_TERM_ZEEMAN, MM_TERM_DEMAG, MM_TERM_THERMAL = 8, 16, 32

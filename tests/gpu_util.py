@@ -20,7 +20,8 @@ def need_gpu():
 
 def make_ctx(mm, grid: W.Grid, mat: W.Material, precision=64, integrator=None, demag=True, terms=0,
              dt=1e-14, rtol=1e-6, T=0.0, seed=0, B=(0.0, 0.0, 0.0), B_cell=None):
-    integ = {None: mm.MM_RK45, "rk45": mm.MM_RK45, "rk4": mm.MM_RK4, "heun": mm.MM_HEUN, "dm": mm.MM_DM}[integrator]
+    integ = {None: mm.MM_RK45, "rk45": mm.MM_RK45, "rk4": mm.MM_RK4, "heun": mm.MM_HEUN, "dm": mm.MM_DM,
+             "dma": mm.MM_DM_ADAPTIVE}[integrator]
     g = mm.make_grid(grid.nx, grid.ny, grid.nz, grid.dx, grid.dy, grid.dz, grid.pbc)
     m = mm.Material(mat.Ms, mat.A, mat.alpha, mat.Ku1, mat.u, mat.D, cells=mat.cell, Db=mat.Db, Kc1=mat.Kc1,
                     Kc2=mat.Kc2, c1=mat.c1, c2=mat.c2, Ks=mat.Ks, B1=mat.B1, B2=mat.B2)

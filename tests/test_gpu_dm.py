@@ -172,3 +172,61 @@ def test_batched_dm_matches_oracle(demag):
             assert err <= 1e-5, (r, sizes[r], err)
     finally:
         mm.mm_destroy(ctx)
+
+
+# -- adaptive variant -------------------------------------------------------------
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("ci", range(len(CASES)))
+def test_adaptive_dm_replay_matches_oracle(prec, ci):
+    """The oracle's accepted adaptive steps replayed on the GPU (mm_step_dt):
+    same trajectory within the bars."""
+    mm = need_gpu()
+    name, grid, mat, B = CASES[ci]
+    m0 = W.random_m(grid, seed=80 + ci)
+    o = _oracle(grid, mat, m0, B, dt=1e-14, rtol=1e-5)
+    dts = [o.dm_adaptive_step() for _ in range(25)]
+    ctx = make_ctx(mm, grid, mat, precision=prec, integrator="dma", demag=True, B=B, dt=1e-14, rtol=1e-5)
+    try:
+        mm.mm_set_m(ctx, 0, m0)
+        mm.mm_step_dt(ctx, dts)
+        err = np.abs(mm.mm_get_m(ctx, 0, m0.shape) - o.m).max()
+        assert err <= (1e-11 if prec == 64 else 1e-5), err
+    finally:
+        mm.mm_destroy(ctx)
+
+
+def test_adaptive_dm_controller_follows_oracle_fp64():
+    """FP64: the device controller takes the oracle's accept/reject decisions
+    and step sizes (a rejection included: the first step is oversized)."""
+    mm = need_gpu()
+    name, grid, mat, B = CASES[0]
+    m0 = W.random_m(grid, seed=90)
+    o = _oracle(grid, mat, m0, B, dt=2e-12, rtol=1e-5)
+    for _ in range(20):
+        o.dm_adaptive_step()
+    assert o.rejected >= 1
+    ctx = make_ctx(mm, grid, mat, precision=64, integrator="dma", demag=True, B=B, dt=2e-12, rtol=1e-5)
+    try:
+        mm.mm_set_m(ctx, 0, m0)
+        mm.mm_step(ctx, 20)
+        st = mm.mm_get_stats(ctx)
+        assert st["accepted"] == 20 and st["rejected"] == o.rejected
+        assert abs(st["t"] - o.t) < 1e-9 * o.t and abs(st["dt"] - o.dt) < 1e-9 * o.dt
+        assert np.abs(mm.mm_get_m(ctx, 0, m0.shape) - o.m).max() <= 1e-11
+    finally:
+        mm.mm_destroy(ctx)
+
+
+def test_adaptive_dm_run_lands_on_t_end():
+    mm = need_gpu()
+    name, grid, mat, B = CASES[2]
+    ctx = make_ctx(mm, grid, mat, precision=32, integrator="dma", demag=True, B=B, dt=1e-13, rtol=1e-5)
+    try:
+        mm.mm_set_m(ctx, 0, W.random_m(grid, seed=91))
+        mm.mm_run(ctx, 3.3e-12)
+        t, _, _ = mm.mm_get_time(ctx)
+        assert abs(t - 3.3e-12) < 1e-24
+        with pytest.raises(mm.MMError):
+            make_ctx(mm, grid, mat, precision=32, integrator="dma", demag=False, T=300.0)
+    finally:
+        mm.mm_destroy(ctx)
