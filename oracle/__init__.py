@@ -2,10 +2,13 @@
 
 A plain, slow FP64 CPU implementation of the micromagnetic hot path of
 arxiv 2608.15253 ("Claude-SpinDynamics"): finite-difference effective field
-(exchange, interfacial DMI, uniaxial anisotropy, Zeeman, Philox thermal
-field, Newell-tensor FFT demagnetisation), the LLG right-hand side with
-spin-orbit / Slonczewski / Zhang-Li torques, Heun and Dormand-Prince RK45
-steps with |m| renormalisation, energy and topological charge.
+(exchange, interfacial and bulk DMI, uniaxial, cubic and surface
+anisotropy, Zeeman, RKKY interlayer exchange, magnetoelastic field, Philox
+thermal field, open and periodic (image-sum) Newell-tensor FFT
+demagnetisation), the LLG right-hand side with spin-orbit / Slonczewski /
+Zhang-Li torques, Heun, Dormand-Prince RK45, classical RK4 and the
+Depondt-Mertens rotation scheme (fixed and adaptive), ensembles of trials
+with retire/refill (``oracle.trials``), energy and topological charge.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
 and reference legs may import it.  It shares no code with the CUDA path
@@ -23,16 +26,16 @@ approximation with no closed form).
 """
 from .constants import MU0, GAMMA0, KB, HBAR, QE, MU_B  # noqa: F401
 from .fields import (  # noqa: F401
-    Problem, h_exchange, h_dmi, h_anisotropy, h_zeeman, h_local, h_eff,
-    neighbour_values,
+    Problem, h_exchange, h_dmi, h_dmi_bulk, h_anisotropy, h_zeeman, h_cubic, h_surface, h_rkky,
+    h_magnetoelastic, h_local, h_eff, neighbour_values,
 )
 from .demag import (  # noqa: F401
     newell_octant, newell_at, newell_analytic, newell_quadrature, newell_f, newell_g,
-    padded_kernel, demag_spectrum, h_demag, h_demag_direct,
+    newell_octant_images, padded_kernel, demag_spectrum, h_demag, h_demag_direct,
 )
 from .philox import philox4x32_10, splitmix64, uniforms, normals, thermal_field  # noqa: F401
 from .llg import (  # noqa: F401
-    Torque, llg_rhs, spin_torque, zhang_li_torque, Solver,
+    Torque, llg_rhs, spin_torque, zhang_li_torque, rotate, Solver,
     DP_A, DP_B5, DP_B4, DP_C,
 )
 from .observables import energy, topological_charge, topological_charge_bl  # noqa: F401
