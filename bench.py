@@ -281,7 +281,8 @@ def variant_batched(mm, stream, steps):
     return {"workload": "1024 perpendicular free layers, sizes {32,48,64,96,128}^2 x 1 of 2x2x1 nm, T=300 K, "
                         "damping-like SOT J in [1e11,3e11] A/m^2, exact demag, FP32 Heun dt=1e-14 s",
             "value": cells * n_acc / (ms * 1e-3), "unit": UNIT, "cells": cells, "replicas": R,
-            "steps": n_acc, "ms_per_step": ms / max(1, n_acc), "launch_shape": {"threads": nt, "ctas": blocks},
+            "steps": n_acc, "ms_per_step": ms / max(1, n_acc),
+            "launch_shape": {"threads": nt, "ctas": blocks, "stacked": nt == 0},
             "autotune_s": round(t_tune, 2),
             "error_vs_fp64": {"max_abs_dm": max(errs), "after_steps": n_total, "replicas_checked": checks,
                               "against": "FP64 single-instance GPU runs with the same Philox key"}}
@@ -318,6 +319,7 @@ def variant_batching_table(mm, stream, steps=2048):
                              np.full(R, 1e12))
         for r in range(R):
             mm.mm_set_m(ctx, r, W.m_perp(W.Grid(nx, ny, 1, 4e-9, 4e-9, 4e-9), seed=r, tilt=0.1))
+        shape = mm.mm_batch_autotune(ctx, None) if demag else None
         mm.mm_step(ctx, 64)
         ms = _timed(stream, lambda: mm.mm_step(ctx, steps))
         per = R * (nx * ny if unit == "cell-steps/s" else 1)
@@ -325,7 +327,9 @@ def variant_batching_table(mm, stream, steps=2048):
         st = mm.mm_get_stats(ctx)
         out.append({"row": name, "grid": [nx, ny, 1], "R": R, "value": value, "unit": unit,
                     "paper_value": paper, "ratio_vs_paper": value / paper, "steps": steps,
-                    "ms_per_step": ms / steps, "kernel_launches_total": st["kernel_launches"]})
+                    "ms_per_step": ms / steps, "kernel_launches_total": st["kernel_launches"],
+                    "launch_shape": None if shape is None else {"threads": shape[0], "ctas": shape[1],
+                                                                "stacked": shape[0] == 0}})
         mm.mm_destroy(ctx)
     return {"integrator": "Depondt-Mertens (MM_DM), FP32", "rows": out,
             "paper_hardware": "RTX 5060 Ti (the paper's); this run: one GB300"}

@@ -223,8 +223,11 @@ MM_API mm_status mm_set_m(mm_ctx* ctx, int replica, const double* m);
 MM_API mm_status mm_get_m(mm_ctx* ctx, int replica, double* m);
 
 /* Device-pointer variants over all replicas at once, in the context's
- * precision (float or double), concatenated replica-outermost.  Ordered on
- * the context stream; no host synchronisation. */
+ * precision (float or double), concatenated replica-outermost in storage
+ * order: replicas of one grid size are stored together (sizes in order of
+ * first appearance, replicas by index within a size), which is replica
+ * order when the replicas come grouped by size.  Ordered on the context
+ * stream; no host synchronisation. */
 MM_API mm_status mm_set_m_device(mm_ctx* ctx, const void* m_dev);
 MM_API mm_status mm_get_m_device(mm_ctx* ctx, void* m_dev);
 
@@ -336,13 +339,23 @@ MM_API mm_status mm_trials_start(mm_ctx* ctx, const mm_trials* spec);
 MM_API mm_status mm_trials_result(mm_ctx* ctx, long long* steps, int* stopped, long long* done);
 
 /* Launch-shape autotuner of a replica-batched context (Methods, "Replica
- * batching": one persistent launch per stage).  Times a few steps for
- * every candidate (threads per CTA x resident CTAs per SM), keeps the
- * fastest and restores the state (m, t, step counters) afterwards.  When
+ * batching").  Candidates: one persistent launch per stage (threads per CTA
+ * x resident CTAs per SM), and the stacked shape (*nt_out = *blocks_out =
+ * 0): per size class, the 2-D demag passes and the field + stage kernel
+ * over all of the class's replicas at once (not used with retire/refill).
+ * Times a few steps for every candidate, keeps the fastest and restores
+ * the state (m, t, step counters) afterwards.  When
  * cache_path is non-NULL the choice is read from / appended to that JSON
  * file, keyed by the replica-size histogram.  nt_out / blocks_out may be
  * NULL.  MM_ERR_STATE for single-instance contexts. */
 MM_API mm_status mm_batch_autotune(mm_ctx* ctx, const char* cache_path, int* nt_out, int* blocks_out);
+
+/* Set the launch shape of a replica-batched context directly: nt = 256 or
+ * 512 threads per CTA with `blocks` persistent CTAs (1 <= blocks), or
+ * nt = 0 for the stacked shape (blocks ignored).  Errors: MM_ERR_STATE
+ * (single-instance context), MM_ERR_ARG (other values), MM_ERR_OOM (the
+ * stacked shape's per-class buffers). */
+MM_API mm_status mm_batch_set_shape(mm_ctx* ctx, int nt, int blocks);
 
 /* Topological charge without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that may not allocate

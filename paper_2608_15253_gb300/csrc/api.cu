@@ -485,18 +485,36 @@ mm_status mm_create_batch(int R, const mm_grid* grids, const mm_material* mat, c
     c->R = R;
     c->grid = grids[0];
     c->Tr = cfg->T;
-    long long off = 0, maxN = 0;
+    // storage: replicas of one grid size together (sizes in order of first
+    // appearance, replicas by index within a size), so that each size class
+    // is one contiguous block [replica][component][y][x]
+    // each size class starts on a 16-byte boundary (the FFT passes load
+    // rows as float2 / float4 vectors); the device-layout calls skip the gaps
+    long long off = 0, packed = 0, maxN = 0;
+    c->roff.assign(R, 0);
+    c->sblocks.clear();
+    std::vector<char> placed(R, 0);
+    for (int r = 0; r < R; ++r) {
+        if (placed[r]) continue;
+        off = (off + 3) / 4 * 4;
+        const long long start = off;
+        for (int q = r; q < R; ++q) {
+            if (placed[q] || grids[q].nx != grids[r].nx || grids[q].ny != grids[r].ny) continue;
+            placed[q] = 1;
+            c->roff[q] = off;
+            off += 3LL * grids[q].nx * grids[q].ny;
+        }
+        c->sblocks.push_back({start, packed, off - start});
+        packed += off - start;
+    }
     for (int r = 0; r < R; ++r) {
         c->rgrid.push_back(grids[r]);
-        c->roff.push_back(off);
-        const long long n = (long long)grids[r].nx * grids[r].ny;
-        off += 3 * n;
-        maxN = std::max(maxN, n);
+        maxN = std::max(maxN, (long long)grids[r].nx * grids[r].ny);
         c->rkey.push_back(seeds ? seeds[r] : splitmix64(cfg->seed + (uint64_t)r));
         c->rT.push_back(cfg->T);
         c->rJ.push_back(0.0);
     }
-    c->Ntot = off / 3;
+    c->Ntot = (off + 2) / 3;
     c->N = maxN;
     c->seed = c->rkey[0];
     cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
@@ -647,8 +665,15 @@ mm_status mm_get_m(mm_ctx* c, int r, double* m) {
 
 mm_status mm_set_m_device(mm_ctx* c, const void* m) {
     if (!c || !m) return MM_ERR_ARG;
-    const long long ncell = c->batch ? c->Ntot : c->N;
-    cudaError_t e = cudaMemcpyAsync(c->d_m, m, 3 * ncell * c->esz, cudaMemcpyDeviceToDevice, c->stream);
+    cudaError_t e = cudaSuccess;
+    if (c->batch) {
+        for (const auto& b : c->sblocks)
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync((char*)c->d_m + b[0] * c->esz, (const char*)m + b[1] * c->esz, b[2] * c->esz,
+                                    cudaMemcpyDeviceToDevice, c->stream);
+    } else {
+        e = cudaMemcpyAsync(c->d_m, m, 3 * c->N * c->esz, cudaMemcpyDeviceToDevice, c->stream);
+    }
     if (c->batch) {
         for (int r = 0; r < c->R; ++r) {
             ReplicaView view(c, r);
@@ -663,9 +688,16 @@ mm_status mm_set_m_device(mm_ctx* c, const void* m) {
 
 mm_status mm_get_m_device(mm_ctx* c, void* m) {
     if (!c || !m) return MM_ERR_ARG;
-    const long long ncell = c->batch ? c->Ntot : c->N;
-    return cuda_check(c, cudaMemcpyAsync(m, c->d_m, 3 * ncell * c->esz, cudaMemcpyDeviceToDevice, c->stream),
-                      "mm_get_m_device");
+    cudaError_t e = cudaSuccess;
+    if (c->batch) {
+        for (const auto& b : c->sblocks)
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync((char*)m + b[1] * c->esz, (const char*)c->d_m + b[0] * c->esz, b[2] * c->esz,
+                                    cudaMemcpyDeviceToDevice, c->stream);
+    } else {
+        e = cudaMemcpyAsync(m, c->d_m, 3 * c->N * c->esz, cudaMemcpyDeviceToDevice, c->stream);
+    }
+    return cuda_check(c, e, "mm_get_m_device");
 }
 
 mm_status mm_set_field(mm_ctx* c, int r, const double B[3], const double* B_cell) {
@@ -1263,6 +1295,20 @@ static bool cache_lookup(const char* path, const std::string& key, int* nt, int*
     return found;
 }
 
+mm_status mm_batch_set_shape(mm_ctx* c, int nt, int blocks) {
+    if (!c) return MM_ERR_ARG;
+    if (!c->batch) return set_error(c, MM_ERR_STATE, "launch shapes apply to replica-batched contexts");
+    if (!(nt == 0 || ((nt == 256 || nt == 512) && blocks >= 1)))
+        return set_error(c, MM_ERR_ARG, "nt must be 0 (stacked), 256 or 512, with blocks >= 1");
+    cudaStreamSynchronize(c->stream);
+    batch_set_shape(c->batch, nt, nt == 0 ? 0 : std::min(blocks, batch_max_blocks(c->batch)));
+    int got_nt = -1, got_b = -1;
+    batch_get_shape(c->batch, &got_nt, &got_b);
+    invalidate_graph(c);
+    if (nt == 0 && got_nt != 0) return set_error(c, MM_ERR_OOM, "stacked shape buffers");
+    return MM_OK;
+}
+
 mm_status mm_batch_autotune(mm_ctx* c, const char* cache_path, int* nt_out, int* blocks_out) {
     if (!c) return MM_ERR_ARG;
     if (!c->batch) return set_error(c, MM_ERR_STATE, "autotuning applies to replica-batched contexts");
@@ -1307,6 +1353,25 @@ mm_status mm_batch_autotune(mm_ctx* c, const char* cache_path, int* nt_out, int*
                 cudaEventElapsedTime(&ms, e0, e1);
                 if (ms < best) { best = ms; bnt = cand_nt; bblocks = nb; }
                 if (nb == c->R) break;
+            }
+        }
+        if (batch_stacked_allowed(c->batch)) {
+            // the stacked shape: per size class, passes over all of its replicas
+            batch_set_shape(c->batch, 0, 0);
+            int got_nt = -1, got_b = -1;
+            batch_get_shape(c->batch, &got_nt, &got_b);
+            if (got_nt == 0) {
+                c->h_state.target = std::numeric_limits<long long>::max();
+                c->h_state.t_end = std::numeric_limits<double>::infinity();
+                push_state(c);
+                launch_attempts(c, 1);
+                cudaEventRecord(e0, c->stream);
+                launch_attempts(c, 3);
+                cudaEventRecord(e1, c->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) { best = ms; bnt = 0; bblocks = 0; }
             }
         }
         c->profiling = prof;

@@ -14,7 +14,19 @@ namespace mm {
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+// one size class of the stacked launch shape: members stored back to back
+struct ClassHost {
+    int nx = 0, ny = 0, Rc = 0;
+    long long off0 = 0;            // element offset of the first member's block
+    std::vector<int> members;      // replica indices in storage order
+    int* d_members = nullptr;
+    void* S = nullptr;             // spectra [member][3][PyA][Wk] complex
+    float* Hd = nullptr;           // demag field [member][3][ny][nx]
+};
+
 struct BatchHost {
+    std::vector<ClassHost> ch;
+    bool stacked = false;          // launch shape: per-class passes instead of the persistent kernel
     std::vector<RepDev> rep;
     std::vector<ClsDev> cls;
     std::vector<DemagPlan> plans;
@@ -71,6 +83,11 @@ void batch_free(BatchHost* b) {
     cudaFree(b->d_trc);
     cudaFree(b->d_trsteps);
     cudaFree(b->d_trstop);
+    for (auto& k : b->ch) {
+        cudaFree(k.d_members);
+        cudaFree(k.S);
+        cudaFree(k.Hd);
+    }
     for (auto& p : b->plans) demag_free_plan(p);
     delete b;
 }
@@ -80,7 +97,6 @@ mm_status batch_setup(mm_ctx* c, BatchHost* b, const std::vector<mm_grid>& grids
                       bool demag) {
     const int R = (int)grids.size();
     b->rep.resize(R);
-    long long off = 0;
     for (int r = 0; r < R; ++r) {
         const mm_grid& g = grids[r];
         int cls = -1;
@@ -96,14 +112,35 @@ mm_status batch_setup(mm_ctx* c, BatchHost* b, const std::vector<mm_grid>& grids
         d.nx = g.nx;
         d.ny = g.ny;
         d.cls = cls;
-        d.off = off;
+        d.off = c->roff[r];
         d.active = 1;
         d.trial = -1;
         d.step0 = 0;
         d.key0 = (uint32_t)(keys[r] & 0xFFFFFFFFull);
         d.key1 = (uint32_t)(keys[r] >> 32);
         b->rep[r] = d;
-        off += 3LL * g.nx * g.ny;
+    }
+    // size classes for the stacked launch shape: members in storage order
+    b->ch.assign(b->cgrid.size(), ClassHost{});
+    {
+        std::vector<int> idx(R);
+        for (int r = 0; r < R; ++r) idx[r] = r;
+        std::sort(idx.begin(), idx.end(), [&](int x, int y) { return b->rep[x].off < b->rep[y].off; });
+        for (int r : idx) {
+            ClassHost& k = b->ch[b->rep[r].cls];
+            if (k.members.empty()) {
+                k.nx = b->rep[r].nx;
+                k.ny = b->rep[r].ny;
+                k.off0 = b->rep[r].off;
+            }
+            k.members.push_back(r);
+        }
+        for (ClassHost& k : b->ch) {
+            k.Rc = (int)k.members.size();
+            cudaError_t e = cudaMalloc(&k.d_members, sizeof(int) * k.Rc);
+            if (e != cudaSuccess) return cuda_check(c, e, "class members");
+            cudaMemcpy(k.d_members, k.members.data(), sizeof(int) * k.Rc, cudaMemcpyHostToDevice);
+        }
     }
     b->macro = !demag;
     b->nmax = 0;
@@ -378,14 +415,73 @@ mm_status batch_trials_result(mm_ctx* c, BatchHost* b, long long* steps, int* st
 
 bool batch_trials_on(BatchHost* b) { return b->trials_on; }
 
+// stacked launch shape: per size class, the 2-D demag passes over all of
+// its films, then the field + stage kernel over all of its cells
+static void stacked_stage(mm_ctx* c, BatchHost* b, int stage) {
+    const bool demag = (c->terms & MM_TERM_DEMAG) != 0;
+    for (size_t q = 0; q < b->ch.size(); ++q) {
+        ClassHost& k = b->ch[q];
+        const float* in = (const float*)(stage == 1 ? c->d_m : c->d_mtmp) + k.off0;
+        if (demag) demag_apply_stacked2d(c, b->plans[q], in, k.Hd, k.S, k.nx, k.ny, k.Rc);
+        StackArgs a{};
+        a.rep = b->d_rep;
+        a.members = k.d_members;
+        a.nx = k.nx;
+        a.ny = k.ny;
+        a.m0 = (float*)c->d_m;
+        a.ms = (float*)c->d_mtmp;
+        a.k1 = (float*)c->d_k[0];
+        a.hd = demag ? k.Hd : nullptr;
+        batch_field_args(c, a.fa);
+        a.fa.terms = c->terms;
+        a.stage = stage;
+        a.dm = c->integrator == MM_DM ? 1 : 0;
+        a.ext = c->ext_terms ? 1 : 0;
+        a.st = c->d_state;
+        const double cells = (double)k.Rc * k.nx * k.ny;
+        LaunchScope ls(c, stage == 1 ? "stacked_field1" : "stacked_field2",
+                       cells * (stage == 1 ? 36.0 : 48.0) + (demag ? cells * 12.0 : 0.0));
+        stacked_field_launch(a, k.Rc, c->stream);
+    }
+}
+
 void batch_step(mm_ctx* c, BatchHost* b) {
+    if (b->stacked && !b->trials_on) {
+        heun_batch_begin(c);
+        stacked_stage(c, b, 1);
+        stacked_stage(c, b, 2);
+        heun_batch_advance(c);
+        return;
+    }
     heun_batch_begin(c);
     launch_stage(c, b, 1);
     launch_stage(c, b, 2);
     heun_batch_advance(c);
 }
 
+// nt = 0 selects the stacked launch shape (its per-class buffers are
+// allocated here, outside any graph capture; on failure the persistent
+// kernel stays)
 void batch_set_shape(BatchHost* b, int nt, int blocks) {
+    if (nt == 0) {
+        bool ok = true;
+        for (size_t q = 0; q < b->ch.size() && ok; ++q) {
+            ClassHost& k = b->ch[q];
+            const DemagPlan& p = b->plans[q];
+            if (!p.on || k.S) continue;
+            const size_t sb = sizeof(float2) * (size_t)k.Rc * 3 * p.PyA * p.Wk;
+            const size_t hb = sizeof(float) * (size_t)k.Rc * 3 * k.nx * k.ny;
+            ok = cudaMalloc(&k.S, sb) == cudaSuccess && cudaMalloc(&k.Hd, hb) == cudaSuccess;
+        }
+        if (ok) {
+            b->stacked = true;
+            return;
+        }
+        cudaGetLastError();
+        nt = 256;
+        blocks = std::max(1, std::min((int)b->rep.size(), 304));
+    }
+    b->stacked = false;
     b->nt = nt;
     b->blocks = blocks;
     b->smem = batch_smem(*b, nt);
@@ -408,9 +504,11 @@ int batch_occupancy(BatchHost* b, int nt) {
 }
 
 void batch_get_shape(BatchHost* b, int* nt, int* blocks) {
-    *nt = b->nt;
-    *blocks = b->blocks;
+    *nt = b->stacked ? 0 : b->nt;
+    *blocks = b->stacked ? 0 : b->blocks;
 }
+
+bool batch_stacked_allowed(BatchHost* b) { return !b->trials_on; }
 
 // signature of the batch for the autotuner cache: sizes histogram + demag flag
 std::string batch_signature(BatchHost* b, unsigned terms) {

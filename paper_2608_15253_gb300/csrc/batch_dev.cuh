@@ -443,6 +443,23 @@ struct MacroArgs {
     int ext;                // bulk DMI or a further local term is on
 };
 constexpr int kTileMaxCells = 1024;
+
+// One size class of the stacked launch shape (batch_stacked.cu).
+struct StackArgs {
+    const RepDev* rep;
+    const int* members;     // replica index of each class member, in storage order
+    int nx, ny;
+    float* m0;              // state (all replicas)
+    float* ms;              // predictor state
+    float* k1;              // predictor slope / rotation vector
+    const float* hd;        // the class's demag field [member][3][ny][nx], or null
+    FieldArgs<float> fa;
+    int stage;              // 1 predictor, 2 corrector
+    int dm;
+    int ext;
+    const DevState* st;
+};
+void stacked_field_launch(const StackArgs& a, int Rc, cudaStream_t s);
 void macro_kernel_launch(const MacroArgs& a, cudaStream_t s);
 void tile_kernel_launch(const MacroArgs& a, cudaStream_t s);
 cudaError_t tile_kernel_attributes();

@@ -7,6 +7,7 @@
 
 #include <cstdint>
 #include <string>
+#include <array>
 #include <vector>
 
 #include "mm.h"
@@ -176,7 +177,8 @@ struct mm_ctx {
     std::vector<long long> roff;       // element offset of replica r's [3][ny][nx] block
     std::vector<uint64_t> rkey;
     std::vector<double> rT, rJ;
-    long long Ntot = 0;                // cells over all replicas
+    long long Ntot = 0;                // cells over all replicas (storage, gaps between size classes included)
+    std::vector<std::array<long long, 3>> sblocks;   // per size class: storage offset, packed offset, length
 
     mm::SurrogateHost* surr = nullptr;  // learned demag surrogate (single instance)
 
@@ -228,6 +230,7 @@ mm_status batch_setup(mm_ctx* c, BatchHost* b, const std::vector<mm_grid>& grids
 mm_status batch_upload(mm_ctx* c, BatchHost* b, const std::vector<double>& T, const std::vector<double>& J);
 void batch_step(mm_ctx* c, BatchHost* b);
 bool batch_is_fused(BatchHost* b);
+bool batch_stacked_allowed(BatchHost* b);
 void batch_macro_steps(mm_ctx* c, BatchHost* b, int nsteps);
 mm_status batch_trials_start(mm_ctx* c, BatchHost* b, const mm_trials* sp, long long step_now);
 mm_status batch_trials_result(mm_ctx* c, BatchHost* b, long long* steps, int* stopped, long long* done);
@@ -236,6 +239,7 @@ void batch_set_shape(BatchHost* b, int nt, int blocks);
 int batch_max_blocks(BatchHost* b);
 size_t batch_smem_for(BatchHost* b, int nt);
 mm_status demag_setup_for(mm_ctx* c, const mm_grid& g, DemagPlan* out);
+void demag_apply_stacked2d(mm_ctx* c, const DemagPlan& p, const float* m, float* Hd, void* S, int nx, int ny, int Rc);
 void demag_free_plan(DemagPlan& d);
 const DemagPlan& batch_plan(BatchHost* b, int r_cls);
 int batch_occupancy(BatchHost* b, int nt);

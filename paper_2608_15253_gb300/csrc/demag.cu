@@ -1206,6 +1206,41 @@ static void demag_apply_t(mm_ctx* c, const T* m, T* Hd, int stage = 0) {
     launch_x<T>(c, false, nullptr, Hd, S, 3 * nz * ny, ny, d.PyA, nx, nx, d.Lh, (const cplx<T>*)d.tw_x, false, N);
 }
 
+// Demag of Rc equal thin films stored back to back ([replica][component][y]
+// [x], FP32): the 2-D passes of one film run over all of them at once -- the
+// X pass over 3 ny Rc rows, the column convolution over Rc film planes with
+// the shared tensor spectrum (it does not depend on the plane), the inverse
+// X pass -- with the spectrum S laid out [replica][component][PyA][Wk].
+void demag_apply_stacked2d(mm_ctx* c, const DemagPlan& p, const float* m, float* Hd, void* S, int nx, int ny,
+                           int Rc) {
+    const DemagPlan saved = c->dm;
+    c->dm = p;                                   // launch_x reads the plan's row pitch
+    cplx<float>* Sp = (cplx<float>*)S;
+    const long long plane = (long long)p.PyA * p.Wk;
+    const long long N = (long long)nx * ny;
+    const double cplxb = sizeof(cplx<float>), realb = sizeof(float);
+    launch_x<float>(c, true, m, nullptr, Sp, 3 * ny * Rc, ny, p.PyA, nx, nx, p.Lh, (const cplx<float>*)p.tw_x, true,
+                    N);
+    {
+        ColArgs<float> a{};
+        a.base = Sp; a.comp_stride = plane; a.nc = 3; a.Kx = p.Kx;
+        a.khat = (const float*)p.khat;
+        a.ncomp = p.ncomp;
+        const long long Ky = p.Py / 2 + 1;
+        a.kc_stride = Ky * p.Wk;
+        a.line_stride = p.Wk; a.other_stride = 3 * plane;
+        a.L = p.Py; a.n_in = ny; a.n_out = ny;
+        a.tw = (const cplx<float>*)p.tw_y;
+        a.kk_stride = p.Wk; a.ko_stride = 0;
+        a.L_other = 1; a.axis_is_y = 1;
+        launch_col<float, 0>(c, a, Rc, "fft_conv_stacked",
+                             Rc * (3.0 * p.Kx * 2 * ny * cplxb) + (double)p.ncomp * Ky * p.Kx * realb);
+    }
+    launch_x<float>(c, false, nullptr, Hd, Sp, 3 * ny * Rc, ny, p.PyA, nx, nx, p.Lh, (const cplx<float>*)p.tw_x,
+                    false, N);
+    c->dm = saved;
+}
+
 void demag_apply(mm_ctx* c, const void* m, void* Hd) {
     if (c->prec == 32) demag_apply_t<float>(c, (const float*)m, (float*)Hd);
     else demag_apply_t<double>(c, (const double*)m, (double*)Hd);

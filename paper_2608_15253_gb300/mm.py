@@ -123,6 +123,7 @@ _SIGS = {
     "mm_topo_charge_noalloc": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
                                C.c_void_p, C.c_void_p],
     "mm_batch_autotune": [C.c_void_p, C.c_char_p, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+    "mm_batch_set_shape": [C.c_void_p, C.c_int, C.c_int],
     "mm_trials_start": [C.c_void_p, C.POINTER(mm_trials)],
     "mm_trials_result": [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_longlong)],
     "mm_surrogate_train": [C.c_void_p, C.POINTER(mm_train_cfg), _D],
@@ -350,6 +351,11 @@ def mm_batch_autotune(ctx, cache_path: str | None = None):
     _check(load().mm_batch_autotune(ctx, cache_path.encode() if cache_path else None, C.byref(nt), C.byref(blocks)),
            ctx)
     return nt.value, blocks.value
+
+
+def mm_batch_set_shape(ctx, nt: int, blocks: int = 0):
+    """nt = 0: stacked shape; 256 or 512 threads with `blocks` persistent CTAs."""
+    _check(load().mm_batch_set_shape(ctx, int(nt), int(blocks)), ctx)
 
 
 def mm_trials_start(ctx, J, T, m_init, axis=(0.0, 0.0, 1.0), threshold=0.0, max_steps=1000, base_seed=0,
