@@ -344,8 +344,8 @@ __global__ void __launch_bounds__(256) fft_x_c2r_direct_kernel(XArgs<float> a) {
     }
 }
 
-// FP32 X passes for long rows (Lh >= 192): one row per warp, eight warps per
-// CTA, no CTA-wide barrier.  R2C: packed pairs straight from global memory
+// FP32 X passes for rows of half length 64 ... 512: one row per warp, eight
+// warps per CTA, no CTA-wide barrier.  R2C: packed pairs straight from global memory
 // into the first pass, later passes in warp-private shared memory, then the
 // split to the Lh+1 spectrum.  C2R: the rebuild of Z' from X[k] and
 // X[M-k] (both read from global memory) feeds the first pass; the last pass
@@ -992,7 +992,8 @@ static CKern<T> col_kernel(int L) {
 static XKern<float> x_warp_kernel(bool fwd, int Lh) {
     switch (Lh) {
 #define MM_CASE(n) case n: return fwd ? fft_x_r2c_warp_kernel<n, 0> : fft_x_c2r_warp_kernel<n>;
-        MM_CASE(192) MM_CASE(216) MM_CASE(256) MM_CASE(324) MM_CASE(432) MM_CASE(512)
+        MM_CASE(64) MM_CASE(96) MM_CASE(128) MM_CASE(192) MM_CASE(216) MM_CASE(256) MM_CASE(324) MM_CASE(432)
+        MM_CASE(512)
 #undef MM_CASE
         default: return nullptr;
     }
