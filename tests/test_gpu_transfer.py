@@ -1,7 +1,6 @@
-"""Host transfers through the C ABI: page-locked host buffers are read and
-written in place by the conversion kernels, pageable ones through the
-staging buffer; both give the same state (renormalised per cell, absent
-cells zero), in FP32 and FP64."""
+"""Host transfers through the C ABI from page-locked and pageable host
+buffers give the same state (renormalised per cell, absent cells zero), in
+FP32 and FP64."""
 import numpy as np
 import pytest
 
@@ -24,12 +23,12 @@ def test_pinned_and_pageable_transfers_agree(prec):
         pinned = torch.empty(m.size, dtype=torch.float64, pin_memory=True)
         mp = pinned.numpy().reshape(m.shape)
         mp[...] = m
-        mm.mm_set_m(ctx, 0, mp)                               # in place over the host link
+        mm.mm_set_m(ctx, 0, mp)                               # page-locked source
         a = mm.mm_get_m(ctx, 0, m.shape)                      # pageable read-back
-        mm.mm_set_m(ctx, 0, m)                                # staged
+        mm.mm_set_m(ctx, 0, m)                                # pageable source
         out = torch.empty(m.size, dtype=torch.float64, pin_memory=True)
         b = out.numpy().reshape(m.shape)
-        mm.mm_get_m(ctx, 0, m.shape, out=b)                   # pinned read-back
+        mm.mm_get_m(ctx, 0, m.shape, out=b)                   # page-locked read-back
         assert np.array_equal(a, b)
         present = mat.cell["Ms"] > 0
         n = np.sqrt((m ** 2).sum(axis=0))
