@@ -1084,7 +1084,10 @@ static void launch_x(mm_ctx* c, bool forward, const T* in, T* out_real, cplx<T>*
             x_stage_kernel(stage, Lh)<<<(rows + kXW - 1) / kXW, 32 * kXW, smem, c->stream>>>(a);
             return;
         }
-        if (XKern<float> wk = x_warp_kernel(forward, Lh)) {
+        // the plain one-row-per-warp kernels take no stage combine: with a
+        // stage to form they are only used through x_stage_kernel above
+        XKern<float> wk = stage == 0 ? x_warp_kernel(forward, Lh) : nullptr;
+        if (wk) {
             const size_t smem = (size_t)kXW * wline(Lh) * sizeof(float2);
             LaunchScope ls(c, forward ? "fft_x_r2c" : "fft_x_c2r",
                            (double)rows * (nx * sizeof(T) + (Lh + 1) * sizeof(cplx<T>)));

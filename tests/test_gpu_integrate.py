@@ -26,6 +26,10 @@ CASES = [
      W.Material(Ms=8e5, A=1.3e-11, alpha=0.02), (-24.6e-3, 4.3e-3, 0.0)),
     ("odd", W.Grid(17, 5, 2, 2e-9, 3e-9, 1e-9),
      W.Material(Ms=7e5, A=1.1e-11, alpha=0.3, Ku1=2e5, u=(0.6, 0, 0.8), D=1.5e-3), (0.0, 0.02, 0.01)),
+    # half length 64 on a small grid: the stage combine runs in the CTA-wide X
+    # pass (the one-row-per-warp kernel of this length forms no stage)
+    ("rows64", W.Grid(64, 12, 2, 2e-9, 2e-9, 2e-9),
+     W.Material(Ms=6e5, A=1.3e-11, alpha=0.2, Ku1=3e5, u=(0, 0, 1), D=2e-3), (0.0, 0.01, 0.03)),
     # half length 192: the FP32 stage combine runs inside the X pass; granular
     # regions with holes exercise the per-cell Ms there
     ("fused", W.Grid(170, 12, 2, 2e-9, 2e-9, 2e-9),
