@@ -213,10 +213,11 @@ MM_API mm_status mm_destroy(mm_ctx* ctx);
 MM_API mm_status mm_set_stream(mm_ctx* ctx, void* stream);
 
 /* Set / read the magnetisation of one replica (host float64, 3N, layout
- * [component][z][y][x]).  The doubles are copied to a device staging buffer
- * (3N doubles, allocated on first use and kept) and converted there:
- * input is renormalised per cell; absent cells and zero vectors are set to
- * zero.  Page-locked host memory gives the fastest copies.  Both calls
+ * [component][z][y][x]).  Page-locked host memory is read / written in place
+ * by the conversion kernel (one pass over the host link); pageable memory
+ * goes through a device staging buffer (3N doubles, allocated on first use
+ * and kept).  Input is renormalised per cell; absent cells and zero vectors
+ * are set to zero.  Both calls
  * return after the copy has completed (they synchronise the context
  * stream).  Errors: MM_ERR_ARG (bad replica, NULL m), MM_ERR_OOM, MM_ERR_CUDA. */
 MM_API mm_status mm_set_m(mm_ctx* ctx, int replica, const double* m);

@@ -616,24 +616,41 @@ struct ReplicaView {
 
 extern "C" {
 
+// Device address of page-locked host memory (null for pageable memory):
+// the transfer kernels then read or write the host buffer directly, one
+// pass over the interconnect instead of a copy plus a device pass.
+static const void* mapped_host(const void* p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 mm_status mm_set_m(mm_ctx* c, int r, const double* m) {
     mm_status s = check_replica(c, r);
     if (s != MM_OK) return s;
     if (!m) return set_error(c, MM_ERR_ARG, "null m");
     ReplicaView view(c, r);
     const long long n3 = 3 * c->N;
-    s = ensure_stage(c, n3);
-    if (s != MM_OK) return s;
-    cudaError_t e = cudaMemcpyAsync(c->d_stage, m, sizeof(double) * n3, cudaMemcpyHostToDevice, c->stream);
+    const double* src = (const double*)mapped_host(m);
+    cudaError_t e = cudaSuccess;
+    if (!src) {
+        s = ensure_stage(c, n3);
+        if (s != MM_OK) return s;
+        e = cudaMemcpyAsync(c->d_stage, m, sizeof(double) * n3, cudaMemcpyHostToDevice, c->stream);
+        src = (const double*)c->d_stage;
+    }
     const unsigned nb = (unsigned)((c->N + 255) / 256);
     const uint8_t* reg = c->uniform ? nullptr : (const uint8_t*)c->d_region;
     if (e == cudaSuccess) {
         if (c->prec == 32)
-            state_in_kernel<float><<<nb, 256, 0, c->stream>>>((const double*)c->d_stage, c->N, reg,
-                                                             (const Region<float>*)c->d_lut, (float*)c->d_m);
+            state_in_kernel<float><<<nb, 256, 0, c->stream>>>(src, c->N, reg, (const Region<float>*)c->d_lut,
+                                                             (float*)c->d_m);
         else
-            state_in_kernel<double><<<nb, 256, 0, c->stream>>>((const double*)c->d_stage, c->N, reg,
-                                                              (const Region<double>*)c->d_lut, (double*)c->d_m);
+            state_in_kernel<double><<<nb, 256, 0, c->stream>>>(src, c->N, reg, (const Region<double>*)c->d_lut,
+                                                              (double*)c->d_m);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -648,7 +665,11 @@ mm_status mm_get_m(mm_ctx* c, int r, double* m) {
     ReplicaView view(c, r);
     const long long n3 = 3 * c->N;
     cudaError_t e;
-    if (c->prec == 32) {
+    double* dst = (double*)mapped_host(m);
+    if (c->prec == 32 && dst) {
+        state_out_kernel<float><<<(unsigned)((n3 + 255) / 256), 256, 0, c->stream>>>((const float*)c->d_m, n3, dst);
+        e = cudaGetLastError();
+    } else if (c->prec == 32) {
         s = ensure_stage(c, n3);
         if (s != MM_OK) return s;
         state_out_kernel<float><<<(unsigned)((n3 + 255) / 256), 256, 0, c->stream>>>((const float*)c->d_m, n3,
