@@ -3,6 +3,7 @@ uniforms, the statistics of the normals, counter/key sensitivity, and the
 macrospin Langevin equilibrium the paper validates sigma against
 (<m_z> = L(3) = coth 3 - 1/3 = 0.672; the paper measures 0.675)."""
 import math
+import os
 
 import numpy as np
 
@@ -63,6 +64,34 @@ def test_normals_statistics():
     g2 = normals(seed=99, step=4, ncell=200000).ravel()
     assert abs(np.corrcoef(g, g2)[0, 1]) < 0.01
     assert np.all(normals(seed=99, step=3, ncell=1000) == normals(seed=99, step=3, ncell=1000))
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _rows(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+def test_philox_known_answer_vectors():
+    """The generator's published known-answer vectors (all-zero, all-ones and
+    pi-digit counters and keys)."""
+    rows = _rows("philox4x32_10_kat.txt")
+    assert len(rows) == 3
+    for row in rows:
+        c0, c1, c2, c3, k0, k1, *want = (int(v, 16) for v in row)
+        got = philox4x32_10([c0], [c1], [c2], [c3], [k0], [k1])
+        assert [int(x[0]) for x in got] == want
+
+
+def test_splitmix64_known_answer_sequence():
+    rows = _rows("splitmix64_kat.txt")
+    assert rows[0][0] == "state"
+    state = int(rows[0][1])
+    for row in rows[1:]:
+        assert splitmix64(state) == int(row[0])
+        state = (state + 0x9E3779B97F4A7C15) % (1 << 64)
 
 
 def test_splitmix64_is_a_bijective_mixer():
