@@ -124,3 +124,54 @@ def test_newell_auxiliary_symmetries():
         assert oracle.newell_f(-x, y, -z) == f
         assert oracle.newell_g(-x, y, z) == -g and oracle.newell_g(x, -y, z) == -g
         assert oracle.newell_g(x, y, -z) == g
+
+
+def _aharoni_prism_factor(a, b, c):
+    """Demagnetising factor along the edge 2c of a uniformly magnetised
+    rectangular prism 2a x 2b x 2c, in the closed form of A. Aharoni,
+    J. Appl. Phys. 83, 3432 (1998) (derived from the prism's magnetostatic
+    energy, independently of Newell's f and g functions)."""
+    r = math.sqrt(a * a + b * b + c * c)
+    ab, bc, ac = math.hypot(a, b), math.hypot(b, c), math.hypot(a, c)
+    ln = math.log
+    s = ((b * b - c * c) / (2 * b * c) * ln((r - a) / (r + a))
+         + (a * a - c * c) / (2 * a * c) * ln((r - b) / (r + b))
+         + b / (2 * c) * ln((ab + a) / (ab - a)) + a / (2 * c) * ln((ab + b) / (ab - b))
+         + c / (2 * a) * ln((bc - b) / (bc + b)) + c / (2 * b) * ln((ac - a) / (ac + a))
+         + 2 * math.atan(a * b / (c * r))
+         + (a ** 3 + b ** 3 - 2 * c ** 3) / (3 * a * b * c)
+         + (a * a + b * b - 2 * c * c) / (3 * a * b * c) * r
+         + c / (a * b) * (ac + bc)
+         - (ab ** 3 + bc ** 3 + ac ** 3) / (3 * a * b * c))
+    return s / math.pi
+
+
+@pytest.mark.parametrize("cell", CELLS + [(4e-9, 2e-9, 1e-9)])
+def test_self_term_equals_the_prism_demagnetising_factors(cell):
+    N = newell_at([(0, 0, 0)], cell)[0]
+    a, b, c = (v / 2 for v in cell)
+    ref = [_aharoni_prism_factor(b, c, a), _aharoni_prism_factor(c, a, b), _aharoni_prism_factor(a, b, c)]
+    assert np.allclose(N[:3], ref, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("shape,cell", [((2, 8, 12), (1.0, 1.0, 1.0)),
+                                        ((3, 5, 40), (2.0, 3.0, 1.5)),
+                                        ((1, 64, 64), (2e-9, 2e-9, 1e-9))])
+def test_block_average_equals_the_prism_demagnetising_factors(shape, cell):
+    """A block of cells magnetised uniformly is one prism: the mean over all
+    cell pairs of the tensor at their displacement is the prism's factor.
+    The sum runs over displacements up to 63 cells, so every quadrature band
+    of the far field enters."""
+    nz, ny, nx = shape
+    N = newell_octant(shape, cell)
+
+    def mult(n):                       # ordered pairs at displacement |u| along one axis
+        m = 2.0 * (n - np.arange(n))
+        m[0] = n
+        return m
+
+    w = mult(nz)[:, None, None] * mult(ny)[None, :, None] * mult(nx)[None, None, :]
+    mean = [float((N[comp] * w).sum()) / (nx * ny * nz) for comp in range(3)]
+    a, b, c = nx * cell[0] / 2, ny * cell[1] / 2, nz * cell[2] / 2
+    ref = [_aharoni_prism_factor(b, c, a), _aharoni_prism_factor(c, a, b), _aharoni_prism_factor(a, b, c)]
+    assert np.allclose(mean, ref, rtol=1e-12, atol=1e-14)
