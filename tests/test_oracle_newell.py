@@ -160,8 +160,8 @@ def test_self_term_equals_the_prism_demagnetising_factors(cell):
 def test_block_average_equals_the_prism_demagnetising_factors(shape, cell):
     """A block of cells magnetised uniformly is one prism: the mean over all
     cell pairs of the tensor at their displacement is the prism's factor.
-    The sum runs over displacements up to 63 cells, so every quadrature band
-    of the far field enters."""
+    The sum runs over displacements up to 63 cells, so the closed form and
+    every quadrature band of the far field below 128 cells enter."""
     nz, ny, nx = shape
     N = newell_octant(shape, cell)
 
