@@ -1,6 +1,7 @@
 """Pins of the oracle's demagnetising field: FFT convolution against the
 brute-force double sum, exact symmetry results for uniformly magnetised
-cubes, and the thin-film limit."""
+cubes, the thin-film limit, periodic images, and Kittel precession of a
+single cell."""
 import numpy as np
 import pytest
 
@@ -142,3 +143,41 @@ def test_periodic_rod_limit():
     my = np.zeros((3,) + p.shape); my[1] = 1
     assert np.abs(h_demag(mx, p, K)[0] / 8e5).max() < 2e-3
     assert np.abs(h_demag(my, p, K)[1] / 8e5 + 0.5).max() < 2e-3
+
+
+def test_single_cell_precesses_at_the_kittel_frequency():
+    """A single cell is magnetised uniformly, so its demagnetising field is
+    -Ms (Nx mx, Ny my, Nz mz) with the prism factors of the cell.  Small-angle
+    precession about an applied field along x then follows Kittel's formula
+    w = gamma0 sqrt((B + mu0 Ms (Ny - Nx)) (B + mu0 Ms (Nz - Nx))), with the
+    factors taken from Aharoni's closed form (independent of the oracle)."""
+    import math
+
+    from oracle.constants import GAMMA0, MU0
+    from oracle.llg import Solver
+    from prism import prism_factor
+
+    d, Ms, B = (4e-9, 2e-9, 1e-9), 8e5, 0.05
+    grid = W.Grid(1, 1, 1, *d)
+    p = Problem.from_workload(grid, W.Material(Ms=Ms, A=1.3e-11, alpha=0.0), B_ext=(B, 0.0, 0.0))
+    a, b, c = (v / 2 for v in d)
+    Nx, Ny, Nz = prism_factor(b, c, a), prism_factor(c, a, b), prism_factor(a, b, c)
+    w_kittel = GAMMA0 * math.sqrt((B + MU0 * Ms * (Ny - Nx)) * (B + MU0 * Ms * (Nz - Nx)))
+    eps = 1e-4
+    m0 = np.array([math.sqrt(1 - eps * eps), eps, 0.0]).reshape(3, 1, 1, 1)
+    s = Solver(p, m0, terms=("zeeman", "demag"))
+    period = 2 * math.pi / w_kittel
+    dt = period / 400
+    ts, ys = [0.0], [float(s.m[1, 0, 0, 0])]
+    for _ in range(1400):
+        s.rk45_step_fixed(dt)
+        ts.append(s.t)
+        ys.append(float(s.m[1, 0, 0, 0]))
+    # downward zero crossings of m_y (it starts at its maximum)
+    cross = [ts[i] + (ts[i + 1] - ts[i]) * ys[i] / (ys[i] - ys[i + 1])
+             for i in range(len(ys) - 1) if ys[i] > 0 >= ys[i + 1]]
+    assert len(cross) >= 3
+    measured = (cross[-1] - cross[0]) / (len(cross) - 1)
+    assert abs(measured / period - 1) < 1e-6
+    # the field alone (no shape anisotropy) would give gamma0 B: far off
+    assert abs(2 * math.pi / (GAMMA0 * B) / measured - 1) > 0.5
