@@ -221,3 +221,43 @@ def test_zhang_li_uniform_is_zero_and_wall_translates():
         s.rk45_step()
     shift = (s.m[2].mean() - mz0) * n * dx / 2      # <mz> = 2 x_centre / L for this wall
     assert abs(shift - (-u * (s.t - t0))) < 0.03 * u * (s.t - t0)
+
+
+@pytest.mark.parametrize("J_over_Jc0,eps_prime", [(2.0, 0.0), (0.5, 0.0), (1.5, 0.3)])
+def test_stt_macrospin_polar_angle_follows_its_scalar_equation(J_over_Jc0, eps_prime):
+    """Perpendicular macrospin with p = -z: precession and the m x p terms
+    only turn the azimuth, so the polar angle obeys the scalar equation
+    dtheta/dt = gamma' mu0 sin(theta) [h_DL(theta) + alpha h_FL - alpha H_K cos(theta)]
+    with h_DL = eps(m.p) hbar J / (e mu0 Ms t_F), m.p = -cos(theta); below
+    the threshold J_c0 = alpha H_K e mu0 Ms t_F / (hbar eps(-1)) the state
+    relaxes, above it the current reverses it.  The oracle's 3-D integration
+    must follow that equation (integrated here by scipy)."""
+    from scipy.integrate import solve_ivp
+
+    from oracle.constants import HBAR, QE
+    Ms, Ku, alpha, P, Lam, dz = 1e6, 1e6, 0.02, 0.6, 2.0, 1e-9
+    grid = W.Grid(1, 1, 1, 2e-9, 2e-9, dz)
+    p = Problem.from_workload(grid, W.Material(Ms=Ms, A=1e-11, alpha=alpha, Ku1=Ku, u=(0, 0, 1)))
+    HK = 2 * Ku / (MU0 * Ms)
+    L2 = Lam ** 2
+    Jc0 = alpha * HK * QE * MU0 * Ms * dz / (HBAR * P * L2 / 2)
+    J = J_over_Jc0 * Jc0
+    base = HBAR * J / (QE * MU0 * Ms * dz)
+    gp = GAMMA0 / (1 + alpha ** 2)
+
+    def rhs(_, y):
+        th = y[0]
+        eps = P * L2 / ((L2 + 1) - (L2 - 1) * math.cos(th))
+        return [gp * MU0 * math.sin(th) * (eps * base + alpha * eps_prime * base - alpha * HK * math.cos(th))]
+
+    th0, t_end = 0.2, 150e-12
+    ref = solve_ivp(rhs, (0, t_end), [th0], rtol=1e-12, atol=1e-14).y[0, -1]
+    m0 = np.array([math.sin(th0), 0.0, math.cos(th0)]).reshape(3, 1, 1, 1)
+    tq = Torque(kind="stt", J=J, p=(0, 0, -1), P=P, Lambda=Lam, eps_prime=eps_prime)
+    s = Solver(p, m0, terms=("anisotropy",), torque=tq, dt=1e-14, rtol=1e-10)
+    while s.t < t_end:
+        s.dt = min(s.dt, t_end - s.t)
+        s.rk45_step()
+    th = math.acos(float(s.m[2, 0, 0, 0]))
+    assert abs(th - ref) < 1e-7
+    assert (th > th0) == (J_over_Jc0 > 1)
