@@ -144,36 +144,67 @@ def cpu_baseline(seconds_budget=60.0):
                       f"FFT and array ops; Newell/FFT setup excluded), {el:.1f} s"}
 
 
+REFERENCE_BUDGET_S = 240.0
+# sample grids of the 256x256x16 workload (same material, 2 nm cells, RK45), largest first
+REFERENCE_SAMPLES = [(256, 256, 16), (128, 128, 16), (64, 64, 16), (32, 32, 16), (16, 16, 16),
+                     (16, 16, 8), (8, 8, 8), (4, 4, 4)]
+
+
+def _oracle_solver(w, nx, ny, nz):
+    from dataclasses import replace
+
+    from oracle.demag import demag_spectrum
+    from oracle.fields import Problem
+    from oracle.llg import Solver
+    g = W.Grid(nx, ny, nz, w.grid.dx, w.grid.dy, w.grid.dz)
+    ws = replace(w, grid=g)
+    p = Problem.from_workload(g, ws.mat)
+    s = Solver(p, W.m_random_sphere(g, seed=2), K_hat=demag_spectrum(p.shape, p.d), dt=1e-14, rtol=w.rtol)
+    s.k1 = s.slope(s.m)
+    return s, g.n
+
+
 def run_reference(args):
+    """The FP64 CPU oracle timed on this host, W warm-up and exactly K timed
+    RK45 steps.  Each step is a bounded sample of the 256x256x16 workload: the
+    largest grid of the same material, cell size and integrator whose K + W
+    steps fit in about REFERENCE_BUDGET_S seconds (cost per cell-step taken
+    from two steps of a 32x32x16 probe)."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
     w = W.dmi_256x256x16()
-    from oracle.demag import demag_spectrum
-    from oracle.fields import Problem
-    from oracle.llg import Solver
-    p = Problem.from_workload(w.grid, w.mat)
-    K = demag_spectrum(p.shape, p.d)
-    s = Solver(p, W.m_random_sphere(w.grid, seed=2), K_hat=K, dt=1e-14, rtol=1e-6)
-    s.k1 = s.slope(s.m)
-    # each "step" is one full RK45 step; the count is bounded so the run ends in minutes
-    warm = min(args.warmup, 1)
-    timed = max(1, min(args.steps, 4))
-    for _ in range(warm):
+    probe, n_probe = _oracle_solver(w, 32, 32, 16)
+    probe.rk45_step_fixed(1e-14)
+    t0 = time.perf_counter()
+    for _ in range(2):
+        probe.rk45_step_fixed(1e-14)
+    per_cell_step = (time.perf_counter() - t0) / (2 * n_probe)
+    total = args.steps + args.warmup
+    shape = REFERENCE_SAMPLES[-1]
+    for cand in REFERENCE_SAMPLES:
+        if per_cell_step * cand[0] * cand[1] * cand[2] * total <= REFERENCE_BUDGET_S:
+            shape = cand
+            break
+    s, n = _oracle_solver(w, *shape)
+    for _ in range(args.warmup):
         s.rk45_step_fixed(1e-14)
     t0 = time.perf_counter()
-    for _ in range(timed):
+    for _ in range(args.steps):
         s.rk45_step_fixed(1e-14)
     el = time.perf_counter() - t0
-    val = w.grid.n * timed / el
+    val = n * args.steps / el
+    sample = (f"each step one RK45 step (dt 1e-14 s) of a {shape[0]}x{shape[1]}x{shape[2]} sample of the "
+              f"workload (same material, 2 nm cells, exact demag; numpy FP64, single-threaded), "
+              f"{args.steps} timed after {args.warmup} warm-up, {el:.1f} s")
     line = {
-        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws, "steps": timed,
-        "warmup": warm, "ms_per_step": 1e3 * el / timed, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "cells": w.grid.n, "grid": [256, 256, 16], "integrator": "rk45",
-                   "precision": "fp64-cpu-oracle"},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{timed} RK45 step(s) of the full workload after {warm} warm-up step(s)"},
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "cells": w.grid.n, "grid": [w.grid.nx, w.grid.ny, w.grid.nz],
+                   "cell_nm": [2, 2, 2], "integrator": "rk45-dopri5", "rtol": w.rtol,
+                   "precision": "fp64-cpu-oracle", "sample_grid": list(shape)},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
