@@ -280,6 +280,15 @@ MM_API mm_status mm_energy(mm_ctx* ctx, int replica, double* E);
  * `layer`, or the mean over layers when layer < 0; FP64 compensated sum. */
 MM_API mm_status mm_topo_charge(mm_ctx* ctx, int replica, int layer, double* Q);
 
+/* Mean magnetisation <m> (Results: the average magnetisation the standard
+ * problems and relaxation runs report): the average of the unit vectors m
+ * over the present cells (Ms > 0) of the replica, or of z-layer `layer`
+ * when layer >= 0; FP64 compensated sums of the working-precision state.
+ * m_mean: host double[3], written only on success (zeros when no cell of
+ * the selection is present).  Errors: MM_ERR_ARG (bad replica, layer >= nz,
+ * m_mean NULL), MM_ERR_CUDA. */
+MM_API mm_status mm_mean_m(mm_ctx* ctx, int replica, int layer, double* m_mean);
+
 MM_API mm_status mm_get_time(mm_ctx* ctx, int replica, double* t, double* dt, long long* steps);
 MM_API mm_status mm_get_stats(mm_ctx* ctx, mm_stats* st);
 

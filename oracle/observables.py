@@ -1,4 +1,4 @@
-"""Energy and topological charge of the oracle.
+"""Energy, topological charge and mean magnetisation of the oracle.
 
 Energy (the quantity behind the energy-balance results, e.g. the
 flower/vortex crossover and the skyrmion phase diagram): per cell
@@ -17,6 +17,10 @@ with central differences inside and one-sided differences at edges and
 next to absent cells (a reading: the paper does not give the stencil); for
 nz > 1 the mean over layers.  ``topological_charge_bl`` is the lattice
 (Berg-Luescher) solid-angle form, used as an independent check.
+
+Mean magnetisation <m> (the averaged magnetisation the standard-problem and
+relaxation results report): the average of the unit vectors over the present
+cells (Ms > 0), of the whole grid or of one z-layer.
 """
 from __future__ import annotations
 
@@ -109,3 +113,13 @@ def topological_charge_bl(m, p: Problem) -> float:
                     s.append(2.0 * math.atan2(num, den))
         tot.append(math.fsum(s) / (4 * math.pi))
     return sum(tot) / len(tot)
+
+
+def mean_magnetisation(m, p: Problem, layer=None) -> np.ndarray:
+    """<m> over the present cells (of z-layer ``layer`` when given)."""
+    pres = p.present if layer is None else p.present[layer:layer + 1]
+    mm = m if layer is None else m[:, layer:layer + 1]
+    n = int(pres.sum())
+    if n == 0:
+        return np.zeros(3)
+    return np.array([math.fsum(mm[c][pres].ravel()) / n for c in range(3)])

@@ -579,6 +579,11 @@ mm_status mm_set_stream(mm_ctx* c, void* stream) {
 
 }  // extern "C"
 
+namespace mm {
+// sums of m_x, m_y, m_z and the present-cell count (reduce.cu)
+void mean_launch(mm_ctx* c, const void* m, int layer, double* d_out);
+}  // namespace mm
+
 static mm_status check_replica(mm_ctx* c, int r) {
     if (!c) return MM_ERR_ARG;
     if (r < 0 || r >= c->R) return set_error(c, MM_ERR_ARG, "replica index out of range");
@@ -1157,6 +1162,21 @@ mm_status mm_topo_charge(mm_ctx* c, int r, int layer, double* Q) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_check(c, e, "mm_topo_charge");
     *Q = layer >= 0 ? h : h / c->grid.nz;
+    return MM_OK;
+}
+
+mm_status mm_mean_m(mm_ctx* c, int r, int layer, double* m_mean) {
+    mm_status s = check_replica(c, r);
+    if (s != MM_OK) return s;
+    ReplicaView view(c, r);
+    if (!m_mean || layer >= c->grid.nz) return set_error(c, MM_ERR_ARG, "bad layer or null output");
+    double* d_out = c->d_red + 2 * 304 + 20;
+    mean_launch(c, c->d_m, layer, d_out);
+    double h[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(h, d_out, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "mm_mean_m");
+    for (int q = 0; q < 3; ++q) m_mean[q] = h[3] > 0 ? h[q] / h[3] : 0.0;
     return MM_OK;
 }
 

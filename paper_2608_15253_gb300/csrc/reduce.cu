@@ -59,6 +59,34 @@ __global__ void finish_sum_kernel(const double* __restrict__ partial, int count,
     }
 }
 
+// Sum over present cells (those of z-layer `layer` when layer >= 0) of
+// component `comp` of m, or of 1 (the present-cell count) when comp < 0.
+template <typename T>
+__global__ void mean_partial_kernel(const T* __restrict__ m, long long N, long long plane, int layer, int comp,
+                                    const uint8_t* __restrict__ region, const Region<T>* __restrict__ lut,
+                                    double* __restrict__ partial) {
+    const long long lo = layer >= 0 ? (long long)layer * plane : 0;
+    const long long hi = layer >= 0 ? lo + plane : N;
+    CompSum acc{0.0, 0.0};
+    for (long long i = lo + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < hi;
+         i += (long long)gridDim.x * blockDim.x) {
+        const Region<T>& R = lut[region ? region[i] : 0];
+        if (R.present == (T)0) continue;
+        acc.add(comp < 0 ? 1.0 : (double)m[comp * N + i]);
+    }
+    acc = warp_sum(acc);
+    __shared__ double s[64];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { s[2 * w] = acc.s; s[2 * w + 1] = acc.c; }
+    __syncthreads();
+    if (w == 0) {
+        CompSum v{0.0, 0.0};
+        if (l < (int)(blockDim.x >> 5)) { v.s = s[2 * l]; v.c = s[2 * l + 1]; }
+        v = warp_sum(v);
+        if (l == 0) { partial[2 * blockIdx.x] = v.s; partial[2 * blockIdx.x + 1] = v.c; }
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ v3<T> ldm(const T* m, long long N, long long i) {
     return mk3<T>(m[i], m[N + i], m[2 * N + i]);
@@ -156,6 +184,27 @@ void topo_launch(mm_ctx* c, const void* m, int layer, double* d_out) {
     }
     LaunchScope ls(c, "sum_finish", 0.0);
     finish_sum_kernel<<<1, 256, 0, c->stream>>>(c->d_red, kRedBlocks, d_out);
+}
+
+// d_out[0..2] = sums of m_x, m_y, m_z over the present cells (of one layer
+// when layer >= 0), d_out[3] = their count.
+void mean_launch(mm_ctx* c, const void* m, int layer, double* d_out) {
+    const uint8_t* reg = c->uniform ? nullptr : (const uint8_t*)c->d_region;
+    const long long plane = (long long)c->grid.nx * c->grid.ny;
+    for (int comp = 0; comp < 4; ++comp) {
+        const int cc = comp < 3 ? comp : -1;
+        {
+            LaunchScope ls(c, "mean_partial", (comp < 3 ? 1.0 : 0.0) * c->esz * c->N);
+            if (c->prec == 32)
+                mean_partial_kernel<float><<<kRedBlocks, 256, 0, c->stream>>>(
+                    (const float*)m, c->N, plane, layer, cc, reg, (const Region<float>*)c->d_lut, c->d_red);
+            else
+                mean_partial_kernel<double><<<kRedBlocks, 256, 0, c->stream>>>(
+                    (const double*)m, c->N, plane, layer, cc, reg, (const Region<double>*)c->d_lut, c->d_red);
+        }
+        LaunchScope ls(c, "sum_finish", 0.0);
+        finish_sum_kernel<<<1, 256, 0, c->stream>>>(c->d_red, kRedBlocks, d_out + comp);
+    }
 }
 
 void normalize_launch(mm_ctx* c, void* m) {

@@ -113,6 +113,7 @@ _SIGS = {
     "mm_get_heff": [C.c_void_p, C.c_int, _D, C.c_uint],
     "mm_energy": [C.c_void_p, C.c_int, _D],
     "mm_topo_charge": [C.c_void_p, C.c_int, C.c_int, _D],
+    "mm_mean_m": [C.c_void_p, C.c_int, C.c_int, _D],
     "mm_get_time": [C.c_void_p, C.c_int, _D, _D, C.POINTER(C.c_longlong)],
     "mm_get_stats": [C.c_void_p, C.POINTER(mm_stats)],
     "mm_get_state": [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)],
@@ -286,6 +287,12 @@ def mm_topo_charge(ctx, replica: int = 0, layer: int = -1):
     q = C.c_double()
     _check(load().mm_topo_charge(ctx, replica, layer, C.byref(q)), ctx)
     return q.value
+
+
+def mm_mean_m(ctx, replica: int = 0, layer: int = -1):
+    out = np.zeros(3, dtype=np.float64)
+    _check(load().mm_mean_m(ctx, replica, layer, _dptr(out)), ctx)
+    return out
 
 
 def mm_get_time(ctx, replica: int = 0):

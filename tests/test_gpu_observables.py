@@ -135,3 +135,53 @@ def test_fault_injection_leaves_context_usable():
         assert e.value.status == mm.MM_ERR_OOM
     finally:
         mm.mm_destroy(c)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_mean_magnetisation_matches_oracle(prec):
+    """<m> over the present cells, whole grid and per layer, on a grid with
+    holes; the oracle averages the host input normalised in FP64."""
+    mm = need_gpu()
+    from oracle.observables import mean_magnetisation
+    grid = W.Grid(37, 21, 3, 2e-9, 2e-9, 2e-9)
+    mat = W.with_cells(W.Material(Ms=5.8e5, A=1.5e-11, alpha=0.1, Ku1=8e5, u=(0, 0, 1), D=3e-3),
+                       W.random_material_cells(grid, 5))
+    ctx = make_ctx(mm, grid, mat, precision=prec, demag=False)
+    try:
+        m = W.random_m(grid, seed=6)
+        m = m + np.array([0.3, -0.2, 0.5])[:, None, None, None]
+        mm.mm_set_m(ctx, 0, m)
+        m_unit = m / np.linalg.norm(m, axis=0, keepdims=True)
+        p = oracle_problem(grid, mat)
+        tol = 1e-13 if prec == 64 else 1e-6
+        got = mm.mm_mean_m(ctx, 0, -1)
+        assert np.abs(got - mean_magnetisation(m_unit, p)).max() < tol
+        for k in range(grid.nz):
+            assert np.abs(mm.mm_mean_m(ctx, 0, k) - mean_magnetisation(m_unit, p, k)).max() < tol
+        with pytest.raises(mm.MMError):
+            mm.mm_mean_m(ctx, 0, grid.nz)
+    finally:
+        mm.mm_destroy(ctx)
+
+
+def test_mean_magnetisation_of_batched_replicas():
+    mm = need_gpu()
+    from oracle.observables import mean_magnetisation
+    sizes = [(32, 32), (17, 9), (48, 48), (32, 32)]
+    mat = W.Material(Ms=1.1e6, A=2e-11, alpha=0.01, Ku1=9e5, u=(0.0, 0.0, 1.0))
+    M = mm.Material(mat.Ms, mat.A, mat.alpha, mat.Ku1, mat.u, mat.D)
+    cfg = mm.make_config(precision=32, integrator=mm.MM_HEUN, demag=mm.MM_DEMAG_OFF, dt=1e-14)
+    ctx = mm.mm_create_batch([mm.make_grid(nx, ny, 1, 2e-9, 2e-9, 1e-9) for nx, ny in sizes], M.s, cfg, None)
+    try:
+        want = []
+        for r, (nx, ny) in enumerate(sizes):
+            grid = W.Grid(nx, ny, 1, 2e-9, 2e-9, 1e-9)
+            m = W.random_m(grid, seed=10 + r) + np.array([0.1 * r, 0.4, -0.3])[:, None, None, None]
+            mm.mm_set_m(ctx, r, m)
+            m_unit = m / np.linalg.norm(m, axis=0, keepdims=True)
+            want.append(mean_magnetisation(m_unit, oracle_problem(grid, mat)))
+        for r in range(len(sizes)):
+            assert np.abs(mm.mm_mean_m(ctx, r, -1) - want[r]).max() < 1e-6
+            assert np.abs(mm.mm_mean_m(ctx, r, 0) - want[r]).max() < 1e-6
+    finally:
+        mm.mm_destroy(ctx)

@@ -1,7 +1,7 @@
-"""Pins of the oracle's energy and topological charge: exact energies of
-uniform states (including the cube demag factor 1/3 by symmetry), the
-charge of a Neel skyrmion against the lattice solid-angle charge, and
-invariances."""
+"""Pins of the oracle's energy, topological charge and mean magnetisation:
+exact energies of uniform states (including the cube demag factor 1/3 by
+symmetry), the charge of a Neel skyrmion against the lattice solid-angle
+charge, invariances, and the present-cell average."""
 import math
 
 import numpy as np
@@ -74,3 +74,32 @@ def test_charge_zero_for_uniform_and_rotation_invariant():
     Rz = np.array([[math.cos(a), -math.sin(a), 0], [math.sin(a), math.cos(a), 0], [0, 0, 1]])
     mr = np.einsum("ab,bkji->akji", Rz, m)
     assert abs(topological_charge(mr, p) - Q) < 1e-12
+
+
+def test_mean_magnetisation_counts_present_cells_only():
+    """<m> is the average over present cells: a uniform state gives itself,
+    values stored in absent cells do not enter, and two layers magnetised
+    oppositely average to zero while each layer keeps its own direction."""
+    from oracle.observables import mean_magnetisation
+    grid = W.Grid(6, 5, 2, 1e-9, 1e-9, 1e-9)
+    mat = W.Material(Ms=8e5, A=1.3e-11, alpha=0.1)
+    Ms = np.full((2, 5, 6), 8e5)
+    Ms[:, 1, 2] = 0.0                    # a hole through both layers
+    Ms[1, 3, 4] = 0.0                    # and one in the top layer
+    p = Problem.from_workload(grid, W.with_cells(mat, {"Ms": Ms}))
+    m = np.zeros((3, 2, 5, 6))
+    m[0, 0] = 1.0
+    m[0, 1] = -1.0
+    m[:, :, 1, 2] = 0.0
+    m[2, :, 1, 2] = 1.0                  # garbage in the absent cells
+    m[0, 1, 3, 4] = 0.0
+    m[2, 1, 3, 4] = 1.0
+    n0, n1 = 29, 28
+    assert np.allclose(mean_magnetisation(m, p, 0), (1, 0, 0), atol=1e-15)
+    assert np.allclose(mean_magnetisation(m, p, 1), (-1, 0, 0), atol=1e-15)
+    assert np.allclose(mean_magnetisation(m, p), ((n0 - n1) / (n0 + n1), 0, 0), atol=1e-15)
+    q = np.zeros_like(m)
+    q[1] = 1.0
+    assert np.allclose(mean_magnetisation(q, p), (0, 1, 0), atol=1e-15)
+    none = Problem.from_workload(grid, W.with_cells(mat, {"Ms": np.zeros((2, 5, 6))}))
+    assert np.all(mean_magnetisation(m, none) == 0)
