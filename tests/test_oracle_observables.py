@@ -103,3 +103,47 @@ def test_mean_magnetisation_counts_present_cells_only():
     assert np.allclose(mean_magnetisation(q, p), (0, 1, 0), atol=1e-15)
     none = Problem.from_workload(grid, W.with_cells(mat, {"Ms": np.zeros((2, 5, 6))}))
     assert np.all(mean_magnetisation(m, none) == 0)
+
+
+def _two_wall_chain(dx, n, D, sense):
+    """Periodic chain holding two Neel walls of the same rotation sense
+    (m = (sin t, 0, cos t), t winding by 2 pi * sense), and the uniform
+    state, on a grid periodic in y too (no free face where the interfacial
+    DMI condition would act)."""
+    A, K = 1.5e-11, 8e5
+    grid = W.Grid(n, 1, 1, dx, 1e-9, 1e-9, (1, 1, 0))
+    p = Problem.from_workload(grid, W.Material(Ms=5.8e5, A=A, alpha=0.1, Ku1=K, u=(0, 0, 1), D=D))
+    delta = math.sqrt(A / K)
+    x = (np.arange(n) + 0.5) * dx
+    L = n * dx
+    t = sense * (2 * np.arctan(np.exp((x - L / 4) / delta)) + 2 * np.arctan(np.exp((x - 3 * L / 4) / delta)))
+    m = np.zeros((3, 1, 1, n))
+    m[0, 0, 0] = np.sin(t)
+    m[2, 0, 0] = np.cos(t)
+    u = np.zeros_like(m)
+    u[2] = 1.0
+    terms = ("exchange", "dmi", "anisotropy")
+    area = grid.dy * grid.dz
+    return (energy(m, p, terms=terms)["total"] - energy(u, p, terms=terms)["total"]) / area / 2
+
+
+@pytest.mark.parametrize("D", [0.0, 1e-3, 3e-3])
+def test_neel_wall_energy_and_the_critical_dmi(D):
+    """The wall energy per area behind the paper's analytic critical DMI
+    D_c = 4 sqrt(AK)/pi (Results, skyrmion D-K phase diagram): a Neel wall of
+    the sense the interfacial DMI favours costs 4 sqrt(AK) - pi|D|, the other
+    sense 4 sqrt(AK) + pi|D|; on the lattice the profile's energy converges
+    to these at second order in the cell size."""
+    A, K = 1.5e-11, 8e5
+    s0 = 4 * math.sqrt(A * K)
+    scale = s0 + math.pi * abs(D)
+    errs = []
+    for dx, n, tol in [(0.5e-9, 400, 1.2e-3), (0.25e-9, 800, 3e-4)]:
+        fav = _two_wall_chain(dx, n, D, sense=-1)       # t decreasing: favoured for D > 0
+        unfav = _two_wall_chain(dx, n, D, sense=+1)
+        errs.append(max(abs(fav - (s0 - math.pi * D)), abs(unfav - (s0 + math.pi * D))))
+        assert errs[-1] < tol * scale
+    assert errs[1] < 0.3 * errs[0]                      # second order in the cell size
+    Dc = s0 / math.pi
+    assert abs(_two_wall_chain(0.25e-9, 800, Dc, sense=-1)) < 2.5e-4 * s0
+    assert _two_wall_chain(0.25e-9, 800, 1.1 * Dc, sense=-1) < 0
