@@ -317,3 +317,43 @@ def test_adaptive_refuses_finite_temperature():
     grid, p, m = _film()
     with pytest.raises(ValueError):
         Solver(p, m, T=300.0).dm_adaptive_step()
+
+
+def test_trial_stop_step_is_the_switching_time_of_the_macrospin():
+    """Deterministic trials (T = 0) of a perpendicular STT macrospin with
+    p = -z, stopped at m_z <= 0: below the threshold current J_c0 a trial
+    runs out its steps; above it the stop step is the first step past the
+    time at which the polar angle, following its scalar equation (integrated
+    by scipy), reaches pi/2."""
+    from scipy.integrate import solve_ivp
+
+    Ms, Ku, alpha, P, Lam, dz, dt = 1e6, 1e6, 0.02, 0.6, 2.0, 1e-9, 1e-13
+    grid = W.Grid(1, 1, 1, 2e-9, 2e-9, dz)
+    p = Problem.from_workload(grid, W.Material(Ms=Ms, A=1e-11, alpha=alpha, Ku1=Ku, u=(0, 0, 1)))
+    HK, L2 = 2 * Ku / (MU0 * Ms), Lam ** 2
+    Jc0 = alpha * HK * QE * MU0 * Ms * dz / (HBAR * P * L2 / 2)
+    mult = np.array([0.5, 2.0, 3.0])
+    th0 = 0.1
+    m0 = np.array([math.sin(th0), 0.0, math.cos(th0)]).reshape(3, 1, 1, 1)
+    spec = TrialSpec(p=p, m_init=m0, J=mult * Jc0, T=np.zeros(3), terms=("anisotropy",),
+                     torque=Torque(kind="stt", p=(0, 0, -1), P=P, Lambda=Lam), dt=dt, axis=(0, 0, 1),
+                     threshold=0.0, max_steps=8000, integrator="dm")
+    gp = GAMMA0 / (1 + alpha ** 2)
+    for q in range(3):
+        n, stopped, m = run_trial(spec, q)
+        if mult[q] < 1:
+            assert not stopped and n == spec.max_steps and m[2, 0, 0, 0] > math.cos(th0)
+            continue
+        base = HBAR * mult[q] * Jc0 / (QE * MU0 * Ms * dz)
+
+        def rhs(_, y, base=base):
+            eps = P * L2 / ((L2 + 1) - (L2 - 1) * math.cos(y[0]))
+            return [gp * MU0 * math.sin(y[0]) * (eps * base - alpha * HK * math.cos(y[0]))]
+
+        def half(_, y):
+            return y[0] - math.pi / 2
+        half.terminal = True
+        t_star = solve_ivp(rhs, (0, spec.max_steps * dt), [th0], rtol=1e-12, atol=1e-14,
+                           events=half).t_events[0][0]
+        assert stopped and m[2, 0, 0, 0] <= 0
+        assert abs(n - t_star / dt) < 3
