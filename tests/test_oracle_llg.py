@@ -261,3 +261,48 @@ def test_stt_macrospin_polar_angle_follows_its_scalar_equation(J_over_Jc0, eps_p
     th = math.acos(float(s.m[2, 0, 0, 0]))
     assert abs(th - ref) < 1e-7
     assert (th > th0) == (J_over_Jc0 > 1)
+
+
+def test_zhang_li_wall_velocity_follows_the_one_dimensional_model():
+    """A wall in a uniaxial chain (no transverse anisotropy, so no Walker
+    limit) driven by the Zhang-Li torque moves steadily at
+    v = u (1 + alpha xi) / (1 + alpha^2) while its plane precesses at
+    |xi - alpha| u / (delta (1 + alpha^2)) (the rigid-profile solution of the
+    collective-coordinate equations).  alpha = 0.5 makes the xi dependence
+    large; the common lattice factor of the central difference
+    (about -(dx/delta)^2/6) cancels in the ratios."""
+    from oracle.constants import MU_B, QE
+    n, dx = 200, 1e-9
+    Ms, A, K, alpha = 8e5, 1.3e-11, 5e5, 0.5
+    grid = W.Grid(n, 1, 1, dx, dx, dx)
+    p = Problem.from_workload(grid, W.Material(Ms=Ms, A=A, alpha=alpha, Ku1=K, u=(0, 0, 1)))
+    delta = math.sqrt(A / K)
+    x = (np.arange(n) - n / 2 + 0.5) * dx
+    th = 2 * np.arctan(np.exp(x / delta))
+    m = np.zeros((3,) + p.shape)
+    m[1, 0, 0] = np.sin(th)
+    m[2, 0, 0] = np.cos(th)
+    s = Solver(p, m, terms=("exchange", "anisotropy"), dt=1e-14, rtol=1e-8)
+    while s.t < 20e-12:
+        s.rk45_step()
+    m_rel = s.m.copy()
+    J, P = 2e12, 0.5
+    u = J * P * MU_B / (QE * Ms)
+    v = {}
+    for xi in (0.0, 0.5, 1.0):
+        s = Solver(p, m_rel, terms=("exchange", "anisotropy"), dt=1e-14, rtol=1e-8,
+                   torque=Torque(kind="zl", J=J, P=P, xi=xi))
+        mz0 = s.m[2].mean()
+        phi0 = math.atan2(s.m[1].sum(), s.m[0].sum())            # azimuth of the wall's moment
+        while s.t < 50e-12:
+            s.rk45_step()
+        v[xi] = -(s.m[2].mean() - mz0) * n * dx / 2 / s.t       # <mz> = 2 x_centre / L
+        lattice = 1 - (dx / delta) ** 2 / 6
+        assert abs(v[xi] / (u * lattice * (1 + alpha * xi) / (1 + alpha ** 2)) - 1) < 2e-3, (xi, v[xi])
+        # the wall drifts along -x (as the rigid translation at xi = alpha
+        # shows), so for this wall the plane turns at -(xi - alpha) u / (delta (1 + alpha^2))
+        rate = (math.atan2(s.m[1].sum(), s.m[0].sum()) - phi0) / s.t
+        want = -(xi - alpha) * u / (delta * (1 + alpha ** 2))
+        assert abs(rate - want) < 2e-3 * u / delta, (xi, rate, want)
+    assert abs(v[1.0] / v[0.0] - (1 + alpha)) < 1e-4
+    assert abs(v[0.5] / v[0.0] - (1 + alpha * 0.5)) < 1e-4
