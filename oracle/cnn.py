@@ -10,11 +10,11 @@ exact FFT convolution.  Convolutions are cross-correlations:
 
     y[co, i, j] = b[co] + sum_ci sum_{p,q in -2..2} w[co, ci, p+2, q+2] x[ci, i+p, j+q]
 
-Parity status: this network has no closed form; its forward pass is pinned
-against scipy's correlate2d and its gradients against finite differences
-of its own loss ("parity unpinned" in physics terms: the surrogate is a
-learned approximation whose error is measured against the exact demag
-field).
+Parity status: the operations are pinned (the forward pass against scipy's
+correlate2d, the gradients against finite differences of the loss, Adam's
+first step and BF16 rounding by their definitions).  A trained network's
+predictions have no closed form: their error is measured against the exact
+demagnetising field, not held to a parity bar.
 """
 from __future__ import annotations
 
