@@ -150,7 +150,7 @@ typedef struct mm_config {
     uint64_t seed;            /* base Philox seed; replica r uses splitmix64(seed + r) */
 } mm_config;
 
-/* Spin-torque parameters (Methods: torques added per integrator stage).
+/* Spin-torque parameters (Methods: the torques enter every integrator stage).
  * Landau-Lifshitz form with damping-like h_DL and field-like h_FL along p:
  *   tau = -gamma' mu0 [(h_DL + alpha h_FL) m x (m x p) + (h_FL - alpha h_DL) m x p]
  *  SOT: h_DL = theta_SH hbar J / (2 e mu0 Ms t_F), h_FL = fl_ratio * h_DL

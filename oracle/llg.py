@@ -3,7 +3,7 @@
 Methods, "Physics and discretization", Eq. 1:
     dm/dt = -gamma' mu0 (m x H) - gamma' alpha mu0 m x (m x H),
     gamma' = gamma0 / (1 + alpha^2),
-with spin torques "added per integrator stage" (Slonczewski STT, spin-orbit
+with the spin torques entering every integrator stage (Slonczewski STT, spin-orbit
 torque, Zhang-Li), and Methods, "Integrators": Heun (stochastic LLG,
 Stratonovich: the same thermal field in predictor and corrector), RK45
 Dormand-Prince (adaptive, first-same-as-last), classical RK4 and the

@@ -1,5 +1,5 @@
 // Fused effective field + LLG torque + stage update (Methods, "Physics and
-// discretization", Eq. 1; spin torques "added per integrator stage").
+// discretization", Eq. 1; the spin torques enter every integrator stage).
 //
 // One thread per cell.  The six-point exchange Laplacian, interfacial DMI
 // (central differences; at an absent neighbour in the plane the ghost value

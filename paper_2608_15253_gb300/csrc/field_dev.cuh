@@ -1,6 +1,6 @@
 // Per-cell effective field and LLG torque shared by the single-instance
 // field kernel and the replica-batched stage kernel (Methods, "Physics and
-// discretization", Eq. 1; torques "added per integrator stage").
+// discretization", Eq. 1; the spin torques enter every integrator stage).
 #pragma once
 
 #include <cuda_runtime.h>
