@@ -66,8 +66,8 @@ typedef enum mm_status {
  * Omega(predictor); one thermal draw serves both.  Rotations keep |m| = 1;
  * the corrector also rescales by 1/|m| (a round-off-level change). */
 enum mm_integrator { MM_HEUN = 0, MM_RK45 = 1, MM_RK4 = 2, MM_DM = 3, MM_DM_ADAPTIVE = 4 };
-/* MM_DM_ADAPTIVE (Methods: the Depondt-Mertens scheme, "optionally
- * adaptive"; T = 0 only): the predictor m* (first order) and the corrector
+/* MM_DM_ADAPTIVE (Methods: the Depondt-Mertens scheme run with an adaptive
+ * step; T = 0 only): the predictor m* (first order) and the corrector
  * (second order) form an embedded pair, err = max over cells |m_new - m*|;
  * accept when err <= rtol; dt *= clamp(0.9 (rtol/err)^(1/2), 0.2, 5), capped
  * at 1 after a rejection, within [dt_min, dt_max]; the controller runs on

@@ -24,7 +24,7 @@ converted to Eq. 1's Landau-Lifshitz form they read
    (u.grad)m by central differences with the absent neighbour taken as the
    cell itself.
 
-Integrator readings (the paper says only "adaptive, first-same-as-last"):
+Integrator readings (the paper names only an adaptive DOPRI5 with FSAL reuse):
 stages are not renormalised; err = max over cells of |m5 - m4|_2; accept
 when err <= rtol; dt_new = dt * clamp(0.9 (rtol/err)^(1/5), 0.2, 5), with
 the factor capped at 1 on the step after a rejection; dt clamped to
@@ -296,8 +296,8 @@ class Solver:
         self.accepted += 1
 
     def dm_adaptive_step(self):
-        """Methods, "Integrators": the Depondt-Mertens scheme, "optionally
-        adaptive".  Reading (the paper gives no controller): the predictor
+        """Methods, "Integrators": the Depondt-Mertens scheme, which the paper
+        allows to run adaptively.  Reading (it gives no controller): the predictor
         m* (a first-order rotation) and the corrector m_{n+1} (second order)
         form an embedded pair; err = max over cells |m_{n+1} - m*|; accept
         when err <= rtol; dt_new = dt * clamp(0.9 (rtol/err)^(1/2), 0.2, 5),
