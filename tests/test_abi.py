@@ -52,3 +52,17 @@ def test_create_rejects_bad_arguments_before_touching_the_device():
     with pytest.raises(mm.MMError) as e:
         mm.mm_create(g, m.s, mm.make_config(integrator=mm.MM_RK45, T=300.0))
     assert e.value.status == mm.MM_ERR_ARG
+
+
+def test_observables_reject_a_null_context_without_a_device():
+    import ctypes
+
+    import numpy as np
+
+    import paper_2608_15253_gb300 as mm
+    lib = mm.load()
+    out = np.zeros(16)
+    p = out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert lib.mm_mean_m(None, 0, -1, p) == mm.MM_ERR_ARG
+    assert lib.mm_topo_charge(None, 0, -1, p) == mm.MM_ERR_ARG
+    assert lib.mm_energy(None, 0, p) == mm.MM_ERR_ARG
