@@ -203,7 +203,9 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "cells": w.grid.n, "grid": [w.grid.nx, w.grid.ny, w.grid.nz],
                    "cell_nm": [2, 2, 2], "integrator": "rk45-dopri5", "rtol": w.rtol,
-                   "precision": "fp64-cpu-oracle", "sample_grid": list(shape)},
+                   "demag": f"exact-fft {2*shape[0]}x{2*shape[1]}x{2*shape[2]} (sample grid)",
+                   "precision": "fp64-cpu-oracle", "parallelism": "one CPU thread (rank 0)",
+                   "sample_grid": list(shape)},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
