@@ -192,6 +192,33 @@ def h_demag(m: np.ndarray, p, K_hat: np.ndarray) -> np.ndarray:
     return H
 
 
+def h_demag_at(m: np.ndarray, p, targets, octant=None) -> np.ndarray:
+    """H at the listed target cells, rows (k, j, i), by the double sum of the
+    definition over every source cell: -sum_{r'} sum_b N_ab(r - r') Ms m_b(r').
+    The tensor at a displacement with negative components is the octant
+    entry at its absolute value times each component's parity, which is
+    what lets large grids be sampled (one octant, then one O(N) sum per
+    target).  Returns (len(targets), 3)."""
+    nz, ny, nx = p.shape
+    if octant is None:
+        octant = newell_octant(p.shape, p.d)
+    M = p.Ms[None] * m
+    out = np.zeros((len(targets), 3))
+    for n, (kt, jt, it) in enumerate(targets):
+        dk, dj, di = kt - np.arange(nz), jt - np.arange(ny), it - np.arange(nx)   # target - source
+        N = []
+        for c in range(6):
+            px, py, pz = _PARITY[c]
+            sx = np.where(di < 0, px, 1.0)
+            sy = np.where(dj < 0, py, 1.0)
+            sz = np.where(dk < 0, pz, 1.0)
+            N.append(octant[c][np.ix_(np.abs(dk), np.abs(dj), np.abs(di))]
+                     * sz[:, None, None] * sy[None, :, None] * sx[None, None, :])
+        for a in range(3):
+            out[n, a] = -sum(float(np.vdot(N[COMP[(a, b)]], M[b])) for b in range(3))
+    return out
+
+
 def h_demag_direct(m: np.ndarray, p) -> np.ndarray:
     """Brute-force double sum over all target/source pairs (tiny grids only)."""
     nz, ny, nx = p.shape

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from oracle.demag import demag_spectrum, h_demag, h_demag_direct, newell_octant
+from oracle.demag import demag_spectrum, h_demag, h_demag_at, h_demag_direct, newell_octant
 from oracle.fields import Problem
 
 
@@ -31,6 +31,34 @@ def test_fft_convolution_equals_direct_sum(shape, cell):
     H_dir = h_demag_direct(m, p)
     scale = np.abs(H_dir).max()
     assert np.max(np.abs(H_fft - H_dir)) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("shape,cell", [((5, 4, 3), (3e-9, 2e-9, 2.5e-9)), ((6, 1, 1), (2e-9, 1e-9, 1e-9))])
+def test_sampled_direct_sum_equals_brute_force(shape, cell):
+    """The per-target sum with the parity-extended octant is the brute-force
+    double sum (which evaluates the tensor at every signed displacement) at
+    every cell, holes and several materials included."""
+    nx, ny, nz = shape
+    grid = W.Grid(nx, ny, nz, *cell)
+    p = _problem(grid, seed=nx + 7 * ny)
+    m = W.random_m(grid, seed=11)
+    H_dir = h_demag_direct(m, p)
+    targets = [(k, j, i) for k in range(nz) for j in range(ny) for i in range(nx)]
+    H_at = h_demag_at(m, p, targets)
+    ref = np.stack([H_dir[:, k, j, i] for (k, j, i) in targets])
+    assert np.max(np.abs(H_at - ref)) <= 1e-12 * np.abs(ref).max()
+
+
+def test_sampled_direct_sum_uniform_cube_centre():
+    """Independently of the brute-force route: the centre of a uniformly
+    magnetised 5x5x5 cube of cubic cells sees -Ms m / 3 (cubic symmetry and
+    the trace identity), for m along each axis and along a diagonal."""
+    grid = W.Grid(5, 5, 5, 2e-9, 2e-9, 2e-9)
+    p = _problem(grid, holes=False)
+    for u in ((1.0, 0, 0), (0, 1.0, 0), (0, 0, 1.0), (0.6, 0.0, 0.8)):
+        m = np.broadcast_to(np.array(u)[:, None, None, None], (3, 5, 5, 5)).copy()
+        H = h_demag_at(m, p, [(2, 2, 2)])[0]
+        assert np.allclose(H, -8e5 * np.array(u) / 3.0, rtol=0, atol=1e-9 * 8e5)
 
 
 @pytest.mark.parametrize("n", [3, 5, 7])
