@@ -213,6 +213,15 @@ bool demag_stage_fusable(const mm_ctx* c);
 void demag_apply_stage(mm_ctx* c, int stage, void* Hd);
 mm_status newell_gpu(long count, const int* ijk, double dx, double dy, double dz, double* out_host);
 
+// conv_split.cu: middle pass for lines split over several threads (FP32)
+bool split_conv_supported(int L);
+cudaError_t split_conv_setup();
+void split_conv_launch_3d(mm_ctx* c, void* spec, const void* khat, int nz, int Py, int Pz, int Kx, int Wk,
+                          double bytes);
+void split_conv_launch_2d(mm_ctx* c, void* spec, const void* khat, int ny, int Py, int Kx, int Wk,
+                          long long comp_stride, long long plane_stride, int n_planes, const char* name,
+                          double bytes);
+
 // field.cu
 // MODE_DM1 / MODE_DM2: Depondt-Mertens predictor (out <- rotated m, out2 <-
 // Omega) and corrector (out <- m0 rotated by the mean Omega, k1 = Omega_1)

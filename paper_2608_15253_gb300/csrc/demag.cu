@@ -1179,6 +1179,9 @@ static void demag_apply_t(mm_ctx* c, const T* m, T* Hd, int stage = 0) {
                            3.0 * d.Py * d.Kx * 2 * nz * cplxb + (double)d.ncomp * Kz * Ky * d.Kx * realb);
             zconv_reg_kernel(d.Pz, 2 * nz <= d.Pz)<<<(unsigned)((cols + kZT - 1) / kZT), 3 * kZT, zconv_reg_smem(d.Pz),
                                                       c->stream>>>(z);
+        } else if (three_d && sizeof(T) == 4 && split_conv_supported(d.Pz)) {
+            split_conv_launch_3d(c, S, d.khat, nz, d.Py, d.Pz, d.Kx, d.Wk,
+                                 3.0 * d.Py * d.Kx * 2 * nz * cplxb + (double)d.ncomp * Kz * Ky * d.Kx * realb);
         } else if (three_d) {
             a.line_stride = plane; a.other_stride = d.Wk;
             a.L = d.Pz; a.n_in = nz; a.n_out = nz;
@@ -1187,6 +1190,9 @@ static void demag_apply_t(mm_ctx* c, const T* m, T* Hd, int stage = 0) {
             a.L_other = d.Py; a.axis_is_y = 0;
             launch_col<T, 0>(c, a, d.Py, "fft_conv",
                              3.0 * d.Py * d.Kx * 2 * nz * cplxb + (double)d.ncomp * Kz * Ky * d.Kx * realb);
+        } else if (sizeof(T) == 4 && split_conv_supported(d.Py)) {
+            split_conv_launch_2d(c, S, d.khat, ny, d.Py, d.Kx, d.Wk, comp, 3 * comp, 1, "fft_conv",
+                                 3.0 * d.Kx * 2 * ny * cplxb + (double)d.ncomp * Ky * d.Kx * realb);
         } else {
             a.line_stride = d.Wk; a.other_stride = plane;
             a.L = d.Py; a.n_in = ny; a.n_out = ny;
@@ -1225,7 +1231,10 @@ void demag_apply_stacked2d(mm_ctx* c, const DemagPlan& p, const float* m, float*
     const double cplxb = sizeof(cplx<float>), realb = sizeof(float);
     launch_x<float>(c, true, m, nullptr, Sp, 3 * ny * Rc, ny, p.PyA, nx, nx, p.Lh, (const cplx<float>*)p.tw_x, true,
                     N);
-    {
+    if (split_conv_supported(p.Py)) {
+        split_conv_launch_2d(c, Sp, p.khat, ny, p.Py, p.Kx, p.Wk, plane, 3 * plane, Rc, "fft_conv_stacked",
+                             Rc * (3.0 * p.Kx * 2 * ny * cplxb) + (double)p.ncomp * (p.Py / 2 + 1) * p.Kx * realb);
+    } else {
         ColArgs<float> a{};
         a.base = Sp; a.comp_stride = plane; a.nc = 3; a.Kx = p.Kx;
         a.khat = (const float*)p.khat;
@@ -1414,6 +1423,7 @@ mm_status demag_setup(mm_ctx* c) {
         tw32[q] = make_float2((float)std::cos(ang), (float)std::sin(ang));
     }
     cudaError_t e = cudaMemcpyToSymbol(c_tw32, tw32, sizeof tw32);
+    if (e == cudaSuccess) e = split_conv_setup();
     if (e != cudaSuccess) return cuda_check(c, e, "twiddle table");
     e = fft_attributes<float>();
     if (e == cudaSuccess) e = fast_attributes();

@@ -124,6 +124,20 @@ DEMAG_GRIDS = [
     W.Grid(200, 20, 2, 2e-9, 2e-9, 2e-9),
     W.Grid(150, 24, 24, 3e-9, 3e-9, 3e-9),
     W.Grid(300, 150, 1, 2e-9, 2e-9, 1e-9),
+    # middle pass split over several threads per line (four-step): padded z
+    # lengths 64 / 81 (n_in at its maximum 41) / 96 / 128 / 81 (ragged n_in),
+    # padded y lengths (2-D) 32 / 64 / 128 / 192 / 256 / 512
+    W.Grid(12, 10, 32, 2e-9, 2e-9, 2e-9),
+    W.Grid(9, 6, 41, 3e-9, 3e-9, 3e-9),
+    W.Grid(10, 8, 48, 2e-9, 2e-9, 1e-9),
+    W.Grid(6, 5, 64, 3e-9, 3e-9, 3e-9),
+    W.Grid(7, 4, 37, 2e-9, 3e-9, 2e-9),
+    W.Grid(16, 16, 1, 2e-9, 2e-9, 1e-9),
+    W.Grid(20, 32, 1, 2e-9, 2e-9, 1e-9),
+    W.Grid(30, 64, 1, 2e-9, 2e-9, 1e-9),
+    W.Grid(12, 96, 1, 2e-9, 2e-9, 1e-9),
+    W.Grid(9, 128, 1, 2e-9, 2e-9, 1e-9),
+    W.Grid(6, 256, 1, 2e-9, 2e-9, 1e-9),
 ]
 
 
