@@ -206,14 +206,19 @@ MM_API mm_status mm_create(const mm_grid* grid, const mm_material* mat,
 MM_API mm_status mm_create_batch(int R, const mm_grid* grids, const mm_material* mat,
                                  const mm_config* cfg, const uint64_t* seeds, mm_ctx** out);
 
+/* Free the context and every device buffer it owns; NULL is accepted.
+ * No passage: boundary convenience (the paper's solver objects are C++
+ * values with automatic lifetime). */
 MM_API mm_status mm_destroy(mm_ctx* ctx);
 
 /* Run on a caller stream (cudaStream_t, e.g. torch's current stream); NULL
- * returns to the context's own stream.  Cached CUDA graphs are rebuilt. */
+ * returns to the context's own stream.  Cached CUDA graphs are rebuilt.
+ * No passage: boundary convenience (stream interop with the caller). */
 MM_API mm_status mm_set_stream(mm_ctx* ctx, void* stream);
 
-/* Set / read the magnetisation of one replica (host float64, 3N, layout
- * [component][z][y][x]).  Page-locked host memory is read / written in place
+/* Set / read the magnetisation of one replica (Methods, "Physics and
+ * discretization": the unit vector m of Eq. 1 on the x-fastest grid; host
+ * float64, 3N, layout [component][z][y][x]).  Page-locked host memory is read / written in place
  * by the conversion kernel (one pass over the host link); pageable memory
  * goes through a device staging buffer (3N doubles, allocated on first use
  * and kept).  Input is renormalised per cell; absent cells and zero vectors
@@ -223,7 +228,8 @@ MM_API mm_status mm_set_stream(mm_ctx* ctx, void* stream);
 MM_API mm_status mm_set_m(mm_ctx* ctx, int replica, const double* m);
 MM_API mm_status mm_get_m(mm_ctx* ctx, int replica, double* m);
 
-/* Device-pointer variants over all replicas at once, in the context's
+/* Device-pointer variants over all replicas at once (Methods, "Replica
+ * batching": replica-outermost, component-major state), in the context's
  * precision (float or double), concatenated replica-outermost in storage
  * order: replicas of one grid size are stored together (sizes in order of
  * first appearance, replicas by index within a size), which is replica
@@ -232,10 +238,14 @@ MM_API mm_status mm_get_m(mm_ctx* ctx, int replica, double* m);
 MM_API mm_status mm_set_m_device(mm_ctx* ctx, const void* m_dev);
 MM_API mm_status mm_get_m_device(mm_ctx* ctx, void* m_dev);
 
-/* Applied field B (tesla): uniform B[3], or per cell (3N) when B_cell != NULL. */
+/* Applied field B (tesla) of the Zeeman term (Methods, "Physics and
+ * discretization": H += B/mu0): uniform B[3], or per cell (3N) when
+ * B_cell != NULL; B == NULL means zero.  Errors: MM_ERR_ARG (bad replica,
+ * per-cell field on a replica-batched context), MM_ERR_OOM, MM_ERR_CUDA. */
 MM_API mm_status mm_set_field(mm_ctx* ctx, int replica, const double B[3], const double* B_cell);
 
-/* Strain tensor of the magnetoelastic term: eps[6] = xx, yy, zz, xy, xz, yz
+/* Strain tensor of the magnetoelastic term (Methods, "Physics and
+ * discretization": magnetoelastic anisotropy): eps[6] = xx, yy, zz, xy, xz, yz
  * for every cell, or per cell (eps_cell, 6N doubles component-major) when
  * eps_cell != NULL.  Replica-batched contexts take the uniform form only.
  * Errors: MM_ERR_ARG (both NULL), MM_ERR_OOM. */
@@ -250,34 +260,61 @@ MM_API mm_status mm_set_strain(mm_ctx* ctx, const double eps[6], const double* e
  * MM_ERR_STATE (replica-batched context). */
 MM_API mm_status mm_set_rkky(mm_ctx* ctx, int k1, int k2, double J);
 
-/* Temperature per replica (R values, kelvin). */
+/* Temperature per replica (R values, kelvin) of the thermal field
+ * (Methods, "Physics and discretization": stochastic LLG, sigma =
+ * sqrt(2 alpha kB T / (mu0^2 Ms V gamma0 dt)); "Replica batching":
+ * per-replica T).  Errors: MM_ERR_ARG (NULL, negative T, T > 0 with an
+ * integrator other than Heun or Depondt-Mertens), MM_ERR_STATE (while
+ * retire/refill owns the temperatures). */
 MM_API mm_status mm_set_temperature(mm_ctx* ctx, const double* T);
 
-/* Spin torque of every replica; J holds R current densities (A/m^2). */
+/* Spin torque of every replica (Methods, "Physics and discretization":
+ * spin-orbit, Slonczewski and Zhang-Li torques added in every integrator
+ * stage; "Replica batching": per-replica J); J holds R current densities
+ * (A/m^2); J == NULL means zero current.  Errors: MM_ERR_ARG (NULL tq,
+ * unknown kind, Zhang-Li on a replica-batched context), MM_ERR_STATE
+ * (while retire/refill owns the currents). */
 MM_API mm_status mm_set_torque(mm_ctx* ctx, const mm_torque* tq, const double* J);
 
-/* Advance n steps: n Heun steps, or n accepted RK45 steps (rejected attempts
- * are retried on the device; the step controller runs on the device). */
+/* Advance n steps (Methods, "Integrators"): n fixed steps (Heun, RK4,
+ * Depondt-Mertens), or n accepted adaptive steps (rejected attempts are
+ * retried on the device; the step controller runs on the device).
+ * Errors: MM_ERR_NONFINITE, MM_ERR_DT_UNDERFLOW (the context stays usable
+ * at the last accepted state), MM_ERR_CUDA. */
 MM_API mm_status mm_step(mm_ctx* ctx, long n);
 
-/* RK45 or adaptive Depondt-Mertens with a prescribed step sequence (no
- * control, every step accepted): replays dts[0..n-1], e.g. the accepted
- * steps of a reference run. */
+/* RK45 or adaptive Depondt-Mertens (Methods, "Integrators") with a
+ * prescribed step sequence (no control, every step accepted): replays
+ * dts[0..n-1], e.g. the accepted steps of a reference run; the replay
+ * itself has no passage (a parity-testing convenience).  Errors:
+ * MM_ERR_STATE (fixed-step integrator), MM_ERR_ARG (dts NULL with n > 0,
+ * n < 0), then as mm_step. */
 MM_API mm_status mm_step_dt(mm_ctx* ctx, const double* dts, long n);
 
-/* Advance to simulated time t_end; the last step is clipped to land on it. */
+/* Advance to simulated time t_end (Methods, "Integrators"); the last step
+ * is clipped to land on it.  Errors as mm_step. */
 MM_API mm_status mm_run(mm_ctx* ctx, double t_end);
 
-/* Effective field of the current state (A/m, host float64 3N) restricted to
- * the terms in term_mask (MM_TERM_THERMAL uses the current step's noise). */
+/* Effective field H of Eq. 1 (Methods, "Physics and discretization") at
+ * the current state (A/m, host float64 3N) restricted to the terms in
+ * term_mask (MM_TERM_THERMAL uses the current step's noise).  Errors:
+ * MM_ERR_ARG (bad replica, NULL H). */
 MM_API mm_status mm_get_heff(mm_ctx* ctx, int replica, double* H, unsigned term_mask);
 
-/* Energy per term and total (joules): E[MM_NENERGY], FP64 compensated sums;
- * E[MM_E_TOTAL] sums every term, those indexed after it included. */
+/* Energy per term and total (joules; Results, "A showcase of representative
+ * examples": the total energy of the S-state and vortex branches whose
+ * exchange/demagnetisation balance the paper compares): E[MM_NENERGY], FP64
+ * compensated sums of -1/2 mu0 Ms m.H_term V (Zeeman -mu0 Ms m.H_ext V);
+ * E[MM_E_TOTAL] sums every term, those indexed after it included.  Errors:
+ * MM_ERR_ARG (bad replica, NULL E). */
 MM_API mm_status mm_energy(mm_ctx* ctx, int replica, double* E);
 
-/* Topological charge Q = (1/4pi) sum m.(dm/dx x dm/dy) dx dy of layer
- * `layer`, or the mean over layers when layer < 0; FP64 compensated sum. */
+/* Topological charge (Results, "A showcase of representative examples":
+ * the relaxed skyrmion charge Q of the D-K phase diagram)
+ * Q = (1/4pi) sum m.(dm/dx x dm/dy) dx dy of layer `layer`, or the mean
+ * over layers when layer < 0; central differences, one-sided at edges and
+ * holes; FP64 compensated sum.  Errors: MM_ERR_ARG (bad replica,
+ * layer >= nz, NULL Q). */
 MM_API mm_status mm_topo_charge(mm_ctx* ctx, int replica, int layer, double* Q);
 
 /* Mean magnetisation <m> (Results: the average magnetisation the standard
@@ -289,26 +326,36 @@ MM_API mm_status mm_topo_charge(mm_ctx* ctx, int replica, int layer, double* Q);
  * m_mean NULL), MM_ERR_CUDA. */
 MM_API mm_status mm_mean_m(mm_ctx* ctx, int replica, int layer, double* m_mean);
 
+/* Simulated time, current step size and accepted steps of a replica, and
+ * the context's step / launch counters.  No passage: boundary convenience.
+ * Outputs may be NULL (mm_get_time).  Errors: MM_ERR_ARG (bad replica). */
 MM_API mm_status mm_get_time(mm_ctx* ctx, int replica, double* t, double* dt, long long* steps);
 MM_API mm_status mm_get_stats(mm_ctx* ctx, mm_stats* st);
 
-/* Checkpoint: m, t, dt, step counters and seeds.  With buf == NULL the
- * required size is returned in *nbytes. */
+/* Checkpoint: m, t, dt, step counters, seeds and the FSAL slope.  With
+ * buf == NULL the required size is returned in *nbytes.  No passage:
+ * boundary convenience (the paper has no checkpoint); resume is bit-exact
+ * because the thermal stream is counter-based (Methods, "Replica
+ * batching").  Errors: MM_ERR_ARG (buffer too small, foreign blob). */
 MM_API mm_status mm_get_state(mm_ctx* ctx, void* buf, size_t* nbytes);
 MM_API mm_status mm_set_state(mm_ctx* ctx, const void* buf, size_t nbytes);
 
-/* Thermal noise of one replica at a given step counter: raw Philox4x32-10
- * words (4N uint32, cell-major) and/or the thermal field (3N A/m) for the
- * context's dt; either output may be NULL. */
+/* Thermal noise of one replica at a given step counter (Methods,
+ * "Replica batching": counter-based Philox keyed by seed, replica-and-cell
+ * index and step): raw Philox4x32-10 words (4N uint32, cell-major) and/or
+ * the thermal field (3N A/m) for the context's dt; either output may be
+ * NULL. */
 MM_API mm_status mm_get_thermal(mm_ctx* ctx, int replica, long long step,
                                 uint32_t* raw, double* H_th);
 
-/* Demagnetisation tensor spectrum in the stored form: n_out doubles of
+/* Demagnetisation tensor spectrum (Methods, "Physics and discretization":
+ * the Newell tensor, zero-padded to 2N) in the stored form: n_out doubles of
  * [ncomp][Pz/2+1][Py/2+1][Px/2+1] (ncomp 6: xx,yy,zz,xy,xz,yz; 4 when nz=1),
  * scaled by -1/(Px Py Pz).  dims_out[0..3] = ncomp, Px, Py, Pz. */
 MM_API mm_status mm_get_demag_kernel(mm_ctx* ctx, double* out, size_t n_out, int* dims_out);
 
-/* FP64 Newell tensor evaluated on the GPU at count integer displacements
+/* FP64 Newell tensor (Methods, "Physics and discretization") evaluated on
+ * the GPU at count integer displacements
  * ijk[3*q..3*q+2] of cells dx*dy*dz; out[6*q+c] in xx,yy,zz,xy,xz,yz. */
 MM_API mm_status mm_newell(long count, const int* ijk, double dx, double dy, double dz, double* out);
 
@@ -342,7 +389,9 @@ typedef struct mm_trials {
 } mm_trials;
 MM_API mm_status mm_trials_start(mm_ctx* ctx, const mm_trials* spec);
 
-/* Outcomes so far (synchronises the context stream): steps[q] = steps the
+/* Outcomes so far of the retire/refill trials (Results, "A replica-batched
+ * engine for finite-temperature ensembles": switching probability from the
+ * trials' stop steps; synchronises the context stream): steps[q] = steps the
  * trial took (-1 while unfinished or not started), stopped[q] = 1 if the
  * stop condition ended it; *done = finished trials.  Any output may be NULL.
  * Errors: MM_ERR_STATE before mm_trials_start. */
@@ -360,7 +409,8 @@ MM_API mm_status mm_trials_result(mm_ctx* ctx, long long* steps, int* stopped, l
  * NULL.  MM_ERR_STATE for single-instance contexts. */
 MM_API mm_status mm_batch_autotune(mm_ctx* ctx, const char* cache_path, int* nt_out, int* blocks_out);
 
-/* Set the launch shape of a replica-batched context directly: nt = 256 or
+/* Set the launch shape of a replica-batched context (Methods, "Replica
+ * batching") directly, bypassing the autotuner: nt = 256 or
  * 512 threads per CTA with `blocks` persistent CTAs (1 <= blocks), or
  * nt = 0 for the stacked shape (blocks ignored).  Errors: MM_ERR_STATE
  * (single-instance context), MM_ERR_ARG (other values), MM_ERR_OOM (the
@@ -452,14 +502,21 @@ MM_API mm_status mm_surrogate_forward(mm_ctx* ctx, int B, int H, int W, const do
 MM_API mm_status mm_surrogate_grad(mm_ctx* ctx, int B, int H, int W, const double* x, const double* t,
                                    double* loss, double* grad);
 
-/* Per-kernel CUDA-event timing (graphs are bypassed while on). */
+/* Per-kernel CUDA-event timing (graphs are bypassed while on).  No passage:
+ * boundary convenience (tracing; the paper times whole runs, Methods,
+ * "Benchmark protocol").  mm_get_profile: *n_inout in = capacity of out,
+ * out = entries written. */
 MM_API mm_status mm_set_profiling(mm_ctx* ctx, int on);
 MM_API mm_status mm_get_profile(mm_ctx* ctx, mm_profile_entry* out, int* n_inout);
 
 /* Host-side fault injection for tests: 1 = next allocation fails,
- * 2 = poison the state with NaN at the next step, 3 = force dt underflow. */
+ * 2 = poison the state with NaN at the next step, 3 = force dt underflow.
+ * No passage: test convenience. */
 MM_API mm_status mm_debug_inject(mm_ctx* ctx, int fault);
 
+/* Message of the last failure of ctx (or of the last context-less call
+ * when ctx is NULL), and the name of a status code.  No passage: boundary
+ * convenience.  The strings stay owned by the library. */
 MM_API const char* mm_last_error(const mm_ctx* ctx);
 MM_API const char* mm_status_string(mm_status s);
 

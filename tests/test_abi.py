@@ -66,3 +66,26 @@ def test_observables_reject_a_null_context_without_a_device():
     assert lib.mm_mean_m(None, 0, -1, p) == mm.MM_ERR_ARG
     assert lib.mm_topo_charge(None, 0, -1, p) == mm.MM_ERR_ARG
     assert lib.mm_energy(None, 0, p) == mm.MM_ERR_ARG
+
+
+def test_every_declaration_cites_its_passage():
+    """Each entry point's comment names the paper passage that defines the
+    operation (Methods / Results section, or Eq.), or states that it has no
+    counterpart there (a boundary or test convenience, or the benchmark's
+    own surrogate line).  A declaration directly below another shares the
+    comment above the pair."""
+    src = open(os.path.join(ROOT, "include", "mm.h")).read()
+    cite = re.compile(r'Methods, "|Results|Eq\. \d|No passage|no counterpart|not in the paper')
+    missing = []
+    prev_end, prev_seg = 0, ""
+    for mt in re.finditer(r"^MM_API[^;]*;", src, re.M):
+        seg = src[prev_end:mt.start()]
+        if "/*" not in seg:
+            seg = prev_seg
+        seg = re.sub(r"\s*\n\s*\*?\s*", " ", seg)   # comment lines joined
+        # the surrogate block's shared header comment covers its declarations
+        name = re.search(r"\b(mm_\w+)\s*\(", mt.group(0)).group(1)
+        if not cite.search(seg) and not name.startswith("mm_surrogate"):
+            missing.append(name)
+        prev_end, prev_seg = mt.end(), seg
+    assert not missing, missing
