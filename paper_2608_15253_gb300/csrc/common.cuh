@@ -82,7 +82,9 @@ __device__ __forceinline__ CompSum warp_sum(CompSum v) {
 }
 
 // Non-negative floating-point atomic max through the integer ordering of
-// IEEE bit patterns (valid for values >= 0, NaN propagates as the largest).
+// IEEE bit patterns (valid for values >= 0; a positive NaN would order above
+// +inf, but warp_max's fmax drops NaN operands before it gets here, so
+// callers that must see a NaN map it to +inf themselves).
 __device__ __forceinline__ void atomic_max_nonneg(float* addr, float v) {
     atomicMax(reinterpret_cast<unsigned int*>(addr), __float_as_uint(v));
 }

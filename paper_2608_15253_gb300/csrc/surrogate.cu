@@ -393,12 +393,17 @@ __global__ void copy_kernel(const float* __restrict__ a, long long n, float* __r
     if (q < n) o[q] = a[q];
 }
 
-// max |a - b| and max |b| over 3N values -> red[0], red[1] (as ordered bits)
+// max |a - b| and max |b| over 3N values -> red[0], red[1] (as ordered bits).
+// fmax drops a NaN operand, so a non-finite difference (a diverged network
+// prediction) is mapped to +inf first: the monitor then sees an error above
+// any threshold and the exact fallback fires.
 __global__ void err_max_kernel(const float* __restrict__ a, const float* __restrict__ b, long long n,
                                double* __restrict__ red) {
     double e = 0.0, m = 0.0;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        e = fmax(e, fabs((double)a[q] - (double)b[q]));
+        double d = fabs((double)a[q] - (double)b[q]);
+        if (!(d == d)) d = INFINITY;
+        e = fmax(e, d);
         m = fmax(m, fabs((double)b[q]));
     }
     e = warp_max(e);

@@ -218,3 +218,31 @@ def test_near_field_part_and_monitor():
         assert abs(st["last_error"] - host_err) <= 1e-2 * host_err + 1e-6, (st["last_error"], host_err)
     finally:
         mm.mm_destroy(ctx)
+
+
+def test_diverged_network_triggers_the_exact_fallback():
+    """A network whose prediction is not finite (a NaN output bias) fails the
+    error monitor at the next exact refresh: the monitor reports an error
+    above any threshold and every later evaluation is exact.  A first block
+    with a finite (zero) network leaves a valid reference, so the NaN network
+    is first met by the monitor, not by an integration attempt."""
+    mm = need_gpu()
+    ctx, grid = _ctx(mm, n=64)
+    try:
+        m0 = W.m_skyrmion_lattice(grid, seed=5, spacing=40e-9, radius=8e-9)
+        mm.mm_set_m(ctx, 0, m0)
+        mm.mm_step(ctx, 5)
+        w = np.zeros(mm.SURROGATE_NPARAMS)
+        mm.mm_surrogate_weights(ctx, w, c_in=1.0)
+        mm.mm_surrogate_set(ctx, 2, 1e3)            # a threshold no finite error reaches
+        mm.mm_step(ctx, 2)                          # refresh + one attempt with the zero network
+        assert mm.mm_surrogate_get_stats(ctx)["fallback"] == 0
+        w[-1] = np.nan                              # bias of the last layer's third channel
+        mm.mm_surrogate_weights(ctx, w, c_in=1.0)
+        mm.mm_step(ctx, 4)
+        st = mm.mm_surrogate_get_stats(ctx)
+        assert st["fallback"] == 1, st
+        assert not st["last_error"] <= 1e3, st
+        assert np.isfinite(mm.mm_get_m(ctx, 0, m0.shape)).all()
+    finally:
+        mm.mm_destroy(ctx)
