@@ -221,6 +221,9 @@ void split_conv_launch_3d(mm_ctx* c, void* spec, const void* khat, int nz, int P
 void split_conv_launch_2d(mm_ctx* c, void* spec, const void* khat, int ny, int Py, int Kx, int Wk,
                           long long comp_stride, long long plane_stride, int n_planes, const char* name,
                           double bytes);
+bool ysplit_supported(int L);
+void ysplit_launch(mm_ctx* c, bool fwd, void* spec, int nz, int Py, int Kx, int Wk, int n_in, int n_out,
+                   const char* name, double bytes);
 
 // field.cu
 // MODE_DM1 / MODE_DM2: Depondt-Mertens predictor (out <- rotated m, out2 <-

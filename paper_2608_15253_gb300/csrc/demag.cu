@@ -585,20 +585,23 @@ struct YArgs {
     const cplx<T>* tw;    // exp(-2 pi i q / Py)
 };
 
-constexpr int kYTK = 16;
-__host__ __device__ constexpr int y_direct_threads(int L) { return L >= 512 ? 512 : 256; }
+// Columns per CTA and threads: 16 columns, except at L >= 1024 where 8
+// columns of 256 threads (64 KB of shared memory) let three CTAs share an SM.
+__host__ __device__ constexpr int y_direct_tk(int L) { return L >= 1024 ? 8 : 16; }
+__host__ __device__ constexpr int y_direct_threads(int L) { return L >= 1024 ? 256 : L >= 512 ? 512 : 256; }
 
 template <typename T, int DIR, int L>
 __global__ void __launch_bounds__(y_direct_threads(L)) fft_y_direct_kernel(YArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw);
-    const int col = blockIdx.x * kYTK + (int)(threadIdx.x % kYTK);
+    constexpr int TK = y_direct_tk(L);
+    const int col = blockIdx.x * TK + (int)(threadIdx.x % TK);
     long long gcol = -1;
     if (col < a.ncols) {
         const int q = col / a.Kx, kx = col - q * a.Kx;
         gcol = (long long)q * a.plane + kx;
     }
-    cd_fft<T, DIR, L, y_direct_threads(L), kYTK>(sm, a.base, a.base, gcol, a.Wk, a.n_in, a.n_out, a.tw);
+    cd_fft<T, DIR, L, y_direct_threads(L), TK>(sm, a.base, a.base, gcol, a.Wk, a.n_in, a.n_out, a.tw);
 }
 
 // Middle (z) pass for Pz a power of two <= 32: one thread per (component,
@@ -1037,7 +1040,7 @@ static ZKern zconv_reg_kernel(int L, bool half) {
     }
 }
 
-static size_t y_direct_smem(int L) { return (size_t)L * kYTK * sizeof(cplx<float>); }
+static size_t y_direct_smem(int L) { return (size_t)L * y_direct_tk(L) * sizeof(cplx<float>); }
 static size_t zconv_reg_smem(int L) { return (size_t)(L + 3 * L * kZT) * sizeof(cplx<float>); }
 
 template <typename T>
@@ -1130,7 +1133,8 @@ static void launch_y_direct(mm_ctx* c, bool fwd, cplx<float>* S, long long plane
     a.n_in = n_in; a.n_out = n_out;
     a.tw = (const cplx<float>*)d.tw_y;
     LaunchScope ls(c, name, bytes);
-    y_direct_kernel(fwd, d.Py)<<<(unsigned)((a.ncols + kYTK - 1) / kYTK), y_direct_threads(d.Py), y_direct_smem(d.Py),
+    const int tk = y_direct_tk(d.Py);
+    y_direct_kernel(fwd, d.Py)<<<(unsigned)((a.ncols + tk - 1) / tk), y_direct_threads(d.Py), y_direct_smem(d.Py),
                                  c->stream>>>(a);
 }
 
@@ -1150,7 +1154,10 @@ static void demag_apply_t(mm_ctx* c, const T* m, T* Hd, int stage = 0) {
     const bool three_d = nz > 1;
     const bool fast_y = sizeof(T) == 4 && three_d && y_direct_kernel(true, d.Py) != nullptr;
     const bool fast_z = sizeof(T) == 4 && three_d && zconv_reg_kernel(d.Pz, false) != nullptr;
-    if (three_d && d.Py > 1 && fast_y) {
+    const bool split_y = sizeof(T) == 4 && three_d && ysplit_supported(d.Py);
+    if (three_d && d.Py > 1 && split_y) {
+        ysplit_launch(c, true, S, nz, d.Py, d.Kx, d.Wk, ny, d.Py, "fft_y_fwd", 3.0 * nz * d.Kx * (ny + d.Py) * cplxb);
+    } else if (three_d && d.Py > 1 && fast_y) {
         launch_y_direct(c, true, (cplx<float>*)S, plane, ny, d.Py, "fft_y_fwd",
                         3.0 * nz * d.Kx * (ny + d.Py) * cplxb);
     } else if (three_d && d.Py > 1) {
@@ -1203,7 +1210,9 @@ static void demag_apply_t(mm_ctx* c, const T* m, T* Hd, int stage = 0) {
                              3.0 * d.Kx * 2 * ny * cplxb + (double)d.ncomp * Ky * d.Kx * realb);
         }
     }
-    if (three_d && d.Py > 1 && fast_y) {
+    if (three_d && d.Py > 1 && split_y) {
+        ysplit_launch(c, false, S, nz, d.Py, d.Kx, d.Wk, d.Py, ny, "fft_y_inv", 3.0 * nz * d.Kx * (ny + d.Py) * cplxb);
+    } else if (three_d && d.Py > 1 && fast_y) {
         launch_y_direct(c, false, (cplx<float>*)S, plane, d.Py, ny, "fft_y_inv",
                         3.0 * nz * d.Kx * (ny + d.Py) * cplxb);
     } else if (three_d && d.Py > 1) {

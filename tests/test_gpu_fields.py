@@ -138,6 +138,10 @@ DEMAG_GRIDS = [
     W.Grid(12, 96, 1, 2e-9, 2e-9, 1e-9),
     W.Grid(9, 128, 1, 2e-9, 2e-9, 1e-9),
     W.Grid(6, 256, 1, 2e-9, 2e-9, 1e-9),
+    # Y passes split over several threads per column: padded y lengths 512
+    # and 1024 with ragged n_in (250 and 500 rows)
+    W.Grid(6, 250, 3, 2e-9, 2e-9, 2e-9),
+    W.Grid(4, 500, 2, 3e-9, 2e-9, 2e-9),
 ]
 
 
