@@ -1005,9 +1005,13 @@ static mm_status advance(mm_ctx* c, long long add_steps, double t_end, int repla
         if (add_steps >= 0) {
             want = c->h_state.target - c->h_state.accepted;
         } else {
+            // attempts still needed at the current step size, at most 64 per
+            // round: an adaptive dt grows by up to 5x a step, so estimates
+            // from an early small dt overshoot, and every attempt past
+            // t_end is a launched no-op
             const double left = t_end - c->h_state.t;
             const double dt = c->h_state.dt > 0 ? c->h_state.dt : 1e-13;
-            want = (long long)std::min(1e6, std::ceil(left / dt)) + 1;
+            want = (long long)std::min(64.0, std::ceil(left / dt) + 1.0);
         }
         if (want <= 0) break;
         if (heun) want = std::min<long long>(want, 1 << 20);
@@ -1154,7 +1158,8 @@ mm_status mm_topo_charge(mm_ctx* c, int r, int layer, double* Q) {
     mm_status s = check_replica(c, r);
     if (s != MM_OK) return s;
     ReplicaView view(c, r);
-    if (!Q || layer >= c->grid.nz) return set_error(c, MM_ERR_ARG, "bad layer or null output");
+    if (!Q || layer >= c->grid.nz || layer < -1)
+        return set_error(c, MM_ERR_ARG, "bad layer (-1 for the mean over layers) or null output");
     double* d_out = c->d_red + 2 * 304 + 16;
     topo_launch(c, c->d_m, layer, d_out);
     double h = 0;
