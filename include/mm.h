@@ -312,9 +312,9 @@ MM_API mm_status mm_energy(mm_ctx* ctx, int replica, double* E);
 /* Topological charge (Results, "A showcase of representative examples":
  * the relaxed skyrmion charge Q of the D-K phase diagram)
  * Q = (1/4pi) sum m.(dm/dx x dm/dy) dx dy of layer `layer`, or the mean
- * over layers when layer < 0; central differences, one-sided at edges and
+ * over layers when layer = -1; central differences, one-sided at edges and
  * holes; FP64 compensated sum.  Errors: MM_ERR_ARG (bad replica,
- * layer >= nz, NULL Q). */
+ * layer >= nz or layer < -1, NULL Q). */
 MM_API mm_status mm_topo_charge(mm_ctx* ctx, int replica, int layer, double* Q);
 
 /* Mean magnetisation <m> (Results: the average magnetisation the standard
@@ -425,7 +425,7 @@ MM_API mm_status mm_batch_set_shape(mm_ctx* ctx, int nt, int blocks);
  * pool.  The caller passes the state m_dev (device, [3][nz][ny][nx] in
  * `precision` 32 = float or 64 = double, every cell present) and the output
  * Q_dev (one device double); the result is the same quantity as
- * mm_topo_charge (layer < 0: mean over layers).  Work is ordered on
+ * mm_topo_charge (layer = -1: mean over layers).  Work is ordered on
  * `stream` (cudaStream_t, NULL = default stream); nothing is synchronised.
  * The only scratch is a fixed 64 KiB file-scope device array (one partial
  * sum per block of 4096 cells) that every GPU loading the library keeps
@@ -433,8 +433,11 @@ MM_API mm_status mm_batch_set_shape(mm_ctx* ctx, int nt, int blocks);
  * that first call before any stream capture.  Calls share the array:
  * calls that overlap on the GPU race.  No cudaMalloc, cudaFree or
  * allocating library routine is used.  Errors: MM_ERR_ARG for bad
- * arguments or more than 16,777,216 cells (4096 blocks) in the reduced
- * range, MM_ERR_DEVICE / MM_ERR_CUDA for runtime failures. */
+ * arguments (layer >= nz or < -1 included) or more than 16,777,216 cells
+ * (4096 blocks) in the reduced range; MM_ERR_STATE, with nothing launched,
+ * when a CUDA error from earlier work is already pending on the calling
+ * thread (it is left in place, not consumed); MM_ERR_DEVICE / MM_ERR_CUDA
+ * for this call's own runtime failures. */
 MM_API mm_status mm_topo_charge_noalloc(const void* m_dev, int precision, int nx, int ny, int nz,
                                         double dx, double dy, int layer, double* Q_dev, void* stream);
 
@@ -508,6 +511,15 @@ MM_API mm_status mm_surrogate_grad(mm_ctx* ctx, int B, int H, int W, const doubl
  * out = entries written. */
 MM_API mm_status mm_set_profiling(mm_ctx* ctx, int on);
 MM_API mm_status mm_get_profile(mm_ctx* ctx, mm_profile_entry* out, int* n_inout);
+
+/* Measured arithmetic throughput of the current device: a grid of
+ * independent fused multiply-add chains in FP32 (precision 32) or FP64
+ * (64), timed with CUDA events on the default stream (about a millisecond);
+ * *flops_per_s = 2 x FMAs / s.  No passage: measurement convenience (the
+ * denominator of ALU-bound rooflines).  Allocates 2 KB for the duration of
+ * the call.  Errors: MM_ERR_ARG (bad precision, NULL), MM_ERR_DEVICE,
+ * MM_ERR_OOM, MM_ERR_CUDA. */
+MM_API mm_status mm_measure_peak(int precision, double* flops_per_s);
 
 /* Host-side fault injection for tests: 1 = next allocation fails,
  * 2 = poison the state with NaN at the next step, 3 = force dt underflow.

@@ -138,6 +138,7 @@ _SIGS = {
     "mm_debug_inject": [C.c_void_p, C.c_int],
     "mm_last_error": [C.c_void_p],
     "mm_status_string": [C.c_int],
+    "mm_measure_peak": [C.c_int, _D],
 }
 
 
@@ -452,6 +453,13 @@ def mm_get_profile(ctx):
     _check(load().mm_get_profile(ctx, arr, C.byref(n)), ctx)
     return [{"name": arr[q].name.decode(), "launches": arr[q].launches, "total_ms": arr[q].total_ms,
              "bytes_per_launch": arr[q].bytes_per_launch} for q in range(n.value)]
+
+
+def mm_measure_peak(precision: int) -> float:
+    """Measured FP32 (32) or FP64 (64) fused multiply-add throughput, flop/s."""
+    v = C.c_double()
+    _check(load().mm_measure_peak(precision, C.byref(v)))
+    return v.value
 
 
 def mm_debug_inject(ctx, fault: int):
