@@ -1,18 +1,18 @@
 """Throughput benchmark of the LLG hot path on GB300.
 
 Metric: LLG cell-steps/s (cells x accepted integrator steps per second).
-Workload (single GPU): 256x256x16 cells of 2 nm, Ms 5.8e5, A 1.5e-11,
-Ku 8e5 along z, interfacial DMI 3e-3, alpha 0.1, seeded random unit
-vectors, FP32 Dormand-Prince RK45 (rtol 1e-6, device-side controller) with
-exact FFT demag on the 512x512x32 padded grid.  One step = one accepted
-RK45 step (6 field evaluations, each exchange+DMI+anisotropy+demag, plus
-the stage, error and controller kernels).
+Headline workload (the largest single-GPU case): 512x512x64 cells of 3 nm
+cubes (16.7 M cells), Ms 8e5, A 1.3e-11, alpha 0.02, seeded random vortex,
+FP32 Dormand-Prince RK45 (rtol 1e-6, device-side controller) with the FP64
+Newell tensor setup and exact FFT demag on the 1024x1024x128 padded grid.
+One step = one accepted RK45 step (6 field evaluations, each
+exchange + demag, plus the stage, error and controller kernels).
 
 Multi-GPU: replicas only (independent runs of the same workload per rank,
 no data-path collective); value = sum of cell-steps over ranks / max time.
 
 --impl reference times the FP64 CPU oracle (the only reference available:
-the paper ships no code) on the same workload on the host cores.
+the paper ships no code) on samples of the same workload on the host cores.
 """
 from __future__ import annotations
 
@@ -101,14 +101,15 @@ def _dist():
     return ws, rank, local
 
 
-def _traffic_for(kernel: str):
-    """ncu DRAM bytes per launch recorded in profiles/traffic.json, used only
-    while the source files that define the kernel still hash to the values
-    recorded with the capture (any change to them makes it null)."""
+def _traffic_for(kernel: str, workload: str):
+    """ncu DRAM bytes per launch recorded in profiles/traffic.json for this
+    kernel on this workload, used only while the source files that define
+    the kernel still hash to the values recorded with the capture (any change
+    to them makes it null)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
-            ent = json.load(f)["kernels"][kernel]
+            ent = json.load(f)["kernels"][f"{kernel}@{workload}"]
         h = hashlib.sha256()
         for rel in ent["sources"]:
             with open(os.path.join(ROOT, rel), "rb") as f:
@@ -120,93 +121,149 @@ def _traffic_for(kernel: str):
         return None
 
 
-def cpu_baseline(seconds_budget=60.0):
-    """The FP64 oracle as it stands on this host's cores: RK45 steps of the
-    same 256x256x16 workload (setup excluded), bounded to about a minute."""
-    from oracle.demag import demag_spectrum
-    from oracle.fields import Problem
-    from oracle.llg import Solver
-    w = W.dmi_256x256x16()
-    p = Problem.from_workload(w.grid, w.mat)
-    K = demag_spectrum(p.shape, p.d)
-    s = Solver(p, W.m_random_sphere(w.grid, seed=2), K_hat=K, dt=1e-14, rtol=1e-6)
-    s.k1 = s.slope(s.m)
-    done = 0
-    t0 = time.perf_counter()
-    while True:
-        s.rk45_step_fixed(1e-14)
-        done += 1
-        el = time.perf_counter() - t0
-        if el > seconds_budget / 3 or done >= 3:
-            break
-    return {"value": w.grid.n * done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} RK45 step(s) of the 256x256x16 workload (numpy FP64, single-threaded "
-                      f"FFT and array ops; Newell/FFT setup excluded), {el:.1f} s"}
-
-
+# Sample grids of the headline workload (same material, 3 nm cubes, vortex
+# start, RK45, exact demag), largest first: the oracle steps the largest one
+# that fits its time budget.
+REFERENCE_SAMPLES = [(512, 512, 64), (256, 256, 64), (256, 256, 32), (128, 128, 32), (128, 128, 16),
+                     (64, 64, 16), (32, 32, 16), (16, 16, 16), (16, 16, 8), (8, 8, 8), (4, 4, 4)]
 REFERENCE_BUDGET_S = 240.0
-# sample grids of the 256x256x16 workload (same material, 2 nm cells, RK45), largest first
-REFERENCE_SAMPLES = [(256, 256, 16), (128, 128, 16), (64, 64, 16), (32, 32, 16), (16, 16, 16),
-                     (16, 16, 8), (8, 8, 8), (4, 4, 4)]
 
 
-def _oracle_solver(w, nx, ny, nz):
+def _host_cores() -> int:
+    return os.cpu_count() or 1
+
+
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def _vortex_sample(shape):
     from dataclasses import replace
+    w = W.vortex_512x512x64()
+    g = W.Grid(shape[0], shape[1], shape[2], w.grid.dx, w.grid.dy, w.grid.dz)
+    return replace(w, grid=g)
 
+
+def _oracle_solver(shape):
     from oracle.demag import demag_spectrum
     from oracle.fields import Problem
     from oracle.llg import Solver
-    g = W.Grid(nx, ny, nz, w.grid.dx, w.grid.dy, w.grid.dz)
-    ws = replace(w, grid=g)
-    p = Problem.from_workload(g, ws.mat)
-    s = Solver(p, W.m_random_sphere(g, seed=2), K_hat=demag_spectrum(p.shape, p.d), dt=1e-14, rtol=w.rtol)
+    w = _vortex_sample(shape)
+    p = Problem.from_workload(w.grid, w.mat)
+    s = Solver(p, W.m_vortex(w.grid, seed=w.seed), K_hat=demag_spectrum(p.shape, p.d), dt=1e-14, rtol=w.rtol)
     s.k1 = s.slope(s.m)
-    return s, g.n
+    return s, w.grid.n
 
 
-def run_reference(args):
-    """The FP64 CPU oracle timed on this host, W warm-up and exactly K timed
-    RK45 steps.  Each step is a bounded sample of the 256x256x16 workload: the
-    largest grid of the same material, cell size and integrator whose K + W
-    steps fit in about REFERENCE_BUDGET_S seconds (cost per cell-step taken
-    from two steps of a 32x32x16 probe)."""
-    ws, rank, _ = _dist()
-    if rank != 0:
-        return 0
-    w = W.dmi_256x256x16()
-    probe, n_probe = _oracle_solver(w, 32, 32, 16)
+def _oracle_run(args):
+    """One oracle process: W untimed and K timed fixed-dt RK45 steps of a
+    sample grid; returns (cells, seconds of the K steps)."""
+    shape, warmup, steps = args
+    s, n = _oracle_solver(shape)
+    for _ in range(warmup):
+        s.rk45_step_fixed(1e-14)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s.rk45_step_fixed(1e-14)
+    return n, time.perf_counter() - t0
+
+
+def _oracle_pool(shape, warmup, steps, procs):
+    """The oracle as it stands in `procs` processes at once (one per host
+    core, spawned so that no CUDA state is inherited), each stepping its own
+    copy of the sample; returns total cell-steps / the slowest process's
+    time, and that time."""
+    import multiprocessing as mp
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            res = pool.map(_oracle_run, [(shape, warmup, steps)] * procs)
+    finally:
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    t = max(r[1] for r in res)
+    return sum(r[0] for r in res) * steps / t, t
+
+
+def _per_cell_step_probe():
+    probe, n = _oracle_solver((32, 32, 16))
     probe.rk45_step_fixed(1e-14)
     t0 = time.perf_counter()
     for _ in range(2):
         probe.rk45_step_fixed(1e-14)
-    per_cell_step = (time.perf_counter() - t0) / (2 * n_probe)
-    total = args.steps + args.warmup
-    shape = REFERENCE_SAMPLES[-1]
+    return (time.perf_counter() - t0) / (2 * n)
+
+
+def _pick_sample(per_cell_step, steps, budget_s):
     for cand in REFERENCE_SAMPLES:
-        if per_cell_step * cand[0] * cand[1] * cand[2] * total <= REFERENCE_BUDGET_S:
-            shape = cand
-            break
-    s, n = _oracle_solver(w, *shape)
-    for _ in range(args.warmup):
-        s.rk45_step_fixed(1e-14)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        s.rk45_step_fixed(1e-14)
-    el = time.perf_counter() - t0
-    val = n * args.steps / el
+        if per_cell_step * cand[0] * cand[1] * cand[2] * steps <= budget_s:
+            return cand
+    return REFERENCE_SAMPLES[-1]
+
+
+def cpu_baseline(seconds_budget=12.0, steps=3):
+    """The FP64 oracle as it stands on this host: fixed-dt RK45 steps of a
+    sample of the headline workload sized to about `seconds_budget` of
+    stepping, once in one process (one core) and once in one process per
+    host core (each stepping its own copy); Newell/FFT setup excluded."""
+    per = _per_cell_step_probe()
+    shape = _pick_sample(per, steps, seconds_budget)
+    _, t1 = _oracle_run((shape, 0, steps))
+    n = shape[0] * shape[1] * shape[2]
+    one = n * steps / t1
+    cores = _host_cores()
+    allv, tall = _oracle_pool(shape, 0, steps, cores)
+    return {"value": allv, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": _cpu_model(),
+            "single_core": {"value": one, "cores": 1, "seconds": round(t1, 2)},
+            "sample": f"{steps} fixed-dt RK45 step(s) of a {shape[0]}x{shape[1]}x{shape[2]} sample of the "
+                      f"512x512x64 workload (same material, 3 nm cubes, vortex start, exact demag; numpy FP64), "
+                      f"in each of {cores} processes at once ({tall:.1f} s); one process alone: {one:.3g} "
+                      f"cell-steps/s ({t1:.1f} s)"}
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on this host's cores, W warm-up and exactly K
+    timed RK45 steps.  Each step is a bounded sample of the headline
+    workload: one process per host core, each stepping its own copy of the
+    largest sample grid (same material, cell size, integrator, exact demag)
+    whose K + W steps fit in about REFERENCE_BUDGET_S seconds (cost per
+    cell-step probed on 32x32x16, doubled for the shared memory system)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    w = W.vortex_512x512x64()
+    per = _per_cell_step_probe()
+    total = args.steps + args.warmup
+    shape = _pick_sample(2.0 * per, total, REFERENCE_BUDGET_S)
+    cores = _host_cores()
+    val, el = _oracle_pool(shape, args.warmup, args.steps, cores)
     sample = (f"each step one RK45 step (dt 1e-14 s) of a {shape[0]}x{shape[1]}x{shape[2]} sample of the "
-              f"workload (same material, 2 nm cells, exact demag; numpy FP64, single-threaded), "
-              f"{args.steps} timed after {args.warmup} warm-up, {el:.1f} s")
+              f"workload (same material, 3 nm cubes, vortex start, exact demag; numpy FP64) in each of "
+              f"{cores} processes at once, {args.steps} timed after {args.warmup} warm-up, {el:.1f} s")
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "cells": w.grid.n, "grid": [w.grid.nx, w.grid.ny, w.grid.nz],
-                   "cell_nm": [2, 2, 2], "integrator": "rk45-dopri5", "rtol": w.rtol,
+                   "cell_nm": [3, 3, 3], "integrator": "rk45-dopri5", "rtol": w.rtol,
                    "demag": f"exact-fft {2*shape[0]}x{2*shape[1]}x{2*shape[2]} (sample grid)",
-                   "precision": "fp64-cpu-oracle", "parallelism": "one CPU thread (rank 0)",
+                   "precision": "fp64-cpu-oracle", "parallelism": f"{cores} oracle processes (rank 0)",
                    "sample_grid": list(shape)},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                         "cpu_model": _cpu_model()},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -240,18 +297,29 @@ def _timed(stream, fn):
     return e0.elapsed_time(e1)
 
 
+def _material(mm, w):
+    return mm.Material(w.mat.Ms, w.mat.A, w.mat.alpha, w.mat.Ku1, w.mat.u, w.mat.D)
+
+
+def _ctx(mm, stream, w, prec=32, dt=1e-14):
+    g = w.grid
+    cfg = mm.make_config(precision=prec, integrator=mm.MM_RK45, demag=mm.MM_DEMAG_EXACT, dt=dt, rtol=w.rtol)
+    c = mm.mm_create(mm.make_grid(g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), _material(mm, w).s, cfg)
+    mm.mm_set_stream(c, stream.cuda_stream)
+    if any(w.B_ext):
+        mm.mm_set_field(c, 0, w.B_ext)
+    return c
+
+
 def fp32_vs_fp64(mm, stream, w, m0, n_steps=20, dt=2e-14):
     """The same n fixed RK45 steps from the same state in FP32 and in FP64:
-    max|m_fp32 - m_fp64| (the FP64 GPU path stands in for the FP64 oracle
-    here; the parity tests hold it to the oracle within 1e-11) and each
-    precision's device throughput on those steps."""
+    max|m_fp32 - m_fp64| and each precision's device throughput on those
+    steps (the FP64 GPU path is held to the FP64 oracle within 1e-11 by the
+    parity tests)."""
     g = w.grid
-    M = mm.Material(w.mat.Ms, w.mat.A, w.mat.alpha, w.mat.Ku1, w.mat.u, w.mat.D)
     out, rate = {}, {}
     for prec in (32, 64):
-        cfg = mm.make_config(precision=prec, integrator=mm.MM_RK45, demag=mm.MM_DEMAG_EXACT, dt=dt, rtol=w.rtol)
-        c = mm.mm_create(mm.make_grid(g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), M.s, cfg)
-        mm.mm_set_stream(c, stream.cuda_stream)
+        c = _ctx(mm, stream, w, prec, dt)
         mm.mm_set_m(c, 0, m0)
         mm.mm_step_dt(c, np.full(3, dt))          # warm-up (graph capture, first slope)
         mm.mm_set_m(c, 0, m0)
@@ -260,6 +328,184 @@ def fp32_vs_fp64(mm, stream, w, m0, n_steps=20, dt=2e-14):
         out[prec] = mm.mm_get_m(c, 0, m0.shape)
         mm.mm_destroy(c)
     return float(np.abs(out[32] - out[64]).max()), rate
+
+
+def error_vs_oracle(mm, stream, shape=(64, 64, 16), n_steps=10):
+    """Trajectory error against the FP64 oracle on a sample of the headline
+    workload (same material, 3 nm cubes, vortex start): the oracle's own
+    accepted RK45 steps, replayed by the GPU in FP32 and in FP64."""
+    from oracle.demag import demag_spectrum
+    from oracle.fields import Problem
+    from oracle.llg import Solver
+    w = _vortex_sample(shape)
+    g = w.grid
+    m0 = W.m_vortex(g, seed=w.seed)
+    p = Problem.from_workload(g, w.mat)
+    o = Solver(p, m0, K_hat=demag_spectrum(p.shape, p.d), dt=1e-14, rtol=w.rtol)
+    dts = [o.rk45_step() for _ in range(n_steps)]
+    out = {}
+    for prec in (32, 64):
+        c = _ctx(mm, stream, w, prec)
+        mm.mm_set_m(c, 0, m0)
+        mm.mm_step_dt(c, np.asarray(dts))
+        out[f"fp{prec}_max_abs_dm"] = float(np.abs(mm.mm_get_m(c, 0, m0.shape) - o.m).max())
+        mm.mm_destroy(c)
+    out.update({"after_steps": n_steps, "t_sim_s": float(sum(dts)),
+                "sample": f"{shape[0]}x{shape[1]}x{shape[2]} of the workload's material and cells, vortex start; "
+                          "the oracle's accepted RK45 steps replayed", "bars": {"fp32": 1e-5, "fp64": 1e-11}})
+    return out
+
+
+def profile_kernels(mm, ctx, steps):
+    """Per-kernel CUDA-event timing of `steps` more steps (graphs bypassed):
+    {name: launches, share, avg_us, GB/s} and the dominant kernel's entry."""
+    mm.mm_set_profiling(ctx, True)
+    mm.mm_step(ctx, steps)
+    prof = mm.mm_get_profile(ctx)
+    mm.mm_set_profiling(ctx, False)
+    tot = sum(p["total_ms"] for p in prof) or 1.0
+    kernels = {p["name"]: {"launches": p["launches"], "share": round(p["total_ms"] / tot, 4),
+                           "avg_us": round(1e3 * p["total_ms"] / max(1, p["launches"]), 2),
+                           "GBps": round(p["bytes_per_launch"] / (p["total_ms"] / max(1, p["launches"]) * 1e-3) / 1e9, 1)
+                           if p["bytes_per_launch"] > 0 else None}
+               for p in sorted(prof, key=lambda p: -p["total_ms"])}
+    return kernels, max(prof, key=lambda p: p["total_ms"])
+
+
+def roofline_of(dom, workload):
+    avg_ms = dom["total_ms"] / max(1, dom["launches"])
+    achieved = dom["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    return {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1), "peak": peak,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "traffic": _traffic_for(dom["name"], workload), "algorithmic_bytes_per_launch": dom["bytes_per_launch"],
+            "avg_launch_us": round(1e3 * avg_ms, 2)}
+
+
+def variant_single(mm, stream, w, m0, steps, warmup=5):
+    """A single-instance RK45 workload timed like the headline: K accepted
+    steps on the library stream, per-kernel shares and the dominant kernel's
+    roofline."""
+    g = w.grid
+    c = _ctx(mm, stream, w)
+    mm.mm_set_m(c, 0, m0)
+    mm.mm_step(c, warmup)
+    s0 = mm.mm_get_stats(c)
+    ms = _timed(stream, lambda: mm.mm_step(c, steps))
+    s1 = mm.mm_get_stats(c)
+    n = s1["accepted"] - s0["accepted"]
+    kernels, dom = profile_kernels(mm, c, 2)
+    mm.mm_destroy(c)
+    return {"workload": w.name, "grid": [g.nx, g.ny, g.nz], "cells": g.n, "value": g.n * n / (ms * 1e-3),
+            "unit": UNIT, "steps": n, "ms_per_step": ms / max(1, n), "kernel_launches_per_step":
+            (s1["kernel_launches"] - s0["kernel_launches"]) / max(1, n),
+            "roofline": roofline_of(dom, w.name), "kernels": kernels}
+
+
+def variant_film_fp64(mm, stream):
+    """The 128x32x1 permalloy film of 3.90625x3.90625x3 nm cells (FP64 RK45,
+    rtol 1e-6, exchange + demag + Zeeman, field (-24.6, 4.3, 0) mT, seeded
+    perturbed (1,1,1) start) over its whole 0.5 ns: a launch- and
+    latency-bound case, reported as microseconds and kernel launches per
+    accepted step (the attempts run as CUDA graphs of 8)."""
+    w = W.film_128x32()
+    g = w.grid
+    m0 = W.m_uniform_perturbed(g, seed=w.seed)
+    c = _ctx(mm, stream, w, prec=64)
+    mm.mm_set_m(c, 0, m0)
+    blob = mm.mm_get_state(c)
+    mm.mm_run(c, 0.05e-9)                 # warm-up (first slope, graph capture)
+    mm.mm_set_state(c, blob)
+    mm.mm_step(c, 1)                      # graphs again after the restore
+    s0 = mm.mm_get_stats(c)
+    ms = _timed(stream, lambda: mm.mm_run(c, w.t_end))
+    s1 = mm.mm_get_stats(c)
+    n = s1["accepted"] - s0["accepted"]
+    att = s1["attempts"] - s0["attempts"]
+    mm.mm_destroy(c)
+    return {"workload": w.name, "grid": [g.nx, g.ny, g.nz], "cells": g.n, "precision": "fp64",
+            "t_sim_ns": w.t_end * 1e9, "accepted_steps": n, "attempts": att, "wall_ms": ms,
+            "us_per_step": 1e3 * ms / max(1, n), "value": g.n * n / (ms * 1e-3), "unit": UNIT,
+            "kernel_launches_per_step": (s1["kernel_launches"] - s0["kernel_launches"]) / max(1, n),
+            "graph_launches_per_step": round(att / 8.0 / max(1, n), 3),
+            "note": "timed from the second step to t_end (the first re-captures the graphs)"}
+
+
+def variant_cufft(mm, stream, reps=5):
+    """The same zero-padded demag convolution through cuFFT (torch.fft R2C /
+    C2R on the library's stream) with the full tensor spectrum expanded from
+    the library's stored half range, against the library's pruned passes on
+    the headline grid and the 256x256x16 film: ms per evaluation and the
+    largest difference of the fields relative to the largest field."""
+    import torch
+    out = []
+    cases = ((W.vortex_512x512x64(), lambda g: W.m_vortex(g, seed=5)),
+             (W.dmi_256x256x16(), lambda g: W.m_random_sphere(g, seed=2)))
+    demag_kernels = ("fft_x_r2c", "fft_y_fwd", "fft_conv", "fft_y_inv", "fft_x_c2r")
+    for w, mk in cases:
+        g = w.grid
+        m0 = mk(g)
+        c = _ctx(mm, stream, w)
+        mm.mm_set_m(c, 0, m0)
+        mm.mm_get_heff(c, 0, m0.shape, 16)            # warm-up
+        mm.mm_set_profiling(c, True)
+        for _ in range(reps):
+            H_ours = mm.mm_get_heff(c, 0, m0.shape, 16)
+        prof = {p["name"]: p for p in mm.mm_get_profile(c)}
+        mm.mm_set_profiling(c, False)
+        ours_ms = sum(prof[k]["total_ms"] / prof[k]["launches"] for k in demag_kernels if k in prof)
+        K, (Px, Py, Pz) = mm.mm_get_demag_kernel(c)
+        m_dev = mm.mm_get_m(c, 0, m0.shape)
+        mm.mm_destroy(c)
+        dev = torch.device("cuda")
+        with torch.cuda.stream(stream):
+            Kt = torch.tensor(K, dtype=torch.float32, device=dev)          # [6][Pz/2+1][Py/2+1][Kx]
+            ky = torch.arange(Py, device=dev)
+            kz = torch.arange(Pz, device=dev)
+            kyf = torch.where(ky <= Py // 2, ky, Py - ky)
+            kzf = torch.where(kz <= Pz // 2, kz, Pz - kz)
+            sy = torch.where(ky <= Py // 2, 1.0, -1.0).to(torch.float32)
+            sz = torch.where(kz <= Pz // 2, 1.0, -1.0).to(torch.float32)
+            Kf = Kt[:, kzf][:, :, kyf]                                      # [6][Pz][Py][Kx]
+            syz = (sy[None, :, None] * sz[:, None, None])
+            Kf[3] *= sy[None, :, None]
+            Kf[4] *= sz[:, None, None]
+            Kf[5] *= syz
+            x = torch.tensor(w.mat.Ms * m_dev, dtype=torch.float32, device=dev)
+            comp = ((0, 3, 4), (3, 1, 5), (4, 5, 2))
+
+            def conv():
+                M = torch.fft.rfftn(x, s=(Pz, Py, Px), dim=(1, 2, 3))
+                Hh = torch.stack([Kf[a] * M[0] + Kf[b] * M[1] + Kf[d] * M[2] for a, b, d in comp])
+                return torch.fft.irfftn(Hh, s=(Pz, Py, Px), dim=(1, 2, 3), norm="forward")[:, :g.nz, :g.ny, :g.nx]
+
+            def ffts():
+                M = torch.fft.rfftn(x, s=(Pz, Py, Px), dim=(1, 2, 3))
+                return torch.fft.irfftn(M, s=(Pz, Py, Px), dim=(1, 2, 3), norm="forward")
+
+            H_cu = conv()
+            ffts()
+            t_all = _timed(stream, lambda: [conv() for _ in range(reps)]) / reps
+            t_fft = _timed(stream, lambda: [ffts() for _ in range(reps)]) / reps
+            Hc = H_cu.double().cpu().numpy()
+        del Kt, Kf, x, H_cu
+        torch.cuda.empty_cache()
+        out.append({"workload": w.name, "grid": [g.nx, g.ny, g.nz], "padded": [Px, Py, Pz],
+                    "ours_ms_per_eval": round(ours_ms, 4), "cufft_ms_per_eval": round(t_all, 4),
+                    "cufft_ffts_only_ms": round(t_fft, 4), "speedup_vs_cufft": round(t_all / ours_ms, 3),
+                    "max_rel_diff": float(np.abs(H_ours - Hc).max() / np.abs(Hc).max())})
+    return {"what": "ours: sum of the five demag kernels' CUDA-event times per evaluation (profiling pass); "
+                    "cuFFT: rfftn of 3 padded components + tensor multiply (torch elementwise) + irfftn, "
+                    "CUDA events, FP32", "cases": out}
+
+
+def variant_peaks(mm):
+    """Measured FMA throughput (FP32, FP64) of this GPU, the denominators of
+    the ALU-bound lines."""
+    f32 = max(mm.mm_measure_peak(32) for _ in range(3))
+    f64 = max(mm.mm_measure_peak(64) for _ in range(3))
+    return {"fp32_tflops": round(f32 / 1e12, 2), "fp64_tflops": round(f64 / 1e12, 3),
+            "how": "grid of 8 independent FMA chains per thread (8 CTAs of 256 per SM), CUDA events"}
 
 
 def variant_batched(mm, stream, steps):
@@ -586,18 +832,15 @@ def run_gpu(args):
     if not os.path.exists(mm.lib_path):
         from paper_2608_15253_gb300 import build as B
         B.build()
-    w = W.dmi_256x256x16()
+    w = W.vortex_512x512x64()
     if args.grid:
-        nx, ny, nz = (int(v) for v in args.grid.split(","))
+        w = _vortex_sample(tuple(int(v) for v in args.grid.split(",")))
         from dataclasses import replace
-        w = replace(w, name=f"dmi_{nx}x{ny}x{nz}_rk45", grid=W.Grid(nx, ny, nz, 2e-9, 2e-9, 2e-9))
+        w = replace(w, name=f"vortex_{w.grid.nx}x{w.grid.ny}x{w.grid.nz}_rk45")
     g = w.grid
-    M = mm.Material(w.mat.Ms, w.mat.A, w.mat.alpha, w.mat.Ku1, w.mat.u, w.mat.D)
-    cfg = mm.make_config(precision=32, integrator=mm.MM_RK45, demag=mm.MM_DEMAG_EXACT, dt=1e-14, rtol=w.rtol)
-    ctx = mm.mm_create(mm.make_grid(g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), M.s, cfg)
     stream = torch.cuda.current_stream()
-    mm.mm_set_stream(ctx, stream.cuda_stream)
-    m0 = W.m_random_sphere(g, seed=2 + rank)
+    ctx = _ctx(mm, stream, w)
+    m0 = W.m_vortex(g, seed=w.seed + rank)
     mm.mm_set_m(ctx, 0, m0)
 
     def barrier():
@@ -625,20 +868,7 @@ def run_gpu(args):
     value = total_cells_steps / (t_max * 1e-3)
 
     # per-kernel CUDA-event timing of the same kind of steps (graphs bypassed)
-    mm.mm_set_profiling(ctx, True)
-    mm.mm_step(ctx, max(2, min(args.steps, 5)))
-    prof = mm.mm_get_profile(ctx)
-    mm.mm_set_profiling(ctx, False)
-    tot = sum(p["total_ms"] for p in prof) or 1.0
-    dom = max(prof, key=lambda p: p["total_ms"])
-    avg_ms = dom["total_ms"] / max(1, dom["launches"])
-    achieved = dom["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
-    peak, peak_kind = _peaks()
-    kernels = {p["name"]: {"launches": p["launches"], "share": round(p["total_ms"] / tot, 4),
-                           "avg_us": round(1e3 * p["total_ms"] / max(1, p["launches"]), 2),
-                           "GBps": round(p["bytes_per_launch"] / (p["total_ms"] / max(1, p["launches"]) * 1e-3) / 1e9, 1)
-                           if p["bytes_per_launch"] > 0 else None}
-               for p in sorted(prof, key=lambda p: -p["total_ms"])}
+    kernels, dom = profile_kernels(mm, ctx, max(2, min(args.steps, 3)))
 
     # end to end through the C ABI with host buffers: every step uploads the
     # state (float64, 3N) from page-locked host memory and reads the new
@@ -656,39 +886,45 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_val = g.n * k_e2e / e2e_s * ws
+    mm.mm_destroy(ctx)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / max(1, steps), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.name, "cells": g.n, "grid": [g.nx, g.ny, g.nz], "cell_nm": [2, 2, 2],
-                   "integrator": "rk45-dopri5", "rtol": w.rtol, "demag": f"exact-fft {2*g.nx}x{2*g.ny}x{2*g.nz}",
-                   "precision": "fp32 (fp64 Newell setup)", "parallelism": f"replicas x{ws}",
+        "config": {"workload": w.name, "cells": g.n, "grid": [g.nx, g.ny, g.nz], "cell_nm": [3, 3, 3],
+                   "integrator": "rk45-dopri5", "rtol": w.rtol,
+                   "demag": f"exact-fft {2*g.nx}x{2*g.ny}x{2*g.nz} (pruned passes, FP64 Newell setup)",
+                   "precision": "fp32 (fp64 Newell setup and reductions)", "parallelism": f"replicas x{ws}",
                    "accepted_steps": steps, "attempts": attempts,
-                   "l2": "working set ~220 MB > 126 MB L2 (state, 7 slopes, spectrum, tensor)"},
+                   "l2": "inputs larger than L2: working set ~3 GB (state, 7 slopes, spectrum, tensor) > 126 MB"},
         "gpu_launches": launches,
-        "roofline": {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1), "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": _traffic_for(dom["name"]), "algorithmic_bytes_per_launch": dom["bytes_per_launch"],
-                     "avg_launch_us": round(1e3 * avg_ms, 2)},
+        "roofline": roofline_of(dom, w.name),
         "kernels": kernels,
         "clocks": clk.summary(),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 3 * g.n * 8,
                 "d2h_bytes_per_step": 3 * g.n * 8, "steps": k_e2e,
                 "host_buffers": "page-locked float64 [3][z][y][x]"},
     }
-    mm.mm_destroy(ctx)
     if not args.no_variants and rank == 0:
-        m0_err = W.m_random_sphere(g, seed=2)
-        err, rate = fp32_vs_fp64(mm, stream, w, m0_err)
-        line["error_vs_fp64"] = {"max_abs_dm": err, "after_steps": 20, "dt_s": 2e-14,
-                                 "against": "FP64 GPU path on the same steps (held to the FP64 oracle "
-                                            "within 1e-11 by the parity tests)"}
+        try:
+            line["error_vs_oracle"] = error_vs_oracle(mm, stream)
+        except Exception as e:
+            line["error_vs_oracle"] = {"error": f"{type(e).__name__}: {e}"}
+        err, rate = fp32_vs_fp64(mm, stream, w, W.m_vortex(g, seed=w.seed), n_steps=5)
         line["fp64"] = {"value": rate[64], "unit": UNIT, "fp32_same_steps": rate[32],
-                        "note": "20 replayed RK45 steps of dt 2e-14 s from the same random state"}
+                        "max_abs_dm_fp32_vs_fp64": err,
+                        "note": "the headline grid, 5 replayed RK45 steps of dt 2e-14 s from the same state, "
+                                "all-FP64 GPU run against the FP32 one"}
         line["variants"] = {}
         wanted = [v for v in args.variants.split(",") if v]
-        for name, fn in (("batched", lambda: variant_batched(mm, stream, args.batch_steps)),
+        dmi = W.dmi_256x256x16()
+        for name, fn in (("peaks", lambda: variant_peaks(mm)),
+                         ("dmi_256x256x16", lambda: variant_single(mm, stream, dmi, W.m_random_sphere(dmi.grid, 2),
+                                                                   args.steps)),
+                         ("film_128x32_fp64", lambda: variant_film_fp64(mm, stream)),
+                         ("cufft", lambda: variant_cufft(mm, stream)),
+                         ("batched", lambda: variant_batched(mm, stream, args.batch_steps)),
                          ("surrogate", lambda: variant_surrogate(mm, stream, args.surrogate_steps)),
                          ("paper_scenarios", lambda: variant_scenarios(mm, stream)),
                          ("batching_table", lambda: variant_batching_table(mm, stream)),
@@ -700,6 +936,9 @@ def run_gpu(args):
                 line["variants"][name] = fn()
             except Exception as e:  # a failed variant is reported, the headline line still prints
                 line["variants"][name] = {"error": f"{type(e).__name__}: {e}"}
+        pk = line["variants"].get("peaks", {})
+        if "fp64_tflops" in pk:
+            line["fp64"]["fp64_peak_tflops"] = pk["fp64_tflops"]
     if rank == 0:
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
@@ -712,13 +951,14 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", default="", help="nx,ny,nz: a smaller case of the same workload (profiling)")
-    ap.add_argument("--no-variants", action="store_true", help="skip the FP64, batched and surrogate lines")
-    ap.add_argument("--variants", default="batched,surrogate,paper_scenarios,batching_table,stt_sweep,sp4",
+    ap.add_argument("--no-variants", action="store_true", help="skip the error, FP64 and variant lines")
+    ap.add_argument("--variants", default="peaks,dmi_256x256x16,film_128x32_fp64,cufft,batched,surrogate,"
+                                          "paper_scenarios,batching_table,stt_sweep,sp4",
                     help="comma list of variant lines to run")
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--surrogate-steps", type=int, default=100)

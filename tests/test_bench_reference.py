@@ -11,6 +11,7 @@ import pytest
 def bench(monkeypatch):
     import bench as b
     monkeypatch.setattr(b, "REFERENCE_SAMPLES", [(8, 8, 4), (4, 4, 2)])
+    monkeypatch.setattr(b, "_host_cores", lambda: 2)
     return b
 
 
@@ -22,9 +23,10 @@ def test_reference_line_times_exactly_k_steps(bench, capsys, monkeypatch):
     assert line["impl"] == "reference"
     assert line["steps"] == 4 and line["warmup"] == 3
     assert line["value"] > 0 and line["unit"] == "cell-steps/s" and line["higher_is_better"] is True
-    assert line["config"]["workload"] == "dmi_256x256x16_rk45"
+    assert line["config"]["workload"] == "vortex_512x512x64_rk45"
     assert line["config"]["sample_grid"] in ([8, 8, 4], [4, 4, 2])
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["cores"] == 2 and line["cpu_baseline"]["cpu_model"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
