@@ -113,11 +113,15 @@ extern "C" mm_status mm_topo_charge_noalloc(const void* m_dev, int precision, in
                                             double dy, int layer, double* Q_dev, void* stream) {
     using namespace mm;
     if (!m_dev || !Q_dev || (precision != 32 && precision != 64) || nx <= 0 || ny <= 0 || nz <= 0 || !(dx > 0) ||
-        !(dy > 0) || layer >= nz)
+        !(dy > 0) || layer >= nz || layer < -1)
         return MM_ERR_ARG;
     const long long plane = (long long)nx * ny;
     const long long cells = layer >= 0 ? plane : plane * nz;
     if (cells > kNoallocMaxCells) return MM_ERR_ARG;   // more partial blocks than the fixed array holds
+    // An error already pending on this thread belongs to earlier work: it is
+    // left in place for its owner and nothing is launched (a failed launch of
+    // this call could not be told apart from it).
+    if (cudaPeekAtLastError() != cudaSuccess) return MM_ERR_STATE;
     mm_status st;
     double* partial = partials_on_current_device(&st);
     if (!partial) return st;

@@ -89,3 +89,20 @@ def test_every_declaration_cites_its_passage():
             missing.append(name)
         prev_end, prev_seg = mt.end(), seg
     assert not missing, missing
+
+
+def test_charge_rejects_layers_below_minus_one_without_a_device():
+    """layer = -1 means the mean over layers; any other negative layer is an
+    argument error in both topological-charge entry points, raised before
+    anything touches a device (the dummy buffers are never read)."""
+    import ctypes
+
+    import numpy as np
+
+    import paper_2608_15253_gb300 as mm
+    lib = mm.load()
+    buf = np.zeros(64)
+    p = buf.ctypes.data_as(ctypes.c_void_p)
+    q = buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert lib.mm_topo_charge_noalloc(p, 64, 4, 4, 2, 1e-9, 1e-9, -2, q, None) == mm.MM_ERR_ARG
+    assert lib.mm_topo_charge_noalloc(p, 64, 4, 4, 2, 1e-9, 1e-9, 2, q, None) == mm.MM_ERR_ARG
