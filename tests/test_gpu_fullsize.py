@@ -2,16 +2,21 @@
 
 * 128x32x1 thin film, FP64 RK45 (rtol 1e-6) for the whole 0.5 ns: the GPU
   replays the oracle's accepted step sequence; every cell compared.
-* 256x256x16 DMI film: FP32 and FP64 replays of the oracle's first accepted
-  RK45 steps from a random state; energy and topological charge of the
-  final state against the oracle's compensated sums.
-* 512x512x64 vortex (16.7 M cells, padded 1024x1024x128): too large for
-  the oracle to step, so the FP32 run is held to the FP64 GPU run (itself
-  held to the oracle at the smaller sizes) on the same steps, plus |m| = 1
-  and energy decay (alpha > 0, no applied field).
+* 256x256x16 DMI film: FP32 and FP64 replays of the oracle's first 20
+  accepted RK45 steps from a random state; energy and topological charge of
+  the final state against the oracle's compensated sums.
+* 512x512x64 vortex (16.7 M cells, padded 1024x1024x128): its demag field
+  against the oracle at every cell and at sampled cells by direct sums; too
+  large for the oracle to step, so the FP32 run is held to the FP64 GPU run
+  (itself held to the oracle at the smaller sizes) on the same steps, plus
+  |m| = 1 and energy decay (alpha > 0, no applied field).
+* 1024 uneven replicas: 200 Heun steps at 300 K with SOT, ten replicas
+  covering every size class against the oracle.
 
 Bars: FP64 max|dm| <= 1e-11, FP32 max|dm| <= 1e-5 (Methods, "Physics and
 discretization": LLG of Eq. 1 integrated by the Dormand-Prince pair)."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -48,24 +53,36 @@ def test_thin_film_full_run_fp64():
         mm.mm_destroy(ctx)
 
 
+_DMI_REPLAY_STEPS = 20
+
+
+@functools.lru_cache(maxsize=1)
+def _dmi_oracle_run():
+    """The oracle's first 20 accepted RK45 steps of the 256x256x16 DMI film
+    from its seeded random state (about 10 s per step on one host core),
+    shared by both precisions."""
+    w = W.dmi_256x256x16()
+    m0 = W.m_random_sphere(w.grid, seed=w.seed)
+    o, p = _solver(w, m0, dt=1e-14, rtol=w.rtol)
+    dts = [o.rk45_step() for _ in range(_DMI_REPLAY_STEPS)]
+    return w, m0, dts, o.m.copy(), p, o.K_hat
+
+
 @pytest.mark.parametrize("prec", [64, 32])
 def test_dmi_film_256x256x16_replay(prec):
     mm = need_gpu()
     from oracle.observables import energy, topological_charge
-    w = W.dmi_256x256x16()
-    m0 = W.m_random_sphere(w.grid, seed=w.seed)
-    o, p = _solver(w, m0, dt=1e-14, rtol=w.rtol)
-    dts = [o.rk45_step() for _ in range(3)]
+    w, m0, dts, m_ref, p, K_hat = _dmi_oracle_run()
     ctx = make_ctx(mm, w.grid, w.mat, precision=prec, demag=True, B=w.B_ext, dt=1e-14, rtol=w.rtol)
     try:
         mm.mm_set_m(ctx, 0, m0)
         mm.mm_step_dt(ctx, dts)
         m = mm.mm_get_m(ctx, 0, m0.shape)
-        err = np.abs(m - o.m).max()
+        err = np.abs(m - m_ref).max()
         assert err <= (1e-11 if prec == 64 else 1e-5), err
         if prec == 64:
             E = mm.mm_energy(ctx, 0)
-            ref = energy(m, p, o.K_hat)
+            ref = energy(m, p, K_hat)
             assert abs(E[5] - ref["total"]) <= 1e-12 * max(abs(v) for v in ref.values())
             Q = mm.mm_topo_charge(ctx, 0)
             assert abs(Q - topological_charge(m, p)) <= 1e-9
@@ -132,6 +149,29 @@ def test_vortex_512x512x64_demag_field_sampled():
     assert err <= 5e-6 * w.mat.Ms, err
 
 
+def test_vortex_512x512x64_demag_field_every_cell():
+    """The same field at every one of the 16.7 M cells against the oracle's
+    FFT route (full complex numpy FFTs of the 1024x1024x128 padded tensor and
+    magnetisation; about 30 GB of host memory, a few minutes)."""
+    mm = need_gpu()
+    from oracle.demag import demag_spectrum, h_demag
+    from gpu_util import TERMS
+    w = W.vortex_512x512x64()
+    g = w.grid
+    ctx = make_ctx(mm, g, w.mat, precision=32, demag=True)
+    try:
+        m = W.m_vortex(g, seed=w.seed)
+        mm.mm_set_m(ctx, 0, m)
+        m_dev = mm.mm_get_m(ctx, 0, m.shape)
+        H = mm.mm_get_heff(ctx, 0, m.shape, TERMS["demag"])
+    finally:
+        mm.mm_destroy(ctx)
+    p = oracle_problem(g, w.mat)
+    ref = h_demag(m_dev, p, demag_spectrum(p.shape, p.d))
+    err = np.abs(H - ref).max()
+    assert err <= 5e-6 * np.abs(ref).max(), err
+
+
 def test_newell_entries_at_the_largest_displacements():
     """FP64 Newell entries of the 512x512x64 grid of 3 nm cubes at the far
     corners of the padded tensor, against the oracle's evaluation."""
@@ -167,8 +207,9 @@ def test_skyrmion_film_512x512_replay_fp32():
 def test_replicas_1024_sampled_against_oracle():
     """All 1024 perpendicular free layers of uneven sizes in one batch
     (T = 300 K, per-replica Philox keys splitmix64(3 + r), SOT current per
-    replica), 10 Heun steps; the smallest, the largest and the first replica
-    against the oracle run replica by replica."""
+    replica), 200 Heun steps; ten replicas -- the first of every size class,
+    the smallest, the largest, the first and the last -- against the oracle
+    run replica by replica (same thermal words, same current)."""
     mm = need_gpu()
     from oracle.llg import Solver, Torque, replica_seed
     R = 1024
@@ -187,9 +228,13 @@ def test_replicas_1024_sampled_against_oracle():
             m = W.m_perp(W.Grid(n, n, 1, 2e-9, 2e-9, 1e-9), seed=1000 + r, tilt=0.05)
             mm.mm_set_m(ctx, r, m)
             m0.append(m)
-        n_steps = 10
+        n_steps = 200
         mm.mm_step(ctx, n_steps)
-        for r in sorted({0, int(np.argmin(sizes)), int(np.argmax(sizes))}):
+        picks = {0, R - 1, int(np.argmin(sizes)), int(np.argmax(sizes))}
+        picks |= {sizes.index(n) for n in sorted(set(sizes))}
+        picks |= {int(v) for v in np.random.default_rng(8).integers(0, R, 10 - len(picks))}
+        assert len(picks) >= 8 and len({sizes[r] for r in picks}) == 5
+        for r in sorted(picks):
             g = W.Grid(sizes[r], sizes[r], 1, 2e-9, 2e-9, 1e-9)
             p = oracle_problem(g, mat)
             o = Solver(p, m0[r], terms=("exchange", "anisotropy", "zeeman", "demag"), T=300.0,
