@@ -211,6 +211,9 @@ void demag_apply(mm_ctx* c, const void* m, void* Hd);   // Hd = H_demag(m)
 // into d_mtmp while transforming it, then Hd = H_demag(m_s)
 bool demag_stage_fusable(const mm_ctx* c);
 void demag_apply_stage(mm_ctx* c, int stage, void* Hd);
+// FP32: every demag pass but the inverse X pass, for the fused inverse-X +
+// field kernel (stage > 0: the RK45 stage state is formed into d_mtmp first)
+void demag_apply_partial(mm_ctx* c, const void* m, int stage);
 mm_status newell_gpu(long count, const int* ijk, double dx, double dy, double dz, double* out_host);
 
 // conv_split.cu: middle pass for lines split over several threads (FP32)
@@ -233,6 +236,12 @@ void field_launch(mm_ctx* c, int mode, unsigned terms, const void* m, const void
                   void* out, void* out2, const void* m0, const void* k1, long long step_override,
                   int gate, int kstage);
 void thermal_raw_launch(mm_ctx* c, long long step, uint32_t* d_raw, void* d_h);
+// inverse X pass + field kernel in one launch (the demag spectrum of the
+// state must be ready); field_c2r_fusable says whether the grid allows it
+bool field_c2r_fusable(const mm_ctx* c);
+cudaError_t field_c2r_setup();
+void field_c2r_launch(mm_ctx* c, int mode, unsigned terms, const void* m, void* out, void* out2, const void* m0,
+                      const void* k1, long long step_override, int gate, int kstage);
 
 // batch.cu
 BatchHost* batch_new();

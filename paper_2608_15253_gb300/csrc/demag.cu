@@ -433,33 +433,17 @@ __global__ void __launch_bounds__(32 * kXW) fft_x_c2r_warp_kernel(XArgs<float> a
     const int row = blockIdx.x * kXW + warp;
     if (row >= a.rows) return;
     float2* sm = reinterpret_cast<float2*>(smem_raw) + warp * wline(LT);
-    constexpr int NP = ct_npass(LT), M = LT;
-    static_assert(NP >= 2, "first and last pass must differ");
-    const float2* X = a.spec + spec_row(a, row) * a.Wk;
-    // Z'[k] = (X[k] + conj X[M-k]) + i (X[k] - conj X[M-k]) conj(W^k)
-    auto load_rebuild = [&](int k) {
-        const float2 xk = X[k];
-        const float2 xc = cconj<float>(X[M - k]);
-        const float2 E = cadd<float>(xk, xc);
-        const float2 O = cmulc<float>(csub<float>(xk, xc), __ldg(&a.tw[k]));
-        return cadd<float>(E, mul_mi<float, -1>(O));
-    };
-    auto to_smem = [&](int i, float2 v) { sm[wpad(i)] = v; };
-    warp_pass<float, -1, LT, ct_radix(LT, 0), 1>(a.tw, 2, load_rebuild, to_smem);
-    warp_fft_smem<float, -1, LT, 1, NP - 1>(sm, a.tw, 2);
     float* out = a.out_real + (long long)row * a.in_pitch;
     const bool vec2 = (a.nx % 2 == 0) && (a.in_pitch % 2 == 0);
     const int nx = a.nx;
-    warp_pass<float, -1, LT, ct_radix(LT, NP - 1), ct_ns(LT, NP - 1)>(
-        a.tw, 2, [&](int i) { return sm[wpad(i)]; },
-        [&](int n, float2 v) {
-            if (2 * n + 1 < nx) {
-                if (vec2) *reinterpret_cast<float2*>(out + 2 * n) = v;
-                else { out[2 * n] = v.x; out[2 * n + 1] = v.y; }
-            } else if (2 * n < nx) {
-                out[2 * n] = v.x;
-            }
-        });
+    warp_c2r<LT>(a.spec + spec_row(a, row) * a.Wk, a.tw, sm, [&](int n, float2 v) {
+        if (2 * n + 1 < nx) {
+            if (vec2) *reinterpret_cast<float2*>(out + 2 * n) = v;
+            else { out[2 * n] = v.x; out[2 * n + 1] = v.y; }
+        } else if (2 * n < nx) {
+            out[2 * n] = v.x;
+        }
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -1138,8 +1122,10 @@ static void launch_y_direct(mm_ctx* c, bool fwd, cplx<float>* S, long long plane
                                  c->stream>>>(a);
 }
 
+// c2r = false: every pass but the inverse X pass (which the fused inverse-X +
+// field kernel then runs); Hd is not written.
 template <typename T>
-static void demag_apply_t(mm_ctx* c, const T* m, T* Hd, int stage = 0) {
+static void demag_apply_t(mm_ctx* c, const T* m, T* Hd, int stage = 0, bool c2r = true) {
     DemagPlan& d = c->dm;
     const mm_grid& g = c->grid;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -1222,7 +1208,8 @@ static void demag_apply_t(mm_ctx* c, const T* m, T* Hd, int stage = 0) {
         a.tw = (const cplx<T>*)d.tw_y;
         launch_col<T, -1>(c, a, nz, "fft_y_inv", 3.0 * nz * d.Kx * (ny + d.Py) * cplxb);
     }
-    launch_x<T>(c, false, nullptr, Hd, S, 3 * nz * ny, ny, d.PyA, nx, nx, d.Lh, (const cplx<T>*)d.tw_x, false, N);
+    if (c2r)
+        launch_x<T>(c, false, nullptr, Hd, S, 3 * nz * ny, ny, d.PyA, nx, nx, d.Lh, (const cplx<T>*)d.tw_x, false, N);
 }
 
 // Demag of Rc equal thin films stored back to back ([replica][component][y]
@@ -1279,6 +1266,10 @@ bool demag_stage_fusable(const mm_ctx* c) {
 
 void demag_apply_stage(mm_ctx* c, int stage, void* Hd) {
     demag_apply_t<float>(c, (const float*)c->d_mtmp, (float*)Hd, stage);
+}
+
+void demag_apply_partial(mm_ctx* c, const void* m, int stage) {
+    demag_apply_t<float>(c, (const float*)(stage > 0 ? c->d_mtmp : m), nullptr, stage, false);
 }
 
 template <typename T>
@@ -1433,6 +1424,7 @@ mm_status demag_setup(mm_ctx* c) {
     }
     cudaError_t e = cudaMemcpyToSymbol(c_tw32, tw32, sizeof tw32);
     if (e == cudaSuccess) e = split_conv_setup();
+    if (e == cudaSuccess) e = field_c2r_setup();
     if (e != cudaSuccess) return cuda_check(c, e, "twiddle table");
     e = fft_attributes<float>();
     if (e == cudaSuccess) e = fast_attributes();

@@ -239,4 +239,29 @@ __device__ __forceinline__ void warp_fft_smem(cplx<T>* sm, const cplx<T>* __rest
     }
 }
 
+// Inverse real transform of one row on one warp: the half spectrum X[0..M]
+// (M = LT, global memory) to 2M real values, of which the caller's store
+// keeps what it needs: store(n, v) receives the pair (2n, 2n+1).  The
+// rebuild Z'[k] = (X[k] + conj X[M-k]) + i (X[k] - conj X[M-k]) conj(W^k)
+// feeds the first pass; the last pass goes straight to the store.  sm is
+// the warp's line of wline(LT) values; tw = exp(-2 pi i q / 2M).
+template <int LT, typename Store>
+__device__ __forceinline__ void warp_c2r(const float2* __restrict__ X, const float2* __restrict__ tw, float2* sm,
+                                         Store store) {
+    constexpr int NP = ct_npass(LT), M = LT;
+    static_assert(NP >= 2, "first and last pass must differ");
+    auto load_rebuild = [&](int k) {
+        const float2 xk = X[k];
+        const float2 xc = cconj<float>(X[M - k]);
+        const float2 E = cadd<float>(xk, xc);
+        const float2 O = cmulc<float>(csub<float>(xk, xc), __ldg(&tw[k]));
+        return cadd<float>(E, mul_mi<float, -1>(O));
+    };
+    auto to_smem = [&](int i, float2 v) { sm[wpad(i)] = v; };
+    warp_pass<float, -1, LT, ct_radix(LT, 0), 1>(tw, 2, load_rebuild, to_smem);
+    warp_fft_smem<float, -1, LT, 1, NP - 1>(sm, tw, 2);
+    warp_pass<float, -1, LT, ct_radix(LT, NP - 1), ct_ns(LT, NP - 1)>(tw, 2, [&](int i) { return sm[wpad(i)]; },
+                                                                      store);
+}
+
 }  // namespace mm

@@ -15,6 +15,7 @@
 #include "common.cuh"
 #include "ctx.h"
 #include "field_dev.cuh"
+#include "fft_direct.cuh"
 
 namespace mm {
 
@@ -115,14 +116,13 @@ __device__ __forceinline__ void fset(float4& v, int q, float x) {
     if (q == 0) v.x = x; else if (q == 1) v.y = x; else if (q == 2) v.z = x; else v.w = x;
 }
 
-template <int V, bool EXT>
-__global__ void __launch_bounds__(256) field_vec_kernel(FieldArgs<float> a) {
+// The V cells x0 .. x0 + V - 1 of row (z, y).  HD_SMEM: the demag field of
+// the cells comes from shared memory (hds[c * hd_stride + q], the fused
+// inverse-X-pass kernel below), else from a.Hd in global memory.
+template <int V, bool EXT, bool HD_SMEM>
+__device__ __forceinline__ void field_vec_cells(const FieldArgs<float>& a, int x0, int y, int z, const float* hds,
+                                                int hd_stride) {
     using VT = typename fvec<V>::t;
-    if (a.gate && !a.st->active) return;
-    const int x0 = V * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x0 >= a.nx || y >= a.ny) return;
     const long long N = a.N;
     const long long i0 = ((long long)z * a.ny + y) * a.nx + x0;
     const Region<float>& R = a.R0;
@@ -170,10 +170,11 @@ __global__ void __launch_bounds__(256) field_vec_kernel(FieldArgs<float> a) {
         }
     }
     VT hd[3];
-    const bool dem = (a.terms & MM_TERM_DEMAG) && a.Hd;
+    const bool dem = (a.terms & MM_TERM_DEMAG) && (HD_SMEM || a.Hd);
     if (dem) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) hd[c] = ldv<V>(a.Hd + c * N + i0);
+        for (int c = 0; c < 3; ++c)
+            hd[c] = HD_SMEM ? *reinterpret_cast<const VT*>(hds + c * hd_stride) : ldv<V>(a.Hd + c * N + i0);
     }
     VT o1[3], o2[3];
 #pragma unroll
@@ -245,11 +246,66 @@ __global__ void __launch_bounds__(256) field_vec_kernel(FieldArgs<float> a) {
     }
 }
 
+template <int V, bool EXT>
+__global__ void __launch_bounds__(256) field_vec_kernel(FieldArgs<float> a) {
+    if (a.gate && !a.st->active) return;
+    const int x0 = V * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x0 >= a.nx || y >= a.ny) return;
+    field_vec_cells<V, EXT, false>(a, x0, y, z, nullptr, 0);
+}
+
+// The last demag pass (inverse X, half spectrum -> real rows) fused with
+// the field kernel: a CTA of 8 warps takes 1024 / nx rows (z, y); its warps
+// transform the three components of those rows (one row of one component
+// per warp at a time) into shared memory, then every thread forms the
+// field, torque and stage output of 4 cells with the demag field read from
+// there -- H_demag never goes through global memory.
+struct C2RSpec {
+    const float2* spec;     // [3][nz][PyA][Wk]
+    const float2* tw;       // exp(-2 pi i q / Px)
+    int PyA, Wk;
+};
+
+template <int LT>
+constexpr size_t c2r_field_smem() { return (size_t)8 * wline(LT) * sizeof(float2) + 3 * 1024 * sizeof(float); }
+
+template <int LT, bool EXT>
+__global__ void __launch_bounds__(256) c2r_field_kernel(FieldArgs<float> a, C2RSpec s) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (a.gate && !a.st->active) return;
+    const int warp = threadIdx.x >> 5;
+    float2* line = reinterpret_cast<float2*>(smem_raw) + warp * wline(LT);
+    float* sH = reinterpret_cast<float*>(smem_raw + (size_t)8 * wline(LT) * sizeof(float2));   // [rpc][3][nx]
+    const int nx = a.nx, rpc = 1024 / nx, nrows = a.ny * a.nz;
+    const int row0 = blockIdx.x * rpc;
+    for (int task = warp; task < 3 * rpc; task += 8) {
+        const int rl = task / 3, comp = task - 3 * rl, row = row0 + rl;
+        if (row >= nrows) break;                      // warp-uniform; later tasks have larger rows
+        const int z = row / a.ny, y = row - z * a.ny;
+        const float2* X = s.spec + ((long long)(comp * a.nz + z) * s.PyA + y) * s.Wk;
+        float* dst = sH + (rl * 3 + comp) * nx;
+        warp_c2r<LT>(X, s.tw, line, [&](int n, float2 v) {
+            if (2 * n + 1 < nx) *reinterpret_cast<float2*>(dst + 2 * n) = v;
+        });
+        __syncwarp();
+    }
+    __syncthreads();
+    const int tpr = nx / 4;
+    const int rl = threadIdx.x / tpr, x0 = 4 * (threadIdx.x - rl * tpr);
+    const int row = row0 + rl;
+    if (rl < rpc && row < nrows) {
+        const int z = row / a.ny, y = row - z * a.ny;
+        field_vec_cells<4, EXT, true>(a, x0, y, z, sH + rl * 3 * nx + x0, nx);
+    }
+}
+
 constexpr int kFieldV = 4;   // cells per thread of the one-material FP32 kernel (4 measured faster than 2)
 
 template <typename T>
-static void field_launch_t(mm_ctx* c, int mode, unsigned terms, const T* m, const T* Hd, T* out, T* out2,
-                           const T* m0, const T* k1, long long step_override, int gate, int kstage) {
+static FieldArgs<T> field_args(mm_ctx* c, int mode, unsigned terms, const T* m, const T* Hd, T* out, T* out2,
+                               const T* m0, const T* k1, long long step_override, int gate, int kstage) {
     FieldArgs<T> a{};
     a.gate = gate;
     a.kstage = kstage;
@@ -305,18 +361,32 @@ static void field_launch_t(mm_ctx* c, int mode, unsigned terms, const T* m, cons
         if (dn == 0) dn = 1;
         for (int d = 0; d < 3; ++d) a.dir[d] = (T)(q.dir[d] / dn);
     }
-    dim3 blk(32, 8);
-    dim3 grd((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
-    const double es = sizeof(T);
+    if constexpr (sizeof(T) == 4) { a.R0 = c->r0f; a.c_uniform = c->c00f; }
+    else { a.R0 = c->r0d; a.c_uniform = c->c00d; }
+    return a;
+}
+
+static double field_bytes(const mm_ctx* c, int mode, unsigned terms, bool hd) {
+    const double es = (double)c->esz;
     double bytes = 3 * es * 2 * c->N;          // read m, write out
-    if (Hd && (terms & MM_TERM_DEMAG)) bytes += 3 * es * c->N;
+    if (hd && (terms & MM_TERM_DEMAG)) bytes += 3 * es * c->N;
     if (mode == MODE_HEUN1 || mode == MODE_DM1) bytes += 3 * es * c->N;
     if (mode == MODE_HEUN2 || mode == MODE_DM2) bytes += 6 * es * c->N;
-    static const char* names[6] = {"field_H", "field_k", "field_heun1", "field_heun2", "field_dm1", "field_dm2"};
-    LaunchScope ls(c, names[mode], bytes);
+    return bytes;
+}
+
+static const char* const kFieldNames[6] = {"field_H", "field_k", "field_heun1", "field_heun2", "field_dm1",
+                                           "field_dm2"};
+
+template <typename T>
+static void field_launch_t(mm_ctx* c, int mode, unsigned terms, const T* m, const T* Hd, T* out, T* out2,
+                           const T* m0, const T* k1, long long step_override, int gate, int kstage) {
+    FieldArgs<T> a = field_args<T>(c, mode, terms, m, Hd, out, out2, m0, k1, step_override, gate, kstage);
+    const mm_grid& g = c->grid;
+    dim3 blk(32, 8);
+    dim3 grd((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+    LaunchScope ls(c, kFieldNames[mode], field_bytes(c, mode, terms, Hd != nullptr));
     if (c->uniform && !a.region) {
-        if constexpr (sizeof(T) == 4) { a.R0 = c->r0f; a.c_uniform = c->c00f; }
-        else { a.R0 = c->r0d; a.c_uniform = c->c00d; }
         if constexpr (sizeof(T) == 4) {
             if (g.nx % kFieldV == 0 && a.R0.present != 0.f) {
                 dim3 grdv((g.nx / kFieldV + 31) / 32, (g.ny + 7) / 8, g.nz);
@@ -341,6 +411,64 @@ void field_launch(mm_ctx* c, int mode, unsigned terms, const void* m, const void
     else
         field_launch_t<double>(c, mode, terms, (const double*)m, (const double*)Hd, (double*)out, (double*)out2,
                                (const double*)m0, (const double*)k1, step_override, gate, kstage);
+}
+
+// Inverse X pass + field kernel in one launch (FP32, one material, nx a
+// multiple of 4 dividing 1024, the one-row-per-warp inverse X transform of
+// the grid's half length available).  Measured against the two separate
+// kernels: 37.6 against 18.2 + 22.4 us per 256x256x16 evaluation, but 430
+// against 204 + 215 us at nx = 512 (two 8-warp CTAs per SM leave the
+// transform and field phases of a CTA unoverlapped), so rows of 512 keep
+// the separate kernels.
+#define MM_C2R_FIELD_LENGTHS(X) X(128) X(256)
+
+bool field_c2r_fusable(const mm_ctx* c) {
+    const mm_grid& g = c->grid;
+    if (c->prec != 32 || !c->dm.on || !c->uniform || c->d_region || c->r0f.present == 0.f) return false;
+    if (g.nx % 4 != 0 || 1024 % g.nx != 0 || c->dm.Lh != g.nx) return false;
+    switch (c->dm.Lh) {
+#define MM_CASE(n) case n: return true;
+        MM_C2R_FIELD_LENGTHS(MM_CASE)
+#undef MM_CASE
+        default: return false;
+    }
+}
+
+cudaError_t field_c2r_setup() {
+    cudaError_t e = cudaSuccess;
+#define MM_CASE(n)                                                                                            \
+    if (e == cudaSuccess)                                                                                     \
+        e = cudaFuncSetAttribute(c2r_field_kernel<n, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                                 (int)c2r_field_smem<n>());                                                   \
+    if (e == cudaSuccess)                                                                                     \
+        e = cudaFuncSetAttribute(c2r_field_kernel<n, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                 (int)c2r_field_smem<n>());
+    MM_C2R_FIELD_LENGTHS(MM_CASE)
+#undef MM_CASE
+    return e;
+}
+
+void field_c2r_launch(mm_ctx* c, int mode, unsigned terms, const void* m, void* out, void* out2, const void* m0,
+                      const void* k1, long long step_override, int gate, int kstage) {
+    FieldArgs<float> a = field_args<float>(c, mode, terms, (const float*)m, nullptr, (float*)out, (float*)out2,
+                                           (const float*)m0, (const float*)k1, step_override, gate, kstage);
+    const DemagPlan& d = c->dm;
+    C2RSpec sp{(const float2*)d.spec, (const float2*)d.tw_x, d.PyA, d.Wk};
+    const int rpc = 1024 / c->grid.nx;
+    const long long rows = (long long)c->grid.ny * c->grid.nz;
+    const unsigned grid = (unsigned)((rows + rpc - 1) / rpc);
+    const double bytes = field_bytes(c, mode, terms, false) + 3.0 * rows * (d.Kx * sizeof(float2));
+    LaunchScope ls(c, "c2r_field", bytes);
+    switch (d.Lh) {
+#define MM_CASE(n)                                                                                            \
+    case n:                                                                                                   \
+        if (c->ext_terms) c2r_field_kernel<n, true><<<grid, 256, c2r_field_smem<n>(), c->stream>>>(a, sp);      \
+        else c2r_field_kernel<n, false><<<grid, 256, c2r_field_smem<n>(), c->stream>>>(a, sp);                 \
+        break;
+        MM_C2R_FIELD_LENGTHS(MM_CASE)
+#undef MM_CASE
+        default: break;
+    }
 }
 
 // Raw Philox words and the thermal field of every cell at a given step.

@@ -218,6 +218,20 @@ void demag_eval(mm_ctx* c, const void* m, void* Hd) {
     else demag_apply(c, m, Hd);
 }
 
+// H_demag(m) followed by the field kernel of `mode`.  With exact demag on a
+// grid that allows it, the last demag pass (inverse X) runs inside the
+// field kernel and H_demag never goes through global memory.
+static void demag_and_field(mm_ctx* c, bool demag, int mode, unsigned terms, const void* m, void* out, void* out2,
+                            const void* m0, const void* k1, int gate, int kstage) {
+    if (demag && !surrogate_active(c) && field_c2r_fusable(c)) {
+        demag_apply_partial(c, m, 0);
+        field_c2r_launch(c, mode, terms, m, out, out2, m0, k1, -1, gate, kstage);
+        return;
+    }
+    if (demag) demag_eval(c, m, c->d_hd);
+    field_launch(c, mode, terms, m, demag ? c->d_hd : nullptr, out, out2, m0, k1, -1, gate, kstage);
+}
+
 template <typename T>
 static void rk45_attempt_t(mm_ctx* c) {
     const long long N = c->N, n3 = 3 * N;
@@ -230,7 +244,15 @@ static void rk45_attempt_t(mm_ctx* c) {
     const unsigned terms = c->terms;
     const bool demag = c->dm.on && (terms & MM_TERM_DEMAG);
     const bool fused = demag && sizeof(T) == 4 && !surrogate_active(c) && demag_stage_fusable(c);
+    const bool fused_c2r = fused && field_c2r_fusable(c);
     for (int s = 1; s < 7; ++s) {
+        if (fused_c2r) {
+            // stage combine inside the forward X pass, inverse X pass inside the field kernel
+            demag_apply_partial(c, nullptr, s);
+            field_c2r_launch(c, MODE_K, terms, c->d_mtmp, s < 6 ? c->d_k[s] : nullptr, nullptr, nullptr, nullptr,
+                             -1, 1, 6);
+            continue;
+        }
         if (fused) {
             demag_apply_stage(c, s, c->d_hd);
         } else {
@@ -281,8 +303,7 @@ void rk45_attempt(mm_ctx* c) {
 void rk45_first_slope(mm_ctx* c) {
     const unsigned terms = c->terms;
     const bool demag = c->dm.on && (terms & MM_TERM_DEMAG);
-    if (demag) demag_eval(c, c->d_m, c->d_hd);
-    field_launch(c, MODE_K, terms, c->d_m, demag ? c->d_hd : nullptr, nullptr, nullptr, nullptr, nullptr, -1, 0, 0);
+    demag_and_field(c, demag, MODE_K, terms, c->d_m, nullptr, nullptr, nullptr, nullptr, 0, 0);
 }
 
 void heun_batch_begin(mm_ctx* c) {
@@ -349,8 +370,7 @@ static void rk4_step_t(mm_ctx* c) {
                                                             cs[s], (T*)c->d_mtmp, n3);
             ms = c->d_mtmp;
         }
-        if (demag) demag_apply(c, ms, c->d_hd);
-        field_launch(c, MODE_K, terms, ms, demag ? c->d_hd : nullptr, c->d_k[s], nullptr, nullptr, nullptr, -1, 1, 0);
+        demag_and_field(c, demag, MODE_K, terms, ms, c->d_k[s], nullptr, nullptr, nullptr, 1, 0);
     }
     {
         LaunchScope ls(c, "rk4_final", (double)sizeof(T) * N * 18);
@@ -374,13 +394,9 @@ void heun_step(mm_ctx* c) {
         heun_begin_kernel<<<1, 1, 0, c->stream>>>(c->d_state);
     }
     // predictor: k1 = f(m, H(m) + H_th); m* = m + dt k1
-    if (demag) demag_apply(c, c->d_m, c->d_hd);
-    field_launch(c, MODE_HEUN1, terms, c->d_m, demag ? c->d_hd : nullptr, c->d_mtmp, c->d_k[0], nullptr, nullptr,
-                 -1, 1, 0);
+    demag_and_field(c, demag, MODE_HEUN1, terms, c->d_m, c->d_mtmp, c->d_k[0], nullptr, nullptr, 1, 0);
     // corrector: m' = normalise(m + dt/2 (k1 + f(m*, H(m*) + H_th))), same noise
-    if (demag) demag_apply(c, c->d_mtmp, c->d_hd);
-    field_launch(c, MODE_HEUN2, terms, c->d_mtmp, demag ? c->d_hd : nullptr, c->d_m, nullptr, c->d_m, c->d_k[0],
-                 -1, 1, 0);
+    demag_and_field(c, demag, MODE_HEUN2, terms, c->d_mtmp, c->d_m, nullptr, c->d_m, c->d_k[0], 1, 0);
     LaunchScope ls(c, "heun_advance", 0.0);
     heun_advance_kernel<<<1, 1, 0, c->stream>>>(c->d_state);
 }
@@ -398,12 +414,8 @@ void dm_step(mm_ctx* c) {
         LaunchScope ls(c, "dm_begin", 0.0);
         heun_begin_kernel<<<1, 1, 0, c->stream>>>(c->d_state);
     }
-    if (demag) demag_apply(c, c->d_m, c->d_hd);
-    field_launch(c, MODE_DM1, terms, c->d_m, demag ? c->d_hd : nullptr, c->d_mtmp, c->d_k[0], nullptr, nullptr,
-                 -1, 1, 0);
-    if (demag) demag_apply(c, c->d_mtmp, c->d_hd);
-    field_launch(c, MODE_DM2, terms, c->d_mtmp, demag ? c->d_hd : nullptr, c->d_m, nullptr, c->d_m, c->d_k[0],
-                 -1, 1, 0);
+    demag_and_field(c, demag, MODE_DM1, terms, c->d_m, c->d_mtmp, c->d_k[0], nullptr, nullptr, 1, 0);
+    demag_and_field(c, demag, MODE_DM2, terms, c->d_mtmp, c->d_m, nullptr, c->d_m, c->d_k[0], 1, 0);
     LaunchScope ls(c, "dm_advance", 0.0);
     heun_advance_kernel<<<1, 1, 0, c->stream>>>(c->d_state);
 }
@@ -447,12 +459,8 @@ static void dm_adaptive_attempt_t(mm_ctx* c) {
         LaunchScope ls(c, "dm_begin", 0.0);
         attempt_begin_kernel<<<1, 1, 0, c->stream>>>(c->d_state);
     }
-    if (demag) demag_apply(c, c->d_m, c->d_hd);
-    field_launch(c, MODE_DM1, terms, c->d_m, demag ? c->d_hd : nullptr, c->d_mtmp, c->d_k[0], nullptr, nullptr,
-                 -1, 1, 0);
-    if (demag) demag_apply(c, c->d_mtmp, c->d_hd);
-    field_launch(c, MODE_DM2, terms, c->d_mtmp, demag ? c->d_hd : nullptr, c->d_k[1], nullptr, c->d_m, c->d_k[0],
-                 -1, 1, 0);
+    demag_and_field(c, demag, MODE_DM1, terms, c->d_m, c->d_mtmp, c->d_k[0], nullptr, nullptr, 1, 0);
+    demag_and_field(c, demag, MODE_DM2, terms, c->d_mtmp, c->d_k[1], nullptr, c->d_m, c->d_k[0], 1, 0);
     {
         LaunchScope ls(c, "dm_error", (double)sizeof(T) * 6 * N);
         dm_error_kernel<T><<<nb, tb, 0, c->stream>>>(c->d_state, (const T*)c->d_k[1], (const T*)c->d_mtmp, N);

@@ -35,6 +35,10 @@ CASES = [
     ("fused", W.Grid(170, 12, 2, 2e-9, 2e-9, 2e-9),
      W.with_cells(W.Material(Ms=5.8e5, A=1.5e-11, alpha=0.1, Ku1=8e5, u=(0, 0, 1), D=3e-3),
                   W.random_material_cells(W.Grid(170, 12, 2, 2e-9, 2e-9, 2e-9), 9)), (0.0, 0.0, 0.05)),
+    # one material, nx = 128 (half length 128): in FP32 the inverse X pass
+    # runs inside the field kernel (H_demag stays in shared memory)
+    ("c2r_field", W.Grid(128, 6, 2, 2e-9, 2e-9, 2e-9),
+     W.Material(Ms=5.8e5, A=1.5e-11, alpha=0.1, Ku1=8e5, u=(0, 0, 1), D=3e-3), (0.01, 0.0, 0.02)),
 ]
 
 
@@ -126,6 +130,40 @@ def test_heun_thermal_with_torque_matches_oracle(prec, torque):
         n = 60
         for _ in range(n):
             o.heun_step()
+        mm.mm_step(ctx, n)
+        err = np.abs(mm.mm_get_m(ctx, 0, m0.shape) - o.m).max()
+        assert err <= (1e-11 if prec == 64 else 1e-5), err
+    finally:
+        mm.mm_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("integ", ["heun", "dm"])
+def test_fused_inverse_x_field_heun_and_dm(prec, integ):
+    """Heun and Depondt-Mertens steps at 300 K with spin-orbit torque on a
+    one-material 256 x 4 film: in FP32 both the predictor and the corrector
+    take the demag field from the fused inverse-X + field kernel."""
+    mm = need_gpu()
+    from oracle.llg import Torque, replica_seed
+    grid = W.Grid(256, 4, 1, 2e-9, 2e-9, 1e-9)
+    mat = W.Material(Ms=1.1e6, A=2e-11, alpha=0.02, Ku1=9e5, u=(0, 0, 1), D=1e-3)
+    J = 2.0e11
+    tq_o = Torque(kind="sot", J=J, p=(0, 1, 0), theta_SH=0.1, fl_ratio=0.2)
+    tq_g = mm.make_torque(mm.MM_TORQUE_SOT, p=(0, 1, 0), theta_SH=0.1, fl_ratio=0.2)
+    m0 = W.m_perp(grid, seed=5, tilt=0.3)
+    seed = 13
+    o = _oracle_solver(grid, mat, m0, terms=("exchange", "dmi", "anisotropy", "demag"), torque=tq_o, T=300.0,
+                       seed=replica_seed(seed, 0), dt=1e-14)
+    ctx = make_ctx(mm, grid, mat, precision=prec, integrator=integ, demag=True, dt=1e-14, T=300.0, seed=seed)
+    try:
+        mm.mm_set_m(ctx, 0, m0)
+        mm.mm_set_torque(ctx, tq_g, [J])
+        n = 40
+        for _ in range(n):
+            if integ == "heun":
+                o.heun_step()
+            else:
+                o.dm_step()
         mm.mm_step(ctx, n)
         err = np.abs(mm.mm_get_m(ctx, 0, m0.shape) - o.m).max()
         assert err <= (1e-11 if prec == 64 else 1e-5), err
