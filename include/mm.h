@@ -521,9 +521,13 @@ MM_API mm_status mm_get_profile(mm_ctx* ctx, mm_profile_entry* out, int* n_inout
  * MM_ERR_OOM, MM_ERR_CUDA. */
 MM_API mm_status mm_measure_peak(int precision, double* flops_per_s);
 
-/* Host-side fault injection for tests: 1 = next allocation fails,
- * 2 = poison the state with NaN at the next step, 3 = force dt underflow.
- * No passage: test convenience. */
+/* Fault injection for tests: 1 = next allocation fails, 2 = poison the
+ * state with NaN at the next step, 3 = force dt underflow, 4 = the next
+ * evaluation of the surrogate network issues no tensor-core work and polls
+ * its accumulator barrier only 1000 times, so the bounded wait runs out with
+ * nothing asynchronous in flight (mm_surrogate_forward then returns
+ * MM_ERR_TIMEOUT and the context stays usable).  No passage: test
+ * convenience.  Errors: MM_ERR_ARG (NULL, fault outside 0..4). */
 MM_API mm_status mm_debug_inject(mm_ctx* ctx, int fault);
 
 /* Message of the last failure of ctx (or of the last context-less call

@@ -1471,7 +1471,7 @@ mm_status mm_get_profile(mm_ctx* c, mm_profile_entry* out, int* n) {
 }
 
 mm_status mm_debug_inject(mm_ctx* c, int fault) {
-    if (!c || fault < 0 || fault > 3) return MM_ERR_ARG;
+    if (!c || fault < 0 || fault > 4) return MM_ERR_ARG;
     c->inject = fault;
     return MM_OK;
 }

@@ -18,6 +18,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -113,31 +114,69 @@ __device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float* v) {
 // ---------------------------------------------------------------------------
 enum { OUT_BF16 = 0, OUT_FIELD = 1, OUT_MASKED = 2 };
 
-template <int CIN, int COUTP, int RPB>
-struct ConvSmem {
+// Row-streaming variant: one CTA walks down a 128-pixel column block of one
+// image over a run of output rows.  The packed weights are loaded once and
+// stay in shared memory; input rows live in a ring of kRing row slots filled
+// by cp.async kPref rows ahead, so every input row is fetched once per CTA
+// (a new output row needs one new input row: the four above are still in
+// the ring).  Thread 0 issues the 25 x CIN/16 MMAs of output row i into one
+// of two tensor-memory accumulators while all four warps drain row i - 1 from
+// the other (tcgen05.ld, bias, ReLU, BF16 pack, store), so loads, MMAs and
+// the epilogue of neighbouring rows overlap.
+//   slots: input row r0 + off of the run sits in slot off % kRing; output
+//          row r0 + i reads offsets i .. i + 4; the load issued at iteration
+//          i (offset i + 4 + kPref) reuses the slot of offset
+//          i + 4 + kPref - kRing = i - 2, whose last reader (output row
+//          i - 2) was drained at iteration i - 1.
+//   waits: every mbarrier wait gives up after a.wait_limit polls (default
+//          2^24); the CTA then records the timeout in a.err, drains nothing
+//          more and frees its tensor memory.  a.skip_mma (a test mode) issues
+//          no MMA and no commit, so the first wait runs out with no
+//          asynchronous work in flight.
+constexpr int kPref = 2;
+constexpr int kRing = 5 + kPref + 1;
+
+template <int CIN, int COUTP>
+struct StreamSmem {
     static constexpr int kChunks = CIN / 8;
-    static constexpr int kStripBytes = kChunks * kStrip * 16;
-    static constexpr int kStrips = RPB + 4;
-    static constexpr int kA = kStrips * kStripBytes;
+    static constexpr int kRowBytes = kChunks * kStrip * 16;
+    static constexpr int kA = kRing * kRowBytes;
     static constexpr int kB = kTaps * kChunks * COUTP * 16;
-    static constexpr int kSlack = 16384;           // keeps every descriptor reach inside the allocation
+    static constexpr int kSlack = 16384;
     static constexpr int kTotal = kA + kB + kSlack + 64;
-    static constexpr int kTmemCols = RPB * COUTP < 32 ? 32 : RPB * COUTP;
+    static constexpr int kTmemCols = 2 * COUTP < 32 ? 32 : 2 * COUTP;
 };
 
-template <int CIN, int COUTP, int RPB, int MODE, bool RELU>
-__global__ void __launch_bounds__(128) conv_tc_kernel(ConvArgs a) {
-    using L = ConvSmem<CIN, COUTP, RPB>;
-    static_assert(L::kTmemCols == 32 || L::kTmemCols == 64 || L::kTmemCols == 128 || L::kTmemCols == 256,
-                  "tensor-memory allocation must be a power of two");
+__device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, bool valid) {
+    const uint32_t sa = smem_u32(smem);
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <int CIN, int COUTP, int MODE, bool RELU>
+__global__ void __launch_bounds__(128, 1) conv_tc_stream_kernel(ConvArgs a) {
+    using L = StreamSmem<CIN, COUTP>;
+    static_assert(L::kTmemCols == 32 || L::kTmemCols == 64, "tensor-memory allocation");
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;
     unsigned char* sB = smem + L::kA;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::kA + L::kB + L::kSlack);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::kA + L::kB + L::kSlack);     // [2]
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::kA + L::kB + L::kSlack + 16);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int H = a.H, W = a.W, Wp = W + 4;
-    const int j0 = blockIdx.x * kTile, i0 = blockIdx.y * RPB, b = blockIdx.z;
+    // run of output rows: blockIdx.x -> (image b, column block jb, rows [r0, r1))
+    const int ncb = (W + kTile - 1) / kTile;
+    const int runs_per_col = (H + a.rows_per_run - 1) / a.rows_per_run;
+    const int run = blockIdx.x % runs_per_col;
+    const int jb = (blockIdx.x / runs_per_col) % ncb;
+    const int b = blockIdx.x / (runs_per_col * ncb);
+    const int r0 = run * a.rows_per_run, r1 = min(H, r0 + a.rows_per_run);
+    const int j0 = jb * kTile;
+    const int nrow = r1 - r0;
+    const long wait_limit = a.wait_limit > 0 ? a.wait_limit : (1L << 24);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -145,61 +184,55 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(ConvArgs a) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        mbar_init(smem_u32(mbar), 1);
+        mbar_init(smem_u32(&mbar[0]), 1);
+        mbar_init(smem_u32(&mbar[1]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // operands: weights (pre-packed in the shared layout) and input row strips
-    const uint4* wsrc = a.wpk;
-    for (int q = tid; q < L::kB / 16; q += 128) reinterpret_cast<uint4*>(sB)[q] = wsrc[q];
-    const uint4 zero = make_uint4(0, 0, 0, 0);
-    for (int q = tid; q < L::kStrips * L::kChunks * kStrip; q += 128) {
-        const int px = q % kStrip;
-        const int rest = q / kStrip;
-        const int ch = rest % L::kChunks, s = rest / L::kChunks;
-        const int row = i0 + s, col = j0 + px;   // padded coordinates
-        uint4 v = zero;
-        if (row < H + 4 && col < Wp)
-            v = *reinterpret_cast<const uint4*>(a.in + (((long long)b * (H + 4) + row) * Wp + col) * CIN + ch * 8);
-        reinterpret_cast<uint4*>(sA)[(s * L::kChunks + ch) * kStrip + px] = v;
+    // padded input row r0 + off (off < nrow + 4) of image b -> ring slot off % kRing
+    auto load_row = [&](int off) {
+        unsigned char* dst = sA + (off % kRing) * L::kRowBytes;
+        const __nv_bfloat16* src = a.in + ((long long)b * (H + 4) + r0 + off) * Wp * CIN;
+        for (int e = tid; e < L::kChunks * kStrip; e += 128) {
+            const int px = e % kStrip, ch = e / kStrip;
+            const int col = j0 + px;
+            const bool ok = col < Wp;
+            cp_async16_zfill(dst + (ch * kStrip + px) * 16, src + (long long)(ok ? col : 0) * CIN + ch * 8, ok);
+        }
+    };
+    // weights (group 0) and the first 4 + kPref input rows (one group each)
+    for (int q = tid; q < L::kB / 16; q += 128)
+        cp_async16_zfill(sB + q * 16, reinterpret_cast<const unsigned char*>(a.wpk) + (long long)q * 16, true);
+    cp_async_commit();
+    for (int q = 0; q < 4 + kPref; ++q) {
+        if (q < nrow + 4) load_row(q);
+        cp_async_commit();
     }
-    fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tslot;
-    if (tid == 0) {
-        const uint32_t idesc = umma_idesc(kTile, COUTP);
-        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-        for (int r = 0; r < RPB; ++r) {
-            for (int p = 0; p < 5; ++p)
-                for (int q = 0; q < 5; ++q)
-#pragma unroll
-                    for (int kk = 0; kk < CIN / 16; ++kk) {
-                        const int tap = p * 5 + q;
-                        const uint32_t aa = a0 + (((r + p) * L::kChunks + 2 * kk) * kStrip + q) * 16;
-                        const uint32_t bb = b0 + ((tap * L::kChunks + 2 * kk) * COUTP) * 16;
-                        umma_f16(tbase + r * COUTP, umma_desc(aa, kStrip * 16, 128), umma_desc(bb, COUTP * 16, 128),
-                                 idesc, (p | q | kk) != 0);
-                    }
+    const uint32_t idesc = umma_idesc(kTile, COUTP);
+    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+    bool ok = true;
+
+    // drain output row i from accumulator i % 2
+    auto epilogue = [&](int i) {
+        uint32_t done = 0;
+        const uint32_t mb = smem_u32(&mbar[i & 1]);
+        for (long it = 0; it < wait_limit && !done; ++it) done = mbar_try_wait(mb, (uint32_t)((i >> 1) & 1));
+        done = __syncthreads_and(done);
+        if (!done) {
+            if (tid == 0 && a.err) atomicExch(a.err, 1);
+            return false;
         }
-        umma_commit(smem_u32(mbar));
-    }
-    // wait for the accumulators (bounded)
-    uint32_t done = 0;
-    for (long it = 0; it < (1L << 24) && !done; ++it) done = mbar_try_wait(smem_u32(mbar), 0);
-    // block-uniform outcome: the warp-collective loads below run in every
-    // warp or in none
-    done = __syncthreads_and(done);
-    if (!done && tid == 0 && a.err) atomicExch(a.err, 1);
-    tc_fence_after();
-    if (done) {
+        tc_fence_after();
         const int m = warp * 32 + (tid & 31);
         const int j = j0 + m;
-        for (int r = 0; r < RPB; ++r) {
-            float v[COUTP];
-            tmem_ld<COUTP>(tbase + ((uint32_t)(warp * 32) << 16) + r * COUTP, v);
-            const int i = i0 + r;
-            if (i >= H || j >= W) continue;
+        float v[COUTP];
+        tmem_ld<COUTP>(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)((i & 1) * COUTP), v);
+        tc_fence_before();
+        const int row = r0 + i;
+        if (j < W) {
             if (a.bias)
 #pragma unroll
                 for (int c = 0; c < COUTP; ++c) v[c] += a.bias[c];
@@ -207,12 +240,12 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(ConvArgs a) {
 #pragma unroll
                 for (int c = 0; c < COUTP; ++c) v[c] = fmaxf(v[c], 0.f);
             if (MODE == OUT_FIELD) {
-                float* o = reinterpret_cast<float*>(a.out) + (((long long)b * H + i) * W + j) * 3;
+                float* o = reinterpret_cast<float*>(a.out) + (((long long)b * H + row) * W + j) * 3;
                 o[0] = v[0] * a.out_scale;
                 o[1] = v[1] * a.out_scale;
                 o[2] = v[2] * a.out_scale;
             } else {
-                const long long pix = ((long long)b * (H + 4) + i + 2) * Wp + j + 2;
+                const long long pix = ((long long)b * (H + 4) + row + 2) * Wp + j + 2;
                 if (MODE == OUT_MASKED) {
                     const __nv_bfloat16* mk = a.mask + pix * COUTP;
 #pragma unroll
@@ -230,7 +263,38 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(ConvArgs a) {
                 }
             }
         }
+        return true;
+    };
+
+    for (int i = 0; i < nrow && ok; ++i) {
+        // next input row kPref ahead (its slot's last reader was drained at i - 1)
+        if (i + 4 + kPref < nrow + 4) load_row(i + 4 + kPref);
+        cp_async_commit();
+        cp_async_wait<kPref>();             // padded rows up to i + 4 have landed
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0 && !a.skip_mma) {
+            const uint32_t dacc = tbase + (uint32_t)((i & 1) * COUTP);
+            for (int p = 0; p < 5; ++p) {
+                const uint32_t arow = a0 + ((i + p) % kRing) * L::kRowBytes;
+                for (int q = 0; q < 5; ++q)
+#pragma unroll
+                    for (int kk = 0; kk < CIN / 16; ++kk) {
+                        const int tap = p * 5 + q;
+                        const uint32_t aa = arow + ((2 * kk) * kStrip + q) * 16;
+                        const uint32_t bb = b0 + ((tap * L::kChunks + 2 * kk) * COUTP) * 16;
+                        umma_f16(dacc, umma_desc(aa, kStrip * 16, 128), umma_desc(bb, COUTP * 16, 128), idesc,
+                                 (p | q | kk) != 0);
+                    }
+            }
+            umma_commit(smem_u32(&mbar[i & 1]));
+        }
+        if (i > 0) ok = epilogue(i - 1);
     }
+    if (ok && nrow > 0) ok = epilogue(nrow - 1);
+    cp_async_wait<0>();
     tc_fence_before();
     __syncthreads();
     if (warp == 0)
@@ -414,42 +478,52 @@ __global__ void field_from_cnn_kernel(const float* __restrict__ out, const T* __
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-template <int CIN, int COUTP, int RPB, int MODE, bool RELU>
-static cudaError_t launch_conv_tc(const ConvArgs& a, int B, cudaStream_t s) {
-    using L = ConvSmem<CIN, COUTP, RPB>;
+// Output rows per CTA of the row-streaming kernel: about one CTA per SM
+// over all images and column blocks, at least 4 rows (the ring's four-row
+// overlap is paid once per run).
+static int stream_rows_per_run(int B, int H, int W) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+    }
+    const long long cols = (long long)B * ((W + kTile - 1) / kTile);
+    const long long rows = (cols * H + sms - 1) / sms;
+    return (int)std::max<long long>(4, std::min<long long>(H, rows));
+}
+
+template <int CIN, int COUTP, int MODE, bool RELU>
+static cudaError_t launch_conv_stream(ConvArgs a, int B, cudaStream_t s) {
+    using L = StreamSmem<CIN, COUTP>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<CIN, COUTP, RPB, MODE, RELU>,
+        cudaError_t e = cudaFuncSetAttribute(conv_tc_stream_kernel<CIN, COUTP, MODE, RELU>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, L::kTotal);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    dim3 grid((a.W + kTile - 1) / kTile, (a.H + RPB - 1) / RPB, B);
-    conv_tc_kernel<CIN, COUTP, RPB, MODE, RELU><<<grid, 128, L::kTotal, s>>>(a);
+    a.rows_per_run = stream_rows_per_run(B, a.H, a.W);
+    const int runs = (a.H + a.rows_per_run - 1) / a.rows_per_run;
+    const int grid = B * ((a.W + kTile - 1) / kTile) * runs;
+    conv_tc_stream_kernel<CIN, COUTP, MODE, RELU><<<grid, 128, L::kTotal, s>>>(a);
     return cudaGetLastError();
 }
 
-// layer shapes of the 3 -> 32 -> 32 -> 32 -> 3 network (input padded to 16 ch,
-// output to 16 ch)
-struct CnnLayer {
-    int cin, cout, cinp, coutp;
-};
-static const CnnLayer kLayers[4] = {{3, 32, 16, 32}, {32, 32, 32, 32}, {32, 32, 32, 32}, {32, 3, 32, 16}};
-
 cudaError_t cnn_conv(int layer, bool backward, const ConvArgs& a, int B, cudaStream_t s) {
-    constexpr int RPB = 4;
     if (!backward) {
         switch (layer) {
-            case 0: return launch_conv_tc<16, 32, RPB, OUT_BF16, true>(a, B, s);
+            case 0: return launch_conv_stream<16, 32, OUT_BF16, true>(a, B, s);
             case 1:
-            case 2: return launch_conv_tc<32, 32, RPB, OUT_BF16, true>(a, B, s);
-            default: return launch_conv_tc<32, 16, RPB, OUT_FIELD, false>(a, B, s);
+            case 2: return launch_conv_stream<32, 32, OUT_BF16, true>(a, B, s);
+            default: return launch_conv_stream<32, 16, OUT_FIELD, false>(a, B, s);
         }
     }
     // input gradient of `layer`: channels in = its cout(p), out = its cin(p), masked by the layer's input
     switch (layer) {
-        case 3: return launch_conv_tc<16, 32, RPB, OUT_MASKED, false>(a, B, s);
-        default: return launch_conv_tc<32, 32, RPB, OUT_MASKED, false>(a, B, s);
+        case 3: return launch_conv_stream<16, 32, OUT_MASKED, false>(a, B, s);
+        default: return launch_conv_stream<32, 32, OUT_MASKED, false>(a, B, s);
     }
 }
 

@@ -18,6 +18,9 @@ struct ConvArgs {
     float out_scale;           // final layer
     int H, W;
     int* err;                  // set to 1 when a bounded wait runs out
+    int rows_per_run;          // row-streaming kernel: output rows per CTA (set by the launcher)
+    long wait_limit;           // polls before a bounded wait gives up (0: the default, 2^24)
+    int skip_mma;              // test mode: issue no MMA and no commit (the wait must run out)
 };
 
 cudaError_t cnn_conv(int layer, bool backward, const ConvArgs& a, int B, cudaStream_t s);

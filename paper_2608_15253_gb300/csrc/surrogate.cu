@@ -270,8 +270,14 @@ static mm_status run_forward(mm_ctx* c, int B, int H, int W, float out_scale, in
     SurrogateHost* s = c->surr;
     __nv_bfloat16* in[4] = {s->x0, s->h1, s->h2, s->h3};
     void* out[4] = {s->h1, s->h2, s->h3, s->y};
+    // test mode (mm_debug_inject 4): no tensor-core work is issued and the
+    // accumulator wait gives up after 1000 polls
+    const bool starve = c->inject == 4;
+    if (starve) c->inject = 0;
     for (int l = 0; l < 4; ++l) {
         ConvArgs a{};
+        a.skip_mma = starve ? 1 : 0;
+        a.wait_limit = starve ? 1000 : 0;
         a.in = in[l];
         a.wpk = reinterpret_cast<const uint4*>(s->wpk[l]);
         a.bias = s->biasp[l];
@@ -543,7 +549,10 @@ mm_status mm_surrogate_forward(mm_ctx* c, int B, int H, int W, const double* x, 
     if (e != cudaSuccess) return cuda_check(c, e, "surrogate forward");
     int err = 0;
     cudaMemcpy(&err, c->surr->d_err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (err) return set_error(c, MM_ERR_TIMEOUT, "tensor-core accumulator wait ran out");
+    if (err) {
+        cudaMemset(c->surr->d_err, 0, sizeof(int));   // reported once; the context stays usable
+        return set_error(c, MM_ERR_TIMEOUT, "tensor-core accumulator wait ran out");
+    }
     for (int b = 0; b < B; ++b)
         for (int cc = 0; cc < 3; ++cc)
             for (long long p = 0; p < (long long)H * W; ++p)

@@ -6,7 +6,13 @@ gradients (themselves pinned by finite differences); training on pairs the
 exact FFT demag generates; surrogate-accelerated stepping with the exact
 demag as monitor and fallback.
 
-Tolerances: relative L2 error 1e-2 (BF16 operands, 8-bit mantissa)."""
+Tolerances (relative L2): forward 3e-3, gradients 3e-2.  In the forward
+pass both sides round the same operands and activations to BF16 at the same
+points; what is left is the FP32 (tensor core) against FP64 (oracle)
+accumulation order, which now and then moves a stored BF16 activation by
+one unit (2^-8 relative).  The backward pass also stores each layer's
+back-propagated gradient in BF16 (the oracle keeps FP64), so the first
+layer's weight gradient, three such roundings deep, sits near 2e-2."""
 import numpy as np
 import pytest
 
@@ -64,8 +70,8 @@ def test_tensor_core_forward_matches_simt_and_oracle():
             y_tc = mm.mm_surrogate_forward(ctx, x, path=0)
             y_simt = mm.mm_surrogate_forward(ctx, x, path=1)
             y_or = _oracle_forward_bf16(_params_from_flat(flat), x)
-            assert _rel(y_tc, y_simt) < 1e-2, _rel(y_tc, y_simt)
-            assert _rel(y_tc, y_or) < 1e-2, _rel(y_tc, y_or)
+            assert _rel(y_tc, y_simt) < 3e-3, _rel(y_tc, y_simt)
+            assert _rel(y_tc, y_or) < 3e-3, _rel(y_tc, y_or)
     finally:
         mm.mm_destroy(ctx)
 
@@ -87,12 +93,12 @@ def test_gradients_match_oracle():
         y, cache = cnn.forward(params, xb)
         L, dy = cnn.mse(y, t)
         grads, _ = cnn.backward(params, cache, dy)
-        assert abs(loss - L) <= 2e-2 * L
+        assert abs(loss - L) <= 3e-3 * L, (loss, L)
         gflat = np.concatenate([np.concatenate([G["w"].ravel(), G["b"]]) for G in grads])
         o = 0
         for li, (co, ci) in enumerate([(32, 3), (32, 32), (32, 32), (3, 32)]):
             n = co * ci * 25 + co
-            assert _rel(g[o:o + n], gflat[o:o + n]) < 5e-2, (li, _rel(g[o:o + n], gflat[o:o + n]))
+            assert _rel(g[o:o + n], gflat[o:o + n]) < 3e-2, (li, _rel(g[o:o + n], gflat[o:o + n]))
             o += n
     finally:
         mm.mm_destroy(ctx)
@@ -151,24 +157,26 @@ def _near_field(mm, grid, dm):
     return out[:, None]
 
 
-def test_trained_network_beats_holding_the_field():
-    """What the network adds: k steps after a refresh, H_ref + network
-    increment is closer to the exact demag field than the refreshed field
-    held constant (the method without the network)."""
+@pytest.mark.parametrize("k", [4, 10])
+def test_trained_network_beats_holding_the_field(k):
+    """What the network adds: k steps after a refresh, H_ref - Ms N_near dm +
+    network increment is closer to the exact demag field than both the
+    exact near-field part alone (what the network rides on) and the
+    refreshed field held constant (the method without any prediction)."""
     mm = need_gpu()
     ctx, grid = _ctx(mm, n=128)
     try:
         m0 = W.m_skyrmion_lattice(grid, seed=4, spacing=40e-9, radius=8e-9)
         mm.mm_set_m(ctx, 0, m0)
         mm.mm_step(ctx, 30)
-        cfg = mm.make_train_cfg(n_snapshots=16, snap_every=2, max_gap=4, crop=64, batch=8, steps=400, lr=2e-3, seed=7)
+        cfg = mm.make_train_cfg(n_snapshots=16, snap_every=2, max_gap=6, crop=64, batch=8, steps=800, lr=2e-3, seed=7)
         mm.mm_surrogate_train(ctx, cfg)
         st = mm.mm_surrogate_get_stats(ctx)
         c_in, c_out = st["c_in"], st["c_out"]
         shape = m0.shape
         m_ref = mm.mm_get_m(ctx, 0, shape)
         H_ref = mm.mm_get_heff(ctx, 0, shape, 16)
-        mm.mm_step(ctx, 4)
+        mm.mm_step(ctx, k)
         m = mm.mm_get_m(ctx, 0, shape)
         H = mm.mm_get_heff(ctx, 0, shape, 16)
         dm = m - m_ref
@@ -180,9 +188,8 @@ def test_trained_network_beats_holding_the_field():
         err_net = np.abs(H_net - H).max() / scale
         err_hold = np.abs(H_ref - H).max() / scale
         err_near = np.abs(H_near - H).max() / scale
-        # the learned part must beat holding the field; report what it adds
-        # on top of the exact near field
-        assert err_net < 0.5 * err_hold, (err_net, err_near, err_hold)
+        assert err_net < err_near, (k, err_net, err_near, err_hold)
+        assert err_net < 0.5 * err_hold, (k, err_net, err_near, err_hold)
     finally:
         mm.mm_destroy(ctx)
 
@@ -244,5 +251,30 @@ def test_diverged_network_triggers_the_exact_fallback():
         assert st["fallback"] == 1, st
         assert not st["last_error"] <= 1e3, st
         assert np.isfinite(mm.mm_get_m(ctx, 0, m0.shape)).all()
+    finally:
+        mm.mm_destroy(ctx)
+
+
+def test_bounded_accumulator_wait_runs_out_and_context_survives():
+    """The tensor-core accumulator wait is bounded: in the test mode no MMA is
+    issued, the barrier is never signalled, the wait gives up after 1000
+    polls and the call returns MM_ERR_TIMEOUT; the next evaluation runs
+    normally and gives the same output as before the fault."""
+    mm = need_gpu()
+    ctx, _ = _ctx(mm)
+    try:
+        rng = np.random.default_rng(9)
+        from oracle import cnn
+        flat = np.concatenate([np.concatenate([P["w"].ravel(), rng.normal(0, 0.05, P["b"].shape)])
+                               for P in cnn.init_params(seed=6)])
+        mm.mm_surrogate_weights(ctx, flat, c_in=1.0)
+        x = rng.normal(size=(1, 3, 24, 150))
+        y0 = mm.mm_surrogate_forward(ctx, x)
+        mm.mm_debug_inject(ctx, 4)
+        with pytest.raises(mm.MMError) as e:
+            mm.mm_surrogate_forward(ctx, x)
+        assert e.value.status == mm.MM_ERR_TIMEOUT
+        y1 = mm.mm_surrogate_forward(ctx, x)
+        assert np.array_equal(y0, y1)
     finally:
         mm.mm_destroy(ctx)
