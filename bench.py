@@ -499,6 +499,31 @@ def variant_cufft(mm, stream, reps=5):
                     "CUDA events, FP32", "cases": out}
 
 
+def variant_drift(mm, stream, steps=200, every=20, dt=2e-14):
+    """FP32 against FP64 on the 256x256x16 DMI film from its random state:
+    the same fixed RK45 steps replayed in both precisions, max|m32 - m64|
+    after every `every` steps up to `steps`."""
+    w = W.dmi_256x256x16()
+    m0 = W.m_random_sphere(w.grid, seed=w.seed)
+    ctx = {p: _ctx(mm, stream, w, p, dt) for p in (32, 64)}
+    curve = []
+    try:
+        for p in (32, 64):
+            mm.mm_set_m(ctx[p], 0, m0)
+        done = 0
+        while done < steps:
+            for p in (32, 64):
+                mm.mm_step_dt(ctx[p], np.full(every, dt))
+            done += every
+            d = np.abs(mm.mm_get_m(ctx[32], 0, m0.shape) - mm.mm_get_m(ctx[64], 0, m0.shape)).max()
+            curve.append([done, float(d)])
+    finally:
+        for c in ctx.values():
+            mm.mm_destroy(c)
+    return {"workload": w.name, "dt_s": dt, "max_abs_dm_fp32_vs_fp64": curve,
+            "note": "fixed RK45 steps replayed in both precisions from the same seeded random state"}
+
+
 def variant_peaks(mm):
     """Measured FMA throughput (FP32, FP64) of this GPU, the denominators of
     the ALU-bound lines."""
@@ -555,6 +580,18 @@ def variant_batched(mm, stream, steps):
         shape = m0[r].shape
         errs.append(float(np.abs(mm.mm_get_m(ctx, r, shape) - mm.mm_get_m(s, 0, shape)).max()))
         mm.mm_destroy(s)
+    # the smallest replica against the FP64 oracle over the same steps (same
+    # Philox key and current; the oracle steps it alone)
+    from oracle.fields import Problem
+    from oracle.llg import Solver, Torque, replica_seed
+    r = int(np.argmin(sizes))
+    n = sizes[r]
+    o = Solver(Problem.from_workload(W.Grid(n, n, 1, 2e-9, 2e-9, 1e-9), mat), m0[r],
+               terms=("exchange", "anisotropy", "zeeman", "demag"), T=300.0, seed=replica_seed(base_seed, r),
+               dt=1e-14, torque=Torque(kind="sot", J=J[r], p=(0, 1, 0), theta_SH=0.1))
+    for _ in range(n_total):
+        o.heun_step()
+    err_oracle = float(np.abs(mm.mm_get_m(ctx, r, m0[r].shape) - o.m).max())
     mm.mm_destroy(ctx)
     torch.cuda.synchronize()
     return {"workload": "1024 perpendicular free layers, sizes {32,48,64,96,128}^2 x 1 of 2x2x1 nm, T=300 K, "
@@ -564,7 +601,9 @@ def variant_batched(mm, stream, steps):
             "launch_shape": {"threads": nt, "ctas": blocks, "stacked": nt == 0},
             "autotune_s": round(t_tune, 2),
             "error_vs_fp64": {"max_abs_dm": max(errs), "after_steps": n_total, "replicas_checked": checks,
-                              "against": "FP64 single-instance GPU runs with the same Philox key"}}
+                              "against": "FP64 single-instance GPU runs with the same Philox key"},
+            "error_vs_oracle": {"max_abs_dm": err_oracle, "after_steps": n_total, "replica": r, "size": n,
+                                "against": "the FP64 CPU oracle stepping that replica alone (same key, current)"}}
 
 
 # The paper's replica-batching table (Results, "Replica batching"): physics,
@@ -923,6 +962,7 @@ def run_gpu(args):
                          ("dmi_256x256x16", lambda: variant_single(mm, stream, dmi, W.m_random_sphere(dmi.grid, 2),
                                                                    args.steps)),
                          ("film_128x32_fp64", lambda: variant_film_fp64(mm, stream)),
+                         ("drift", lambda: variant_drift(mm, stream)),
                          ("cufft", lambda: variant_cufft(mm, stream)),
                          ("batched", lambda: variant_batched(mm, stream, args.batch_steps)),
                          ("surrogate", lambda: variant_surrogate(mm, stream, args.surrogate_steps)),
@@ -957,7 +997,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", default="", help="nx,ny,nz: a smaller case of the same workload (profiling)")
     ap.add_argument("--no-variants", action="store_true", help="skip the error, FP64 and variant lines")
-    ap.add_argument("--variants", default="peaks,dmi_256x256x16,film_128x32_fp64,cufft,batched,surrogate,"
+    ap.add_argument("--variants", default="peaks,dmi_256x256x16,film_128x32_fp64,drift,cufft,batched,surrogate,"
                                           "paper_scenarios,batching_table,stt_sweep,sp4",
                     help="comma list of variant lines to run")
     ap.add_argument("--batch-steps", type=int, default=200)
