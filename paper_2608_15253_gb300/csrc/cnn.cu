@@ -133,17 +133,19 @@ enum { OUT_BF16 = 0, OUT_FIELD = 1, OUT_MASKED = 2 };
 //          more and frees its tensor memory.  a.skip_mma (a test mode) issues
 //          no MMA and no commit, so the first wait runs out with no
 //          asynchronous work in flight.
-constexpr int kPref = 2;
+constexpr int kPref = 1;
 constexpr int kRing = 5 + kPref + 1;
 
+// Every MMA operand window lies inside its ring slot or the weight block
+// (pixels q .. q + 127 of a 132-pixel strip, COUTP weight rows), so the
+// allocation needs no slack past them: two CTAs fit on an SM.
 template <int CIN, int COUTP>
 struct StreamSmem {
     static constexpr int kChunks = CIN / 8;
     static constexpr int kRowBytes = kChunks * kStrip * 16;
     static constexpr int kA = kRing * kRowBytes;
     static constexpr int kB = kTaps * kChunks * COUTP * 16;
-    static constexpr int kSlack = 16384;
-    static constexpr int kTotal = kA + kB + kSlack + 64;
+    static constexpr int kTotal = kA + kB + 64;
     static constexpr int kTmemCols = 2 * COUTP < 32 ? 32 : 2 * COUTP;
 };
 
@@ -157,14 +159,14 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 template <int CIN, int COUTP, int MODE, bool RELU>
-__global__ void __launch_bounds__(128, 1) conv_tc_stream_kernel(ConvArgs a) {
+__global__ void __launch_bounds__(128, 2) conv_tc_stream_kernel(ConvArgs a) {
     using L = StreamSmem<CIN, COUTP>;
     static_assert(L::kTmemCols == 32 || L::kTmemCols == 64, "tensor-memory allocation");
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;
     unsigned char* sB = smem + L::kA;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::kA + L::kB + L::kSlack);     // [2]
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::kA + L::kB + L::kSlack + 16);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::kA + L::kB);     // [2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::kA + L::kB + 16);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int H = a.H, W = a.W, Wp = W + 4;
     // run of output rows: blockIdx.x -> (image b, column block jb, rows [r0, r1))
@@ -212,7 +214,8 @@ __global__ void __launch_bounds__(128, 1) conv_tc_stream_kernel(ConvArgs a) {
     tc_fence_after();
     const uint32_t tbase = *tslot;
     const uint32_t idesc = umma_idesc(kTile, COUTP);
-    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+    const uint64_t dA0 = umma_desc(smem_u32(sA), kStrip * 16, 128);
+    const uint64_t dB0 = umma_desc(smem_u32(sB), COUTP * 16, 128);
     bool ok = true;
 
     // drain output row i from accumulator i % 2
@@ -276,17 +279,20 @@ __global__ void __launch_bounds__(128, 1) conv_tc_stream_kernel(ConvArgs a) {
         __syncthreads();
         tc_fence_after();
         if (tid == 0 && !a.skip_mma) {
+            // descriptors are linear in the start address (its 16-byte units
+            // in the low field), so each MMA's operands are a base plus an offset
             const uint32_t dacc = tbase + (uint32_t)((i & 1) * COUTP);
+#pragma unroll 1
             for (int p = 0; p < 5; ++p) {
-                const uint32_t arow = a0 + ((i + p) % kRing) * L::kRowBytes;
+                const uint64_t drow = dA0 + (uint64_t)((((i + p) % kRing) * L::kRowBytes) >> 4);
+#pragma unroll
                 for (int q = 0; q < 5; ++q)
 #pragma unroll
                     for (int kk = 0; kk < CIN / 16; ++kk) {
                         const int tap = p * 5 + q;
-                        const uint32_t aa = arow + ((2 * kk) * kStrip + q) * 16;
-                        const uint32_t bb = b0 + ((tap * L::kChunks + 2 * kk) * COUTP) * 16;
-                        umma_f16(dacc, umma_desc(aa, kStrip * 16, 128), umma_desc(bb, COUTP * 16, 128), idesc,
-                                 (p | q | kk) != 0);
+                        const uint64_t da = drow + (uint64_t)((2 * kk) * kStrip + q);
+                        const uint64_t db = dB0 + (uint64_t)((tap * L::kChunks + 2 * kk) * COUTP);
+                        umma_f16(dacc, da, db, idesc, (p | q | kk) != 0);
                     }
             }
             umma_commit(smem_u32(&mbar[i & 1]));
@@ -478,7 +484,7 @@ __global__ void field_from_cnn_kernel(const float* __restrict__ out, const T* __
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-// Output rows per CTA of the row-streaming kernel: about one CTA per SM
+// Output rows per CTA of the row-streaming kernel: about two CTAs per SM
 // over all images and column blocks, at least 4 rows (the ring's four-row
 // overlap is paid once per run).
 static int stream_rows_per_run(int B, int H, int W) {
@@ -490,7 +496,7 @@ static int stream_rows_per_run(int B, int H, int W) {
         if (sms <= 0) sms = 148;
     }
     const long long cols = (long long)B * ((W + kTile - 1) / kTile);
-    const long long rows = (cols * H + sms - 1) / sms;
+    const long long rows = (cols * H + 2 * sms - 1) / (2 * sms);   // two CTAs per SM
     return (int)std::max<long long>(4, std::min<long long>(H, rows));
 }
 
