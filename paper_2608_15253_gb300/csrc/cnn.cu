@@ -114,31 +114,38 @@ __device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float* v) {
 // ---------------------------------------------------------------------------
 enum { OUT_BF16 = 0, OUT_FIELD = 1, OUT_MASKED = 2 };
 
-// Row-streaming variant: one CTA walks down a 128-pixel column block of one
-// image over a run of output rows.  The packed weights are loaded once and
-// stay in shared memory; input rows live in a ring of kRing row slots filled
-// by cp.async kPref rows ahead, so every input row is fetched once per CTA
-// (a new output row needs one new input row: the four above are still in
-// the ring).  Thread 0 issues the 25 x CIN/16 MMAs of output row i into one
-// of two tensor-memory accumulators while all four warps drain row i - 1 from
-// the other (tcgen05.ld, bias, ReLU, BF16 pack, store), so loads, MMAs and
-// the epilogue of neighbouring rows overlap.
-//   slots: input row r0 + off of the run sits in slot off % kRing; output
-//          row r0 + i reads offsets i .. i + 4; the load issued at iteration
-//          i (offset i + 4 + kPref) reuses the slot of offset
-//          i + 4 + kPref - kRing = i - 2, whose last reader (output row
-//          i - 2) was drained at iteration i - 1.
+// Row-streaming convolution.  One CTA walks down a 128-pixel column block of
+// one image over a run of output rows.  The packed weights are loaded once
+// and stay in shared memory; input rows live in a ring of kRing row slots
+// filled by cp.async kPref rows ahead (every input row fetched once per CTA).
+//
+// The loop runs over INPUT rows: padded input row k feeds the five output
+// rows k - 4 .. k (tap row p = k - i for output row i), so its 5 x CIN/16
+// operand windows (one per tap column q and channel chunk) are each read
+// once for all of those rows: the weights of the five tap rows are laid out
+// side by side along N (tap row descending, so output rows ascend), and one
+// MMA D[128 px][count x COUTP] += A[128 px][16 ch] B[16 ch][count x COUTP]
+// adds row k's contribution to every output row it reaches.  The output rows
+// accumulate in a ring of kAcc tensor-memory blocks of COUTP columns (block
+// i % kAcc), zeroed before their first contribution, so every MMA
+// accumulates; a run of blocks that wraps the ring takes two MMAs.
+//   iteration k: wait for the MMAs of input row k - 2, drain output row
+//          k - 6 (complete after input row k - 2) and zero its block, load
+//          input row k + kPref into the slot of row k + kPref - kRing
+//          (<= k - 2, already read), wait for row k, issue its MMAs, commit.
+//          The MMAs of row k - 1 run while row k - 6 is drained.
 //   waits: every mbarrier wait gives up after a.wait_limit polls (default
 //          2^24); the CTA then records the timeout in a.err, drains nothing
-//          more and frees its tensor memory.  a.skip_mma (a test mode) issues
-//          no MMA and no commit, so the first wait runs out with no
-//          asynchronous work in flight.
-constexpr int kPref = 1;
-constexpr int kRing = 5 + kPref + 1;
+//          more, waits for its copies and frees its tensor memory.
+//          a.skip_mma (a test mode) issues no MMA and no commit, so the
+//          first wait runs out with no asynchronous work in flight.
+constexpr int kPref = 2;
+constexpr int kRing = kPref + 2;
+constexpr int kAcc = 8;
 
 // Every MMA operand window lies inside its ring slot or the weight block
-// (pixels q .. q + 127 of a 132-pixel strip, COUTP weight rows), so the
-// allocation needs no slack past them: two CTAs fit on an SM.
+// (pixels q .. q + 127 of a 132-pixel strip; at most 5 x COUTP weight rows
+// from the run's start row), so the allocation needs no slack past them.
 template <int CIN, int COUTP>
 struct StreamSmem {
     static constexpr int kChunks = CIN / 8;
@@ -146,7 +153,7 @@ struct StreamSmem {
     static constexpr int kA = kRing * kRowBytes;
     static constexpr int kB = kTaps * kChunks * COUTP * 16;
     static constexpr int kTotal = kA + kB + 64;
-    static constexpr int kTmemCols = 2 * COUTP < 32 ? 32 : 2 * COUTP;
+    static constexpr int kTmemCols = kAcc * COUTP;
 };
 
 __device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, bool valid) {
@@ -158,10 +165,20 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// zero 16 tensor-memory columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
+    const uint32_t z = 0u;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+        "r"(z)
+        : "memory");
+}
+
 template <int CIN, int COUTP, int MODE, bool RELU>
 __global__ void __launch_bounds__(128, 2) conv_tc_stream_kernel(ConvArgs a) {
     using L = StreamSmem<CIN, COUTP>;
-    static_assert(L::kTmemCols == 32 || L::kTmemCols == 64, "tensor-memory allocation");
+    static_assert(L::kTmemCols == 128 || L::kTmemCols == 256, "tensor-memory allocation");
+    static_assert(COUTP % 16 == 0, "N of every MMA a multiple of 16");
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;
     unsigned char* sB = smem + L::kA;
@@ -177,8 +194,9 @@ __global__ void __launch_bounds__(128, 2) conv_tc_stream_kernel(ConvArgs a) {
     const int b = blockIdx.x / (runs_per_col * ncb);
     const int r0 = run * a.rows_per_run, r1 = min(H, r0 + a.rows_per_run);
     const int j0 = jb * kTile;
-    const int nrow = r1 - r0;
+    const int nrow = r1 - r0, nin = nrow + 4;
     const long wait_limit = a.wait_limit > 0 ? a.wait_limit : (1L << 24);
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -190,49 +208,66 @@ __global__ void __launch_bounds__(128, 2) conv_tc_stream_kernel(ConvArgs a) {
         mbar_init(smem_u32(&mbar[1]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // padded input row r0 + off (off < nrow + 4) of image b -> ring slot off % kRing
+    // padded input row r0 + off (off < nin) of image b -> ring slot off % kRing
     auto load_row = [&](int off) {
         unsigned char* dst = sA + (off % kRing) * L::kRowBytes;
         const __nv_bfloat16* src = a.in + ((long long)b * (H + 4) + r0 + off) * Wp * CIN;
         for (int e = tid; e < L::kChunks * kStrip; e += 128) {
             const int px = e % kStrip, ch = e / kStrip;
             const int col = j0 + px;
-            const bool ok = col < Wp;
-            cp_async16_zfill(dst + (ch * kStrip + px) * 16, src + (long long)(ok ? col : 0) * CIN + ch * 8, ok);
+            const bool okc = col < Wp;
+            cp_async16_zfill(dst + (ch * kStrip + px) * 16, src + (long long)(okc ? col : 0) * CIN + ch * 8, okc);
         }
     };
-    // weights (group 0) and the first 4 + kPref input rows (one group each)
-    for (int q = tid; q < L::kB / 16; q += 128)
-        cp_async16_zfill(sB + q * 16, reinterpret_cast<const unsigned char*>(a.wpk) + (long long)q * 16, true);
+    // weights (group 0): global [tap][ch][co] 16-byte pieces -> shared
+    // [q][ch][tap row descending][co], so the five tap rows of one (q, ch)
+    // are consecutive N rows
+    for (int e = tid; e < L::kB / 16; e += 128) {
+        const int co = e % COUTP, rest = e / COUTP;
+        const int ch = rest % L::kChunks, tap = rest / L::kChunks;
+        const int p = tap / 5, q = tap - 5 * p;
+        const int dst = ((q * L::kChunks + ch) * 5 + (4 - p)) * COUTP + co;
+        cp_async16_zfill(sB + dst * 16, reinterpret_cast<const unsigned char*>(a.wpk) + (long long)e * 16, true);
+    }
     cp_async_commit();
-    for (int q = 0; q < 4 + kPref; ++q) {
-        if (q < nrow + 4) load_row(q);
+    for (int q = 0; q < kPref; ++q) {             // input rows 0 .. kPref - 1, one group each
+        if (q < nin) load_row(q);
         cp_async_commit();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tslot;
-    const uint32_t idesc = umma_idesc(kTile, COUTP);
+    // every accumulator block starts at zero
+    for (int c = 0; c < L::kTmemCols; c += 16) tmem_zero16(tbase + lane_base + c);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
     const uint64_t dA0 = umma_desc(smem_u32(sA), kStrip * 16, 128);
-    const uint64_t dB0 = umma_desc(smem_u32(sB), COUTP * 16, 128);
+    const uint64_t dB0 = umma_desc(smem_u32(sB), 5 * COUTP * 16, 128);
     bool ok = true;
 
-    // drain output row i from accumulator i % 2
-    auto epilogue = [&](int i) {
+    // wait for the MMAs of input row k (commit into mbar[k % 2])
+    auto wait_commit = [&](int k) {
         uint32_t done = 0;
-        const uint32_t mb = smem_u32(&mbar[i & 1]);
-        for (long it = 0; it < wait_limit && !done; ++it) done = mbar_try_wait(mb, (uint32_t)((i >> 1) & 1));
+        const uint32_t mb = smem_u32(&mbar[k & 1]);
+        for (long it = 0; it < wait_limit && !done; ++it) done = mbar_try_wait(mb, (uint32_t)((k >> 1) & 1));
         done = __syncthreads_and(done);
-        if (!done) {
-            if (tid == 0 && a.err) atomicExch(a.err, 1);
-            return false;
-        }
+        if (!done && tid == 0 && a.err) atomicExch(a.err, 1);
+        return done != 0;
+    };
+    // drain output row i (relative to r0) from block i % kAcc, then zero it
+    auto drain = [&](int i) {
         tc_fence_after();
         const int m = warp * 32 + (tid & 31);
         const int j = j0 + m;
+        const uint32_t col = (uint32_t)((i % kAcc) * COUTP);
         float v[COUTP];
-        tmem_ld<COUTP>(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)((i & 1) * COUTP), v);
+        tmem_ld<COUTP>(tbase + lane_base + col, v);
+#pragma unroll
+        for (int c = 0; c < COUTP; c += 16) tmem_zero16(tbase + lane_base + col + c);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         tc_fence_before();
         const int row = r0 + i;
         if (j < W) {
@@ -266,40 +301,57 @@ __global__ void __launch_bounds__(128, 2) conv_tc_stream_kernel(ConvArgs a) {
                 }
             }
         }
-        return true;
     };
 
-    for (int i = 0; i < nrow && ok; ++i) {
-        // next input row kPref ahead (its slot's last reader was drained at i - 1)
-        if (i + 4 + kPref < nrow + 4) load_row(i + 4 + kPref);
+    for (int k = 0; k < nin && ok; ++k) {
+        if (k >= 2) {
+            ok = wait_commit(k - 2);              // input rows <= k - 2 consumed
+            if (!ok) break;
+            if (k - 6 >= 0) drain(k - 6);         // output row k - 6: last input row k - 2
+        }
+        if (k + kPref < nin) load_row(k + kPref); // slot of row k + kPref - kRing = k - 2
         cp_async_commit();
-        cp_async_wait<kPref>();             // padded rows up to i + 4 have landed
+        cp_async_wait<kPref>();                   // input row k has landed
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
         if (tid == 0 && !a.skip_mma) {
-            // descriptors are linear in the start address (its 16-byte units
-            // in the low field), so each MMA's operands are a base plus an offset
-            const uint32_t dacc = tbase + (uint32_t)((i & 1) * COUTP);
-#pragma unroll 1
-            for (int p = 0; p < 5; ++p) {
-                const uint64_t drow = dA0 + (uint64_t)((((i + p) % kRing) * L::kRowBytes) >> 4);
+            // output rows lo .. hi receive input row k (tap row k - i)
+            const int lo = max(k - 4, 0), hi = min(k, nrow - 1);
+            if (lo <= hi) {
+                const uint64_t darow = dA0 + (uint64_t)(((k % kRing) * L::kRowBytes) >> 4);
+                // split the block run lo % kAcc .. hi % kAcc where it wraps
+                const int s0 = lo, n0 = min(hi - lo + 1, kAcc - lo % kAcc);
+                const int s1 = lo + n0, n1 = hi - lo + 1 - n0;
 #pragma unroll
-                for (int q = 0; q < 5; ++q)
+                for (int seg = 0; seg < 2; ++seg) {
+                    const int st = seg == 0 ? s0 : s1, cnt = seg == 0 ? n0 : n1;
+                    if (cnt <= 0) continue;
+                    const uint32_t dacc = tbase + (uint32_t)((st % kAcc) * COUTP);
+                    const uint32_t idesc = umma_idesc(kTile, cnt * COUTP);
+                    const int brow = (4 - (k - st)) * COUTP;      // first weight row: tap row k - st
 #pragma unroll
-                    for (int kk = 0; kk < CIN / 16; ++kk) {
-                        const int tap = p * 5 + q;
-                        const uint64_t da = drow + (uint64_t)((2 * kk) * kStrip + q);
-                        const uint64_t db = dB0 + (uint64_t)((tap * L::kChunks + 2 * kk) * COUTP);
-                        umma_f16(dacc, da, db, idesc, (p | q | kk) != 0);
-                    }
+                    for (int q = 0; q < 5; ++q)
+#pragma unroll
+                        for (int kk = 0; kk < CIN / 16; ++kk) {
+                            const uint64_t da = darow + (uint64_t)((2 * kk) * kStrip + q);
+                            const uint64_t db =
+                                dB0 + (uint64_t)((q * L::kChunks + 2 * kk) * 5 * COUTP + brow);
+                            umma_f16(dacc, da, db, idesc, 1u);
+                        }
+                }
             }
-            umma_commit(smem_u32(&mbar[i & 1]));
+            umma_commit(smem_u32(&mbar[k & 1]));
         }
-        if (i > 0) ok = epilogue(i - 1);
     }
-    if (ok && nrow > 0) ok = epilogue(nrow - 1);
+    // the loop drained output rows 0 .. nrow - 3 (row k - 6 at input row
+    // k <= nin - 1); the last two are complete after the last input row
+    if (ok) {
+        ok = wait_commit(nin - 1);
+        if (ok)
+            for (int i = max(0, nrow - 2); i < nrow; ++i) drain(i);
+    }
     cp_async_wait<0>();
     tc_fence_before();
     __syncthreads();
