@@ -524,6 +524,44 @@ def variant_drift(mm, stream, steps=200, every=20, dt=2e-14):
             "note": "fixed RK45 steps replayed in both precisions from the same seeded random state"}
 
 
+def variant_cnn_forward(mm, reps=5):
+    """The surrogate network's forward pass on the 512x512 film (BF16 tcgen05
+    convolutions), per layer from the library's CUDA-event profile: time,
+    and throughput on the network's algorithmic FLOPs (real channels:
+    2 x 25 x (3*32 + 32*32 + 32*32 + 32*3) per pixel) against the measured
+    BF16 peak."""
+    w = W.skyrmion_512()
+    g = w.grid
+    M = mm.Material(w.mat.Ms, w.mat.A, w.mat.alpha, w.mat.Ku1, w.mat.u, w.mat.D)
+    c = mm.mm_create(mm.make_grid(g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), M.s,
+                     mm.make_config(precision=32, integrator=mm.MM_RK45, demag=mm.MM_DEMAG_EXACT, dt=1e-13))
+    try:
+        rng = np.random.default_rng(4)
+        mm.mm_surrogate_weights(c, rng.normal(0.0, 0.05, mm.SURROGATE_NPARAMS), c_in=1.0)
+        x = rng.normal(size=(1, 3, g.ny, g.nx))
+        mm.mm_surrogate_forward(c, x)
+        mm.mm_set_profiling(c, True)
+        for _ in range(reps):
+            mm.mm_surrogate_forward(c, x)
+        prof = [p for p in mm.mm_get_profile(c) if p["name"].startswith("cnn_conv")]
+        mm.mm_set_profiling(c, False)
+    finally:
+        mm.mm_destroy(c)
+    fwd_us = 1e3 * sum(p["total_ms"] for p in prof) / reps
+    flops = 2.0 * 25 * (3 * 32 + 32 * 32 + 32 * 32 + 32 * 3) * g.nx * g.ny
+    peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+    except Exception:
+        peak = 1900.0
+    tf = flops / (fwd_us * 1e-6) / 1e12
+    return {"grid": [g.nx, g.ny], "forward_us": round(fwd_us, 2),
+            "layers_us": {p["name"]: round(1e3 * p["total_ms"] / p["launches"], 2) for p in prof},
+            "algorithmic_gflop": round(flops / 1e9, 3), "tflops": round(tf, 1), "bf16_peak_tflops": peak,
+            "frac_of_bf16_peak": round(tf / peak, 4)}
+
+
 def variant_peaks(mm):
     """Measured FMA throughput (FP32, FP64) of this GPU, the denominators of
     the ALU-bound lines."""
@@ -963,6 +1001,7 @@ def run_gpu(args):
                                                                    args.steps)),
                          ("film_128x32_fp64", lambda: variant_film_fp64(mm, stream)),
                          ("drift", lambda: variant_drift(mm, stream)),
+                         ("cnn_forward", lambda: variant_cnn_forward(mm)),
                          ("cufft", lambda: variant_cufft(mm, stream)),
                          ("batched", lambda: variant_batched(mm, stream, args.batch_steps)),
                          ("surrogate", lambda: variant_surrogate(mm, stream, args.surrogate_steps)),
@@ -997,7 +1036,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", default="", help="nx,ny,nz: a smaller case of the same workload (profiling)")
     ap.add_argument("--no-variants", action="store_true", help="skip the error, FP64 and variant lines")
-    ap.add_argument("--variants", default="peaks,dmi_256x256x16,film_128x32_fp64,drift,cufft,batched,surrogate,"
+    ap.add_argument("--variants", default="peaks,dmi_256x256x16,film_128x32_fp64,drift,cufft,cnn_forward,batched,"
+                                          "surrogate,"
                                           "paper_scenarios,batching_table,stt_sweep,sp4",
                     help="comma list of variant lines to run")
     ap.add_argument("--batch-steps", type=int, default=200)
