@@ -501,9 +501,14 @@ MM_API mm_status mm_surrogate_weights(mm_ctx* ctx, double* get, const double* se
 MM_API mm_status mm_surrogate_forward(mm_ctx* ctx, int B, int H, int W, const double* x, double* y, int path);
 
 /* One forward + mean-squared-error loss against t + backward pass: loss and
- * the gradient of every parameter (n = 56099, same order as the weights). */
+ * the gradient of every parameter (n = 56099, same order as the weights).
+ * path 0 = weight gradients on the tensor cores (per-CTA partial sums added
+ * in a fixed order, so repeated calls agree bit for bit), 1 = SIMT
+ * cross-check kernels (FP32 atomics).  Errors: MM_ERR_ARG (NULL x or t,
+ * non-positive sizes, path not 0 or 1), MM_ERR_TIMEOUT (a bounded
+ * tensor-core wait ran out; reported once, the context stays usable). */
 MM_API mm_status mm_surrogate_grad(mm_ctx* ctx, int B, int H, int W, const double* x, const double* t,
-                                   double* loss, double* grad);
+                                   double* loss, double* grad, int path);
 
 /* Per-kernel CUDA-event timing (graphs are bypassed while on).  No passage:
  * boundary convenience (tracing; the paper times whole runs, Methods,

@@ -435,7 +435,8 @@ __global__ void plain_weights_kernel(const float* __restrict__ w, int cout, int 
     out[q] = __float2bfloat16_rn(co < cout && ci < cin ? w[(co * cin + ci) * 25 + t] : 0.f);
 }
 
-// dW[co][ci][p][q] += sum over pixels dZ[pix][co] * X[pix + (p-2, q-2)][ci]
+// SIMT reference of the weight gradient (on-GPU cross-check of the tensor
+// path): dW[co][ci][p][q] += sum over pixels dZ[pix][co] * X[pix + (p-2, q-2)][ci];
 // one block per (tap, pixel chunk); thread (co, ci); FP32 atomics.
 __global__ void dweight_kernel(const __nv_bfloat16* __restrict__ dz, int CZ, int cout,
                                const __nv_bfloat16* __restrict__ x, int CX, int cin, int B, int H, int W,
@@ -474,6 +475,260 @@ __global__ void dweight_kernel(const __nv_bfloat16* __restrict__ dz, int CZ, int
     }
     if (co < cout && ci < cin) atomicAdd(&dw[((co * cin + ci) * 5 + p) * 5 + q], acc);
     if (tap == 0 && ci == 0 && co < cout) atomicAdd(&db[co], accb);
+}
+
+// ---------------------------------------------------------------------------
+// weight gradient on tensor cores
+// ---------------------------------------------------------------------------
+//   dW[co][ci][ty][tx] = sum over output pixels (y, j) of
+//                        dZ[y][j][co] * X[y + ty - 2][j + tx - 2][ci]
+//   db[co]             = sum over output pixels of dZ[y][j][co]
+// (X zero-padded).  The contraction runs over pixels, and both operands are
+// stored pixel by pixel with their channels innermost: MN-major for this
+// product.  The MMA reads them that way (no swizzle: a core matrix is 8
+// channels x 8 pixels, 128 contiguous bytes), so 16-byte channel groups are
+// copied into shared memory unchanged.
+//
+// Input row R meets the dZ rows R - 2 .. R + 2 (tap row ty = 4 - r for dZ
+// row R - 2 + r).  With Xs_tx[p] = X[R][p + tx - 2] (five shifted copies of
+// input row R, built in shared memory),
+//   D[(copy, ci)][(r, co)] += sum over 16 pixels p of Xs_copy[p][ci] dZ[R - 2 + r][p][co]
+// accumulates every tap into one tensor-memory tile that stays put for the
+// whole kernel: M = 128 rows of (copy, channel) (copies 0..3 then 4..7 when
+// X has 32 channels, 0..7 when it has 16), N = 5 dZ rows x CZ channels.
+// Copy 5 is all ones, so its rows collect the bias gradient; copies 6 and 7
+// are zero.  dZ rows sit in a ring of 6 slots (a window that wraps takes two
+// MMAs); the row copies are double buffered: row R's MMAs are issued, then
+// the CTA waits for row R - 1's and loads the copies of row R + 1 (and dZ row
+// R + 3) into the buffers row R - 1 used.
+//
+// A CTA takes a contiguous share of all (image, 128-pixel column block,
+// padded input row) triples, one per SM; at the end it writes its partial
+// sums, and a second kernel adds them over CTAs in a fixed order.
+constexpr int kWgCopies = 8;
+constexpr int kWgRing = 6;
+constexpr int kWgPlane = kTile * 16;        // one 8-channel group of 128 pixels
+
+template <int CX, int CZ>
+struct WgSmem {
+    static constexpr int kCopyBytes = (CX / 8) * kWgPlane;
+    static constexpr int kA = kWgCopies * kCopyBytes;         // copies of one input row
+    static constexpr int kSlot = (CZ / 8) * kWgPlane;         // one dZ row
+    static constexpr int kMmas = CX == 32 ? 2 : 1;            // 128-row MMAs per K step
+    static constexpr int kN = 5 * CZ;
+    static constexpr int kUsedCols = kMmas * kN;
+    static constexpr int kCols = kUsedCols <= 256 ? 256 : 512;
+    static constexpr int kBar = 2 * kA + kWgRing * kSlot;
+    // 8 KB past the barriers: every operand window stays inside the
+    // allocation whichever way the descriptor strides were read
+    static constexpr int kTotal = kBar + 64 + 8192;
+    static constexpr int kPartFloats = 25 * CX * CZ + CZ;
+};
+
+struct WgArgs {
+    const __nv_bfloat16* dz;   // [B][H+4][W+4][CZ], interior read
+    const __nv_bfloat16* x;    // [B][H+4][W+4][CX], zero halo
+    float* part;               // [gridDim.x][kWgPartFloats]
+    int B, H, W;
+    int* err;
+    long wait_limit;
+};
+
+__host__ __device__ constexpr uint32_t umma_idesc_mn(int M, int N) {
+    return umma_idesc(M, N) | (1u << 15) | (1u << 16);       // A and B MN-major
+}
+
+template <int CX, int CZ>
+__global__ void __launch_bounds__(128, 1) dweight_tc_kernel(WgArgs a) {
+    using L = WgSmem<CX, CZ>;
+    static_assert(L::kPartFloats <= kWgPartFloats, "partial-sum block");
+    static_assert(L::kUsedCols % 16 == 0, "tensor-memory columns");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sA = smem;                         // [2][copy][CX/8][128 px][16 B]
+    unsigned char* sZ = smem + 2 * L::kA;             // [slot][CZ/8][128 px][16 B]
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::kBar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::kBar + 16);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int H = a.H, W = a.W, Wp = W + 4, Hp = H + 4;
+    const int ncb = (W + kTile - 1) / kTile;
+    const long long F = (long long)a.B * ncb * Hp;
+    const long long f0 = F * blockIdx.x / gridDim.x, f1 = F * (blockIdx.x + 1) / gridDim.x;
+    const long wait_limit = a.wait_limit > 0 ? a.wait_limit : (1L << 24);
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"((uint32_t)L::kCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        mbar_init(smem_u32(&mbar[0]), 1);
+        mbar_init(smem_u32(&mbar[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // constant copies of both buffers: 5 = ones (bf16 1.0 = 0x3F80), 6, 7 = zero
+    for (int e = tid; e < 2 * 3 * (L::kCopyBytes / 16); e += 128) {
+        const int per = 3 * (L::kCopyBytes / 16);
+        const int buf = e / per, rest = e % per;
+        const int cp = 5 + rest / (L::kCopyBytes / 16), off = rest % (L::kCopyBytes / 16);
+        const uint32_t w = cp == 5 ? 0x3F803F80u : 0u;
+        *reinterpret_cast<uint4*>(sA + buf * L::kA + cp * L::kCopyBytes + off * 16) = make_uint4(w, w, w, w);
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+    for (int c = 0; c < L::kUsedCols; c += 16) tmem_zero16(tbase + lane_base + c);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+
+    // copies 0..4 of padded input row pr of image b, column block j0 -> buffer buf
+    auto load_x = [&](int buf, int b, int pr, int j0) {
+        unsigned char* dst = sA + buf * L::kA;
+        const __nv_bfloat16* src = a.x + ((long long)b * Hp + pr) * Wp * CX;
+        for (int e = tid; e < 5 * (CX / 8) * kTile; e += 128) {
+            const int cg = e % (CX / 8), rest = e / (CX / 8);
+            const int p = rest % kTile, tx = rest / kTile;
+            const int col = j0 + p + tx;              // padded column
+            const bool ok = col < Wp;
+            cp_async16_zfill(dst + (tx * (CX / 8) + cg) * kWgPlane + p * 16,
+                             src + (long long)(ok ? col : 0) * CX + cg * 8, ok);
+        }
+    };
+    // dZ row y (interior numbering) of image b -> ring slot; zero outside the image
+    auto load_z = [&](int b, int y, int j0, int slot) {
+        unsigned char* dst = sZ + slot * L::kSlot;
+        const bool rok = y >= 0 && y < H;
+        const __nv_bfloat16* src = a.dz + ((long long)b * Hp + (rok ? y + 2 : 0)) * Wp * CZ;
+        for (int e = tid; e < (CZ / 8) * kTile; e += 128) {
+            const int cg = e % (CZ / 8), p = e / (CZ / 8);
+            const int col = j0 + p;                   // interior column
+            const bool ok = rok && col < W;
+            cp_async16_zfill(dst + cg * kWgPlane + p * 16, src + (long long)(ok ? col + 2 : 0) * CZ + cg * 8, ok);
+        }
+    };
+    // wait for the MMAs of row k (commit into mbar[k % 2])
+    auto wait_commit = [&](long long k) {
+        uint32_t done = 0;
+        const uint32_t mb = smem_u32(&mbar[k & 1]);
+        for (long it = 0; it < wait_limit && !done; ++it) done = mbar_try_wait(mb, (uint32_t)((k >> 1) & 1));
+        done = __syncthreads_and(done);
+        if (!done && tid == 0 && a.err) atomicExch(a.err, 1);
+        return done != 0;
+    };
+
+    // no swizzle, MN-major: 8-pixel core matrices 128 B apart along K, 8-channel groups kWgPlane apart
+    const uint64_t dA0 = umma_desc(smem_u32(sA), 128, kWgPlane);
+    const uint64_t dZ0 = umma_desc(smem_u32(sZ), 128, kWgPlane);
+    long long it = 0;                                 // rows issued by this CTA
+    bool ok = true;
+    for (long long f = f0; f < f1 && ok;) {
+        const long long u = f / Hp;
+        const int t0 = (int)(f - u * Hp);
+        const long long left = f1 - f;
+        const int n = left < (long long)(Hp - t0) ? (int)left : Hp - t0;
+        const int b = (int)(u / ncb), j0 = (int)(u % ncb) * kTile;
+        const int Rs = t0 - 2;                        // first input row (interior numbering)
+        // every earlier MMA has finished: dZ rows Rs - 2 .. Rs + 2 -> slots 0..4
+        for (int r = 0; r < 5; ++r) load_z(b, Rs - 2 + r, j0, r);
+        load_x((int)(it & 1), b, Rs + 2, j0);
+        cp_async_commit();
+        for (int jj = 0; jj < n; ++jj, ++it) {
+            cp_async_wait<0>();                       // row Rs + jj and its dZ rows have landed
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if (tid == 0) {
+                const int s0 = jj % kWgRing;          // slot of dZ row R - 2
+                const int n0 = min(5, kWgRing - s0);
+#pragma unroll
+                for (int g = 0; g < L::kMmas; ++g) {
+                    const uint64_t da = dA0 + (uint64_t)(((int)(it & 1) * L::kA + g * 4 * L::kCopyBytes) >> 4);
+#pragma unroll
+                    for (int seg = 0; seg < 2; ++seg) {
+                        const int cnt = seg == 0 ? n0 : 5 - n0;
+                        if (cnt <= 0) continue;
+                        const int slot = seg == 0 ? s0 : 0, r0 = seg == 0 ? 0 : n0;
+                        const uint32_t dacc = tbase + (uint32_t)(g * L::kN + r0 * CZ);
+                        const uint64_t db = dZ0 + (uint64_t)((slot * L::kSlot) >> 4);
+                        const uint32_t idesc = umma_idesc_mn(kTile, cnt * CZ);
+#pragma unroll
+                        for (int kk = 0; kk < kTile / 16; ++kk)       // 16 pixels = 256 B per step
+                            umma_f16(dacc, da + 16 * kk, db + 16 * kk, idesc, 1u);
+                    }
+                }
+                umma_commit(smem_u32(&mbar[it & 1]));
+            }
+            if (it > 0) {
+                ok = wait_commit(it - 1);             // buffers of row R - 1 are free
+                if (!ok) break;
+            }
+            if (jj + 1 < n) {
+                const int R = Rs + jj;
+                load_x((int)((it + 1) & 1), b, R + 3, j0);     // padded row of input row R + 1
+                load_z(b, R + 3, j0, (jj + 5) % kWgRing);      // replaces dZ row R - 3
+                cp_async_commit();
+            }
+        }
+        if (ok) ok = wait_commit(it - 1);             // buffers free for the next share
+        f += n;
+    }
+    cp_async_wait<0>();
+    tc_fence_after();
+    if (ok) {
+        float* part = a.part + (long long)blockIdx.x * kWgPartFloats;
+        const int m = warp * 32 + (tid & 31);
+#pragma unroll
+        for (int g = 0; g < L::kMmas; ++g) {
+            const int copy = g * (128 / CX) + m / CX, ci = m % CX;
+            for (int c = 0; c < L::kN; c += 16) {
+                float v[16];
+                tmem_ld<16>(tbase + lane_base + (uint32_t)(g * L::kN + c), v);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int r = (c + q) / CZ, co = (c + q) % CZ;
+                    if (copy < 5)
+                        part[(((4 - r) * 5 + copy) * CZ + co) * CX + ci] = v[q];
+                    else if (copy == 5 && ci == 0 && r == 2)
+                        part[25 * CZ * CX + co] = v[q];
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"((uint32_t)L::kCols));
+}
+
+// dW (+)= sum over CTAs of the partial sums, in CTA order
+template <int CX, int CZ>
+__global__ void dweight_reduce_kernel(const float* __restrict__ part, int nparts, int cout, int cin,
+                                      float* __restrict__ dw, float* __restrict__ db) {
+    const int n = WgSmem<CX, CZ>::kPartFloats;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int c = 0;
+    for (; c + 4 <= nparts; c += 4) {
+        s0 += part[(long long)c * kWgPartFloats + i];
+        s1 += part[(long long)(c + 1) * kWgPartFloats + i];
+        s2 += part[(long long)(c + 2) * kWgPartFloats + i];
+        s3 += part[(long long)(c + 3) * kWgPartFloats + i];
+    }
+    for (; c < nparts; ++c) s0 += part[(long long)c * kWgPartFloats + i];
+    const float s = (s0 + s1) + (s2 + s3);
+    if (i < 25 * CZ * CX) {
+        const int ci = i % CX, co = (i / CX) % CZ, tap = i / (CX * CZ);   // tap = ty * 5 + tx
+        if (co < cout && ci < cin) dw[(co * cin + ci) * 25 + tap] += s;
+    } else {
+        const int co = i - 25 * CZ * CX;
+        if (co < cout) db[co] += s;
+    }
 }
 
 // loss = sum (y - t)^2 / n; dy = 2 (y - t) / n scaled by gscale, as bf16 NHWC (16 ch)
@@ -539,7 +794,7 @@ __global__ void field_from_cnn_kernel(const float* __restrict__ out, const T* __
 // Output rows per CTA of the row-streaming kernel: about two CTAs per SM
 // over all images and column blocks, at least 4 rows (the ring's four-row
 // overlap is paid once per run).
-static int stream_rows_per_run(int B, int H, int W) {
+static int device_sms() {
     static int sms = 0;
     if (!sms) {
         int dev = 0;
@@ -547,6 +802,11 @@ static int stream_rows_per_run(int B, int H, int W) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 148;
     }
+    return sms;
+}
+
+static int stream_rows_per_run(int B, int H, int W) {
+    const int sms = device_sms();
     const long long cols = (long long)B * ((W + kTile - 1) / kTile);
     const long long rows = (cols * H + 2 * sms - 1) / (2 * sms);   // two CTAs per SM
     return (int)std::max<long long>(4, std::min<long long>(H, rows));
@@ -606,12 +866,40 @@ void cnn_plain(cudaStream_t s, const float* w, int cout, int cin, int CINP, int 
     plain_weights_kernel<<<(n + 255) / 256, 256, 0, s>>>(w, cout, cin, CINP, COUTP, out);
 }
 
-void cnn_dweight(cudaStream_t s, const __nv_bfloat16* dz, int CZ, int cout, const __nv_bfloat16* x, int CX, int cin,
-                 int B, int H, int W, float* dw, float* db) {
+int cnn_dweight_parts() { return device_sms(); }
+
+template <int CX, int CZ>
+static cudaError_t launch_dweight_tc(cudaStream_t s, const __nv_bfloat16* dz, int cout, const __nv_bfloat16* x,
+                                     int cin, int B, int H, int W, float* part, int* err, float* dw, float* db) {
+    using L = WgSmem<CX, CZ>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(dweight_tc_kernel<CX, CZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kTotal);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const long long F = (long long)B * ((W + kTile - 1) / kTile) * (H + 4);
+    const int grid = (int)std::min<long long>(cnn_dweight_parts(), F);
+    WgArgs a{dz, x, part, B, H, W, err, 0};
+    dweight_tc_kernel<CX, CZ><<<grid, 128, L::kTotal, s>>>(a);
+    dweight_reduce_kernel<CX, CZ><<<(L::kPartFloats + 255) / 256, 256, 0, s>>>(part, grid, cout, cin, dw, db);
+    return cudaGetLastError();
+}
+
+cudaError_t cnn_dweight(cudaStream_t s, int path, const __nv_bfloat16* dz, int CZ, int cout, const __nv_bfloat16* x,
+                        int CX, int cin, int B, int H, int W, float* part, int* err, float* dw, float* db) {
+    if (path == 0) {
+        if (CX == 32 && CZ == 32) return launch_dweight_tc<32, 32>(s, dz, cout, x, cin, B, H, W, part, err, dw, db);
+        if (CX == 32 && CZ == 16) return launch_dweight_tc<32, 16>(s, dz, cout, x, cin, B, H, W, part, err, dw, db);
+        if (CX == 16 && CZ == 32) return launch_dweight_tc<16, 32>(s, dz, cout, x, cin, B, H, W, part, err, dw, db);
+        return cudaErrorInvalidValue;
+    }
     const long long npix = (long long)B * H * W;
     const int chunk = 4096;
     const dim3 g((unsigned)((npix + chunk - 1) / chunk), kTaps);
     dweight_kernel<<<g, 1024, 0, s>>>(dz, CZ, cout, x, CX, cin, B, H, W, chunk, dw, db);
+    return cudaGetLastError();
 }
 
 void cnn_mse_grad(cudaStream_t s, const float* y, const float* t, int B, int H, int W, __nv_bfloat16* dy,

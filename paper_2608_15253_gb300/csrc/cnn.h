@@ -27,8 +27,15 @@ cudaError_t cnn_conv(int layer, bool backward, const ConvArgs& a, int B, cudaStr
 cudaError_t cnn_conv_simt(int layer, const ConvArgs& a, const __nv_bfloat16* wplain, int B, cudaStream_t s);
 void cnn_pack(cudaStream_t s, const float* w, int cout, int cin, int CINP, int COUTP, int flip, __nv_bfloat16* out);
 void cnn_plain(cudaStream_t s, const float* w, int cout, int cin, int CINP, int COUTP, __nv_bfloat16* out);
-void cnn_dweight(cudaStream_t s, const __nv_bfloat16* dz, int CZ, int cout, const __nv_bfloat16* x, int CX, int cin,
-                 int B, int H, int W, float* dw, float* db);
+// Weight and bias gradients of one layer, added into dw [cout][cin][5][5]
+// and db [cout].  path 0: tensor-core kernel (CX, CZ in {16, 32}, not both
+// 16), partial sums per CTA in part (cnn_dweight_parts() x kWgPartFloats
+// floats), then a fixed-order reduction; err as in ConvArgs.  path 1: the
+// SIMT cross-check (FP32 atomics; part and err unused).
+constexpr int kWgPartFloats = 25 * 32 * 32 + 32;
+int cnn_dweight_parts();
+cudaError_t cnn_dweight(cudaStream_t s, int path, const __nv_bfloat16* dz, int CZ, int cout, const __nv_bfloat16* x,
+                        int CX, int cin, int B, int H, int W, float* part, int* err, float* dw, float* db);
 void cnn_mse_grad(cudaStream_t s, const float* y, const float* t, int B, int H, int W, __nv_bfloat16* dy,
                   double* loss);
 void cnn_adam(cudaStream_t s, float* p, const float* g, float* m, float* v, int n, float lr, int t);

@@ -102,6 +102,7 @@ struct SurrogateHost {
     float *y = nullptr, *t = nullptr;
     double* d_loss = nullptr;
     int* d_err = nullptr;
+    float* d_wpart = nullptr;   // per-CTA partial weight gradients of the tensor-core kernel
     // stepping
     int k = 0;
     double tol = 1e-3;
@@ -120,7 +121,7 @@ static void sfree(SurrogateHost* s) {
     if (!s) return;
     if (s->g_attempt) cudaGraphExecDestroy(s->g_attempt);
     void* ptrs[] = {s->d_p, s->d_g, s->d_m, s->d_v, s->x0, s->h1, s->h2, s->h3, s->dy, s->dza, s->dzb,
-                    s->y, s->t, s->d_loss, s->d_err, s->d_mref, s->d_href, s->d_red};
+                    s->y, s->t, s->d_loss, s->d_err, s->d_mref, s->d_href, s->d_red, s->d_wpart};
     for (void* p : ptrs) cudaFree(p);
     for (int l = 0; l < 4; ++l) {
         cudaFree(s->wpk[l]);
@@ -170,6 +171,7 @@ static mm_status ensure_surrogate(mm_ctx* c) {
     A((void**)&s->d_loss, sizeof(double));
     A((void**)&s->d_err, sizeof(int));
     A((void**)&s->d_red, sizeof(double) * 4);
+    A((void**)&s->d_wpart, sizeof(float) * (size_t)cnn_dweight_parts() * kWgPartFloats);
     if (e != cudaSuccess) {
         sfree(s);
         return cuda_check(c, e, "surrogate parameters");
@@ -294,7 +296,8 @@ static mm_status run_forward(mm_ctx* c, int B, int H, int W, float out_scale, in
     return MM_OK;
 }
 
-static mm_status run_backward(mm_ctx* c, int B, int H, int W) {
+// path 0: tensor-core weight gradients, 1: the SIMT cross-check
+static mm_status run_backward(mm_ctx* c, int B, int H, int W, int path) {
     SurrogateHost* s = c->surr;
     cudaMemsetAsync(s->d_g, 0, sizeof(float) * s->np, c->stream);
     __nv_bfloat16* xin[4] = {s->x0, s->h1, s->h2, s->h3};
@@ -306,8 +309,9 @@ static mm_status run_backward(mm_ctx* c, int B, int H, int W) {
     for (int l = 3; l >= 0; --l) {
         {
             LaunchScope ls(c, "cnn_dweight", 0.0);
-            cnn_dweight(c->stream, dz, cz, kCout[l], xin[l], cx[l], kCin[l], B, H, W, s->d_g + s->off_w[l],
-                        s->d_g + s->off_b[l]);
+            cudaError_t e = cnn_dweight(c->stream, path, dz, cz, kCout[l], xin[l], cx[l], kCin[l], B, H, W, s->d_wpart,
+                                        s->d_err, s->d_g + s->off_w[l], s->d_g + s->off_b[l]);
+            if (e != cudaSuccess) return cuda_check(c, e, "surrogate weight gradient");
         }
         if (l == 0) break;
         ConvArgs a{};
@@ -535,6 +539,15 @@ mm_status mm_surrogate_weights(mm_ctx* c, double* get, const double* set, size_t
     return cuda_check(c, cudaDeviceSynchronize(), "surrogate weights");
 }
 
+// true once if a bounded tensor-core wait ran out since the last call
+// (the flag is cleared: the error is reported once and the context stays usable)
+static bool take_timeout(mm_ctx* c) {
+    int err = 0;
+    cudaMemcpy(&err, c->surr->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (err) cudaMemset(c->surr->d_err, 0, sizeof(int));
+    return err != 0;
+}
+
 mm_status mm_surrogate_forward(mm_ctx* c, int B, int H, int W, const double* x, double* y, int path) {
     if (!c || !x || !y || B <= 0 || H <= 0 || W <= 0 || (path != 0 && path != 1)) return MM_ERR_ARG;
     mm_status st = ensure_surrogate(c);
@@ -547,12 +560,7 @@ mm_status mm_surrogate_forward(mm_ctx* c, int B, int H, int W, const double* x, 
     cudaError_t e = cudaMemcpyAsync(h.data(), c->surr->y, h.size() * 4, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_check(c, e, "surrogate forward");
-    int err = 0;
-    cudaMemcpy(&err, c->surr->d_err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (err) {
-        cudaMemset(c->surr->d_err, 0, sizeof(int));   // reported once; the context stays usable
-        return set_error(c, MM_ERR_TIMEOUT, "tensor-core accumulator wait ran out");
-    }
+    if (take_timeout(c)) return set_error(c, MM_ERR_TIMEOUT, "tensor-core accumulator wait ran out");
     for (int b = 0; b < B; ++b)
         for (int cc = 0; cc < 3; ++cc)
             for (long long p = 0; p < (long long)H * W; ++p)
@@ -561,8 +569,8 @@ mm_status mm_surrogate_forward(mm_ctx* c, int B, int H, int W, const double* x, 
 }
 
 mm_status mm_surrogate_grad(mm_ctx* c, int B, int H, int W, const double* x, const double* t, double* loss,
-                            double* grad) {
-    if (!c || !x || !t || B <= 0 || H <= 0 || W <= 0) return MM_ERR_ARG;
+                            double* grad, int path) {
+    if (!c || !x || !t || B <= 0 || H <= 0 || W <= 0 || (path != 0 && path != 1)) return MM_ERR_ARG;
     mm_status st = ensure_surrogate(c);
     if (st == MM_OK && !c->surr->have_weights) st = mm_surrogate_weights(c, nullptr, nullptr, 0, nullptr);
     if (st == MM_OK) st = ensure_buffers(c, B, H, W);
@@ -579,7 +587,7 @@ mm_status mm_surrogate_grad(mm_ctx* c, int B, int H, int W, const double* x, con
     cudaMemcpy(s->t, ht.data(), n * 4, cudaMemcpyHostToDevice);
     cudaMemsetAsync(s->d_loss, 0, sizeof(double), c->stream);
     cnn_mse_grad(c->stream, s->y, s->t, B, H, W, s->dy, s->d_loss);
-    st = run_backward(c, B, H, W);
+    st = run_backward(c, B, H, W, path);
     if (st != MM_OK) return st;
     std::vector<float> hg(s->np);
     double l = 0;
@@ -587,6 +595,7 @@ mm_status mm_surrogate_grad(mm_ctx* c, int B, int H, int W, const double* x, con
     if (e == cudaSuccess) e = cudaMemcpyAsync(&l, s->d_loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_check(c, e, "surrogate gradient");
+    if (take_timeout(c)) return set_error(c, MM_ERR_TIMEOUT, "tensor-core accumulator wait ran out");
     if (loss) *loss = l;
     if (grad)
         for (int q = 0; q < s->np; ++q) grad[q] = hg[q];
@@ -683,7 +692,7 @@ mm_status mm_surrogate_train(mm_ctx* c, const mm_train_cfg* cfg, double* final_l
         run_forward(c, B, S, S, 1.f, 0);
         cudaMemsetAsync(s->d_loss, 0, sizeof(double), c->stream);
         cnn_mse_grad(c->stream, s->y, s->t, B, S, S, s->dy, s->d_loss);
-        run_backward(c, B, S, S);
+        run_backward(c, B, S, S, 0);
         s->adam_t += 1;
         cnn_adam(c->stream, s->d_p, s->d_g, s->d_m, s->d_v, s->np, (float)cfg->lr, s->adam_t);
         pack_all(c);
@@ -697,12 +706,15 @@ mm_status mm_surrogate_train(mm_ctx* c, const mm_train_cfg* cfg, double* final_l
     cudaFree(dm);
     cudaFree(dh);
     if (e != cudaSuccess) return cuda_check(c, e, "surrogate training");
+    const bool timed_out = take_timeout(c);
     s->train_loss = loss;
     surrogate_invalidate_graph(c);
     if (final_loss) *final_loss = loss;
     s->k = k_saved;
     s->ref_valid = false;
-    return mm_set_state(c, ck.data(), nb);
+    st = mm_set_state(c, ck.data(), nb);
+    if (st == MM_OK && timed_out) return set_error(c, MM_ERR_TIMEOUT, "tensor-core accumulator wait ran out");
+    return st;
 }
 
 mm_status mm_surrogate_set(mm_ctx* c, int k, double tol) {

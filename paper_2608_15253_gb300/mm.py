@@ -132,7 +132,7 @@ _SIGS = {
     "mm_surrogate_get_stats": [C.c_void_p, C.POINTER(mm_surrogate_stats)],
     "mm_surrogate_weights": [C.c_void_p, _D, _D, C.c_size_t, _D],
     "mm_surrogate_forward": [C.c_void_p, C.c_int, C.c_int, C.c_int, _D, _D, C.c_int],
-    "mm_surrogate_grad": [C.c_void_p, C.c_int, C.c_int, C.c_int, _D, _D, _D, _D],
+    "mm_surrogate_grad": [C.c_void_p, C.c_int, C.c_int, C.c_int, _D, _D, _D, _D, C.c_int],
     "mm_set_profiling": [C.c_void_p, C.c_int],
     "mm_get_profile": [C.c_void_p, C.POINTER(mm_profile_entry), C.POINTER(C.c_int)],
     "mm_debug_inject": [C.c_void_p, C.c_int],
@@ -428,13 +428,13 @@ def mm_surrogate_forward(ctx, x, path: int = 0):
     return y
 
 
-def mm_surrogate_grad(ctx, x, t):
+def mm_surrogate_grad(ctx, x, t, path: int = 0):
     x = _f64(x)
     t = _f64(t)
     B, _, H, W = x.shape
     loss = C.c_double(0.0)
     g = np.zeros(SURROGATE_NPARAMS)
-    _check(load().mm_surrogate_grad(ctx, B, H, W, _dptr(x), _dptr(t), C.byref(loss), _dptr(g)), ctx)
+    _check(load().mm_surrogate_grad(ctx, B, H, W, _dptr(x), _dptr(t), C.byref(loss), _dptr(g), path), ctx)
     return loss.value, g
 
 

@@ -2,7 +2,8 @@
 the paper has no learned part): the tensor-core (tcgen05) forward pass
 against the SIMT kernels and against the FP64 oracle network evaluated with
 the same BF16 rounding points; the backward pass against the oracle's
-gradients (themselves pinned by finite differences); training on pairs the
+gradients (themselves pinned by finite differences), and its tensor-core
+weight gradients against the SIMT kernel; training on pairs the
 exact FFT demag generates; surrogate-accelerated stepping with the exact
 demag as monitor and fallback.
 
@@ -87,7 +88,11 @@ def test_gradients_match_oracle():
         mm.mm_surrogate_weights(ctx, flat, c_in=1.0)
         x = rng.normal(size=(2, 3, 24, 40))
         t = rng.normal(size=(2, 3, 24, 40))
-        loss, g = mm.mm_surrogate_grad(ctx, x, t)
+        loss, g = mm.mm_surrogate_grad(ctx, x, t, path=0)
+        loss1, g1 = mm.mm_surrogate_grad(ctx, x, t, path=1)
+        assert loss1 == loss
+        # same BF16 operands, FP32 sums in another order
+        assert np.abs(g - g1).max() <= 1e-4 * np.abs(g1).max(), np.abs(g - g1).max() / np.abs(g1).max()
         params = _params_from_flat(flat)
         xb = cnn.bf16(x)
         y, cache = cnn.forward(params, xb)
@@ -100,6 +105,38 @@ def test_gradients_match_oracle():
             n = co * ci * 25 + co
             assert _rel(g[o:o + n], gflat[o:o + n]) < 3e-2, (li, _rel(g[o:o + n], gflat[o:o + n]))
             o += n
+    finally:
+        mm.mm_destroy(ctx)
+
+
+@pytest.mark.parametrize("B,H,Wd", [(16, 128, 128), (3, 9, 200), (1, 1, 5), (2, 37, 129)])
+def test_tensor_core_weight_gradient_matches_simt(B, H, Wd):
+    """The tensor-core weight gradients (MN-major operands, shifted row
+    copies, dZ row ring, per-CTA partial sums) against the SIMT kernel on the
+    same back-propagated BF16 gradients: the training batch shape (many rows
+    per CTA, shares crossing image boundaries), several ragged column blocks
+    with fewer rows than CTAs, a single row, and a column block one pixel
+    past 128.  Repeated calls are bit-identical (fixed-order reduction)."""
+    mm = need_gpu()
+    from oracle import cnn
+    ctx, _ = _ctx(mm)
+    try:
+        rng = np.random.default_rng(11)
+        flat = np.concatenate([np.concatenate([P["w"].ravel(), rng.normal(0, 0.05, P["b"].shape)])
+                               for P in cnn.init_params(seed=8)])
+        mm.mm_surrogate_weights(ctx, flat, c_in=1.0)
+        x = rng.normal(size=(B, 3, H, Wd))
+        t = rng.normal(size=(B, 3, H, Wd))
+        _, g0 = mm.mm_surrogate_grad(ctx, x, t, path=0)
+        _, g0b = mm.mm_surrogate_grad(ctx, x, t, path=0)
+        _, g1 = mm.mm_surrogate_grad(ctx, x, t, path=1)
+        assert np.array_equal(g0, g0b)
+        o = 0
+        for li, (co, ci) in enumerate([(32, 3), (32, 32), (32, 32), (3, 32)]):
+            for n in (co * ci * 25, co):                     # weights, then bias
+                a, b = g0[o:o + n], g1[o:o + n]
+                assert np.abs(a - b).max() <= 1e-4 * max(np.abs(b).max(), 1e-30), (li, n, np.abs(a - b).max())
+                o += n
     finally:
         mm.mm_destroy(ctx)
 
