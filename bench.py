@@ -524,17 +524,23 @@ def variant_drift(mm, stream, steps=200, every=20, dt=2e-14):
             "note": "fixed RK45 steps replayed in both precisions from the same seeded random state"}
 
 
-def variant_cnn_forward(mm, reps=5):
-    """The surrogate network's forward pass on the 512x512 film (BF16 tcgen05
-    convolutions), per layer from the library's CUDA-event profile: time,
-    and throughput on the network's algorithmic FLOPs (real channels:
-    2 x 25 x (3*32 + 32*32 + 32*32 + 32*3) per pixel) against the measured
-    BF16 peak."""
+def variant_cnn(mm, reps=5):
+    """The surrogate network on the tensor cores: the forward pass on the
+    512x512 film and one training step's backward pass (batch of 16 128x128
+    windows), per kernel from the library's CUDA-event profile, with
+    throughput on the network's algorithmic FLOPs (real channels:
+    2 x 25 x (3*32 + 32*32 + 32*32 + 32*3) per pixel per contraction)
+    against the measured BF16 peak."""
     w = W.skyrmion_512()
     g = w.grid
     M = mm.Material(w.mat.Ms, w.mat.A, w.mat.alpha, w.mat.Ku1, w.mat.u, w.mat.D)
     c = mm.mm_create(mm.make_grid(g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), M.s,
                      mm.make_config(precision=32, integrator=mm.MM_RK45, demag=mm.MM_DEMAG_EXACT, dt=1e-13))
+    per_px = 2.0 * 25 * (3 * 32 + 32 * 32 + 32 * 32 + 32 * 3)
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except Exception:
+        peak = 1900.0
     try:
         rng = np.random.default_rng(4)
         mm.mm_surrogate_weights(c, rng.normal(0.0, 0.05, mm.SURROGATE_NPARAMS), c_in=1.0)
@@ -543,23 +549,35 @@ def variant_cnn_forward(mm, reps=5):
         mm.mm_set_profiling(c, True)
         for _ in range(reps):
             mm.mm_surrogate_forward(c, x)
-        prof = [p for p in mm.mm_get_profile(c) if p["name"].startswith("cnn_conv")]
+        fwd = [p for p in mm.mm_get_profile(c) if p["name"].startswith("cnn_conv")]
+        mm.mm_set_profiling(c, False)
+        xb = rng.normal(size=(16, 3, 128, 128))
+        tb = rng.normal(size=(16, 3, 128, 128))
+        mm.mm_surrogate_grad(c, xb, tb)
+        mm.mm_set_profiling(c, True)
+        for _ in range(reps):
+            mm.mm_surrogate_grad(c, xb, tb)
+        bwd = [p for p in mm.mm_get_profile(c) if p["name"] in ("cnn_dweight", "cnn_dgrad")]
         mm.mm_set_profiling(c, False)
     finally:
         mm.mm_destroy(c)
-    fwd_us = 1e3 * sum(p["total_ms"] for p in prof) / reps
-    flops = 2.0 * 25 * (3 * 32 + 32 * 32 + 32 * 32 + 32 * 3) * g.nx * g.ny
-    peak = None
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peak = float(json.load(f)["bf16_tflops"])
-    except Exception:
-        peak = 1900.0
-    tf = flops / (fwd_us * 1e-6) / 1e12
-    return {"grid": [g.nx, g.ny], "forward_us": round(fwd_us, 2),
-            "layers_us": {p["name"]: round(1e3 * p["total_ms"] / p["launches"], 2) for p in prof},
-            "algorithmic_gflop": round(flops / 1e9, 3), "tflops": round(tf, 1), "bf16_peak_tflops": peak,
-            "frac_of_bf16_peak": round(tf / peak, 4)}
+    fwd_us = 1e3 * sum(p["total_ms"] for p in fwd) / reps
+    tf = per_px * g.nx * g.ny / (fwd_us * 1e-6) / 1e12
+    bw = {p["name"]: {"per_step_us": round(1e3 * p["total_ms"] / reps, 2),
+                      "per_launch_us": round(1e3 * p["total_ms"] / p["launches"], 2)} for p in bwd}
+    dw_us = bw.get("cnn_dweight", {}).get("per_step_us")
+    out = {"forward": {"grid": [g.nx, g.ny], "us": round(fwd_us, 2),
+                       "layers_us": {p["name"]: round(1e3 * p["total_ms"] / p["launches"], 2) for p in fwd},
+                       "algorithmic_gflop": round(per_px * g.nx * g.ny / 1e9, 3), "tflops": round(tf, 1),
+                       "frac_of_bf16_peak": round(tf / peak, 4)},
+           "backward": {"batch": [16, 128, 128], "kernels": bw},
+           "bf16_peak_tflops": peak}
+    if dw_us:
+        # weight gradients of all four layers: the same FLOPs as one forward pass
+        tfw = per_px * 16 * 128 * 128 / (dw_us * 1e-6) / 1e12
+        out["backward"]["weight_grad_tflops"] = round(tfw, 1)
+        out["backward"]["weight_grad_frac_of_bf16_peak"] = round(tfw / peak, 4)
+    return out
 
 
 def variant_peaks(mm):
@@ -1001,7 +1019,7 @@ def run_gpu(args):
                                                                    args.steps)),
                          ("film_128x32_fp64", lambda: variant_film_fp64(mm, stream)),
                          ("drift", lambda: variant_drift(mm, stream)),
-                         ("cnn_forward", lambda: variant_cnn_forward(mm)),
+                         ("cnn", lambda: variant_cnn(mm)),
                          ("cufft", lambda: variant_cufft(mm, stream)),
                          ("batched", lambda: variant_batched(mm, stream, args.batch_steps)),
                          ("surrogate", lambda: variant_surrogate(mm, stream, args.surrogate_steps)),
@@ -1036,7 +1054,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", default="", help="nx,ny,nz: a smaller case of the same workload (profiling)")
     ap.add_argument("--no-variants", action="store_true", help="skip the error, FP64 and variant lines")
-    ap.add_argument("--variants", default="peaks,dmi_256x256x16,film_128x32_fp64,drift,cufft,cnn_forward,batched,"
+    ap.add_argument("--variants", default="peaks,dmi_256x256x16,film_128x32_fp64,drift,cufft,cnn,batched,"
                                           "surrogate,"
                                           "paper_scenarios,batching_table,stt_sweep,sp4",
                     help="comma list of variant lines to run")
