@@ -662,6 +662,44 @@ def variant_batched(mm, stream, steps):
                                 "against": "the FP64 CPU oracle stepping that replica alone (same key, current)"}}
 
 
+def variant_trials_films(mm, stream, steps=200, R=512, n=64, n_trials=16384):
+    """Retire/refill over thermal switching trials of 64x64 films with exact
+    demag (Results, "Replica batching"): 512 slots, 16384 trials with their
+    own current and Philox key, FP32 Depondt-Mertens, stop test after every
+    step; the same run timed on the persistent launch shape and on the
+    stacked shape."""
+    mat = W.Material(Ms=1.1e6, A=2e-11, alpha=0.02, Ku1=9e5, u=(0.0, 0.0, 1.0))
+    M = mm.Material(mat.Ms, mat.A, mat.alpha, mat.Ku1, mat.u, mat.D)
+    g = mm.make_grid(n, n, 1, 2e-9, 2e-9, 1e-9)
+    J = np.linspace(2e11, 2e12, n_trials)
+    m_init = np.zeros((3, 1, n, n))
+    m_init[2] = 1.0
+    out = {"workload": f"{R} slots of {n}x{n}x1 films of 2x2x1 nm, {n_trials} trials (STT J in [2e11, 2e12] A/m^2, "
+                       "300 K), exact demag, FP32 Depondt-Mertens dt=1e-13 s, retire at m_z <= 0",
+           "unit": "cell-steps/s", "steps": steps}
+    for shape in ("persistent", "stacked"):
+        cfg = mm.make_config(precision=32, integrator=mm.MM_DM, demag=mm.MM_DEMAG_EXACT, dt=1e-13, T=0.0,
+                             terms=1 | 4 | 8 | 16 | 32)
+        ctx = mm.mm_create_batch([g] * R, M.s, cfg, None)
+        try:
+            mm.mm_set_stream(ctx, stream.cuda_stream)
+            mm.mm_set_torque(ctx, mm.make_torque(mm.MM_TORQUE_STT, p=(0, 0, -1), P=0.6, Lambda=1.0), np.zeros(R))
+            if shape == "stacked":
+                mm.mm_batch_set_shape(ctx, 0)
+            else:
+                mm.mm_batch_set_shape(ctx, 256, min(R, 304))
+            mm.mm_trials_start(ctx, J, np.full(n_trials, 300.0), m_init, axis=(0, 0, 1), threshold=0.0,
+                               max_steps=4000, base_seed=5, refill=True)
+            mm.mm_step(ctx, 5)
+            ms = _timed(stream, lambda: mm.mm_step(ctx, steps))
+            done = mm.mm_trials_result(ctx)[2]
+        finally:
+            mm.mm_destroy(ctx)
+        out[shape] = {"ms_per_step": ms / steps, "value": R * n * n * steps / (ms * 1e-3), "trials_done": int(done)}
+    out["stacked_over_persistent"] = out["persistent"]["ms_per_step"] / out["stacked"]["ms_per_step"]
+    return out
+
+
 # The paper's replica-batching table (Results, "Replica batching"): physics,
 # replica grid, replica count R, and its published throughput (on its own
 # hardware, an RTX 5060 Ti).  Materials are not printed there; the
@@ -1020,6 +1058,7 @@ def run_gpu(args):
                          ("film_128x32_fp64", lambda: variant_film_fp64(mm, stream)),
                          ("drift", lambda: variant_drift(mm, stream)),
                          ("cnn", lambda: variant_cnn(mm)),
+                         ("trials_films", lambda: variant_trials_films(mm, stream)),
                          ("cufft", lambda: variant_cufft(mm, stream)),
                          ("batched", lambda: variant_batched(mm, stream, args.batch_steps)),
                          ("surrogate", lambda: variant_surrogate(mm, stream, args.surrogate_steps)),
@@ -1054,7 +1093,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", default="", help="nx,ny,nz: a smaller case of the same workload (profiling)")
     ap.add_argument("--no-variants", action="store_true", help="skip the error, FP64 and variant lines")
-    ap.add_argument("--variants", default="peaks,dmi_256x256x16,film_128x32_fp64,drift,cufft,cnn,batched,"
+    ap.add_argument("--variants", default="peaks,dmi_256x256x16,film_128x32_fp64,drift,cufft,cnn,batched,trials_films,"
                                           "surrogate,"
                                           "paper_scenarios,batching_table,stt_sweep,sp4",
                     help="comma list of variant lines to run")

@@ -201,8 +201,10 @@ MM_API mm_status mm_create(const mm_grid* grid, const mm_material* mat,
  * Depondt-Mertens, nz = 1 open films sharing one cell size and one uniform
  * material (Ms > 0);
  * nx, ny may differ per replica (sizes of the same shape share one tensor
- * spectrum).  Each stage is one persistent launch (mm_batch_autotune
- * picks its shape).  Errors: MM_ERR_ARG for any other combination. */
+ * spectrum).  A stage runs as one persistent launch or, in the stacked
+ * shape, as per-size-class passes (mm_batch_autotune picks the shape,
+ * mm_batch_set_shape sets it; retire/refill runs on both).  Errors:
+ * MM_ERR_ARG for any other combination. */
 MM_API mm_status mm_create_batch(int R, const mm_grid* grids, const mm_material* mat,
                                  const mm_config* cfg, const uint64_t* seeds, mm_ctx** out);
 

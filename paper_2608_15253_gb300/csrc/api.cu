@@ -1401,7 +1401,7 @@ mm_status mm_batch_autotune(mm_ctx* c, const char* cache_path, int* nt_out, int*
                 if (nb == c->R) break;
             }
         }
-        if (batch_stacked_allowed(c->batch)) {
+        {
             // the stacked shape: per size class, passes over all of its replicas
             batch_set_shape(c->batch, 0, 0);
             int got_nt = -1, got_b = -1;

@@ -446,10 +446,20 @@ static void stacked_stage(mm_ctx* c, BatchHost* b, int stage) {
 }
 
 void batch_step(mm_ctx* c, BatchHost* b) {
-    if (b->stacked && !b->trials_on) {
+    if (b->stacked) {
         heun_batch_begin(c);
         stacked_stage(c, b, 1);
         stacked_stage(c, b, 2);
+        if (b->trials_on) {
+            BatchArgs a{};
+            a.rep = b->d_rep;
+            a.m0 = (float*)c->d_m;
+            a.trials = 1;
+            a.tr = b->tr;
+            a.st = c->d_state;
+            LaunchScope ls(c, "stacked_trials", 12.0 * (double)c->Ntot);
+            stacked_trials_launch(a, (int)b->rep.size(), c->stream);
+        }
         heun_batch_advance(c);
         return;
     }
@@ -508,7 +518,6 @@ void batch_get_shape(BatchHost* b, int* nt, int* blocks) {
     *blocks = b->stacked ? 0 : b->blocks;
 }
 
-bool batch_stacked_allowed(BatchHost* b) { return !b->trials_on; }
 
 // signature of the batch for the autotuner cache: sizes histogram + demag flag
 std::string batch_signature(BatchHost* b, unsigned terms) {

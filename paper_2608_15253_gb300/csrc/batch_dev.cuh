@@ -460,6 +460,7 @@ struct StackArgs {
     const DevState* st;
 };
 void stacked_field_launch(const StackArgs& a, int Rc, cudaStream_t s);
+void stacked_trials_launch(const BatchArgs& a, int R, cudaStream_t s);
 void macro_kernel_launch(const MacroArgs& a, cudaStream_t s);
 void tile_kernel_launch(const MacroArgs& a, cudaStream_t s);
 cudaError_t tile_kernel_attributes();

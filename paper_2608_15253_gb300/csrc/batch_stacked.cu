@@ -4,7 +4,8 @@
 // then this kernel: field, torque and the Heun or Depondt-Mertens stage
 // update of every cell of the class, one thread per cell, each replica with
 // its own Philox key, temperature and current.  A few well-filled launches
-// per class replace one CTA per replica.
+// per class replace one CTA per replica.  With retire/refill on, idle slots
+// are skipped and a per-slot stop test follows the corrector.
 #include <cuda_runtime.h>
 
 #include "batch_dev.cuh"
@@ -20,6 +21,7 @@ __global__ void __launch_bounds__(256) stacked_field_kernel(StackArgs a) {
     const int nx = a.nx, ny = a.ny;
     if (x >= nx || y >= ny) return;
     const RepDev& rp = a.rep[a.members[q]];
+    if (!rp.active) return;              // an idle retire/refill slot keeps its state
     const long long N = (long long)nx * ny;
     const long long i = (long long)y * nx + x;
     FieldArgs<float> fa = a.fa;
@@ -80,6 +82,27 @@ __global__ void __launch_bounds__(256) stacked_field_kernel(StackArgs a) {
         const v3<float> mn = a.dm ? rodrigues<float>(m0, 0.5f * (kp + k), dt) : m0 + (0.5f * dt) * (kp + k);
         st3(a.m0 + rp.off, N, i, rsqrtf(dot(mn, mn)) * mn);
     }
+}
+
+// Retire/refill on the stacked shape (Results, "Replica batching"): after
+// the corrector of every class, one CTA per slot forms the mean of m . axis
+// over its replica, runs the stop test and, when a new trial takes the
+// slot, writes its initial state.
+__global__ void __launch_bounds__(256) stacked_trials_kernel(BatchArgs a) {
+    if (!a.st->active) return;
+    const int idx = blockIdx.x;
+    const RepDev rp = a.rep[idx];
+    if (!rp.active) return;                           // uniform over the CTA
+    const long long N = (long long)rp.nx * rp.ny;
+    const float* m = a.m0 + rp.off;
+    const float ax = a.tr.axis[0], ay = a.tr.axis[1], az = a.tr.axis[2];
+    float part = 0.f;
+    for (long long i = threadIdx.x; i < N; i += 256) part += m[i] * ax + m[N + i] * ay + m[2 * N + i] * az;
+    slot_retire_refill<256>(a, rp, idx, part, N, a.st->step);
+}
+
+void stacked_trials_launch(const BatchArgs& a, int R, cudaStream_t s) {
+    stacked_trials_kernel<<<R, 256, 0, s>>>(a);
 }
 
 void stacked_field_launch(const StackArgs& a, int Rc, cudaStream_t s) {

@@ -251,7 +251,6 @@ mm_status batch_setup(mm_ctx* c, BatchHost* b, const std::vector<mm_grid>& grids
 mm_status batch_upload(mm_ctx* c, BatchHost* b, const std::vector<double>& T, const std::vector<double>& J);
 void batch_step(mm_ctx* c, BatchHost* b);
 bool batch_is_fused(BatchHost* b);
-bool batch_stacked_allowed(BatchHost* b);
 void batch_macro_steps(mm_ctx* c, BatchHost* b, int nsteps);
 mm_status batch_trials_start(mm_ctx* c, BatchHost* b, const mm_trials* sp, long long step_now);
 mm_status batch_trials_result(mm_ctx* c, BatchHost* b, long long* steps, int* stopped, long long* done);

@@ -156,10 +156,13 @@ def test_retire_refill_macrospins_match_oracle():
         mm.mm_destroy(ctx)
 
 
-def test_retire_refill_films_match_oracle():
+@pytest.mark.parametrize("shape", ["persistent", "stacked"])
+def test_retire_refill_films_match_oracle(shape):
     """10 trials over 4 slots of 8 x 8 films with exchange, anisotropy,
-    demag, STT and the thermal field (one persistent launch per stage, the
-    stop test after the corrector)."""
+    demag, STT and the thermal field, on both launch shapes: one persistent
+    launch per stage with the stop test inside the corrector, or the
+    per-class passes with idle slots skipped and a per-slot stop-test
+    launch after the corrector."""
     mm = need_gpu()
     grid = W.Grid(8, 8, 1, D1, D1, D1)
     mat = W.Material(Ms=1e6, A=1.5e-11, alpha=0.05, Ku1=1.1e6, u=(0, 0, 1))
@@ -168,6 +171,8 @@ def test_retire_refill_films_match_oracle():
                  np.full(n, 300.0), 1e-13, 0.98, 300)
     ctx = _context(mm, spec, 4, mm.MM_DM, 1 | 4 | 8 | 16 | 32, True)
     try:
+        if shape == "stacked":
+            mm.mm_batch_set_shape(ctx, 0)
         mm.mm_trials_start(ctx, spec.J, spec.T, spec.m_init, axis=spec.axis, threshold=spec.threshold,
                            max_steps=spec.max_steps, base_seed=spec.base_seed, refill=True)
         steps, stopped = _run_to_completion(mm, ctx, n, chunk=50)
