@@ -118,8 +118,10 @@ __device__ __forceinline__ void fset(float4& v, int q, float x) {
 
 // The V cells x0 .. x0 + V - 1 of row (z, y).  HD_SMEM: the demag field of
 // the cells comes from shared memory (hds[c * hd_stride + q], the fused
-// inverse-X-pass kernel below), else from a.Hd in global memory.
-template <int V, bool EXT, bool HD_SMEM>
+// inverse-X-pass kernel below), else from a.Hd in global memory.  QUIET:
+// slopes only (MODE_K), no thermal field, no spin torque -- the variant for
+// deterministic runs without current, with far fewer registers.
+template <int V, bool EXT, bool HD_SMEM, bool QUIET = false>
 __device__ __forceinline__ void field_vec_cells(const FieldArgs<float>& a, int x0, int y, int z, const float* hds,
                                                 int hd_stride) {
     using VT = typename fvec<V>::t;
@@ -131,7 +133,7 @@ __device__ __forceinline__ void field_vec_cells(const FieldArgs<float>& a, int x
 #pragma unroll
     for (int c = 0; c < 3; ++c) mc[c] = ldv<V>(a.m + c * N + i0);
     const unsigned nbt = MM_TERM_EXCHANGE | MM_TERM_DMI | (EXT ? MM_TERM_SURFACE : 0u);
-    const bool need_nb = (a.terms & nbt) || a.tq == MM_TORQUE_ZL;
+    const bool need_nb = (a.terms & nbt) || (!QUIET && a.tq == MM_TORQUE_ZL);
     // neighbour rows (y+, y-, z+, z-) as vectors, row-end x neighbours as scalars
     VT nr[4][3];
     bool rin[4] = {false, false, false, false};
@@ -205,11 +207,12 @@ __device__ __forceinline__ void field_vec_cells(const FieldArgs<float>& a, int x
         }
         const v3<float> hq = dem ? mk3<float>(fget(hd[0], q), fget(hd[1], q), fget(hd[2], q)) : mk3<float>(0, 0, 0);
         v3<float> H, k;
-        cell_field_nb<float, EXT>(a, i0 + q, R, m, nbv, nbp, cnb, dem, hq, step, H, k, a.mode != MODE_H,
-                                  a.mode >= MODE_DM1);
+        cell_field_nb<float, EXT, QUIET>(a, i0 + q, R, m, nbv, nbp, cnb, dem, hq, step, H, k,
+                                         QUIET || a.mode != MODE_H, !QUIET && a.mode >= MODE_DM1);
         v3<float> r1 = H, r2 = k;
-        if (a.mode == MODE_K) r1 = k;
-        else if (a.mode == MODE_HEUN1) {
+        if (QUIET || a.mode == MODE_K) r1 = k;
+        else if (QUIET) {
+        } else if (a.mode == MODE_HEUN1) {
             const float dt = (float)a.st->dt_eff;
             r1 = m + dt * k;
             r2 = k;
@@ -240,20 +243,20 @@ __device__ __forceinline__ void field_vec_cells(const FieldArgs<float>& a, int x
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) stv<V>(o + c * N + i0, o1[c]);
-    if (a.mode == MODE_HEUN1 || a.mode == MODE_DM1) {
+    if (!QUIET && (a.mode == MODE_HEUN1 || a.mode == MODE_DM1)) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) stv<V>(a.out2 + c * N + i0, o2[c]);
     }
 }
 
-template <int V, bool EXT>
+template <int V, bool EXT, bool QUIET = false>
 __global__ void __launch_bounds__(256) field_vec_kernel(FieldArgs<float> a) {
     if (a.gate && !a.st->active) return;
     const int x0 = V * (blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x0 >= a.nx || y >= a.ny) return;
-    field_vec_cells<V, EXT, false>(a, x0, y, z, nullptr, 0);
+    field_vec_cells<V, EXT, false, QUIET>(a, x0, y, z, nullptr, 0);
 }
 
 // The last demag pass (inverse X, half spectrum -> real rows) fused with
@@ -271,7 +274,7 @@ struct C2RSpec {
 template <int LT>
 constexpr size_t c2r_field_smem() { return (size_t)8 * wline(LT) * sizeof(float2) + 3 * 1024 * sizeof(float); }
 
-template <int LT, bool EXT>
+template <int LT, bool EXT, bool QUIET = false>
 __global__ void __launch_bounds__(256) c2r_field_kernel(FieldArgs<float> a, C2RSpec s) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (a.gate && !a.st->active) return;
@@ -297,7 +300,7 @@ __global__ void __launch_bounds__(256) c2r_field_kernel(FieldArgs<float> a, C2RS
     const int row = row0 + rl;
     if (rl < rpc && row < nrows) {
         const int z = row / a.ny, y = row - z * a.ny;
-        field_vec_cells<4, EXT, true>(a, x0, y, z, sH + rl * 3 * nx + x0, nx);
+        field_vec_cells<4, EXT, true, QUIET>(a, x0, y, z, sH + rl * 3 * nx + x0, nx);
     }
 }
 
@@ -366,6 +369,14 @@ static FieldArgs<T> field_args(mm_ctx* c, int mode, unsigned terms, const T* m, 
     return a;
 }
 
+// The QUIET kernels apply: slopes only, no thermal field, no spin torque,
+// none of the further local terms.
+template <typename T>
+static bool field_quiet(const mm_ctx* c, int mode, unsigned terms, const FieldArgs<T>& a) {
+    return mode == MODE_K && !c->ext_terms && a.tq == MM_TORQUE_NONE &&
+           (!(terms & MM_TERM_THERMAL) || a.th_scale == (T)0);
+}
+
 static double field_bytes(const mm_ctx* c, int mode, unsigned terms, bool hd) {
     const double es = (double)c->esz;
     double bytes = 3 * es * 2 * c->N;          // read m, write out
@@ -391,6 +402,8 @@ static void field_launch_t(mm_ctx* c, int mode, unsigned terms, const T* m, cons
             if (g.nx % kFieldV == 0 && a.R0.present != 0.f) {
                 dim3 grdv((g.nx / kFieldV + 31) / 32, (g.ny + 7) / 8, g.nz);
                 if (c->ext_terms) field_vec_kernel<kFieldV, true><<<grdv, blk, 0, c->stream>>>(a);
+                else if (field_quiet(c, mode, terms, a))
+                    field_vec_kernel<kFieldV, false, true><<<grdv, blk, 0, c->stream>>>(a);
                 else field_vec_kernel<kFieldV, false><<<grdv, blk, 0, c->stream>>>(a);
                 return;
             }
@@ -442,6 +455,9 @@ cudaError_t field_c2r_setup() {
                                  (int)c2r_field_smem<n>());                                                   \
     if (e == cudaSuccess)                                                                                     \
         e = cudaFuncSetAttribute(c2r_field_kernel<n, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                 (int)c2r_field_smem<n>());                                                   \
+    if (e == cudaSuccess)                                                                                     \
+        e = cudaFuncSetAttribute(c2r_field_kernel<n, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                  (int)c2r_field_smem<n>());
     MM_C2R_FIELD_LENGTHS(MM_CASE)
 #undef MM_CASE
@@ -459,10 +475,12 @@ void field_c2r_launch(mm_ctx* c, int mode, unsigned terms, const void* m, void* 
     const unsigned grid = (unsigned)((rows + rpc - 1) / rpc);
     const double bytes = field_bytes(c, mode, terms, false) + 3.0 * rows * (d.Kx * sizeof(float2));
     LaunchScope ls(c, "c2r_field", bytes);
+    const bool quiet = field_quiet(c, mode, terms, a);
     switch (d.Lh) {
 #define MM_CASE(n)                                                                                            \
     case n:                                                                                                   \
         if (c->ext_terms) c2r_field_kernel<n, true><<<grid, 256, c2r_field_smem<n>(), c->stream>>>(a, sp);      \
+        else if (quiet) c2r_field_kernel<n, false, true><<<grid, 256, c2r_field_smem<n>(), c->stream>>>(a, sp); \
         else c2r_field_kernel<n, false><<<grid, 256, c2r_field_smem<n>(), c->stream>>>(a, sp);                 \
         break;
         MM_C2R_FIELD_LENGTHS(MM_CASE)

@@ -140,7 +140,9 @@ __device__ __forceinline__ void st3(T* a, long long N, long long i, v3<T> v) {
 // u' = (u.grad) m, so that Omega x m is the slope.
 // EXT = false compiles out bulk DMI and the further local terms (cubic,
 // surface, RKKY, magnetoelastic): the lean kernel for contexts without them.
-template <typename T, bool EXT = true>
+// QUIET = true also compiles out the thermal field and every spin torque
+// (contexts at T = 0 without current).
+template <typename T, bool EXT = true, bool QUIET = false>
 __device__ __forceinline__ void cell_field_nb(const FieldArgs<T>& a, long long i, const Region<T>& R,
                                               const v3<T>& m, const v3<T>* nbv, const bool* nbp, const T* cnb,
                                               bool use_hd, const v3<T>& hdv, long long step, v3<T>& H, v3<T>& k,
@@ -217,12 +219,13 @@ __device__ __forceinline__ void cell_field_nb(const FieldArgs<T>& a, long long i
         if (use_hd) H = H + hdv;
         else if (a.Hd) H = H + ld3(a.Hd, N, i);
     }
-    if ((a.terms & MM_TERM_THERMAL) && a.th_scale != (T)0) H = H + thermal_h<T>(a, i, R, step);
+    if (!QUIET && (a.terms & MM_TERM_THERMAL) && a.th_scale != (T)0) H = H + thermal_h<T>(a, i, R, step);
     if (!want_k) return;
     // LLG torque, Eq. 1: -gamma' mu0 [m x H + alpha m x (m x H)]
     const v3<T> mxH = cross(m, H);
     if (as_omega) k = R.gm * (H + R.alpha * mxH);
     else k = (-R.gm) * (mxH + R.alpha * cross(m, mxH));
+    if (QUIET) return;
     if (a.tq == MM_TORQUE_SOT || a.tq == MM_TORQUE_STT) {
         const v3<T> p = mk3<T>(a.p[0], a.p[1], a.p[2]);
         const T base = a.tq_base * R.inv_Ms;
