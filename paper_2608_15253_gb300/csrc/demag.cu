@@ -446,6 +446,68 @@ __global__ void __launch_bounds__(32 * kXW) fft_x_c2r_warp_kernel(XArgs<float> a
     });
 }
 
+// C2R with the spectrum rows prefetched: persistent warps, each with two
+// line buffers in shared memory.  While a warp transforms one row (in place
+// in one buffer), cp.async brings its next row into the other, so the
+// global-memory latency of a row hides behind the transform of the previous
+// one instead of stalling the first pass.
+__device__ __forceinline__ void cpa16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cpa8(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// float2 per line buffer: the padded line, rounded to 16 bytes
+template <int LT> constexpr int xpipe_buf() { return (wline(LT) + 1) & ~1; }
+template <int LT> constexpr size_t xpipe_smem() { return (size_t)kXW * 2 * xpipe_buf<LT>() * sizeof(float2); }
+
+template <int LT>
+__global__ void __launch_bounds__(32 * kXW, 3) fft_x_c2r_pipe_kernel(XArgs<float> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int BS = xpipe_buf<LT>();
+    static_assert(LT % 2 == 0, "16-byte pieces of the half spectrum");
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2* buf = reinterpret_cast<float2*>(smem_raw) + warp * 2 * BS;
+    const int nw = gridDim.x * kXW;
+    float* const out0 = a.out_real;
+    const bool vec2 = (a.nx % 2 == 0) && (a.in_pitch % 2 == 0);
+    const int nx = a.nx;
+    // row r's LT + 1 spectrum values (16-byte aligned: the pitch Wk is even)
+    auto fetch = [&](int r, float2* dst) {
+        const float2* src = a.spec + spec_row(a, r) * a.Wk;
+        for (int q = lane; q < LT / 2; q += 32) cpa16(dst + 2 * q, src + 2 * q);
+        if (lane == 0) cpa8(dst + LT, src + LT);
+        cpa_commit();
+    };
+    int row = blockIdx.x * kXW + warp;
+    if (row < a.rows) fetch(row, buf);
+    for (int it = 0; row < a.rows; ++it, row += nw) {
+        float2* cur = buf + (it & 1) * BS;
+        if (row + nw < a.rows) {
+            fetch(row + nw, buf + ((it + 1) & 1) * BS);
+            cpa_wait<1>();
+        } else {
+            cpa_wait<0>();
+        }
+        __syncwarp();
+        float* out = out0 + (long long)row * a.in_pitch;
+        warp_c2r_inplace<LT>(cur, a.tw, [&](int n, float2 v) {
+            if (2 * n + 1 < nx) {
+                if (vec2) *reinterpret_cast<float2*>(out + 2 * n) = v;
+                else { out[2 * n] = v.x; out[2 * n + 1] = v.y; }
+            } else if (2 * n < nx) {
+                out[2 * n] = v.x;
+            }
+        });
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Column passes (strided axes), optionally with the tensor multiply
 // ---------------------------------------------------------------------------
@@ -986,6 +1048,25 @@ static XKern<float> x_warp_kernel(bool fwd, int Lh) {
     }
 }
 
+// prefetching C2R (persistent warps); null where the plain warp kernel is used
+#define MM_XPIPE_LENGTHS(X) X(256) X(512)
+static XKern<float> x_c2r_pipe_kernel(int Lh) {
+    switch (Lh) {
+#define MM_CASE(n) case n: return fft_x_c2r_pipe_kernel<n>;
+        MM_XPIPE_LENGTHS(MM_CASE)
+#undef MM_CASE
+        default: return nullptr;
+    }
+}
+static size_t x_c2r_pipe_smem(int Lh) {
+    switch (Lh) {
+#define MM_CASE(n) case n: return xpipe_smem<n>();
+        MM_XPIPE_LENGTHS(MM_CASE)
+#undef MM_CASE
+        default: return 0;
+    }
+}
+
 // R2C fused with RK45 stage s (1..6); null where the warp path does not apply
 static XKern<float> x_stage_kernel(int s, int Lh) {
 #define MM_ST(n) \
@@ -1069,6 +1150,19 @@ static void launch_x(mm_ctx* c, bool forward, const T* in, T* out_real, cplx<T>*
             LaunchScope ls(c, "fft_x_r2c_stage",
                            (double)rows * ((reads + 1.0) * nx * sizeof(T) + (Lh + 1) * sizeof(cplx<T>)));
             x_stage_kernel(stage, Lh)<<<(rows + kXW - 1) / kXW, 32 * kXW, smem, c->stream>>>(a);
+            return;
+        }
+        if (!forward && stage == 0 && x_c2r_pipe_kernel(Lh) && c->dm.Wk % 2 == 0) {
+            static int occ[1024] = {};
+            if (!occ[Lh]) {
+                int o = 0;
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, x_c2r_pipe_kernel(Lh), 32 * kXW,
+                                                              x_c2r_pipe_smem(Lh));
+                occ[Lh] = std::max(1, o);
+            }
+            const int grid = std::max(1, std::min((rows + kXW - 1) / kXW, occ[Lh] * sm_count()));
+            LaunchScope ls(c, "fft_x_c2r", (double)rows * (nx * sizeof(T) + (Lh + 1) * sizeof(cplx<T>)));
+            x_c2r_pipe_kernel(Lh)<<<grid, 32 * kXW, x_c2r_pipe_smem(Lh), c->stream>>>(a);
             return;
         }
         // the plain one-row-per-warp kernels take no stage combine: with a
@@ -1406,6 +1500,8 @@ static cudaError_t fast_attributes() {
         if (e == cudaSuccess) e = smem_attr(zconv_reg_kernel(L, false));
         if (e == cudaSuccess) e = smem_attr(zconv_reg_kernel(L, true));
     }
+    for (int L : {256, 512})
+        if (e == cudaSuccess) e = smem_attr(x_c2r_pipe_kernel(L));
     for (int L : {192, 216, 256, 324, 432, 512}) {
         if (e == cudaSuccess) e = smem_attr(x_warp_kernel(true, L));
         if (e == cudaSuccess) e = smem_attr(x_warp_kernel(false, L));

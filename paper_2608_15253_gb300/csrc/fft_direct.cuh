@@ -264,4 +264,26 @@ __device__ __forceinline__ void warp_c2r(const float2* __restrict__ X, const flo
                                                                       store);
 }
 
+// The same inverse real transform with the half spectrum already in the
+// warp's line: sm[0 .. M] holds X[k] at plain index k.  The first pass reads
+// every value it needs before its __syncwarp and writes its outputs to the
+// padded positions afterwards, so it runs in place.
+template <int LT, typename Store>
+__device__ __forceinline__ void warp_c2r_inplace(float2* sm, const float2* __restrict__ tw, Store store) {
+    constexpr int NP = ct_npass(LT), M = LT;
+    static_assert(NP >= 2, "first and last pass must differ");
+    auto load_rebuild = [&](int k) {
+        const float2 xk = sm[k];
+        const float2 xc = cconj<float>(sm[M - k]);
+        const float2 E = cadd<float>(xk, xc);
+        const float2 O = cmulc<float>(csub<float>(xk, xc), __ldg(&tw[k]));
+        return cadd<float>(E, mul_mi<float, -1>(O));
+    };
+    auto to_smem = [&](int i, float2 v) { sm[wpad(i)] = v; };
+    warp_pass<float, -1, LT, ct_radix(LT, 0), 1>(tw, 2, load_rebuild, to_smem);
+    warp_fft_smem<float, -1, LT, 1, NP - 1>(sm, tw, 2);
+    warp_pass<float, -1, LT, ct_radix(LT, NP - 1), ct_ns(LT, NP - 1)>(tw, 2, [&](int i) { return sm[wpad(i)]; },
+                                                                      store);
+}
+
 }  // namespace mm
