@@ -114,10 +114,10 @@ __device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float* v) {
 // ---------------------------------------------------------------------------
 enum { OUT_BF16 = 0, OUT_FIELD = 1, OUT_MASKED = 2 };
 
-// Row-streaming convolution.  One CTA walks down a 128-pixel column block of
-// one image over a run of output rows.  The packed weights are loaded once
-// and stay in shared memory; input rows live in a ring of kRing row slots
-// filled by cp.async kPref rows ahead (every input row fetched once per CTA).
+// Row-streaming convolution, warp-specialised.  One CTA walks down a
+// 128-pixel column block of one image over a run of output rows.  The
+// packed weights are loaded once and stay in shared memory; input rows live
+// in a ring of kWsRing row slots (every input row fetched once per CTA).
 //
 // The loop runs over INPUT rows: padded input row k feeds the five output
 // rows k - 4 .. k (tap row p = k - i for output row i), so its 5 x CIN/16
@@ -127,20 +127,29 @@ enum { OUT_BF16 = 0, OUT_FIELD = 1, OUT_MASKED = 2 };
 // MMA D[128 px][count x COUTP] += A[128 px][16 ch] B[16 ch][count x COUTP]
 // adds row k's contribution to every output row it reaches.  The output rows
 // accumulate in a ring of kAcc tensor-memory blocks of COUTP columns (block
-// i % kAcc), zeroed before their first contribution, so every MMA
+// i % kAcc), zero before their first contribution, so every MMA
 // accumulates; a run of blocks that wraps the ring takes two MMAs.
-//   iteration k: wait for the MMAs of input row k - 2, drain output row
-//          k - 6 (complete after input row k - 2) and zero its block, load
-//          input row k + kPref into the slot of row k + kPref - kRing
-//          (<= k - 2, already read), wait for row k, issue its MMAs, commit.
-//          The MMAs of row k - 1 run while row k - 6 is drained.
-//   waits: every mbarrier wait gives up after a.wait_limit polls (default
-//          2^24); the CTA then records the timeout in a.err, drains nothing
-//          more, waits for its copies and frees its tensor memory.
-//          a.skip_mma (a test mode) issues no MMA and no commit, so the
-//          first wait runs out with no asynchronous work in flight.
-constexpr int kPref = 2;
-constexpr int kRing = kPref + 2;
+//
+// Roles (kWsThreads = 5 warps):
+//   warp 4 (producer): loads input row k into its slot with cp.async once
+//          the MMAs of row k - kWsRing have released it (mbarrier empty),
+//          then, kWsDist rows behind, waits for its own copies of row r,
+//          waits until the block of output row r is free (mbarrier free,
+//          first contribution) and lane 0 issues row r's MMAs; one commit
+//          releases the slot, a second marks output row r - 4 complete
+//          (mbarrier full).
+//   warps 0-3 (epilogue, one tensor-memory lane quarter each): for output
+//          row i, wait for full, tcgen05.ld the block, zero it, arrive on
+//          free, then bias / ReLU / BF16 and store.
+// So a drain never sits between two rows' MMA issue.  Every mbarrier wait
+// gives up after a.wait_limit polls (default 2^24): the warp records the
+// timeout in a.err and stops; before freeing its tensor memory the CTA
+// waits (bounded) for a final commit covering every MMA it issued.
+// a.skip_mma (a test mode) issues no MMA and no commit, so the waits run
+// out with no asynchronous work in flight.
+constexpr int kWsRing = 4;
+constexpr int kWsDist = 2;
+constexpr int kWsThreads = 160;
 constexpr int kAcc = 8;
 
 // Every MMA operand window lies inside its ring slot or the weight block
@@ -150,9 +159,11 @@ template <int CIN, int COUTP>
 struct StreamSmem {
     static constexpr int kChunks = CIN / 8;
     static constexpr int kRowBytes = kChunks * kStrip * 16;
-    static constexpr int kA = kRing * kRowBytes;
+    static constexpr int kA = kWsRing * kRowBytes;
     static constexpr int kB = kTaps * kChunks * COUTP * 16;
-    static constexpr int kTotal = kA + kB + 64;
+    static constexpr int kNBar = kWsRing + 2 * kAcc + 1;     // empty[ring], full[acc], free[acc], fin
+    static constexpr int kBar = kA + kB;
+    static constexpr int kTotal = kBar + kNBar * 8 + 16;
     static constexpr int kTmemCols = kAcc * COUTP;
 };
 
@@ -174,17 +185,26 @@ __device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
         : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
 template <int CIN, int COUTP, int MODE, bool RELU>
-__global__ void __launch_bounds__(128, 2) conv_tc_stream_kernel(ConvArgs a) {
+__global__ void __launch_bounds__(kWsThreads, 2) conv_tc_stream_kernel(ConvArgs a) {
     using L = StreamSmem<CIN, COUTP>;
     static_assert(L::kTmemCols == 128 || L::kTmemCols == 256, "tensor-memory allocation");
     static_assert(COUTP % 16 == 0, "N of every MMA a multiple of 16");
+    static_assert(kWsDist < kWsRing && kAcc > 4, "pipeline depths");
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;
     unsigned char* sB = smem + L::kA;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::kA + L::kB);     // [2]
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::kA + L::kB + 16);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::kBar);
+    uint64_t* b_empty = bar;                      // [kWsRing]: the MMAs reading a slot have finished
+    uint64_t* b_full = bar + kWsRing;             // [kAcc]: an output row's accumulation has finished
+    uint64_t* b_free = b_full + kAcc;             // [kAcc]: its block is drained and zeroed (4 arrivals)
+    uint64_t* b_fin = b_free + kAcc;              // every MMA of the CTA has finished
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + L::kNBar);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int H = a.H, W = a.W, Wp = W + 4;
     // run of output rows: blockIdx.x -> (image b, column block jb, rows [r0, r1))
     const int ncb = (W + kTile - 1) / kTile;
@@ -196,7 +216,7 @@ __global__ void __launch_bounds__(128, 2) conv_tc_stream_kernel(ConvArgs a) {
     const int j0 = jb * kTile;
     const int nrow = r1 - r0, nin = nrow + 4;
     const long wait_limit = a.wait_limit > 0 ? a.wait_limit : (1L << 24);
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -204,25 +224,16 @@ __global__ void __launch_bounds__(128, 2) conv_tc_stream_kernel(ConvArgs a) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        mbar_init(smem_u32(&mbar[0]), 1);
-        mbar_init(smem_u32(&mbar[1]), 1);
+        for (int q = 0; q < L::kNBar; ++q) {
+            const bool is_free = q >= kWsRing + kAcc && q < kWsRing + 2 * kAcc;
+            mbar_init(smem_u32(&bar[q]), is_free ? 4u : 1u);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // padded input row r0 + off (off < nin) of image b -> ring slot off % kRing
-    auto load_row = [&](int off) {
-        unsigned char* dst = sA + (off % kRing) * L::kRowBytes;
-        const __nv_bfloat16* src = a.in + ((long long)b * (H + 4) + r0 + off) * Wp * CIN;
-        for (int e = tid; e < L::kChunks * kStrip; e += 128) {
-            const int px = e % kStrip, ch = e / kStrip;
-            const int col = j0 + px;
-            const bool okc = col < Wp;
-            cp_async16_zfill(dst + (ch * kStrip + px) * 16, src + (long long)(okc ? col : 0) * CIN + ch * 8, okc);
-        }
-    };
-    // weights (group 0): global [tap][ch][co] 16-byte pieces -> shared
+    // weights: global [tap][ch][co] 16-byte pieces -> shared
     // [q][ch][tap row descending][co], so the five tap rows of one (q, ch)
     // are consecutive N rows
-    for (int e = tid; e < L::kB / 16; e += 128) {
+    for (int e = tid; e < L::kB / 16; e += kWsThreads) {
         const int co = e % COUTP, rest = e / COUTP;
         const int ch = rest % L::kChunks, tap = rest / L::kChunks;
         const int p = tap / 5, q = tap - 5 * p;
@@ -230,129 +241,151 @@ __global__ void __launch_bounds__(128, 2) conv_tc_stream_kernel(ConvArgs a) {
         cp_async16_zfill(sB + dst * 16, reinterpret_cast<const unsigned char*>(a.wpk) + (long long)e * 16, true);
     }
     cp_async_commit();
-    for (int q = 0; q < kPref; ++q) {             // input rows 0 .. kPref - 1, one group each
-        if (q < nin) load_row(q);
-        cp_async_commit();
-    }
+    cp_async_wait<0>();
+    fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tslot;
-    // every accumulator block starts at zero
-    for (int c = 0; c < L::kTmemCols; c += 16) tmem_zero16(tbase + lane_base + c);
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    if (warp < 4) {                               // every accumulator block starts at zero
+        for (int c = 0; c < L::kTmemCols; c += 16) tmem_zero16(tbase + lane_base + c);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint64_t dA0 = umma_desc(smem_u32(sA), kStrip * 16, 128);
-    const uint64_t dB0 = umma_desc(smem_u32(sB), 5 * COUTP * 16, 128);
+
+    // phase `parity` of an mbarrier, polled by every lane of the warp (bounded)
+    auto wait_bar = [&](uint64_t* bb, uint32_t parity) {
+        uint32_t done = 0;
+        const uint32_t mb = smem_u32(bb);
+        for (long it = 0; it < wait_limit && !done; ++it) done = mbar_try_wait(mb, parity);
+        return __all_sync(0xffffffffu, done) != 0;
+    };
     bool ok = true;
 
-    // wait for the MMAs of input row k (commit into mbar[k % 2])
-    auto wait_commit = [&](int k) {
-        uint32_t done = 0;
-        const uint32_t mb = smem_u32(&mbar[k & 1]);
-        for (long it = 0; it < wait_limit && !done; ++it) done = mbar_try_wait(mb, (uint32_t)((k >> 1) & 1));
-        done = __syncthreads_and(done);
-        if (!done && tid == 0 && a.err) atomicExch(a.err, 1);
-        return done != 0;
-    };
-    // drain output row i (relative to r0) from block i % kAcc, then zero it
-    auto drain = [&](int i) {
-        tc_fence_after();
-        const int m = warp * 32 + (tid & 31);
+    if (warp == 4) {
+        // ---- producer: loads and MMA issue
+        auto load_row = [&](int off) {            // padded input row r0 + off -> its slot
+            unsigned char* dst = sA + (off % kWsRing) * L::kRowBytes;
+            const __nv_bfloat16* src = a.in + ((long long)b * (H + 4) + r0 + off) * Wp * CIN;
+            for (int e = lane; e < L::kChunks * kStrip; e += 32) {
+                const int px = e % kStrip, ch = e / kStrip;
+                const int col = j0 + px;
+                const bool okc = col < Wp;
+                cp_async16_zfill(dst + (ch * kStrip + px) * 16, src + (long long)(okc ? col : 0) * CIN + ch * 8, okc);
+            }
+        };
+        const uint64_t dA0 = umma_desc(smem_u32(sA), kStrip * 16, 128);
+        const uint64_t dB0 = umma_desc(smem_u32(sB), 5 * COUTP * 16, 128);
+        for (int k = 0; k < nin + kWsDist; ++k) {
+            if (k < nin) {
+                if (k >= kWsRing) {               // the MMAs of input row k - kWsRing have read the slot
+                    ok = wait_bar(&b_empty[k % kWsRing], (uint32_t)(((k / kWsRing) - 1) & 1));
+                    if (!ok) break;
+                }
+                load_row(k);
+            }
+            cp_async_commit();                    // one group per k (possibly empty)
+            const int r = k - kWsDist;
+            if (r < 0) continue;
+            cp_async_wait<kWsDist>();             // this lane's copies of input row r have landed
+            fence_async_smem();
+            __syncwarp();
+            if (r < nrow && r >= kAcc) {          // first contribution to output row r: block drained
+                ok = wait_bar(&b_free[r % kAcc], (uint32_t)(((r / kAcc) - 1) & 1));
+                if (!ok) break;
+            }
+            tc_fence_after();
+            if (lane == 0 && !a.skip_mma) {
+                // output rows lo .. hi receive input row r (tap row r - i)
+                const int lo = max(r - 4, 0), hi = min(r, nrow - 1);
+                if (lo <= hi) {
+                    const uint64_t darow = dA0 + (uint64_t)(((r % kWsRing) * L::kRowBytes) >> 4);
+                    // split the block run lo % kAcc .. hi % kAcc where it wraps
+                    const int s0 = lo, n0 = min(hi - lo + 1, kAcc - lo % kAcc);
+                    const int s1 = lo + n0, n1 = hi - lo + 1 - n0;
+#pragma unroll
+                    for (int seg = 0; seg < 2; ++seg) {
+                        const int st = seg == 0 ? s0 : s1, cnt = seg == 0 ? n0 : n1;
+                        if (cnt <= 0) continue;
+                        const uint32_t dacc = tbase + (uint32_t)((st % kAcc) * COUTP);
+                        const uint32_t idesc = umma_idesc(kTile, cnt * COUTP);
+                        const int brow = (4 - (r - st)) * COUTP;      // first weight row: tap row r - st
+#pragma unroll
+                        for (int q = 0; q < 5; ++q)
+#pragma unroll
+                            for (int kk = 0; kk < CIN / 16; ++kk) {
+                                const uint64_t da = darow + (uint64_t)((2 * kk) * kStrip + q);
+                                const uint64_t db =
+                                    dB0 + (uint64_t)((q * L::kChunks + 2 * kk) * 5 * COUTP + brow);
+                                umma_f16(dacc, da, db, idesc, 1u);
+                            }
+                    }
+                }
+                umma_commit(smem_u32(&b_empty[r % kWsRing]));
+                if (r - 4 >= 0 && r - 4 < nrow) umma_commit(smem_u32(&b_full[(r - 4) % kAcc]));
+            }
+            __syncwarp();
+        }
+        cp_async_wait<0>();
+        if (lane == 0 && !a.skip_mma) umma_commit(smem_u32(b_fin));   // after every MMA issued above
+    } else {
+        // ---- epilogue: output rows in order, lane quarter `warp` of each block
+        const int m = warp * 32 + lane;
         const int j = j0 + m;
-        const uint32_t col = (uint32_t)((i % kAcc) * COUTP);
-        float v[COUTP];
-        tmem_ld<COUTP>(tbase + lane_base + col, v);
-#pragma unroll
-        for (int c = 0; c < COUTP; c += 16) tmem_zero16(tbase + lane_base + col + c);
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        tc_fence_before();
-        const int row = r0 + i;
-        if (j < W) {
-            if (a.bias)
-#pragma unroll
-                for (int c = 0; c < COUTP; ++c) v[c] += a.bias[c];
-            if (RELU)
-#pragma unroll
-                for (int c = 0; c < COUTP; ++c) v[c] = fmaxf(v[c], 0.f);
-            if (MODE == OUT_FIELD) {
-                float* o = reinterpret_cast<float*>(a.out) + (((long long)b * H + row) * W + j) * 3;
-                o[0] = v[0] * a.out_scale;
-                o[1] = v[1] * a.out_scale;
-                o[2] = v[2] * a.out_scale;
-            } else {
-                const long long pix = ((long long)b * (H + 4) + row + 2) * Wp + j + 2;
-                if (MODE == OUT_MASKED) {
-                    const __nv_bfloat16* mk = a.mask + pix * COUTP;
-#pragma unroll
-                    for (int c = 0; c < COUTP; ++c)
-                        if (!(__bfloat162float(mk[c]) > 0.f)) v[c] = 0.f;
-                }
-                __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(a.out) + pix * COUTP;
-#pragma unroll
-                for (int c = 0; c < COUTP; c += 8) {
-                    uint4 pk;
-                    __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(&pk);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) h2[e] = __floats2bfloat162_rn(v[c + 2 * e], v[c + 2 * e + 1]);
-                    *reinterpret_cast<uint4*>(o + c) = pk;
-                }
-            }
-        }
-    };
-
-    for (int k = 0; k < nin && ok; ++k) {
-        if (k >= 2) {
-            ok = wait_commit(k - 2);              // input rows <= k - 2 consumed
+        for (int i = 0; i < nrow; ++i) {
+            const int blk = i % kAcc;
+            ok = wait_bar(&b_full[blk], (uint32_t)((i / kAcc) & 1));
             if (!ok) break;
-            if (k - 6 >= 0) drain(k - 6);         // output row k - 6: last input row k - 2
-        }
-        if (k + kPref < nin) load_row(k + kPref); // slot of row k + kPref - kRing = k - 2
-        cp_async_commit();
-        cp_async_wait<kPref>();                   // input row k has landed
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (tid == 0 && !a.skip_mma) {
-            // output rows lo .. hi receive input row k (tap row k - i)
-            const int lo = max(k - 4, 0), hi = min(k, nrow - 1);
-            if (lo <= hi) {
-                const uint64_t darow = dA0 + (uint64_t)(((k % kRing) * L::kRowBytes) >> 4);
-                // split the block run lo % kAcc .. hi % kAcc where it wraps
-                const int s0 = lo, n0 = min(hi - lo + 1, kAcc - lo % kAcc);
-                const int s1 = lo + n0, n1 = hi - lo + 1 - n0;
+            tc_fence_after();
+            const uint32_t col = (uint32_t)(blk * COUTP);
+            float v[COUTP];
+            tmem_ld<COUTP>(tbase + lane_base + col, v);
 #pragma unroll
-                for (int seg = 0; seg < 2; ++seg) {
-                    const int st = seg == 0 ? s0 : s1, cnt = seg == 0 ? n0 : n1;
-                    if (cnt <= 0) continue;
-                    const uint32_t dacc = tbase + (uint32_t)((st % kAcc) * COUTP);
-                    const uint32_t idesc = umma_idesc(kTile, cnt * COUTP);
-                    const int brow = (4 - (k - st)) * COUTP;      // first weight row: tap row k - st
+            for (int c = 0; c < COUTP; c += 16) tmem_zero16(tbase + lane_base + col + c);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&b_free[blk]));
+            const int row = r0 + i;
+            if (j < W) {
+                if (a.bias)
 #pragma unroll
-                    for (int q = 0; q < 5; ++q)
+                    for (int c = 0; c < COUTP; ++c) v[c] += a.bias[c];
+                if (RELU)
 #pragma unroll
-                        for (int kk = 0; kk < CIN / 16; ++kk) {
-                            const uint64_t da = darow + (uint64_t)((2 * kk) * kStrip + q);
-                            const uint64_t db =
-                                dB0 + (uint64_t)((q * L::kChunks + 2 * kk) * 5 * COUTP + brow);
-                            umma_f16(dacc, da, db, idesc, 1u);
-                        }
+                    for (int c = 0; c < COUTP; ++c) v[c] = fmaxf(v[c], 0.f);
+                if (MODE == OUT_FIELD) {
+                    float* o = reinterpret_cast<float*>(a.out) + (((long long)b * H + row) * W + j) * 3;
+                    o[0] = v[0] * a.out_scale;
+                    o[1] = v[1] * a.out_scale;
+                    o[2] = v[2] * a.out_scale;
+                } else {
+                    const long long pix = ((long long)b * (H + 4) + row + 2) * Wp + j + 2;
+                    if (MODE == OUT_MASKED) {
+                        const __nv_bfloat16* mk = a.mask + pix * COUTP;
+#pragma unroll
+                        for (int c = 0; c < COUTP; ++c)
+                            if (!(__bfloat162float(mk[c]) > 0.f)) v[c] = 0.f;
+                    }
+                    __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(a.out) + pix * COUTP;
+#pragma unroll
+                    for (int c = 0; c < COUTP; c += 8) {
+                        uint4 pk;
+                        __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(&pk);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) h2[e] = __floats2bfloat162_rn(v[c + 2 * e], v[c + 2 * e + 1]);
+                        *reinterpret_cast<uint4*>(o + c) = pk;
+                    }
                 }
             }
-            umma_commit(smem_u32(&mbar[k & 1]));
         }
     }
-    // the loop drained output rows 0 .. nrow - 3 (row k - 6 at input row
-    // k <= nin - 1); the last two are complete after the last input row
-    if (ok) {
-        ok = wait_commit(nin - 1);
-        if (ok)
-            for (int i = max(0, nrow - 2); i < nrow; ++i) drain(i);
-    }
-    cp_async_wait<0>();
+    if (!ok && lane == 0 && a.err) atomicExch(a.err, 1);
+    // every MMA has finished before the tensor memory goes (bounded wait;
+    // with skip_mma nothing was issued)
+    if (!a.skip_mma) wait_bar(b_fin, 0u);
     tc_fence_before();
     __syncthreads();
     if (warp == 0)
@@ -825,7 +858,7 @@ static cudaError_t launch_conv_stream(ConvArgs a, int B, cudaStream_t s) {
     a.rows_per_run = stream_rows_per_run(B, a.H, a.W);
     const int runs = (a.H + a.rows_per_run - 1) / a.rows_per_run;
     const int grid = B * ((a.W + kTile - 1) / kTile) * runs;
-    conv_tc_stream_kernel<CIN, COUTP, MODE, RELU><<<grid, 128, L::kTotal, s>>>(a);
+    conv_tc_stream_kernel<CIN, COUTP, MODE, RELU><<<grid, kWsThreads, L::kTotal, s>>>(a);
     return cudaGetLastError();
 }
 
