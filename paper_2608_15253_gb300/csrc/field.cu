@@ -429,11 +429,10 @@ void field_launch(mm_ctx* c, int mode, unsigned terms, const void* m, const void
 // Inverse X pass + field kernel in one launch (FP32, one material, nx a
 // multiple of 4 dividing 1024, the one-row-per-warp inverse X transform of
 // the grid's half length available).  Measured against the two separate
-// kernels: 37.6 against 18.2 + 22.4 us per 256x256x16 evaluation, but 430
-// against 204 + 215 us at nx = 512 (two 8-warp CTAs per SM leave the
-// transform and field phases of a CTA unoverlapped), so rows of 512 keep
-// the separate kernels.
-#define MM_C2R_FIELD_LENGTHS(X) X(128) X(256)
+// kernels: 37.6 against 18.2 + 22.4 us per 256x256x16 evaluation; at
+// nx = 512 with the QUIET field variant 385 against 198 + 201 us (the
+// general field variant had made it slower there: 430 against 204 + 215).
+#define MM_C2R_FIELD_LENGTHS(X) X(128) X(256) X(512)
 
 bool field_c2r_fusable(const mm_ctx* c) {
     const mm_grid& g = c->grid;
