@@ -530,16 +530,19 @@ __global__ void dweight_kernel(const __nv_bfloat16* __restrict__ dz, int CZ, int
 // whole kernel: M = 128 rows of (copy, channel) (copies 0..3 then 4..7 when
 // X has 32 channels, 0..7 when it has 16), N = 5 dZ rows x CZ channels.
 // Copy 5 is all ones, so its rows collect the bias gradient; copies 6 and 7
-// are zero.  dZ rows sit in a ring of 6 slots (a window that wraps takes two
-// MMAs); the row copies are double buffered: row R's MMAs are issued, then
-// the CTA waits for row R - 1's and loads the copies of row R + 1 (and dZ row
-// R + 3) into the buffers row R - 1 used.
+// are not stored (their operand rows read on into the next buffer, and
+// their rows of D are never used).  dZ rows sit in a ring of 7 slots (a
+// window that wraps takes two MMAs); the row copies are triple buffered:
+// row R's MMAs are issued, then the CTA waits for row R - 1's and loads the
+// copies of row R + 2 (and dZ row R + 4) into what row R - 1 used, so every
+// load has two rows' worth of MMAs to land behind.
 //
 // A CTA takes a contiguous share of all (image, 128-pixel column block,
 // padded input row) triples, one per SM; at the end it writes its partial
 // sums, and a second kernel adds them over CTAs in a fixed order.
-constexpr int kWgCopies = 8;
-constexpr int kWgRing = 6;
+constexpr int kWgCopies = 6;                // stored copies per buffer (0..4 shifted, 5 ones)
+constexpr int kWgBufs = 3;
+constexpr int kWgRing = 7;
 constexpr int kWgPlane = kTile * 16;        // one 8-channel group of 128 pixels
 
 template <int CX, int CZ>
@@ -551,7 +554,7 @@ struct WgSmem {
     static constexpr int kN = 5 * CZ;
     static constexpr int kUsedCols = kMmas * kN;
     static constexpr int kCols = kUsedCols <= 256 ? 256 : 512;
-    static constexpr int kBar = 2 * kA + kWgRing * kSlot;
+    static constexpr int kBar = kWgBufs * kA + kWgRing * kSlot;
     // 8 KB past the barriers: every operand window stays inside the
     // allocation whichever way the descriptor strides were read
     static constexpr int kTotal = kBar + 64 + 8192;
@@ -576,9 +579,11 @@ __global__ void __launch_bounds__(128, 1) dweight_tc_kernel(WgArgs a) {
     using L = WgSmem<CX, CZ>;
     static_assert(L::kPartFloats <= kWgPartFloats, "partial-sum block");
     static_assert(L::kUsedCols % 16 == 0, "tensor-memory columns");
+    static_assert(kWgRing * L::kSlot >= 2 * L::kCopyBytes, "copies 6, 7 of the last buffer read into the ring");
+    static_assert(L::kTotal <= 227 * 1024, "shared memory");
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;                         // [2][copy][CX/8][128 px][16 B]
-    unsigned char* sZ = smem + 2 * L::kA;             // [slot][CZ/8][128 px][16 B]
+    unsigned char* sZ = smem + kWgBufs * L::kA;       // [slot][CZ/8][128 px][16 B]
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::kBar);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::kBar + 16);
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -599,13 +604,11 @@ __global__ void __launch_bounds__(128, 1) dweight_tc_kernel(WgArgs a) {
         mbar_init(smem_u32(&mbar[1]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // constant copies of both buffers: 5 = ones (bf16 1.0 = 0x3F80), 6, 7 = zero
-    for (int e = tid; e < 2 * 3 * (L::kCopyBytes / 16); e += 128) {
-        const int per = 3 * (L::kCopyBytes / 16);
-        const int buf = e / per, rest = e % per;
-        const int cp = 5 + rest / (L::kCopyBytes / 16), off = rest % (L::kCopyBytes / 16);
-        const uint32_t w = cp == 5 ? 0x3F803F80u : 0u;
-        *reinterpret_cast<uint4*>(sA + buf * L::kA + cp * L::kCopyBytes + off * 16) = make_uint4(w, w, w, w);
+    // copy 5 of every buffer: ones (bf16 1.0 = 0x3F80)
+    for (int e = tid; e < kWgBufs * (L::kCopyBytes / 16); e += 128) {
+        const int buf = e / (L::kCopyBytes / 16), off = e % (L::kCopyBytes / 16);
+        const uint32_t w = 0x3F803F80u;
+        *reinterpret_cast<uint4*>(sA + buf * L::kA + 5 * L::kCopyBytes + off * 16) = make_uint4(w, w, w, w);
     }
     fence_async_smem();
     tc_fence_before();
@@ -665,12 +668,19 @@ __global__ void __launch_bounds__(128, 1) dweight_tc_kernel(WgArgs a) {
         const int n = left < (long long)(Hp - t0) ? (int)left : Hp - t0;
         const int b = (int)(u / ncb), j0 = (int)(u % ncb) * kTile;
         const int Rs = t0 - 2;                        // first input row (interior numbering)
-        // every earlier MMA has finished: dZ rows Rs - 2 .. Rs + 2 -> slots 0..4
+        // every earlier MMA has finished: dZ rows Rs - 2 .. Rs + 2 -> slots
+        // 0..4 with the copies of row Rs (one group), dZ row Rs + 3 with
+        // those of row Rs + 1 (a second group, empty for a one-row share)
         for (int r = 0; r < 5; ++r) load_z(b, Rs - 2 + r, j0, r);
-        load_x((int)(it & 1), b, Rs + 2, j0);
+        load_x((int)(it % kWgBufs), b, Rs + 2, j0);
+        cp_async_commit();
+        if (n > 1) {
+            load_z(b, Rs + 3, j0, 5);
+            load_x((int)((it + 1) % kWgBufs), b, Rs + 3, j0);
+        }
         cp_async_commit();
         for (int jj = 0; jj < n; ++jj, ++it) {
-            cp_async_wait<0>();                       // row Rs + jj and its dZ rows have landed
+            cp_async_wait<1>();                       // row Rs + jj and its dZ rows have landed
             fence_async_smem();
             tc_fence_before();
             __syncthreads();
@@ -680,7 +690,8 @@ __global__ void __launch_bounds__(128, 1) dweight_tc_kernel(WgArgs a) {
                 const int n0 = min(5, kWgRing - s0);
 #pragma unroll
                 for (int g = 0; g < L::kMmas; ++g) {
-                    const uint64_t da = dA0 + (uint64_t)(((int)(it & 1) * L::kA + g * 4 * L::kCopyBytes) >> 4);
+                    const uint64_t da =
+                        dA0 + (uint64_t)(((int)(it % kWgBufs) * L::kA + g * 4 * L::kCopyBytes) >> 4);
 #pragma unroll
                     for (int seg = 0; seg < 2; ++seg) {
                         const int cnt = seg == 0 ? n0 : 5 - n0;
@@ -700,12 +711,12 @@ __global__ void __launch_bounds__(128, 1) dweight_tc_kernel(WgArgs a) {
                 ok = wait_commit(it - 1);             // buffers of row R - 1 are free
                 if (!ok) break;
             }
-            if (jj + 1 < n) {
+            if (jj + 2 < n) {
                 const int R = Rs + jj;
-                load_x((int)((it + 1) & 1), b, R + 3, j0);     // padded row of input row R + 1
-                load_z(b, R + 3, j0, (jj + 5) % kWgRing);      // replaces dZ row R - 3
-                cp_async_commit();
+                load_x((int)((it + 2) % kWgBufs), b, R + 4, j0);   // padded row of input row R + 2
+                load_z(b, R + 4, j0, (jj + 6) % kWgRing);          // replaces dZ row R - 3
             }
+            cp_async_commit();                                    // one group per row (possibly empty)
         }
         if (ok) ok = wait_commit(it - 1);             // buffers free for the next share
         f += n;
@@ -738,23 +749,32 @@ __global__ void __launch_bounds__(128, 1) dweight_tc_kernel(WgArgs a) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"((uint32_t)L::kCols));
 }
 
-// dW (+)= sum over CTAs of the partial sums, in CTA order
+// dW (+)= sum over CTAs of the partial sums.  A block takes 32 consecutive
+// elements; its 8 warps each add every 8th CTA's partials (warp g: CTAs
+// g, g + 8, ...) and the 8 sums are added in warp order, so the result does
+// not depend on timing.
 template <int CX, int CZ>
-__global__ void dweight_reduce_kernel(const float* __restrict__ part, int nparts, int cout, int cin,
-                                      float* __restrict__ dw, float* __restrict__ db) {
+__global__ void __launch_bounds__(256) dweight_reduce_kernel(const float* __restrict__ part, int nparts, int cout,
+                                                             int cin, float* __restrict__ dw, float* __restrict__ db) {
+    __shared__ float red[8][33];
     const int n = WgSmem<CX, CZ>::kPartFloats;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    int c = 0;
-    for (; c + 4 <= nparts; c += 4) {
-        s0 += part[(long long)c * kWgPartFloats + i];
-        s1 += part[(long long)(c + 1) * kWgPartFloats + i];
-        s2 += part[(long long)(c + 2) * kWgPartFloats + i];
-        s3 += part[(long long)(c + 3) * kWgPartFloats + i];
+    const int e = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + e;
+    float s0 = 0.f, s1 = 0.f;
+    if (i < n) {
+        int c = g;
+        for (; c + 8 < nparts; c += 16) {
+            s0 += part[(long long)c * kWgPartFloats + i];
+            s1 += part[(long long)(c + 8) * kWgPartFloats + i];
+        }
+        if (c < nparts) s0 += part[(long long)c * kWgPartFloats + i];
     }
-    for (; c < nparts; ++c) s0 += part[(long long)c * kWgPartFloats + i];
-    const float s = (s0 + s1) + (s2 + s3);
+    red[g][e] = s0 + s1;
+    __syncthreads();
+    if (g != 0 || i >= n) return;
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s += red[q][e];
     if (i < 25 * CZ * CX) {
         const int ci = i % CX, co = (i / CX) % CZ, tap = i / (CX * CZ);   // tap = ty * 5 + tx
         if (co < cout && ci < cin) dw[(co * cin + ci) * 25 + tap] += s;
@@ -916,7 +936,7 @@ static cudaError_t launch_dweight_tc(cudaStream_t s, const __nv_bfloat16* dz, in
     const int grid = (int)std::min<long long>(cnn_dweight_parts(), F);
     WgArgs a{dz, x, part, B, H, W, err, 0};
     dweight_tc_kernel<CX, CZ><<<grid, 128, L::kTotal, s>>>(a);
-    dweight_reduce_kernel<CX, CZ><<<(L::kPartFloats + 255) / 256, 256, 0, s>>>(part, grid, cout, cin, dw, db);
+    dweight_reduce_kernel<CX, CZ><<<(L::kPartFloats + 31) / 32, 256, 0, s>>>(part, grid, cout, cin, dw, db);
     return cudaGetLastError();
 }
 
