@@ -156,3 +156,61 @@ def test_block_average_equals_the_prism_demagnetising_factors(shape, cell):
     a, b, c = nx * cell[0] / 2, ny * cell[1] / 2, nz * cell[2] / 2
     ref = [_aharoni_prism_factor(b, c, a), _aharoni_prism_factor(c, a, b), _aharoni_prism_factor(a, b, c)]
     assert np.allclose(mean, ref, rtol=1e-12, atol=1e-14)
+
+
+def _asymptotic_newell():
+    """Far-field expansion of the cell-averaged tensor, written from the
+    mathematics alone: N_ab(R) = -(V / 4 pi) < d_a d_b 1/|R + w| >, with w the
+    difference of two independent uniform points of the cell (per axis a
+    triangular variable: <w^2> = h^2 / 6, <w^4> = h^4 / 15), expanded to
+    fourth order:
+      f + sum_d h_d^2 / 12 d_d^2 f + sum_d h_d^4 / 360 d_d^4 f
+        + sum_{d<e} h_d^2 h_e^2 / 144 d_d^2 d_e^2 f,   f = d_a d_b 1/R.
+    The omitted sixth-order terms are O((h / R)^6) relative."""
+    sp = pytest.importorskip("sympy")
+    X, Y, Z = sp.symbols("X Y Z", real=True)
+    g = 1 / sp.sqrt(X ** 2 + Y ** 2 + Z ** 2)
+    ax = [X, Y, Z]
+    fns = []
+    for a, b in [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]:
+        f = sp.diff(g, ax[a], ax[b])
+        exprs = [f] + [sp.diff(f, ax[d], 2) for d in range(3)] + [sp.diff(f, ax[d], 4) for d in range(3)] + \
+                [sp.diff(f, ax[d], 2, ax[e], 2) for d, e in [(0, 1), (0, 2), (1, 2)]]
+        fns.append(sp.lambdify((X, Y, Z), exprs, "numpy"))
+
+    def at(ijk, h):
+        R = np.asarray(ijk, float) * np.asarray(h, float)
+        V = h[0] * h[1] * h[2]
+        out = []
+        for fn in fns:
+            v = fn(*R)
+            s = v[0] + sum(h[d] ** 2 / 12 * v[1 + d] for d in range(3)) + \
+                sum(h[d] ** 4 / 360 * v[4 + d] for d in range(3))
+            s += h[0] ** 2 * h[1] ** 2 / 144 * v[7] + h[0] ** 2 * h[2] ** 2 / 144 * v[8] + \
+                h[1] ** 2 * h[2] ** 2 / 144 * v[9]
+            out.append(-V / (4 * math.pi) * s)
+        return np.array(out)
+    return at
+
+
+@pytest.mark.parametrize("cell", [(2.0, 2.0, 1.0), (3.0, 3.0, 3.0), (3.90625, 3.90625, 3.0)])
+def test_every_band_agrees_with_the_fourth_order_far_field_expansion(cell):
+    """Every distance band of the tensor evaluation -- the closed form near
+    the source and each Gauss quadrature order further out, the 3-point band
+    beyond 128 cells included -- against the fourth-order expansion of the
+    cell average of the point-dipole kernel: the difference must shrink like
+    (h / R)^6 down to rounding, at the displacements the demag grids use
+    (up to 511 x 511 x 63 cells)."""
+    asym = _asymptotic_newell()
+    hmax = max(cell)
+    dirs = [(1, 0, 0), (1, 1, 0), (0.3, 0.7, 0.2), (2, -1, 3), (-5, 4, 1)]
+    for R in (10, 16, 24, 40, 64, 100, 130, 200, 400, 700):
+        for dv in dirs:
+            u = np.array(dv, float) / np.linalg.norm(dv)
+            ijk = np.round(u * R).astype(int)
+            ijk = np.clip(ijk, -511, 511)
+            N = newell_at([ijk], cell)[0]
+            A = asym(ijk, cell)
+            rel = np.max(np.abs(N - A)) / np.max(np.abs(A))
+            dist = np.linalg.norm(ijk * np.asarray(cell)) / hmax
+            assert rel <= (1.0 / dist) ** 6 + 1e-13, (cell, tuple(ijk), rel)
