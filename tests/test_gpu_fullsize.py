@@ -186,6 +186,51 @@ def test_newell_entries_at_the_largest_displacements():
     assert np.all(np.abs(g - o) <= 1e-11 * scale + 1e-18)
 
 
+def _far_field_second_order(ijk, h):
+    """-(V/4 pi) [d_a d_b 1/R + sum_d h_d^2/12 d_d^2 d_a d_b 1/R]: the cell
+    average of the point-dipole kernel to second order (the moments of the
+    difference of two uniform points per axis), from the closed forms of the
+    second and fourth derivatives of 1/R; relative error O((h/R)^4)."""
+    x = np.asarray(ijk, float) * np.asarray(h, float)
+    R2 = float(x @ x)
+    R = np.sqrt(R2)
+    V = h[0] * h[1] * h[2]
+    dlt = np.eye(3)
+
+    def t2(i, j):
+        return 3 * x[i] * x[j] / R ** 5 - dlt[i, j] / R ** 3
+
+    def t4(i, j, k, l):
+        xs = x
+        return (105 * xs[i] * xs[j] * xs[k] * xs[l] / R ** 9
+                - 15 * (dlt[i, j] * xs[k] * xs[l] + dlt[i, k] * xs[j] * xs[l] + dlt[i, l] * xs[j] * xs[k]
+                        + dlt[j, k] * xs[i] * xs[l] + dlt[j, l] * xs[i] * xs[k] + dlt[k, l] * xs[i] * xs[j]) / R ** 7
+                + 3 * (dlt[i, j] * dlt[k, l] + dlt[i, k] * dlt[j, l] + dlt[i, l] * dlt[j, k]) / R ** 5)
+
+    out = []
+    for a, b in [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]:
+        s = t2(a, b) + sum(h[d] ** 2 / 12.0 * t4(a, b, d, d) for d in range(3))
+        out.append(-V / (4 * np.pi) * s)
+    return np.array(out)
+
+
+def test_newell_far_band_against_the_far_field_expansion():
+    """The GPU's FP64 Newell entries beyond 128 cells (its 3-point quadrature
+    band) against the second-order far-field expansion of the cell-averaged
+    dipole kernel -- a check that does not go through the oracle: the
+    difference must stay within (h/R)^4 (the expansion's own truncation)."""
+    mm = need_gpu()
+    for h in [(3e-9, 3e-9, 3e-9), (2e-9, 2e-9, 1e-9), (3.90625e-9, 3.90625e-9, 3e-9)]:
+        ijk = np.array([[511, 511, 63], [511, 0, 0], [0, 511, 0], [300, 200, 40], [140, 0, 0], [0, 135, 20],
+                        [-200, 150, -10], [130, 60, 63]], dtype=np.int32)
+        g = mm.mm_newell(ijk, h)
+        for q in range(ijk.shape[0]):
+            A = _far_field_second_order(ijk[q], h)
+            dist = np.linalg.norm(ijk[q] * np.asarray(h)) / max(h)
+            rel = np.abs(g[q] - A).max() / np.abs(A).max()
+            assert rel <= 2.0 / dist ** 4, (h, tuple(ijk[q]), rel)
+
+
 def test_skyrmion_film_512x512_replay_fp32():
     """The 512x512x1 DMI film (the surrogate workload's exact path: one-row-per-
     warp X passes, stage combine fused into them) against the oracle."""
