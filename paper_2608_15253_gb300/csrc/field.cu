@@ -260,19 +260,23 @@ __global__ void __launch_bounds__(256) field_vec_kernel(FieldArgs<float> a) {
 }
 
 // The last demag pass (inverse X, half spectrum -> real rows) fused with
-// the field kernel: a CTA of 8 warps takes 1024 / nx rows (z, y); its warps
-// transform the three components of those rows (one row of one component
-// per warp at a time) into shared memory, then every thread forms the
-// field, torque and stage output of 4 cells with the demag field read from
-// there -- H_demag never goes through global memory.
+// the field kernel: a CTA of 8 warps takes kC2RRows = 8 rows (z, y); its
+// warps transform the three components of those rows (one row of one
+// component per warp at a time, three each) into shared memory, then every
+// thread forms the field, torque and stage output of 4 cells at a time with
+// the demag field read from there -- H_demag never goes through global
+// memory.
 struct C2RSpec {
     const float2* spec;     // [3][nz][PyA][Wk]
     const float2* tw;       // exp(-2 pi i q / Px)
     int PyA, Wk;
 };
 
+constexpr int kC2RRows = 8;
 template <int LT>
-constexpr size_t c2r_field_smem() { return (size_t)8 * wline(LT) * sizeof(float2) + 3 * 1024 * sizeof(float); }
+constexpr size_t c2r_field_smem() {
+    return (size_t)8 * wline(LT) * sizeof(float2) + (size_t)3 * kC2RRows * LT * sizeof(float);
+}
 
 template <int LT, bool EXT, bool QUIET = false>
 __global__ void __launch_bounds__(256) c2r_field_kernel(FieldArgs<float> a, C2RSpec s) {
@@ -281,7 +285,7 @@ __global__ void __launch_bounds__(256) c2r_field_kernel(FieldArgs<float> a, C2RS
     const int warp = threadIdx.x >> 5;
     float2* line = reinterpret_cast<float2*>(smem_raw) + warp * wline(LT);
     float* sH = reinterpret_cast<float*>(smem_raw + (size_t)8 * wline(LT) * sizeof(float2));   // [rpc][3][nx]
-    const int nx = a.nx, rpc = 1024 / nx, nrows = a.ny * a.nz;
+    const int nx = a.nx, rpc = kC2RRows, nrows = a.ny * a.nz;
     const int row0 = blockIdx.x * rpc;
     for (int task = warp; task < 3 * rpc; task += 8) {
         const int rl = task / 3, comp = task - 3 * rl, row = row0 + rl;
@@ -296,11 +300,13 @@ __global__ void __launch_bounds__(256) c2r_field_kernel(FieldArgs<float> a, C2RS
     }
     __syncthreads();
     const int tpr = nx / 4;
-    const int rl = threadIdx.x / tpr, x0 = 4 * (threadIdx.x - rl * tpr);
-    const int row = row0 + rl;
-    if (rl < rpc && row < nrows) {
-        const int z = row / a.ny, y = row - z * a.ny;
-        field_vec_cells<4, EXT, true, QUIET>(a, x0, y, z, sH + rl * 3 * nx + x0, nx);
+    for (int c = threadIdx.x; c < rpc * tpr; c += 256) {
+        const int rl = c / tpr, x0 = 4 * (c - rl * tpr);
+        const int row = row0 + rl;
+        if (row < nrows) {
+            const int z = row / a.ny, y = row - z * a.ny;
+            field_vec_cells<4, EXT, true, QUIET>(a, x0, y, z, sH + rl * 3 * nx + x0, nx);
+        }
     }
 }
 
@@ -469,7 +475,7 @@ void field_c2r_launch(mm_ctx* c, int mode, unsigned terms, const void* m, void* 
                                            (const float*)m0, (const float*)k1, step_override, gate, kstage);
     const DemagPlan& d = c->dm;
     C2RSpec sp{(const float2*)d.spec, (const float2*)d.tw_x, d.PyA, d.Wk};
-    const int rpc = 1024 / c->grid.nx;
+    const int rpc = kC2RRows;
     const long long rows = (long long)c->grid.ny * c->grid.nz;
     const unsigned grid = (unsigned)((rows + rpc - 1) / rpc);
     const double bytes = field_bytes(c, mode, terms, false) + 3.0 * rows * (d.Kx * sizeof(float2));
