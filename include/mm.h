@@ -223,8 +223,13 @@ MM_API mm_status mm_set_stream(mm_ctx* ctx, void* stream);
  * float64, 3N, layout [component][z][y][x]).  Page-locked host memory is read / written in place
  * by the conversion kernel (one pass over the host link); pageable memory
  * goes through a device staging buffer (3N doubles, allocated on first use
- * and kept).  Input is renormalised per cell; absent cells and zero vectors
- * are set to zero.  Both calls
+ * and kept).  Input is renormalised per cell unless its length is already
+ * 1 to within a few units in the last place of the context's precision
+ * (|m|^2 - 1 within 4.8e-7 in FP32, 8.9e-16 in FP64), in which case it is
+ * taken as it is; absent cells and zero vectors are set to zero.  A state
+ * read with mm_get_m and written back unchanged is therefore the same bit
+ * for bit, and mm_set_m then keeps the integrator's first-same-as-last
+ * slope (any changed cell discards it).  Both calls
  * return after the copy has completed (they synchronise the context
  * stream).  Errors: MM_ERR_ARG (bad replica, NULL m), MM_ERR_OOM, MM_ERR_CUDA. */
 MM_API mm_status mm_set_m(mm_ctx* ctx, int replica, const double* m);

@@ -243,7 +243,7 @@ static void free_all(mm_ctx* c) {
     c->batch = nullptr;
     surrogate_free(c);
     void* bufs[] = {c->d_region, c->d_lut, c->d_cpair, c->d_m, c->d_mtmp, c->d_kslot, c->d_hd, c->d_hbuf,
-                    c->d_bcell, c->d_state, c->d_replay, c->d_red, c->d_stage, c->d_strain};
+                    c->d_bcell, c->d_state, c->d_replay, c->d_red, c->d_stage, c->d_strain, c->d_flag};
     for (void* b : bufs) cudaFree(b);
     for (auto& k : c->d_k) cudaFree(k);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -297,15 +297,31 @@ static void host_to_state(const double* m, long long N, const std::vector<uint8_
 // working precision; absent cells (Ms = 0) and zero vectors become 0.
 template <typename T>
 __global__ void state_in_kernel(const double* __restrict__ src, long long N, const uint8_t* __restrict__ region,
-                                const Region<T>* __restrict__ lut, T* __restrict__ dst) {
+                                const Region<T>* __restrict__ lut, T* __restrict__ dst, int* __restrict__ changed) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     const bool present = region ? lut[region[i]].present != (T)0 : true;
     double x = src[i], y = src[N + i], z = src[2 * N + i];
-    const double n = sqrt(x * x + y * y + z * z);
-    if (!present || n == 0.0) x = y = z = 0.0;
-    else { x /= n; y /= n; z /= n; }
-    dst[i] = (T)x; dst[N + i] = (T)y; dst[2 * N + i] = (T)z;
+    const double n2 = x * x + y * y + z * z;
+    // unit to within a few units in the last place of T: taken as it is
+    // (a state read back and written again stays bit for bit the same)
+    const double tol = sizeof(T) == 4 ? 4.8e-7 : 8.9e-16;
+    if (!present || n2 == 0.0) {
+        x = y = z = 0.0;
+    } else if (fabs(n2 - 1.0) > tol) {
+        const double n = sqrt(n2);
+        x /= n; y /= n; z /= n;
+    }
+    const T v[3] = {(T)x, (T)y, (T)z};
+    bool diff = false;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const T old = dst[c * N + i];
+        if (sizeof(T) == 4) diff = diff || __float_as_uint((float)old) != __float_as_uint((float)v[c]);
+        else diff = diff || __double_as_longlong((double)old) != __double_as_longlong((double)v[c]);
+        dst[c * N + i] = v[c];
+    }
+    if (diff) *changed = 1;
 }
 
 template <typename T>
@@ -405,6 +421,7 @@ mm_status mm_create(const mm_grid* grid, const mm_material* mat, const mm_config
     TRY(alloc(c, (void**)&c->d_state, sizeof(DevState), "device state"));
     c->red_cap = 2 * 304 + 32;
     TRY(alloc(c, (void**)&c->d_red, sizeof(double) * c->red_cap, "reduction partials"));
+    TRY(alloc(c, (void**)&c->d_flag, sizeof(int), "state flag"));
     if (c->terms & MM_TERM_DEMAG) {
         TRY(alloc(c, &c->d_hd, vb, "demag field"));
         TRY(demag_setup(c));
@@ -534,6 +551,7 @@ mm_status mm_create_batch(int R, const mm_grid* grids, const mm_material* mat, c
     TRY(alloc(c, (void**)&c->d_state, sizeof(DevState), "device state"));
     c->red_cap = 2 * 304 + 32;
     TRY(alloc(c, (void**)&c->d_red, sizeof(double) * c->red_cap, "reduction partials"));
+    TRY(alloc(c, (void**)&c->d_flag, sizeof(int), "state flag"));
     c->batch = batch_new();
     TRY(batch_setup(c, c->batch, c->rgrid, c->rkey, (c->terms & MM_TERM_DEMAG) != 0));
     TRY(batch_upload(c, c->batch, c->rT, c->rJ));
@@ -649,17 +667,21 @@ mm_status mm_set_m(mm_ctx* c, int r, const double* m) {
     }
     const unsigned nb = (unsigned)((c->N + 255) / 256);
     const uint8_t* reg = c->uniform ? nullptr : (const uint8_t*)c->d_region;
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream);
     if (e == cudaSuccess) {
         if (c->prec == 32)
             state_in_kernel<float><<<nb, 256, 0, c->stream>>>(src, c->N, reg, (const Region<float>*)c->d_lut,
-                                                             (float*)c->d_m);
+                                                             (float*)c->d_m, c->d_flag);
         else
             state_in_kernel<double><<<nb, 256, 0, c->stream>>>(src, c->N, reg, (const Region<double>*)c->d_lut,
-                                                              (double*)c->d_m);
+                                                              (double*)c->d_m, c->d_flag);
         e = cudaGetLastError();
     }
+    int changed = 1;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&changed, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    c->k1_valid = false;
+    // the first-same-as-last slope stays valid only for the very same state
+    if (e != cudaSuccess || changed) c->k1_valid = false;
     return cuda_check(c, e, "mm_set_m");
 }
 

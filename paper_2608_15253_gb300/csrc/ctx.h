@@ -156,6 +156,7 @@ struct mm_ctx {
     double* d_replay = nullptr;
     size_t replay_cap = 0;
     double* d_red = nullptr;    // reduction partials
+    int* d_flag = nullptr;      // one device int (mm_set_m: did the state change)
     size_t red_cap = 0;
 
     mm::DemagPlan dm;

@@ -221,3 +221,48 @@ def test_rk4_rejects_finite_temperature():
     name, grid, mat, B = CASES[0]
     with pytest.raises(mm.MMError):
         make_ctx(mm, grid, mat, precision=32, integrator="rk4", demag=False, T=300.0)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_state_written_back_unchanged_keeps_the_fsal_slope(prec):
+    """mm_set_m with the state mm_get_m just returned leaves the state bit for
+    bit as it was, so the next RK45 step keeps its first-same-as-last slope:
+    it launches fewer kernels than the same step after a real change (one
+    cell turned), and the trajectory equals one that never left the device."""
+    mm = need_gpu()
+    grid = W.Grid(32, 16, 4, 3e-9, 3e-9, 3e-9)
+    mat = W.Material(Ms=8e5, A=1.3e-11, alpha=0.02)
+    m0 = W.m_random_sphere(grid, seed=12)
+    dts = np.full(1, 2e-14)
+    ctx = make_ctx(mm, grid, mat, precision=prec, dt=2e-14)
+    try:
+        mm.mm_set_m(ctx, 0, m0)
+        mm.mm_step_dt(ctx, np.full(4, 2e-14))
+        m = mm.mm_get_m(ctx, 0, m0.shape)
+        s0 = mm.mm_get_stats(ctx)
+        mm.mm_set_m(ctx, 0, m)
+        mm.mm_step_dt(ctx, dts)
+        s1 = mm.mm_get_stats(ctx)
+        m2 = mm.mm_get_m(ctx, 0, m0.shape)
+        m2[:, 0, 0, 0] = [0.0, 0.0, 1.0]
+        mm.mm_set_m(ctx, 0, m2)
+        mm.mm_step_dt(ctx, dts)
+        s2 = mm.mm_get_stats(ctx)
+        same = s1["kernel_launches"] - s0["kernel_launches"]
+        changed = s2["kernel_launches"] - s1["kernel_launches"]
+        assert changed > same, (same, changed)
+    finally:
+        mm.mm_destroy(ctx)
+    res = []
+    for roundtrip in (False, True):
+        ctx = make_ctx(mm, grid, mat, precision=prec, dt=2e-14)
+        try:
+            mm.mm_set_m(ctx, 0, m0)
+            mm.mm_step_dt(ctx, np.full(4, 2e-14))
+            if roundtrip:
+                mm.mm_set_m(ctx, 0, mm.mm_get_m(ctx, 0, m0.shape))
+            mm.mm_step_dt(ctx, np.full(3, 2e-14))
+            res.append(mm.mm_get_m(ctx, 0, m0.shape))
+        finally:
+            mm.mm_destroy(ctx)
+    assert np.array_equal(res[0], res[1])
