@@ -1155,14 +1155,15 @@ static void launch_x(mm_ctx* c, bool forward, const T* in, T* out_real, cplx<T>*
             return;
         }
         if (!forward && stage == 0 && x_c2r_pipe_kernel(Lh) && c->dm.Wk % 2 == 0) {
-            static int occ[1024] = {};
-            if (!occ[Lh]) {
+            static int occ_by_len[2] = {0, 0};     // Lh = 256, 512
+            int& occ = occ_by_len[Lh == 512 ? 1 : 0];
+            if (!occ) {
                 int o = 0;
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, x_c2r_pipe_kernel(Lh), 32 * kXW,
                                                               x_c2r_pipe_smem(Lh));
-                occ[Lh] = std::max(1, o);
+                occ = std::max(1, o);
             }
-            const int grid = std::max(1, std::min((rows + kXW - 1) / kXW, occ[Lh] * sm_count()));
+            const int grid = std::max(1, std::min((rows + kXW - 1) / kXW, occ * sm_count()));
             LaunchScope ls(c, "fft_x_c2r", (double)rows * (nx * sizeof(T) + (Lh + 1) * sizeof(cplx<T>)));
             x_c2r_pipe_kernel(Lh)<<<grid, 32 * kXW, x_c2r_pipe_smem(Lh), c->stream>>>(a);
             return;
