@@ -233,12 +233,14 @@ def test_newell_far_band_against_the_far_field_expansion():
 
 def test_skyrmion_film_512x512_replay_fp32():
     """The 512x512x1 DMI film (the surrogate workload's exact path: one-row-per-
-    warp X passes, stage combine fused into them) against the oracle."""
+    warp X passes with the stage combine fused in, the fused inverse-X +
+    field kernel) against the oracle after 10 of the oracle's accepted RK45
+    steps, replayed."""
     mm = need_gpu()
     w = W.skyrmion_512()
     m0 = W.m_skyrmion_lattice(w.grid, seed=w.seed, spacing=40e-9, radius=8e-9)
     o, p = _solver(w, m0, dt=1e-14, rtol=w.rtol)
-    dts = [o.rk45_step() for _ in range(3)]
+    dts = [o.rk45_step() for _ in range(10)]
     ctx = make_ctx(mm, w.grid, w.mat, precision=32, demag=True, B=w.B_ext, dt=1e-14, rtol=w.rtol)
     try:
         mm.mm_set_m(ctx, 0, m0)
