@@ -90,7 +90,8 @@ def test_gradients_match_oracle():
         t = rng.normal(size=(2, 3, 24, 40))
         loss, g = mm.mm_surrogate_grad(ctx, x, t, path=0)
         loss1, g1 = mm.mm_surrogate_grad(ctx, x, t, path=1)
-        assert loss1 == loss
+        # the loss is an FP64 sum of atomics: equal up to the order of addition
+        assert abs(loss1 - loss) <= 1e-12 * abs(loss), (loss, loss1)
         # same BF16 operands, FP32 sums in another order
         assert np.abs(g - g1).max() <= 1e-4 * np.abs(g1).max(), np.abs(g - g1).max() / np.abs(g1).max()
         params = _params_from_flat(flat)
