@@ -530,8 +530,9 @@ __global__ void dweight_kernel(const __nv_bfloat16* __restrict__ dz, int CZ, int
 // whole kernel: M = 128 rows of (copy, channel) (copies 0..3 then 4..7 when
 // X has 32 channels, 0..7 when it has 16), N = 5 dZ rows x CZ channels.
 // Copy 5 is all ones, so its rows collect the bias gradient; copies 6 and 7
-// are not stored (their operand rows read on into the next buffer, and
-// their rows of D are never used).  dZ rows sit in a ring of 7 slots (a
+// are not stored (their operand rows read on past the buffer -- into the
+// next one, or the dZ ring after the last -- and their rows of D are never
+// used).  dZ rows sit in a ring of 7 slots (a
 // window that wraps takes two MMAs); the row copies are triple buffered:
 // row R's MMAs are issued, then the CTA waits for row R - 1's and loads the
 // copies of row R + 2 (and dZ row R + 4) into what row R - 1 used, so every
