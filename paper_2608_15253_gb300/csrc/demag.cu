@@ -381,10 +381,15 @@ template <int LT, int S>
 __global__ void __launch_bounds__(32 * kXW, 4) fft_x_r2c_warp_kernel(XArgs<float> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (S > 0 && !a.st->active) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * kXW + warp;
-    if (row >= a.rows) return;                  // whole warp: no CTA barrier below
-    float2* sm = reinterpret_cast<float2*>(smem_raw) + warp * wline(LT);
+    // a group of GW lanes per row (a warp takes 32 / GW rows of a short line)
+    constexpr int GW = warp_group(LT), RPW = 32 / GW;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & (GW - 1);
+    const int wrow = (blockIdx.x * kXW + warp) * RPW;
+    if (wrow >= a.rows) return;                 // whole warp: no CTA barrier below
+    const int slot = warp * RPW + (threadIdx.x & 31) / GW;
+    const bool rvalid = wrow + (threadIdx.x & 31) / GW < a.rows;
+    const int row = rvalid ? wrow + (threadIdx.x & 31) / GW : wrow;   // a spare group repeats the first row
+    float2* sm = reinterpret_cast<float2*>(smem_raw) + slot * wline(LT);
     constexpr int NP = ct_npass(LT);
     const int nin = (a.nx + 1) / 2;
     const long long g0 = (long long)row * a.in_pitch;
@@ -398,7 +403,7 @@ __global__ void __launch_bounds__(32 * kXW, 4) fft_x_r2c_warp_kernel(XArgs<float
             const bool has_y = 2 * n + 1 < a.nx;
             if constexpr (S > 0) {
                 z = stage_pair<S>(a, cf, kf, q);
-                *reinterpret_cast<float2*>(a.ms + q) = z;
+                if (rvalid) *reinterpret_cast<float2*>(a.ms + q) = z;
             } else if (vec2) {
                 z = *reinterpret_cast<const float2*>(a.in + q);
             } else {
@@ -415,30 +420,35 @@ __global__ void __launch_bounds__(32 * kXW, 4) fft_x_r2c_warp_kernel(XArgs<float
         }
         return z;
     };
-    warp_pass<float, 1, LT, ct_radix(LT, 0), 1>(a.tw, 2, load_in, [&](int i, float2 v) { sm[wpad(i)] = v; });
-    warp_fft_smem<float, 1, LT, 1, NP>(sm, a.tw, 2);
+    warp_pass<float, 1, LT, ct_radix(LT, 0), 1, GW>(a.tw, 2, load_in, [&](int i, float2 v) { sm[wpad(i)] = v; });
+    warp_fft_smem<float, 1, LT, 1, NP, GW>(sm, a.tw, 2);
     constexpr int M = LT, Kx = LT + 1;
     float2* out = a.spec + spec_row(a, row) * a.Wk;
-    for (int k = lane; k < Kx; k += 32) {
+    for (int k = lane; k < Kx; k += GW) {
         const float2 zk = sm[wpad(k == M ? 0 : k)];
         const float2 zc = cconj<float>(sm[wpad(k == 0 ? 0 : M - k)]);
         const float2 E = cscale<float>(cadd<float>(zk, zc), 0.5f);
         const float2 O = cscale<float>(mul_mi<float, 1>(csub<float>(zk, zc)), 0.5f);
-        out[k] = cadd<float>(E, cmul<float>(__ldg(&a.tw[k]), O));
+        if (rvalid) out[k] = cadd<float>(E, cmul<float>(__ldg(&a.tw[k]), O));
     }
 }
 
 template <int LT>
 __global__ void __launch_bounds__(32 * kXW) fft_x_c2r_warp_kernel(XArgs<float> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int GW = warp_group(LT), RPW = 32 / GW;
     const int warp = threadIdx.x >> 5;
-    const int row = blockIdx.x * kXW + warp;
-    if (row >= a.rows) return;
-    float2* sm = reinterpret_cast<float2*>(smem_raw) + warp * wline(LT);
+    const int wrow = (blockIdx.x * kXW + warp) * RPW;
+    if (wrow >= a.rows) return;                 // whole warp
+    const int slot = warp * RPW + (threadIdx.x & 31) / GW;
+    const bool rvalid = wrow + (threadIdx.x & 31) / GW < a.rows;
+    const int row = rvalid ? wrow + (threadIdx.x & 31) / GW : wrow;   // a spare group repeats the first row
+    float2* sm = reinterpret_cast<float2*>(smem_raw) + slot * wline(LT);
     float* out = a.out_real + (long long)row * a.in_pitch;
     const bool vec2 = (a.nx % 2 == 0) && (a.in_pitch % 2 == 0);
     const int nx = a.nx;
-    warp_c2r<LT>(a.spec + spec_row(a, row) * a.Wk, a.tw, sm, [&](int n, float2 v) {
+    warp_c2r<LT, GW>(a.spec + spec_row(a, row) * a.Wk, a.tw, sm, [&](int n, float2 v) {
+        if (!rvalid) return;
         if (2 * n + 1 < nx) {
             if (vec2) *reinterpret_cast<float2*>(out + 2 * n) = v;
             else { out[2 * n] = v.x; out[2 * n + 1] = v.y; }
@@ -1040,6 +1050,17 @@ static CKern<T> col_kernel(int L) {
     return fft_col_kernel<T, MODE, 0>;
 }
 
+// lanes per row of the one-row-per-warp kernels (warp_group of the length)
+static int x_warp_group(int Lh) {
+    switch (Lh) {
+#define MM_CASE(n) case n: return warp_group(n);
+        MM_CASE(64) MM_CASE(96) MM_CASE(128) MM_CASE(192) MM_CASE(216) MM_CASE(256) MM_CASE(324) MM_CASE(432)
+        MM_CASE(512)
+#undef MM_CASE
+        default: return 32;
+    }
+}
+
 static XKern<float> x_warp_kernel(bool fwd, int Lh) {
     switch (Lh) {
 #define MM_CASE(n) case n: return fwd ? fft_x_r2c_warp_kernel<n, 0> : fft_x_c2r_warp_kernel<n>;
@@ -1172,10 +1193,11 @@ static void launch_x(mm_ctx* c, bool forward, const T* in, T* out_real, cplx<T>*
         // stage to form they are only used through x_stage_kernel above
         XKern<float> wk = stage == 0 ? x_warp_kernel(forward, Lh) : nullptr;
         if (wk) {
-            const size_t smem = (size_t)kXW * wline(Lh) * sizeof(float2);
+            const int rpc = kXW * (32 / x_warp_group(Lh));      // rows per CTA
+            const size_t smem = (size_t)rpc * wline(Lh) * sizeof(float2);
             LaunchScope ls(c, forward ? "fft_x_r2c" : "fft_x_c2r",
                            (double)rows * (nx * sizeof(T) + (Lh + 1) * sizeof(cplx<T>)));
-            wk<<<(rows + kXW - 1) / kXW, 32 * kXW, smem, c->stream>>>(a);
+            wk<<<(rows + rpc - 1) / rpc, 32 * kXW, smem, c->stream>>>(a);
             return;
         }
     }

@@ -183,25 +183,38 @@ __device__ __forceinline__ void cd_fft(cplx<T>* sm, const cplx<T>* gin, cplx<T>*
 }
 
 // ---------------------------------------------------------------------------
-// One line per warp.  The line lives in warp-private shared memory with one
-// pad slot every 8 entries (index i at wpad(i)), which keeps the stride-R
-// writes of the early Stockham passes free of bank conflicts; passes are
-// separated by __syncwarp only, so warps never wait on each other.
+// One line per warp, or per group of GW lanes when the line is short (a
+// warp then transforms 32 / GW lines at once, so that the passes' NB
+// butterflies fill its lanes).  The line lives in warp-private shared memory
+// with one pad slot every 8 entries (index i at wpad(i)), which keeps the
+// stride-R writes of the early Stockham passes free of bank conflicts;
+// passes are separated by __syncwarp only, so warps never wait on each
+// other.
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int wpad(int i) { return i + (i >> 3); }
 __host__ __device__ constexpr int wline(int L) { return wpad(L) + 1; }
 
-template <typename T, int DIR, int L, int R, int NS, typename Load, typename Store>
+// lanes per line: the smallest power of two that covers the narrowest pass
+// of the plan (at most 32)
+__host__ __device__ constexpr int warp_group(int L) {
+    int nb = L;
+    for (int p = 0; p < ct_npass(L); ++p) nb = L / ct_radix(L, p) < nb ? L / ct_radix(L, p) : nb;
+    int g = 1;
+    while (g < nb && g < 32) g *= 2;
+    return g;
+}
+
+template <typename T, int DIR, int L, int R, int NS, int GW = 32, typename Load, typename Store>
 __device__ __forceinline__ void warp_pass(const cplx<T>* __restrict__ tw, int tws, Load load, Store store) {
     constexpr int NB = L / R;
     constexpr int SPAN = L / (NS * R);
-    constexpr int NBL = (NB + 31) / 32;
-    const int lane = threadIdx.x & 31;
+    constexpr int NBL = (NB + GW - 1) / GW;
+    const int lane = threadIdx.x & (GW - 1);
     cplx<T> v[NBL][R];
 #pragma unroll
     for (int i = 0; i < NBL; ++i) {
-        const int j = lane + 32 * i;
-        if (NB % 32 == 0 || j < NB) {
+        const int j = lane + GW * i;
+        if (NB % GW == 0 || j < NB) {
 #pragma unroll
             for (int t = 0; t < R; ++t) v[i][t] = load(j + t * NB);
         }
@@ -209,8 +222,8 @@ __device__ __forceinline__ void warp_pass(const cplx<T>* __restrict__ tw, int tw
     __syncwarp();
 #pragma unroll
     for (int i = 0; i < NBL; ++i) {
-        const int j = lane + 32 * i;
-        if (NB % 32 != 0 && j >= NB) continue;
+        const int j = lane + GW * i;
+        if (NB % GW != 0 && j >= NB) continue;
         const int k = j % NS;
         if constexpr (NS > 1) {
 #pragma unroll
@@ -227,15 +240,16 @@ __device__ __forceinline__ void warp_pass(const cplx<T>* __restrict__ tw, int tw
     __syncwarp();
 }
 
-// Passes P .. PEND-1 of a warp's line, all shared memory -> shared memory.
-template <typename T, int DIR, int L, int P, int PEND>
+// Passes P .. PEND-1 of a warp's (or lane group's) line, all shared memory
+// -> shared memory.
+template <typename T, int DIR, int L, int P, int PEND, int GW = 32>
 __device__ __forceinline__ void warp_fft_smem(cplx<T>* sm, const cplx<T>* __restrict__ tw, int tws) {
     if constexpr (P < PEND) {
         constexpr int R = ct_radix(L, P);
         constexpr int NS = ct_ns(L, P);
-        warp_pass<T, DIR, L, R, NS>(tw, tws, [&](int i) { return sm[wpad(i)]; },
-                                    [&](int i, cplx<T> v) { sm[wpad(i)] = v; });
-        warp_fft_smem<T, DIR, L, P + 1, PEND>(sm, tw, tws);
+        warp_pass<T, DIR, L, R, NS, GW>(tw, tws, [&](int i) { return sm[wpad(i)]; },
+                                        [&](int i, cplx<T> v) { sm[wpad(i)] = v; });
+        warp_fft_smem<T, DIR, L, P + 1, PEND, GW>(sm, tw, tws);
     }
 }
 
@@ -245,7 +259,7 @@ __device__ __forceinline__ void warp_fft_smem(cplx<T>* sm, const cplx<T>* __rest
 // rebuild Z'[k] = (X[k] + conj X[M-k]) + i (X[k] - conj X[M-k]) conj(W^k)
 // feeds the first pass; the last pass goes straight to the store.  sm is
 // the warp's line of wline(LT) values; tw = exp(-2 pi i q / 2M).
-template <int LT, typename Store>
+template <int LT, int GW = 32, typename Store>
 __device__ __forceinline__ void warp_c2r(const float2* __restrict__ X, const float2* __restrict__ tw, float2* sm,
                                          Store store) {
     constexpr int NP = ct_npass(LT), M = LT;
@@ -258,10 +272,10 @@ __device__ __forceinline__ void warp_c2r(const float2* __restrict__ X, const flo
         return cadd<float>(E, mul_mi<float, -1>(O));
     };
     auto to_smem = [&](int i, float2 v) { sm[wpad(i)] = v; };
-    warp_pass<float, -1, LT, ct_radix(LT, 0), 1>(tw, 2, load_rebuild, to_smem);
-    warp_fft_smem<float, -1, LT, 1, NP - 1>(sm, tw, 2);
-    warp_pass<float, -1, LT, ct_radix(LT, NP - 1), ct_ns(LT, NP - 1)>(tw, 2, [&](int i) { return sm[wpad(i)]; },
-                                                                      store);
+    warp_pass<float, -1, LT, ct_radix(LT, 0), 1, GW>(tw, 2, load_rebuild, to_smem);
+    warp_fft_smem<float, -1, LT, 1, NP - 1, GW>(sm, tw, 2);
+    warp_pass<float, -1, LT, ct_radix(LT, NP - 1), ct_ns(LT, NP - 1), GW>(tw, 2,
+                                                                          [&](int i) { return sm[wpad(i)]; }, store);
 }
 
 // The same inverse real transform with the half spectrum already in the
