@@ -1054,7 +1054,7 @@ static CKern<T> col_kernel(int L) {
 static int x_warp_group(int Lh) {
     switch (Lh) {
 #define MM_CASE(n) case n: return warp_group(n);
-        MM_CASE(64) MM_CASE(96) MM_CASE(128) MM_CASE(192) MM_CASE(216) MM_CASE(256) MM_CASE(324) MM_CASE(432)
+        MM_CASE(32) MM_CASE(48) MM_CASE(64) MM_CASE(96) MM_CASE(128) MM_CASE(192) MM_CASE(216) MM_CASE(256) MM_CASE(324) MM_CASE(432)
         MM_CASE(512)
 #undef MM_CASE
         default: return 32;
@@ -1064,7 +1064,7 @@ static int x_warp_group(int Lh) {
 static XKern<float> x_warp_kernel(bool fwd, int Lh) {
     switch (Lh) {
 #define MM_CASE(n) case n: return fwd ? fft_x_r2c_warp_kernel<n, 0> : fft_x_c2r_warp_kernel<n>;
-        MM_CASE(64) MM_CASE(96) MM_CASE(128) MM_CASE(192) MM_CASE(216) MM_CASE(256) MM_CASE(324) MM_CASE(432)
+        MM_CASE(32) MM_CASE(48) MM_CASE(64) MM_CASE(96) MM_CASE(128) MM_CASE(192) MM_CASE(216) MM_CASE(256) MM_CASE(324) MM_CASE(432)
         MM_CASE(512)
 #undef MM_CASE
         default: return nullptr;
