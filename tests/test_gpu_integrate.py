@@ -39,6 +39,9 @@ CASES = [
     # runs inside the field kernel (H_demag stays in shared memory)
     ("c2r_field", W.Grid(128, 6, 2, 2e-9, 2e-9, 2e-9),
      W.Material(Ms=5.8e5, A=1.5e-11, alpha=0.1, Ku1=8e5, u=(0, 0, 1), D=3e-3), (0.01, 0.0, 0.02)),
+    # the same kernel with a ragged last CTA: 7 rows, CTAs of 4 rows
+    ("c2r_field_ragged", W.Grid(128, 7, 1, 2e-9, 2e-9, 2e-9),
+     W.Material(Ms=5.8e5, A=1.5e-11, alpha=0.1, Ku1=8e5, u=(0, 0, 1), D=3e-3), (0.0, 0.01, 0.02)),
 ]
 
 
