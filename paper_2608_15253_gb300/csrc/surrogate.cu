@@ -137,8 +137,6 @@ void surrogate_free(mm_ctx* c) {
     c->surr = nullptr;
 }
 
-static mm_status scheck(mm_ctx* c, cudaError_t e, const char* what) { return cuda_check(c, e, what); }
-
 static mm_status ensure_surrogate(mm_ctx* c) {
     if (c->surr) return MM_OK;
     if (c->batch || c->prec != 32 || c->grid.nz != 1 || !c->dm.on)
@@ -216,8 +214,16 @@ static mm_status ensure_buffers(mm_ctx* c, int B, int H, int W) {
     SurrogateHost* s = c->surr;
     if (B <= s->cB && H == s->cH && W == s->cW) return MM_OK;
     surrogate_invalidate_graph(c);   // the captured attempt holds the old buffers
-    void* ptrs[] = {s->x0, s->h1, s->h2, s->h3, s->dy, s->dza, s->dzb, s->y, s->t};
-    for (void* p : ptrs) cudaFree(p);
+    void** ptrs[] = {(void**)&s->x0, (void**)&s->h1, (void**)&s->h2, (void**)&s->h3, (void**)&s->dy,
+                     (void**)&s->dza, (void**)&s->dzb, (void**)&s->y, (void**)&s->t};
+    auto release = [&] {
+        for (void** p : ptrs) {
+            cudaFree(*p);
+            *p = nullptr;
+        }
+        s->cB = s->cH = s->cW = 0;
+    };
+    release();
     const size_t pp = (size_t)B * (H + 4) * (W + 4);
     cudaError_t e = cudaSuccess;
     auto A = [&](void** p, size_t b) { if (e == cudaSuccess) e = cudaMalloc(p, b); if (e == cudaSuccess) e = cudaMemset(*p, 0, b); };
@@ -230,10 +236,14 @@ static mm_status ensure_buffers(mm_ctx* c, int B, int H, int W) {
     A((void**)&s->dzb, pp * 32 * 2);
     A((void**)&s->y, (size_t)B * H * W * 3 * 4);
     A((void**)&s->t, (size_t)B * H * W * 3 * 4);
+    if (e != cudaSuccess) {
+        release();   // no shape is recorded for a partial set
+        return cuda_check(c, e, "surrogate activations");
+    }
     s->cB = B;
     s->cH = H;
     s->cW = W;
-    return cuda_check(c, e, "surrogate activations");
+    return MM_OK;
 }
 
 static void pack_all(mm_ctx* c) {
@@ -621,15 +631,29 @@ mm_status mm_surrogate_train(mm_ctx* c, const mm_train_cfg* cfg, double* final_l
     if (st != MM_OK) return st;
     const int k_saved = s->k;
     s->k = 0;
+    float *snaps = nullptr, *dm = nullptr, *dh = nullptr;
+    int* d_idx = nullptr;
+    // every exit from here on: free the scratch buffers, restore the
+    // stepping mode and the caller's state (the first error is returned)
+    auto finish = [&](mm_status r) {
+        cudaFree(snaps);
+        cudaFree(dm);
+        cudaFree(dh);
+        cudaFree(d_idx);
+        s->k = k_saved;
+        s->ref_valid = false;
+        surrogate_invalidate_graph(c);
+        const mm_status rs = mm_set_state(c, ck.data(), nb);
+        return r != MM_OK ? r : rs;
+    };
     // snapshots of an exact relaxation
     const int ns = cfg->n_snapshots;
-    float* snaps = nullptr;
     cudaError_t e = cudaMalloc(&snaps, sizeof(float) * fe * ns);
-    if (e != cudaSuccess) return cuda_check(c, e, "snapshots");
+    if (e != cudaSuccess) return finish(cuda_check(c, e, "snapshots"));
     for (int q = 0; q < ns; ++q) {
         if (q > 0) {
             st = mm_step(c, cfg->snap_every);
-            if (st != MM_OK) { cudaFree(snaps); return st; }
+            if (st != MM_OK) return finish(st);
         }
         cudaMemcpyAsync(snaps + q * fe, c->d_m, sizeof(float) * fe, cudaMemcpyDeviceToDevice, c->stream);
     }
@@ -637,13 +661,9 @@ mm_status mm_surrogate_train(mm_ctx* c, const mm_train_cfg* cfg, double* final_l
     for (int i = 0; i < ns; ++i)
         for (int j = i + 1; j < ns && j - i <= cfg->max_gap; ++j) pairs.push_back({i, j});
     const int np = (int)pairs.size();
-    float *dm = nullptr, *dh = nullptr;
     e = cudaMalloc(&dm, sizeof(float) * fe * np);
     if (e == cudaSuccess) e = cudaMalloc(&dh, sizeof(float) * fe * np);
-    if (e != cudaSuccess) {
-        cudaFree(snaps); cudaFree(dm); cudaFree(dh);
-        return cuda_check(c, e, "training pairs");
-    }
+    if (e != cudaSuccess) return finish(cuda_check(c, e, "training pairs"));
     const unsigned gb = (unsigned)((fe + 255) / 256);
     for (int q = 0; q < np; ++q) {
         diff_kernel<<<gb, 256, 0, c->stream>>>(snaps + pairs[q].second * fe, snaps + pairs[q].first * fe, fe, dm + q * fe);
@@ -656,8 +676,9 @@ mm_status mm_surrogate_train(mm_ctx* c, const mm_train_cfg* cfg, double* final_l
     double ss = 0;
     cudaMemcpyAsync(&ss, s->d_red, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     e = cudaStreamSynchronize(c->stream);
-    cudaFree(snaps);
-    if (e != cudaSuccess) { cudaFree(dm); cudaFree(dh); return cuda_check(c, e, "training data"); }
+    if (e != cudaSuccess) return finish(cuda_check(c, e, "training data"));
+    cudaFree(snaps);   // the pairs hold what training needs
+    snaps = nullptr;
     const double rms = std::sqrt(ss / (double)(fe * np));
     s->c_in = rms > 0 ? (float)(1.0 / rms) : 1.f;
     // output scale: unit rms targets (the far-field residual is much smaller than dm)
@@ -666,16 +687,16 @@ mm_status mm_surrogate_train(mm_ctx* c, const mm_train_cfg* cfg, double* final_l
     double sr = 0;
     cudaMemcpyAsync(&sr, s->d_red, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) { cudaFree(dm); cudaFree(dh); return cuda_check(c, e, "training targets"); }
+    if (e != cudaSuccess) return finish(cuda_check(c, e, "training targets"));
     const double rr = std::sqrt(sr / (double)(fe * np)) / c->regions[0].Ms;
     s->c_out = rr > 0 ? (float)(1.0 / rr) : 1.f;
     if (!s->have_weights) set_he_init(c, cfg->seed);
     pack_all(c);
     const int B = cfg->batch;
     st = ensure_buffers(c, B, S, S);
-    if (st != MM_OK) { cudaFree(dm); cudaFree(dh); return st; }
-    int* d_idx = nullptr;
-    cudaMalloc(&d_idx, sizeof(int) * 3 * B);
+    if (st != MM_OK) return finish(st);
+    e = cudaMalloc(&d_idx, sizeof(int) * 3 * B);
+    if (e != cudaSuccess) return finish(cuda_check(c, e, "training indices"));
     std::mt19937_64 gen(cfg->seed ^ 0x5DEECE66Dull);
     std::vector<int> idx(3 * B);
     const float inv_ms = (float)(1.0 / c->regions[0].Ms);
@@ -702,17 +723,11 @@ mm_status mm_surrogate_train(mm_ctx* c, const mm_train_cfg* cfg, double* final_l
         }
     }
     e = cudaStreamSynchronize(c->stream);
-    cudaFree(d_idx);
-    cudaFree(dm);
-    cudaFree(dh);
-    if (e != cudaSuccess) return cuda_check(c, e, "surrogate training");
+    if (e != cudaSuccess) return finish(cuda_check(c, e, "surrogate training"));
     const bool timed_out = take_timeout(c);
     s->train_loss = loss;
-    surrogate_invalidate_graph(c);
     if (final_loss) *final_loss = loss;
-    s->k = k_saved;
-    s->ref_valid = false;
-    st = mm_set_state(c, ck.data(), nb);
+    st = finish(MM_OK);
     if (st == MM_OK && timed_out) return set_error(c, MM_ERR_TIMEOUT, "tensor-core accumulator wait ran out");
     return st;
 }
@@ -723,10 +738,18 @@ mm_status mm_surrogate_set(mm_ctx* c, int k, double tol) {
     if (st != MM_OK) return st;
     SurrogateHost* s = c->surr;
     if (k > 0 && !s->have_weights) return set_error(c, MM_ERR_STATE, "train or set the surrogate weights first");
-    if (k > 0 && !s->d_mref) {
+    if (k > 0 && !(s->d_mref && s->d_href)) {
+        cudaFree(s->d_mref);
+        cudaFree(s->d_href);
+        s->d_mref = s->d_href = nullptr;
         cudaError_t e = cudaMalloc(&s->d_mref, sizeof(float) * 3 * c->N);
         if (e == cudaSuccess) e = cudaMalloc(&s->d_href, sizeof(float) * 3 * c->N);
-        if (e != cudaSuccess) return cuda_check(c, e, "surrogate reference");
+        if (e != cudaSuccess) {
+            cudaFree(s->d_mref);
+            cudaFree(s->d_href);
+            s->d_mref = s->d_href = nullptr;
+            return cuda_check(c, e, "surrogate reference");
+        }
         st = ensure_buffers(c, 1, c->grid.ny, c->grid.nx);
         if (st != MM_OK) return st;
     }
