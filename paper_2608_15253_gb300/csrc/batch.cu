@@ -478,10 +478,20 @@ void batch_set_shape(BatchHost* b, int nt, int blocks) {
         for (size_t q = 0; q < b->ch.size() && ok; ++q) {
             ClassHost& k = b->ch[q];
             const DemagPlan& p = b->plans[q];
-            if (!p.on || k.S) continue;
+            if (!p.on || (k.S && k.Hd)) continue;
+            cudaFree(k.S);
+            cudaFree(k.Hd);
+            k.S = nullptr;
+            k.Hd = nullptr;
             const size_t sb = sizeof(float2) * (size_t)k.Rc * 3 * p.PyA * p.Wk;
             const size_t hb = sizeof(float) * (size_t)k.Rc * 3 * k.nx * k.ny;
             ok = cudaMalloc(&k.S, sb) == cudaSuccess && cudaMalloc(&k.Hd, hb) == cudaSuccess;
+            if (!ok) {   // neither half of a pair is kept
+                cudaFree(k.S);
+                cudaFree(k.Hd);
+                k.S = nullptr;
+                k.Hd = nullptr;
+            }
         }
         if (ok) {
             b->stacked = true;
