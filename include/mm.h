@@ -343,7 +343,10 @@ MM_API mm_status mm_get_stats(mm_ctx* ctx, mm_stats* st);
  * buf == NULL the required size is returned in *nbytes.  No passage:
  * boundary convenience (the paper has no checkpoint); resume is bit-exact
  * because the thermal stream is counter-based (Methods, "Replica
- * batching").  Errors: MM_ERR_ARG (buffer too small, foreign blob). */
+ * batching").  Errors: MM_ERR_ARG (buffer too small, foreign blob, or an
+ * integrator record that no run produces: slope slot other than 0 or 6,
+ * non-finite t, negative or non-finite dt), checked before anything is
+ * copied to the device. */
 MM_API mm_status mm_get_state(mm_ctx* ctx, void* buf, size_t* nbytes);
 MM_API mm_status mm_set_state(mm_ctx* ctx, const void* buf, size_t nbytes);
 

@@ -1282,6 +1282,11 @@ mm_status mm_set_state(mm_ctx* c, const void* buf, size_t nbytes) {
     const char* p = (const char*)buf;
     DevState st;
     memcpy(&st, p + sizeof h, sizeof st);
+    // the slope-slot index selects device pointers: a damaged blob must not
+    // reach the kernels
+    if ((st.k_first != 0 && st.k_first != 6) || (st.fsal != 0 && st.fsal != 1) || !std::isfinite(st.t) ||
+        !(st.dt >= 0) || !std::isfinite(st.dt))
+        return set_error(c, MM_ERR_ARG, "checkpoint integrator state is damaged");
     st.replay = 0;
     st.replay_dts = nullptr;
     c->h_state = st;
