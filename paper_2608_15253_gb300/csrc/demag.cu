@@ -1418,12 +1418,26 @@ static mm_status demag_setup_t(mm_ctx* c) {
     void* tw64x = make_twiddles<double>(d.Px);
     void* tw64y = make_twiddles<double>(d.Py);
     void* tw64z = make_twiddles<double>(d.Pz);
-    if (!d.tw_x || !d.tw_y || !d.tw_z || !tw64x || !tw64y || !tw64z) return set_error(c, MM_ERR_OOM, "twiddles");
+    auto free_tw64 = [&] {   // the FP64 setup twiddles live until the tensor is built
+        cudaFree(tw64x);
+        cudaFree(tw64y);
+        cudaFree(tw64z);
+    };
+    if (!d.tw_x || !d.tw_y || !d.tw_z || !tw64x || !tw64y || !tw64z) {
+        free_tw64();
+        return set_error(c, MM_ERR_OOM, "twiddles");
+    }
 
     const size_t spec_bytes = (size_t)3 * nz * d.PyA * d.Wk * sizeof(cplx<T>);
     const size_t khat_bytes = (size_t)d.ncomp * Kz * Ky * d.Wk * sizeof(T);
-    if (cudaMalloc(&d.spec, spec_bytes) != cudaSuccess) return set_error(c, MM_ERR_OOM, "demag spectrum");
-    if (cudaMalloc(&d.khat, khat_bytes) != cudaSuccess) return set_error(c, MM_ERR_OOM, "demag kernel");
+    if (cudaMalloc(&d.spec, spec_bytes) != cudaSuccess) {
+        free_tw64();
+        return set_error(c, MM_ERR_OOM, "demag spectrum");
+    }
+    if (cudaMalloc(&d.khat, khat_bytes) != cudaSuccess) {
+        free_tw64();
+        return set_error(c, MM_ERR_OOM, "demag kernel");
+    }
     cudaMemsetAsync(d.spec, 0, spec_bytes, c->stream);
 
     // FP64 Newell tensor on the non-negative octant
@@ -1437,6 +1451,7 @@ static mm_status demag_setup_t(mm_ctx* c) {
         cudaMalloc(&pad, sizeof(double) * P) != cudaSuccess ||
         cudaMalloc(&sp, sizeof(double2) * sp_elems) != cudaSuccess) {
         cudaFree(oct); cudaFree(pad); cudaFree(sp);
+        free_tw64();
         return set_error(c, MM_ERR_OOM, "demag setup scratch");
     }
     GLTable gl = make_gl();
@@ -1484,9 +1499,7 @@ static mm_status demag_setup_t(mm_ctx* c) {
     cudaFree(oct);
     cudaFree(pad);
     cudaFree(sp);
-    cudaFree(tw64x);
-    cudaFree(tw64y);
-    cudaFree(tw64z);
+    free_tw64();
     if (e != cudaSuccess) return cuda_check(c, e, "demag setup");
     d.on = 1;
     return MM_OK;
