@@ -84,6 +84,29 @@ def test_heun_second_order_and_dopri_fifth_order():
     assert all(4.6 < r < 6.5 for r in rate_d), rate_d
 
 
+def test_dopri_error_estimate_is_the_fourth_order_local_error():
+    """The embedded estimate |m5 - m4| that drives the step controller falls
+    as h^5 over one step (the local error of the 4th-order solution), while
+    the 5th-order solution's own local error against the closed form falls
+    as h^6 and stays well below the estimate (Dormand & Prince 1980: the
+    5th-order solution is propagated, the 4th-order one only measured).  A
+    wrong 4th-order weight lowers the estimate's order; a wrong stage or
+    5th-order weight lowers the local error's."""
+    alpha, H0 = 0.05, 5e5
+    p, m0 = _macrospin(alpha, H0)
+    errs, locs = [], []
+    for h in (2e-12, 1e-12, 5e-13):
+        s = Solver(p, m0, terms=("zeeman",))
+        m5, err, _ = s.dopri_attempt(h)
+        errs.append(err)
+        locs.append(np.abs(m5[:, 0, 0, 0] - _closed_form(h, alpha, H0, 1.0, 0.3)).max())
+    r_err = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    r_loc = [math.log2(locs[i] / locs[i + 1]) for i in range(2)]
+    assert all(4.8 < r < 5.2 for r in r_err), r_err
+    assert all(5.7 < r < 6.4 for r in r_loc), r_loc
+    assert all(loc < 0.1 * e for loc, e in zip(locs, errs)), (locs, errs)
+
+
 def test_rk4_fourth_order_on_the_macrospin():
     """Classical RK4 against the closed-form damped precession: halving the
     step divides the error by ~16."""
